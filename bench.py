@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark of the noisy-circuit hot path on GB300.
+
+Workload (default): batched Monte Carlo noisy QFT, n = 20 qubits, 1024
+complex64 trajectories with FP32 arithmetic, e = 0.01 (noisy Hadamards with
+the rotation noise of Eq. 1, noisy controlled phases theta -> theta + e xi),
+random basis input from the seed.  One step = set every trajectory to the
+input, run the 210-gate circuit (fused passes, CUDA graph), and read the 1024
+fidelities with the ideal output (FP64 reduction, read back to the host).
+
+Metric: amplitude-gate updates/s = trajectories * 2^n * gates / time.
+Prints one JSON line (rank 0).  --impl reference times the oracle (the plain
+complex128 CPU simulator) on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "amplitude-gate updates/s"
+UNIT = "updates/s"
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, which):
+        if which == 0:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [l for t, l in self.lines if self.t0 is not None and self.t0 - 0.1 <= t <= (self.t1 or t) + 0.1]
+        if not rows:
+            rows = [l for _, l in self.lines]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            f = [x.strip() for x in r.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def plan_source_hash():
+    h = hashlib.sha256()
+    for f in ("plan.cu", "internal.cuh", "philox.cuh"):
+        with open(os.path.join(ROOT, "paper_1412_2293_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kind):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except Exception:
+        return None
+    if t.get("source_hash") != plan_source_hash():
+        return None
+    v = t.get("kernels", {}).get(kind)
+    return None if v is None else float(v)
+
+
+def workload_setup(name):
+    from paper_1412_2293_gb300 import inputs
+    W = inputs.WORKLOADS[name]
+    ops = W.ops()
+    x0 = W.initial_basis()
+    return W, ops, x0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_1412_2293_gb300 import build as qbuild
+    from paper_1412_2293_gb300 import circuits as pcirc
+    from paper_1412_2293_gb300 import qs
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    qbuild.build()
+    W, ops, x0 = workload_setup(args.workload)
+    n, T, e, seed = W.n, W.trajectories, W.e, W.seed
+    dtype = qs.QS_C64 if W.dtype == "c64" else qs.QS_C128
+    esize = 8 if dtype == qs.QS_C64 else 16
+    stream = torch.cuda.Stream()
+    traj0 = rank * T                                    # weak scaling: each rank its own trajectories
+    h = qs.qs_create(n, T, 0, qs.QS_STATEVEC, dtype, stream)
+    ref = pcirc.ideal_reference(n, ops, x0, dtype, stream)
+    qs.qs_set_reference_from(h, ref, 0)
+    qs.qs_destroy(ref)
+    qs.qs_set_trajectory_offset(h, traj0)
+    p = qs.qs_plan_create(h, pcirc.to_gates(ops))
+    passes, launches = qs.qs_plan_info(p, h)
+    qs.qs_plan_set_timing(p, True, h)
+    updates_per_step = T * (1 << n) * len(ops)
+
+    def step():
+        qs.qs_set_basis_state(h, x0)
+        qs.qs_plan_run(p, e, seed, 0, h)
+        return qs.qs_fidelity_stored(h)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        fid = step()
+    # timed region: device time with CUDA events on the library's stream
+    kern = {}
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.mark(0)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        fid = step()
+        ms, kinds = qs.qs_plan_last_times(p, h=h)
+        for m, k in zip(ms, kinds):
+            kern.setdefault(k, []).append(m)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    if sampler:
+        sampler.mark(1)
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    value = updates_per_step * world / (ms_per_step / 1e3)
+    clocks = sampler.stop() if sampler else None
+
+    # end to end through the C ABI with host buffers: every step uploads the
+    # members' inputs (basis state, noise key, trajectory counter, e) from host
+    # memory and reads the fidelities back.
+    xs = np.full(T, x0, dtype=np.uint64)
+    e_arr = np.full(T, e, dtype=np.float64)
+    s_arr = np.full(T, seed, dtype=np.uint64)
+    t_arr = np.arange(traj0, traj0 + T, dtype=np.uint64)
+
+    def step_e2e():
+        qs.qs_set_member_noise(h, e_arr, s_arr, t_arr)
+        qs.qs_set_basis_states(h, xs)
+        qs.qs_plan_run(p, e, seed, 0, h)
+        return qs.qs_fidelity_stored(h)
+
+    qs.qs_plan_set_timing(p, False, h)
+    for _ in range(max(1, args.warmup)):
+        fid_e2e = step_e2e()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        fid_e2e = step_e2e()
+    torch.cuda.synchronize()
+    t_e2e = (time.perf_counter() - t0) / args.steps
+    if dist is not None:
+        t = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e_value = updates_per_step * world / t_e2e
+    assert np.allclose(fid_e2e, fid, atol=1e-6), "end-to-end run disagrees with the device-resident run"
+
+    # roofline of the dominant kernel (the fused pass with the most time)
+    peaks, peak_src = measured_peaks()
+    bytes_per_pass = 2 * T * (1 << n) * esize
+    dom = max((k for k in kern if k.startswith("pass")), key=lambda k: sum(kern[k]))
+    per_launch = {k: statistics.mean(v) for k, v in kern.items()}
+    # there are several launches of the same kind per step; each moves the state once
+    avg_ms = statistics.mean(kern[dom])
+    achieved = bytes_per_pass / (avg_ms / 1e3) / 1e9
+    traffic = ncu_traffic(dom)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+                "kernel": "k_pass_high" if dom == "pass_high" else "k_pass_low",
+                "algorithmic_bytes_per_launch": bytes_per_pass, "avg_launch_ms": round(avg_ms, 4),
+                "peak_source": f"{peak_src} hbm_gbs (copy bandwidth)",
+                "launch_ms_by_kind": {k: round(v, 4) for k, v in per_launch.items()}}
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if dtype == qs.QS_C64 else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "circuit": W.circuit, "n": n, "trajectories_per_gpu": T,
+                   "gates": len(ops), "e": e, "noise": "rotation (H), phase (CP), Philox on device",
+                   "passes_per_step": passes, "parallelism": f"trajectories sharded over {world} GPU(s)",
+                   "circuits_per_s": T * world / (ms_per_step / 1e3),
+                   "state_bytes": T * (1 << n) * esize,
+                   "l2": "inputs larger than L2 (state of every step is %d MiB)" % (T * (1 << n) * esize >> 20),
+                   "fidelity_mean": float(np.mean(fid)), "fidelity_min": float(np.min(fid))},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(xs.nbytes + e_arr.nbytes + s_arr.nbytes + t_arr.nbytes),
+                "d2h_bytes_per_step": int(fid.nbytes), "ms_per_step": t_e2e * 1e3},
+        "gpu_launches": args.steps * (launches + 1 + 2),
+        "roofline": roofline,
+    }
+    qs.qs_plan_destroy(p)
+    qs.qs_destroy(h)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(W, ops, x0)
+    if dist is not None:
+        dist.destroy_process_group()
+    return result
+
+
+def cpu_baseline(W, ops, x0):
+    """The oracle as it stands, on the host: one whole trajectory of the workload."""
+    from oracle import circuits as ocirc
+    t0 = time.perf_counter()
+    ocirc.run_trajectory(W.n, ops, x0, W.e, W.seed, 0)
+    dt = time.perf_counter() - t0
+    return {"value": (1 << W.n) * len(ops) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 of {W.trajectories} trajectories of {W.name} (complex128 NumPy, single thread), {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, rank, world):
+    """The oracle on the host cores, each step a slice of one trajectory's gates."""
+    import numpy as np
+
+    from oracle import circuits as ocirc
+    from oracle import gates as ogates
+    from oracle import philox as ophilox
+    from oracle import statevec as osv
+
+    if rank != 0:
+        return None
+    W, ops, x0 = workload_setup(args.workload)
+    n = W.n
+    slice_gates = 21
+    psi = osv.basis_state(n, x0)
+    pos = 0
+
+    def step():
+        nonlocal psi, pos
+        for _ in range(slice_gates):
+            g = pos % len(ops)
+            if g == 0:
+                psi = osv.basis_state(n, x0)
+            op = ops[g]
+            if op.kind == "FLIP":
+                psi = osv.phase_flip(psi, op.index)
+            else:
+                U = ocirc.op_unitary(op)
+                if op.noisy:
+                    xa, xb = ophilox.normal_pair(W.seed, 0, g)
+                    U = ogates.noisy_unitary(U, ocirc.op_noise(op), W.e, xa, xb)
+                psi = osv.apply_gate(psi, n, ocirc.op_targets(op), U)
+            pos += 1
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = (1 << n) * slice_gates / dt
+    sample = f"{slice_gates} consecutive gates of one trajectory of {W.name} per step (oracle, complex128 NumPy)"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "circuit": W.circuit, "n": n, "gates": len(ops), "e": W.e},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="mc_qft_n20_c64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local_rank = env_rank()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local_rank)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,259 @@
+/*
+ * qs.h -- C ABI of the GB300 noisy-circuit simulator hot path.
+ *
+ * The operations are those of Bogdanov et al., "Numerical and analytical
+ * research of the impact of decoherence on quantum circuits"
+ * (arXiv:1412.2293):
+ *   - the amplitude update of Sec. 2 (one qubit: b[..i_k..] =
+ *     u[i_k,0] a[..0..] + u[i_k,1] a[..1..]; k qubits likewise);
+ *   - Monte Carlo noisy gates, Sec. 2, Eqs. 1-2 (rotation V_noise(e xi) acting
+ *     before the gate, Eq. 5; controlled-phase angle theta -> theta + e xi,
+ *     Eqs. 7-8), xi ~ N(0,1) drawn on the device;
+ *   - the density matrix and quantum operations, Sec. 3, Eq. 3, in the
+ *     vectorised form (U (x) U*) vec(rho) of Sec. 3;
+ *   - the fixed-rank approximation of Sec. 3.2 (factor L, rho = L L^dagger,
+ *     Gram-matrix eigendecomposition, truncation to rank r);
+ *   - fidelity and trace reductions (Figs. 1-4, Eq. 10).
+ *
+ * Conventions (all entry points):
+ *   - Qubit t is bit t of the amplitude index (qubit 0 least significant).
+ *   - A k-qubit matrix is 2^k x 2^k, row-major, complex numbers interleaved
+ *     (re, im) as doubles; its local index is sum_j bit(targets[j]) << j.
+ *   - Host arrays passed in are owned by the caller and are read (copied)
+ *     before the call returns; output arrays are written before it returns.
+ *   - Work is issued on the CUDA stream given to qs_create, in call order.
+ *     Calls that return results (qs_fidelity, qs_trace, qs_get_state, ...)
+ *     synchronise that stream; the others return once the work is enqueued.
+ *   - Every entry point returns a qs_status; no C++ exception crosses the
+ *     ABI.  qs_last_error(h) gives a human-readable detail string.
+ *   - A handle is not thread-safe: one host thread at a time per handle.
+ *   - The library never falls back to the CPU: without a usable CUDA device
+ *     qs_create fails with QS_ERR_CUDA.
+ */
+#ifndef QS_H
+#define QS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qs_ctx* qs_handle;
+typedef struct qs_plan_s* qs_plan;
+
+typedef enum {
+  QS_OK = 0,
+  QS_ERR_INVALID_ARG = 1,    /* bad size, target, pointer or Kraus set     */
+  QS_ERR_OUT_OF_MEMORY = 2,  /* device allocation or memory budget refused */
+  QS_ERR_CUDA = 3,           /* a CUDA runtime call or kernel failed        */
+  QS_ERR_NOT_SUPPORTED = 4,  /* operation undefined for the handle's mode   */
+  QS_ERR_TIMEOUT = 5         /* a bounded device wait gave up               */
+} qs_status;
+
+typedef enum {
+  QS_STATEVEC = 0,   /* `batch` independent state vectors (Monte Carlo, Sec. 2) */
+  QS_DENSITY = 1,    /* exact vectorised density matrix (Sec. 3)               */
+  QS_FIXED_RANK = 2  /* rank-r factor of the density matrix (Sec. 3.2)         */
+} qs_mode;
+
+typedef enum { QS_C64 = 0, QS_C128 = 1 } qs_dtype;
+
+typedef enum {
+  QS_NOISE_ROTATION = 0, /* Eq. 1: U V_noise(e xi) on each target (V first, Eq. 5) */
+  QS_NOISE_PHASE = 1     /* Eqs. 7-8: U diag(1,..,1, e^{-i e xi})                 */
+} qs_noise;
+
+/* ------------------------------------------------------------------ handles */
+
+/* Create a simulator on the current CUDA device.
+ *   n       qubits, 1 <= n; memory: STATEVEC batch * 2^n, DENSITY 4^n,
+ *           FIXED_RANK 5 * rank * 2^n complex elements (plus small scratch).
+ *   batch   STATEVEC: number of trajectories (>= 1); other modes: must be 1.
+ *   rank    FIXED_RANK: truncation rank r >= 1; other modes: ignored (0).
+ *   dtype   QS_C64 (complex float, FP32 arithmetic) or QS_C128 (FP64).
+ *           Reductions (fidelity, trace, Gram matrix, eigensolver) always
+ *           accumulate in FP64.
+ *   cuda_stream  a cudaStream_t (may be NULL = legacy default stream).
+ * The state starts as |0...0> in every batch member.  Device memory is
+ * owned by the handle and released by qs_destroy.
+ * Errors: INVALID_ARG (sizes), OUT_OF_MEMORY, CUDA (no device). */
+qs_status qs_create(int n, int batch, int rank, qs_mode mode, qs_dtype dtype,
+                    void* cuda_stream, qs_handle* out);
+qs_status qs_destroy(qs_handle h);
+const char* qs_last_error(qs_handle h);
+qs_status qs_synchronize(qs_handle h);
+
+/* Shape of a handle (any pointer may be NULL).  *results = number of doubles
+ * qs_fidelity / qs_trace write (batch for STATEVEC, 1 otherwise). */
+qs_status qs_info(qs_handle h, int* n, int* batch, int* rank, int* mode, int* dtype, int* results);
+
+/* Every batch member (trajectory / density matrix / factor) <- |x><x|.
+ * FIXED_RANK: the factor becomes one column.  Errors: INVALID_ARG if x >= 2^n. */
+qs_status qs_set_basis_state(qs_handle h, uint64_t x);
+
+/* Per-member basis states: xs[b] for b < batch (STATEVEC only). */
+qs_status qs_set_basis_states(qs_handle h, const uint64_t* xs);
+
+/* ------------------------------------------------------------------- gates */
+
+/* Ideal k-qubit gate U (k = 1..4) on `targets` (distinct, < n) -- Sec. 2.
+ * DENSITY: rho <- U rho U^dagger via (U (x) U*) on bits (t, t + n), Sec. 3.
+ * FIXED_RANK: L <- U L (no truncation).
+ * Errors: INVALID_ARG for bad targets / k / NULL pointers. */
+qs_status qs_apply_gate(qs_handle h, const int* targets, int k, const double* U);
+
+/* I - 2|index><index| on every member (Grover oracle; the diffusion with its
+ * global phase dropped is the flip of index 0).  Errors: INVALID_ARG. */
+qs_status qs_apply_phase_flip(qs_handle h, uint64_t index);
+
+/* Noisy gate, k = 1 or 2 (Sec. 2, Eqs. 1, 2, 5, 7, 8).
+ * STATEVEC: member b applies U * N_b with N_b from xi drawn by Philox4x32-10
+ *   (key = seed, counter = (traj_b, gate_id)); traj_b = offset + b (see
+ *   qs_set_trajectory_offset) unless per-slot noise is set.  Rotation noise
+ *   uses xi_a on targets[0] and xi_b on targets[1]; phase noise uses xi_a.
+ * DENSITY / FIXED_RANK: the xi-averaged channel (Eqs. 6, 9): rotation ->
+ *   {sqrt(l1) U, sqrt(l2) U J} per target (l1,2 = (1 +- exp(-2e^2))/2),
+ *   phase -> {U diag(1,..,sqrt P), U diag(0,..,sqrt(1-P))}, P = exp(-e^2);
+ *   FIXED_RANK truncates to the handle's rank afterwards (Sec. 3.2).
+ * Errors: INVALID_ARG (k, targets, e < 0). */
+qs_status qs_apply_noisy_gate(qs_handle h, const int* targets, int k, const double* U,
+                              qs_noise noise, double e, uint64_t seed, uint64_t gate_id);
+
+/* Quantum operation sum_i E_i rho E_i^dagger (Eq. 3) with num_ops Kraus
+ * operators E (num_ops consecutive 2^k x 2^k matrices), k = 1..2.
+ * The set must satisfy sum_i E_i^dagger E_i = I within 1e-12 (else
+ * INVALID_ARG).  DENSITY: superoperator sum_i E_i (x) E_i* on bits (t, t+n).
+ * FIXED_RANK: L' = [E_1 L | ... | E_K L], then truncation to the handle's
+ * rank when num_ops > 1.  STATEVEC: NOT_SUPPORTED. */
+qs_status qs_apply_kraus(qs_handle h, const int* targets, int k, const double* E, int num_ops);
+
+/* FIXED_RANK: truncate the current factor to rank r (<= handle rank) by the
+ * Gram-matrix eigendecomposition (Sec. 3.2).  normalize = 0 keeps the trace
+ * sum of the kept eigenvalues; 1 rescales to unit trace.  Eigenvalues within
+ * 1e-10 * Lambda_1 form one cluster whose basis is made canonical by
+ * Gram-Schmidt of the projected Gram-space axes.  Other modes: NOT_SUPPORTED. */
+qs_status qs_truncate_rank(qs_handle h, int r, int normalize);
+
+/* FIXED_RANK: normalisation used by the automatic truncations (default 0). */
+qs_status qs_set_normalize(qs_handle h, int normalize);
+
+/* FIXED_RANK: current number of factor columns (<= rank). */
+qs_status qs_get_rank(qs_handle h, int* out);
+
+/* ------------------------------------------------------------ reductions */
+
+/* Fidelity with a pure reference phi, per member, FP64 accumulation:
+ *   STATEVEC |<phi|psi_b>|^2 (out[batch]); DENSITY <phi|rho|phi> (out[1]);
+ *   FIXED_RANK sum_c |<phi|L_c>|^2 (out[1]).
+ * phi = `ref` (2^n interleaved complex doubles, host) if ref != NULL, else
+ * the basis state |ref_basis>.  Synchronises.  Errors: INVALID_ARG. */
+qs_status qs_fidelity(qs_handle h, const double* ref, uint64_t ref_basis, double* out);
+
+/* Store a reference phi on the device once (2^n complex doubles, host), for
+ * qs_fidelity_stored.  Or copy member `b` of a STATEVEC handle `src` with the
+ * same n (device to device). */
+qs_status qs_set_reference(qs_handle h, const double* ref);
+qs_status qs_set_reference_from(qs_handle h, qs_handle src, int b);
+qs_status qs_fidelity_stored(qs_handle h, double* out);
+
+/* Trace: STATEVEC squared norm per member (out[batch]); DENSITY tr(rho);
+ * FIXED_RANK sum_c ||L_c||^2.  Synchronises. */
+qs_status qs_trace(qs_handle h, double* out);
+
+/* ------------------------------------------------------- state transfer */
+
+/* Number of complex elements of the state: STATEVEC batch * 2^n,
+ * DENSITY 4^n (vec index i * 2^n + j for rho[i][j]), FIXED_RANK rank * 2^n
+ * (column-major: column c at offset c * 2^n; columns >= qs_get_rank are 0). */
+qs_status qs_state_size(qs_handle h, size_t* out);
+/* Copy the state to / from host memory as interleaved complex doubles
+ * (count = qs_state_size).  Synchronises. */
+qs_status qs_get_state(qs_handle h, double* host, size_t count);
+qs_status qs_set_state(qs_handle h, const double* host, size_t count);
+/* FIXED_RANK: set the number of live columns after qs_set_state. */
+qs_status qs_set_rank_columns(qs_handle h, int m);
+
+/* --------------------------------------------------- Monte Carlo counters */
+
+/* STATEVEC: member b uses trajectory counter offset + b (default 0), so a
+ * run split across processes draws the same noise as one run. */
+qs_status qs_set_trajectory_offset(qs_handle h, uint64_t offset);
+
+/* STATEVEC: per-member noise (continuous batching of different jobs in one
+ * handle).  e[b], seed[b], traj[b] override the call arguments and the
+ * offset for member b; marked[b] (may be NULL) replaces the index of plan
+ * flips marked QS_FLIP_PER_MEMBER.  Pass all NULL to clear. */
+qs_status qs_set_member_noise(qs_handle h, const double* e, const uint64_t* seed,
+                              const uint64_t* traj, const uint64_t* marked);
+
+/* ----------------------------------------------------------------- plans */
+
+/* A circuit applied as a whole: the planner groups the gates into fused
+ * passes (runs of gates on a window of qubits applied in one read and one
+ * write of the state; diagonal gates folded in), and the run is replayed
+ * from a captured CUDA graph.  Noisy gates draw with gate_id = gate_id0 +
+ * position in the list, so a plan run equals the same gates issued one by
+ * one through qs_apply_noisy_gate / qs_apply_gate / qs_apply_phase_flip. */
+typedef enum {
+  QS_GATE_DENSE = 0,       /* matrix U on targets[0..k-1]                  */
+  QS_GATE_FLIP = 1,        /* I - 2|index><index|                          */
+  QS_FLIP_PER_MEMBER = 2   /* flip of marked[b] (qs_set_member_noise)      */
+} qs_gate_kind;
+
+typedef struct {
+  int kind;            /* qs_gate_kind                                   */
+  int k;               /* 1 or 2 for QS_GATE_DENSE                       */
+  int targets[2];
+  int noisy;           /* 0 = ideal; 1 = noisy with `noise`              */
+  int noise;           /* qs_noise                                       */
+  uint64_t index;      /* QS_GATE_FLIP                                   */
+  double U[32];        /* 2^k x 2^k interleaved complex                  */
+} qs_gate;
+
+/* Build a plan for `h` (the plan keeps a reference to h; destroy it first).
+ * STATEVEC handles with n >= 10 get fused passes; other shapes run gate by
+ * gate with the same kernels as the single-gate calls.
+ * Errors: INVALID_ARG for a malformed gate (nothing is built). */
+qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_plan* out);
+/* Run the plan once on the handle's stream with noise level e and key seed
+ * (per-member values from qs_set_member_noise take precedence). */
+qs_status qs_plan_run(qs_plan p, double e, uint64_t seed, uint64_t gate_id0);
+/* Number of passes over the state one run makes, and kernels it launches. */
+qs_status qs_plan_info(qs_plan p, int* passes, int* launches);
+qs_status qs_plan_destroy(qs_plan p);
+
+/* Time each kernel of one plan run with CUDA events on the handle's stream
+ * (eager launches, `reps` runs averaged; the state is modified as by
+ * qs_plan_run).  ms[i] = mean duration of launch i of a run, kinds[i] =
+ * 0 noise/parameter precompute, 1 low-window pass, 2 high-window pass,
+ * 3 single-gate step (all kernels of the step together); at most `cap`
+ * entries, *count = launches per run.  Synchronises. */
+qs_status qs_plan_profile(qs_plan p, int reps, double e, uint64_t seed, uint64_t gate_id0,
+                          double* ms, int* kinds, int cap, int* count);
+
+/* Per-launch timing of plan runs: with on = 1 every later qs_plan_run also
+ * records CUDA events around each kernel launch it makes (inside the graph);
+ * qs_plan_last_times then gives the durations of the most recent run (it
+ * waits for that run), kinds as for qs_plan_profile. */
+qs_status qs_plan_set_timing(qs_plan p, int on);
+qs_status qs_plan_last_times(qs_plan p, double* ms, int* kinds, int cap, int* count);
+
+/* ------------------------------------------------------------ utilities */
+
+/* The Philox4x32-10 words and normals the device draws for (seed, traj,
+ * gate_id), count consecutive trajectories starting at traj (for checking
+ * the device stream against an independent implementation).
+ * words: 4 * count uint32; normals: 2 * count doubles (xi_a, xi_b). */
+qs_status qs_debug_noise(uint64_t seed, uint64_t traj, uint64_t gate_id, int count,
+                         uint32_t* words, double* normals);
+
+/* Library version string. */
+const char* qs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QS_H */

@@ -20,7 +20,7 @@ from functools import lru_cache
 import numpy as np
 
 
-@lru_cache(maxsize=256)
+@lru_cache(maxsize=48)
 def group_indices(n: int, targets: tuple) -> np.ndarray:
     """(2^(n-k), 2^k) array: row = the non-target bits, column = local index."""
     k = len(targets)

@@ -1,0 +1,681 @@
+// C ABI of the simulator (include/qs.h): argument checks, device memory,
+// and the dispatch of each call to the kernels of the handle's mode.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using qs::Targets;
+using cd = std::complex<double>;
+
+namespace {
+
+// layout of the small FP64 scratch buffer
+constexpr size_t kSmallG = 0;                          // Gram matrix, 2*32*32
+constexpr size_t kSmallW = 2048;                       // eigenvectors, 2*32*16
+constexpr size_t kSmallLam = 3072;                     // eigenvalues, 32
+constexpr size_t kSmallScale = 3104;                   // 1
+constexpr size_t kSmallE = 3200;                       // Kraus operators, <= 2*8*16
+constexpr size_t kSmallOut = 4096;                     // results, batch doubles
+constexpr int kMaxKraus = 8;
+
+qs_status fail(qs_handle h, qs_status code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+qs_status cuda_fail(qs_handle h, cudaError_t e, const char* where) {
+  return fail(h, QS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define QS_CUDA(h, call)                                   \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+bool valid_targets(const qs_ctx* h, const int* t, int k, std::string* why) {
+  if (!t) { *why = "targets is NULL"; return false; }
+  for (int j = 0; j < k; ++j) {
+    if (t[j] < 0 || t[j] >= h->n) { *why = "target out of range"; return false; }
+    for (int i = 0; i < j; ++i)
+      if (t[i] == t[j]) { *why = "duplicate target"; return false; }
+  }
+  return true;
+}
+
+std::vector<cd> to_cplx(const double* U, int d) {
+  std::vector<cd> m((size_t)d * d);
+  for (int i = 0; i < d * d; ++i) m[i] = cd(U[2 * i], U[2 * i + 1]);
+  return m;
+}
+
+std::vector<double> to_interleaved(const std::vector<cd>& m) {
+  std::vector<double> v(2 * m.size());
+  for (size_t i = 0; i < m.size(); ++i) { v[2 * i] = m[i].real(); v[2 * i + 1] = m[i].imag(); }
+  return v;
+}
+
+bool is_diagonal(const std::vector<cd>& m, int d) {
+  for (int r = 0; r < d; ++r)
+    for (int c = 0; c < d; ++c)
+      if (r != c && m[r * d + c] != cd(0.0, 0.0)) return false;
+  return true;
+}
+
+std::vector<cd> matmul(const std::vector<cd>& a, const std::vector<cd>& b, int d) {
+  std::vector<cd> c((size_t)d * d, cd(0.0, 0.0));
+  for (int i = 0; i < d; ++i)
+    for (int k = 0; k < d; ++k)
+      for (int j = 0; j < d; ++j) c[i * d + j] += a[i * d + k] * b[k * d + j];
+  return c;
+}
+
+// xi-averaged Kraus sets (Eqs. 6 and 9); k = 1 or 2.
+std::vector<std::vector<cd>> averaged_kraus(const std::vector<cd>& U, int k, int noise, double e) {
+  const int d = 1 << k;
+  std::vector<std::vector<cd>> out;
+  if (noise == QS_NOISE_ROTATION) {
+    const double q = std::exp(-2.0 * e * e);
+    const double l1 = 0.5 * (1.0 + q), l2 = 0.5 * (1.0 - q);
+    // one-qubit noise operators A_0 = sqrt(l1) I, A_1 = sqrt(l2) J, J = [[0,1],[-1,0]]
+    auto one = [&](int which, int r, int c) -> double {
+      if (which == 0) return r == c ? std::sqrt(l1) : 0.0;
+      if (r == 0 && c == 1) return std::sqrt(l2);
+      if (r == 1 && c == 0) return -std::sqrt(l2);
+      return 0.0;
+    };
+    const int nops = k == 1 ? 2 : 4;
+    for (int op = 0; op < nops; ++op) {
+      const int wa = op & 1, wb = (op >> 1) & 1;       // targets[0] varies fastest
+      std::vector<cd> N((size_t)d * d, cd(0.0, 0.0));
+      for (int r = 0; r < d; ++r)
+        for (int c = 0; c < d; ++c) {
+          double v = one(wa, r & 1, c & 1);
+          if (k == 2) v *= one(wb, (r >> 1) & 1, (c >> 1) & 1);
+          N[r * d + c] = v;
+        }
+      out.push_back(matmul(U, N, d));
+    }
+  } else {
+    const double P = std::exp(-e * e);
+    std::vector<cd> d1((size_t)d * d, cd(0.0, 0.0)), d2((size_t)d * d, cd(0.0, 0.0));
+    for (int i = 0; i < d; ++i) d1[i * d + i] = 1.0;
+    d1[(d - 1) * d + (d - 1)] = std::sqrt(P);
+    d2[(d - 1) * d + (d - 1)] = std::sqrt(1.0 - P);
+    out.push_back(matmul(U, d1, d));
+    out.push_back(matmul(U, d2, d));
+  }
+  return out;
+}
+
+bool kraus_complete(const std::vector<std::vector<cd>>& ks, int d, double tol) {
+  for (int r = 0; r < d; ++r)
+    for (int c = 0; c < d; ++c) {
+      cd s(0.0, 0.0);
+      for (const auto& E : ks)
+        for (int m = 0; m < d; ++m) s += std::conj(E[m * d + r]) * E[m * d + c];
+      if (std::abs(s - (r == c ? cd(1.0, 0.0) : cd(0.0, 0.0))) > tol) return false;
+    }
+  return true;
+}
+
+// superoperator sum_i E_i (x) conj(E_i): row factor on the high local bits
+std::vector<cd> superop(const std::vector<std::vector<cd>>& ks, int d) {
+  const int D = d * d;
+  std::vector<cd> S((size_t)D * D, cd(0.0, 0.0));
+  for (const auto& E : ks)
+    for (int ro = 0; ro < d; ++ro)
+      for (int co = 0; co < d; ++co)
+        for (int ri = 0; ri < d; ++ri)
+          for (int ci = 0; ci < d; ++ci)
+            S[(size_t)(ro * d + co) * D + (ri * d + ci)] += E[ro * d + ri] * std::conj(E[co * d + ci]);
+  return S;
+}
+
+template <typename R>
+std::vector<R> to_real_array(const std::vector<cd>& m) {
+  std::vector<R> v(2 * m.size());
+  for (size_t i = 0; i < m.size(); ++i) { v[2 * i] = (R)m[i].real(); v[2 * i + 1] = (R)m[i].imag(); }
+  return v;
+}
+
+// Upload a uniform matrix (or diagonal) in the handle's precision into h->mats.
+qs_status upload_mat(qs_handle h, const std::vector<cd>& m) {
+  const size_t bytes = m.size() * 2 * (h->esize / 2);
+  if (bytes > h->mats_cap) return fail(h, QS_ERR_INVALID_ARG, "matrix too large");
+  if (h->dtype == QS_C64) {
+    auto v = to_real_array<float>(m);
+    QS_CUDA(h, cudaMemcpyAsync(h->mats, v.data(), bytes, cudaMemcpyHostToDevice, h->stream));
+  } else {
+    auto v = to_real_array<double>(m);
+    QS_CUDA(h, cudaMemcpyAsync(h->mats, v.data(), bytes, cudaMemcpyHostToDevice, h->stream));
+  }
+  return QS_OK;
+}
+
+// Apply a uniform matrix U (dimension d = 2^k) on `targets` of every member.
+qs_status apply_uniform(qs_handle h, void* psi, int n, int members, const int* targets, int k,
+                        const std::vector<cd>& U) {
+  const int d = 1 << k;
+  const Targets tg = qs::make_targets(n, targets, k);
+  if (is_diagonal(U, d)) {
+    uint32_t mask = 0;
+    std::vector<cd> diag(d);
+    for (int l = 0; l < d; ++l) {
+      diag[l] = U[l * d + l];
+      if (diag[l] != cd(1.0, 0.0)) mask |= 1u << l;
+    }
+    if (!mask) return QS_OK;
+    qs_status st = upload_mat(h, diag);
+    if (st != QS_OK) return st;
+    QS_CUDA(h, qs::launch_apply_diag(h, psi, n, members, tg, h->mats, false, mask));
+    return QS_OK;
+  }
+  if (k == 1) {
+    const auto v = to_interleaved(U);
+    QS_CUDA(h, qs::launch_apply_1q(h, psi, n, members, targets[0], v.data(), nullptr));
+    return QS_OK;
+  }
+  qs_status st = upload_mat(h, U);
+  if (st != QS_OK) return st;
+  QS_CUDA(h, qs::launch_apply_kq(h, psi, n, members, tg, h->mats, false));
+  return QS_OK;
+}
+
+// DENSITY: superoperator of a Kraus set on bits (t, t + n).
+qs_status dm_apply_channel(qs_handle h, const int* targets, int k, const std::vector<std::vector<cd>>& ks) {
+  int t2[2 * qs::kMaxK];
+  for (int j = 0; j < k; ++j) { t2[j] = targets[j]; t2[k + j] = targets[j] + h->n; }
+  return apply_uniform(h, h->state, 2 * h->n, 1, t2, 2 * k, superop(ks, 1 << k));
+}
+
+qs_status rank_truncate_from_work(qs_handle h, int M, int r, int normalize) {
+  double* G = h->small + kSmallG;
+  double* W = h->small + kSmallW;
+  double* lam = h->small + kSmallLam;
+  double* scale = h->small + kSmallScale;
+  QS_CUDA(h, qs::launch_gram(h, h->work, h->n, M, G));
+  QS_CUDA(h, qs::launch_eig_truncate(h, G, M, r, normalize, W, lam, scale, h->dstatus, h->dstatus + 1));
+  QS_CUDA(h, qs::launch_project(h, h->work, h->state, h->n, M, W, scale, h->dstatus));
+  const int keep = std::min(r, M);
+  // columns that are no longer live read as zero
+  if (keep < h->cols) {
+    const size_t N = 1ull << h->n;
+    QS_CUDA(h, cudaMemsetAsync((char*)h->state + (size_t)keep * N * h->esize, 0,
+                               (size_t)(h->cols - keep) * N * h->esize, h->stream));
+  }
+  h->cols = keep;
+  return QS_OK;
+}
+
+// FIXED_RANK: L' = [E_1 L | ..], then truncation when K > 1.
+qs_status rank_apply_kraus(qs_handle h, const int* targets, int k, const std::vector<std::vector<cd>>& ks) {
+  const int K = (int)ks.size();
+  const int d = 1 << k;
+  if (K == 1) {
+    return apply_uniform(h, h->state, h->n, h->cols, targets, k, ks[0]);
+  }
+  const int M = K * h->cols;
+  if (M > qs::kMaxGramDim)
+    return fail(h, QS_ERR_NOT_SUPPORTED, "Kraus count times rank exceeds the Gram-matrix limit of 32");
+  std::vector<double> e;
+  for (const auto& E : ks) { auto v = to_interleaved(E); e.insert(e.end(), v.begin(), v.end()); }
+  (void)d;
+  QS_CUDA(h, cudaMemcpyAsync(h->small + kSmallE, e.data(), e.size() * sizeof(double),
+                             cudaMemcpyHostToDevice, h->stream));
+  const Targets tg = qs::make_targets(h->n, targets, k);
+  QS_CUDA(h, qs::launch_kraus_expand(h, h->state, h->work, h->n, h->cols, tg, h->small + kSmallE, K));
+  return rank_truncate_from_work(h, M, h->rank, h->normalize);
+}
+
+qs_status read_out(qs_handle h, double* out, int count) {
+  QS_CUDA(h, cudaMemcpyAsync(out, h->small + kSmallOut, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  QS_CUDA(h, cudaStreamSynchronize(h->stream));
+  int status[2] = {0, 0};
+  QS_CUDA(h, cudaMemcpy(status, h->dstatus, sizeof(status), cudaMemcpyDeviceToHost));
+  if (h->mode == QS_FIXED_RANK && status[1] != 0)
+    return fail(h, QS_ERR_CUDA, status[1] == 1 ? "eigensolver did not converge" : "tie-cluster basis incomplete");
+  return QS_OK;
+}
+
+}  // namespace
+
+namespace qs {
+NoiseSrc noise_src(qs_ctx* h, double e, uint64_t seed) {
+  NoiseSrc s{};
+  s.e0 = e;
+  s.seed0 = seed;
+  s.traj0 = h->traj_offset;
+  if (h->member_noise) { s.e = h->m_e; s.seed = h->m_seed; s.traj = h->m_traj; }
+  return s;
+}
+}  // namespace qs
+
+extern "C" {
+
+const char* qs_version(void) { return "paper_1412_2293_gb300 0.1 (sm_103a)"; }
+
+qs_status qs_create(int n, int batch, int rank, qs_mode mode, qs_dtype dtype, void* cuda_stream,
+                    qs_handle* out) {
+  if (!out) return QS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n < 1 || n > 40) return QS_ERR_INVALID_ARG;
+  if (mode != QS_STATEVEC && mode != QS_DENSITY && mode != QS_FIXED_RANK) return QS_ERR_INVALID_ARG;
+  if (dtype != QS_C64 && dtype != QS_C128) return QS_ERR_INVALID_ARG;
+  if (mode == QS_STATEVEC && batch < 1) return QS_ERR_INVALID_ARG;
+  if (mode != QS_STATEVEC && batch != 1) return QS_ERR_INVALID_ARG;
+  if (mode == QS_FIXED_RANK && (rank < 1 || rank > qs::kMaxRank)) return QS_ERR_INVALID_ARG;
+  if (mode == QS_DENSITY && 2 * n > 40) return QS_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) { cudaGetLastError(); return QS_ERR_CUDA; }
+
+  qs_ctx* h = new (std::nothrow) qs_ctx();
+  if (!h) return QS_ERR_OUT_OF_MEMORY;
+  h->n = n;
+  h->batch = batch;
+  h->rank = mode == QS_FIXED_RANK ? rank : 0;
+  h->mode = mode;
+  h->dtype = dtype;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->esize = qs::elem_size(dtype);
+  cudaGetDevice(&h->device);
+
+  const uint64_t N = 1ull << n;
+  size_t members = mode == QS_STATEVEC ? (size_t)batch : 1;
+  if (mode == QS_STATEVEC) h->state_elems = (size_t)batch * N;
+  else if (mode == QS_DENSITY) h->state_elems = N * N;
+  else h->state_elems = (size_t)rank * N;
+
+  auto bail = [&](qs_status st) { qs_destroy(h); return st; };
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  if (h->state_elems * h->esize > free_b) return bail(QS_ERR_OUT_OF_MEMORY);
+  if (cudaMalloc(&h->state, h->state_elems * h->esize) != cudaSuccess) { cudaGetLastError(); return bail(QS_ERR_OUT_OF_MEMORY); }
+  if (mode == QS_FIXED_RANK) {
+    h->work_elems = (size_t)qs::kMaxGramDim * N;
+    if (cudaMalloc(&h->work, h->work_elems * h->esize) != cudaSuccess) { cudaGetLastError(); return bail(QS_ERR_OUT_OF_MEMORY); }
+    members = qs::kMaxGramDim;
+  }
+  // scratch sized for every reduction of this shape, so that runs never allocate
+  const uint64_t chunks = (N + 4095) / 4096;
+  size_t partials = 2 * chunks * members;
+  if (mode == QS_DENSITY) partials = std::max<size_t>(partials, 2 * N);
+  if (mode == QS_FIXED_RANK) partials = std::max<size_t>(partials, ((N + 63) / 64) * 2 * qs::kMaxGramDim * qs::kMaxGramDim);
+  h->partials_cap = partials;
+  if (cudaMalloc((void**)&h->partials, partials * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return bail(QS_ERR_OUT_OF_MEMORY); }
+  h->mats_cap = std::max<size_t>((size_t)batch * 2 * 16, 2 * 256) * (h->esize / 2);
+  if (cudaMalloc(&h->mats, h->mats_cap) != cudaSuccess) { cudaGetLastError(); return bail(QS_ERR_OUT_OF_MEMORY); }
+  h->small_cap = kSmallOut + std::max<size_t>((size_t)batch, 64);
+  if (cudaMalloc((void**)&h->small, h->small_cap * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return bail(QS_ERR_OUT_OF_MEMORY); }
+  if (cudaMalloc((void**)&h->dstatus, 4 * sizeof(int)) != cudaSuccess) { cudaGetLastError(); return bail(QS_ERR_OUT_OF_MEMORY); }
+  if (cudaMemsetAsync(h->dstatus, 0, 4 * sizeof(int), h->stream) != cudaSuccess) return bail(QS_ERR_CUDA);
+  h->cols = 1;
+  cudaError_t e = qs::launch_set_basis(h, h->state, n, (int)(mode == QS_STATEVEC ? batch : 1), 0, nullptr);
+  if (mode == QS_FIXED_RANK && e == cudaSuccess)
+    e = cudaMemsetAsync(h->state, 0, h->state_elems * h->esize, h->stream),
+    e = e == cudaSuccess ? qs::launch_set_basis(h, h->state, n, 1, 0, nullptr) : e;
+  if (e != cudaSuccess) return bail(QS_ERR_CUDA);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(QS_ERR_CUDA);
+  *out = h;
+  return QS_OK;
+}
+
+qs_status qs_destroy(qs_handle h) {
+  if (!h) return QS_ERR_INVALID_ARG;
+  cudaStreamSynchronize(h->stream);
+  void* ptrs[] = {h->state, h->work, h->partials, h->mats, h->small, h->dstatus, h->m_e,
+                  h->m_seed, h->m_traj, h->m_marked, h->ref};
+  for (void* p : ptrs) if (p) cudaFree(p);
+  if (h->hpinned) cudaFreeHost(h->hpinned);
+  delete h;
+  return QS_OK;
+}
+
+const char* qs_last_error(qs_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+qs_status qs_info(qs_handle h, int* n, int* batch, int* rank, int* mode, int* dtype, int* results) {
+  if (!h) return QS_ERR_INVALID_ARG;
+  if (n) *n = h->n;
+  if (batch) *batch = h->batch;
+  if (rank) *rank = h->rank;
+  if (mode) *mode = (int)h->mode;
+  if (dtype) *dtype = (int)h->dtype;
+  if (results) *results = h->mode == QS_STATEVEC ? h->batch : 1;
+  return QS_OK;
+}
+
+qs_status qs_synchronize(qs_handle h) {
+  if (!h) return QS_ERR_INVALID_ARG;
+  QS_CUDA(h, cudaStreamSynchronize(h->stream));
+  return QS_OK;
+}
+
+qs_status qs_set_basis_state(qs_handle h, uint64_t x) {
+  if (!h) return QS_ERR_INVALID_ARG;
+  if (x >= (1ull << h->n)) return fail(h, QS_ERR_INVALID_ARG, "basis index out of range");
+  if (h->mode == QS_STATEVEC) {
+    QS_CUDA(h, qs::launch_set_basis(h, h->state, h->n, h->batch, x, nullptr));
+  } else if (h->mode == QS_DENSITY) {
+    const uint64_t N = 1ull << h->n;
+    QS_CUDA(h, qs::launch_set_basis(h, h->state, 2 * h->n, 1, x * N + x, nullptr));
+  } else {
+    QS_CUDA(h, cudaMemsetAsync(h->state, 0, h->state_elems * h->esize, h->stream));
+    QS_CUDA(h, qs::launch_set_basis(h, h->state, h->n, 1, x, nullptr));
+    h->cols = 1;
+  }
+  return QS_OK;
+}
+
+qs_status qs_set_basis_states(qs_handle h, const uint64_t* xs) {
+  if (!h || !xs) return QS_ERR_INVALID_ARG;
+  if (h->mode != QS_STATEVEC) return fail(h, QS_ERR_NOT_SUPPORTED, "per-member basis states need STATEVEC");
+  for (int b = 0; b < h->batch; ++b)
+    if (xs[b] >= (1ull << h->n)) return fail(h, QS_ERR_INVALID_ARG, "basis index out of range");
+  // stage through the member-index buffer
+  if (!h->m_marked) QS_CUDA(h, cudaMalloc((void**)&h->m_marked, h->batch * sizeof(uint64_t)));
+  uint64_t* tmp = nullptr;
+  QS_CUDA(h, cudaMallocAsync((void**)&tmp, h->batch * sizeof(uint64_t), h->stream));
+  QS_CUDA(h, cudaMemcpyAsync(tmp, xs, h->batch * sizeof(uint64_t), cudaMemcpyHostToDevice, h->stream));
+  QS_CUDA(h, qs::launch_set_basis(h, h->state, h->n, h->batch, 0, tmp));
+  QS_CUDA(h, cudaFreeAsync(tmp, h->stream));
+  return QS_OK;
+}
+
+qs_status qs_apply_gate(qs_handle h, const int* targets, int k, const double* U) {
+  if (!h) return QS_ERR_INVALID_ARG;
+  if (k < 1 || k > qs::kMaxK) return fail(h, QS_ERR_INVALID_ARG, "k must be 1..4");
+  if (!U) return fail(h, QS_ERR_INVALID_ARG, "U is NULL");
+  std::string why;
+  if (!valid_targets(h, targets, k, &why)) return fail(h, QS_ERR_INVALID_ARG, why);
+  const auto M = to_cplx(U, 1 << k);
+  if (h->mode == QS_STATEVEC) return apply_uniform(h, h->state, h->n, h->batch, targets, k, M);
+  if (h->mode == QS_FIXED_RANK) return apply_uniform(h, h->state, h->n, h->cols, targets, k, M);
+  if (k > 2) return fail(h, QS_ERR_NOT_SUPPORTED, "DENSITY gates are limited to k <= 2");
+  return dm_apply_channel(h, targets, k, {M});
+}
+
+qs_status qs_apply_phase_flip(qs_handle h, uint64_t index) {
+  if (!h) return QS_ERR_INVALID_ARG;
+  if (index >= (1ull << h->n)) return fail(h, QS_ERR_INVALID_ARG, "index out of range");
+  if (h->mode == QS_STATEVEC) { QS_CUDA(h, qs::launch_phase_flip(h, h->state, h->n, h->batch, index, nullptr)); }
+  else if (h->mode == QS_FIXED_RANK) { QS_CUDA(h, qs::launch_phase_flip(h, h->state, h->n, h->cols, index, nullptr)); }
+  else { QS_CUDA(h, qs::launch_dm_flip(h, h->state, h->n, index)); }
+  return QS_OK;
+}
+
+qs_status qs_apply_noisy_gate(qs_handle h, const int* targets, int k, const double* U, qs_noise noise,
+                              double e, uint64_t seed, uint64_t gate_id) {
+  if (!h) return QS_ERR_INVALID_ARG;
+  if (k < 1 || k > 2) return fail(h, QS_ERR_INVALID_ARG, "noisy gates are defined for k = 1, 2");
+  if (!U) return fail(h, QS_ERR_INVALID_ARG, "U is NULL");
+  if (!(e >= 0.0) || !std::isfinite(e)) return fail(h, QS_ERR_INVALID_ARG, "e must be finite and >= 0");
+  if (noise != QS_NOISE_ROTATION && noise != QS_NOISE_PHASE) return fail(h, QS_ERR_INVALID_ARG, "bad noise kind");
+  std::string why;
+  if (!valid_targets(h, targets, k, &why)) return fail(h, QS_ERR_INVALID_ARG, why);
+  const int d = 1 << k;
+  const auto M = to_cplx(U, d);
+  if (h->mode == QS_STATEVEC) {
+    const qs::NoiseSrc src = qs::noise_src(h, e, seed);
+    const Targets tg = qs::make_targets(h->n, targets, k);
+    const bool diag = noise == QS_NOISE_PHASE && is_diagonal(M, d);
+    QS_CUDA(h, qs::launch_noise_mats(h, h->mats, h->batch, k, U, noise, diag ? 1 : 0, src, gate_id));
+    if (diag) {
+      uint32_t mask = 1u << (d - 1);
+      for (int l = 0; l < d - 1; ++l) if (M[l * d + l] != cd(1.0, 0.0)) mask |= 1u << l;
+      QS_CUDA(h, qs::launch_apply_diag(h, h->state, h->n, h->batch, tg, h->mats, true, mask));
+    } else if (k == 1) {
+      QS_CUDA(h, qs::launch_apply_1q(h, h->state, h->n, h->batch, targets[0], nullptr, h->mats));
+    } else {
+      QS_CUDA(h, qs::launch_apply_kq(h, h->state, h->n, h->batch, tg, h->mats, true));
+    }
+    return QS_OK;
+  }
+  const auto ks = averaged_kraus(M, k, noise, e);
+  if (h->mode == QS_DENSITY) return dm_apply_channel(h, targets, k, ks);
+  return rank_apply_kraus(h, targets, k, ks);
+}
+
+qs_status qs_apply_kraus(qs_handle h, const int* targets, int k, const double* E, int num_ops) {
+  if (!h) return QS_ERR_INVALID_ARG;
+  if (h->mode == QS_STATEVEC) return fail(h, QS_ERR_NOT_SUPPORTED, "Kraus channels need DENSITY or FIXED_RANK");
+  if (k < 1 || k > 2) return fail(h, QS_ERR_INVALID_ARG, "Kraus operators are limited to k = 1, 2");
+  if (!E || num_ops < 1 || num_ops > kMaxKraus) return fail(h, QS_ERR_INVALID_ARG, "need 1..8 Kraus operators");
+  std::string why;
+  if (!valid_targets(h, targets, k, &why)) return fail(h, QS_ERR_INVALID_ARG, why);
+  const int d = 1 << k;
+  std::vector<std::vector<cd>> ks;
+  for (int i = 0; i < num_ops; ++i) ks.push_back(to_cplx(E + (size_t)i * 2 * d * d, d));
+  if (!kraus_complete(ks, d, 1e-12)) return fail(h, QS_ERR_INVALID_ARG, "sum E^dagger E != I (tolerance 1e-12)");
+  if (h->mode == QS_DENSITY) return dm_apply_channel(h, targets, k, ks);
+  return rank_apply_kraus(h, targets, k, ks);
+}
+
+qs_status qs_truncate_rank(qs_handle h, int r, int normalize) {
+  if (!h) return QS_ERR_INVALID_ARG;
+  if (h->mode != QS_FIXED_RANK) return fail(h, QS_ERR_NOT_SUPPORTED, "truncation needs FIXED_RANK");
+  if (r < 1 || r > h->rank) return fail(h, QS_ERR_INVALID_ARG, "r must be 1..rank");
+  const int M = h->cols;
+  // copy L into the work buffer, then truncate from there back into L
+  QS_CUDA(h, cudaMemcpyAsync(h->work, h->state, (size_t)M * (1ull << h->n) * h->esize,
+                             cudaMemcpyDeviceToDevice, h->stream));
+  return rank_truncate_from_work(h, M, r, normalize);
+}
+
+qs_status qs_set_normalize(qs_handle h, int normalize) {
+  if (!h) return QS_ERR_INVALID_ARG;
+  h->normalize = normalize ? 1 : 0;
+  return QS_OK;
+}
+
+qs_status qs_get_rank(qs_handle h, int* out) {
+  if (!h || !out) return QS_ERR_INVALID_ARG;
+  *out = h->mode == QS_FIXED_RANK ? h->cols : 1;
+  return QS_OK;
+}
+
+static qs_status upload_ref(qs_handle h, const double* ref, void* dst) {
+  const size_t N = 1ull << h->n;
+  double* tmp = nullptr;
+  QS_CUDA(h, cudaMallocAsync((void**)&tmp, N * 2 * sizeof(double), h->stream));
+  QS_CUDA(h, cudaMemcpyAsync(tmp, ref, N * 2 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  QS_CUDA(h, qs::launch_convert_ref(h, tmp, dst, N));
+  QS_CUDA(h, cudaFreeAsync(tmp, h->stream));
+  return QS_OK;
+}
+
+static qs_status fidelity_dev(qs_handle h, const void* phi_dev, double* out) {
+  double* o = h->small + kSmallOut;
+  if (h->mode == QS_STATEVEC) {
+    QS_CUDA(h, qs::launch_dot(h, h->state, phi_dev, h->n, h->batch, false, o));
+    return read_out(h, out, h->batch);
+  }
+  if (h->mode == QS_FIXED_RANK) {
+    QS_CUDA(h, qs::launch_dot(h, h->state, phi_dev, h->n, h->cols, true, o));
+    return read_out(h, out, 1);
+  }
+  QS_CUDA(h, qs::launch_dm_expect(h, h->state, phi_dev, h->n, o));
+  return read_out(h, out, 1);
+}
+
+qs_status qs_fidelity(qs_handle h, const double* ref, uint64_t ref_basis, double* out) {
+  if (!h || !out) return QS_ERR_INVALID_ARG;
+  const uint64_t N = 1ull << h->n;
+  double* o = h->small + kSmallOut;
+  if (!ref) {
+    if (ref_basis >= N) return fail(h, QS_ERR_INVALID_ARG, "basis index out of range");
+    if (h->mode == QS_STATEVEC) {
+      QS_CUDA(h, qs::launch_basis_prob(h, h->state, h->n, h->batch, ref_basis, false, o));
+      return read_out(h, out, h->batch);
+    }
+    if (h->mode == QS_FIXED_RANK) {
+      QS_CUDA(h, qs::launch_basis_prob(h, h->state, h->n, h->cols, ref_basis, true, o));
+      return read_out(h, out, 1);
+    }
+    // rho[x][x]
+    double v[2] = {0.0, 0.0};
+    if (h->dtype == QS_C128) {
+      QS_CUDA(h, cudaMemcpyAsync(v, (const char*)h->state + (ref_basis * N + ref_basis) * 16, 16,
+                                 cudaMemcpyDeviceToHost, h->stream));
+      QS_CUDA(h, cudaStreamSynchronize(h->stream));
+    } else {
+      float f[2];
+      QS_CUDA(h, cudaMemcpyAsync(f, (const char*)h->state + (ref_basis * N + ref_basis) * 8, 8,
+                                 cudaMemcpyDeviceToHost, h->stream));
+      QS_CUDA(h, cudaStreamSynchronize(h->stream));
+      v[0] = f[0];
+    }
+    out[0] = v[0];
+    return QS_OK;
+  }
+  void* tmp = nullptr;
+  QS_CUDA(h, cudaMallocAsync(&tmp, N * h->esize, h->stream));
+  qs_status st = upload_ref(h, ref, tmp);
+  if (st != QS_OK) { cudaFreeAsync(tmp, h->stream); return st; }
+  st = fidelity_dev(h, tmp, out);
+  cudaFreeAsync(tmp, h->stream);
+  return st;
+}
+
+qs_status qs_set_reference(qs_handle h, const double* ref) {
+  if (!h || !ref) return QS_ERR_INVALID_ARG;
+  if (!h->ref) QS_CUDA(h, cudaMalloc(&h->ref, (1ull << h->n) * h->esize));
+  qs_status st = upload_ref(h, ref, h->ref);
+  if (st == QS_OK) h->has_ref = true;
+  return st;
+}
+
+qs_status qs_set_reference_from(qs_handle h, qs_handle src, int b) {
+  if (!h || !src) return QS_ERR_INVALID_ARG;
+  if (src->mode != QS_STATEVEC || src->n != h->n || src->dtype != h->dtype || b < 0 || b >= src->batch)
+    return fail(h, QS_ERR_INVALID_ARG, "reference must be a member of a STATEVEC handle with the same n and dtype");
+  if (!h->ref) QS_CUDA(h, cudaMalloc(&h->ref, (1ull << h->n) * h->esize));
+  QS_CUDA(h, cudaStreamSynchronize(src->stream));
+  QS_CUDA(h, cudaMemcpyAsync(h->ref, (const char*)src->state + ((size_t)b << h->n) * h->esize,
+                             (1ull << h->n) * h->esize, cudaMemcpyDeviceToDevice, h->stream));
+  h->has_ref = true;
+  return QS_OK;
+}
+
+qs_status qs_fidelity_stored(qs_handle h, double* out) {
+  if (!h || !out) return QS_ERR_INVALID_ARG;
+  if (!h->has_ref) return fail(h, QS_ERR_INVALID_ARG, "no stored reference");
+  return fidelity_dev(h, h->ref, out);
+}
+
+qs_status qs_trace(qs_handle h, double* out) {
+  if (!h || !out) return QS_ERR_INVALID_ARG;
+  double* o = h->small + kSmallOut;
+  if (h->mode == QS_STATEVEC) {
+    QS_CUDA(h, qs::launch_norm(h, h->state, h->n, h->batch, false, o));
+    return read_out(h, out, h->batch);
+  }
+  if (h->mode == QS_FIXED_RANK) {
+    QS_CUDA(h, qs::launch_norm(h, h->state, h->n, h->cols, true, o));
+    return read_out(h, out, 1);
+  }
+  QS_CUDA(h, qs::launch_dm_trace(h, h->state, h->n, o));
+  return read_out(h, out, 1);
+}
+
+qs_status qs_state_size(qs_handle h, size_t* out) {
+  if (!h || !out) return QS_ERR_INVALID_ARG;
+  *out = h->state_elems;
+  return QS_OK;
+}
+
+qs_status qs_get_state(qs_handle h, double* host, size_t count) {
+  if (!h || !host) return QS_ERR_INVALID_ARG;
+  if (count != h->state_elems) return fail(h, QS_ERR_INVALID_ARG, "count must equal qs_state_size");
+  QS_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (h->dtype == QS_C128) {
+    QS_CUDA(h, cudaMemcpy(host, h->state, count * 16, cudaMemcpyDeviceToHost));
+  } else {
+    std::vector<float> f(2 * count);
+    QS_CUDA(h, cudaMemcpy(f.data(), h->state, count * 8, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < 2 * count; ++i) host[i] = f[i];
+  }
+  return QS_OK;
+}
+
+qs_status qs_set_state(qs_handle h, const double* host, size_t count) {
+  if (!h || !host) return QS_ERR_INVALID_ARG;
+  if (count != h->state_elems) return fail(h, QS_ERR_INVALID_ARG, "count must equal qs_state_size");
+  QS_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (h->dtype == QS_C128) {
+    QS_CUDA(h, cudaMemcpy(h->state, host, count * 16, cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> f(2 * count);
+    for (size_t i = 0; i < 2 * count; ++i) f[i] = (float)host[i];
+    QS_CUDA(h, cudaMemcpy(h->state, f.data(), count * 8, cudaMemcpyHostToDevice));
+  }
+  return QS_OK;
+}
+
+qs_status qs_set_rank_columns(qs_handle h, int m) {
+  if (!h) return QS_ERR_INVALID_ARG;
+  if (h->mode != QS_FIXED_RANK) return fail(h, QS_ERR_NOT_SUPPORTED, "needs FIXED_RANK");
+  if (m < 1 || m > h->rank) return fail(h, QS_ERR_INVALID_ARG, "m must be 1..rank");
+  h->cols = m;
+  return QS_OK;
+}
+
+qs_status qs_set_trajectory_offset(qs_handle h, uint64_t offset) {
+  if (!h) return QS_ERR_INVALID_ARG;
+  h->traj_offset = offset;
+  return QS_OK;
+}
+
+qs_status qs_set_member_noise(qs_handle h, const double* e, const uint64_t* seed, const uint64_t* traj,
+                              const uint64_t* marked) {
+  if (!h) return QS_ERR_INVALID_ARG;
+  if (h->mode != QS_STATEVEC) return fail(h, QS_ERR_NOT_SUPPORTED, "per-member noise needs STATEVEC");
+  if (!e && !seed && !traj && !marked) { h->member_noise = false; h->member_marked = false; return QS_OK; }
+  if (!e || !seed || !traj) return fail(h, QS_ERR_INVALID_ARG, "e, seed and traj must all be given");
+  for (int b = 0; b < h->batch; ++b)
+    if (!(e[b] >= 0.0) || !std::isfinite(e[b])) return fail(h, QS_ERR_INVALID_ARG, "e must be finite and >= 0");
+  const size_t B = h->batch;
+  if (!h->m_e) QS_CUDA(h, cudaMalloc((void**)&h->m_e, B * sizeof(double)));
+  if (!h->m_seed) QS_CUDA(h, cudaMalloc((void**)&h->m_seed, B * sizeof(uint64_t)));
+  if (!h->m_traj) QS_CUDA(h, cudaMalloc((void**)&h->m_traj, B * sizeof(uint64_t)));
+  QS_CUDA(h, cudaMemcpyAsync(h->m_e, e, B * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  QS_CUDA(h, cudaMemcpyAsync(h->m_seed, seed, B * sizeof(uint64_t), cudaMemcpyHostToDevice, h->stream));
+  QS_CUDA(h, cudaMemcpyAsync(h->m_traj, traj, B * sizeof(uint64_t), cudaMemcpyHostToDevice, h->stream));
+  h->member_noise = true;
+  if (marked) {
+    for (int b = 0; b < h->batch; ++b)
+      if (marked[b] >= (1ull << h->n)) return fail(h, QS_ERR_INVALID_ARG, "marked index out of range");
+    if (!h->m_marked) QS_CUDA(h, cudaMalloc((void**)&h->m_marked, B * sizeof(uint64_t)));
+    QS_CUDA(h, cudaMemcpyAsync(h->m_marked, marked, B * sizeof(uint64_t), cudaMemcpyHostToDevice, h->stream));
+    h->member_marked = true;
+  } else {
+    h->member_marked = false;
+  }
+  // the host arrays are consumed by the time the stream reaches the copies
+  QS_CUDA(h, cudaStreamSynchronize(h->stream));
+  return QS_OK;
+}
+
+qs_status qs_debug_noise(uint64_t seed, uint64_t traj, uint64_t gate_id, int count, uint32_t* words,
+                         double* normals) {
+  if (count < 1 || !words || !normals) return QS_ERR_INVALID_ARG;
+  uint32_t* dw = nullptr;
+  double* dn = nullptr;
+  if (cudaMalloc((void**)&dw, (size_t)count * 4 * sizeof(uint32_t)) != cudaSuccess) return QS_ERR_OUT_OF_MEMORY;
+  if (cudaMalloc((void**)&dn, (size_t)count * 2 * sizeof(double)) != cudaSuccess) { cudaFree(dw); return QS_ERR_OUT_OF_MEMORY; }
+  cudaError_t e = qs::launch_debug_noise(seed, traj, gate_id, count, dw, dn, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(words, dw, (size_t)count * 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(normals, dn, (size_t)count * 2 * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(dw);
+  cudaFree(dn);
+  return e == cudaSuccess ? QS_OK : QS_ERR_CUDA;
+}
+
+}  // extern "C"

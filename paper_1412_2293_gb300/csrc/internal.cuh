@@ -1,0 +1,165 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "qs.h"
+
+namespace qs {
+
+// ------------------------------------------------------------ complex types
+template <typename R> struct CT;
+template <> struct CT<float> { using C = float2; };
+template <> struct CT<double> { using C = double2; };
+template <typename R> using cplx = typename CT<R>::C;
+
+template <typename R> __host__ __device__ __forceinline__ cplx<R> mk(R re, R im) {
+  cplx<R> c; c.x = re; c.y = im; return c;
+}
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+  C c; c.x = a.x * b.x - a.y * b.y; c.y = a.x * b.y + a.y * b.x; return c;
+}
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) {
+  C c; c.x = a.x + b.x; c.y = a.y + b.y; return c;
+}
+// a + m * b
+template <typename C> __host__ __device__ __forceinline__ C cfma(C m, C b, C a) {
+  C c; c.x = a.x + m.x * b.x - m.y * b.y; c.y = a.y + m.x * b.y + m.y * b.x; return c;
+}
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+
+// ----------------------------------------------------------- small structs
+constexpr int kMaxK = 4;                 // dense gates up to 4 qubits (16 x 16)
+constexpr int kMaxGramDim = 32;          // K * m of a fixed-rank channel
+constexpr int kMaxRank = 16;             // largest truncation rank
+
+// Targets of a k-qubit operation: original order (local-index bits) and the
+// ascending positions used to enumerate the untouched bits.
+struct Targets {
+  int k;
+  int t[kMaxK];
+  int sorted[kMaxK];
+  uint64_t off[1 << kMaxK];              // index offset of each local index
+};
+
+// Where member b of a batch takes its noise: arrays override scalars.
+struct NoiseSrc {
+  const double* e;                       // may be null
+  const uint64_t* seed;                  // may be null
+  const uint64_t* traj;                  // may be null
+  double e0;
+  uint64_t seed0;
+  uint64_t traj0;                        // member b draws traj0 + b
+};
+
+// ------------------------------------------------------------- error state
+struct Status {
+  qs_status code = QS_OK;
+  std::string msg;
+};
+
+}  // namespace qs
+
+// The opaque handle of the C ABI.
+struct qs_ctx {
+  int n = 0;
+  int batch = 1;
+  int rank = 0;
+  qs_mode mode = QS_STATEVEC;
+  qs_dtype dtype = QS_C64;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  size_t esize = 8;                      // bytes per complex element
+
+  void* state = nullptr;                 // STATEVEC batch*2^n, DENSITY 4^n, FIXED_RANK rank*2^n
+  size_t state_elems = 0;
+
+  // fixed rank: L' (up to kMaxGramDim columns) and the live column count
+  void* work = nullptr;
+  size_t work_elems = 0;
+  int cols = 1;
+  int normalize = 0;
+
+  // scratch (device)
+  double* partials = nullptr;            // reduction partials
+  size_t partials_cap = 0;               // doubles
+  void* mats = nullptr;                  // per-member gate matrices
+  size_t mats_cap = 0;                   // bytes
+  double* small = nullptr;               // Gram matrix, eigenvectors, results
+  size_t small_cap = 0;                  // doubles
+  int* dstatus = nullptr;                // device status words
+  double* hpinned = nullptr;             // pinned host staging for results
+  size_t hpinned_cap = 0;
+
+  // per-member noise (continuous batching)
+  uint64_t traj_offset = 0;
+  double* m_e = nullptr;
+  uint64_t* m_seed = nullptr;
+  uint64_t* m_traj = nullptr;
+  uint64_t* m_marked = nullptr;
+  bool member_noise = false;
+  bool member_marked = false;
+
+  // stored fidelity reference (2^n complex in the handle's dtype)
+  void* ref = nullptr;
+  bool has_ref = false;
+
+  std::string err;
+};
+
+namespace qs {
+
+// ------------------------------------------------------------ launch glue
+// Every function below enqueues on `s` and returns cudaGetLastError().
+
+size_t elem_size(qs_dtype d);
+
+cudaError_t launch_set_basis(qs_ctx* h, void* psi, int n, int members, uint64_t x,
+                             const uint64_t* xs_dev);
+cudaError_t launch_noise_mats(qs_ctx* h, void* mats, int members, int k, const double* U,
+                              int noise, int diag_only, const NoiseSrc& src, uint64_t gate_id);
+cudaError_t launch_apply_1q(qs_ctx* h, void* psi, int n, int members, int t,
+                            const double* U, const void* mats_dev);
+cudaError_t launch_apply_kq(qs_ctx* h, void* psi, int n, int members, const Targets& tg,
+                            const void* mat_dev, bool per_member);
+cudaError_t launch_apply_diag(qs_ctx* h, void* psi, int n, int members, const Targets& tg,
+                              const void* diag_dev, bool per_member, uint32_t active_mask);
+cudaError_t launch_phase_flip(qs_ctx* h, void* psi, int n, int members, uint64_t index,
+                              const uint64_t* per_member);
+cudaError_t launch_dm_flip(qs_ctx* h, void* rho, int n, uint64_t index);
+
+// reductions (results land in h->small, as doubles)
+cudaError_t launch_dot(qs_ctx* h, const void* psi, const void* ref, int n, int members,
+                       bool sum_members, double* out_dev);
+cudaError_t launch_norm(qs_ctx* h, const void* psi, int n, int members, bool sum_members,
+                        double* out_dev);
+cudaError_t launch_basis_prob(qs_ctx* h, const void* psi, int n, int members, uint64_t x,
+                              bool sum_members, double* out_dev);
+cudaError_t launch_dm_trace(qs_ctx* h, const void* rho, int n, double* out_dev);
+cudaError_t launch_dm_expect(qs_ctx* h, const void* rho, const void* ref, int n, double* out_dev);
+cudaError_t launch_convert_ref(qs_ctx* h, const double* src_dev, void* dst, size_t count);
+
+// fixed rank
+cudaError_t launch_kraus_expand(qs_ctx* h, const void* L, void* Lp, int n, int m, const Targets& tg,
+                                const void* E_dev, int K);
+cudaError_t launch_gram(qs_ctx* h, const void* Lp, int n, int M, double* G_dev);
+cudaError_t launch_eig_truncate(qs_ctx* h, const double* G_dev, int M, int r, int normalize,
+                                double* W_dev, double* lam_dev, double* scale_dev, int* keep_dev,
+                                int* status_dev);
+cudaError_t launch_project(qs_ctx* h, const void* Lp, void* L, int n, int M, const double* W_dev,
+                           const double* scale_dev, const int* keep_dev);
+
+// debug noise
+cudaError_t launch_debug_noise(uint64_t seed, uint64_t traj, uint64_t gate_id, int count,
+                               uint32_t* words_dev, double* normals_dev, cudaStream_t s);
+
+// helpers
+int num_sms();
+NoiseSrc noise_src(qs_ctx* h, double e, uint64_t seed);
+Targets make_targets(int n, const int* targets, int k);
+
+}  // namespace qs

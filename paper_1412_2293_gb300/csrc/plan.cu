@@ -1,0 +1,1245 @@
+// Circuit plans: fused window passes over the state, replayed as CUDA graphs.
+//
+// A pass applies every gate of a run whose dense targets lie in a window of
+// 10 qubits with one read and one write of the state (the amplitude update of
+// Sec. 2 done on a tile in registers and shared memory instead of once per
+// gate in HBM).  Each thread holds 32 amplitudes of a tile that differ in 5
+// "register" bits of the window; a one-qubit gate on a register bit is a
+// butterfly over the thread's registers; an exchange through shared memory
+// swaps which 5 window bits are in registers.
+//
+// Diagonal two-qubit gates with the form diag(1, 1, 1, x) -- the controlled
+// phase shift of Eq. 2 and its Monte Carlo version theta -> theta + e xi
+// (Eqs. 7-8) -- are folded in without touching memory:
+//   * both qubits in the window: applied right where they occur, attached to
+//     the qubit with the higher local index a (a register bit at that point);
+//     consecutive ones attached to the same a form one table
+//     T[x & (2^a - 1)] of products of their factors;
+//   * one or no qubit in the window ("out" terms): they commute with every
+//     dense gate of the pass except ones on their window qubit, so the
+//     planner forbids those and the pass applies all of them at its end.
+// Grover's oracle and diffusion are single-amplitude flips.
+//
+// Geometry LOW: window = qubits 0..9, one warp per 1024 consecutive
+// amplitudes.  Geometry HIGH: 10 qubits >= COLB; a block handles 2^COLB
+// consecutive "columns" (qubits 0..COLB-1) of 1024 window combinations, so
+// every global access moves 2^COLB consecutive elements.
+//
+// Noise of a run: a precompute kernel draws xi for every noisy gate of a pass
+// and every member (Philox, same counters as the single-gate calls), builds
+// the members' matrices, phase tables and out factors, and the pass kernel
+// reads them from a per-member parameter block.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+#include "philox.cuh"
+
+using cd = std::complex<double>;
+
+namespace qs {
+namespace fused {
+
+constexpr int kWin = 10;
+constexpr int kRegBits = 5;
+constexpr int kAmps = 32;
+constexpr int kLowWarps = 8;
+constexpr int kMaxOther = 48;
+// per-pass limits (precompute shared memory <= 24 KB, bounded parameter block)
+constexpr size_t kMaxContribs = 1024;
+constexpr size_t kMaxDwin = 64;
+constexpr size_t kMaxTableEntries = 8192;
+constexpr size_t kMaxOut = 1024;
+constexpr size_t kMaxOps = 4096;
+
+enum : uint8_t { OP_DENSE = 0, OP_DWIN = 1, OP_FLIP = 2, OP_FLIPM = 3, OP_EXCH = 4 };
+
+struct FOp {
+  uint8_t type;
+  uint8_t j;          // local window bit (DENSE, DWIN)
+  uint8_t real;       // DENSE: matrix is real
+  uint8_t pad;
+  uint32_t off;       // parameter offset (R units) in the member block
+  uint64_t index;     // FLIP: member-local amplitude index
+};
+
+struct OutTerm {
+  int32_t a;          // attach local bit, or -1
+  uint32_t off;       // parameter offset of the factor
+  uint64_t cmask;     // member-local out-of-window bits that must be set
+};
+
+struct PassArgs {
+  int n;
+  int start_stage;    // 0 = A, 1 = B
+  int win[kWin];
+  int num_other;      // HIGH: member-local bits that enumerate tiles
+  int other[kMaxOther];
+  int num_ops;
+  const FOp* ops;
+  int out_start[12];  // out terms grouped by attach a (0..9) and 10 = none
+  const OutTerm* outs;
+  int param_stride;   // R units per member
+  const void* params;
+  const uint64_t* marked;
+  uint64_t tiles;
+};
+
+// ---------------------------------------------------------------- registers
+
+template <typename R>
+__device__ __forceinline__ cplx<R> ld_c(const R* p) { return mk<R>(p[0], p[1]); }
+
+template <typename R, int RJ>
+__device__ __forceinline__ void dense_reg(cplx<R> (&a)[kAmps], const R* m, bool real) {
+  if (real) {
+    const R u00 = m[0], u01 = m[2], u10 = m[4], u11 = m[6];
+#pragma unroll
+    for (int r = 0; r < kAmps; ++r) {
+      if (r & (1 << RJ)) continue;
+      const cplx<R> x0 = a[r], x1 = a[r | (1 << RJ)];
+      a[r] = mk<R>(u00 * x0.x + u01 * x1.x, u00 * x0.y + u01 * x1.y);
+      a[r | (1 << RJ)] = mk<R>(u10 * x0.x + u11 * x1.x, u10 * x0.y + u11 * x1.y);
+    }
+  } else {
+    const cplx<R> u00 = ld_c(m), u01 = ld_c(m + 2), u10 = ld_c(m + 4), u11 = ld_c(m + 6);
+#pragma unroll
+    for (int r = 0; r < kAmps; ++r) {
+      if (r & (1 << RJ)) continue;
+      const cplx<R> x0 = a[r], x1 = a[r | (1 << RJ)];
+      a[r] = cfma(u01, x1, cmul(u00, x0));
+      a[r | (1 << RJ)] = cfma(u11, x1, cmul(u10, x0));
+    }
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void dense_dispatch(cplx<R> (&a)[kAmps], int rj, const R* m, bool real) {
+  switch (rj) {
+    case 0: dense_reg<R, 0>(a, m, real); break;
+    case 1: dense_reg<R, 1>(a, m, real); break;
+    case 2: dense_reg<R, 2>(a, m, real); break;
+    case 3: dense_reg<R, 3>(a, m, real); break;
+    default: dense_reg<R, 4>(a, m, real); break;
+  }
+}
+
+// Multiply registers with bit RJ set by T[idx]: stage A idx = tbits | (low
+// register bits << 5), stage B idx = low register bits (bits below RJ).
+template <typename R, int RJ, bool STAGE_A>
+__device__ __forceinline__ void dwin_reg(cplx<R> (&a)[kAmps], const R* T, int tbits) {
+  constexpr int Q = 1 << RJ;
+  cplx<R> f[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int idx = STAGE_A ? (tbits | (q << 5)) : q;
+    f[q] = ld_c(T + 2 * idx);
+  }
+#pragma unroll
+  for (int r = 0; r < kAmps; ++r)
+    if (r & (1 << RJ)) a[r] = cmul(f[r & (Q - 1)], a[r]);
+}
+
+template <typename R>
+__device__ __forceinline__ void dwin_dispatch(cplx<R> (&a)[kAmps], int rj, bool stage_a, const R* T, int tbits) {
+  if (stage_a) {
+    switch (rj) {
+      case 0: dwin_reg<R, 0, true>(a, T, tbits); break;
+      case 1: dwin_reg<R, 1, true>(a, T, tbits); break;
+      case 2: dwin_reg<R, 2, true>(a, T, tbits); break;
+      case 3: dwin_reg<R, 3, true>(a, T, tbits); break;
+      default: dwin_reg<R, 4, true>(a, T, tbits); break;
+    }
+  } else {
+    switch (rj) {
+      case 0: dwin_reg<R, 0, false>(a, T, tbits); break;
+      case 1: dwin_reg<R, 1, false>(a, T, tbits); break;
+      case 2: dwin_reg<R, 2, false>(a, T, tbits); break;
+      case 3: dwin_reg<R, 3, false>(a, T, tbits); break;
+      default: dwin_reg<R, 4, false>(a, T, tbits); break;
+    }
+  }
+}
+
+// Negate register rw when `match`.
+template <typename R>
+__device__ __forceinline__ void flip_reg(cplx<R> (&a)[kAmps], bool match, int rw) {
+#pragma unroll
+  for (int r = 0; r < kAmps; ++r)
+    if (match && r == rw) { a[r].x = -a[r].x; a[r].y = -a[r].y; }
+}
+
+// Register table over the 5 register bits: factor(rho) = c * prod_{r in rho} alpha[r].
+template <typename R>
+__device__ __forceinline__ void apply_reg_product(cplx<R> (&a)[kAmps], cplx<R> c, const cplx<R> (&al)[kRegBits]) {
+  cplx<R> t[kAmps];
+  t[0] = c;
+#pragma unroll
+  for (int r = 0; r < kRegBits; ++r)
+#pragma unroll
+    for (int q = 0; q < (1 << r); ++q) t[q | (1 << r)] = cmul(t[q], al[r]);
+#pragma unroll
+  for (int r = 0; r < kAmps; ++r) a[r] = cmul(t[r], a[r]);
+}
+
+// Member-local index bits of the thread's fixed (non-register) position.
+// gbit(l) = global bit of local window bit l.
+
+// Out factor of attach a for this thread: product of the out terms of a
+// whose out-of-window bits are all set in `fixed`.
+template <typename R>
+__device__ __forceinline__ cplx<R> out_alpha(const PassArgs& A, const R* P, int a, uint64_t fixed) {
+  cplx<R> acc = mk<R>(R(1), R(0));
+  for (int i = A.out_start[a]; i < A.out_start[a + 1]; ++i) {
+    const OutTerm t = A.outs[i];
+    if ((fixed & t.cmask) == t.cmask) acc = cmul(acc, ld_c(P + t.off));
+  }
+  return acc;
+}
+
+// ---------------------------------------------------------------- LOW pass
+// One warp per tile of 1024 consecutive amplitudes (window = qubits 0..9).
+template <typename R>
+__global__ void __launch_bounds__(kLowWarps * 32) k_pass_low(cplx<R>* __restrict__ psi, PassArgs A) {
+  using C = cplx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  C* wsm = sm + warp * 1056;
+  C* alpha_sm = sm + kLowWarps * 1056 + warp * 12;
+  const uint64_t nmask = (1ull << A.n) - 1;
+  const R* params = static_cast<const R*>(A.params);
+
+  for (uint64_t t = (uint64_t)blockIdx.x * kLowWarps + warp; t < A.tiles; t += (uint64_t)gridDim.x * kLowWarps) {
+    const uint64_t base = t << kWin;
+    const uint64_t member = base >> A.n;
+    const uint64_t mloc = base & nmask;                 // member-local tile bits (>= 10)
+    const R* P = params + member * (uint64_t)A.param_stride;
+    C a[kAmps];
+#pragma unroll
+    for (int r = 0; r < kAmps; ++r) a[r] = psi[base + lane + 32 * r];
+    int stage = 0;                                       // loads are in stage A layout
+    for (int i = 0; i < A.num_ops; ++i) {
+      const FOp op = A.ops[i];
+      if (op.type == OP_DENSE) {
+        dense_dispatch<R>(a, stage == 0 ? op.j - 5 : op.j, P + op.off, op.real);
+      } else if (op.type == OP_DWIN) {
+        dwin_dispatch<R>(a, stage == 0 ? op.j - 5 : op.j, stage == 0, P + op.off, lane);
+      } else if (op.type == OP_FLIP || op.type == OP_FLIPM) {
+        const uint64_t w = op.type == OP_FLIP ? op.index : A.marked[member];
+        const uint64_t fixed = mloc | (stage == 0 ? (uint64_t)lane : ((uint64_t)lane << 5));
+        const uint64_t regmask = stage == 0 ? (31ull << 5) : 31ull;
+        const bool match = (w & ~regmask) == fixed;
+        const int rw = stage == 0 ? (int)((w >> 5) & 31) : (int)(w & 31);
+        flip_reg<R>(a, match, rw);
+      } else {                                           // exchange A <-> B
+#pragma unroll
+        for (int r = 0; r < kAmps; ++r) wsm[stage == 0 ? lane + 33 * r : r + 33 * lane] = a[r];
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < kAmps; ++r) a[r] = wsm[stage == 0 ? r + 33 * lane : lane + 33 * r];
+        __syncwarp();
+        stage ^= 1;
+      }
+    }
+    if (A.out_start[11] > 0) {
+      // out terms: all out-of-window bits are the tile's (uniform per warp)
+      if (lane < 11) alpha_sm[lane] = out_alpha<R>(A, P, lane, mloc);
+      __syncwarp();
+      C al[kRegBits];
+      C c = alpha_sm[10];
+#pragma unroll
+      for (int r = 0; r < kRegBits; ++r) {
+        const int lr = stage == 0 ? r + 5 : r;           // local bit of register r
+        al[r] = alpha_sm[lr];
+        const int lt = stage == 0 ? r : r + 5;           // local bit of lane bit r
+        if ((lane >> r) & 1) c = cmul(c, alpha_sm[lt]);
+      }
+      apply_reg_product<R>(a, c, al);
+      __syncwarp();
+    }
+    if (stage == 1) {
+#pragma unroll
+      for (int r = 0; r < kAmps; ++r) wsm[r + 33 * lane] = a[r];
+      __syncwarp();
+#pragma unroll
+      for (int r = 0; r < kAmps; ++r) a[r] = wsm[lane + 33 * r];
+      __syncwarp();
+    }
+#pragma unroll
+    for (int r = 0; r < kAmps; ++r) psi[base + lane + 32 * r] = a[r];
+  }
+}
+
+// ---------------------------------------------------------------- HIGH pass
+template <int COLB> struct HighShape {
+  static constexpr int COLS = 1 << COLB;
+  static constexpr int LW = kRegBits - COLB;            // lane bits that are window bits
+  static constexpr int WARPS = 1 << COLB;               // warp bits = COLB window bits
+  static constexpr int THREADS = WARPS * 32;
+  static constexpr int TILE = COLS * 1024;
+  static constexpr int SMEM_ELEMS = TILE + 32 * 8;      // + padding (x >> 5) * 8
+};
+
+template <int COLB>
+__device__ __forceinline__ int high_sidx(int x, int col) {
+  return x * HighShape<COLB>::COLS + col + (x >> 5) * 8;
+}
+
+template <typename R, int COLB>
+__global__ void __launch_bounds__(HighShape<COLB>::THREADS) k_pass_high(cplx<R>* __restrict__ psi, PassArgs A) {
+  using C = cplx<R>;
+  using S = HighShape<COLB>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  C* alpha_sm = sm + S::SMEM_ELEMS;                     // [COLS][12]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int col = lane & (S::COLS - 1);
+  const int lh = lane >> COLB;
+  const R* params = static_cast<const R*>(A.params);
+  const int tile_shift = A.n - 10 - COLB;               // log2(tiles per member)
+
+  // thread window bits in each stage layout (local x without register bits)
+  const int xa = lh | (warp << S::LW);                  // stage A: local bits 0..4
+  const int xb = (lh << 5) | (warp << (5 + S::LW));     // stage B: local bits 5..9
+  uint64_t offa = 0, offb = 0;
+  for (int l = 0; l < kRegBits; ++l) {
+    if ((xa >> l) & 1) offa |= 1ull << A.win[l];
+    if ((xb >> (l + 5)) & 1) offb |= 1ull << A.win[l + 5];
+  }
+
+  for (uint64_t t = blockIdx.x; t < A.tiles; t += gridDim.x) {
+    const uint64_t member = t >> tile_shift;
+    const uint64_t tl = t & ((1ull << tile_shift) - 1);
+    uint64_t tbits = 0;
+    for (int i = 0; i < A.num_other; ++i) tbits |= ((tl >> i) & 1) << A.other[i];
+    const uint64_t mbase = member << A.n;
+    const R* P = params + member * (uint64_t)A.param_stride;
+    C a[kAmps];
+    int stage = A.start_stage;
+    {
+      const uint64_t b0 = mbase + tbits + col + (stage == 0 ? offa : offb);
+#pragma unroll
+      for (int r = 0; r < kAmps; ++r) {
+        uint64_t off = 0;
+#pragma unroll
+        for (int q = 0; q < kRegBits; ++q)
+          if ((r >> q) & 1) off += 1ull << A.win[stage == 0 ? q + 5 : q];
+        a[r] = psi[b0 + off];
+      }
+    }
+    for (int i = 0; i < A.num_ops; ++i) {
+      const FOp op = A.ops[i];
+      if (op.type == OP_DENSE) {
+        dense_dispatch<R>(a, stage == 0 ? op.j - 5 : op.j, P + op.off, op.real);
+      } else if (op.type == OP_DWIN) {
+        dwin_dispatch<R>(a, stage == 0 ? op.j - 5 : op.j, stage == 0, P + op.off, xa);
+      } else if (op.type == OP_FLIP || op.type == OP_FLIPM) {
+        const uint64_t w = op.type == OP_FLIP ? op.index : A.marked[member];
+        uint64_t regmask = 0;
+        int rw = 0;
+#pragma unroll
+        for (int q = 0; q < kRegBits; ++q) {
+          const int g = A.win[stage == 0 ? q + 5 : q];
+          regmask |= 1ull << g;
+          rw |= (int)((w >> g) & 1) << q;
+        }
+        const uint64_t fixed = tbits | (uint64_t)col | (stage == 0 ? offa : offb);
+        flip_reg<R>(a, (w & ~regmask) == fixed, rw);
+      } else {
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kAmps; ++r) {
+          const int x = stage == 0 ? (xa | (r << 5)) : (r | xb);
+          sm[high_sidx<COLB>(x, col)] = a[r];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kAmps; ++r) {
+          const int x = stage == 0 ? (r | xb) : (xa | (r << 5));
+          a[r] = sm[high_sidx<COLB>(x, col)];
+        }
+        stage ^= 1;
+      }
+    }
+    if (A.out_start[11] > 0) {
+      __syncthreads();
+      // alpha[col][a] for a = 0..9 (window bits) and 10 (no window bit)
+      for (int i = threadIdx.x; i < S::COLS * 11; i += S::THREADS) {
+        const int c = i / 11, aa = i % 11;
+        alpha_sm[c * 12 + aa] = out_alpha<R>(A, P, aa, tbits | (uint64_t)c);
+      }
+      __syncthreads();
+      const C* al_c = alpha_sm + col * 12;
+      C c = al_c[10];
+      C al[kRegBits];
+      const int xt = stage == 0 ? xa : xb;
+#pragma unroll
+      for (int r = 0; r < kRegBits; ++r) {
+        al[r] = al_c[stage == 0 ? r + 5 : r];
+        const int lt = stage == 0 ? r : r + 5;           // thread (non-register) local bit
+        if ((xt >> lt) & 1) c = cmul(c, al_c[lt]);
+      }
+      apply_reg_product<R>(a, c, al);
+    }
+    {
+      const uint64_t b0 = mbase + tbits + col + (stage == 0 ? offa : offb);
+#pragma unroll
+      for (int r = 0; r < kAmps; ++r) {
+        uint64_t off = 0;
+#pragma unroll
+        for (int q = 0; q < kRegBits; ++q)
+          if ((r >> q) & 1) off += 1ull << A.win[stage == 0 ? q + 5 : q];
+        psi[b0 + off] = a[r];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- precompute
+enum : int { PD_DENSE = 0, PD_OUT = 1, PD_DWIN = 2 };
+
+struct DGate {            // a gate as the precompute kernel sees it
+  double U[32];
+  int k;
+  int noisy;
+  int noise;
+  int pad;
+  uint64_t gate_pos;      // position in the circuit (gate id offset)
+};
+
+struct Producer {
+  int kind;
+  int gate;               // DENSE / OUT: gate index
+  int j;                  // DWIN: attach bit; table has 2^j entries
+  int contrib_start, contrib_count;
+  uint32_t off;
+};
+
+struct Contrib {          // DWIN contribution: partner local bit m, gate
+  int m;
+  int gate;
+};
+
+struct RunParams {        // values of one run (written before each launch)
+  double e;
+  uint64_t seed;
+  uint64_t gate_id0;
+  uint64_t traj0;
+};
+
+__device__ __forceinline__ void member_noise(const NoiseSrc& src, const RunParams* rp, int b, double* e,
+                                             uint64_t* seed, uint64_t* traj) {
+  *e = src.e ? src.e[b] : rp->e;
+  *seed = src.seed ? src.seed[b] : rp->seed;
+  *traj = src.traj ? src.traj[b] : rp->traj0 + (uint64_t)b;
+}
+
+// factor of the |1..1> entry of a diag(1,..,1,x) gate for one member
+__device__ __forceinline__ double2 diag_factor(const DGate& g, double e, uint64_t seed, uint64_t traj,
+                                               uint64_t gid) {
+  const int d = 1 << g.k;
+  double re = g.U[2 * ((d - 1) * d + (d - 1))], im = g.U[2 * ((d - 1) * d + (d - 1)) + 1];
+  if (g.noisy && g.noise == QS_NOISE_PHASE) {
+    const double2 xi = noise_normals(seed, traj, gid);
+    double s, c;
+    sincos(e * xi.x, &s, &c);
+    const double t = re * c + im * s;                   // x * e^{-i e xi}
+    im = im * c - re * s;
+    re = t;
+  }
+  return make_double2(re, im);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int stride, const DGate* __restrict__ gates,
+                                                    const Producer* __restrict__ prods, int num_prods,
+                                                    const Contrib* __restrict__ contribs, int num_contribs,
+                                                    int num_dwin, NoiseSrc src, const RunParams* rp) {
+  extern __shared__ double2 pre_sm[];                   // [num_contribs] factors, then [num_dwin][10]
+  const int b = blockIdx.x;
+  double e;
+  uint64_t seed, traj;
+  member_noise(src, rp, b, &e, &seed, &traj);
+  R* out = params + (uint64_t)b * stride;
+  // contributions of the phase tables
+  for (int i = threadIdx.x; i < num_contribs; i += blockDim.x) {
+    const DGate& g = gates[contribs[i].gate];
+    pre_sm[i] = diag_factor(g, e, seed, traj, rp->gate_id0 + g.gate_pos);
+  }
+  // dense matrices and out factors
+  for (int i = threadIdx.x; i < num_prods; i += blockDim.x) {
+    const Producer p = prods[i];
+    if (p.kind == PD_DENSE) {
+      const DGate& g = gates[p.gate];
+      double m[8];
+      for (int q = 0; q < 8; ++q) m[q] = g.U[q];
+      if (g.noisy) {
+        const double2 xi = noise_normals(seed, traj, rp->gate_id0 + g.gate_pos);
+        double s, c;
+        sincos(e * xi.x, &s, &c);
+        if (g.noise == QS_NOISE_ROTATION) {
+          // U * [[c, s], [-s, c]]
+          for (int r = 0; r < 2; ++r) {
+            const double u0r = g.U[4 * r], u0i = g.U[4 * r + 1], u1r = g.U[4 * r + 2], u1i = g.U[4 * r + 3];
+            m[4 * r] = u0r * c - u1r * s;
+            m[4 * r + 1] = u0i * c - u1i * s;
+            m[4 * r + 2] = u0r * s + u1r * c;
+            m[4 * r + 3] = u0i * s + u1i * c;
+          }
+        } else {
+          // U * diag(1, e^{-i e xi})
+          for (int r = 0; r < 2; ++r) {
+            const double ur = g.U[4 * r + 2], ui = g.U[4 * r + 3];
+            m[4 * r + 2] = ur * c + ui * s;
+            m[4 * r + 3] = ui * c - ur * s;
+          }
+        }
+      }
+      for (int q = 0; q < 8; ++q) out[p.off + q] = (R)m[q];
+    } else if (p.kind == PD_OUT) {
+      const DGate& g = gates[p.gate];
+      const double2 f = diag_factor(g, e, seed, traj, rp->gate_id0 + g.gate_pos);
+      out[p.off] = (R)f.x;
+      out[p.off + 1] = (R)f.y;
+    }
+  }
+  __syncthreads();
+  // per-table partner factors f[m], m = 0..9
+  double2* fm = pre_sm + num_contribs;
+  int w = 0;
+  for (int i = 0; i < num_prods; ++i) {
+    const Producer p = prods[i];
+    if (p.kind != PD_DWIN) continue;
+    if (threadIdx.x < kWin) {
+      double2 acc = make_double2(1.0, 0.0);
+      for (int c = p.contrib_start; c < p.contrib_start + p.contrib_count; ++c)
+        if (contribs[c].m == (int)threadIdx.x) {
+          const double2 f = pre_sm[c];
+          acc = make_double2(acc.x * f.x - acc.y * f.y, acc.x * f.y + acc.y * f.x);
+        }
+      fm[w * kWin + threadIdx.x] = acc;
+    }
+    ++w;
+  }
+  __syncthreads();
+  // tables T[x] = prod_{m in x} f[m]
+  w = 0;
+  for (int i = 0; i < num_prods; ++i) {
+    const Producer p = prods[i];
+    if (p.kind != PD_DWIN) continue;
+    const int size = 1 << p.j;
+    for (int x = threadIdx.x; x < size; x += blockDim.x) {
+      double2 acc = make_double2(1.0, 0.0);
+      for (int m = 0; m < p.j; ++m)
+        if ((x >> m) & 1) {
+          const double2 f = fm[w * kWin + m];
+          acc = make_double2(acc.x * f.x - acc.y * f.y, acc.x * f.y + acc.y * f.x);
+        }
+      out[p.off + 2 * x] = (R)acc.x;
+      out[p.off + 2 * x + 1] = (R)acc.y;
+    }
+    ++w;
+  }
+}
+
+}  // namespace fused
+}  // namespace qs
+
+// ======================================================================= host
+using namespace qs;
+using namespace qs::fused;
+
+namespace {
+
+struct PGate {
+  qs_gate g;
+  std::vector<cd> U;
+  bool dense1 = false;    // fusable one-qubit gate
+  bool cp = false;        // fusable diag(1, .., 1, x) two-qubit gate
+  bool flip = false;
+  bool diag = false;      // any diagonal gate (for commutation)
+  uint64_t qmask = 0;     // qubits touched (all for flips)
+};
+
+struct PassPlan {
+  bool high = false;
+  int colb = 3;
+  int win[kWin];
+  int start_stage = 0;
+  std::vector<FOp> ops;
+  std::vector<OutTerm> outs;      // sorted by attach
+  int out_start[12];
+  std::vector<Producer> prods;
+  std::vector<Contrib> contribs;
+  int num_dwin = 0;
+  int stride = 0;                 // R units per member
+  std::vector<int> other;
+  // device copies
+  FOp* d_ops = nullptr;
+  OutTerm* d_outs = nullptr;
+  Producer* d_prods = nullptr;
+  Contrib* d_contribs = nullptr;
+  void* d_params = nullptr;
+};
+
+struct Step {
+  int kind;               // 0 = fused pass, 1 = single gate
+  int pass = -1;
+  int gate = -1;
+};
+
+}  // namespace
+
+struct qs_plan_s {
+  qs_ctx* h = nullptr;
+  std::vector<PGate> gates;
+  std::vector<PassPlan> passes;
+  std::vector<Step> steps;
+  DGate* d_gates = nullptr;
+  RunParams* d_run = nullptr;
+  RunParams* h_run = nullptr;     // pinned
+  cudaGraphExec_t exec = nullptr;
+  bool graph_member_noise = false;
+  bool graph_member_marked = false;
+  void* graph_state = nullptr;
+  int launches = 0;
+  bool timing = false;
+  bool graph_timing = false;
+  std::vector<cudaEvent_t> events;     // launches + 1 when timing
+  std::vector<int> event_kinds;
+  std::string err;
+};
+
+namespace {
+
+qs_status pfail(qs_plan p, qs_status st, const std::string& m) {
+  if (p && p->h) p->h->err = m;
+  if (p) p->err = m;
+  return st;
+}
+
+bool is_diag(const std::vector<cd>& U, int d) {
+  for (int r = 0; r < d; ++r)
+    for (int c = 0; c < d; ++c)
+      if (r != c && U[r * d + c] != cd(0, 0)) return false;
+  return true;
+}
+
+PGate classify(const qs_gate& g, int n) {
+  PGate p;
+  p.g = g;
+  if (g.kind == QS_GATE_FLIP || g.kind == QS_FLIP_PER_MEMBER) {
+    p.flip = true;
+    p.diag = true;
+    p.qmask = n >= 64 ? ~0ull : ((1ull << n) - 1);
+    return p;
+  }
+  const int d = 1 << g.k;
+  p.U.resize(d * d);
+  for (int i = 0; i < d * d; ++i) p.U[i] = cd(g.U[2 * i], g.U[2 * i + 1]);
+  for (int j = 0; j < g.k; ++j) p.qmask |= 1ull << g.targets[j];
+  const bool diag = is_diag(p.U, d);
+  p.diag = diag && (!g.noisy || g.noise == QS_NOISE_PHASE);
+  if (g.k == 1) p.dense1 = true;
+  if (g.k == 2 && diag && (!g.noisy || g.noise == QS_NOISE_PHASE) && p.U[0] == cd(1, 0) &&
+      p.U[5] == cd(1, 0) && p.U[10] == cd(1, 0))
+    p.cp = true;
+  return p;
+}
+
+bool commute(const PGate& a, const PGate& b) {
+  if (a.diag && b.diag) return true;
+  return (a.qmask & b.qmask) == 0;
+}
+
+int stage_of(int j) { return j >= 5 ? 0 : 1; }
+
+// Greedy pass builder starting at remaining[0]; returns absorbed flags.
+bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n, PassPlan* P,
+                std::vector<char>* absorbed) {
+  // window from the first fusable dense gate (lookahead)
+  int q = -1;
+  for (size_t i = 0; i < rem.size() && i < 64; ++i) {
+    const PGate& g = G[rem[i]];
+    if (!g.dense1 && !g.cp && !g.flip) break;
+    if (g.dense1) { q = g.g.targets[0]; break; }
+  }
+  P->high = false;
+  if (q >= 10) {
+    if (n < 13) return false;
+    P->high = true;
+  }
+  for (int l = 0; l < kWin; ++l) P->win[l] = P->high ? n - kWin + l : l;
+  int loc[64];
+  for (int i = 0; i < 64; ++i) loc[i] = -1;
+  for (int l = 0; l < kWin; ++l) loc[P->win[l]] = l;
+
+  std::vector<int> skipped;
+  uint64_t locked = 0;                                  // window local bits with out terms
+  int stage = -1;
+  int dense_count = 0;
+  struct Dw { int j; std::vector<Contrib> cs; };
+  std::vector<Dw> dwins;                                // indexed by producer order
+  std::vector<std::pair<int, int>> out_gates;           // (attach, gate) in order
+  std::vector<uint64_t> out_masks;
+  P->ops.clear();
+  auto need_stage = [&](int st) {
+    if (stage == -1) { stage = st; P->start_stage = P->high ? st : 0; if (!P->high && st == 1) { FOp x{}; x.type = OP_EXCH; P->ops.push_back(x); } }
+    else if (stage != st) { FOp x{}; x.type = OP_EXCH; P->ops.push_back(x); stage = st; }
+  };
+  size_t ncontrib = 0, table_entries = 0;
+  for (size_t i = 0; i < rem.size(); ++i) {
+    const PGate& g = G[rem[i]];
+    if (!g.dense1 && !g.cp && !g.flip) break;           // a gate the pass cannot hold ends the scan
+    // bounds of one pass: precompute shared memory and the per-member block
+    if (ncontrib >= kMaxContribs || dwins.size() >= kMaxDwin || table_entries >= kMaxTableEntries ||
+        out_gates.size() >= kMaxOut || P->ops.size() >= kMaxOps)
+      break;
+    bool ok = true;
+    for (int s : skipped) if (!commute(G[s], g)) { ok = false; break; }
+    bool can = false;
+    if (ok) {
+      if (g.dense1) {
+        const int l = loc[g.g.targets[0]];
+        can = l >= 0 && !((locked >> l) & 1);
+      } else {
+        can = true;                                     // diagonal gates always fit
+      }
+    }
+    if (!can) {
+      skipped.push_back(rem[i]);
+      if (skipped.size() > 96) break;
+      continue;
+    }
+    (*absorbed)[i] = 1;
+    if (g.dense1) {
+      const int l = loc[g.g.targets[0]];
+      need_stage(stage_of(l));
+      FOp x{};
+      x.type = OP_DENSE;
+      x.j = (uint8_t)l;
+      bool real = true;
+      for (const auto& v : g.U) if (v.imag() != 0.0) real = false;
+      if (g.g.noisy && g.g.noise == QS_NOISE_PHASE) real = false;
+      x.real = real ? 1 : 0;
+      Producer pr{};
+      pr.kind = PD_DENSE;
+      pr.gate = rem[i];
+      x.off = (uint32_t)P->prods.size();                // patched to an offset below
+      P->prods.push_back(pr);
+      P->ops.push_back(x);
+      ++dense_count;
+    } else if (g.flip) {
+      FOp x{};
+      x.type = g.g.kind == QS_GATE_FLIP ? OP_FLIP : OP_FLIPM;
+      x.index = g.g.index;
+      P->ops.push_back(x);
+    } else {
+      const int p0 = g.g.targets[0], p1 = g.g.targets[1];
+      const int l0 = loc[p0], l1 = loc[p1];
+      if (l0 >= 0 && l1 >= 0) {
+        const int a = std::max(l0, l1), m = std::min(l0, l1);
+        need_stage(stage_of(a));
+        if (!P->ops.empty() && P->ops.back().type == OP_DWIN && P->ops.back().j == a) {
+          dwins[P->ops.back().off].cs.push_back(Contrib{m, rem[i]});
+        } else {
+          FOp x{};
+          x.type = OP_DWIN;
+          x.j = (uint8_t)a;
+          x.off = (uint32_t)dwins.size();
+          dwins.push_back(Dw{a, {Contrib{m, rem[i]}}});
+          P->ops.push_back(x);
+          table_entries += 1u << a;
+        }
+        ++ncontrib;
+      } else {
+        int a = -1;
+        uint64_t cm = 0;
+        if (l0 >= 0) { a = l0; cm = 1ull << p1; }
+        else if (l1 >= 0) { a = l1; cm = 1ull << p0; }
+        else { cm = (1ull << p0) | (1ull << p1); }
+        if (a >= 0) locked |= 1ull << a;
+        out_gates.push_back({a, rem[i]});
+        out_masks.push_back(cm);
+      }
+    }
+  }
+  if (dense_count == 0 && out_gates.empty() && dwins.empty()) {
+    // only flips (or nothing): not worth a pass unless something was absorbed
+    bool any = false;
+    for (char c : *absorbed) any |= c != 0;
+    if (!any) return false;
+  }
+  if (stage == -1) { stage = 0; P->start_stage = 0; }
+
+  // parameter layout: dense matrices, tables, out factors
+  std::vector<Producer> prods;
+  uint32_t off = 0;
+  for (auto& x : P->ops) {
+    if (x.type == OP_DENSE) {
+      Producer pr = P->prods[x.off];
+      pr.off = off;
+      x.off = off;
+      off += 8;
+      prods.push_back(pr);
+    }
+  }
+  P->contribs.clear();
+  P->num_dwin = 0;
+  for (auto& x : P->ops) {
+    if (x.type == OP_DWIN) {
+      Dw& d = dwins[x.off];
+      Producer pr{};
+      pr.kind = PD_DWIN;
+      pr.j = d.j;
+      pr.contrib_start = (int)P->contribs.size();
+      pr.contrib_count = (int)d.cs.size();
+      for (auto& c : d.cs) P->contribs.push_back(c);
+      pr.off = off;
+      x.off = off;
+      off += 2u << d.j;
+      prods.push_back(pr);
+      ++P->num_dwin;
+    }
+  }
+  // out terms sorted by attach (a = -1 last)
+  std::vector<int> order(out_gates.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const int ax = out_gates[x].first < 0 ? 10 : out_gates[x].first;
+    const int ay = out_gates[y].first < 0 ? 10 : out_gates[y].first;
+    return ax < ay;
+  });
+  P->outs.clear();
+  for (int i = 0; i < 12; ++i) P->out_start[i] = 0;
+  int cnt[11] = {0};
+  for (int idx : order) {
+    const int a = out_gates[idx].first;
+    OutTerm t{};
+    t.a = a;
+    t.off = off;
+    t.cmask = out_masks[idx];
+    Producer pr{};
+    pr.kind = PD_OUT;
+    pr.gate = out_gates[idx].second;
+    pr.off = off;
+    off += 2;
+    prods.push_back(pr);
+    P->outs.push_back(t);
+    cnt[a < 0 ? 10 : a]++;
+  }
+  int acc = 0;
+  for (int a = 0; a < 11; ++a) { P->out_start[a] = acc; acc += cnt[a]; }
+  P->out_start[11] = acc;
+  P->prods = prods;
+  P->stride = (int)((off + 3) & ~3u);
+  if (P->high) {
+    P->other.clear();
+    for (int b = P->colb; b < n; ++b) if (loc[b] < 0) P->other.push_back(b);
+  }
+  return true;
+}
+
+template <typename T>
+qs_status upload(qs_plan p, T** dst, const std::vector<T>& v) {
+  if (v.empty()) { *dst = nullptr; return QS_OK; }
+  if (cudaMalloc((void**)dst, v.size() * sizeof(T)) != cudaSuccess) return pfail(p, QS_ERR_OUT_OF_MEMORY, "plan upload");
+  if (cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+    return pfail(p, QS_ERR_CUDA, "plan upload copy");
+  return QS_OK;
+}
+
+size_t high_smem(int colb, size_t esize) {
+  const size_t cols = 1u << colb;
+  return (cols * 1024 + 32 * 8) * esize + cols * 12 * esize;
+}
+
+size_t low_smem(size_t esize) { return (kLowWarps * 1056 + kLowWarps * 12) * esize; }
+
+PassArgs pass_args(qs_plan p, const PassPlan& P) {
+  qs_ctx* h = p->h;
+  PassArgs A{};
+  A.n = h->n;
+  A.start_stage = P.start_stage;
+  for (int l = 0; l < kWin; ++l) A.win[l] = P.win[l];
+  A.num_other = (int)P.other.size();
+  for (int i = 0; i < A.num_other && i < kMaxOther; ++i) A.other[i] = P.other[i];
+  A.num_ops = (int)P.ops.size();
+  A.ops = P.d_ops;
+  for (int i = 0; i < 12; ++i) A.out_start[i] = P.out_start[i];
+  A.outs = P.d_outs;
+  A.param_stride = P.stride;
+  A.params = P.d_params;
+  A.marked = h->m_marked;
+  const uint64_t total = (uint64_t)h->batch << h->n;
+  A.tiles = P.high ? total >> (10 + P.colb) : total >> 10;
+  return A;
+}
+
+// Members' noise draws, matrices, phase tables and out factors of one pass.
+template <typename R>
+cudaError_t launch_precompute(qs_plan p, const PassPlan& P, cudaStream_t s) {
+  qs_ctx* h = p->h;
+  NoiseSrc src{};
+  if (h->member_noise) { src.e = h->m_e; src.seed = h->m_seed; src.traj = h->m_traj; }
+  const size_t pre_smem = (P.contribs.size() + (size_t)P.num_dwin * kWin) * sizeof(double2);
+  k_precompute<R><<<h->batch, 128, pre_smem, s>>>((R*)P.d_params, P.stride, p->d_gates, P.d_prods,
+                                                   (int)P.prods.size(), P.d_contribs, (int)P.contribs.size(),
+                                                   P.num_dwin, src, p->d_run);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_pass_kernel(qs_plan p, const PassPlan& P, cudaStream_t s) {
+  qs_ctx* h = p->h;
+  const PassArgs A = pass_args(p, P);
+  const int sms = num_sms();
+  if (!P.high) {
+    const size_t sm = low_smem(sizeof(cplx<R>));
+    uint64_t blocks = (A.tiles + kLowWarps - 1) / kLowWarps;
+    const uint64_t cap = (uint64_t)sms * 8;
+    if (blocks > cap) blocks = cap;
+    k_pass_low<R><<<(int)blocks, kLowWarps * 32, sm, s>>>((cplx<R>*)h->state, A);
+  } else {
+    const size_t sm = high_smem(P.colb, sizeof(cplx<R>));
+    uint64_t blocks = A.tiles;
+    const uint64_t cap = (uint64_t)sms * 8;
+    if (blocks > cap) blocks = cap;
+    if constexpr (sizeof(R) == 4) {
+      if (P.colb == 4) k_pass_high<R, 4><<<(int)blocks, HighShape<4>::THREADS, sm, s>>>((cplx<R>*)h->state, A);
+      else k_pass_high<R, 3><<<(int)blocks, HighShape<3>::THREADS, sm, s>>>((cplx<R>*)h->state, A);
+    } else {
+      k_pass_high<R, 3><<<(int)blocks, HighShape<3>::THREADS, sm, s>>>((cplx<R>*)h->state, A);
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass(qs_plan p, const PassPlan& P, cudaStream_t s) {
+  const bool f32 = p->h->dtype == QS_C64;
+  cudaError_t e = f32 ? launch_precompute<float>(p, P, s) : launch_precompute<double>(p, P, s);
+  if (e != cudaSuccess) return e;
+  return f32 ? launch_pass_kernel<float>(p, P, s) : launch_pass_kernel<double>(p, P, s);
+}
+
+cudaError_t set_smem_attrs(size_t esize) {
+  static bool done[2] = {false, false};
+  const int which = esize == 8 ? 0 : 1;
+  if (done[which]) return cudaSuccess;
+  cudaError_t e;
+  if (esize == 8) {
+    e = cudaFuncSetAttribute(k_pass_low<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)low_smem(8));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass_high<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)high_smem(3, 8));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass_high<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)high_smem(4, 8));
+  } else {
+    e = cudaFuncSetAttribute(k_pass_low<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)low_smem(16));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass_high<double, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)high_smem(3, 16));
+  }
+  if (e == cudaSuccess) done[which] = true;
+  return e;
+}
+
+}  // namespace
+
+namespace {
+
+qs_status run_single(qs_plan p, const PGate& g, const RunParams& rp, int pos) {
+  qs_ctx* h = p->h;
+  if (g.g.kind == QS_GATE_FLIP) return qs_apply_phase_flip(h, g.g.index);
+  if (g.g.kind == QS_FLIP_PER_MEMBER) {
+    cudaError_t e = launch_phase_flip(h, h->state, h->n, h->batch, 0, h->m_marked);
+    return e == cudaSuccess ? QS_OK : pfail(p, QS_ERR_CUDA, cudaGetErrorString(e));
+  }
+  if (g.g.noisy)
+    return qs_apply_noisy_gate(h, g.g.targets, g.g.k, g.g.U, (qs_noise)g.g.noise, rp.e, rp.seed,
+                               rp.gate_id0 + (uint64_t)pos);
+  return qs_apply_gate(h, g.g.targets, g.g.k, g.g.U);
+}
+
+qs_status enqueue_run(qs_plan p, cudaStream_t s) {
+  qs_ctx* h = p->h;
+  cudaStream_t saved = h->stream;
+  h->stream = s;
+  size_t ev = 0;
+  auto mark = [&](int kind) {
+    if (!p->timing) return;
+    // external: under stream capture this becomes an event-record node
+    cudaEventRecordWithFlags(p->events[ev], s, cudaEventRecordExternal);
+    if (ev > 0) p->event_kinds[ev - 1] = kind;
+    ++ev;
+  };
+  mark(-1);
+  const bool f32 = h->dtype == QS_C64;
+  for (const Step& st : p->steps) {
+    if (st.kind == 0) {
+      const PassPlan& P = p->passes[st.pass];
+      cudaError_t e = f32 ? launch_precompute<float>(p, P, s) : launch_precompute<double>(p, P, s);
+      mark(0);
+      if (e == cudaSuccess) e = f32 ? launch_pass_kernel<float>(p, P, s) : launch_pass_kernel<double>(p, P, s);
+      mark(P.high ? 2 : 1);
+      if (e != cudaSuccess) { h->stream = saved; return pfail(p, QS_ERR_CUDA, std::string("fused pass: ") + cudaGetErrorString(e)); }
+    } else {
+      qs_status r = run_single(p, p->gates[st.gate], *p->h_run, st.gate);
+      mark(3);
+      if (r != QS_OK) { h->stream = saved; return r; }
+    }
+  }
+  h->stream = saved;
+  return QS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_plan* out) {
+  if (!h || !out || (num_gates > 0 && !gates) || num_gates < 0) return QS_ERR_INVALID_ARG;
+  *out = nullptr;
+  qs_plan p = new (std::nothrow) qs_plan_s();
+  if (!p) return QS_ERR_OUT_OF_MEMORY;
+  p->h = h;
+  // validate
+  for (int i = 0; i < num_gates; ++i) {
+    const qs_gate& g = gates[i];
+    if (g.kind == QS_GATE_FLIP) {
+      if (g.index >= (1ull << h->n)) { delete p; h->err = "flip index out of range"; return QS_ERR_INVALID_ARG; }
+    } else if (g.kind == QS_FLIP_PER_MEMBER) {
+      if (h->mode != QS_STATEVEC) { delete p; h->err = "per-member flips need STATEVEC"; return QS_ERR_NOT_SUPPORTED; }
+    } else if (g.kind == QS_GATE_DENSE) {
+      if (g.k < 1 || g.k > 2) { delete p; h->err = "plan gates must have k = 1 or 2"; return QS_ERR_INVALID_ARG; }
+      for (int j = 0; j < g.k; ++j) {
+        if (g.targets[j] < 0 || g.targets[j] >= h->n) { delete p; h->err = "target out of range"; return QS_ERR_INVALID_ARG; }
+        for (int q = 0; q < j; ++q)
+          if (g.targets[q] == g.targets[j]) { delete p; h->err = "duplicate target"; return QS_ERR_INVALID_ARG; }
+      }
+      if (g.noisy && g.noise != QS_NOISE_ROTATION && g.noise != QS_NOISE_PHASE) { delete p; h->err = "bad noise kind"; return QS_ERR_INVALID_ARG; }
+    } else {
+      delete p;
+      h->err = "bad gate kind";
+      return QS_ERR_INVALID_ARG;
+    }
+    p->gates.push_back(classify(g, h->n));
+  }
+  const bool fuse = h->mode == QS_STATEVEC && h->n >= 10;
+  std::vector<int> rem;
+  for (int i = 0; i < num_gates; ++i) rem.push_back(i);
+  while (!rem.empty()) {
+    if (fuse) {
+      PassPlan P;
+      std::vector<char> absorbed(rem.size(), 0);
+      if (build_pass(p->gates, rem, h->n, &P, &absorbed)) {
+        bool any = false;
+        for (char c : absorbed) any |= c != 0;
+        if (any) {
+          p->passes.push_back(P);
+          p->steps.push_back(Step{0, (int)p->passes.size() - 1, -1});
+          std::vector<int> next;
+          for (size_t i = 0; i < rem.size(); ++i) if (!absorbed[i]) next.push_back(rem[i]);
+          rem.swap(next);
+          continue;
+        }
+      }
+    }
+    p->steps.push_back(Step{1, -1, rem[0]});
+    rem.erase(rem.begin());
+  }
+  // device data
+  std::vector<DGate> dg(p->gates.size());
+  for (size_t i = 0; i < p->gates.size(); ++i) {
+    const qs_gate& g = p->gates[i].g;
+    DGate x{};
+    for (int q = 0; q < 32; ++q) x.U[q] = g.U[q];
+    x.k = g.k;
+    x.noisy = g.noisy;
+    x.noise = g.noise;
+    x.gate_pos = i;
+    dg[i] = x;
+  }
+  qs_status st = upload(p, &p->d_gates, dg);
+  for (auto& P : p->passes) {
+    if (st != QS_OK) break;
+    st = upload(p, &P.d_ops, P.ops);
+    if (st == QS_OK) st = upload(p, &P.d_outs, P.outs);
+    if (st == QS_OK) st = upload(p, &P.d_prods, P.prods);
+    if (st == QS_OK) st = upload(p, &P.d_contribs, P.contribs);
+    if (st == QS_OK) {
+      const size_t bytes = (size_t)P.stride * h->batch * (h->esize / 2);
+      if (cudaMalloc(&P.d_params, std::max<size_t>(bytes, 16)) != cudaSuccess) st = pfail(p, QS_ERR_OUT_OF_MEMORY, "plan params");
+    }
+  }
+  if (st == QS_OK && cudaMalloc((void**)&p->d_run, sizeof(RunParams)) != cudaSuccess) st = pfail(p, QS_ERR_OUT_OF_MEMORY, "run params");
+  if (st == QS_OK && cudaMallocHost((void**)&p->h_run, sizeof(RunParams)) != cudaSuccess) st = pfail(p, QS_ERR_OUT_OF_MEMORY, "run params");
+  if (st == QS_OK && set_smem_attrs(h->esize) != cudaSuccess) st = pfail(p, QS_ERR_CUDA, "shared memory attribute");
+  if (st != QS_OK) { qs_plan_destroy(p); return st; }
+  p->launches = 0;
+  for (const Step& s : p->steps) p->launches += s.kind == 0 ? 2 : 1;
+  *out = p;
+  return QS_OK;
+}
+
+qs_status qs_plan_run(qs_plan p, double e, uint64_t seed, uint64_t gate_id0) {
+  if (!p) return QS_ERR_INVALID_ARG;
+  qs_ctx* h = p->h;
+  if (!(e >= 0.0) || !std::isfinite(e)) return pfail(p, QS_ERR_INVALID_ARG, "e must be finite and >= 0");
+  for (const PGate& g : p->gates)
+    if (g.g.kind == QS_FLIP_PER_MEMBER && !h->member_marked)
+      return pfail(p, QS_ERR_INVALID_ARG, "per-member flips need marked indices (qs_set_member_noise)");
+  // the pinned run block may still be read by an earlier launch of the graph
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "stream sync");
+  p->h_run->e = e;
+  p->h_run->seed = seed;
+  p->h_run->gate_id0 = gate_id0;
+  p->h_run->traj0 = h->traj_offset;
+  const bool has_single = std::any_of(p->steps.begin(), p->steps.end(), [](const Step& s) { return s.kind == 1; });
+  if (has_single) {
+    // single-gate steps take e, seed and ids as host arguments: run eagerly
+    if (cudaMemcpyAsync(p->d_run, p->h_run, sizeof(RunParams), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+      return pfail(p, QS_ERR_CUDA, "run params copy");
+    return enqueue_run(p, h->stream);
+  }
+  const bool stale = p->exec && (p->graph_member_noise != h->member_noise ||
+                                 p->graph_member_marked != h->member_marked || p->graph_state != h->state ||
+                                 p->graph_timing != p->timing);
+  if (stale) { cudaGraphExecDestroy(p->exec); p->exec = nullptr; }
+  if (!p->exec) {
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "capture stream");
+    cudaGraph_t graph;
+    cudaError_t e1 = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e1 == cudaSuccess) e1 = cudaMemcpyAsync(p->d_run, p->h_run, sizeof(RunParams), cudaMemcpyHostToDevice, cs);
+    qs_status st = e1 == cudaSuccess ? enqueue_run(p, cs) : QS_ERR_CUDA;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    if (st != QS_OK) return st;
+    if (e1 != cudaSuccess || e2 != cudaSuccess) return pfail(p, QS_ERR_CUDA, "graph capture");
+    cudaError_t e3 = cudaGraphInstantiate(&p->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e3 != cudaSuccess) { p->exec = nullptr; return pfail(p, QS_ERR_CUDA, "graph instantiate"); }
+    p->graph_member_noise = h->member_noise;
+    p->graph_member_marked = h->member_marked;
+    p->graph_state = h->state;
+    p->graph_timing = p->timing;
+  }
+  if (cudaGraphLaunch(p->exec, h->stream) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "graph launch");
+  return QS_OK;
+}
+
+qs_status qs_plan_profile(qs_plan p, int reps, double e, uint64_t seed, uint64_t gate_id0, double* ms,
+                          int* kinds, int cap, int* count) {
+  if (!p || reps < 1 || !ms || !kinds || !count) return QS_ERR_INVALID_ARG;
+  qs_ctx* h = p->h;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "stream sync");
+  p->h_run->e = e;
+  p->h_run->seed = seed;
+  p->h_run->gate_id0 = gate_id0;
+  p->h_run->traj0 = h->traj_offset;
+  if (cudaMemcpyAsync(p->d_run, p->h_run, sizeof(RunParams), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return pfail(p, QS_ERR_CUDA, "run params copy");
+  int nl = 0;
+  for (const Step& st : p->steps) nl += st.kind == 0 ? 2 : 1;
+  std::vector<cudaEvent_t> ev((size_t)nl * reps + 1);
+  for (auto& x : ev) if (cudaEventCreate(&x) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "event create");
+  std::vector<int> kind(nl);
+  size_t k = 0;
+  qs_status result = QS_OK;
+  cudaEventRecord(ev[k++], h->stream);
+  for (int r = 0; r < reps && result == QS_OK; ++r) {
+    int li = 0;
+    for (const Step& st : p->steps) {
+      if (st.kind == 0) {
+        const PassPlan& P = p->passes[st.pass];
+        const bool f32 = h->dtype == QS_C64;
+        cudaError_t x = f32 ? launch_precompute<float>(p, P, h->stream) : launch_precompute<double>(p, P, h->stream);
+        cudaEventRecord(ev[k++], h->stream);
+        kind[li++] = 0;
+        if (x == cudaSuccess) x = f32 ? launch_pass_kernel<float>(p, P, h->stream) : launch_pass_kernel<double>(p, P, h->stream);
+        cudaEventRecord(ev[k++], h->stream);
+        kind[li++] = P.high ? 2 : 1;
+        if (x != cudaSuccess) { result = pfail(p, QS_ERR_CUDA, cudaGetErrorString(x)); break; }
+      } else {
+        result = run_single(p, p->gates[st.gate], *p->h_run, st.gate);
+        cudaEventRecord(ev[k++], h->stream);
+        kind[li++] = 3;
+        if (result != QS_OK) break;
+      }
+    }
+  }
+  if (cudaEventSynchronize(ev[k - 1]) != cudaSuccess && result == QS_OK) result = pfail(p, QS_ERR_CUDA, "profile sync");
+  if (result == QS_OK) {
+    for (int i = 0; i < nl && i < cap; ++i) {
+      double acc = 0.0;
+      for (int r = 0; r < reps; ++r) {
+        float t = 0.f;
+        const size_t a = (size_t)r * nl + i;
+        cudaEventElapsedTime(&t, ev[a], ev[a + 1]);
+        acc += t;
+      }
+      ms[i] = acc / reps;
+      kinds[i] = kind[i];
+    }
+    *count = nl;
+  }
+  for (auto& x : ev) cudaEventDestroy(x);
+  return result;
+}
+
+qs_status qs_plan_set_timing(qs_plan p, int on) {
+  if (!p) return QS_ERR_INVALID_ARG;
+  if (on && p->events.empty()) {
+    p->events.resize((size_t)p->launches + 1);
+    p->event_kinds.assign((size_t)p->launches, 0);
+    for (auto& e : p->events)
+      if (cudaEventCreate(&e) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "event create");
+  }
+  p->timing = on != 0;
+  return QS_OK;
+}
+
+qs_status qs_plan_last_times(qs_plan p, double* ms, int* kinds, int cap, int* count) {
+  if (!p || !ms || !kinds || !count) return QS_ERR_INVALID_ARG;
+  if (!p->timing || p->events.empty()) return pfail(p, QS_ERR_INVALID_ARG, "timing is off");
+  if (cudaEventSynchronize(p->events.back()) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "event sync");
+  const int nl = p->launches;
+  for (int i = 0; i < nl && i < cap; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, p->events[i], p->events[i + 1]) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "elapsed");
+    ms[i] = t;
+    kinds[i] = p->event_kinds[i];
+  }
+  *count = nl;
+  return QS_OK;
+}
+
+qs_status qs_plan_info(qs_plan p, int* passes, int* launches) {
+  if (!p) return QS_ERR_INVALID_ARG;
+  if (passes) *passes = (int)p->steps.size();
+  if (launches) *launches = p->launches;
+  return QS_OK;
+}
+
+qs_status qs_plan_destroy(qs_plan p) {
+  if (!p) return QS_ERR_INVALID_ARG;
+  if (p->h) cudaStreamSynchronize(p->h->stream);
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  for (auto& P : p->passes) {
+    void* ptrs[] = {P.d_ops, P.d_outs, P.d_prods, P.d_contribs, P.d_params};
+    for (void* x : ptrs) if (x) cudaFree(x);
+  }
+  if (p->d_gates) cudaFree(p->d_gates);
+  if (p->d_run) cudaFree(p->d_run);
+  if (p->h_run) cudaFreeHost(p->h_run);
+  for (auto& e : p->events) cudaEventDestroy(e);
+  delete p;
+  return QS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,390 @@
+// Amplitude sweeps: one HBM read and write of the state per gate.
+//
+// The update is the one of Sec. 2: for a one-qubit gate on qubit t every
+// pair (a[i0], a[i0 | 2^t]) with bit t of i0 clear is replaced by U times the
+// pair; a k-qubit gate does the same on groups of 2^k amplitudes.  A batch of
+// members (Monte Carlo trajectories, or factor columns) is one long array;
+// the member of a pair is its index >> n, which gives per-member noisy
+// matrices (Eqs. 1-2) without any extra indexing.
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+#include "philox.cuh"
+
+namespace qs {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+inline int grid_for(uint64_t work, int per_thread = 1) {
+  const uint64_t threads = (work + per_thread - 1) / per_thread;
+  uint64_t blocks = (threads + kBlock - 1) / kBlock;
+  const uint64_t cap = (uint64_t)num_sms() * 16;   // enough resident blocks; grid-stride beyond
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  return (int)blocks;
+}
+
+// insert a zero bit at position s
+__device__ __forceinline__ uint64_t insert0(uint64_t v, int s) {
+  const uint64_t low = v & ((1ull << s) - 1);
+  return ((v >> s) << (s + 1)) | low;
+}
+
+template <typename R>
+__global__ void k_set_basis(cplx<R>* psi, int n, int members, uint64_t x, const uint64_t* xs) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < members) {
+    const uint64_t xi = xs ? xs[b] : x;
+    psi[((uint64_t)b << n) + xi] = mk<R>(R(1), R(0));
+  }
+}
+
+// One matrix per member: the ideal U (FP64, interleaved) times the noise of
+// that member (Eqs. 1, 2, 5, 7, 8), rounded to R.  diag_only writes only the
+// 2^k diagonal entries (a diagonal U under phase noise stays diagonal).
+struct DMat { double v[2 * 16]; };
+
+template <typename R>
+__global__ void k_noise_mats(R* out, int members, int k, DMat U, int noise, int diag_only,
+                             NoiseSrc src, uint64_t gate_id) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= members) return;
+  const double e = src.e ? src.e[b] : src.e0;
+  const uint64_t seed = src.seed ? src.seed[b] : src.seed0;
+  const uint64_t traj = src.traj ? src.traj[b] : src.traj0 + (uint64_t)b;
+  const double2 xi = noise_normals(seed, traj, gate_id);
+  const int d = 1 << k;
+  double N[16][2];   // noise matrix entries of column c used below, real or complex
+  (void)N;
+  if (noise == QS_NOISE_ROTATION) {
+    // V(a) = [[cos a, sin a], [-sin a, cos a]] on each target; targets[0] is
+    // the low local bit.  Real matrix NV[r][c] = prod_j V_j[r_j][c_j].
+    double ca, sa, cb = 1.0, sb = 0.0;
+    sincos(e * xi.x, &sa, &ca);
+    if (k == 2) sincos(e * xi.y, &sb, &cb);
+    const double Va[2][2] = {{ca, sa}, {-sa, ca}};
+    const double Vb[2][2] = {{cb, sb}, {-sb, cb}};
+    R* o = out + (size_t)b * 2 * d * d;
+    for (int r = 0; r < d; ++r) {
+      for (int c = 0; c < d; ++c) {
+        double re = 0.0, im = 0.0;
+        for (int m = 0; m < d; ++m) {
+          double nv = Va[m & 1][c & 1];
+          if (k == 2) nv *= Vb[(m >> 1) & 1][(c >> 1) & 1];
+          re += U.v[2 * (r * d + m)] * nv;
+          im += U.v[2 * (r * d + m) + 1] * nv;
+        }
+        o[2 * (r * d + c)] = (R)re;
+        o[2 * (r * d + c) + 1] = (R)im;
+      }
+    }
+  } else {
+    // U * diag(1, .., 1, e^{-i e xi_a})
+    double s, c;
+    sincos(e * xi.x, &s, &c);
+    const double pr = c, pi = -s;
+    if (diag_only) {
+      R* o = out + (size_t)b * 2 * d;
+      for (int r = 0; r < d; ++r) {
+        double re = U.v[2 * (r * d + r)], im = U.v[2 * (r * d + r) + 1];
+        if (r == d - 1) {
+          const double t = re * pr - im * pi;
+          im = re * pi + im * pr;
+          re = t;
+        }
+        o[2 * r] = (R)re;
+        o[2 * r + 1] = (R)im;
+      }
+    } else {
+      R* o = out + (size_t)b * 2 * d * d;
+      for (int r = 0; r < d; ++r) {
+        for (int cc = 0; cc < d; ++cc) {
+          double re = U.v[2 * (r * d + cc)], im = U.v[2 * (r * d + cc) + 1];
+          if (cc == d - 1) {
+            const double t = re * pr - im * pi;
+            im = re * pi + im * pr;
+            re = t;
+          }
+          o[2 * (r * d + cc)] = (R)re;
+          o[2 * (r * d + cc) + 1] = (R)im;
+        }
+      }
+    }
+  }
+}
+
+template <typename R> struct Mat2 { cplx<R> m00, m01, m10, m11; };
+
+template <typename R>
+__device__ __forceinline__ Mat2<R> load_mat2(const R* p) {
+  Mat2<R> m;
+  m.m00 = mk<R>(p[0], p[1]); m.m01 = mk<R>(p[2], p[3]);
+  m.m10 = mk<R>(p[4], p[5]); m.m11 = mk<R>(p[6], p[7]);
+  return m;
+}
+
+// Pair sweep (Sec. 2): npairs = members * 2^(n-1).  Member of pair p is
+// p >> (n-1); its matrix is mats[member] when PER_MEMBER.
+template <typename R, bool PER_MEMBER>
+__global__ void __launch_bounds__(kBlock) k_apply_1q(cplx<R>* __restrict__ psi, int n, int t,
+                                                     uint64_t npairs, Mat2<R> mu,
+                                                     const R* __restrict__ mats) {
+  using C = cplx<R>;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t bit = 1ull << t;
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += stride) {
+    const uint64_t i0 = insert0(p, t);
+    const uint64_t i1 = i0 | bit;
+    Mat2<R> m = mu;
+    if (PER_MEMBER) m = load_mat2<R>(mats + (p >> (n - 1)) * 8);
+    const C a0 = psi[i0], a1 = psi[i1];
+    psi[i0] = cfma(m.m01, a1, cmul(m.m00, a0));
+    psi[i1] = cfma(m.m11, a1, cmul(m.m10, a0));
+  }
+}
+
+// Dense k-qubit gate (k <= 4) on groups of 2^k amplitudes.
+template <typename R, int K>
+__global__ void __launch_bounds__(kBlock) k_apply_kq(cplx<R>* __restrict__ psi, int n,
+                                                     uint64_t ngroups, Targets tg,
+                                                     const R* __restrict__ mat, int per_member) {
+  using C = cplx<R>;
+  constexpr int D = 1 << K;
+  __shared__ C sm[D * D];
+  if (!per_member) {
+    for (int i = threadIdx.x; i < D * D; i += blockDim.x) sm[i] = mk<R>(mat[2 * i], mat[2 * i + 1]);
+    __syncthreads();
+  }
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
+    uint64_t base = g;
+#pragma unroll
+    for (int j = 0; j < K; ++j) base = insert0(base, tg.sorted[j]);
+    C a[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) a[l] = psi[base + tg.off[l]];
+    const R* mp = per_member ? mat + (g >> (n - K)) * 2 * D * D : nullptr;
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      C acc = mk<R>(R(0), R(0));
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const C m = per_member ? mk<R>(mp[2 * (r * D + c)], mp[2 * (r * D + c) + 1]) : sm[r * D + c];
+        acc = cfma(m, a[c], acc);
+      }
+      psi[base + tg.off[r]] = acc;
+    }
+  }
+}
+
+// Diagonal k-qubit gate: amplitude with local index l is multiplied by d[l];
+// only the local indices in active_mask are touched (d[l] = 1 elsewhere).
+template <typename R, int K>
+__global__ void __launch_bounds__(kBlock) k_apply_diag(cplx<R>* __restrict__ psi, int n,
+                                                       uint64_t ngroups, Targets tg,
+                                                       const R* __restrict__ diag, int per_member,
+                                                       uint32_t active_mask) {
+  using C = cplx<R>;
+  constexpr int D = 1 << K;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
+    uint64_t base = g;
+#pragma unroll
+    for (int j = 0; j < K; ++j) base = insert0(base, tg.sorted[j]);
+    const R* dp = per_member ? diag + (g >> (n - K)) * 2 * D : diag;
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+      if (active_mask & (1u << l)) {
+        const uint64_t i = base + tg.off[l];
+        psi[i] = cmul(mk<R>(dp[2 * l], dp[2 * l + 1]), psi[i]);
+      }
+    }
+  }
+}
+
+template <typename R>
+__global__ void k_phase_flip(cplx<R>* psi, int n, int members, uint64_t index, const uint64_t* per) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < members) {
+    const uint64_t i = ((uint64_t)b << n) + (per ? per[b] : index);
+    cplx<R> v = psi[i];
+    v.x = -v.x; v.y = -v.y;
+    psi[i] = v;
+  }
+}
+
+// rho <- F rho F, F = I - 2|w><w|, on vec index i * 2^n + j: negate row w
+// and column w (the (w, w) entry twice, i.e. unchanged).
+template <typename R>
+__global__ void k_dm_flip(cplx<R>* rho, int n, uint64_t w) {
+  const uint64_t N = 1ull << n;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (uint64_t)gridDim.x * blockDim.x) {
+    if (j == w) continue;
+    cplx<R>* a = rho + w * N + j;
+    cplx<R>* c = rho + j * N + w;
+    a->x = -a->x; a->y = -a->y;
+    c->x = -c->x; c->y = -c->y;
+  }
+}
+
+__global__ void k_debug_noise(uint64_t seed, uint64_t traj, uint64_t gate_id, int count,
+                              uint32_t* words, double* normals) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) {
+    const Words4 w = noise_words(seed, traj + (uint64_t)i, gate_id);
+    for (int j = 0; j < 4; ++j) words[4 * i + j] = w.w[j];
+    const double2 xi = noise_normals(seed, traj + (uint64_t)i, gate_id);
+    normals[2 * i] = xi.x;
+    normals[2 * i + 1] = xi.y;
+  }
+}
+
+template <typename R>
+cudaError_t apply_kq_dispatch(qs_ctx* h, void* psi, int n, int members, const Targets& tg,
+                              const void* mat, bool per_member) {
+  const uint64_t ng = (uint64_t)members << (n - tg.k);
+  const int g = grid_for(ng);
+  auto* p = static_cast<cplx<R>*>(psi);
+  const R* m = static_cast<const R*>(mat);
+  switch (tg.k) {
+    case 1: k_apply_kq<R, 1><<<g, kBlock, 0, h->stream>>>(p, n, ng, tg, m, per_member); break;
+    case 2: k_apply_kq<R, 2><<<g, kBlock, 0, h->stream>>>(p, n, ng, tg, m, per_member); break;
+    case 3: k_apply_kq<R, 3><<<g, kBlock, 0, h->stream>>>(p, n, ng, tg, m, per_member); break;
+    case 4: k_apply_kq<R, 4><<<g, kBlock, 0, h->stream>>>(p, n, ng, tg, m, per_member); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t apply_diag_dispatch(qs_ctx* h, void* psi, int n, int members, const Targets& tg,
+                                const void* diag, bool per_member, uint32_t mask) {
+  const uint64_t ng = (uint64_t)members << (n - tg.k);
+  const int g = grid_for(ng);
+  auto* p = static_cast<cplx<R>*>(psi);
+  const R* d = static_cast<const R*>(diag);
+  switch (tg.k) {
+    case 1: k_apply_diag<R, 1><<<g, kBlock, 0, h->stream>>>(p, n, ng, tg, d, per_member, mask); break;
+    case 2: k_apply_diag<R, 2><<<g, kBlock, 0, h->stream>>>(p, n, ng, tg, d, per_member, mask); break;
+    case 3: k_apply_diag<R, 3><<<g, kBlock, 0, h->stream>>>(p, n, ng, tg, d, per_member, mask); break;
+    case 4: k_apply_diag<R, 4><<<g, kBlock, 0, h->stream>>>(p, n, ng, tg, d, per_member, mask); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t elem_size(qs_dtype d) { return d == QS_C64 ? 8 : 16; }
+
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+Targets make_targets(int n, const int* targets, int k) {
+  (void)n;
+  Targets tg{};
+  tg.k = k;
+  for (int j = 0; j < k; ++j) { tg.t[j] = targets[j]; tg.sorted[j] = targets[j]; }
+  for (int a = 0; a < k; ++a)
+    for (int b = a + 1; b < k; ++b)
+      if (tg.sorted[b] < tg.sorted[a]) { const int x = tg.sorted[a]; tg.sorted[a] = tg.sorted[b]; tg.sorted[b] = x; }
+  for (int l = 0; l < (1 << k); ++l) {
+    uint64_t o = 0;
+    for (int j = 0; j < k; ++j) if ((l >> j) & 1) o |= 1ull << targets[j];
+    tg.off[l] = o;
+  }
+  return tg;
+}
+
+cudaError_t launch_set_basis(qs_ctx* h, void* psi, int n, int members, uint64_t x, const uint64_t* xs) {
+  cudaError_t e = cudaMemsetAsync(psi, 0, ((size_t)members << n) * h->esize, h->stream);
+  if (e != cudaSuccess) return e;
+  const int g = (members + kBlock - 1) / kBlock;
+  if (h->dtype == QS_C64) k_set_basis<float><<<g, kBlock, 0, h->stream>>>((float2*)psi, n, members, x, xs);
+  else k_set_basis<double><<<g, kBlock, 0, h->stream>>>((double2*)psi, n, members, x, xs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_noise_mats(qs_ctx* h, void* mats, int members, int k, const double* U, int noise,
+                              int diag_only, const NoiseSrc& src, uint64_t gate_id) {
+  DMat m{};
+  const int d = 1 << k;
+  for (int i = 0; i < 2 * d * d; ++i) m.v[i] = U[i];
+  const int g = (members + 127) / 128;
+  if (h->dtype == QS_C64)
+    k_noise_mats<float><<<g, 128, 0, h->stream>>>((float*)mats, members, k, m, noise, diag_only, src, gate_id);
+  else
+    k_noise_mats<double><<<g, 128, 0, h->stream>>>((double*)mats, members, k, m, noise, diag_only, src, gate_id);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_1q(qs_ctx* h, void* psi, int n, int members, int t, const double* U,
+                            const void* mats) {
+  const uint64_t np = (uint64_t)members << (n - 1);
+  const int g = grid_for(np);
+  if (h->dtype == QS_C64) {
+    Mat2<float> mu{};
+    if (U) {
+      mu.m00 = make_float2((float)U[0], (float)U[1]); mu.m01 = make_float2((float)U[2], (float)U[3]);
+      mu.m10 = make_float2((float)U[4], (float)U[5]); mu.m11 = make_float2((float)U[6], (float)U[7]);
+      k_apply_1q<float, false><<<g, kBlock, 0, h->stream>>>((float2*)psi, n, t, np, mu, nullptr);
+    } else {
+      k_apply_1q<float, true><<<g, kBlock, 0, h->stream>>>((float2*)psi, n, t, np, mu, (const float*)mats);
+    }
+  } else {
+    Mat2<double> mu{};
+    if (U) {
+      mu.m00 = make_double2(U[0], U[1]); mu.m01 = make_double2(U[2], U[3]);
+      mu.m10 = make_double2(U[4], U[5]); mu.m11 = make_double2(U[6], U[7]);
+      k_apply_1q<double, false><<<g, kBlock, 0, h->stream>>>((double2*)psi, n, t, np, mu, nullptr);
+    } else {
+      k_apply_1q<double, true><<<g, kBlock, 0, h->stream>>>((double2*)psi, n, t, np, mu, (const double*)mats);
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_kq(qs_ctx* h, void* psi, int n, int members, const Targets& tg,
+                            const void* mat, bool per_member) {
+  if (h->dtype == QS_C64) return apply_kq_dispatch<float>(h, psi, n, members, tg, mat, per_member);
+  return apply_kq_dispatch<double>(h, psi, n, members, tg, mat, per_member);
+}
+
+cudaError_t launch_apply_diag(qs_ctx* h, void* psi, int n, int members, const Targets& tg,
+                              const void* diag, bool per_member, uint32_t mask) {
+  if (h->dtype == QS_C64) return apply_diag_dispatch<float>(h, psi, n, members, tg, diag, per_member, mask);
+  return apply_diag_dispatch<double>(h, psi, n, members, tg, diag, per_member, mask);
+}
+
+cudaError_t launch_phase_flip(qs_ctx* h, void* psi, int n, int members, uint64_t index,
+                              const uint64_t* per) {
+  const int g = (members + kBlock - 1) / kBlock;
+  if (h->dtype == QS_C64) k_phase_flip<float><<<g, kBlock, 0, h->stream>>>((float2*)psi, n, members, index, per);
+  else k_phase_flip<double><<<g, kBlock, 0, h->stream>>>((double2*)psi, n, members, index, per);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dm_flip(qs_ctx* h, void* rho, int n, uint64_t w) {
+  const int g = grid_for(1ull << n);
+  if (h->dtype == QS_C64) k_dm_flip<float><<<g, kBlock, 0, h->stream>>>((float2*)rho, n, w);
+  else k_dm_flip<double><<<g, kBlock, 0, h->stream>>>((double2*)rho, n, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_debug_noise(uint64_t seed, uint64_t traj, uint64_t gate_id, int count,
+                               uint32_t* words, double* normals, cudaStream_t s) {
+  k_debug_noise<<<(count + 127) / 128, 128, 0, s>>>(seed, traj, gate_id, count, words, normals);
+  return cudaGetLastError();
+}
+
+}  // namespace qs

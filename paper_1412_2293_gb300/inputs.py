@@ -141,6 +141,8 @@ class Workload:
 WORKLOADS = {
     "mc_grover_n10_c128": Workload("mc_grover_n10_c128", 10, "grover", "statevec", "c128", 0.01, trajectories=100),
     "mc_qft_n20_c64": Workload("mc_qft_n20_c64", 20, "qft", "statevec", "c64", 0.01, trajectories=1024),
+    # same circuit with 128 trajectories (1 GiB state): the profiling size
+    "mc_qft_n20_c64_t128": Workload("mc_qft_n20_c64_t128", 20, "qft", "statevec", "c64", 0.01, trajectories=128),
     "mc_qft_n20_c64_e1e-3": Workload("mc_qft_n20_c64_e1e-3", 20, "qft", "statevec", "c64", 0.001, trajectories=1024),
     "mc_qft_n20_c128": Workload("mc_qft_n20_c128", 20, "qft", "statevec", "c128", 0.01, trajectories=1024),
     "rank_grover_n16": Workload("rank_grover_n16", 16, "grover", "fixed_rank", "c128", 0.01, rank=8),

@@ -1,0 +1,395 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle, on the GPU.
+
+Tolerances: complex128 results within 1e-12 (amplitudes absolute, fidelities
+relative), complex64 within 1e-5; Philox words bit-exact; the Gaussian draws
+within a few ulp (libm against CUDA's FP64 log/sincos).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import circuits as ocirc
+from oracle import density as odm
+from oracle import fixed_rank as ofr
+from oracle import gates as ogates
+from oracle import philox as ophilox
+from oracle import statevec as osv
+from paper_1412_2293_gb300 import circuits as pcirc
+from paper_1412_2293_gb300 import inputs, qs
+
+pytestmark = pytest.mark.gpu
+
+SEED = inputs.DEFAULT_SEED
+TOL = {qs.QS_C128: 1e-12, qs.QS_C64: 1e-5}
+DTYPES = [qs.QS_C128, qs.QS_C64]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def library():
+    from paper_1412_2293_gb300 import build
+    build.build()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return qs.lib()
+
+
+class Handle:
+    def __init__(self, *a, **k):
+        self.h = qs.qs_create(*a, **k)
+
+    def __enter__(self):
+        return self.h
+
+    def __exit__(self, *exc):
+        qs.qs_destroy(self.h)
+
+
+def rand_unitary(rng, d):
+    z = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+    q, r = np.linalg.qr(z)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+def rand_states(rng, n, batch):
+    v = rng.normal(size=(batch, 1 << n)) + 1j * rng.normal(size=(batch, 1 << n))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+# ----------------------------------------------------------------- noise draw
+
+@pytest.mark.parametrize("seed", [SEED, 0, 2**63 + 12345])
+@pytest.mark.parametrize("gate_id", [0, 7, 2**32 + 5])
+def test_philox_words_bit_exact_and_normals(seed, gate_id):
+    traj0, count = 3, 1024
+    words, normals = qs.qs_debug_noise(seed, traj0, gate_id, count)
+    for i in range(0, count, 37):
+        assert tuple(int(w) for w in words[i]) == ophilox.noise_words(seed, traj0 + i, gate_id)
+    xa, xb = ophilox.normal_pairs_array(seed, np.arange(traj0, traj0 + count), gate_id)
+    np.testing.assert_allclose(normals[:, 0], xa, rtol=4e-15, atol=4e-15)
+    np.testing.assert_allclose(normals[:, 1], xb, rtol=4e-15, atol=4e-15)
+
+
+# ----------------------------------------------------------------- single gates
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("targets", [(0,), (6,), (3,), (1, 5), (6, 0), (2, 4, 0), (0, 1, 2, 3), (6, 3, 1, 5)])
+def test_ideal_gate_matches_oracle(dtype, targets):
+    rng = np.random.default_rng(len(targets) * 10 + targets[0])
+    n, batch = 7, 3
+    psi = rand_states(rng, n, batch)
+    U = rand_unitary(rng, 1 << len(targets))
+    with Handle(n, batch, 0, qs.QS_STATEVEC, dtype) as h:
+        qs.qs_set_state(h, psi.reshape(-1))
+        qs.qs_apply_gate(h, targets, U)
+        got = qs.qs_get_state(h).reshape(batch, -1)
+    for b in range(batch):
+        np.testing.assert_allclose(got[b], osv.apply_gate(psi[b], n, targets, U), atol=TOL[dtype])
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_diagonal_gate_path_matches_oracle(dtype):
+    rng = np.random.default_rng(5)
+    n, batch = 8, 2
+    psi = rand_states(rng, n, batch)
+    U = np.diag(np.exp(1j * rng.uniform(0, 6, size=4)))
+    U[0, 0] = 1.0
+    with Handle(n, batch, 0, qs.QS_STATEVEC, dtype) as h:
+        qs.qs_set_state(h, psi.reshape(-1))
+        qs.qs_apply_gate(h, (5, 2), U)
+        qs.qs_apply_phase_flip(h, 77)
+        got = qs.qs_get_state(h).reshape(batch, -1)
+    for b in range(batch):
+        want = osv.phase_flip(osv.apply_gate(psi[b], n, (5, 2), U), 77)
+        np.testing.assert_allclose(got[b], want, atol=TOL[dtype])
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("case", ["H_rot", "U1_rot", "U1_phase", "CP_phase", "U2_rot", "U2_phase"])
+def test_noisy_gate_matches_oracle(dtype, case):
+    rng = np.random.default_rng(abs(hash(case)) % 1000)
+    n, batch, e, gid, off = 6, 5, 0.07, 1234, 7
+    psi = rand_states(rng, n, batch)
+    if case == "H_rot":
+        targets, U, noise = (4,), ogates.hadamard(), "rotation"
+    elif case == "U1_rot":
+        targets, U, noise = (0,), rand_unitary(rng, 2), "rotation"
+    elif case == "U1_phase":
+        targets, U, noise = (2,), rand_unitary(rng, 2), "phase"
+    elif case == "CP_phase":
+        targets, U, noise = (1, 5), ogates.controlled_phase(0.3), "phase"
+    elif case == "U2_rot":
+        targets, U, noise = (3, 0), rand_unitary(rng, 4), "rotation"
+    else:
+        targets, U, noise = (5, 1), rand_unitary(rng, 4), "phase"
+    qn = qs.QS_NOISE_ROTATION if noise == "rotation" else qs.QS_NOISE_PHASE
+    with Handle(n, batch, 0, qs.QS_STATEVEC, dtype) as h:
+        qs.qs_set_state(h, psi.reshape(-1))
+        qs.qs_set_trajectory_offset(h, off)
+        qs.qs_apply_noisy_gate(h, targets, U, qn, e, SEED, gid)
+        got = qs.qs_get_state(h).reshape(batch, -1)
+    for b in range(batch):
+        xa, xb = ophilox.normal_pair(SEED, off + b, gid)
+        Ub = ogates.noisy_unitary(U, noise, e, xa, xb)
+        np.testing.assert_allclose(got[b], osv.apply_gate(psi[b], n, targets, Ub), atol=TOL[dtype])
+
+
+# ----------------------------------------------------------------- circuits
+
+def oracle_traj(n, ops, x0, e, b):
+    return ocirc.run_trajectory(n, ops, x0, e, SEED, b)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("circ,n", [("qft", 10), ("qft", 12), ("qft", 13), ("qft", 15), ("grover", 10),
+                                    ("grover", 11), ("grover", 13)])
+def test_plan_trajectories_match_oracle(dtype, circ, n):
+    batch, e = 3, 0.05
+    if circ == "qft":
+        ops, x0 = inputs.qft_circuit(n), inputs.draw_basis_input(n, SEED)
+    else:
+        ops, x0 = inputs.grover_circuit(n, 2, inputs.draw_marked(n, SEED)), 0
+    with Handle(n, batch, 0, qs.QS_STATEVEC, dtype) as h:
+        qs.qs_set_basis_state(h, x0)
+        p = qs.qs_plan_create(h, pcirc.to_gates(ops))
+        passes, _ = qs.qs_plan_info(p)
+        qs.qs_plan_run(p, e, SEED, 0, h)
+        qs.qs_plan_destroy(p)
+        got = qs.qs_get_state(h).reshape(batch, -1)
+    if circ == "qft" and n >= 13:
+        assert passes == 2            # one high-window and one low-window pass
+    for b in range(batch):
+        np.testing.assert_allclose(got[b], oracle_traj(n, ops, x0, e, b), atol=TOL[dtype])
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_gate_by_gate_equals_plan(dtype):
+    n, batch, e = 12, 4, 0.02
+    ops, x0 = inputs.qft_circuit(n), 1234
+    with Handle(n, batch, 0, qs.QS_STATEVEC, dtype) as h1, Handle(n, batch, 0, qs.QS_STATEVEC, dtype) as h2:
+        qs.qs_set_basis_state(h1, x0)
+        qs.qs_set_basis_state(h2, x0)
+        pcirc.apply_ops(h1, ops, e, SEED)
+        p = qs.qs_plan_create(h2, pcirc.to_gates(ops))
+        qs.qs_plan_run(p, e, SEED, 0, h2)
+        a = qs.qs_get_state(h1)
+        b = qs.qs_get_state(h2)
+        np.testing.assert_allclose(a, b, atol=TOL[dtype])
+        # a second run (graph replay) from the same start gives the same state
+        qs.qs_set_basis_state(h2, x0)
+        qs.qs_plan_run(p, e, SEED, 0, h2)
+        np.testing.assert_allclose(qs.qs_get_state(h2), b, atol=0)
+        qs.qs_plan_destroy(p)
+
+
+def test_plan_with_unfusable_gates_matches_oracle():
+    rng = np.random.default_rng(9)
+    n, batch, e = 11, 2, 0.03
+    U2 = rand_unitary(rng, 4)
+    gates = [qs.make_gate((q,), ogates.hadamard(), noisy=True) for q in range(n)]
+    gates.append(qs.make_gate((3, 9), U2))                     # dense 2-qubit: single step
+    gates += [qs.make_gate((q,), ogates.hadamard(), noisy=True) for q in (0, 10, 5)]
+    gates.append(qs.make_gate((10, 2), ogates.controlled_phase(0.4), noisy=True, noise=qs.QS_NOISE_PHASE))
+    with Handle(n, batch, 0, qs.QS_STATEVEC, qs.QS_C128) as h:
+        p = qs.qs_plan_create(h, gates)
+        qs.qs_plan_run(p, e, SEED, 100, h)
+        qs.qs_plan_destroy(p)
+        got = qs.qs_get_state(h).reshape(batch, -1)
+    for b in range(batch):
+        psi = osv.basis_state(n, 0)
+        for g, gate in enumerate(gates):
+            d = 1 << gate.k
+            U = np.array(gate.U[:2 * d * d]).view(np.complex128).reshape(d, d)
+            t = tuple(gate.targets[:gate.k])
+            if gate.noisy:
+                xa, xb = ophilox.normal_pair(SEED, b, 100 + g)
+                U = ogates.noisy_unitary(U, "phase" if gate.noise == qs.QS_NOISE_PHASE else "rotation", e, xa, xb)
+            psi = osv.apply_gate(psi, n, t, U)
+        np.testing.assert_allclose(got[b], psi, atol=1e-12)
+
+
+def test_qft_full_size_sampled_trajectories():
+    """The benchmark shape: n = 20, 1024 complex64 trajectories, fused plan."""
+    n, T, e = 20, 1024, 0.01
+    ops, x0 = inputs.qft_circuit(n), inputs.draw_basis_input(n, SEED)
+    with Handle(n, T, 0, qs.QS_STATEVEC, qs.QS_C64) as h:
+        ref = pcirc.ideal_reference(n, ops, x0, qs.QS_C64)
+        try:
+            qs.qs_set_reference_from(h, ref, 0)
+        finally:
+            qs.qs_destroy(ref)
+        qs.qs_set_basis_state(h, x0)
+        p = qs.qs_plan_create(h, pcirc.to_gates(ops))
+        qs.qs_plan_run(p, e, SEED, 0, h)
+        f = qs.qs_fidelity_stored(h)
+        norms = qs.qs_trace(h)
+        qs.qs_plan_destroy(p)
+    np.testing.assert_allclose(norms, 1.0, atol=1e-5)
+    ideal = ocirc.ideal_state(n, ops, x0)
+    for b in (0, 513, T - 1):
+        want = osv.fidelity(ideal, oracle_traj(n, ops, x0, e, b))
+        assert abs(f[b] - want) < 1e-5, (b, f[b], want)
+    # distribution sanity against Eq. 11 (lower estimate) and 1
+    assert np.all(f <= 1 + 1e-5)
+    assert f.mean() > ogates.qft_estimate_eq11(n, e) - 0.01
+
+
+# ----------------------------------------------------------------- density matrix
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("circ", ["qft", "grover"])
+def test_density_circuit_matches_oracle(dtype, circ):
+    n, e = 4, 0.05
+    ops = inputs.qft_circuit(n) if circ == "qft" else inputs.grover_circuit(n, 3, 11)
+    x0 = 9 if circ == "qft" else 0
+    with Handle(n, 1, 0, qs.QS_DENSITY, dtype) as h:
+        qs.qs_set_basis_state(h, x0)
+        pcirc.apply_ops(h, ops, e, SEED)
+        got = qs.qs_get_state(h).reshape(1 << n, 1 << n)
+        ideal = ocirc.ideal_state(n, ops, x0)
+        f = qs.qs_fidelity(h, ideal)[0]
+        tr = qs.qs_trace(h)[0]
+    rho = ocirc.run_density(n, ops, x0, e)
+    np.testing.assert_allclose(got, rho, atol=TOL[dtype])
+    assert abs(f - odm.fidelity(ideal, rho)) <= TOL[dtype] * max(1.0, f)
+    assert abs(tr - 1.0) <= TOL[dtype]
+
+
+def test_density_custom_kraus_matches_oracle():
+    rng = np.random.default_rng(12)
+    n = 3
+    # a random CPTP map from an isometry (4 operators of size 4x4)
+    V = np.linalg.qr(rng.normal(size=(16, 4)) + 1j * rng.normal(size=(16, 4)))[0]
+    ks = [V[4 * i:4 * i + 4, :] for i in range(4)]
+    rho0 = np.zeros((8, 8), complex)
+    rho0[5, 5] = 1
+    rho0 = odm.apply_unitary(rho0, n, (0,), ogates.hadamard())
+    with Handle(n, 1, 0, qs.QS_DENSITY, qs.QS_C128) as h:
+        qs.qs_set_state(h, rho0.reshape(-1))
+        qs.qs_apply_kraus(h, (2, 0), ks)
+        got = qs.qs_get_state(h).reshape(8, 8)
+    np.testing.assert_allclose(got, odm.apply_channel(rho0, n, (2, 0), ks), atol=1e-12)
+
+
+# ----------------------------------------------------------------- fixed rank
+
+@pytest.mark.parametrize("n,e", [(5, 0.05), (6, 0.01), (8, 0.02)])
+def test_rank1_grover_reproduces_eq10(n, e):
+    k = inputs.grover_iterations(n)
+    w = inputs.draw_marked(n, SEED)
+    ops = inputs.grover_circuit(n, k, w)
+    with Handle(n, 1, 1, qs.QS_FIXED_RANK, qs.QS_C128) as h:
+        pcirc.apply_ops(h, ops, e, SEED)
+        p = qs.qs_fidelity(h, None, w)[0]
+    want = ogates.grover_rank1_success(n, k, e)
+    assert abs(p - want) <= 1e-12 * want
+    with Handle(n, 1, 1, qs.QS_FIXED_RANK, qs.QS_C128) as h:
+        qs.qs_set_normalize(h, 1)
+        pcirc.apply_ops(h, ops, e, SEED)
+        p = qs.qs_fidelity(h, None, w)[0]
+    assert abs(p - ogates.grover_ideal_success(n, k)) <= 1e-12
+
+
+@pytest.mark.parametrize("circ,n,r,normalize", [("grover", 5, 2, 0), ("grover", 5, 4, 0), ("grover", 6, 3, 1),
+                                                ("qft", 5, 2, 0), ("qft", 5, 4, 1), ("qft", 4, 16, 0)])
+def test_fixed_rank_matches_oracle(circ, n, r, normalize):
+    e = 0.05
+    if circ == "qft":
+        ops, x0 = inputs.qft_circuit(n), 5
+    else:
+        ops, x0 = inputs.grover_circuit(n, inputs.grover_iterations(n), 6), 0
+    ideal = ocirc.ideal_state(n, ops, x0)
+    with Handle(n, 1, r, qs.QS_FIXED_RANK, qs.QS_C128) as h:
+        qs.qs_set_normalize(h, normalize)
+        qs.qs_set_basis_state(h, x0)
+        pcirc.apply_ops(h, ops, e, SEED)
+        f = qs.qs_fidelity(h, ideal)[0]
+        tr = qs.qs_trace(h)[0]
+        m = qs.qs_get_rank(h)
+        L = qs.qs_get_state(h).reshape(r, 1 << n)[:m].T
+    Lo = ocirc.run_fixed_rank(n, ops, x0, e, r, normalize=bool(normalize))
+    assert m == Lo.shape[1]
+    np.testing.assert_allclose(L @ L.conj().T, Lo @ Lo.conj().T, atol=1e-12)
+    fo = ofr.fidelity(ideal, Lo)
+    assert abs(f - fo) <= 1e-12 * max(fo, 1e-300)
+    assert abs(tr - ofr.trace(Lo)) <= 1e-12
+    if r >= (1 << n):
+        rho = ocirc.run_density(n, ops, x0, e)
+        np.testing.assert_allclose(L @ L.conj().T, rho, atol=1e-12)
+
+
+def test_explicit_truncation_matches_oracle():
+    rng = np.random.default_rng(2)
+    n, r = 6, 6
+    L0 = rng.normal(size=(1 << n, r)) + 1j * rng.normal(size=(1 << n, r))
+    with Handle(n, 1, r, qs.QS_FIXED_RANK, qs.QS_C128) as h:
+        qs.qs_set_state(h, L0.T.reshape(-1))
+        qs.qs_set_rank_columns(h, r)
+        qs.qs_truncate_rank(h, 3, 0)
+        assert qs.qs_get_rank(h) == 3
+        L = qs.qs_get_state(h).reshape(r, 1 << n)[:3].T
+        rest = qs.qs_get_state(h).reshape(r, 1 << n)[3:]
+    Lo, _ = ofr.truncate(L0, 3)
+    np.testing.assert_allclose(L @ L.conj().T, Lo @ Lo.conj().T, atol=1e-11)
+    assert np.all(rest == 0)
+
+
+# ----------------------------------------------------------------- batching, errors
+
+def test_member_noise_equals_separate_runs():
+    n, e_list = 11, [0.01, 0.03, 0.0, 0.05]
+    seeds = [11, 22, 33, 44]
+    trajs = [5, 0, 9, 2]
+    ops = inputs.qft_circuit(n)
+    gates = pcirc.to_gates(ops)
+    with Handle(n, 4, 0, qs.QS_STATEVEC, qs.QS_C128) as h:
+        qs.qs_set_member_noise(h, e_list, seeds, trajs)
+        qs.qs_set_basis_state(h, 3)
+        p = qs.qs_plan_create(h, gates)
+        qs.qs_plan_run(p, 0.5, 999, 0, h)        # call values are overridden per member
+        qs.qs_plan_destroy(p)
+        mixed = qs.qs_get_state(h).reshape(4, -1)
+    for b in range(4):
+        with Handle(n, 1, 0, qs.QS_STATEVEC, qs.QS_C128) as h1:
+            qs.qs_set_trajectory_offset(h1, trajs[b])
+            qs.qs_set_basis_state(h1, 3)
+            p = qs.qs_plan_create(h1, gates)
+            qs.qs_plan_run(p, e_list[b], seeds[b], 0, h1)
+            qs.qs_plan_destroy(p)
+            alone = qs.qs_get_state(h1)
+        np.testing.assert_allclose(mixed[b], alone, atol=1e-13)
+
+
+def test_invalid_arguments_are_rejected():
+    with Handle(5, 2, 0, qs.QS_STATEVEC, qs.QS_C128) as h:
+        for bad in [lambda: qs.qs_apply_gate(h, (5,), np.eye(2)),
+                    lambda: qs.qs_apply_gate(h, (1, 1), np.eye(4)),
+                    lambda: qs.qs_apply_phase_flip(h, 32),
+                    lambda: qs.qs_set_basis_state(h, 1 << 5),
+                    lambda: qs.qs_apply_noisy_gate(h, (0,), np.eye(2), 0, -1.0, 1, 1),
+                    lambda: qs.qs_apply_noisy_gate(h, (0, 1, 2), np.eye(8), 0, 0.1, 1, 1)]:
+            with pytest.raises(qs.QSError) as ei:
+                bad()
+            assert ei.value.status == qs.QS_ERR_INVALID_ARG
+        with pytest.raises(qs.QSError) as ei:
+            qs.qs_apply_kraus(h, (0,), [np.eye(2)])
+        assert ei.value.status == qs.QS_ERR_NOT_SUPPORTED
+    with Handle(3, 1, 0, qs.QS_DENSITY, qs.QS_C128) as h:
+        with pytest.raises(qs.QSError) as ei:
+            qs.qs_apply_kraus(h, (0,), [np.eye(2), np.eye(2)])      # not trace preserving
+        assert ei.value.status == qs.QS_ERR_INVALID_ARG
+    with pytest.raises(qs.QSError):
+        qs.qs_create(0, 1, 0, qs.QS_STATEVEC, qs.QS_C64)
+    with pytest.raises(qs.QSError):
+        qs.qs_create(4, 2, 0, qs.QS_DENSITY, qs.QS_C64)
+
+
+def test_smallest_sizes():
+    # one qubit, one member; ragged sizes below one tile
+    with Handle(1, 1, 0, qs.QS_STATEVEC, qs.QS_C128) as h:
+        qs.qs_apply_gate(h, (0,), ogates.hadamard())
+        np.testing.assert_allclose(qs.qs_get_state(h), [2 ** -0.5, 2 ** -0.5], atol=1e-15)
+        assert abs(qs.qs_fidelity(h, None, 1)[0] - 0.5) < 1e-15
+    with Handle(3, 7, 0, qs.QS_STATEVEC, qs.QS_C64) as h:
+        qs.qs_apply_gate(h, (2,), ogates.hadamard())
+        np.testing.assert_allclose(qs.qs_trace(h), 1.0, atol=1e-6)
