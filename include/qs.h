@@ -249,6 +249,33 @@ qs_status qs_plan_last_times(qs_plan p, double* ms, int* kinds, int cap, int* co
 qs_status qs_debug_noise(uint64_t seed, uint64_t traj, uint64_t gate_id, int count,
                          uint32_t* words, double* normals);
 
+/* Allocation-free fidelity.  The paper has no counterpart: this is a
+ * deployment variant of qs_fidelity for callers that cannot allocate device
+ * memory -- a host application or framework that owns the GPU's memory
+ * through its own pool and forbids other allocators, or a latency-critical
+ * loop that cannot afford cudaMalloc's device-wide synchronisation.
+ *   states  device pointer, `members` consecutive state vectors of 2^n
+ *           complex elements of `dtype` (the STATEVEC layout), caller-owned.
+ *   ref     device pointer, 2^n complex elements of `dtype`, caller-owned.
+ *   out     host pointer, `members` doubles: |<ref|states_b>|^2, FP64
+ *           accumulation across blocks as in qs_fidelity.
+ *   cuda_stream  the stream the work is issued on (NULL = legacy stream);
+ *           the call synchronises it before returning.
+ * The call allocates nothing: its scratch is a fixed array of
+ * 2 * QS_NOALLOC_MAX_PARTIALS + QS_NOALLOC_MAX_MEMBERS doubles (1.5 MiB) that
+ * every GPU loading this library holds until the process exits.  The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress
+ * with the device current); make that first call before any stream capture.
+ * All calls on a device share the array: calls whose work overlaps on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller.  Errors: INVALID_ARG for NULL pointers, n outside 1..40, members < 1
+ * or members > QS_NOALLOC_MAX_MEMBERS (the scratch limit); CUDA on a failed
+ * launch or copy. */
+#define QS_NOALLOC_MAX_MEMBERS 65535
+#define QS_NOALLOC_MAX_PARTIALS 65536
+qs_status qs_fidelity_noalloc(const void* states, const void* ref, int n, int members, qs_dtype dtype,
+                              void* cuda_stream, double* out);
+
 /* Library version string. */
 const char* qs_version(void);
 

@@ -76,6 +76,7 @@ _SIGS = {
     "qs_plan_destroy": ([_P], ct.c_int),
     "qs_plan_set_timing": ([_P, ct.c_int], ct.c_int),
     "qs_plan_last_times": ([_P, _D, _I, ct.c_int, _I], ct.c_int),
+    "qs_fidelity_noalloc": ([_P, _P, ct.c_int, ct.c_int, ct.c_int, _P, _D], ct.c_int),
     "qs_debug_noise": ([ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_int, ct.POINTER(ct.c_uint32), _D], ct.c_int),
 }
 
@@ -329,6 +330,24 @@ def qs_plan_last_times(p, cap=4096, h=None):
 
 def qs_plan_destroy(p):
     _check(lib().qs_plan_destroy(p))
+
+
+QS_NOALLOC_MAX_MEMBERS = 65535
+
+
+def qs_fidelity_noalloc(states_ptr, ref_ptr, n, members, dtype, stream=None):
+    """|<ref|states_b>|^2 for caller-held device buffers, with no device allocation.
+
+    For callers that cannot allocate device memory (their host application
+    owns the GPU's memory, or cudaMalloc's synchronisation is unaffordable):
+    `states_ptr` / `ref_ptr` are device addresses (e.g. a tensor's
+    ``data_ptr()``) in the STATEVEC layout of `dtype`.  Calls on one device
+    share a fixed scratch array, so calls that overlap on the GPU race.
+    """
+    out = np.zeros(int(members), dtype=np.float64)
+    _check(lib().qs_fidelity_noalloc(ct.c_void_p(int(states_ptr)), ct.c_void_p(int(ref_ptr)), int(n),
+                                     int(members), int(dtype), _stream_ptr(stream), _dptr(out)))
+    return out
 
 
 def qs_debug_noise(seed, traj, gate_id, count):
