@@ -220,6 +220,14 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
 /* Run the plan once on the handle's stream with noise level e and key seed
  * (per-member values from qs_set_member_noise take precedence). */
 qs_status qs_plan_run(qs_plan p, double e, uint64_t seed, uint64_t gate_id0);
+/* Run the plan and return the fidelity of every member with the stored
+ * reference (qs_set_reference / qs_set_reference_from) in out[batch]: when
+ * the plan ends with a fused pass, that pass also reduces <phi|psi_b> (FP64
+ * across blocks) instead of a separate read of the state.  A start state set
+ * by qs_set_basis_state(s) is created by the first fused pass instead of being
+ * written to memory first.  STATEVEC only.  Synchronises. */
+qs_status qs_plan_run_fidelity(qs_plan p, double e, uint64_t seed, uint64_t gate_id0, double* out);
+
 /* Number of passes over the state one run makes, and kernels it launches. */
 qs_status qs_plan_info(qs_plan p, int* passes, int* launches);
 qs_status qs_plan_destroy(qs_plan p);

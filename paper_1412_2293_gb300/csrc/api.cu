@@ -17,13 +17,12 @@ using cd = std::complex<double>;
 
 namespace {
 
-// layout of the small FP64 scratch buffer
-constexpr size_t kSmallG = 0;                          // Gram matrix, 2*32*32
-constexpr size_t kSmallW = 2048;                       // eigenvectors, 2*32*16
-constexpr size_t kSmallLam = 3072;                     // eigenvalues, 32
-constexpr size_t kSmallScale = 3104;                   // 1
-constexpr size_t kSmallE = 3200;                       // Kraus operators, <= 2*8*16
-constexpr size_t kSmallOut = 4096;                     // results, batch doubles
+using qs::kSmallG;
+using qs::kSmallW;
+using qs::kSmallLam;
+using qs::kSmallScale;
+using qs::kSmallE;
+constexpr size_t kSmallOut = qs::kSmallOutIndex;
 constexpr int kMaxKraus = 8;
 
 qs_status fail(qs_handle h, qs_status code, const std::string& msg) {
@@ -236,19 +235,30 @@ qs_status rank_apply_kraus(qs_handle h, const int* targets, int k, const std::ve
   return rank_truncate_from_work(h, M, h->rank, h->normalize);
 }
 
-qs_status read_out(qs_handle h, double* out, int count) {
+qs_status read_out(qs_handle h, double* out, int count) { return qs::read_results(h, out, count); }
+
+}  // namespace
+
+namespace qs {
+qs_status read_results(qs_ctx* h, double* out, int count) {
   QS_CUDA(h, cudaMemcpyAsync(out, h->small + kSmallOut, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   QS_CUDA(h, cudaStreamSynchronize(h->stream));
-  int status[2] = {0, 0};
+  int status[4] = {0, 0, 0, 0};
   QS_CUDA(h, cudaMemcpy(status, h->dstatus, sizeof(status), cudaMemcpyDeviceToHost));
+  if (status[2] != 0) return fail(h, QS_ERR_TIMEOUT, "a fused pass timed out waiting for a tile copy");
   if (h->mode == QS_FIXED_RANK && status[1] != 0)
     return fail(h, QS_ERR_CUDA, status[1] == 1 ? "eigensolver did not converge" : "tie-cluster basis incomplete");
   return QS_OK;
 }
 
-}  // namespace
+qs_status materialize_basis(qs_ctx* h) {
+  if (!h->pending) return QS_OK;
+  const uint64_t* xs = h->pending == 2 ? h->m_basis : nullptr;
+  QS_CUDA(h, launch_set_basis(h, h->state, h->n, h->batch, h->pending_x, xs));
+  h->pending = 0;
+  return QS_OK;
+}
 
-namespace qs {
 NoiseSrc noise_src(qs_ctx* h, double e, uint64_t seed) {
   NoiseSrc s{};
   s.e0 = e;
@@ -318,7 +328,9 @@ qs_status qs_create(int n, int batch, int rank, qs_mode mode, qs_dtype dtype, vo
   if (cudaMalloc((void**)&h->dstatus, 4 * sizeof(int)) != cudaSuccess) { cudaGetLastError(); return bail(QS_ERR_OUT_OF_MEMORY); }
   if (cudaMemsetAsync(h->dstatus, 0, 4 * sizeof(int), h->stream) != cudaSuccess) return bail(QS_ERR_CUDA);
   h->cols = 1;
-  cudaError_t e = qs::launch_set_basis(h, h->state, n, (int)(mode == QS_STATEVEC ? batch : 1), 0, nullptr);
+  cudaError_t e = cudaSuccess;
+  if (mode == QS_STATEVEC) { h->pending = 1; h->pending_x = 0; }
+  else e = qs::launch_set_basis(h, h->state, n, 1, 0, nullptr);
   if (mode == QS_FIXED_RANK && e == cudaSuccess)
     e = cudaMemsetAsync(h->state, 0, h->state_elems * h->esize, h->stream),
     e = e == cudaSuccess ? qs::launch_set_basis(h, h->state, n, 1, 0, nullptr) : e;
@@ -332,7 +344,7 @@ qs_status qs_destroy(qs_handle h) {
   if (!h) return QS_ERR_INVALID_ARG;
   cudaStreamSynchronize(h->stream);
   void* ptrs[] = {h->state, h->work, h->partials, h->mats, h->small, h->dstatus, h->m_e,
-                  h->m_seed, h->m_traj, h->m_marked, h->ref};
+                  h->m_seed, h->m_traj, h->m_marked, h->ref, h->m_basis};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (h->hpinned) cudaFreeHost(h->hpinned);
   delete h;
@@ -362,7 +374,8 @@ qs_status qs_set_basis_state(qs_handle h, uint64_t x) {
   if (!h) return QS_ERR_INVALID_ARG;
   if (x >= (1ull << h->n)) return fail(h, QS_ERR_INVALID_ARG, "basis index out of range");
   if (h->mode == QS_STATEVEC) {
-    QS_CUDA(h, qs::launch_set_basis(h, h->state, h->n, h->batch, x, nullptr));
+    h->pending = 1;                       // written by its first consumer
+    h->pending_x = x;
   } else if (h->mode == QS_DENSITY) {
     const uint64_t N = 1ull << h->n;
     QS_CUDA(h, qs::launch_set_basis(h, h->state, 2 * h->n, 1, x * N + x, nullptr));
@@ -379,18 +392,17 @@ qs_status qs_set_basis_states(qs_handle h, const uint64_t* xs) {
   if (h->mode != QS_STATEVEC) return fail(h, QS_ERR_NOT_SUPPORTED, "per-member basis states need STATEVEC");
   for (int b = 0; b < h->batch; ++b)
     if (xs[b] >= (1ull << h->n)) return fail(h, QS_ERR_INVALID_ARG, "basis index out of range");
-  // stage through the member-index buffer
-  if (!h->m_marked) QS_CUDA(h, cudaMalloc((void**)&h->m_marked, h->batch * sizeof(uint64_t)));
-  uint64_t* tmp = nullptr;
-  QS_CUDA(h, cudaMallocAsync((void**)&tmp, h->batch * sizeof(uint64_t), h->stream));
-  QS_CUDA(h, cudaMemcpyAsync(tmp, xs, h->batch * sizeof(uint64_t), cudaMemcpyHostToDevice, h->stream));
-  QS_CUDA(h, qs::launch_set_basis(h, h->state, h->n, h->batch, 0, tmp));
-  QS_CUDA(h, cudaFreeAsync(tmp, h->stream));
+  if (!h->m_basis) QS_CUDA(h, cudaMalloc((void**)&h->m_basis, h->batch * sizeof(uint64_t)));
+  // an earlier run may still read m_basis
+  QS_CUDA(h, cudaStreamSynchronize(h->stream));
+  QS_CUDA(h, cudaMemcpy(h->m_basis, xs, h->batch * sizeof(uint64_t), cudaMemcpyHostToDevice));
+  h->pending = 2;                         // written by its first consumer
   return QS_OK;
 }
 
 qs_status qs_apply_gate(qs_handle h, const int* targets, int k, const double* U) {
   if (!h) return QS_ERR_INVALID_ARG;
+  { const qs_status st = qs::materialize_basis(h); if (st != QS_OK) return st; }
   if (k < 1 || k > qs::kMaxK) return fail(h, QS_ERR_INVALID_ARG, "k must be 1..4");
   if (!U) return fail(h, QS_ERR_INVALID_ARG, "U is NULL");
   std::string why;
@@ -404,6 +416,7 @@ qs_status qs_apply_gate(qs_handle h, const int* targets, int k, const double* U)
 
 qs_status qs_apply_phase_flip(qs_handle h, uint64_t index) {
   if (!h) return QS_ERR_INVALID_ARG;
+  { const qs_status st = qs::materialize_basis(h); if (st != QS_OK) return st; }
   if (index >= (1ull << h->n)) return fail(h, QS_ERR_INVALID_ARG, "index out of range");
   if (h->mode == QS_STATEVEC) { QS_CUDA(h, qs::launch_phase_flip(h, h->state, h->n, h->batch, index, nullptr)); }
   else if (h->mode == QS_FIXED_RANK) { QS_CUDA(h, qs::launch_phase_flip(h, h->state, h->n, h->cols, index, nullptr)); }
@@ -414,6 +427,7 @@ qs_status qs_apply_phase_flip(qs_handle h, uint64_t index) {
 qs_status qs_apply_noisy_gate(qs_handle h, const int* targets, int k, const double* U, qs_noise noise,
                               double e, uint64_t seed, uint64_t gate_id) {
   if (!h) return QS_ERR_INVALID_ARG;
+  { const qs_status st = qs::materialize_basis(h); if (st != QS_OK) return st; }
   if (k < 1 || k > 2) return fail(h, QS_ERR_INVALID_ARG, "noisy gates are defined for k = 1, 2");
   if (!U) return fail(h, QS_ERR_INVALID_ARG, "U is NULL");
   if (!(e >= 0.0) || !std::isfinite(e)) return fail(h, QS_ERR_INVALID_ARG, "e must be finite and >= 0");
@@ -507,6 +521,7 @@ static qs_status fidelity_dev(qs_handle h, const void* phi_dev, double* out) {
 
 qs_status qs_fidelity(qs_handle h, const double* ref, uint64_t ref_basis, double* out) {
   if (!h || !out) return QS_ERR_INVALID_ARG;
+  { const qs_status st = qs::materialize_basis(h); if (st != QS_OK) return st; }
   const uint64_t N = 1ull << h->n;
   double* o = h->small + kSmallOut;
   if (!ref) {
@@ -554,6 +569,7 @@ qs_status qs_set_reference(qs_handle h, const double* ref) {
 
 qs_status qs_set_reference_from(qs_handle h, qs_handle src, int b) {
   if (!h || !src) return QS_ERR_INVALID_ARG;
+  { const qs_status st = qs::materialize_basis(src); if (st != QS_OK) return fail(h, st, src->err); }
   if (src->mode != QS_STATEVEC || src->n != h->n || src->dtype != h->dtype || b < 0 || b >= src->batch)
     return fail(h, QS_ERR_INVALID_ARG, "reference must be a member of a STATEVEC handle with the same n and dtype");
   if (!h->ref) QS_CUDA(h, cudaMalloc(&h->ref, (1ull << h->n) * h->esize));
@@ -566,12 +582,14 @@ qs_status qs_set_reference_from(qs_handle h, qs_handle src, int b) {
 
 qs_status qs_fidelity_stored(qs_handle h, double* out) {
   if (!h || !out) return QS_ERR_INVALID_ARG;
+  { const qs_status st = qs::materialize_basis(h); if (st != QS_OK) return st; }
   if (!h->has_ref) return fail(h, QS_ERR_INVALID_ARG, "no stored reference");
   return fidelity_dev(h, h->ref, out);
 }
 
 qs_status qs_trace(qs_handle h, double* out) {
   if (!h || !out) return QS_ERR_INVALID_ARG;
+  { const qs_status st = qs::materialize_basis(h); if (st != QS_OK) return st; }
   double* o = h->small + kSmallOut;
   if (h->mode == QS_STATEVEC) {
     QS_CUDA(h, qs::launch_norm(h, h->state, h->n, h->batch, false, o));
@@ -593,6 +611,7 @@ qs_status qs_state_size(qs_handle h, size_t* out) {
 
 qs_status qs_get_state(qs_handle h, double* host, size_t count) {
   if (!h || !host) return QS_ERR_INVALID_ARG;
+  { const qs_status st = qs::materialize_basis(h); if (st != QS_OK) return st; }
   if (count != h->state_elems) return fail(h, QS_ERR_INVALID_ARG, "count must equal qs_state_size");
   QS_CUDA(h, cudaStreamSynchronize(h->stream));
   if (h->dtype == QS_C128) {
@@ -609,6 +628,7 @@ qs_status qs_set_state(qs_handle h, const double* host, size_t count) {
   if (!h || !host) return QS_ERR_INVALID_ARG;
   if (count != h->state_elems) return fail(h, QS_ERR_INVALID_ARG, "count must equal qs_state_size");
   QS_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->pending = 0;
   if (h->dtype == QS_C128) {
     QS_CUDA(h, cudaMemcpy(h->state, host, count * 16, cudaMemcpyHostToDevice));
   } else {

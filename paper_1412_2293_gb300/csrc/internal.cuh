@@ -108,6 +108,13 @@ struct qs_ctx {
   void* ref = nullptr;
   bool has_ref = false;
 
+  // STATEVEC start state not yet written: 1 = every member |pending_x>,
+  // 2 = member b |m_basis[b]>.  Written by the first consumer (a fused first
+  // pass creates it in registers instead of reading memory).
+  int pending = 0;
+  uint64_t pending_x = 0;
+  uint64_t* m_basis = nullptr;
+
   std::string err;
 };
 
@@ -156,6 +163,20 @@ cudaError_t launch_project(qs_ctx* h, const void* Lp, void* L, int n, int M, con
 // debug noise
 cudaError_t launch_debug_noise(uint64_t seed, uint64_t traj, uint64_t gate_id, int count,
                                uint32_t* words_dev, double* normals_dev, cudaStream_t s);
+
+// layout of the small FP64 scratch block of a handle (doubles)
+constexpr size_t kSmallG = 0;          // Gram matrix, 2 * 32 * 32
+constexpr size_t kSmallW = 2048;       // eigenvectors, 2 * 32 * 16
+constexpr size_t kSmallLam = 3072;     // eigenvalues, 32
+constexpr size_t kSmallScale = 3104;   // 1
+constexpr size_t kSmallE = 3200;       // Kraus operators, <= 2 * 8 * 16
+constexpr size_t kSmallOutIndex = 4096;  // results, batch doubles
+
+// Write a pending basis start state into memory (no-op when none is pending).
+qs_status materialize_basis(qs_ctx* h);
+// Copy `count` results from the small block to the host and check the
+// device status words (eigensolver, timed-out waits).  Synchronises.
+qs_status read_results(qs_ctx* h, double* out, int count);
 
 // helpers
 int num_sms();

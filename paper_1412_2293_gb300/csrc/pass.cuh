@@ -1,0 +1,588 @@
+// Fused window passes (device side).  See plan.cu for the planner.
+//
+// A pass applies a run of gates whose dense targets lie in a window of 10
+// qubits to every tile of the state in one HBM read and one HBM write (the
+// amplitude update of Sec. 2, with the memory dependence the paper describes
+// kept inside a tile).  Each thread holds 32 amplitudes that differ in 5
+// "register" bits of the window: a one-qubit gate on a register bit is a
+// butterfly over registers; an exchange through shared memory swaps the
+// register bits (stage A: window bits 5..9, stage B: bits 0..4).
+//
+// Tiles stream through shared memory: while a block computes tile i, the copy
+// engine fills the other buffer with tile i+1 (a 1D bulk copy per warp for the
+// low window, a 2D tensor-map copy per block for the high window), completion
+// tracked by mbarriers.  Every wait is bounded: on timeout the kernel records
+// an error in a device status word, waits (bounded) for copies it still has
+// in flight, and returns.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.cuh"
+
+namespace qs {
+namespace fused {
+
+constexpr int kWin = 10;
+constexpr int kRegBits = 5;
+constexpr int kAmps = 32;
+constexpr int kMaxOther = 48;
+constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr int kStatusTimeout = 0x51;       // value written to the status word on a timed-out wait
+constexpr int kMaxPassOps = 256;           // ops of one pass, held in the kernel parameters
+
+enum : uint8_t { OP_DENSE = 0, OP_DWIN = 1, OP_FLIP = 2, OP_FLIPM = 3, OP_EXCH = 4 };
+
+struct FOp {
+  uint8_t type;
+  uint8_t j;          // local window bit (DENSE, DWIN)
+  uint8_t real;       // DENSE: matrix is real
+  uint8_t pad;
+  uint32_t off;       // parameter offset (R units) in the member block
+  uint64_t index;     // FLIP: member-local amplitude index
+};
+
+struct OutTerm {
+  int32_t a;          // attach local bit, or -1
+  uint32_t off;       // parameter offset of the factor
+  uint64_t cmask;     // member-local out-of-window bits that must be set
+};
+
+struct PassArgs {
+  int n;
+  int start_stage;            // 0 = A, 1 = B
+  int win[kWin];
+  int num_ops;
+  FOp ops[kMaxPassOps];       // the program (constant bank: uniform, cached)
+  int out_start[12];          // out terms grouped by attach a (0..9) and 10 = none
+  const OutTerm* outs;
+  int param_stride;           // R units per member
+  const void* params;
+  const uint64_t* marked;     // per-member flip index
+  uint64_t tiles;
+  int tile_shift;             // log2(tiles per member)
+  int* status;                // device status word
+  // first pass of a run started from basis states: synthesise, do not load
+  int synth;
+  const uint64_t* basis;      // per-member basis index, or null: basis0
+  const uint64_t* basis0;     // device word
+  // last pass of a run with a fused fidelity: partials of <ref|psi>
+  int fid;
+  const void* ref;            // 2^n reference amplitudes
+  double* fid_partials;       // [member][tile in member] complex
+};
+
+// ---------------------------------------------------------------- async copies
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done) : "r"(a), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// 1D bulk copy global -> shared, completion on `bar` (bytes % 16 == 0, both 16-B aligned)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+// 2D tensor-map copy of one box to shared memory
+__device__ __forceinline__ void tma_g2s_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void report_timeout(int* status) {
+  if (status) atomicExch(status, kStatusTimeout);
+}
+
+// ---------------------------------------------------------------- arithmetic
+template <typename R>
+__device__ __forceinline__ cplx<R> ld_c(const R* p) { return mk<R>(p[0], p[1]); }
+
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d)
+      : "l"(*reinterpret_cast<uint64_t*>(&a)), "l"(*reinterpret_cast<uint64_t*>(&b)));
+  return *reinterpret_cast<float2*>(&d);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d)
+      : "l"(*reinterpret_cast<uint64_t*>(&a)), "l"(*reinterpret_cast<uint64_t*>(&b)),
+        "l"(*reinterpret_cast<uint64_t*>(&c)));
+  return *reinterpret_cast<float2*>(&d);
+}
+
+// Real 2x2 on a complex pair: both components scaled by the same real entry,
+// so complex64 uses the packed two-lane FP32 FMA (one instruction per output
+// amplitude and matrix entry).
+template <typename R>
+__device__ __forceinline__ void butterfly_real(cplx<R>& x0, cplx<R>& x1, R u00, R u01, R u10, R u11) {
+  if constexpr (sizeof(R) == 4) {
+    const float2 a = x0, b = x1;
+    x0 = fma2(make_float2(u01, u01), b, mul2(make_float2(u00, u00), a));
+    x1 = fma2(make_float2(u11, u11), b, mul2(make_float2(u10, u10), a));
+  } else {
+    const cplx<R> a = x0, b = x1;
+    x0 = mk<R>(u00 * a.x + u01 * b.x, u00 * a.y + u01 * b.y);
+    x1 = mk<R>(u10 * a.x + u11 * b.x, u10 * a.y + u11 * b.y);
+  }
+}
+
+template <typename R, int RJ>
+__device__ __forceinline__ void dense_reg(cplx<R> (&a)[kAmps], const R* m, bool real) {
+  if (real) {
+    const R u00 = m[0], u01 = m[2], u10 = m[4], u11 = m[6];
+#pragma unroll
+    for (int r = 0; r < kAmps; ++r) {
+      if (r & (1 << RJ)) continue;
+      butterfly_real<R>(a[r], a[r | (1 << RJ)], u00, u01, u10, u11);
+    }
+  } else {
+    const cplx<R> u00 = ld_c(m), u01 = ld_c(m + 2), u10 = ld_c(m + 4), u11 = ld_c(m + 6);
+#pragma unroll
+    for (int r = 0; r < kAmps; ++r) {
+      if (r & (1 << RJ)) continue;
+      const cplx<R> x0 = a[r], x1 = a[r | (1 << RJ)];
+      a[r] = cfma(u01, x1, cmul(u00, x0));
+      a[r | (1 << RJ)] = cfma(u11, x1, cmul(u10, x0));
+    }
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void dense_dispatch(cplx<R> (&a)[kAmps], int rj, const R* m, bool real) {
+  switch (rj) {
+    case 0: dense_reg<R, 0>(a, m, real); break;
+    case 1: dense_reg<R, 1>(a, m, real); break;
+    case 2: dense_reg<R, 2>(a, m, real); break;
+    case 3: dense_reg<R, 3>(a, m, real); break;
+    default: dense_reg<R, 4>(a, m, real); break;
+  }
+}
+
+// Multiply registers with bit RJ set by T[idx]: stage A idx = tbits | (low
+// register bits << 5), stage B idx = the register bits below RJ.
+template <typename R, int RJ, bool STAGE_A>
+__device__ __forceinline__ void dwin_reg(cplx<R> (&a)[kAmps], const R* T, int tbits) {
+  constexpr int Q = 1 << RJ;
+  cplx<R> f[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int idx = STAGE_A ? (tbits | (q << 5)) : q;
+    f[q] = ld_c(T + 2 * idx);
+  }
+#pragma unroll
+  for (int r = 0; r < kAmps; ++r)
+    if (r & (1 << RJ)) a[r] = cmul(f[r & (Q - 1)], a[r]);
+}
+
+template <typename R>
+__device__ __forceinline__ void dwin_dispatch(cplx<R> (&a)[kAmps], int rj, bool stage_a, const R* T, int tbits) {
+  if (stage_a) {
+    switch (rj) {
+      case 0: dwin_reg<R, 0, true>(a, T, tbits); break;
+      case 1: dwin_reg<R, 1, true>(a, T, tbits); break;
+      case 2: dwin_reg<R, 2, true>(a, T, tbits); break;
+      case 3: dwin_reg<R, 3, true>(a, T, tbits); break;
+      default: dwin_reg<R, 4, true>(a, T, tbits); break;
+    }
+  } else {
+    switch (rj) {
+      case 0: dwin_reg<R, 0, false>(a, T, tbits); break;
+      case 1: dwin_reg<R, 1, false>(a, T, tbits); break;
+      case 2: dwin_reg<R, 2, false>(a, T, tbits); break;
+      case 3: dwin_reg<R, 3, false>(a, T, tbits); break;
+      default: dwin_reg<R, 4, false>(a, T, tbits); break;
+    }
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void flip_reg(cplx<R> (&a)[kAmps], bool match, int rw) {
+#pragma unroll
+  for (int r = 0; r < kAmps; ++r)
+    if (match && r == rw) { a[r].x = -a[r].x; a[r].y = -a[r].y; }
+}
+
+// a[rho] *= c * prod_{r in rho} alpha[r]: a 16-entry table over register bits
+// 0..3 by doubling, applied to the lower half, then scaled by alpha[4] for
+// the upper half (the table never holds more than 16 factors).
+template <typename R>
+__device__ __forceinline__ void apply_reg_product(cplx<R> (&a)[kAmps], cplx<R> c, const cplx<R> (&al)[kRegBits]) {
+  cplx<R> t[16];
+  t[0] = c;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < (1 << r); ++q) t[q | (1 << r)] = cmul(t[q], al[r]);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) a[r] = cmul(t[r], a[r]);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) a[r + 16] = cmul(cmul(t[r], al[4]), a[r + 16]);
+}
+
+// product of the out terms of attach a whose out-of-window bits are set in `fixed`
+template <typename R>
+__device__ __forceinline__ cplx<R> out_alpha(const PassArgs& A, const R* P, int a, uint64_t fixed) {
+  cplx<R> acc = mk<R>(R(1), R(0));
+  for (int i = A.out_start[a]; i < A.out_start[a + 1]; ++i) {
+    const OutTerm t = A.outs[i];
+    if ((fixed & t.cmask) == t.cmask) acc = cmul(acc, ld_c(P + t.off));
+  }
+  return acc;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- LOW pass
+// Window = qubits 0..9.  Each warp streams a contiguous range of tiles of 1024
+// consecutive amplitudes (consecutive tiles mostly share a member, so its
+// parameters stay in L1): double-buffered bulk copies into shared memory, a
+// padded exchange buffer, coalesced stores from the stage-A layout.
+template <int WARPS> struct LowShape {
+  static constexpr int XPAD = 1056;                    // 1024 + 32 padding
+  static constexpr int PER_WARP = 2 * 1024 + XPAD + 12;
+  static constexpr int THREADS = WARPS * 32;
+};
+
+template <typename R, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict__ psi, const __grid_constant__ PassArgs A) {
+  using C = cplx<R>;
+  using S = LowShape<WARPS>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[WARPS][2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  C* wbase = reinterpret_cast<C*>(smem_raw) + (size_t)warp * S::PER_WARP;
+  C* xbuf = wbase + 2048;
+  C* alpha_sm = wbase + 2048 + S::XPAD;
+  const uint64_t nmask = (1ull << A.n) - 1;
+  const R* params = static_cast<const R*>(A.params);
+  const uint32_t tile_bytes = 1024u * (uint32_t)sizeof(C);
+  // contiguous tile range of this warp
+  const uint64_t nwarps = (uint64_t)gridDim.x * WARPS;
+  const uint64_t gw = (uint64_t)blockIdx.x * WARPS + warp;
+  const uint64_t per = (A.tiles + nwarps - 1) / nwarps;
+  const uint64_t first = gw * per;
+  const uint64_t last = first + per < A.tiles ? first + per : A.tiles;
+
+  if (lane == 0) {
+    mbar_init(&bars[warp][0], 1);
+    mbar_init(&bars[warp][1], 1);
+    mbar_fence_init();
+  }
+  __syncwarp();
+  if (!A.synth && lane == 0 && first < last) {
+    mbar_expect_tx(&bars[warp][0], tile_bytes);
+    bulk_g2s(wbase, psi + (first << kWin), tile_bytes, &bars[warp][0]);
+  }
+  int in_flight = (!A.synth && first < last) ? 1 : 0;
+  uint32_t it = 0;
+  for (uint64_t t = first; t < last; ++t, ++it) {
+    const int cur = it & 1;
+    C* cbuf = wbase + cur * 1024;
+    if (!A.synth && lane == 0 && t + 1 < last) {
+      fence_proxy_async();
+      mbar_expect_tx(&bars[warp][cur ^ 1], tile_bytes);
+      bulk_g2s(wbase + (cur ^ 1) * 1024, psi + ((t + 1) << kWin), tile_bytes, &bars[warp][cur ^ 1]);
+      ++in_flight;
+    }
+    const uint64_t base = t << kWin;
+    const uint64_t member = base >> A.n;
+    const uint64_t mloc = base & nmask;
+    const R* P = params + member * (uint64_t)A.param_stride;
+    C a[kAmps];
+    if (A.synth) {
+      const uint64_t x = A.basis ? A.basis[member] : A.basis0[0];
+#pragma unroll
+      for (int r = 0; r < kAmps; ++r)
+        a[r] = mk<R>((mloc | (uint64_t)(lane + 32 * r)) == x ? R(1) : R(0), R(0));
+    } else {
+      if (!mbar_wait(&bars[warp][cur], (it >> 1) & 1)) {
+        report_timeout(A.status);
+        if (lane == 0 && in_flight > 1) mbar_wait(&bars[warp][cur ^ 1], ((it + 1) >> 1) & 1);
+        return;
+      }
+      if (lane == 0) --in_flight;
+#pragma unroll
+      for (int r = 0; r < kAmps; ++r) a[r] = cbuf[lane + 32 * r];
+    }
+    int stage = 0;
+    for (int i = 0; i < A.num_ops; ++i) {
+      const FOp op = A.ops[i];
+      if (op.type == OP_DENSE) {
+        dense_dispatch<R>(a, stage == 0 ? op.j - 5 : op.j, P + op.off, op.real);
+      } else if (op.type == OP_DWIN) {
+        dwin_dispatch<R>(a, stage == 0 ? op.j - 5 : op.j, stage == 0, P + op.off, lane);
+      } else if (op.type == OP_FLIP || op.type == OP_FLIPM) {
+        const uint64_t w = op.type == OP_FLIP ? op.index : A.marked[member];
+        const uint64_t fixed = mloc | (stage == 0 ? (uint64_t)lane : ((uint64_t)lane << 5));
+        const uint64_t regmask = stage == 0 ? (31ull << 5) : 31ull;
+        flip_reg<R>(a, (w & ~regmask) == fixed, stage == 0 ? (int)((w >> 5) & 31) : (int)(w & 31));
+      } else {
+        if (stage == 0) {
+#pragma unroll
+          for (int r = 0; r < kAmps; ++r) xbuf[lane + 33 * r] = a[r];
+          __syncwarp();
+#pragma unroll
+          for (int r = 0; r < kAmps; ++r) a[r] = xbuf[r + 33 * lane];
+        } else {
+#pragma unroll
+          for (int r = 0; r < kAmps; ++r) xbuf[r + 33 * lane] = a[r];
+          __syncwarp();
+#pragma unroll
+          for (int r = 0; r < kAmps; ++r) a[r] = xbuf[lane + 33 * r];
+        }
+        __syncwarp();
+        stage ^= 1;
+      }
+    }
+    if (A.out_start[11] > 0) {
+      if (lane < 11) alpha_sm[lane] = out_alpha<R>(A, P, lane, mloc);
+      __syncwarp();
+      C al[kRegBits];
+      C c = alpha_sm[10];
+#pragma unroll
+      for (int r = 0; r < kRegBits; ++r) {
+        al[r] = alpha_sm[stage == 0 ? r + 5 : r];
+        if ((lane >> r) & 1) c = cmul(c, alpha_sm[stage == 0 ? r : r + 5]);
+      }
+      apply_reg_product<R>(a, c, al);
+      __syncwarp();
+    }
+    if (stage == 1) {
+#pragma unroll
+      for (int r = 0; r < kAmps; ++r) xbuf[r + 33 * lane] = a[r];
+      __syncwarp();
+#pragma unroll
+      for (int r = 0; r < kAmps; ++r) a[r] = xbuf[lane + 33 * r];
+      __syncwarp();
+    }
+    if (A.fid) {
+      const C* ref = static_cast<const C*>(A.ref) + mloc;
+      R re = 0, im = 0;
+#pragma unroll
+      for (int r = 0; r < kAmps; ++r) {
+        const C f = ref[lane + 32 * r];
+        re += f.x * a[r].x + f.y * a[r].y;
+        im += f.x * a[r].y - f.y * a[r].x;
+      }
+      const double sre = warp_sum_d((double)re), sim = warp_sum_d((double)im);
+      if (lane == 0) {
+        const uint64_t slot = member * (1ull << A.tile_shift) + (mloc >> kWin);
+        A.fid_partials[2 * slot] = sre;
+        A.fid_partials[2 * slot + 1] = sim;
+      }
+    }
+    C* out = psi + base + lane;
+#pragma unroll
+    for (int r = 0; r < kAmps; ++r) out[32 * r] = a[r];
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------- HIGH pass
+// Window = the 10 highest qubits (all >= COLB).  A block streams a contiguous
+// range of tiles of 2^COLB consecutive "columns" (qubits 0..COLB-1) x 1024
+// window rows, each loaded as four 256-row boxes of a 2D tensor map
+// [members * 1024 rows][2^(n-10) columns].  The window bits are contiguous,
+// so register r of stage A sits at offset r << win[5] and of stage B at
+// r << win[0].
+template <int COLB> struct HighShape {
+  static constexpr int COLS = 1 << COLB;
+  static constexpr int LW = kRegBits - COLB;            // lane bits that are window bits
+  static constexpr int WARPS = 1 << COLB;               // warp bits = COLB window bits
+  static constexpr int THREADS = WARPS * 32;
+  static constexpr int TILE = COLS * 1024;
+};
+
+template <typename R, int COLB>
+__global__ void __launch_bounds__(HighShape<COLB>::THREADS, 1)
+    k_pass_high(cplx<R>* __restrict__ psi, const __grid_constant__ CUtensorMap tmap, const __grid_constant__ PassArgs A) {
+  using C = cplx<R>;
+  using S = HighShape<COLB>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ double fid_red[2][S::WARPS];
+  C* smbase = reinterpret_cast<C*>(smem_raw);
+  C* alpha_sm = smbase + 2 * S::TILE;                   // [COLS][12]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int col = lane & (S::COLS - 1);
+  const int lh = lane >> COLB;
+  const R* params = static_cast<const R*>(A.params);
+  const uint32_t tile_bytes = (uint32_t)(S::TILE * sizeof(C));
+  const int elem_cols = (int)(sizeof(C) / 8);          // 8-byte tensor elements per amplitude
+
+  const int xa = lh | (warp << S::LW);                  // stage A: local bits 0..4
+  const int xb = (lh << 5) | (warp << (5 + S::LW));     // stage B: local bits 5..9
+  const uint32_t offa = (uint32_t)xa << A.win[0];       // member-local offsets of the thread bits
+  const uint32_t offb = (uint32_t)(xb >> 5) << A.win[5];
+  const int sha = A.win[5], shb = A.win[0];             // register r: r << sha (A), r << shb (B)
+  const uint64_t per = (A.tiles + gridDim.x - 1) / gridDim.x;
+  const uint64_t first = (uint64_t)blockIdx.x * per;
+  const uint64_t last = first + per < A.tiles ? first + per : A.tiles;
+
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](uint64_t t, int which) {
+    const uint64_t member = t >> A.tile_shift;
+    const uint64_t tl = t & ((1ull << A.tile_shift) - 1);
+    mbar_expect_tx(&bars[which], tile_bytes);
+    const int x = (int)(tl * S::COLS) * elem_cols;
+    C* dst = smbase + which * S::TILE;
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+      tma_g2s_2d(dst + b * 256 * S::COLS, &tmap, x, (int)(member * 1024 + b * 256), &bars[which]);
+  };
+  if (!A.synth && threadIdx.x == 0 && first < last) issue(first, 0);
+  int in_flight = (!A.synth && first < last) ? 1 : 0;
+  uint32_t it = 0;
+  for (uint64_t t = first; t < last; ++t, ++it) {
+    const int cur = it & 1;
+    if (!A.synth && threadIdx.x == 0 && t + 1 < last) {
+      fence_proxy_async();
+      issue(t + 1, cur ^ 1);
+      ++in_flight;
+    }
+    const uint64_t member = t >> A.tile_shift;
+    const uint64_t tl = t & ((1ull << A.tile_shift) - 1);
+    const uint32_t tbits = (uint32_t)(tl << COLB);      // the other bits are COLB .. n-11
+    const R* P = params + member * (uint64_t)A.param_stride;
+    C* sm = smbase + cur * S::TILE;
+    C a[kAmps];
+    int stage = A.start_stage;
+    if (A.synth) {
+      const uint64_t x = A.basis ? A.basis[member] : A.basis0[0];
+      const uint32_t fixed = tbits | (uint32_t)col | (stage == 0 ? offa : offb);
+      const int sh = stage == 0 ? sha : shb;
+#pragma unroll
+      for (int r = 0; r < kAmps; ++r)
+        a[r] = mk<R>((uint64_t)(fixed | ((uint32_t)r << sh)) == x ? R(1) : R(0), R(0));
+    } else {
+      if (!mbar_wait(&bars[cur], (it >> 1) & 1)) {
+        report_timeout(A.status);
+        if (threadIdx.x == 0 && in_flight > 1) mbar_wait(&bars[cur ^ 1], ((it + 1) >> 1) & 1);
+        return;
+      }
+      if (threadIdx.x == 0) --in_flight;
+      if (stage == 0) {
+#pragma unroll
+        for (int r = 0; r < kAmps; ++r) a[r] = sm[(xa | (r << 5)) * S::COLS + col];
+      } else {
+#pragma unroll
+        for (int r = 0; r < kAmps; ++r) a[r] = sm[(r | xb) * S::COLS + col];
+      }
+    }
+    for (int i = 0; i < A.num_ops; ++i) {
+      const FOp op = A.ops[i];
+      if (op.type == OP_DENSE) {
+        dense_dispatch<R>(a, stage == 0 ? op.j - 5 : op.j, P + op.off, op.real);
+      } else if (op.type == OP_DWIN) {
+        dwin_dispatch<R>(a, stage == 0 ? op.j - 5 : op.j, stage == 0, P + op.off, xa);
+      } else if (op.type == OP_FLIP || op.type == OP_FLIPM) {
+        const uint64_t w = op.type == OP_FLIP ? op.index : A.marked[member];
+        const int sh = stage == 0 ? sha : shb;
+        const uint64_t regmask = 31ull << sh;
+        const uint64_t fixed = tbits | (uint32_t)col | (stage == 0 ? offa : offb);
+        flip_reg<R>(a, (w & ~regmask) == fixed, (int)((w >> sh) & 31));
+      } else {
+        __syncthreads();
+        if (stage == 0) {
+#pragma unroll
+          for (int r = 0; r < kAmps; ++r) sm[(xa | (r << 5)) * S::COLS + col] = a[r];
+          __syncthreads();
+#pragma unroll
+          for (int r = 0; r < kAmps; ++r) a[r] = sm[(r | xb) * S::COLS + col];
+        } else {
+#pragma unroll
+          for (int r = 0; r < kAmps; ++r) sm[(r | xb) * S::COLS + col] = a[r];
+          __syncthreads();
+#pragma unroll
+          for (int r = 0; r < kAmps; ++r) a[r] = sm[(xa | (r << 5)) * S::COLS + col];
+        }
+        stage ^= 1;
+      }
+    }
+    if (A.out_start[11] > 0) {
+      __syncthreads();
+      for (int i = threadIdx.x; i < S::COLS * 11; i += S::THREADS) {
+        const int c = i / 11, aa = i % 11;
+        alpha_sm[c * 12 + aa] = out_alpha<R>(A, P, aa, (uint64_t)(tbits | (uint32_t)c));
+      }
+      __syncthreads();
+      const C* al_c = alpha_sm + col * 12;
+      C c = al_c[10];
+      C al[kRegBits];
+      const int xt = stage == 0 ? xa : xb;
+#pragma unroll
+      for (int r = 0; r < kRegBits; ++r) {
+        al[r] = al_c[stage == 0 ? r + 5 : r];
+        const int lt = stage == 0 ? r : r + 5;
+        if ((xt >> lt) & 1) c = cmul(c, al_c[lt]);
+      }
+      apply_reg_product<R>(a, c, al);
+    }
+    const uint32_t fixed = tbits + (uint32_t)col + (stage == 0 ? offa : offb);
+    const int sh = stage == 0 ? sha : shb;
+    if (A.fid) {
+      const C* ref = static_cast<const C*>(A.ref) + fixed;
+      R re = 0, im = 0;
+#pragma unroll
+      for (int r = 0; r < kAmps; ++r) {
+        const C f = ref[(uint32_t)r << sh];
+        re += f.x * a[r].x + f.y * a[r].y;
+        im += f.x * a[r].y - f.y * a[r].x;
+      }
+      const double sre = warp_sum_d((double)re), sim = warp_sum_d((double)im);
+      if (lane == 0) { fid_red[0][warp] = sre; fid_red[1][warp] = sim; }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double tr = 0.0, ti = 0.0;
+        for (int w = 0; w < S::WARPS; ++w) { tr += fid_red[0][w]; ti += fid_red[1][w]; }
+        const uint64_t slot = member * (1ull << A.tile_shift) + tl;
+        A.fid_partials[2 * slot] = tr;
+        A.fid_partials[2 * slot + 1] = ti;
+      }
+    }
+    C* out = psi + (member << A.n) + fixed;
+#pragma unroll
+    for (int r = 0; r < kAmps; ++r) out[(uint32_t)r << sh] = a[r];
+    __syncthreads();
+  }
+}
+
+}  // namespace fused
+}  // namespace qs

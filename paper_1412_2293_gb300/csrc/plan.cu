@@ -40,7 +40,10 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "internal.cuh"
+#include "pass.cuh"
 #include "philox.cuh"
 
 using cd = std::complex<double>;
@@ -48,361 +51,12 @@ using cd = std::complex<double>;
 namespace qs {
 namespace fused {
 
-constexpr int kWin = 10;
-constexpr int kRegBits = 5;
-constexpr int kAmps = 32;
-constexpr int kLowWarps = 8;
-constexpr int kMaxOther = 48;
 // per-pass limits (precompute shared memory <= 24 KB, bounded parameter block)
 constexpr size_t kMaxContribs = 1024;
 constexpr size_t kMaxDwin = 64;
 constexpr size_t kMaxTableEntries = 8192;
 constexpr size_t kMaxOut = 1024;
-constexpr size_t kMaxOps = 4096;
-
-enum : uint8_t { OP_DENSE = 0, OP_DWIN = 1, OP_FLIP = 2, OP_FLIPM = 3, OP_EXCH = 4 };
-
-struct FOp {
-  uint8_t type;
-  uint8_t j;          // local window bit (DENSE, DWIN)
-  uint8_t real;       // DENSE: matrix is real
-  uint8_t pad;
-  uint32_t off;       // parameter offset (R units) in the member block
-  uint64_t index;     // FLIP: member-local amplitude index
-};
-
-struct OutTerm {
-  int32_t a;          // attach local bit, or -1
-  uint32_t off;       // parameter offset of the factor
-  uint64_t cmask;     // member-local out-of-window bits that must be set
-};
-
-struct PassArgs {
-  int n;
-  int start_stage;    // 0 = A, 1 = B
-  int win[kWin];
-  int num_other;      // HIGH: member-local bits that enumerate tiles
-  int other[kMaxOther];
-  int num_ops;
-  const FOp* ops;
-  int out_start[12];  // out terms grouped by attach a (0..9) and 10 = none
-  const OutTerm* outs;
-  int param_stride;   // R units per member
-  const void* params;
-  const uint64_t* marked;
-  uint64_t tiles;
-};
-
-// ---------------------------------------------------------------- registers
-
-template <typename R>
-__device__ __forceinline__ cplx<R> ld_c(const R* p) { return mk<R>(p[0], p[1]); }
-
-template <typename R, int RJ>
-__device__ __forceinline__ void dense_reg(cplx<R> (&a)[kAmps], const R* m, bool real) {
-  if (real) {
-    const R u00 = m[0], u01 = m[2], u10 = m[4], u11 = m[6];
-#pragma unroll
-    for (int r = 0; r < kAmps; ++r) {
-      if (r & (1 << RJ)) continue;
-      const cplx<R> x0 = a[r], x1 = a[r | (1 << RJ)];
-      a[r] = mk<R>(u00 * x0.x + u01 * x1.x, u00 * x0.y + u01 * x1.y);
-      a[r | (1 << RJ)] = mk<R>(u10 * x0.x + u11 * x1.x, u10 * x0.y + u11 * x1.y);
-    }
-  } else {
-    const cplx<R> u00 = ld_c(m), u01 = ld_c(m + 2), u10 = ld_c(m + 4), u11 = ld_c(m + 6);
-#pragma unroll
-    for (int r = 0; r < kAmps; ++r) {
-      if (r & (1 << RJ)) continue;
-      const cplx<R> x0 = a[r], x1 = a[r | (1 << RJ)];
-      a[r] = cfma(u01, x1, cmul(u00, x0));
-      a[r | (1 << RJ)] = cfma(u11, x1, cmul(u10, x0));
-    }
-  }
-}
-
-template <typename R>
-__device__ __forceinline__ void dense_dispatch(cplx<R> (&a)[kAmps], int rj, const R* m, bool real) {
-  switch (rj) {
-    case 0: dense_reg<R, 0>(a, m, real); break;
-    case 1: dense_reg<R, 1>(a, m, real); break;
-    case 2: dense_reg<R, 2>(a, m, real); break;
-    case 3: dense_reg<R, 3>(a, m, real); break;
-    default: dense_reg<R, 4>(a, m, real); break;
-  }
-}
-
-// Multiply registers with bit RJ set by T[idx]: stage A idx = tbits | (low
-// register bits << 5), stage B idx = low register bits (bits below RJ).
-template <typename R, int RJ, bool STAGE_A>
-__device__ __forceinline__ void dwin_reg(cplx<R> (&a)[kAmps], const R* T, int tbits) {
-  constexpr int Q = 1 << RJ;
-  cplx<R> f[Q];
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    const int idx = STAGE_A ? (tbits | (q << 5)) : q;
-    f[q] = ld_c(T + 2 * idx);
-  }
-#pragma unroll
-  for (int r = 0; r < kAmps; ++r)
-    if (r & (1 << RJ)) a[r] = cmul(f[r & (Q - 1)], a[r]);
-}
-
-template <typename R>
-__device__ __forceinline__ void dwin_dispatch(cplx<R> (&a)[kAmps], int rj, bool stage_a, const R* T, int tbits) {
-  if (stage_a) {
-    switch (rj) {
-      case 0: dwin_reg<R, 0, true>(a, T, tbits); break;
-      case 1: dwin_reg<R, 1, true>(a, T, tbits); break;
-      case 2: dwin_reg<R, 2, true>(a, T, tbits); break;
-      case 3: dwin_reg<R, 3, true>(a, T, tbits); break;
-      default: dwin_reg<R, 4, true>(a, T, tbits); break;
-    }
-  } else {
-    switch (rj) {
-      case 0: dwin_reg<R, 0, false>(a, T, tbits); break;
-      case 1: dwin_reg<R, 1, false>(a, T, tbits); break;
-      case 2: dwin_reg<R, 2, false>(a, T, tbits); break;
-      case 3: dwin_reg<R, 3, false>(a, T, tbits); break;
-      default: dwin_reg<R, 4, false>(a, T, tbits); break;
-    }
-  }
-}
-
-// Negate register rw when `match`.
-template <typename R>
-__device__ __forceinline__ void flip_reg(cplx<R> (&a)[kAmps], bool match, int rw) {
-#pragma unroll
-  for (int r = 0; r < kAmps; ++r)
-    if (match && r == rw) { a[r].x = -a[r].x; a[r].y = -a[r].y; }
-}
-
-// Register table over the 5 register bits: factor(rho) = c * prod_{r in rho} alpha[r].
-template <typename R>
-__device__ __forceinline__ void apply_reg_product(cplx<R> (&a)[kAmps], cplx<R> c, const cplx<R> (&al)[kRegBits]) {
-  cplx<R> t[kAmps];
-  t[0] = c;
-#pragma unroll
-  for (int r = 0; r < kRegBits; ++r)
-#pragma unroll
-    for (int q = 0; q < (1 << r); ++q) t[q | (1 << r)] = cmul(t[q], al[r]);
-#pragma unroll
-  for (int r = 0; r < kAmps; ++r) a[r] = cmul(t[r], a[r]);
-}
-
-// Member-local index bits of the thread's fixed (non-register) position.
-// gbit(l) = global bit of local window bit l.
-
-// Out factor of attach a for this thread: product of the out terms of a
-// whose out-of-window bits are all set in `fixed`.
-template <typename R>
-__device__ __forceinline__ cplx<R> out_alpha(const PassArgs& A, const R* P, int a, uint64_t fixed) {
-  cplx<R> acc = mk<R>(R(1), R(0));
-  for (int i = A.out_start[a]; i < A.out_start[a + 1]; ++i) {
-    const OutTerm t = A.outs[i];
-    if ((fixed & t.cmask) == t.cmask) acc = cmul(acc, ld_c(P + t.off));
-  }
-  return acc;
-}
-
-// ---------------------------------------------------------------- LOW pass
-// One warp per tile of 1024 consecutive amplitudes (window = qubits 0..9).
-template <typename R>
-__global__ void __launch_bounds__(kLowWarps * 32) k_pass_low(cplx<R>* __restrict__ psi, PassArgs A) {
-  using C = cplx<R>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* sm = reinterpret_cast<C*>(smem_raw);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  C* wsm = sm + warp * 1056;
-  C* alpha_sm = sm + kLowWarps * 1056 + warp * 12;
-  const uint64_t nmask = (1ull << A.n) - 1;
-  const R* params = static_cast<const R*>(A.params);
-
-  for (uint64_t t = (uint64_t)blockIdx.x * kLowWarps + warp; t < A.tiles; t += (uint64_t)gridDim.x * kLowWarps) {
-    const uint64_t base = t << kWin;
-    const uint64_t member = base >> A.n;
-    const uint64_t mloc = base & nmask;                 // member-local tile bits (>= 10)
-    const R* P = params + member * (uint64_t)A.param_stride;
-    C a[kAmps];
-#pragma unroll
-    for (int r = 0; r < kAmps; ++r) a[r] = psi[base + lane + 32 * r];
-    int stage = 0;                                       // loads are in stage A layout
-    for (int i = 0; i < A.num_ops; ++i) {
-      const FOp op = A.ops[i];
-      if (op.type == OP_DENSE) {
-        dense_dispatch<R>(a, stage == 0 ? op.j - 5 : op.j, P + op.off, op.real);
-      } else if (op.type == OP_DWIN) {
-        dwin_dispatch<R>(a, stage == 0 ? op.j - 5 : op.j, stage == 0, P + op.off, lane);
-      } else if (op.type == OP_FLIP || op.type == OP_FLIPM) {
-        const uint64_t w = op.type == OP_FLIP ? op.index : A.marked[member];
-        const uint64_t fixed = mloc | (stage == 0 ? (uint64_t)lane : ((uint64_t)lane << 5));
-        const uint64_t regmask = stage == 0 ? (31ull << 5) : 31ull;
-        const bool match = (w & ~regmask) == fixed;
-        const int rw = stage == 0 ? (int)((w >> 5) & 31) : (int)(w & 31);
-        flip_reg<R>(a, match, rw);
-      } else {                                           // exchange A <-> B
-#pragma unroll
-        for (int r = 0; r < kAmps; ++r) wsm[stage == 0 ? lane + 33 * r : r + 33 * lane] = a[r];
-        __syncwarp();
-#pragma unroll
-        for (int r = 0; r < kAmps; ++r) a[r] = wsm[stage == 0 ? r + 33 * lane : lane + 33 * r];
-        __syncwarp();
-        stage ^= 1;
-      }
-    }
-    if (A.out_start[11] > 0) {
-      // out terms: all out-of-window bits are the tile's (uniform per warp)
-      if (lane < 11) alpha_sm[lane] = out_alpha<R>(A, P, lane, mloc);
-      __syncwarp();
-      C al[kRegBits];
-      C c = alpha_sm[10];
-#pragma unroll
-      for (int r = 0; r < kRegBits; ++r) {
-        const int lr = stage == 0 ? r + 5 : r;           // local bit of register r
-        al[r] = alpha_sm[lr];
-        const int lt = stage == 0 ? r : r + 5;           // local bit of lane bit r
-        if ((lane >> r) & 1) c = cmul(c, alpha_sm[lt]);
-      }
-      apply_reg_product<R>(a, c, al);
-      __syncwarp();
-    }
-    if (stage == 1) {
-#pragma unroll
-      for (int r = 0; r < kAmps; ++r) wsm[r + 33 * lane] = a[r];
-      __syncwarp();
-#pragma unroll
-      for (int r = 0; r < kAmps; ++r) a[r] = wsm[lane + 33 * r];
-      __syncwarp();
-    }
-#pragma unroll
-    for (int r = 0; r < kAmps; ++r) psi[base + lane + 32 * r] = a[r];
-  }
-}
-
-// ---------------------------------------------------------------- HIGH pass
-template <int COLB> struct HighShape {
-  static constexpr int COLS = 1 << COLB;
-  static constexpr int LW = kRegBits - COLB;            // lane bits that are window bits
-  static constexpr int WARPS = 1 << COLB;               // warp bits = COLB window bits
-  static constexpr int THREADS = WARPS * 32;
-  static constexpr int TILE = COLS * 1024;
-  static constexpr int SMEM_ELEMS = TILE + 32 * 8;      // + padding (x >> 5) * 8
-};
-
-template <int COLB>
-__device__ __forceinline__ int high_sidx(int x, int col) {
-  return x * HighShape<COLB>::COLS + col + (x >> 5) * 8;
-}
-
-template <typename R, int COLB>
-__global__ void __launch_bounds__(HighShape<COLB>::THREADS) k_pass_high(cplx<R>* __restrict__ psi, PassArgs A) {
-  using C = cplx<R>;
-  using S = HighShape<COLB>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* sm = reinterpret_cast<C*>(smem_raw);
-  C* alpha_sm = sm + S::SMEM_ELEMS;                     // [COLS][12]
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int col = lane & (S::COLS - 1);
-  const int lh = lane >> COLB;
-  const R* params = static_cast<const R*>(A.params);
-  const int tile_shift = A.n - 10 - COLB;               // log2(tiles per member)
-
-  // thread window bits in each stage layout (local x without register bits)
-  const int xa = lh | (warp << S::LW);                  // stage A: local bits 0..4
-  const int xb = (lh << 5) | (warp << (5 + S::LW));     // stage B: local bits 5..9
-  uint64_t offa = 0, offb = 0;
-  for (int l = 0; l < kRegBits; ++l) {
-    if ((xa >> l) & 1) offa |= 1ull << A.win[l];
-    if ((xb >> (l + 5)) & 1) offb |= 1ull << A.win[l + 5];
-  }
-
-  for (uint64_t t = blockIdx.x; t < A.tiles; t += gridDim.x) {
-    const uint64_t member = t >> tile_shift;
-    const uint64_t tl = t & ((1ull << tile_shift) - 1);
-    uint64_t tbits = 0;
-    for (int i = 0; i < A.num_other; ++i) tbits |= ((tl >> i) & 1) << A.other[i];
-    const uint64_t mbase = member << A.n;
-    const R* P = params + member * (uint64_t)A.param_stride;
-    C a[kAmps];
-    int stage = A.start_stage;
-    {
-      const uint64_t b0 = mbase + tbits + col + (stage == 0 ? offa : offb);
-#pragma unroll
-      for (int r = 0; r < kAmps; ++r) {
-        uint64_t off = 0;
-#pragma unroll
-        for (int q = 0; q < kRegBits; ++q)
-          if ((r >> q) & 1) off += 1ull << A.win[stage == 0 ? q + 5 : q];
-        a[r] = psi[b0 + off];
-      }
-    }
-    for (int i = 0; i < A.num_ops; ++i) {
-      const FOp op = A.ops[i];
-      if (op.type == OP_DENSE) {
-        dense_dispatch<R>(a, stage == 0 ? op.j - 5 : op.j, P + op.off, op.real);
-      } else if (op.type == OP_DWIN) {
-        dwin_dispatch<R>(a, stage == 0 ? op.j - 5 : op.j, stage == 0, P + op.off, xa);
-      } else if (op.type == OP_FLIP || op.type == OP_FLIPM) {
-        const uint64_t w = op.type == OP_FLIP ? op.index : A.marked[member];
-        uint64_t regmask = 0;
-        int rw = 0;
-#pragma unroll
-        for (int q = 0; q < kRegBits; ++q) {
-          const int g = A.win[stage == 0 ? q + 5 : q];
-          regmask |= 1ull << g;
-          rw |= (int)((w >> g) & 1) << q;
-        }
-        const uint64_t fixed = tbits | (uint64_t)col | (stage == 0 ? offa : offb);
-        flip_reg<R>(a, (w & ~regmask) == fixed, rw);
-      } else {
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < kAmps; ++r) {
-          const int x = stage == 0 ? (xa | (r << 5)) : (r | xb);
-          sm[high_sidx<COLB>(x, col)] = a[r];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < kAmps; ++r) {
-          const int x = stage == 0 ? (r | xb) : (xa | (r << 5));
-          a[r] = sm[high_sidx<COLB>(x, col)];
-        }
-        stage ^= 1;
-      }
-    }
-    if (A.out_start[11] > 0) {
-      __syncthreads();
-      // alpha[col][a] for a = 0..9 (window bits) and 10 (no window bit)
-      for (int i = threadIdx.x; i < S::COLS * 11; i += S::THREADS) {
-        const int c = i / 11, aa = i % 11;
-        alpha_sm[c * 12 + aa] = out_alpha<R>(A, P, aa, tbits | (uint64_t)c);
-      }
-      __syncthreads();
-      const C* al_c = alpha_sm + col * 12;
-      C c = al_c[10];
-      C al[kRegBits];
-      const int xt = stage == 0 ? xa : xb;
-#pragma unroll
-      for (int r = 0; r < kRegBits; ++r) {
-        al[r] = al_c[stage == 0 ? r + 5 : r];
-        const int lt = stage == 0 ? r : r + 5;           // thread (non-register) local bit
-        if ((xt >> lt) & 1) c = cmul(c, al_c[lt]);
-      }
-      apply_reg_product<R>(a, c, al);
-    }
-    {
-      const uint64_t b0 = mbase + tbits + col + (stage == 0 ? offa : offb);
-#pragma unroll
-      for (int r = 0; r < kAmps; ++r) {
-        uint64_t off = 0;
-#pragma unroll
-        for (int q = 0; q < kRegBits; ++q)
-          if ((r >> q) & 1) off += 1ull << A.win[stage == 0 ? q + 5 : q];
-        psi[b0 + off] = a[r];
-      }
-    }
-  }
-}
+constexpr size_t kMaxOps = kMaxPassOps;
 
 // ---------------------------------------------------------------- precompute
 enum : int { PD_DENSE = 0, PD_OUT = 1, PD_DWIN = 2 };
@@ -434,6 +88,7 @@ struct RunParams {        // values of one run (written before each launch)
   uint64_t seed;
   uint64_t gate_id0;
   uint64_t traj0;
+  uint64_t basis;         // basis state of every member when the run starts from one
 };
 
 __device__ __forceinline__ void member_noise(const NoiseSrc& src, const RunParams* rp, int b, double* e,
@@ -583,6 +238,8 @@ struct PassPlan {
   int num_dwin = 0;
   int stride = 0;                 // R units per member
   std::vector<int> other;
+  int tile_shift = 0;             // log2(tiles per member)
+  CUtensorMap tmap;               // HIGH: [members * 1024 rows][2^(n-10) columns]
   // device copies
   FOp* d_ops = nullptr;
   OutTerm* d_outs = nullptr;
@@ -607,13 +264,16 @@ struct qs_plan_s {
   DGate* d_gates = nullptr;
   RunParams* d_run = nullptr;
   RunParams* h_run = nullptr;     // pinned
-  cudaGraphExec_t exec = nullptr;
-  bool graph_member_noise = false;
-  bool graph_member_marked = false;
-  void* graph_state = nullptr;
+  // captured graphs, one per run variant: start (0 loaded, 1 one basis state,
+  // 2 per-member basis states) x fused fidelity (0, 1)
+  cudaGraphExec_t exec[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool graph_member_noise[6] = {false, false, false, false, false, false};
+  bool graph_member_marked[6] = {false, false, false, false, false, false};
+  bool graph_timing[6] = {false, false, false, false, false, false};
+  double* d_fid = nullptr;        // fused-fidelity partials [member][tile] complex
+  int colb = 3;
   int launches = 0;
   bool timing = false;
-  bool graph_timing = false;
   std::vector<cudaEvent_t> events;     // launches + 1 when timing
   std::vector<int> event_kinds;
   std::string err;
@@ -664,8 +324,9 @@ bool commute(const PGate& a, const PGate& b) {
 int stage_of(int j) { return j >= 5 ? 0 : 1; }
 
 // Greedy pass builder starting at remaining[0]; returns absorbed flags.
-bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n, PassPlan* P,
+bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n, int colb, PassPlan* P,
                 std::vector<char>* absorbed) {
+  P->colb = colb;
   // window from the first fusable dense gate (lookahead)
   int q = -1;
   for (size_t i = 0; i < rem.size() && i < 64; ++i) {
@@ -675,7 +336,7 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
   }
   P->high = false;
   if (q >= 10) {
-    if (n < 13) return false;
+    if (n < kWin + colb) return false;               // a high tile needs 2^colb columns
     P->high = true;
   }
   for (int l = 0; l < kWin; ++l) P->win[l] = P->high ? n - kWin + l : l;
@@ -702,7 +363,7 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
     if (!g.dense1 && !g.cp && !g.flip) break;           // a gate the pass cannot hold ends the scan
     // bounds of one pass: precompute shared memory and the per-member block
     if (ncontrib >= kMaxContribs || dwins.size() >= kMaxDwin || table_entries >= kMaxTableEntries ||
-        out_gates.size() >= kMaxOut || P->ops.size() >= kMaxOps)
+        out_gates.size() >= kMaxOut || P->ops.size() + 2 > kMaxOps)
       break;
     bool ok = true;
     for (int s : skipped) if (!commute(G[s], g)) { ok = false; break; }
@@ -842,9 +503,12 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
   P->out_start[11] = acc;
   P->prods = prods;
   P->stride = (int)((off + 3) & ~3u);
+  P->other.clear();
   if (P->high) {
-    P->other.clear();
     for (int b = P->colb; b < n; ++b) if (loc[b] < 0) P->other.push_back(b);
+    P->tile_shift = n - kWin - P->colb;
+  } else {
+    P->tile_shift = n - kWin;
   }
   return true;
 }
@@ -858,30 +522,69 @@ qs_status upload(qs_plan p, T** dst, const std::vector<T>& v) {
   return QS_OK;
 }
 
-size_t high_smem(int colb, size_t esize) {
-  const size_t cols = 1u << colb;
-  return (cols * 1024 + 32 * 8) * esize + cols * 12 * esize;
+constexpr int kLowWarpsF = 8;   // complex64: 8 warps per block
+constexpr int kLowWarpsD = 4;   // complex128: 4 warps (same shared memory)
+
+template <typename R> constexpr int low_warps() { return sizeof(R) == 4 ? kLowWarpsF : kLowWarpsD; }
+template <typename R> constexpr int high_colb() { return sizeof(R) == 4 ? 3 : 2; }
+
+template <typename R>
+size_t low_smem() { return (size_t)low_warps<R>() * LowShape<low_warps<R>()>::PER_WARP * sizeof(cplx<R>); }
+template <typename R>
+size_t high_smem() {
+  constexpr int colb = high_colb<R>();
+  return (2 * (size_t)HighShape<colb>::TILE + HighShape<colb>::COLS * 12) * sizeof(cplx<R>);
 }
 
-size_t low_smem(size_t esize) { return (kLowWarps * 1056 + kLowWarps * 12) * esize; }
+// Tensor map of the state as [batch * 1024 rows][2^(n-10) columns] of 8-byte
+// elements (a complex128 amplitude is two of them), boxes of 2^colb amplitudes
+// x 256 rows.
+qs_status make_tmap(qs_plan p, PassPlan* P) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return pfail(p, QS_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  qs_ctx* h = p->h;
+  const uint64_t per = h->esize / 8;                     // 8-byte elements per amplitude
+  cuuint64_t dims[2] = {(cuuint64_t)(1ull << (h->n - kWin)) * per, (cuuint64_t)h->batch * 1024};
+  cuuint64_t strides[1] = {dims[0] * 8};
+  cuuint32_t box[2] = {(cuuint32_t)((1u << P->colb) * per), 256};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(&P->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, h->state, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return pfail(p, QS_ERR_CUDA, "tensor map encode failed");
+  return QS_OK;
+}
 
-PassArgs pass_args(qs_plan p, const PassPlan& P) {
+PassArgs pass_args(qs_plan p, const PassPlan& P, int synth, int fid) {
   qs_ctx* h = p->h;
   PassArgs A{};
   A.n = h->n;
   A.start_stage = P.start_stage;
   for (int l = 0; l < kWin; ++l) A.win[l] = P.win[l];
-  A.num_other = (int)P.other.size();
-  for (int i = 0; i < A.num_other && i < kMaxOther; ++i) A.other[i] = P.other[i];
   A.num_ops = (int)P.ops.size();
-  A.ops = P.d_ops;
+  for (int i = 0; i < A.num_ops; ++i) A.ops[i] = P.ops[i];
   for (int i = 0; i < 12; ++i) A.out_start[i] = P.out_start[i];
   A.outs = P.d_outs;
   A.param_stride = P.stride;
   A.params = P.d_params;
   A.marked = h->m_marked;
   const uint64_t total = (uint64_t)h->batch << h->n;
-  A.tiles = P.high ? total >> (10 + P.colb) : total >> 10;
+  A.tiles = P.high ? total >> (kWin + P.colb) : total >> kWin;
+  A.tile_shift = P.tile_shift;
+  A.status = h->dstatus + 2;
+  A.synth = synth ? 1 : 0;
+  A.basis = synth == 2 ? h->m_basis : nullptr;
+  A.basis0 = &p->d_run->basis;
+  A.fid = fid;
+  A.ref = h->ref;
+  A.fid_partials = p->d_fid;
   return A;
 }
 
@@ -899,36 +602,34 @@ cudaError_t launch_precompute(qs_plan p, const PassPlan& P, cudaStream_t s) {
 }
 
 template <typename R>
-cudaError_t launch_pass_kernel(qs_plan p, const PassPlan& P, cudaStream_t s) {
+cudaError_t launch_pass_kernel(qs_plan p, const PassPlan& P, cudaStream_t s, int synth, int fid) {
   qs_ctx* h = p->h;
-  const PassArgs A = pass_args(p, P);
+  const PassArgs A = pass_args(p, P, synth, fid);
   const int sms = num_sms();
   if (!P.high) {
-    const size_t sm = low_smem(sizeof(cplx<R>));
-    uint64_t blocks = (A.tiles + kLowWarps - 1) / kLowWarps;
-    const uint64_t cap = (uint64_t)sms * 8;
-    if (blocks > cap) blocks = cap;
-    k_pass_low<R><<<(int)blocks, kLowWarps * 32, sm, s>>>((cplx<R>*)h->state, A);
+    constexpr int W = low_warps<R>();
+    uint64_t blocks = (A.tiles + W - 1) / W;
+    if (blocks > (uint64_t)sms) blocks = sms;
+    k_pass_low<R, W><<<(int)blocks, W * 32, low_smem<R>(), s>>>((cplx<R>*)h->state, A);
   } else {
-    const size_t sm = high_smem(P.colb, sizeof(cplx<R>));
+    constexpr int CB = high_colb<R>();
     uint64_t blocks = A.tiles;
-    const uint64_t cap = (uint64_t)sms * 8;
-    if (blocks > cap) blocks = cap;
-    if constexpr (sizeof(R) == 4) {
-      if (P.colb == 4) k_pass_high<R, 4><<<(int)blocks, HighShape<4>::THREADS, sm, s>>>((cplx<R>*)h->state, A);
-      else k_pass_high<R, 3><<<(int)blocks, HighShape<3>::THREADS, sm, s>>>((cplx<R>*)h->state, A);
-    } else {
-      k_pass_high<R, 3><<<(int)blocks, HighShape<3>::THREADS, sm, s>>>((cplx<R>*)h->state, A);
-    }
+    if (blocks > (uint64_t)sms) blocks = sms;
+    k_pass_high<R, CB><<<(int)blocks, HighShape<CB>::THREADS, high_smem<R>(), s>>>((cplx<R>*)h->state, P.tmap, A);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_pass(qs_plan p, const PassPlan& P, cudaStream_t s) {
-  const bool f32 = p->h->dtype == QS_C64;
-  cudaError_t e = f32 ? launch_precompute<float>(p, P, s) : launch_precompute<double>(p, P, s);
-  if (e != cudaSuccess) return e;
-  return f32 ? launch_pass_kernel<float>(p, P, s) : launch_pass_kernel<double>(p, P, s);
+// fused fidelity: out[b] = |sum over the last pass's tiles of member b|^2
+__global__ void k_fid_finalize(const double* __restrict__ partials, int members, int tiles, double* __restrict__ out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= members) return;
+  double re = 0.0, im = 0.0;
+  for (int t = 0; t < tiles; ++t) {
+    re += partials[2 * ((uint64_t)b * tiles + t)];
+    im += partials[2 * ((uint64_t)b * tiles + t) + 1];
+  }
+  out[b] = re * re + im * im;
 }
 
 cudaError_t set_smem_attrs(size_t esize) {
@@ -937,20 +638,17 @@ cudaError_t set_smem_attrs(size_t esize) {
   if (done[which]) return cudaSuccess;
   cudaError_t e;
   if (esize == 8) {
-    e = cudaFuncSetAttribute(k_pass_low<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)low_smem(8));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass_high<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)high_smem(3, 8));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass_high<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)high_smem(4, 8));
+    e = cudaFuncSetAttribute(k_pass_low<float, kLowWarpsF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)low_smem<float>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_pass_high<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)high_smem<float>());
   } else {
-    e = cudaFuncSetAttribute(k_pass_low<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)low_smem(16));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass_high<double, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)high_smem(3, 16));
+    e = cudaFuncSetAttribute(k_pass_low<double, kLowWarpsD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)low_smem<double>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_pass_high<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)high_smem<double>());
   }
   if (e == cudaSuccess) done[which] = true;
   return e;
 }
-
-}  // namespace
-
-namespace {
 
 qs_status run_single(qs_plan p, const PGate& g, const RunParams& rp, int pos) {
   qs_ctx* h = p->h;
@@ -965,7 +663,10 @@ qs_status run_single(qs_plan p, const PGate& g, const RunParams& rp, int pos) {
   return qs_apply_gate(h, g.g.targets, g.g.k, g.g.U);
 }
 
-qs_status enqueue_run(qs_plan p, cudaStream_t s) {
+// Enqueue one run.  synth: the first pass creates the start state (1: one
+// basis state, 2: per-member basis states); fid: the last pass also reduces
+// the fidelity with the stored reference into h->small (kSmallOut).
+qs_status enqueue_run(qs_plan p, cudaStream_t s, int synth, int fid) {
   qs_ctx* h = p->h;
   cudaStream_t saved = h->stream;
   h->stream = s;
@@ -979,13 +680,21 @@ qs_status enqueue_run(qs_plan p, cudaStream_t s) {
   };
   mark(-1);
   const bool f32 = h->dtype == QS_C64;
-  for (const Step& st : p->steps) {
+  for (size_t i = 0; i < p->steps.size(); ++i) {
+    const Step& st = p->steps[i];
     if (st.kind == 0) {
       const PassPlan& P = p->passes[st.pass];
+      const int sy = i == 0 ? synth : 0;
+      const int fd = (i + 1 == p->steps.size()) ? fid : 0;
       cudaError_t e = f32 ? launch_precompute<float>(p, P, s) : launch_precompute<double>(p, P, s);
       mark(0);
-      if (e == cudaSuccess) e = f32 ? launch_pass_kernel<float>(p, P, s) : launch_pass_kernel<double>(p, P, s);
+      if (e == cudaSuccess) e = f32 ? launch_pass_kernel<float>(p, P, s, sy, fd) : launch_pass_kernel<double>(p, P, s, sy, fd);
       mark(P.high ? 2 : 1);
+      if (e == cudaSuccess && fd) {
+        const int tiles = 1 << P.tile_shift;
+        k_fid_finalize<<<(h->batch + 255) / 256, 256, 0, s>>>(p->d_fid, h->batch, tiles, h->small + kSmallOutIndex);
+        e = cudaGetLastError();
+      }
       if (e != cudaSuccess) { h->stream = saved; return pfail(p, QS_ERR_CUDA, std::string("fused pass: ") + cudaGetErrorString(e)); }
     } else {
       qs_status r = run_single(p, p->gates[st.gate], *p->h_run, st.gate);
@@ -995,6 +704,73 @@ qs_status enqueue_run(qs_plan p, cudaStream_t s) {
   }
   h->stream = saved;
   return QS_OK;
+}
+
+bool fusable_start(qs_plan p) { return !p->steps.empty() && p->steps[0].kind == 0; }
+bool fusable_end(qs_plan p) { return !p->steps.empty() && p->steps.back().kind == 0; }
+
+// One run of the plan (graph replay when every step is a fused pass).
+qs_status run_plan(qs_plan p, double e, uint64_t seed, uint64_t gate_id0, int want_fid) {
+  qs_ctx* h = p->h;
+  if (!(e >= 0.0) || !std::isfinite(e)) return pfail(p, QS_ERR_INVALID_ARG, "e must be finite and >= 0");
+  for (const PGate& g : p->gates)
+    if (g.g.kind == QS_FLIP_PER_MEMBER && !h->member_marked)
+      return pfail(p, QS_ERR_INVALID_ARG, "per-member flips need marked indices (qs_set_member_noise)");
+  // a pending basis start is synthesised by the first pass when there is one
+  int synth = 0;
+  if (h->pending) {
+    if (fusable_start(p)) {
+      synth = h->pending;
+    } else {
+      qs_status st = materialize_basis(h);
+      if (st != QS_OK) return st;
+    }
+  }
+  const int fid = want_fid && fusable_end(p) ? 1 : 0;
+  // the pinned run block may still be read by an earlier launch of the graph
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "stream sync");
+  p->h_run->e = e;
+  p->h_run->seed = seed;
+  p->h_run->gate_id0 = gate_id0;
+  p->h_run->traj0 = h->traj_offset;
+  p->h_run->basis = h->pending_x;
+  // the run owns the start state from here on: later steps (single gates)
+  // must not write the basis state again
+  if (synth) h->pending = 0;
+  const bool has_single = std::any_of(p->steps.begin(), p->steps.end(), [](const Step& s) { return s.kind == 1; });
+  qs_status st = QS_OK;
+  if (has_single) {
+    if (cudaMemcpyAsync(p->d_run, p->h_run, sizeof(RunParams), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+      return pfail(p, QS_ERR_CUDA, "run params copy");
+    st = enqueue_run(p, h->stream, synth, fid);
+  } else {
+    const int v = synth * 2 + fid;
+    if (p->exec[v] && (p->graph_member_noise[v] != h->member_noise || p->graph_member_marked[v] != h->member_marked ||
+                       p->graph_timing[v] != p->timing)) {
+      cudaGraphExecDestroy(p->exec[v]);
+      p->exec[v] = nullptr;
+    }
+    if (!p->exec[v]) {
+      cudaStream_t cs;
+      if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "capture stream");
+      cudaGraph_t graph;
+      cudaError_t e1 = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e1 == cudaSuccess) e1 = cudaMemcpyAsync(p->d_run, p->h_run, sizeof(RunParams), cudaMemcpyHostToDevice, cs);
+      qs_status cst = e1 == cudaSuccess ? enqueue_run(p, cs, synth, fid) : QS_ERR_CUDA;
+      cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+      cudaStreamDestroy(cs);
+      if (cst != QS_OK) return cst;
+      if (e1 != cudaSuccess || e2 != cudaSuccess) return pfail(p, QS_ERR_CUDA, "graph capture");
+      cudaError_t e3 = cudaGraphInstantiate(&p->exec[v], graph, 0);
+      cudaGraphDestroy(graph);
+      if (e3 != cudaSuccess) { p->exec[v] = nullptr; return pfail(p, QS_ERR_CUDA, "graph instantiate"); }
+      p->graph_member_noise[v] = h->member_noise;
+      p->graph_member_marked[v] = h->member_marked;
+      p->graph_timing[v] = p->timing;
+    }
+    if (cudaGraphLaunch(p->exec[v], h->stream) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "graph launch");
+  }
+  return st;
 }
 
 }  // namespace
@@ -1007,7 +783,6 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
   qs_plan p = new (std::nothrow) qs_plan_s();
   if (!p) return QS_ERR_OUT_OF_MEMORY;
   p->h = h;
-  // validate
   for (int i = 0; i < num_gates; ++i) {
     const qs_gate& g = gates[i];
     if (g.kind == QS_GATE_FLIP) {
@@ -1029,14 +804,16 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
     }
     p->gates.push_back(classify(g, h->n));
   }
-  const bool fuse = h->mode == QS_STATEVEC && h->n >= 10;
+  p->colb = h->dtype == QS_C64 ? 3 : 2;
+  // fused passes use 32-bit member-local offsets
+  const bool fuse = h->mode == QS_STATEVEC && h->n >= kWin && h->n <= 32;
   std::vector<int> rem;
   for (int i = 0; i < num_gates; ++i) rem.push_back(i);
   while (!rem.empty()) {
     if (fuse) {
       PassPlan P;
       std::vector<char> absorbed(rem.size(), 0);
-      if (build_pass(p->gates, rem, h->n, &P, &absorbed)) {
+      if (build_pass(p->gates, rem, h->n, p->colb, &P, &absorbed)) {
         bool any = false;
         for (char c : absorbed) any |= c != 0;
         if (any) {
@@ -1052,7 +829,6 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
     p->steps.push_back(Step{1, -1, rem[0]});
     rem.erase(rem.begin());
   }
-  // device data
   std::vector<DGate> dg(p->gates.size());
   for (size_t i = 0; i < p->gates.size(); ++i) {
     const qs_gate& g = p->gates[i].g;
@@ -1065,6 +841,7 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
     dg[i] = x;
   }
   qs_status st = upload(p, &p->d_gates, dg);
+  size_t fid_tiles = 0;
   for (auto& P : p->passes) {
     if (st != QS_OK) break;
     st = upload(p, &P.d_ops, P.ops);
@@ -1075,7 +852,12 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
       const size_t bytes = (size_t)P.stride * h->batch * (h->esize / 2);
       if (cudaMalloc(&P.d_params, std::max<size_t>(bytes, 16)) != cudaSuccess) st = pfail(p, QS_ERR_OUT_OF_MEMORY, "plan params");
     }
+    if (st == QS_OK && P.high) st = make_tmap(p, &P);
+    fid_tiles = (size_t)1 << P.tile_shift;
   }
+  if (st == QS_OK && !p->passes.empty() &&
+      cudaMalloc((void**)&p->d_fid, 2 * fid_tiles * h->batch * sizeof(double)) != cudaSuccess)
+    st = pfail(p, QS_ERR_OUT_OF_MEMORY, "fidelity partials");
   if (st == QS_OK && cudaMalloc((void**)&p->d_run, sizeof(RunParams)) != cudaSuccess) st = pfail(p, QS_ERR_OUT_OF_MEMORY, "run params");
   if (st == QS_OK && cudaMallocHost((void**)&p->h_run, sizeof(RunParams)) != cudaSuccess) st = pfail(p, QS_ERR_OUT_OF_MEMORY, "run params");
   if (st == QS_OK && set_smem_attrs(h->esize) != cudaSuccess) st = pfail(p, QS_ERR_CUDA, "shared memory attribute");
@@ -1088,60 +870,31 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
 
 qs_status qs_plan_run(qs_plan p, double e, uint64_t seed, uint64_t gate_id0) {
   if (!p) return QS_ERR_INVALID_ARG;
+  return run_plan(p, e, seed, gate_id0, 0);
+}
+
+qs_status qs_plan_run_fidelity(qs_plan p, double e, uint64_t seed, uint64_t gate_id0, double* out) {
+  if (!p || !out) return QS_ERR_INVALID_ARG;
   qs_ctx* h = p->h;
-  if (!(e >= 0.0) || !std::isfinite(e)) return pfail(p, QS_ERR_INVALID_ARG, "e must be finite and >= 0");
-  for (const PGate& g : p->gates)
-    if (g.g.kind == QS_FLIP_PER_MEMBER && !h->member_marked)
-      return pfail(p, QS_ERR_INVALID_ARG, "per-member flips need marked indices (qs_set_member_noise)");
-  // the pinned run block may still be read by an earlier launch of the graph
-  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "stream sync");
-  p->h_run->e = e;
-  p->h_run->seed = seed;
-  p->h_run->gate_id0 = gate_id0;
-  p->h_run->traj0 = h->traj_offset;
-  const bool has_single = std::any_of(p->steps.begin(), p->steps.end(), [](const Step& s) { return s.kind == 1; });
-  if (has_single) {
-    // single-gate steps take e, seed and ids as host arguments: run eagerly
-    if (cudaMemcpyAsync(p->d_run, p->h_run, sizeof(RunParams), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
-      return pfail(p, QS_ERR_CUDA, "run params copy");
-    return enqueue_run(p, h->stream);
-  }
-  const bool stale = p->exec && (p->graph_member_noise != h->member_noise ||
-                                 p->graph_member_marked != h->member_marked || p->graph_state != h->state ||
-                                 p->graph_timing != p->timing);
-  if (stale) { cudaGraphExecDestroy(p->exec); p->exec = nullptr; }
-  if (!p->exec) {
-    cudaStream_t cs;
-    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "capture stream");
-    cudaGraph_t graph;
-    cudaError_t e1 = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e1 == cudaSuccess) e1 = cudaMemcpyAsync(p->d_run, p->h_run, sizeof(RunParams), cudaMemcpyHostToDevice, cs);
-    qs_status st = e1 == cudaSuccess ? enqueue_run(p, cs) : QS_ERR_CUDA;
-    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
-    cudaStreamDestroy(cs);
-    if (st != QS_OK) return st;
-    if (e1 != cudaSuccess || e2 != cudaSuccess) return pfail(p, QS_ERR_CUDA, "graph capture");
-    cudaError_t e3 = cudaGraphInstantiate(&p->exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e3 != cudaSuccess) { p->exec = nullptr; return pfail(p, QS_ERR_CUDA, "graph instantiate"); }
-    p->graph_member_noise = h->member_noise;
-    p->graph_member_marked = h->member_marked;
-    p->graph_state = h->state;
-    p->graph_timing = p->timing;
-  }
-  if (cudaGraphLaunch(p->exec, h->stream) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "graph launch");
-  return QS_OK;
+  if (h->mode != QS_STATEVEC) return pfail(p, QS_ERR_NOT_SUPPORTED, "fused fidelity needs STATEVEC");
+  if (!h->has_ref) return pfail(p, QS_ERR_INVALID_ARG, "no stored reference (qs_set_reference)");
+  qs_status st = run_plan(p, e, seed, gate_id0, 1);
+  if (st != QS_OK) return st;
+  if (!fusable_end(p)) return qs_fidelity_stored(h, out);
+  return read_results(h, out, h->batch);
 }
 
 qs_status qs_plan_profile(qs_plan p, int reps, double e, uint64_t seed, uint64_t gate_id0, double* ms,
                           int* kinds, int cap, int* count) {
   if (!p || reps < 1 || !ms || !kinds || !count) return QS_ERR_INVALID_ARG;
   qs_ctx* h = p->h;
+  if (h->pending) { qs_status st = materialize_basis(h); if (st != QS_OK) return st; }
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "stream sync");
   p->h_run->e = e;
   p->h_run->seed = seed;
   p->h_run->gate_id0 = gate_id0;
   p->h_run->traj0 = h->traj_offset;
+  p->h_run->basis = 0;
   if (cudaMemcpyAsync(p->d_run, p->h_run, sizeof(RunParams), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
     return pfail(p, QS_ERR_CUDA, "run params copy");
   int nl = 0;
@@ -1161,7 +914,7 @@ qs_status qs_plan_profile(qs_plan p, int reps, double e, uint64_t seed, uint64_t
         cudaError_t x = f32 ? launch_precompute<float>(p, P, h->stream) : launch_precompute<double>(p, P, h->stream);
         cudaEventRecord(ev[k++], h->stream);
         kind[li++] = 0;
-        if (x == cudaSuccess) x = f32 ? launch_pass_kernel<float>(p, P, h->stream) : launch_pass_kernel<double>(p, P, h->stream);
+        if (x == cudaSuccess) x = f32 ? launch_pass_kernel<float>(p, P, h->stream, 0, 0) : launch_pass_kernel<double>(p, P, h->stream, 0, 0);
         cudaEventRecord(ev[k++], h->stream);
         kind[li++] = P.high ? 2 : 1;
         if (x != cudaSuccess) { result = pfail(p, QS_ERR_CUDA, cudaGetErrorString(x)); break; }
@@ -1229,12 +982,13 @@ qs_status qs_plan_info(qs_plan p, int* passes, int* launches) {
 qs_status qs_plan_destroy(qs_plan p) {
   if (!p) return QS_ERR_INVALID_ARG;
   if (p->h) cudaStreamSynchronize(p->h->stream);
-  if (p->exec) cudaGraphExecDestroy(p->exec);
+  for (auto& x : p->exec) if (x) cudaGraphExecDestroy(x);
   for (auto& P : p->passes) {
     void* ptrs[] = {P.d_ops, P.d_outs, P.d_prods, P.d_contribs, P.d_params};
     for (void* x : ptrs) if (x) cudaFree(x);
   }
   if (p->d_gates) cudaFree(p->d_gates);
+  if (p->d_fid) cudaFree(p->d_fid);
   if (p->d_run) cudaFree(p->d_run);
   if (p->h_run) cudaFreeHost(p->h_run);
   for (auto& e : p->events) cudaEventDestroy(e);

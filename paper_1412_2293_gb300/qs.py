@@ -71,6 +71,7 @@ _SIGS = {
     "qs_set_member_noise": ([_P, _D, _U64, _U64, _U64], ct.c_int),
     "qs_plan_create": ([_P, ct.POINTER(qs_gate), ct.c_int, ct.POINTER(_P)], ct.c_int),
     "qs_plan_run": ([_P, ct.c_double, ct.c_uint64, ct.c_uint64], ct.c_int),
+    "qs_plan_run_fidelity": ([_P, ct.c_double, ct.c_uint64, ct.c_uint64, _D], ct.c_int),
     "qs_plan_info": ([_P, _I, _I], ct.c_int),
     "qs_plan_profile": ([_P, ct.c_int, ct.c_double, ct.c_uint64, ct.c_uint64, _D, _I, ct.c_int, _I], ct.c_int),
     "qs_plan_destroy": ([_P], ct.c_int),
@@ -292,6 +293,13 @@ def qs_plan_create(h, gates):
 
 def qs_plan_run(p, e, seed, gate_id0=0, h=None):
     _check(lib().qs_plan_run(p, float(e), int(seed), int(gate_id0)), h)
+
+
+def qs_plan_run_fidelity(p, e, seed, gate_id0, h):
+    """Run the plan and return the members' fidelities with the stored reference."""
+    out = np.zeros(_results(h), dtype=np.float64)
+    _check(lib().qs_plan_run_fidelity(p, float(e), int(seed), int(gate_id0), _dptr(out)), h)
+    return out
 
 
 def qs_plan_info(p, h=None):

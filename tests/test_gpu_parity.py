@@ -182,6 +182,47 @@ def test_gate_by_gate_equals_plan(dtype):
         qs.qs_plan_destroy(p)
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n", [11, 14])
+def test_fused_fidelity_and_per_member_starts_match_oracle(dtype, n):
+    """The first pass creates per-member basis starts; the last pass reduces the fidelity."""
+    batch, e = 5, 0.03
+    ops = inputs.qft_circuit(n)
+    xs = [(37 * b + 5) % (1 << n) for b in range(batch)]
+    ideal0 = ocirc.ideal_state(n, ops, xs[0])
+    with Handle(n, batch, 0, qs.QS_STATEVEC, dtype) as h:
+        ref = np.asarray(ideal0)
+        qs.qs_set_reference(h, ref)
+        qs.qs_set_basis_states(h, xs)
+        p = qs.qs_plan_create(h, pcirc.to_gates(ops))
+        f_fused = qs.qs_plan_run_fidelity(p, e, SEED, 0, h)
+        got = qs.qs_get_state(h).reshape(batch, -1)
+        f_sep = qs.qs_fidelity_stored(h)
+        # run again from the same starts: replays the captured graph
+        qs.qs_set_basis_states(h, xs)
+        f_again = qs.qs_plan_run_fidelity(p, e, SEED, 0, h)
+        qs.qs_plan_destroy(p)
+    np.testing.assert_allclose(f_fused, f_sep, rtol=TOL[dtype], atol=TOL[dtype])
+    np.testing.assert_allclose(f_again, f_fused, rtol=0, atol=0)
+    for b in range(batch):
+        want = oracle_traj(n, ops, xs[b], e, b)
+        np.testing.assert_allclose(got[b], want, atol=TOL[dtype])
+        assert abs(f_fused[b] - osv.fidelity(ideal0, want)) <= TOL[dtype] * 10
+
+
+def test_lazy_start_state_is_written_before_other_consumers():
+    n = 10
+    with Handle(n, 2, 0, qs.QS_STATEVEC, qs.QS_C128) as h:
+        qs.qs_set_basis_state(h, 7)
+        st = qs.qs_get_state(h).reshape(2, -1)
+        assert st[:, 7].tolist() == [1, 1] and np.count_nonzero(st) == 2
+        qs.qs_set_basis_states(h, [3, 9])
+        qs.qs_apply_gate(h, (0,), ogates.hadamard())
+        st = qs.qs_get_state(h).reshape(2, -1)
+        np.testing.assert_allclose(st[0], osv.apply_gate(osv.basis_state(n, 3), n, (0,), ogates.hadamard()), atol=1e-15)
+        np.testing.assert_allclose(st[1], osv.apply_gate(osv.basis_state(n, 9), n, (0,), ogates.hadamard()), atol=1e-15)
+
+
 def test_plan_with_unfusable_gates_matches_oracle():
     rng = np.random.default_rng(9)
     n, batch, e = 11, 2, 0.03
