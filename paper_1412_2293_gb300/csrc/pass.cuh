@@ -32,10 +32,13 @@ constexpr int kAmps = 32;
 constexpr int kMaxOther = 48;
 constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr int kStatusTimeout = 0x51;       // value written to the status word on a timed-out wait
-constexpr int kMaxPassOps = 256;           // ops of one pass, held in the kernel parameters
+constexpr int kMaxPassOps = 256;           // ops of one pass before segmentation
+constexpr int kMaxSegs = 48;               // segments of one pass (kernel parameters)
+constexpr int kMaxFlips = 64;
 
 enum : uint8_t { OP_DENSE = 0, OP_DWIN = 1, OP_FLIP = 2, OP_FLIPM = 3, OP_EXCH = 4 };
 
+// One planner op (host side; the kernels see segments).
 struct FOp {
   uint8_t type;
   uint8_t j;          // local window bit (DENSE, DWIN)
@@ -43,6 +46,29 @@ struct FOp {
   uint8_t pad;
   uint32_t off;       // parameter offset (R units) in the member block
   uint64_t index;     // FLIP: member-local amplitude index
+};
+
+// A segment: gates of one register stage applied in a canonical order --
+// for each register bit rj, descending (desc = 1) or ascending, the dense
+// gate on rj (if in `dense`) then the phase table attached to rj (if in
+// `dwin`) -- followed by `nflip` flips.  The planner only forms a segment
+// when that order keeps every pair of non-commuting gates in circuit order.
+struct Seg {
+  uint8_t stage;      // 0 = A (registers = window bits 5..9), 1 = B (0..4)
+  uint8_t dense;
+  uint8_t dwin;
+  uint8_t real;
+  uint8_t desc;
+  uint8_t nflip;
+  uint16_t flip0;
+  uint32_t doff[kRegBits];
+  uint32_t woff[kRegBits];
+};
+
+struct Flip {
+  uint64_t index;     // member-local amplitude index
+  uint32_t per_member;  // 1: the member's marked index instead
+  uint32_t pad;
 };
 
 struct OutTerm {
@@ -55,8 +81,9 @@ struct PassArgs {
   int n;
   int start_stage;            // 0 = A, 1 = B
   int win[kWin];
-  int num_ops;
-  FOp ops[kMaxPassOps];       // the program (constant bank: uniform, cached)
+  int nseg;
+  Seg segs[kMaxSegs];         // the program (constant bank: uniform, cached)
+  Flip flips[kMaxFlips];
   int out_start[12];          // out terms grouped by attach a (0..9) and 10 = none
   const OutTerm* outs;
   int param_stride;           // R units per member
@@ -175,17 +202,6 @@ __device__ __forceinline__ void dense_reg(cplx<R> (&a)[kAmps], const R* m, bool 
   }
 }
 
-template <typename R>
-__device__ __forceinline__ void dense_dispatch(cplx<R> (&a)[kAmps], int rj, const R* m, bool real) {
-  switch (rj) {
-    case 0: dense_reg<R, 0>(a, m, real); break;
-    case 1: dense_reg<R, 1>(a, m, real); break;
-    case 2: dense_reg<R, 2>(a, m, real); break;
-    case 3: dense_reg<R, 3>(a, m, real); break;
-    default: dense_reg<R, 4>(a, m, real); break;
-  }
-}
-
 // Multiply registers with bit RJ set by T[idx]: stage A idx = tbits | (low
 // register bits << 5), stage B idx = the register bits below RJ.
 template <typename R, int RJ, bool STAGE_A>
@@ -200,27 +216,6 @@ __device__ __forceinline__ void dwin_reg(cplx<R> (&a)[kAmps], const R* T, int tb
 #pragma unroll
   for (int r = 0; r < kAmps; ++r)
     if (r & (1 << RJ)) a[r] = cmul(f[r & (Q - 1)], a[r]);
-}
-
-template <typename R>
-__device__ __forceinline__ void dwin_dispatch(cplx<R> (&a)[kAmps], int rj, bool stage_a, const R* T, int tbits) {
-  if (stage_a) {
-    switch (rj) {
-      case 0: dwin_reg<R, 0, true>(a, T, tbits); break;
-      case 1: dwin_reg<R, 1, true>(a, T, tbits); break;
-      case 2: dwin_reg<R, 2, true>(a, T, tbits); break;
-      case 3: dwin_reg<R, 3, true>(a, T, tbits); break;
-      default: dwin_reg<R, 4, true>(a, T, tbits); break;
-    }
-  } else {
-    switch (rj) {
-      case 0: dwin_reg<R, 0, false>(a, T, tbits); break;
-      case 1: dwin_reg<R, 1, false>(a, T, tbits); break;
-      case 2: dwin_reg<R, 2, false>(a, T, tbits); break;
-      case 3: dwin_reg<R, 3, false>(a, T, tbits); break;
-      default: dwin_reg<R, 4, false>(a, T, tbits); break;
-    }
-  }
 }
 
 template <typename R>
@@ -264,16 +259,44 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// ---------------------------------------------------------------- segments
+template <typename R, int J, bool SA>
+__device__ __forceinline__ void seg_step(cplx<R> (&a)[kAmps], const Seg& sg, const R* P, int tbits) {
+  if ((sg.dense >> J) & 1) dense_reg<R, J>(a, P + sg.doff[J], (sg.real >> J) & 1);
+  if ((sg.dwin >> J) & 1) dwin_reg<R, J, SA>(a, P + sg.woff[J], tbits);
+}
+
+template <typename R, bool SA>
+__device__ __forceinline__ void run_seg(cplx<R> (&a)[kAmps], const Seg& sg, const R* P, int tbits) {
+  if (sg.desc) {
+    seg_step<R, 4, SA>(a, sg, P, tbits);
+    seg_step<R, 3, SA>(a, sg, P, tbits);
+    seg_step<R, 2, SA>(a, sg, P, tbits);
+    seg_step<R, 1, SA>(a, sg, P, tbits);
+    seg_step<R, 0, SA>(a, sg, P, tbits);
+  } else {
+    seg_step<R, 0, SA>(a, sg, P, tbits);
+    seg_step<R, 1, SA>(a, sg, P, tbits);
+    seg_step<R, 2, SA>(a, sg, P, tbits);
+    seg_step<R, 3, SA>(a, sg, P, tbits);
+    seg_step<R, 4, SA>(a, sg, P, tbits);
+  }
+}
+
 // ---------------------------------------------------------------- LOW pass
 // Window = qubits 0..9.  Each warp streams a contiguous range of tiles of 1024
 // consecutive amplitudes (consecutive tiles mostly share a member, so its
-// parameters stay in L1): double-buffered bulk copies into shared memory, a
-// padded exchange buffer, coalesced stores from the stage-A layout.
+// parameters stay in L1) through two shared-memory buffers filled by bulk
+// copies.  Register exchanges happen in place in the current buffer with an
+// XOR swizzle, x -> x ^ ((x >> 5) & 15), under which both register layouts
+// (stage A: x = lane + 32 r, stage B: x = r + 32 lane) are free of bank
+// conflicts; stores are coalesced from the stage-A layout.
 template <int WARPS> struct LowShape {
-  static constexpr int XPAD = 1056;                    // 1024 + 32 padding
-  static constexpr int PER_WARP = 2 * 1024 + XPAD + 12;
+  static constexpr int PER_WARP = 2 * 1024 + 12;       // two tile buffers + out factors
   static constexpr int THREADS = WARPS * 32;
 };
+
+__device__ __forceinline__ int low_swz(int x) { return x ^ ((x >> 5) & 15); }
 
 template <typename R, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict__ psi, const __grid_constant__ PassArgs A) {
@@ -283,12 +306,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
   __shared__ __align__(8) uint64_t bars[WARPS][2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   C* wbase = reinterpret_cast<C*>(smem_raw) + (size_t)warp * S::PER_WARP;
-  C* xbuf = wbase + 2048;
-  C* alpha_sm = wbase + 2048 + S::XPAD;
+  C* alpha_sm = wbase + 2048;
   const uint64_t nmask = (1ull << A.n) - 1;
   const R* params = static_cast<const R*>(A.params);
   const uint32_t tile_bytes = 1024u * (uint32_t)sizeof(C);
-  // contiguous tile range of this warp
   const uint64_t nwarps = (uint64_t)gridDim.x * WARPS;
   const uint64_t gw = (uint64_t)blockIdx.x * WARPS + warp;
   const uint64_t per = (A.tiles + nwarps - 1) / nwarps;
@@ -337,33 +358,33 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
       for (int r = 0; r < kAmps; ++r) a[r] = cbuf[lane + 32 * r];
     }
     int stage = 0;
-    for (int i = 0; i < A.num_ops; ++i) {
-      const FOp op = A.ops[i];
-      if (op.type == OP_DENSE) {
-        dense_dispatch<R>(a, stage == 0 ? op.j - 5 : op.j, P + op.off, op.real);
-      } else if (op.type == OP_DWIN) {
-        dwin_dispatch<R>(a, stage == 0 ? op.j - 5 : op.j, stage == 0, P + op.off, lane);
-      } else if (op.type == OP_FLIP || op.type == OP_FLIPM) {
-        const uint64_t w = op.type == OP_FLIP ? op.index : A.marked[member];
+    for (int si = 0; si < A.nseg; ++si) {
+      const Seg& sg = A.segs[si];
+      if (sg.stage != stage) {
+        __syncwarp();
+        if (stage == 0) {
+#pragma unroll
+          for (int r = 0; r < kAmps; ++r) cbuf[low_swz(lane + 32 * r)] = a[r];
+          __syncwarp();
+#pragma unroll
+          for (int r = 0; r < kAmps; ++r) a[r] = cbuf[low_swz(r + 32 * lane)];
+        } else {
+#pragma unroll
+          for (int r = 0; r < kAmps; ++r) cbuf[low_swz(r + 32 * lane)] = a[r];
+          __syncwarp();
+#pragma unroll
+          for (int r = 0; r < kAmps; ++r) a[r] = cbuf[low_swz(lane + 32 * r)];
+        }
+        stage ^= 1;
+      }
+      if (stage == 0) run_seg<R, true>(a, sg, P, lane);
+      else run_seg<R, false>(a, sg, P, 0);
+      for (int f = 0; f < sg.nflip; ++f) {
+        const Flip fl = A.flips[sg.flip0 + f];
+        const uint64_t w = fl.per_member ? A.marked[member] : fl.index;
         const uint64_t fixed = mloc | (stage == 0 ? (uint64_t)lane : ((uint64_t)lane << 5));
         const uint64_t regmask = stage == 0 ? (31ull << 5) : 31ull;
         flip_reg<R>(a, (w & ~regmask) == fixed, stage == 0 ? (int)((w >> 5) & 31) : (int)(w & 31));
-      } else {
-        if (stage == 0) {
-#pragma unroll
-          for (int r = 0; r < kAmps; ++r) xbuf[lane + 33 * r] = a[r];
-          __syncwarp();
-#pragma unroll
-          for (int r = 0; r < kAmps; ++r) a[r] = xbuf[r + 33 * lane];
-        } else {
-#pragma unroll
-          for (int r = 0; r < kAmps; ++r) xbuf[r + 33 * lane] = a[r];
-          __syncwarp();
-#pragma unroll
-          for (int r = 0; r < kAmps; ++r) a[r] = xbuf[lane + 33 * r];
-        }
-        __syncwarp();
-        stage ^= 1;
       }
     }
     if (A.out_start[11] > 0) {
@@ -377,15 +398,14 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
         if ((lane >> r) & 1) c = cmul(c, alpha_sm[stage == 0 ? r : r + 5]);
       }
       apply_reg_product<R>(a, c, al);
-      __syncwarp();
     }
     if (stage == 1) {
-#pragma unroll
-      for (int r = 0; r < kAmps; ++r) xbuf[r + 33 * lane] = a[r];
       __syncwarp();
 #pragma unroll
-      for (int r = 0; r < kAmps; ++r) a[r] = xbuf[lane + 33 * r];
+      for (int r = 0; r < kAmps; ++r) cbuf[low_swz(r + 32 * lane)] = a[r];
       __syncwarp();
+#pragma unroll
+      for (int r = 0; r < kAmps; ++r) a[r] = cbuf[low_swz(lane + 32 * r)];
     }
     if (A.fid) {
       const C* ref = static_cast<const C*>(A.ref) + mloc;
@@ -416,7 +436,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
 // window rows, each loaded as four 256-row boxes of a 2D tensor map
 // [members * 1024 rows][2^(n-10) columns].  The window bits are contiguous,
 // so register r of stage A sits at offset r << win[5] and of stage B at
-// r << win[0].
+// r << win[0].  With 8 columns the in-place exchange swizzles element
+// x * 8 + col by flipping bit 3 with bit 5 of x (conflict-free both ways).
 template <int COLB> struct HighShape {
   static constexpr int COLS = 1 << COLB;
   static constexpr int LW = kRegBits - COLB;            // lane bits that are window bits
@@ -424,6 +445,13 @@ template <int COLB> struct HighShape {
   static constexpr int THREADS = WARPS * 32;
   static constexpr int TILE = COLS * 1024;
 };
+
+template <int COLB>
+__device__ __forceinline__ int high_idx(int x, int col) {
+  const int e = x * (1 << COLB) + col;
+  if constexpr (COLB == 3) return e ^ (((x >> 5) & 1) << 3);
+  else return e;
+}
 
 template <typename R, int COLB>
 __global__ void __launch_bounds__(HighShape<COLB>::THREADS, 1)
@@ -498,6 +526,7 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, 1)
         return;
       }
       if (threadIdx.x == 0) --in_flight;
+      // the copy lands in the plain layout [x][col]
       if (stage == 0) {
 #pragma unroll
         for (int r = 0; r < kAmps; ++r) a[r] = sm[(xa | (r << 5)) * S::COLS + col];
@@ -506,34 +535,34 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, 1)
         for (int r = 0; r < kAmps; ++r) a[r] = sm[(r | xb) * S::COLS + col];
       }
     }
-    for (int i = 0; i < A.num_ops; ++i) {
-      const FOp op = A.ops[i];
-      if (op.type == OP_DENSE) {
-        dense_dispatch<R>(a, stage == 0 ? op.j - 5 : op.j, P + op.off, op.real);
-      } else if (op.type == OP_DWIN) {
-        dwin_dispatch<R>(a, stage == 0 ? op.j - 5 : op.j, stage == 0, P + op.off, xa);
-      } else if (op.type == OP_FLIP || op.type == OP_FLIPM) {
-        const uint64_t w = op.type == OP_FLIP ? op.index : A.marked[member];
+    for (int si = 0; si < A.nseg; ++si) {
+      const Seg& sg = A.segs[si];
+      if (sg.stage != stage) {
+        __syncthreads();
+        if (stage == 0) {
+#pragma unroll
+          for (int r = 0; r < kAmps; ++r) sm[high_idx<COLB>(xa | (r << 5), col)] = a[r];
+          __syncthreads();
+#pragma unroll
+          for (int r = 0; r < kAmps; ++r) a[r] = sm[high_idx<COLB>(r | xb, col)];
+        } else {
+#pragma unroll
+          for (int r = 0; r < kAmps; ++r) sm[high_idx<COLB>(r | xb, col)] = a[r];
+          __syncthreads();
+#pragma unroll
+          for (int r = 0; r < kAmps; ++r) a[r] = sm[high_idx<COLB>(xa | (r << 5), col)];
+        }
+        stage ^= 1;
+      }
+      if (stage == 0) run_seg<R, true>(a, sg, P, xa);
+      else run_seg<R, false>(a, sg, P, 0);
+      for (int f = 0; f < sg.nflip; ++f) {
+        const Flip fl = A.flips[sg.flip0 + f];
+        const uint64_t w = fl.per_member ? A.marked[member] : fl.index;
         const int sh = stage == 0 ? sha : shb;
         const uint64_t regmask = 31ull << sh;
         const uint64_t fixed = tbits | (uint32_t)col | (stage == 0 ? offa : offb);
         flip_reg<R>(a, (w & ~regmask) == fixed, (int)((w >> sh) & 31));
-      } else {
-        __syncthreads();
-        if (stage == 0) {
-#pragma unroll
-          for (int r = 0; r < kAmps; ++r) sm[(xa | (r << 5)) * S::COLS + col] = a[r];
-          __syncthreads();
-#pragma unroll
-          for (int r = 0; r < kAmps; ++r) a[r] = sm[(r | xb) * S::COLS + col];
-        } else {
-#pragma unroll
-          for (int r = 0; r < kAmps; ++r) sm[(r | xb) * S::COLS + col] = a[r];
-          __syncthreads();
-#pragma unroll
-          for (int r = 0; r < kAmps; ++r) a[r] = sm[(xa | (r << 5)) * S::COLS + col];
-        }
-        stage ^= 1;
       }
     }
     if (A.out_start[11] > 0) {

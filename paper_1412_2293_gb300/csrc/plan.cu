@@ -239,6 +239,8 @@ struct PassPlan {
   int stride = 0;                 // R units per member
   std::vector<int> other;
   int tile_shift = 0;             // log2(tiles per member)
+  std::vector<Seg> segs;          // the ops in canonical segments (what the kernels run)
+  std::vector<Flip> flips;
   CUtensorMap tmap;               // HIGH: [members * 1024 rows][2^(n-10) columns]
   // device copies
   FOp* d_ops = nullptr;
@@ -324,8 +326,8 @@ bool commute(const PGate& a, const PGate& b) {
 int stage_of(int j) { return j >= 5 ? 0 : 1; }
 
 // Greedy pass builder starting at remaining[0]; returns absorbed flags.
-bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n, int colb, PassPlan* P,
-                std::vector<char>* absorbed) {
+bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n, int colb, size_t op_budget,
+                PassPlan* P, std::vector<char>* absorbed) {
   P->colb = colb;
   // window from the first fusable dense gate (lookahead)
   int q = -1;
@@ -363,7 +365,7 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
     if (!g.dense1 && !g.cp && !g.flip) break;           // a gate the pass cannot hold ends the scan
     // bounds of one pass: precompute shared memory and the per-member block
     if (ncontrib >= kMaxContribs || dwins.size() >= kMaxDwin || table_entries >= kMaxTableEntries ||
-        out_gates.size() >= kMaxOut || P->ops.size() + 2 > kMaxOps)
+        out_gates.size() >= kMaxOut || P->ops.size() + 2 > op_budget)
       break;
     bool ok = true;
     for (int s : skipped) if (!commute(G[s], g)) { ok = false; break; }
@@ -513,6 +515,98 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
   return true;
 }
 
+// Group a pass's ops into segments (see Seg).  Returns false when they do
+// not fit the kernel-parameter limits.
+bool segment_pass(PassPlan* P) {
+  // partner masks of the phase tables, in op order
+  std::vector<uint32_t> partners;
+  for (const Producer& pr : P->prods) {
+    if (pr.kind != PD_DWIN) continue;
+    uint32_t m = 0;
+    for (int c = pr.contrib_start; c < pr.contrib_start + pr.contrib_count; ++c) m |= 1u << P->contribs[c].m;
+    partners.push_back(m);
+  }
+  struct Item { int type; int j; uint32_t partners; const FOp* op; };
+  std::vector<Item> cur;
+  int cur_stage = 0;
+  bool open = false;
+  P->segs.clear();
+  P->flips.clear();
+  auto order_ok = [&](const std::vector<Item>& items, bool desc) {
+    auto pos = [&](const Item& it) {
+      const int rj = cur_stage == 0 ? it.j - 5 : it.j;
+      const int idx = desc ? 4 - rj : rj;
+      return 2 * idx + (it.type == OP_DWIN ? 1 : 0);
+    };
+    for (size_t x = 0; x < items.size(); ++x)
+      for (size_t y = x + 1; y < items.size(); ++y) {
+        const Item& a = items[x];
+        const Item& b = items[y];
+        bool commute = true;
+        if (a.type == OP_DENSE && b.type == OP_DENSE) commute = a.j != b.j;
+        else if (a.type == OP_DENSE && b.type == OP_DWIN) commute = a.j != b.j && !((b.partners >> a.j) & 1);
+        else if (a.type == OP_DWIN && b.type == OP_DENSE) commute = a.j != b.j && !((a.partners >> b.j) & 1);
+        if (!commute && pos(a) >= pos(b)) return false;
+      }
+    return true;
+  };
+  std::vector<FOp> pending_flips;
+  auto close = [&]() {
+    if (!open) return;
+    Seg sg{};
+    sg.stage = (uint8_t)cur_stage;
+    sg.desc = order_ok(cur, true) ? 1 : 0;
+    for (const Item& it : cur) {
+      const int rj = cur_stage == 0 ? it.j - 5 : it.j;
+      if (it.type == OP_DENSE) {
+        sg.dense |= 1u << rj;
+        sg.doff[rj] = it.op->off;
+        if (it.op->real) sg.real |= 1u << rj;
+      } else {
+        sg.dwin |= 1u << rj;
+        sg.woff[rj] = it.op->off;
+      }
+    }
+    sg.flip0 = (uint16_t)P->flips.size();
+    sg.nflip = (uint8_t)pending_flips.size();
+    for (const FOp& f : pending_flips) {
+      Flip fl{};
+      fl.index = f.index;
+      fl.per_member = f.type == OP_FLIPM ? 1 : 0;
+      P->flips.push_back(fl);
+    }
+    P->segs.push_back(sg);
+    cur.clear();
+    pending_flips.clear();
+    open = false;
+  };
+  int stage = P->high ? P->start_stage : 0;
+  size_t dw = 0;
+  for (const FOp& op : P->ops) {
+    if (op.type == OP_EXCH) { close(); stage ^= 1; continue; }
+    if (op.type == OP_FLIP || op.type == OP_FLIPM) {
+      if (!open) { open = true; cur_stage = stage; }
+      pending_flips.push_back(op);
+      close();                                          // nothing dense may follow a flip in a segment
+      continue;
+    }
+    Item it{op.type, op.j, op.type == OP_DWIN ? partners[dw++] : 0u, &op};
+    bool fits = open && cur_stage == stage;
+    if (fits)
+      for (const Item& x : cur)
+        if (x.type == it.type && x.j == it.j) fits = false;          // one of each per register bit
+    if (fits) {
+      std::vector<Item> trial = cur;
+      trial.push_back(it);
+      fits = order_ok(trial, true) || order_ok(trial, false);
+    }
+    if (!fits) { close(); open = true; cur_stage = stage; }
+    cur.push_back(it);
+  }
+  close();
+  return P->segs.size() <= (size_t)kMaxSegs && P->flips.size() <= (size_t)kMaxFlips;
+}
+
 template <typename T>
 qs_status upload(qs_plan p, T** dst, const std::vector<T>& v) {
   if (v.empty()) { *dst = nullptr; return QS_OK; }
@@ -522,7 +616,7 @@ qs_status upload(qs_plan p, T** dst, const std::vector<T>& v) {
   return QS_OK;
 }
 
-constexpr int kLowWarpsF = 8;   // complex64: 8 warps per block
+constexpr int kLowWarpsF = 12;  // complex64: 12 warps per block (registers <= 170)
 constexpr int kLowWarpsD = 4;   // complex128: 4 warps (same shared memory)
 
 template <typename R> constexpr int low_warps() { return sizeof(R) == 4 ? kLowWarpsF : kLowWarpsD; }
@@ -568,8 +662,9 @@ PassArgs pass_args(qs_plan p, const PassPlan& P, int synth, int fid) {
   A.n = h->n;
   A.start_stage = P.start_stage;
   for (int l = 0; l < kWin; ++l) A.win[l] = P.win[l];
-  A.num_ops = (int)P.ops.size();
-  for (int i = 0; i < A.num_ops; ++i) A.ops[i] = P.ops[i];
+  A.nseg = (int)P.segs.size();
+  for (int i = 0; i < A.nseg; ++i) A.segs[i] = P.segs[i];
+  for (size_t i = 0; i < P.flips.size(); ++i) A.flips[i] = P.flips[i];
   for (int i = 0; i < 12; ++i) A.out_start[i] = P.out_start[i];
   A.outs = P.d_outs;
   A.param_stride = P.stride;
@@ -813,7 +908,14 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
     if (fuse) {
       PassPlan P;
       std::vector<char> absorbed(rem.size(), 0);
-      if (build_pass(p->gates, rem, h->n, p->colb, &P, &absorbed)) {
+      bool built = false;
+      for (size_t budget = kMaxOps; budget >= 4 && !built; budget /= 2) {
+        P = PassPlan();
+        std::fill(absorbed.begin(), absorbed.end(), 0);
+        if (!build_pass(p->gates, rem, h->n, p->colb, budget, &P, &absorbed)) break;
+        built = segment_pass(&P);
+      }
+      if (built) {
         bool any = false;
         for (char c : absorbed) any |= c != 0;
         if (any) {

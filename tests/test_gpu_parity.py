@@ -223,6 +223,43 @@ def test_lazy_start_state_is_written_before_other_consumers():
         np.testing.assert_allclose(st[1], osv.apply_gate(osv.basis_state(n, 9), n, (0,), ogates.hadamard()), atol=1e-15)
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n,seed", [(10, 1), (13, 2), (14, 3), (16, 4)])
+def test_random_circuits_through_the_planner_match_oracle(dtype, n, seed):
+    """Random noisy H / controlled phases / flips: windows, segments and the
+    commutation checks of the planner against the plain gate-by-gate oracle."""
+    rng = np.random.default_rng(seed)
+    ops = []
+    for _ in range(120):
+        r = rng.random()
+        if r < 0.45:
+            ops.append(inputs.Op("H", (int(rng.integers(n)),), noisy=bool(rng.random() < 0.8)))
+        elif r < 0.93:
+            j, k = rng.choice(n, size=2, replace=False)
+            ops.append(inputs.Op("CP", (int(j), int(k)), theta=float(rng.uniform(0, 6)), noisy=bool(rng.random() < 0.8)))
+        else:
+            ops.append(inputs.Op("FLIP", index=int(rng.integers(1 << n))))
+    batch, e, x0 = 3, 0.07, int(rng.integers(1 << n))
+    with Handle(n, batch, 0, qs.QS_STATEVEC, dtype) as h:
+        qs.qs_set_basis_state(h, x0)
+        p = qs.qs_plan_create(h, pcirc.to_gates(ops))
+        qs.qs_plan_run(p, e, SEED, 11, h)
+        qs.qs_plan_destroy(p)
+        got = qs.qs_get_state(h).reshape(batch, -1)
+    for b in range(batch):
+        psi = osv.basis_state(n, x0)
+        for g, op in enumerate(ops):
+            if op.kind == "FLIP":
+                psi = osv.phase_flip(psi, op.index)
+                continue
+            U = ocirc.op_unitary(op)
+            if op.noisy:
+                xa, xb = ophilox.normal_pair(SEED, b, 11 + g)
+                U = ogates.noisy_unitary(U, ocirc.op_noise(op), e, xa, xb)
+            psi = osv.apply_gate(psi, n, ocirc.op_targets(op), U)
+        np.testing.assert_allclose(got[b], psi, atol=TOL[dtype] * (10 if dtype == qs.QS_C64 else 1))
+
+
 def test_plan_with_unfusable_gates_matches_oracle():
     rng = np.random.default_rng(9)
     n, batch, e = 11, 2, 0.03
