@@ -281,23 +281,146 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": args.steps * (launches + 1),
         "roofline": roofline,
     }
+    if not args.no_extras:
+        result["rows"] = extra_rows(h, n, T, esize, stream, peaks)
     qs.qs_plan_destroy(p)
     qs.qs_destroy(h)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(W, ops, x0)
+        result["cpu_baseline"] = cpu_baseline(W, ops, x0, fid[0])
     if dist is not None:
         dist.destroy_process_group()
     return result
 
 
-def cpu_baseline(W, ops, x0):
-    """The oracle as it stands, on the host: one whole trajectory of the workload."""
+def cpu_baseline(W, ops, x0, gpu_fid0):
+    """The oracle as it stands, on the host: one whole trajectory of the workload.
+
+    The same trajectory (counter 0) was run on the GPU in complex64; the
+    difference of the two fidelities is the error of the GPU result against
+    the FP64 oracle."""
     from oracle import circuits as ocirc
+    from oracle import statevec as osv
     t0 = time.perf_counter()
-    ocirc.run_trajectory(W.n, ops, x0, W.e, W.seed, 0)
+    psi = ocirc.run_trajectory(W.n, ops, x0, W.e, W.seed, 0)
     dt = time.perf_counter() - t0
+    f0 = osv.fidelity(ocirc.ideal_state(W.n, ops, x0), psi)
     return {"value": (1 << W.n) * len(ops) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"1 of {W.trajectories} trajectories of {W.name} (complex128 NumPy, single thread), {dt:.1f} s"}
+            "sample": f"1 of {W.trajectories} trajectories of {W.name} (complex128 NumPy, single thread), {dt:.1f} s",
+            "fidelity_oracle": f0, "fidelity_gpu": float(gpu_fid0), "fidelity_abs_error": abs(f0 - float(gpu_fid0))}
+
+
+def extra_rows(h, n, T, esize, stream, peaks):
+    """Bounded measurements of the other hot-path rows (a few seconds each)."""
+    import numpy as np
+    import torch
+
+    from paper_1412_2293_gb300 import circuits as pcirc
+    from paper_1412_2293_gb300 import inputs, qs
+
+    out = {}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    # a1: single-gate pair sweep over the whole batched state (one HBM read + write per gate)
+    Hm = pcirc.hadamard()
+    for t in (0, 7, 19):
+        qs.qs_apply_gate(h, (t,), Hm)
+    e0, e1 = ev(), ev()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    targets = [0, 3, 7, 12, 19, 5, 16, 9]
+    for t in targets:
+        qs.qs_apply_gate(h, (t,), Hm)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / len(targets)
+    gbs = 2 * T * (1 << n) * esize / (ms / 1e3) / 1e9
+    out["a1_pair_sweep"] = {"kernel": "k_apply_1q", "state_bytes": T * (1 << n) * esize, "ms_per_gate": round(ms, 4),
+                            "achieved_GBps": round(gbs, 1), "frac_of_measured_hbm": round(gbs / peaks["hbm_gbs"], 4),
+                            "targets": targets}
+
+    # plain FP64 one trajectory per launch sequence vs batched complex64 (Grover n = 10)
+    W1 = inputs.WORKLOADS["mc_grover_n10_c128"]
+    ops1, x1 = W1.ops(), W1.initial_basis()
+    marked = inputs.draw_marked(W1.n, W1.seed)
+    hp = qs.qs_create(W1.n, 1, 0, qs.QS_STATEVEC, qs.QS_C128, stream)
+    plain_f = []
+    reps = 3
+    t0 = time.perf_counter()
+    for b in range(reps):
+        qs.qs_set_trajectory_offset(hp, b)
+        qs.qs_set_basis_state(hp, x1)
+        pcirc.apply_ops(hp, ops1, W1.e, W1.seed)
+        plain_f.append(float(qs.qs_fidelity(hp, None, marked)[0]))
+    dt_plain = (time.perf_counter() - t0) / reps
+    qs.qs_destroy(hp)
+    hb = qs.qs_create(W1.n, 1024, 0, qs.QS_STATEVEC, qs.QS_C64, stream)
+    pb = qs.qs_plan_create(hb, pcirc.to_gates(ops1))
+    qs.qs_set_basis_state(hb, x1)
+    qs.qs_plan_run(pb, W1.e, W1.seed, 0, hb)
+    qs.qs_synchronize(hb)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        qs.qs_set_basis_state(hb, x1)
+        qs.qs_plan_run(pb, W1.e, W1.seed, 0, hb)
+        fb = qs.qs_fidelity(hb, None, marked)
+    dt_batch = (time.perf_counter() - t0) / reps
+    passes, _ = qs.qs_plan_info(pb, hb)
+    qs.qs_plan_destroy(pb)
+    qs.qs_destroy(hb)
+    err = max(abs(fb[b] - plain_f[b]) for b in range(reps))
+    out["plain_vs_batched_grover_n10"] = {
+        "plain_c128_gate_by_gate_circuits_per_s": round(1.0 / dt_plain, 2),
+        "batched_c64_fused_circuits_per_s": round(1024 / dt_batch, 1),
+        "speedup": round((1024 / dt_batch) * dt_plain, 1), "fused_passes": passes,
+        "success_prob_max_abs_diff_c64_vs_c128": err, "gates": len(ops1)}
+
+    # a6: exact density matrix of the noisy QFT, n = 14 (2^28 complex128 entries)
+    W4 = inputs.WORKLOADS["dm_qft_n14"]
+    ops4, x4 = W4.ops(), W4.initial_basis()
+    hd = qs.qs_create(W4.n, 1, 0, qs.QS_DENSITY, qs.QS_C128, stream)
+    qs.qs_set_basis_state(hd, x4)
+    pcirc.apply_ops(hd, ops4[:3], W4.e, W4.seed)
+    qs.qs_synchronize(hd)
+    qs.qs_set_basis_state(hd, x4)
+    e0, e1 = ev(), ev()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    pcirc.apply_ops(hd, ops4, W4.e, W4.seed)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_dm = e0.elapsed_time(e1)
+    tr = float(qs.qs_trace(hd)[0])
+    qs.qs_destroy(hd)
+    out["a6_density_qft_n14"] = {"ms_per_circuit": round(ms_dm, 2), "channels": len(ops4),
+                                 "entries": 1 << (2 * W4.n), "trace": tr,
+                                 "updates_per_s": (1 << (2 * W4.n)) * len(ops4) / (ms_dm / 1e3)}
+
+    # a7: fixed-rank Grover n = 16, r = 8: a bounded run of channels, extrapolated
+    W3 = inputs.WORKLOADS["rank_grover_n16"]
+    ops3 = W3.ops()
+    nch = 160
+    hr = qs.qs_create(W3.n, 1, W3.rank, qs.QS_FIXED_RANK, qs.QS_C128, stream)
+    qs.qs_set_basis_state(hr, 0)
+    pcirc.apply_ops(hr, ops3[:40], W3.e, W3.seed)
+    qs.qs_synchronize(hr)
+    sub = ops3[40:40 + nch]
+    e0, e1 = ev(), ev()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    pcirc.apply_ops(hr, sub, W3.e, W3.seed, gate_id0=40)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_r = e0.elapsed_time(e1)
+    noisy = sum(1 for o in sub if o.noisy)
+    per_ch = ms_r / max(noisy, 1)
+    total_noisy = sum(1 for o in ops3 if o.noisy)
+    qs.qs_destroy(hr)
+    out["a7_fixed_rank_grover_n16_r8"] = {
+        "ms_per_channel": round(per_ch, 4), "channels_timed": noisy,
+        "circuit_channels": total_noisy,
+        "circuits_per_s_extrapolated": round(1e3 / (per_ch * total_noisy), 4),
+        "note": "time of a bounded run of channels (expand, FP64 Gram, FP64 Jacobi, projection) x channels"}
+    return out
 
 
 # ------------------------------------------------------------------ reference arm
@@ -360,6 +483,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="mc_qft_n20_c64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the bounded measurements of the other rows")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -45,7 +45,9 @@ def to_gates(ops: List[Op], per_member_flip: bool = False):
 
 
 def apply_ops(h, ops: List[Op], e: float, seed: int, gate_id0: int = 0):
-    """Issue a circuit gate by gate through the single-gate entry points."""
+    """Issue a circuit gate by gate through the single-gate entry points.
+
+    Gate g of the list draws its noise with gate id gate_id0 + g."""
     for g, op in enumerate(ops):
         if op.kind == "FLIP":
             qs.qs_apply_phase_flip(h, op.index)

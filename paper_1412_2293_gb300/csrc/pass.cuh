@@ -148,22 +148,12 @@ __device__ __forceinline__ void report_timeout(int* status) {
 }
 
 // ---------------------------------------------------------------- arithmetic
+// One complex parameter (8- or 16-byte aligned): a single vector load.
 template <typename R>
-__device__ __forceinline__ cplx<R> ld_c(const R* p) { return mk<R>(p[0], p[1]); }
+__device__ __forceinline__ cplx<R> ld_c(const R* p) { return __ldg(reinterpret_cast<const cplx<R>*>(p)); }
 
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
-  uint64_t d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d)
-      : "l"(*reinterpret_cast<uint64_t*>(&a)), "l"(*reinterpret_cast<uint64_t*>(&b)));
-  return *reinterpret_cast<float2*>(&d);
-}
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-  uint64_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d)
-      : "l"(*reinterpret_cast<uint64_t*>(&a)), "l"(*reinterpret_cast<uint64_t*>(&b)),
-        "l"(*reinterpret_cast<uint64_t*>(&c)));
-  return *reinterpret_cast<float2*>(&d);
-}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 // Real 2x2 on a complex pair: both components scaled by the same real entry,
 // so complex64 uses the packed two-lane FP32 FMA (one instruction per output
@@ -184,7 +174,14 @@ __device__ __forceinline__ void butterfly_real(cplx<R>& x0, cplx<R>& x1, R u00, 
 template <typename R, int RJ>
 __device__ __forceinline__ void dense_reg(cplx<R> (&a)[kAmps], const R* m, bool real) {
   if (real) {
-    const R u00 = m[0], u01 = m[2], u10 = m[4], u11 = m[6];
+    R u00, u01, u10, u11;
+    if constexpr (sizeof(R) == 4) {                     // the 2x2 block is 32-byte aligned
+      const float4 r0 = __ldg(reinterpret_cast<const float4*>(m));
+      const float4 r1 = __ldg(reinterpret_cast<const float4*>(m) + 1);
+      u00 = r0.x; u01 = r0.z; u10 = r1.x; u11 = r1.z;
+    } else {
+      u00 = __ldg(m); u01 = __ldg(m + 2); u10 = __ldg(m + 4); u11 = __ldg(m + 6);
+    }
 #pragma unroll
     for (int r = 0; r < kAmps; ++r) {
       if (r & (1 << RJ)) continue;
@@ -412,7 +409,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
       R re = 0, im = 0;
 #pragma unroll
       for (int r = 0; r < kAmps; ++r) {
-        const C f = ref[lane + 32 * r];
+        const C f = __ldcg(ref + lane + 32 * r);
         re += f.x * a[r].x + f.y * a[r].y;
         im += f.x * a[r].y - f.y * a[r].x;
       }
@@ -591,7 +588,7 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, 1)
       R re = 0, im = 0;
 #pragma unroll
       for (int r = 0; r < kAmps; ++r) {
-        const C f = ref[(uint32_t)r << sh];
+        const C f = __ldcg(ref + ((uint32_t)r << sh));
         re += f.x * a[r].x + f.y * a[r].y;
         im += f.x * a[r].y - f.y * a[r].x;
       }
