@@ -423,6 +423,91 @@ def extra_rows(h, n, T, esize, stream, peaks):
     return out
 
 
+# ------------------------------------------------------------------ density / fixed rank
+
+
+def run_channels(args, rank, world, local_rank):
+    """Exact density matrix or fixed-rank workload: one step = the whole circuit
+    (every noisy gate replaced by its xi-averaged Kraus channel) + the fidelity."""
+    import numpy as np
+    import torch
+
+    from paper_1412_2293_gb300 import build as qbuild
+    from paper_1412_2293_gb300 import circuits as pcirc
+    from paper_1412_2293_gb300 import qs
+
+    torch.cuda.set_device(local_rank)
+    qbuild.build()
+    W, ops, x0 = workload_setup(args.workload)
+    n = W.n
+    mode = qs.QS_DENSITY if W.mode == "density" else qs.QS_FIXED_RANK
+    stream = torch.cuda.Stream()
+    h = qs.qs_create(n, 1, W.rank, mode, qs.QS_C128, stream)
+    ref = pcirc.ideal_reference(n, ops, x0, qs.QS_C128, stream)
+    qs.qs_set_reference_from(h, ref, 0)
+    qs.qs_destroy(ref)
+    channels = sum(1 for o in ops if o.noisy)
+    entries = (1 << (2 * n)) if mode == qs.QS_DENSITY else (1 << n) * W.rank
+    updates_per_step = entries * len(ops)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    per_kind = {}
+
+    def step(timed):
+        qs.qs_set_basis_state(h, x0)
+        for g, op in enumerate(ops):
+            if timed:
+                a, b = ev(), ev()
+                a.record(stream)
+            pcirc.apply_ops(h, [op], W.e, W.seed, gate_id0=g)
+            if timed:
+                b.record(stream)
+                kind = "flip" if op.kind == "FLIP" else (op.kind + ("_channel" if op.noisy else "_gate"))
+                per_kind.setdefault(kind, []).append((a, b))
+        return qs.qs_fidelity_stored(h)
+
+    for _ in range(args.warmup):
+        f = step(False)
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    for _ in range(args.steps):
+        f = step(True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    kinds = {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in per_kind.items()}
+    if mode == qs.QS_DENSITY:
+        # superoperator of a noisy H: a real 4x4 matrix (l1 H (x) H + l2 HJ (x) HJ) on 2^(2n)
+        # entries; algorithmic FP64 work 4 real-by-complex multiply-adds (16 flop) per entry
+        dom = "H_channel"
+        flop = (1 << (2 * n)) * 16
+        bytes_ = 2 * (1 << (2 * n)) * 16
+    else:
+        dom = "H_channel"
+        M = 2 * W.rank
+        # Gram (M(M+1)/2 pairs) + projection (M x r), complex FP64 multiply-adds over 2^n rows
+        flop = (1 << n) * (M * (M + 1) // 2 + M * W.rank) * 8
+        bytes_ = 3 * (1 << n) * W.rank * 16
+    avg = kinds.get(dom, ms)
+    achieved = flop / (avg / 1e3) / 1e12
+    fp64_peak, _ = qs.qs_measure_peaks()
+    out = {"metric": METRIC, "value": updates_per_step / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "mode": W.mode, "circuit": W.circuit, "n": n, "rank": W.rank,
+                      "channels": channels, "gates": len(ops), "e": W.e, "circuits_per_s": 1e3 / ms,
+                      "fidelity": float(f[0]), "trace": float(qs.qs_trace(h)[0])},
+           "gpu_launches": None,
+           "roofline": {"bound": "alu", "achieved": round(achieved, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+                        "frac": round(achieved / fp64_peak, 4), "traffic": None,
+                        "kernel": "noisy-H channel (all its launches)", "avg_launch_ms": round(avg, 4),
+                        "algorithmic_flop_per_launch": flop, "algorithmic_bytes_per_launch": bytes_,
+                        "peak_source": "FP64 FMA rate measured live (qs_measure_peaks)",
+                        "launch_ms_by_kind": {k: round(v, 4) for k, v in kinds.items()}}}
+    qs.qs_destroy(h)
+    return out
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, rank, world):
     """The oracle on the host cores, each step a slice of one trajectory's gates."""
@@ -488,8 +573,12 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     rank, world, local_rank = env_rank()
+    from paper_1412_2293_gb300 import inputs
+    mode = inputs.WORKLOADS[args.workload].mode
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif mode != "statevec":
+        out = run_channels(args, rank, world, local_rank) if rank == 0 else None
     else:
         out = run_ours(args, rank, world, local_rank)
     if rank == 0 and out is not None:

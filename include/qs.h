@@ -284,6 +284,11 @@ qs_status qs_debug_noise(uint64_t seed, uint64_t traj, uint64_t gate_id, int cou
 qs_status qs_fidelity_noalloc(const void* states, const void* ref, int n, int members, qs_dtype dtype,
                               void* cuda_stream, double* out);
 
+/* Measured FP64 and FP32 multiply-add rates of the current device (TFLOP/s),
+ * from dependent FMA chains on every SM (the denominators of the rooflines of
+ * arithmetic-bound kernels).  Synchronises the device. */
+qs_status qs_measure_peaks(double* fp64_tflops, double* fp32_tflops);
+
 /* Library version string. */
 const char* qs_version(void);
 

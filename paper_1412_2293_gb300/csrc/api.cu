@@ -185,7 +185,9 @@ qs_status apply_uniform(qs_handle h, void* psi, int n, int members, const int* t
   }
   qs_status st = upload_mat(h, U);
   if (st != QS_OK) return st;
-  QS_CUDA(h, qs::launch_apply_kq(h, psi, n, members, tg, h->mats, false));
+  bool real = true;
+  for (const auto& v : U) if (v.imag() != 0.0) real = false;
+  QS_CUDA(h, qs::launch_apply_kq(h, psi, n, members, tg, h->mats, false, real));
   return QS_OK;
 }
 
@@ -681,6 +683,11 @@ qs_status qs_set_member_noise(qs_handle h, const double* e, const uint64_t* seed
   // the host arrays are consumed by the time the stream reaches the copies
   QS_CUDA(h, cudaStreamSynchronize(h->stream));
   return QS_OK;
+}
+
+qs_status qs_measure_peaks(double* fp64_tflops, double* fp32_tflops) {
+  if (!fp64_tflops || !fp32_tflops) return QS_ERR_INVALID_ARG;
+  return qs::measure_fma_rates(fp64_tflops, fp32_tflops) == cudaSuccess ? QS_OK : QS_ERR_CUDA;
 }
 
 qs_status qs_debug_noise(uint64_t seed, uint64_t traj, uint64_t gate_id, int count, uint32_t* words,

@@ -132,7 +132,7 @@ cudaError_t launch_noise_mats(qs_ctx* h, void* mats, int members, int k, const d
 cudaError_t launch_apply_1q(qs_ctx* h, void* psi, int n, int members, int t,
                             const double* U, const void* mats_dev);
 cudaError_t launch_apply_kq(qs_ctx* h, void* psi, int n, int members, const Targets& tg,
-                            const void* mat_dev, bool per_member);
+                            const void* mat_dev, bool per_member, bool real = false);
 cudaError_t launch_apply_diag(qs_ctx* h, void* psi, int n, int members, const Targets& tg,
                               const void* diag_dev, bool per_member, uint32_t active_mask);
 cudaError_t launch_phase_flip(qs_ctx* h, void* psi, int n, int members, uint64_t index,
@@ -179,6 +179,7 @@ qs_status materialize_basis(qs_ctx* h);
 qs_status read_results(qs_ctx* h, double* out, int count);
 
 // helpers
+cudaError_t measure_fma_rates(double* fp64_tflops, double* fp32_tflops);
 int num_sms();
 NoiseSrc noise_src(qs_ctx* h, double e, uint64_t seed);
 Targets make_targets(int n, const int* targets, int k);

@@ -24,6 +24,7 @@ constexpr int kJacobiSweeps = 40;        // bound on the eigensolver's sweeps
 constexpr double kTieTol = 1e-10;        // cluster: within 1e-10 * Lambda_1
 constexpr double kGsAccept = 1e-3;       // residual norm to accept a projection
 constexpr double kGsFallback = 1e-8;
+constexpr double kRotTol = 4e-16;        // rotate while |a_pq| > kRotTol * max|a_ii|
 
 __device__ __forceinline__ uint64_t insert0(uint64_t v, int s) {
   return ((v >> s) << (s + 1)) | (v & ((1ull << s) - 1));
@@ -98,21 +99,33 @@ __global__ void __launch_bounds__(256) k_gram_partials(const cplx<R>* __restrict
   }
 }
 
-// G[p][q] = sum over blocks (fixed order); lower triangle by conjugation.
-__global__ void k_gram_reduce(const double* __restrict__ partials, int blocks, int M, double* G) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= M * M) return;
-  const int p = idx / M, q = idx % M;
+// G[p][q] = sum over the partial blocks (fixed-order tree); one block per
+// entry, lower triangle by conjugation.
+__global__ void __launch_bounds__(256) k_gram_reduce(const double* __restrict__ partials, int blocks, int M, double* G) {
+  const int p = blockIdx.x / M, q = blockIdx.x % M;
   if (q < p) return;
+  __shared__ double sre[256], sim[256];
   double re = 0.0, im = 0.0;
-  for (int b = 0; b < blocks; ++b) {
+  for (int b = threadIdx.x; b < blocks; b += blockDim.x) {
     re += partials[(size_t)b * 2 * M * M + 2 * (p * M + q)];
     im += partials[(size_t)b * 2 * M * M + 2 * (p * M + q) + 1];
   }
-  G[2 * (p * M + q)] = re;
-  G[2 * (p * M + q) + 1] = im;
-  G[2 * (q * M + p)] = re;
-  G[2 * (q * M + p) + 1] = p == q ? 0.0 : -im;
+  sre[threadIdx.x] = re;
+  sim[threadIdx.x] = im;
+  __syncthreads();
+  for (int o = 128; o; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sre[threadIdx.x] += sre[threadIdx.x + o];
+      sim[threadIdx.x] += sim[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    G[2 * (p * M + q)] = sre[0];
+    G[2 * (p * M + q) + 1] = p == q ? 0.0 : sim[0];
+    G[2 * (q * M + p)] = sre[0];
+    G[2 * (q * M + p) + 1] = p == q ? 0.0 : -sim[0];
+  }
 }
 
 __device__ __forceinline__ double2 zmul(double2 a, double2 b) {
@@ -123,22 +136,145 @@ __device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 zsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 zscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 
+// Scalar helpers for the real (double) and complex (double2) Jacobi variants.
+__device__ __forceinline__ double tmul(double a, double b) { return a * b; }
+__device__ __forceinline__ double2 tmul(double2 a, double2 b) { return zmul(a, b); }
+__device__ __forceinline__ double tadd(double a, double b) { return a + b; }
+__device__ __forceinline__ double2 tadd(double2 a, double2 b) { return zadd(a, b); }
+__device__ __forceinline__ double tconj(double a) { return a; }
+__device__ __forceinline__ double2 tconj(double2 a) { return zconj(a); }
+__device__ __forceinline__ double tre(double a) { return a; }
+__device__ __forceinline__ double tre(double2 a) { return a.x; }
+__device__ __forceinline__ double tabs2(double a) { return a * a; }
+__device__ __forceinline__ double tabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+template <typename T> __device__ __forceinline__ T tscal(double v);
+template <> __device__ __forceinline__ double tscal<double>(double v) { return v; }
+template <> __device__ __forceinline__ double2 tscal<double2>(double v) { return make_double2(v, 0.0); }
+__device__ __forceinline__ double tscale(double a, double v) { return a * v; }
+__device__ __forceinline__ double2 tscale(double2 a, double v) { return make_double2(a.x * v, a.y * v); }
+__device__ __forceinline__ double tphase(double a, double inv) { return a * inv; }                     // sign
+__device__ __forceinline__ double2 tphase(double2 a, double inv) { return make_double2(a.x * inv, -a.y * inv); }  // e^{-i arg}
+
+constexpr int kJP = kMaxGramDim + 1;                    // pitch of the Jacobi arrays
+
+// Parallel cyclic Jacobi on the Hermitian (or real symmetric) A (M x M,
+// pitch kJP), accumulating V.  Each step applies Mp/2 disjoint rotations
+// from the round-robin schedule: pair 0 = (Mp-1, s), pair i = ((s+i) mod
+// (Mp-1), (s-i) mod (Mp-1)).  A rotation zeroes a_pq: a phase makes a_pq
+// real, then the classical angle; the tangent is found in FP32 (any tangent
+// gives an exactly unitary rotation in FP64, the next sweep removes what is
+// left), cos and sin from one FP64 rsqrt.  The update A <- R^dagger A R is
+// done per 2x2 block of the upper triangle and mirrored.  Sweeps stop when
+// no |a_pq| exceeds kRotTol * max|a_ii|.
+template <typename T>
+__device__ void jacobi(T* A, T* V, int M, int* status) {
+  __shared__ T rot[kMaxGramDim / 2][4];
+  __shared__ int pp[kMaxGramDim / 2], qq[kMaxGramDim / 2];
+  __shared__ double thr2;
+  const int tid = threadIdx.x;
+  const int Mp = M + (M & 1);
+  const int nb = Mp / 2;
+  const int nblk = nb * (nb + 1) / 2;
+  for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
+    if (tid == 0) {
+      double dmax = 0.0;
+      for (int p = 0; p < M; ++p) dmax = fmax(dmax, fabs(tre(A[p * kJP + p])));
+      thr2 = (kRotTol * dmax) * (kRotTol * dmax);
+    }
+    __syncthreads();
+    int did = 0;
+    for (int st = 0; st < Mp - 1; ++st) {
+      if (tid < nb) {
+        int p, q;
+        if (tid == 0) { p = st; q = Mp - 1; }
+        else { p = (st + tid) % (Mp - 1); q = (st - tid + Mp - 1) % (Mp - 1); }
+        if (p > q) { const int t = p; p = q; q = t; }
+        pp[tid] = p;
+        qq[tid] = q;
+        T R00 = tscal<T>(1.0), R01 = tscal<T>(0.0), R10 = tscal<T>(0.0), R11 = tscal<T>(1.0);
+        if (q < M) {
+          const T apq = A[p * kJP + q];
+          const double a2 = tabs2(apq);
+          if (a2 > thr2 && a2 > 0.0) {
+            did = 1;
+            const double inv = rsqrt(a2);
+            const T ph = tphase(apq, inv);
+            const double theta = (tre(A[q * kJP + q]) - tre(A[p * kJP + p])) * 0.5 * inv;
+            const float th = (float)theta;
+            const float tf = copysignf(1.0f, th) / (fabsf(th) + sqrtf(1.0f + th * th));
+            const double t = (double)tf;
+            const double c = rsqrt(1.0 + t * t), sn = t * c;
+            R00 = tscal<T>(c);
+            R01 = tscal<T>(sn);
+            R10 = tscale(ph, -sn);
+            R11 = tscale(ph, c);
+          }
+        }
+        rot[tid][0] = R00; rot[tid][1] = R01; rot[tid][2] = R10; rot[tid][3] = R11;
+      }
+      __syncthreads();
+      for (int w = tid; w < nblk + M * nb; w += blockDim.x) {
+        if (w < nblk) {
+          // block (i, j), i <= j: Y = R_i^dagger X R_j
+          int i = 0, rem = w;
+          while (rem >= nb - i) { rem -= nb - i; ++i; }
+          const int j = i + rem;
+          const int r0 = pp[i], r1 = qq[i], c0 = pp[j], c1 = qq[j];
+          const bool vr1 = r1 < M, vc1 = c1 < M;
+          const T z = tscal<T>(0.0);
+          const T x00 = A[r0 * kJP + c0];
+          const T x01 = vc1 ? A[r0 * kJP + c1] : z;
+          const T x10 = vr1 ? A[r1 * kJP + c0] : z;
+          const T x11 = (vr1 && vc1) ? A[r1 * kJP + c1] : z;
+          const T a00 = rot[j][0], a01 = rot[j][1], a10 = rot[j][2], a11 = rot[j][3];
+          const T t00 = tadd(tmul(x00, a00), tmul(x01, a10)), t01 = tadd(tmul(x00, a01), tmul(x01, a11));
+          const T t10 = tadd(tmul(x10, a00), tmul(x11, a10)), t11 = tadd(tmul(x10, a01), tmul(x11, a11));
+          const T b00 = tconj(rot[i][0]), b01 = tconj(rot[i][2]), b10 = tconj(rot[i][1]), b11 = tconj(rot[i][3]);
+          const T y00 = tadd(tmul(b00, t00), tmul(b01, t10)), y01 = tadd(tmul(b00, t01), tmul(b01, t11));
+          const T y10 = tadd(tmul(b10, t00), tmul(b11, t10)), y11 = tadd(tmul(b10, t01), tmul(b11, t11));
+          A[r0 * kJP + c0] = y00;
+          if (vc1) A[r0 * kJP + c1] = y01;
+          if (vr1) A[r1 * kJP + c0] = y10;
+          if (vr1 && vc1) A[r1 * kJP + c1] = y11;
+          if (i != j) {                                  // Hermitian mirror
+            A[c0 * kJP + r0] = tconj(y00);
+            if (vc1) A[c1 * kJP + r0] = tconj(y01);
+            if (vr1) A[c0 * kJP + r1] = tconj(y10);
+            if (vr1 && vc1) A[c1 * kJP + r1] = tconj(y11);
+          }
+        } else {
+          // V <- V R for row k and pair j
+          const int v = w - nblk;
+          const int k = v / nb, j = v % nb;
+          const int p = pp[j], q = qq[j];
+          if (q < M) {
+            const T vp = V[k * kJP + p], vq = V[k * kJP + q];
+            V[k * kJP + p] = tadd(tmul(vp, rot[j][0]), tmul(vq, rot[j][2]));
+            V[k * kJP + q] = tadd(tmul(vp, rot[j][1]), tmul(vq, rot[j][3]));
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (!__syncthreads_or(did)) return;                  // no rotation in the whole sweep
+  }
+  if (tid == 0) status[0] = 1;                           // not converged within the sweep bound
+}
+
 // One block: eigendecomposition of the Hermitian G (M x M) by parallel cyclic
-// Jacobi (round-robin pairing, M/2 disjoint rotations per step), eigenvalues
-// sorted descending, clusters of ties given a canonical basis, then
-// W = first r canonical eigenvectors (M x keep), keep = min(r, M), and
-// lam[0..M) sorted descending; out_scale = 1/sqrt(sum lam[:keep]) or 1.
+// Jacobi (real arithmetic when G is real), eigenvalues sorted descending,
+// clusters of ties given a canonical basis, then W = first r canonical
+// eigenvectors (M x keep), keep = min(r, M), and lam[0..M) sorted
+// descending; out_scale = 1/sqrt(sum lam[:keep]) or 1.
 __global__ void __launch_bounds__(512) k_eig_truncate(const double* __restrict__ Gin, int M, int r,
                                                       int normalize, double* __restrict__ W,
                                                       double* __restrict__ lam_out, int* keep_out,
                                                       double* scale_out, int* status) {
-  __shared__ double2 A[kMaxGramDim][kMaxGramDim + 1];
-  __shared__ double2 V[kMaxGramDim][kMaxGramDim + 1];
-  __shared__ double2 rot[kMaxGramDim / 2][4];          // R[p][p], R[p][q], R[q][p], R[q][q]
-  __shared__ int pp[kMaxGramDim / 2], qq[kMaxGramDim / 2];
+  __shared__ double2 A[kMaxGramDim][kJP];
+  __shared__ double2 V[kMaxGramDim][kJP];
+  __shared__ double2 rot[kMaxGramDim / 2][4];          // Gram-Schmidt scratch
   __shared__ int order[kMaxGramDim + 1];
   __shared__ double lam[kMaxGramDim];
-  __shared__ double off_norm, tot_norm;
   // canonical vectors (columns) reuse A's storage once the eigenvalues are read
   auto& basis = A;
   __shared__ double2 vtmp[kMaxGramDim];
@@ -146,98 +282,41 @@ __global__ void __launch_bounds__(512) k_eig_truncate(const double* __restrict__
   __shared__ int nbasis;
 
   const int tid = threadIdx.x;
-  const int Mp = M + (M & 1);                           // even number of players
-  for (int i = tid; i < M * M; i += blockDim.x) {
-    const int p = i / M, q = i % M;
-    A[p][q] = make_double2(Gin[2 * i], Gin[2 * i + 1]);
-    V[p][q] = make_double2(p == q ? 1.0 : 0.0, 0.0);
-  }
-  if (tid == 0) {
-    for (int i = 0; i < Mp; ++i) order[i] = i;
-  }
-  __syncthreads();
-
-  for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
-    if (tid == 0) {
-      double off = 0.0, tot = 0.0;
-      for (int p = 0; p < M; ++p)
-        for (int q = 0; q < M; ++q) {
-          const double v = A[p][q].x * A[p][q].x + A[p][q].y * A[p][q].y;
-          tot += v;
-          if (p != q) off += v;
-        }
-      off_norm = off;
-      tot_norm = tot;
+  int cplx = 0;
+  for (int i = tid; i < M * M; i += blockDim.x) cplx |= Gin[2 * i + 1] != 0.0;
+  cplx = __syncthreads_or(cplx);
+  if (cplx) {
+    for (int i = tid; i < M * M; i += blockDim.x) {
+      const int p = i / M, q = i % M;
+      A[p][q] = make_double2(Gin[2 * i], Gin[2 * i + 1]);
+      V[p][q] = make_double2(p == q ? 1.0 : 0.0, 0.0);
     }
     __syncthreads();
-    if (off_norm <= 1e-32 * tot_norm || off_norm == 0.0) break;
-    for (int step = 0; step < Mp - 1; ++step) {
-      // pairs of this step from the round-robin arrangement
-      if (tid < Mp / 2) {
-        int p = order[tid], q = order[Mp - 1 - tid];
-        if (p > q) { const int t = p; p = q; q = t; }
-        pp[tid] = p;
-        qq[tid] = q;
-        double2 R00 = make_double2(1.0, 0.0), R01 = make_double2(0.0, 0.0);
-        double2 R10 = make_double2(0.0, 0.0), R11 = make_double2(1.0, 0.0);
-        if (q < M) {
-          const double2 apq = A[p][q];
-          const double mag = sqrt(apq.x * apq.x + apq.y * apq.y);
-          const double app = A[p][p].x, aqq = A[q][q].x;
-          if (mag > 1e-300) {
-            // phase e^{-i phi} on q makes the (p, q) entry real, then a real rotation
-            const double2 ph = make_double2(apq.x / mag, -apq.y / mag);    // e^{-i phi}
-            const double theta = (aqq - app) / (2.0 * mag);
-            const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
-            const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
-            R00 = make_double2(c, 0.0);
-            R01 = make_double2(s, 0.0);
-            R10 = zscale(ph, -s);
-            R11 = zscale(ph, c);
-          }
-        }
-        rot[tid][0] = R00; rot[tid][1] = R01; rot[tid][2] = R10; rot[tid][3] = R11;
-      }
-      __syncthreads();
-      const int npairs = Mp / 2;
-      // A <- A R (columns p, q), V <- V R
-      for (int i = tid; i < npairs * M; i += blockDim.x) {
-        const int j = i / M, k = i % M;
-        const int p = pp[j], q = qq[j];
-        if (q >= M) continue;
-        const double2 R00 = rot[j][0], R01 = rot[j][1], R10 = rot[j][2], R11 = rot[j][3];
-        const double2 akp = A[k][p], akq = A[k][q];
-        A[k][p] = zadd(zmul(akp, R00), zmul(akq, R10));
-        A[k][q] = zadd(zmul(akp, R01), zmul(akq, R11));
-        const double2 vkp = V[k][p], vkq = V[k][q];
-        V[k][p] = zadd(zmul(vkp, R00), zmul(vkq, R10));
-        V[k][q] = zadd(zmul(vkp, R01), zmul(vkq, R11));
-      }
-      __syncthreads();
-      // A <- R^dagger A (rows p, q)
-      for (int i = tid; i < npairs * M; i += blockDim.x) {
-        const int j = i / M, k = i % M;
-        const int p = pp[j], q = qq[j];
-        if (q >= M) continue;
-        const double2 R00 = rot[j][0], R01 = rot[j][1], R10 = rot[j][2], R11 = rot[j][3];
-        const double2 apk = A[p][k], aqk = A[q][k];
-        A[p][k] = zadd(zmul(zconj(R00), apk), zmul(zconj(R10), aqk));
-        A[q][k] = zadd(zmul(zconj(R01), apk), zmul(zconj(R11), aqk));
-      }
-      __syncthreads();
-      if (tid == 0) {                                   // rotate all but order[0]
-        const int last = order[Mp - 1];
-        for (int i = Mp - 1; i > 1; --i) order[i] = order[i - 1];
-        order[1] = last;
-      }
-      __syncthreads();
+    jacobi<double2>(&A[0][0], &V[0][0], M, status);
+    for (int i = tid; i < M; i += blockDim.x) lam[i] = A[i][i].x;
+    __syncthreads();
+  } else {
+    double* Ar = reinterpret_cast<double*>(&A[0][0]);
+    double* Vr = reinterpret_cast<double*>(&V[0][0]);
+    for (int i = tid; i < M * M; i += blockDim.x) {
+      const int p = i / M, q = i % M;
+      Ar[p * kJP + q] = Gin[2 * i];
+      Vr[p * kJP + q] = p == q ? 1.0 : 0.0;
     }
-    if (sweep == kJacobiSweeps - 1 && tid == 0) status[0] = 1;   // not converged
+    __syncthreads();
+    jacobi<double>(Ar, Vr, M, status);
+    for (int i = tid; i < M; i += blockDim.x) lam[i] = Ar[i * kJP + i];
+    // widen V to complex in place: read everything first
+    double hold[2] = {0.0, 0.0};
+    for (int i = tid, c = 0; i < M * M && c < 2; i += blockDim.x, ++c) hold[c] = Vr[(i / M) * kJP + i % M];
+    __syncthreads();
+    for (int i = tid, c = 0; i < M * M && c < 2; i += blockDim.x, ++c) V[i / M][i % M] = make_double2(hold[c], 0.0);
+    __syncthreads();
   }
 
   // sort eigenvalues descending (selection sort, ties keep index order)
   if (tid == 0) {
-    for (int i = 0; i < M; ++i) { order[i] = i; lam[i] = A[i][i].x; }
+    for (int i = 0; i < M; ++i) order[i] = i;
     for (int i = 0; i < M; ++i) {
       int best = i;
       for (int j = i + 1; j < M; ++j)
@@ -273,11 +352,14 @@ __global__ void __launch_bounds__(512) k_eig_truncate(const double* __restrict__
         __syncthreads();
         for (int rep = 0; rep < 2; ++rep) {
           for (int u = first; u < nbasis; ++u) {
-            // v -= basis_u * <basis_u, v>
-            if (tid == 0) {
-              double2 d = make_double2(0.0, 0.0);
-              for (int k = 0; k < M; ++k) d = zadd(d, zmul(zconj(basis[k][u]), vtmp[k]));
-              rot[0][0] = d;
+            // v -= basis_u * <basis_u, v>   (dot product by warp 0)
+            if (tid < 32) {
+              double2 d = tid < M ? zmul(zconj(basis[tid][u]), vtmp[tid]) : make_double2(0.0, 0.0);
+              for (int o = 16; o; o >>= 1) {
+                d.x += __shfl_xor_sync(0xffffffffu, d.x, o);
+                d.y += __shfl_xor_sync(0xffffffffu, d.y, o);
+              }
+              if (tid == 0) rot[0][0] = d;
             }
             __syncthreads();
             const double2 d = rot[0][0];
@@ -285,10 +367,10 @@ __global__ void __launch_bounds__(512) k_eig_truncate(const double* __restrict__
             __syncthreads();
           }
         }
-        if (tid == 0) {
-          double nv = 0.0;
-          for (int k = 0; k < M; ++k) nv += vtmp[k].x * vtmp[k].x + vtmp[k].y * vtmp[k].y;
-          vnorm = sqrt(nv);
+        if (tid < 32) {
+          double nv = tid < M ? vtmp[tid].x * vtmp[tid].x + vtmp[tid].y * vtmp[tid].y : 0.0;
+          for (int o = 16; o; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
+          if (tid == 0) vnorm = sqrt(nv);
         }
         __syncthreads();
         if (vnorm > thr) {
@@ -321,7 +403,7 @@ __global__ void __launch_bounds__(512) k_eig_truncate(const double* __restrict__
   }
 }
 
-// L[c'] = scale * sum_p Lp[p] W[p][c'] for c' < keep; one thread per row.
+// L[c] = scale * sum_p Lp[p] W[p][c] for c < keep; one thread per (row, c).
 template <typename R>
 __global__ void __launch_bounds__(256) k_project(const cplx<R>* __restrict__ Lp, cplx<R>* __restrict__ L,
                                                  int n, int M, const double* __restrict__ W,
@@ -334,21 +416,17 @@ __global__ void __launch_bounds__(256) k_project(const cplx<R>* __restrict__ Lp,
     sW[i] = make_double2(W[2 * i] * scale, W[2 * i + 1] * scale);
   __syncthreads();
   const uint64_t N = 1ull << n;
-  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N;
-       x += (uint64_t)gridDim.x * blockDim.x) {
-    double2 acc[kMaxRank];
-#pragma unroll
-    for (int c = 0; c < kMaxRank; ++c) acc[c] = make_double2(0.0, 0.0);
+  const uint64_t work = N * (uint64_t)keep;
+  for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < work;
+       w += (uint64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(w / N);
+    const uint64_t x = w - (uint64_t)c * N;
+    double2 acc = make_double2(0.0, 0.0);
     for (int p = 0; p < M; ++p) {
       const cplx<R> a = Lp[(uint64_t)p * N + x];
-      const double2 ad = make_double2(a.x, a.y);
-#pragma unroll
-      for (int c = 0; c < kMaxRank; ++c)
-        if (c < keep) acc[c] = zadd(acc[c], zmul(ad, sW[p * keep + c]));
+      acc = zadd(acc, zmul(make_double2(a.x, a.y), sW[p * keep + c]));
     }
-#pragma unroll
-    for (int c = 0; c < kMaxRank; ++c)
-      if (c < keep) L[(uint64_t)c * N + x] = mk<R>((R)acc[c].x, (R)acc[c].y);
+    L[(uint64_t)c * N + x] = mk<R>((R)acc.x, (R)acc.y);
   }
 }
 
@@ -395,7 +473,7 @@ cudaError_t launch_gram(qs_ctx* h, const void* Lp, int n, int M, double* G) {
     k_gram_partials<float><<<blocks, 256, 0, h->stream>>>((const float2*)Lp, n, M, h->partials);
   else
     k_gram_partials<double><<<blocks, 256, 0, h->stream>>>((const double2*)Lp, n, M, h->partials);
-  k_gram_reduce<<<(M * M + 255) / 256, 256, 0, h->stream>>>(h->partials, blocks, M, G);
+  k_gram_reduce<<<M * M, 256, 0, h->stream>>>(h->partials, blocks, M, G);
   return cudaGetLastError();
 }
 
@@ -408,7 +486,7 @@ cudaError_t launch_eig_truncate(qs_ctx* h, const double* G, int M, int r, int no
 cudaError_t launch_project(qs_ctx* h, const void* Lp, void* L, int n, int M, const double* W,
                            const double* scale, const int* keep) {
   const uint64_t N = 1ull << n;
-  uint64_t blocks = (N + 255) / 256;
+  uint64_t blocks = (N * kMaxRank + 255) / 256;
   const uint64_t cap = (uint64_t)num_sms() * 8;
   if (blocks > cap) blocks = cap;
   if (h->dtype == QS_C64)

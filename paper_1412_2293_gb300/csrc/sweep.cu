@@ -8,6 +8,8 @@
 // matrices (Eqs. 1-2) without any extra indexing.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.cuh"
 #include "philox.cuh"
 
@@ -56,8 +58,6 @@ __global__ void k_noise_mats(R* out, int members, int k, DMat U, int noise, int 
   const uint64_t traj = src.traj ? src.traj[b] : src.traj0 + (uint64_t)b;
   const double2 xi = noise_normals(seed, traj, gate_id);
   const int d = 1 << k;
-  double N[16][2];   // noise matrix entries of column c used below, real or complex
-  (void)N;
   if (noise == QS_NOISE_ROTATION) {
     // V(a) = [[cos a, sin a], [-sin a, cos a]] on each target; targets[0] is
     // the low local bit.  Real matrix NV[r][c] = prod_j V_j[r_j][c_j].
@@ -145,17 +145,45 @@ __global__ void __launch_bounds__(kBlock) k_apply_1q(cplx<R>* __restrict__ psi, 
   }
 }
 
-// Dense k-qubit gate (k <= 4) on groups of 2^k amplitudes.
-template <typename R, int K>
+// Dense k-qubit gate (k <= 4) on groups of 2^k amplitudes.  REAL: the
+// (uniform) matrix has no imaginary part, so each entry costs two multiply-adds.
+template <typename R, int K, bool REAL>
 __global__ void __launch_bounds__(kBlock) k_apply_kq(cplx<R>* __restrict__ psi, int n,
                                                      uint64_t ngroups, Targets tg,
                                                      const R* __restrict__ mat, int per_member) {
   using C = cplx<R>;
   constexpr int D = 1 << K;
   __shared__ C sm[D * D];
+  __shared__ R smr[REAL ? D * D : 1];
   if (!per_member) {
-    for (int i = threadIdx.x; i < D * D; i += blockDim.x) sm[i] = mk<R>(mat[2 * i], mat[2 * i + 1]);
+    for (int i = threadIdx.x; i < D * D; i += blockDim.x) {
+      if (REAL) smr[i] = mat[2 * i];
+      else sm[i] = mk<R>(mat[2 * i], mat[2 * i + 1]);
+    }
     __syncthreads();
+  }
+  if (REAL && !per_member) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
+      uint64_t base = g;
+#pragma unroll
+      for (int j = 0; j < K; ++j) base = insert0(base, tg.sorted[j]);
+      C a[D];
+#pragma unroll
+      for (int l = 0; l < D; ++l) a[l] = psi[base + tg.off[l]];
+#pragma unroll
+      for (int r = 0; r < D; ++r) {
+        R re = 0, im = 0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const R m = smr[r * D + c];
+          re += m * a[c].x;
+          im += m * a[c].y;
+        }
+        psi[base + tg.off[r]] = mk<R>(re, im);
+      }
+    }
+    return;
   }
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
@@ -241,7 +269,7 @@ __global__ void k_debug_noise(uint64_t seed, uint64_t traj, uint64_t gate_id, in
   }
 }
 
-template <typename R>
+template <typename R, bool REAL>
 cudaError_t apply_kq_dispatch(qs_ctx* h, void* psi, int n, int members, const Targets& tg,
                               const void* mat, bool per_member) {
   const uint64_t ng = (uint64_t)members << (n - tg.k);
@@ -249,10 +277,10 @@ cudaError_t apply_kq_dispatch(qs_ctx* h, void* psi, int n, int members, const Ta
   auto* p = static_cast<cplx<R>*>(psi);
   const R* m = static_cast<const R*>(mat);
   switch (tg.k) {
-    case 1: k_apply_kq<R, 1><<<g, kBlock, 0, h->stream>>>(p, n, ng, tg, m, per_member); break;
-    case 2: k_apply_kq<R, 2><<<g, kBlock, 0, h->stream>>>(p, n, ng, tg, m, per_member); break;
-    case 3: k_apply_kq<R, 3><<<g, kBlock, 0, h->stream>>>(p, n, ng, tg, m, per_member); break;
-    case 4: k_apply_kq<R, 4><<<g, kBlock, 0, h->stream>>>(p, n, ng, tg, m, per_member); break;
+    case 1: k_apply_kq<R, 1, REAL><<<g, kBlock, 0, h->stream>>>(p, n, ng, tg, m, per_member); break;
+    case 2: k_apply_kq<R, 2, REAL><<<g, kBlock, 0, h->stream>>>(p, n, ng, tg, m, per_member); break;
+    case 3: k_apply_kq<R, 3, REAL><<<g, kBlock, 0, h->stream>>>(p, n, ng, tg, m, per_member); break;
+    case 4: k_apply_kq<R, 4, REAL><<<g, kBlock, 0, h->stream>>>(p, n, ng, tg, m, per_member); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -275,7 +303,57 @@ cudaError_t apply_diag_dispatch(qs_ctx* h, void* psi, int n, int members, const 
   return cudaGetLastError();
 }
 
+// Dependent multiply-add chains (8 per thread) to measure the arithmetic rate.
+template <typename T>
+__global__ void k_fma_chain(T* out, int iters, T a, T b) {
+  T x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = (T)(threadIdx.x + i);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = x[i] * a + b;
+  }
+  T s = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += x[i];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace
+
+cudaError_t measure_fma_rates(double* fp64_tflops, double* fp32_tflops) {
+  const int grid = num_sms() * 8, block = 256;
+  double* d = nullptr;
+  cudaError_t e = cudaMalloc((void**)&d, (size_t)grid * block * sizeof(double));
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best64 = 0.0, best32 = 0.0;
+  for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+    const int it64 = 2048, it32 = 65536;
+    float ms = 0.f;
+    cudaEventRecord(e0);
+    k_fma_chain<double><<<grid, block>>>(d, it64, 0.999999, 1e-7);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    best64 = std::max(best64, 2.0 * 8 * it64 * (double)grid * block / (ms * 1e-3) / 1e12);
+    cudaEventRecord(e0);
+    k_fma_chain<float><<<grid, block>>>((float*)d, it32, 0.999999f, 1e-7f);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    best32 = std::max(best32, 2.0 * 8 * it32 * (double)grid * block / (ms * 1e-3) / 1e12);
+    e = cudaGetLastError();
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d);
+  *fp64_tflops = best64;
+  *fp32_tflops = best32;
+  return e;
+}
 
 size_t elem_size(qs_dtype d) { return d == QS_C64 ? 8 : 16; }
 
@@ -355,9 +433,13 @@ cudaError_t launch_apply_1q(qs_ctx* h, void* psi, int n, int members, int t, con
 }
 
 cudaError_t launch_apply_kq(qs_ctx* h, void* psi, int n, int members, const Targets& tg,
-                            const void* mat, bool per_member) {
-  if (h->dtype == QS_C64) return apply_kq_dispatch<float>(h, psi, n, members, tg, mat, per_member);
-  return apply_kq_dispatch<double>(h, psi, n, members, tg, mat, per_member);
+                            const void* mat, bool per_member, bool real) {
+  if (real && !per_member) {
+    if (h->dtype == QS_C64) return apply_kq_dispatch<float, true>(h, psi, n, members, tg, mat, false);
+    return apply_kq_dispatch<double, true>(h, psi, n, members, tg, mat, false);
+  }
+  if (h->dtype == QS_C64) return apply_kq_dispatch<float, false>(h, psi, n, members, tg, mat, per_member);
+  return apply_kq_dispatch<double, false>(h, psi, n, members, tg, mat, per_member);
 }
 
 cudaError_t launch_apply_diag(qs_ctx* h, void* psi, int n, int members, const Targets& tg,

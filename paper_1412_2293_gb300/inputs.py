@@ -147,6 +147,9 @@ WORKLOADS = {
     "mc_qft_n20_c128": Workload("mc_qft_n20_c128", 20, "qft", "statevec", "c128", 0.01, trajectories=1024),
     "rank_grover_n16": Workload("rank_grover_n16", 16, "grover", "fixed_rank", "c128", 0.01, rank=8),
     "dm_qft_n14": Workload("dm_qft_n14", 14, "qft", "density", "c128", 0.01),
+    # smaller cases of the same two shapes (profiling, quick runs)
+    "rank_grover_n12": Workload("rank_grover_n12", 12, "grover", "fixed_rank", "c128", 0.01, rank=8),
+    "dm_qft_n10": Workload("dm_qft_n10", 10, "qft", "density", "c128", 0.01),
 }
 
 

@@ -78,6 +78,7 @@ _SIGS = {
     "qs_plan_set_timing": ([_P, ct.c_int], ct.c_int),
     "qs_plan_last_times": ([_P, _D, _I, ct.c_int, _I], ct.c_int),
     "qs_fidelity_noalloc": ([_P, _P, ct.c_int, ct.c_int, ct.c_int, _P, _D], ct.c_int),
+    "qs_measure_peaks": ([_D, _D], ct.c_int),
     "qs_debug_noise": ([ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_int, ct.POINTER(ct.c_uint32), _D], ct.c_int),
 }
 
@@ -356,6 +357,13 @@ def qs_fidelity_noalloc(states_ptr, ref_ptr, n, members, dtype, stream=None):
     _check(lib().qs_fidelity_noalloc(ct.c_void_p(int(states_ptr)), ct.c_void_p(int(ref_ptr)), int(n),
                                      int(members), int(dtype), _stream_ptr(stream), _dptr(out)))
     return out
+
+
+def qs_measure_peaks():
+    """(fp64_tflops, fp32_tflops) measured on the current device."""
+    a, b = ct.c_double(), ct.c_double()
+    _check(lib().qs_measure_peaks(ct.byref(a), ct.byref(b)))
+    return a.value, b.value
 
 
 def qs_debug_noise(seed, traj, gate_id, count):
