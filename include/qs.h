@@ -158,6 +158,12 @@ qs_status qs_set_reference(qs_handle h, const double* ref);
 qs_status qs_set_reference_from(qs_handle h, qs_handle src, int b);
 qs_status qs_fidelity_stored(qs_handle h, double* out);
 
+/* STATEVEC: |<ref_0|psi_b>|^2 for members b = first .. first+count-1, with
+ * ref_0 = member 0 of the STATEVEC handle `ref` (same n and dtype; read in
+ * place on the device, after `ref`'s stream is synchronised).  out[count].
+ * Lets members of one batch (different jobs) use different references. */
+qs_status qs_fidelity_ref(qs_handle h, qs_handle ref, int first, int count, double* out);
+
 /* Trace: STATEVEC squared norm per member (out[batch]); DENSITY tr(rho);
  * FIXED_RANK sum_c ||L_c||^2.  Synchronises. */
 qs_status qs_trace(qs_handle h, double* out);

@@ -589,6 +589,19 @@ qs_status qs_fidelity_stored(qs_handle h, double* out) {
   return fidelity_dev(h, h->ref, out);
 }
 
+qs_status qs_fidelity_ref(qs_handle h, qs_handle ref, int first, int count, double* out) {
+  if (!h || !ref || !out) return QS_ERR_INVALID_ARG;
+  if (h->mode != QS_STATEVEC || ref->mode != QS_STATEVEC || ref->n != h->n || ref->dtype != h->dtype)
+    return fail(h, QS_ERR_INVALID_ARG, "reference must be a STATEVEC handle with the same n and dtype");
+  if (first < 0 || count < 1 || first + count > h->batch) return fail(h, QS_ERR_INVALID_ARG, "member range out of bounds");
+  { const qs_status st = qs::materialize_basis(h); if (st != QS_OK) return st; }
+  { const qs_status st = qs::materialize_basis(ref); if (st != QS_OK) return fail(h, st, ref->err); }
+  QS_CUDA(h, cudaStreamSynchronize(ref->stream));
+  const char* psi = (const char*)h->state + ((size_t)first << h->n) * h->esize;
+  QS_CUDA(h, qs::launch_dot(h, psi, ref->state, h->n, count, false, h->small + kSmallOut));
+  return read_out(h, out, count);
+}
+
 qs_status qs_trace(qs_handle h, double* out) {
   if (!h || !out) return QS_ERR_INVALID_ARG;
   { const qs_status st = qs::materialize_basis(h); if (st != QS_OK) return st; }

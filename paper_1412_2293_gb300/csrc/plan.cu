@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -634,7 +635,8 @@ size_t high_smem() {
 // elements (a complex128 amplitude is two of them), boxes of 2^colb amplitudes
 // x 256 rows.
 qs_status make_tmap(qs_plan p, PassPlan* P) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static std::atomic<PFN_cuTensorMapEncodeTiled_v12000> encode_fn{nullptr};
+  PFN_cuTensorMapEncodeTiled_v12000 encode = encode_fn.load();
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
@@ -642,6 +644,7 @@ qs_status make_tmap(qs_plan p, PassPlan* P) {
         q != cudaDriverEntryPointSuccess || !fn)
       return pfail(p, QS_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    encode_fn.store(encode);
   }
   qs_ctx* h = p->h;
   const uint64_t per = h->esize / 8;                     // 8-byte elements per amplitude
@@ -728,7 +731,7 @@ __global__ void k_fid_finalize(const double* __restrict__ partials, int members,
 }
 
 cudaError_t set_smem_attrs(size_t esize) {
-  static bool done[2] = {false, false};
+  static std::atomic<bool> done[2] = {false, false};
   const int which = esize == 8 ? 0 : 1;
   if (done[which]) return cudaSuccess;
   cudaError_t e;

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "internal.cuh"
 #include "philox.cuh"
@@ -358,12 +359,14 @@ cudaError_t measure_fma_rates(double* fp64_tflops, double* fp32_tflops) {
 size_t elem_size(qs_dtype d) { return d == QS_C64 ? 8 : 16; }
 
 int num_sms() {
-  static int sms = 0;
+  static std::atomic<int> cached{0};
+  int sms = cached.load();
   if (!sms) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
+    cached.store(sms);
   }
   return sms;
 }

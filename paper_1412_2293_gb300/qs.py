@@ -63,6 +63,7 @@ _SIGS = {
     "qs_set_reference_from": ([_P, _P, ct.c_int], ct.c_int),
     "qs_fidelity_stored": ([_P, _D], ct.c_int),
     "qs_trace": ([_P, _D], ct.c_int),
+    "qs_fidelity_ref": ([_P, _P, ct.c_int, ct.c_int, _D], ct.c_int),
     "qs_state_size": ([_P, ct.POINTER(ct.c_size_t)], ct.c_int),
     "qs_get_state": ([_P, _D, ct.c_size_t], ct.c_int),
     "qs_set_state": ([_P, _D, ct.c_size_t], ct.c_int),
@@ -224,6 +225,12 @@ def qs_set_reference_from(h, src, b=0):
 def qs_fidelity_stored(h):
     out = np.zeros(_results(h), dtype=np.float64)
     _check(lib().qs_fidelity_stored(h, _dptr(out)), h)
+    return out
+
+
+def qs_fidelity_ref(h, ref, first, count):
+    out = np.zeros(int(count), dtype=np.float64)
+    _check(lib().qs_fidelity_ref(h, ref, int(first), int(count), _dptr(out)), h)
     return out
 
 

@@ -1,0 +1,554 @@
+"""Continuous-batching server for fidelity-estimation jobs.
+
+A job asks for the fidelity of a noisy circuit (Grover or QFT, n qubits,
+noise level e) with its ideal output, either as a Monte Carlo estimate over
+T trajectories (Sec. 2: complex64, one fidelity per trajectory) or through
+the fixed-rank density matrix (Sec. 3.2: complex128, rank r).
+
+* Admission: jobs wait until their device memory fits an HBM budget
+  (cudaMemGetInfo at start minus a reserve, or a given byte count).
+* Batching: Monte Carlo trajectories of every pending job with the same
+  shape (circuit, n, Grover iteration count) are packed into one launch of
+  one plan; a batch member carries its own job's noise level, key, trajectory
+  counter, basis input and marked item (qs_set_member_noise /
+  qs_set_basis_states), so a trajectory gives the same result alone and in
+  any mix.  Jobs larger than the per-launch member limit run in waves.
+* Overlap: several worker threads, each with its own CUDA stream, run units
+  concurrently; new arrivals are admitted as soon as memory and a worker
+  free up (continuous batching at launch granularity).
+* Each job records its arrival and completion time; `run_stream` reports
+  circuits/s and p50/p99 latency.
+
+The scheduling logic (`Scheduler`) holds no GPU calls and is tested on the
+CPU with a fake executor; `GpuExecutor` does the CUDA work through the C ABI.
+"""
+from __future__ import annotations
+
+import collections
+import math
+import threading
+import time
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional, Tuple
+
+import numpy as np
+
+from . import inputs
+
+C64_BYTES = 8
+C128_BYTES = 16
+
+
+# ------------------------------------------------------------------ work units
+@dataclass
+class Slice:
+    job_id: int
+    first: int              # first trajectory counter of this slice
+    count: int
+
+
+@dataclass
+class Unit:
+    """One launch of work: a Monte Carlo round or a whole fixed-rank job."""
+
+    kind: str                         # "mc" | "rank"
+    key: Tuple
+    slices: List[Slice]
+    members: int                      # launch batch (MC: a power of two >= sum of counts)
+    bytes: int                        # device memory of the launch's own buffers
+    uid: int = 0
+
+    @property
+    def cache_key(self) -> Tuple:
+        return self.key + (self.members,)
+
+
+@dataclass
+class JobState:
+    job: inputs.Job
+    arrival: float
+    next_traj: int = 0                # MC: first trajectory not yet scheduled
+    done_traj: int = 0
+    fidelities: Optional[np.ndarray] = None
+    finish: Optional[float] = None
+    ref_bytes: int = 0                # MC: the ideal reference, held from first launch to completion
+    ref_charged: bool = False
+
+
+def mc_key(job: inputs.Job) -> Tuple:
+    return ("mc", job.circuit, job.n, job.iterations)
+
+
+def member_bytes(n: int) -> int:
+    """Device bytes of one complex64 trajectory (upper bound): its amplitudes,
+    reduction partials (1/64 of the state) and at most 512 KiB of per-member
+    gate parameters and phase tables of the fused passes."""
+    return (1 << n) * C64_BYTES + (1 << n) // 64 + (1 << 19)
+
+
+def rank_bytes(n: int, r: int) -> int:
+    """Device bytes of a fixed-rank job: factor, 32-column work buffer, scratch and reference."""
+    N = 1 << n
+    return (r + 32) * N * C128_BYTES + N * 256 + N * C128_BYTES
+
+
+def bucket_for(members: int, lo: int, hi: int) -> int:
+    b = lo
+    while b < members:
+        b *= 2
+    return min(max(b, lo), hi)
+
+
+def largest_bucket(limit: int, hi: int) -> int:
+    """Largest power of two <= min(limit, hi), or 0."""
+    limit = min(limit, hi)
+    if limit < 1:
+        return 0
+    return 1 << (int(limit).bit_length() - 1)
+
+
+class Scheduler:
+    """Admission and batching decisions (no device calls).
+
+    Launch batches are powers of two between `min_bucket` and `max_members`
+    so that launches of one shape reuse cached handles and plans."""
+
+    def __init__(self, budget_bytes: int, max_members: int = 4096, min_bucket: int = 16,
+                 starve_s: float = 2.0):
+        if max_members & (max_members - 1) or min_bucket & (min_bucket - 1) or min_bucket > max_members:
+            raise ValueError("min_bucket and max_members must be powers of two, min_bucket <= max_members")
+        self.budget = int(budget_bytes)
+        self.max_members = max_members
+        self.min_bucket = min_bucket
+        self.starve_s = starve_s              # after this wait the oldest job stops backfilling
+        self.used = 0
+        self.jobs: Dict[int, JobState] = {}
+        self.order: List[int] = []            # job ids in arrival order with work left
+        self.in_flight: Dict[int, Unit] = {}
+        self.finished: List[int] = []
+        self._uid = 0
+        self.peak_used = 0
+        self.max_in_flight = 0
+
+    # -- bookkeeping -------------------------------------------------------
+    def min_bytes(self, job: inputs.Job) -> int:
+        """Device memory of the smallest unit a job can run in."""
+        if job.mode == "fixed_rank":
+            return rank_bytes(job.n, job.rank)
+        return member_bytes(job.n) * self.min_bucket + (1 << job.n) * C64_BYTES
+
+    def submit(self, job: inputs.Job, now: float) -> None:
+        if job.mode not in ("statevec", "fixed_rank") or job.trajectories < 1:
+            raise ValueError(f"job {job.job_id}: unsupported mode {job.mode!r}")
+        if job.job_id in self.jobs:
+            raise ValueError(f"job {job.job_id} submitted twice")
+        if self.min_bytes(job) > self.budget:
+            raise MemoryError(f"job {job.job_id} needs {self.min_bytes(job)} bytes, more than the budget {self.budget}")
+        st = JobState(job, now)
+        if job.mode == "statevec":
+            st.fidelities = np.full(job.trajectories, np.nan)
+            st.ref_bytes = (1 << job.n) * C64_BYTES
+        self.jobs[job.job_id] = st
+        self.order.append(job.job_id)
+
+    def pending(self) -> int:
+        return len(self.order)
+
+    def busy(self) -> bool:
+        return bool(self.order) or bool(self.in_flight)
+
+    # -- decisions ---------------------------------------------------------
+    def next_unit(self, now: float = 0.0) -> Optional[Unit]:
+        """The next unit that fits the budget, oldest job first, or None.
+
+        Younger jobs backfill memory the oldest cannot use yet, until the
+        oldest has waited `starve_s` seconds: then nothing new starts before it."""
+        free = self.budget - self.used
+        for pos, jid in enumerate(list(self.order)):
+            st = self.jobs[jid]
+            job = st.job
+            if job.mode == "fixed_rank":
+                b = rank_bytes(job.n, job.rank)
+                if b <= free:
+                    self.order.remove(jid)
+                    return self._issue(Unit("rank", ("rank", job.n, job.rank), [Slice(jid, 0, 1)], 1, b), [])
+            else:
+                made = self._mc_unit(mc_key(job), free)
+                if made is not None:
+                    return self._issue(*made)
+            if pos == 0 and now - st.arrival > self.starve_s:
+                return None
+        return None
+
+    def _mc_unit(self, key, free):
+        """Pack pending trajectories of every job of one shape into one launch."""
+        per = member_bytes(key[2])
+        slices, total, refs, charge = [], 0, 0, []
+        for jid in self.order:
+            st = self.jobs[jid]
+            if st.job.mode != "statevec" or mc_key(st.job) != key:
+                continue
+            left = st.job.trajectories - st.next_traj
+            if left <= 0:
+                continue
+            ref = 0 if st.ref_charged or jid in charge else st.ref_bytes
+            fit = largest_bucket((free - refs - ref) // per, self.max_members)
+            if fit < self.min_bucket or fit <= total:
+                break
+            take = min(left, fit - total)
+            slices.append(Slice(jid, st.next_traj, take))
+            total += take
+            refs += ref
+            if ref:
+                charge.append(jid)
+            if total >= self.max_members:
+                break
+        if not slices:
+            return None
+        members = bucket_for(total, self.min_bucket, self.max_members)
+        for sl in slices:
+            st = self.jobs[sl.job_id]
+            st.next_traj += sl.count
+            if st.next_traj >= st.job.trajectories:
+                self.order.remove(sl.job_id)
+        return Unit("mc", key, slices, members, members * per), charge
+
+    def _issue(self, unit: Unit, charge: List[int]) -> Unit:
+        self._uid += 1
+        unit.uid = self._uid
+        self.used += unit.bytes
+        for jid in charge:
+            st = self.jobs[jid]
+            st.ref_charged = True
+            self.used += st.ref_bytes
+        if self.used > self.budget:
+            raise AssertionError("scheduler exceeded its memory budget")
+        self.peak_used = max(self.peak_used, self.used)
+        self.in_flight[unit.uid] = unit
+        self.max_in_flight = max(self.max_in_flight, len(self.in_flight))
+        return unit
+
+    def complete(self, unit: Unit, results: List[np.ndarray], now: float) -> List[int]:
+        """Record a finished unit; returns the ids of jobs that are now complete."""
+        self.in_flight.pop(unit.uid)
+        self.used -= unit.bytes
+        done = []
+        for sl, res in zip(unit.slices, results):
+            st = self.jobs[sl.job_id]
+            if unit.kind == "rank":
+                st.fidelities = np.asarray(res, dtype=np.float64).reshape(-1)
+                st.done_traj = 1
+                st.finish = now
+                done.append(sl.job_id)
+                continue
+            st.fidelities[sl.first:sl.first + sl.count] = res
+            st.done_traj += sl.count
+            if st.done_traj >= st.job.trajectories:
+                st.finish = now
+                if st.ref_charged:
+                    self.used -= st.ref_bytes
+                done.append(sl.job_id)
+        self.finished.extend(done)
+        return done
+
+
+# ------------------------------------------------------------------ GPU executor
+class GpuExecutor:
+    """Runs units through the C ABI; one CUDA stream per worker thread.
+
+    Idle handles (with their plans) stay in a cache of at most `cache_bytes`
+    so that launches of a recurring shape skip allocation and planning; the
+    server keeps that many bytes out of its scheduling budget."""
+
+    def __init__(self, workers: int = 4, cache_bytes: int = 4 << 30):
+        import torch
+
+        from . import build, qs
+        build.build()
+        self.qs = qs
+        self.workers = workers
+        self.streams = [torch.cuda.Stream() for _ in range(workers)]
+        self.ref_streams = [torch.cuda.Stream() for _ in range(workers)]
+        self.refs: Dict[int, object] = {}          # job id -> reference handle
+        self.lock = threading.Lock()
+        self.cache_bytes = cache_bytes
+        self.idle: "collections.OrderedDict[Tuple, List]" = collections.OrderedDict()   # key -> [(h, p, bytes)]
+        self.idle_bytes = 0
+
+    # -- handle cache ------------------------------------------------------
+    def _checkout(self, key):
+        with self.lock:
+            lst = self.idle.get(key)
+            if not lst:
+                return None
+            ent = lst.pop()
+            if not lst:
+                del self.idle[key]
+            self.idle_bytes -= ent[2]
+            return ent
+
+    def _checkin(self, key, ent):
+        drop = []
+        with self.lock:
+            while self.idle and self.idle_bytes + ent[2] > self.cache_bytes:
+                k0, lst = next(iter(self.idle.items()))
+                old = lst.pop(0)
+                if not lst:
+                    del self.idle[k0]
+                self.idle_bytes -= old[2]
+                drop.append(old)
+            if self.idle_bytes + ent[2] <= self.cache_bytes:
+                self.idle.setdefault(key, []).append(ent)
+                self.idle.move_to_end(key)
+                self.idle_bytes += ent[2]
+            else:
+                drop.append(ent)
+        for h, p, _ in drop:
+            self._free(h, p)
+
+    def _free(self, h, p):
+        if p is not None:
+            self.qs.qs_plan_destroy(p)
+        self.qs.qs_destroy(h)
+
+    def close(self):
+        with self.lock:
+            ents = [e for lst in self.idle.values() for e in lst]
+            self.idle.clear()
+            self.idle_bytes = 0
+            refs = list(self.refs.values())
+            self.refs.clear()
+        for h, p, _ in ents:
+            self._free(h, p)
+        for h in refs:
+            self.qs.qs_destroy(h)
+
+    # -- references --------------------------------------------------------
+    def release_job(self, job_id: int) -> None:
+        with self.lock:
+            h = self.refs.pop(job_id, None)
+        if h is not None:
+            self.qs.qs_destroy(h)
+
+    def _reference(self, w: int, job: inputs.Job, dtype: int):
+        """Ideal output of a job (batch-1 handle on worker w's reference stream, synchronised)."""
+        from . import circuits as pc
+        with self.lock:
+            h = self.refs.get(job.job_id)
+        if h is not None:
+            return h
+        h = pc.ideal_reference(job.n, inputs.job_ops(job), inputs.job_initial_basis(job), dtype,
+                               self.ref_streams[w])
+        with self.lock:
+            if job.job_id in self.refs:          # built concurrently by another worker
+                other, h = h, self.refs[job.job_id]
+            else:
+                self.refs[job.job_id] = h
+                other = None
+        if other is not None:
+            self.qs.qs_destroy(other)
+        return h
+
+    # -- units -------------------------------------------------------------
+    def run(self, w: int, unit: Unit, jobs: Dict[int, JobState]) -> List[np.ndarray]:
+        if unit.kind == "rank":
+            return self._run_rank(w, unit, jobs)
+        return self._run_mc(w, unit, jobs)
+
+    def _run_rank(self, w, unit, jobs):
+        qs = self.qs
+        from . import circuits as pc
+        job = jobs[unit.slices[0].job_id].job
+        ref = self._reference(w, job, qs.QS_C128)
+        ent = self._checkout(unit.cache_key)
+        if ent is None:
+            h = qs.qs_create(job.n, 1, job.rank, qs.QS_FIXED_RANK, qs.QS_C128, self.streams[w])
+            ent = (h, None, unit.bytes)
+        h = ent[0]
+        try:
+            qs.qs_set_reference_from(h, ref, 0)
+            qs.qs_set_basis_state(h, inputs.job_initial_basis(job))
+            pc.apply_ops(h, inputs.job_ops(job), job.e, job.seed)
+            out = [qs.qs_fidelity_stored(h)]
+        except BaseException:
+            self._free(h, None)
+            raise
+        self._checkin(unit.cache_key, ent)
+        return out
+
+    def _run_mc(self, w, unit, jobs):
+        qs = self.qs
+        from . import circuits as pc
+        _, circuit, n, iters = unit.key
+        ent = self._checkout(unit.cache_key)
+        if ent is None:
+            # the oracle's phase flip runs per member, so one plan serves every marked item
+            ops = inputs.grover_circuit(n, iters, 1) if circuit == "grover" else inputs.qft_circuit(n)
+            h = qs.qs_create(n, unit.members, 0, qs.QS_STATEVEC, qs.QS_C64, self.streams[w])
+            try:
+                p = qs.qs_plan_create(h, pc.to_gates(ops, per_member_flip=True))
+            except BaseException:
+                qs.qs_destroy(h)
+                raise
+            ent = (h, p, unit.bytes)
+        h, p, _ = ent
+        try:
+            B = unit.members
+            e = np.zeros(B)
+            seed = np.zeros(B, dtype=np.uint64)
+            traj = np.zeros(B, dtype=np.uint64)
+            basis = np.zeros(B, dtype=np.uint64)
+            marked = np.zeros(B, dtype=np.uint64)
+            m, spans = 0, []
+            for sl in unit.slices:
+                job = jobs[sl.job_id].job
+                e[m:m + sl.count] = job.e
+                seed[m:m + sl.count] = job.seed
+                traj[m:m + sl.count] = np.arange(sl.first, sl.first + sl.count, dtype=np.uint64)
+                basis[m:m + sl.count] = inputs.job_initial_basis(job)
+                if circuit == "grover":
+                    marked[m:m + sl.count] = inputs.draw_marked(job.n, job.seed)
+                spans.append((m, sl.count))
+                m += sl.count
+            # padding members rerun the last trajectory; their results are dropped
+            if m < B:
+                e[m:], seed[m:], traj[m:], basis[m:], marked[m:] = e[m - 1], seed[m - 1], traj[m - 1], basis[m - 1], marked[m - 1]
+            qs.qs_set_member_noise(h, e, seed, traj, marked)
+            qs.qs_set_basis_states(h, basis)
+            qs.qs_plan_run(p, 0.0, 0, 0, h)
+            out = []
+            for sl, (first, count) in zip(unit.slices, spans):
+                ref = self._reference(w, jobs[sl.job_id].job, qs.QS_C64)
+                out.append(qs.qs_fidelity_ref(h, ref, first, count))
+        except BaseException:
+            self._free(h, p)
+            raise
+        self._checkin(unit.cache_key, ent)
+        return out
+
+
+# ------------------------------------------------------------------ the server
+@dataclass
+class JobResult:
+    job_id: int
+    fidelities: np.ndarray
+    arrival: float
+    finish: float
+
+    @property
+    def latency(self) -> float:
+        return self.finish - self.arrival
+
+
+class Server:
+    """Request loop: admission, batching and overlapped execution of jobs."""
+
+    def __init__(self, executor=None, workers: int = 4, budget_bytes: Optional[int] = None,
+                 reserve_bytes: int = 8 << 30, max_members: int = 4096, min_bucket: int = 16):
+        if executor is None:
+            executor = GpuExecutor(workers)
+        if budget_bytes is None:
+            import torch
+            free, _ = torch.cuda.mem_get_info()
+            budget_bytes = max(free - reserve_bytes - getattr(executor, "cache_bytes", 0), 1 << 28)
+        self.ex = executor
+        self.sched = Scheduler(budget_bytes, max_members, min_bucket)
+        self.lock = threading.Condition()
+        self.t0 = time.perf_counter()
+        self.results: Dict[int, JobResult] = {}
+        self.errors: List[BaseException] = []
+        self.free_workers = list(range(executor.workers))
+        self.stop = False
+        self.threads: List[threading.Thread] = []
+        self.dispatcher = threading.Thread(target=self._dispatch, daemon=True)
+        self.dispatcher.start()
+
+    def now(self) -> float:
+        return time.perf_counter() - self.t0
+
+    def submit(self, job: inputs.Job) -> None:
+        with self.lock:
+            self.sched.submit(job, self.now())
+            self.lock.notify_all()
+
+    def _dispatch(self):
+        while True:
+            with self.lock:
+                while not self.stop and not (self.free_workers and self.sched.pending()):
+                    self.lock.wait(0.05)
+                if self.stop:
+                    return
+                try:
+                    unit = self.sched.next_unit(self.now())
+                except BaseException as exc:               # a job that can never fit
+                    self.errors.append(exc)
+                    self.stop = True
+                    self.lock.notify_all()
+                    return
+                if unit is None:
+                    self.lock.wait(0.01)
+                    continue
+                w = self.free_workers.pop()
+                th = threading.Thread(target=self._work, args=(w, unit), daemon=True)
+                self.threads.append(th)
+                th.start()
+
+    def _work(self, w: int, unit: Unit):
+        try:
+            res = self.ex.run(w, unit, self.sched.jobs)
+            err = None
+        except BaseException as exc:
+            res, err = None, exc
+        with self.lock:
+            if err is not None:
+                self.errors.append(err)
+                self.stop = True
+            else:
+                done = self.sched.complete(unit, res, self.now())
+                for jid in done:
+                    st = self.sched.jobs[jid]
+                    self.results[jid] = JobResult(jid, st.fidelities, st.arrival, st.finish)
+                    self.ex.release_job(jid)
+            self.free_workers.append(w)
+            self.lock.notify_all()
+
+    def drain(self, timeout: float = 600.0) -> Dict[int, JobResult]:
+        end = time.perf_counter() + timeout
+        with self.lock:
+            while self.sched.busy() and not self.stop:
+                left = end - time.perf_counter()
+                if left <= 0:
+                    raise TimeoutError("server did not finish its jobs in time")
+                self.lock.wait(min(left, 0.05))
+        if self.errors:
+            raise self.errors[0]
+        return dict(self.results)
+
+    def close(self):
+        with self.lock:
+            self.stop = True
+            self.lock.notify_all()
+        self.dispatcher.join(timeout=5)
+        for th in self.threads:
+            th.join(timeout=60)
+        self.ex.close()
+
+
+def run_stream(jobs: List[inputs.Job], server: Server, time_scale: float = 1.0, timeout: float = 600.0):
+    """Submit jobs at their (scaled) arrival times; return results and statistics."""
+    t_start = server.now()
+    for job in sorted(jobs, key=lambda j: j.arrival_s):
+        delay = t_start + job.arrival_s * time_scale - server.now()
+        if delay > 0:
+            time.sleep(delay)
+        server.submit(job)
+    results = server.drain(timeout)
+    lat = np.array([r.latency for r in results.values()])
+    span = max(r.finish for r in results.values()) - t_start
+    circuits = sum(len(r.fidelities) for r in results.values())
+    stats = {"jobs": len(results), "circuits": int(circuits), "span_s": span,
+             "circuits_per_s": circuits / span if span > 0 else math.inf,
+             "jobs_per_s": len(results) / span if span > 0 else math.inf,
+             "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+             "peak_budget_used": server.sched.peak_used, "budget": server.sched.budget}
+    return results, stats

@@ -1,0 +1,179 @@
+"""Scheduler and request loop of the continuous-batching server, on the CPU.
+
+A fake executor stands in for the GPU: it sleeps for a time that grows with
+the launch and returns a value that names the job and trajectory, so every
+result can be traced back to the work that made it."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_1412_2293_gb300 import inputs
+from paper_1412_2293_gb300.server import (Scheduler, Server, Unit, bucket_for, largest_bucket,
+                                          member_bytes, rank_bytes, run_stream)
+
+
+def job(i, n=12, traj=64, circuit="qft", mode="statevec", rank=0, arrival=0.0, iters=0):
+    return inputs.Job(i, arrival, circuit, n, mode, traj if mode == "statevec" else 1, rank,
+                      1e-3, 1000 + i, iters)
+
+
+def value(job_id, t):
+    return job_id + t * 1e-6
+
+
+class FakeExecutor:
+    def __init__(self, workers=3, sec_per_member=2e-6):
+        self.workers = workers
+        self.sec = sec_per_member
+        self.lock = threading.Lock()
+        self.running = 0
+        self.max_running = 0
+        self.units = []
+        self.released = []
+
+    def run(self, w, unit, jobs):
+        with self.lock:
+            self.running += 1
+            self.max_running = max(self.max_running, self.running)
+            self.units.append(unit)
+        time.sleep(0.002 + self.sec * unit.members)
+        out = []
+        for sl in unit.slices:
+            if unit.kind == "rank":
+                out.append(np.array([value(sl.job_id, 0)]))
+            else:
+                out.append(np.array([value(sl.job_id, t) for t in range(sl.first, sl.first + sl.count)]))
+        with self.lock:
+            self.running -= 1
+        return out
+
+    def release_job(self, job_id):
+        self.released.append(job_id)
+
+    def close(self):
+        pass
+
+
+def test_buckets():
+    assert bucket_for(1, 16, 4096) == 16
+    assert bucket_for(17, 16, 4096) == 32
+    assert bucket_for(5000, 16, 4096) == 4096
+    assert largest_bucket(1000, 4096) == 512
+    assert largest_bucket(0, 4096) == 0
+    assert largest_bucket(10 ** 9, 4096) == 4096
+
+
+def test_same_shape_jobs_share_one_launch():
+    s = Scheduler(1 << 40)
+    s.submit(job(0, traj=64), 0.0)
+    s.submit(job(1, traj=32), 0.0)
+    s.submit(job(2, n=13, traj=64), 0.0)          # another shape
+    u = s.next_unit()
+    assert u.kind == "mc" and u.key == ("mc", "qft", 12, 0)
+    assert [(x.job_id, x.first, x.count) for x in u.slices] == [(0, 0, 64), (1, 0, 32)]
+    assert u.members == 128
+    u2 = s.next_unit()
+    assert [(x.job_id, x.count) for x in u2.slices] == [(2, 64)]
+    assert s.next_unit() is None
+
+
+def test_large_job_runs_in_waves_and_budget_holds():
+    n = 16
+    per = member_bytes(n)
+    ref = (1 << n) * 8
+    budget = 300 * per + ref
+    s = Scheduler(budget, max_members=4096)
+    s.submit(job(0, n=n, traj=1000), 0.0)
+    units = []
+    while True:
+        u = s.next_unit()
+        if u is None:
+            break
+        units.append(u)
+    # the reference is held for the job's lifetime; the other 300 members' room
+    # takes the largest power-of-two launches that fit
+    assert [u.members for u in units] == [256, 32]
+    assert s.used <= budget
+    covered = []
+    for u in units:
+        s.complete(u, [np.zeros(u.slices[0].count)], 1.0)
+        covered.append((u.slices[0].first, u.slices[0].count))
+    while s.busy():
+        u = s.next_unit()
+        assert u is not None and s.used <= budget
+        covered.append((u.slices[0].first, u.slices[0].count))
+        s.complete(u, [np.zeros(u.slices[0].count)], 2.0)
+    starts = [c[0] for c in covered]
+    assert starts == sorted(starts) and sum(c[1] for c in covered) == 1000
+    assert s.used == 0 and s.finished == [0]
+
+
+def test_job_that_can_never_fit_is_refused():
+    s = Scheduler(1 << 20)
+    with pytest.raises(MemoryError):
+        s.submit(job(0, n=20, traj=64), 0.0)
+    with pytest.raises(MemoryError):
+        s.submit(job(1, n=16, mode="fixed_rank", rank=4), 0.0)
+    with pytest.raises(ValueError):
+        s.submit(inputs.Job(2, 0.0, "qft", 10, "density", 1, 0, 1e-3, 1, 0), 0.0)
+
+
+def test_backfill_stops_when_the_oldest_job_starves():
+    n = 14
+    big = rank_bytes(18, 8)
+    # one 16-member launch with its reference beside the rank job, less a byte
+    s = Scheduler(big + 16 * member_bytes(n) + (1 << n) * 8 - 1, starve_s=1.0)
+    s.submit(job(0, n=14, traj=16), 0.0)
+    u0 = s.next_unit(0.0)                         # occupies memory
+    s.submit(job(1, n=18, mode="fixed_rank", rank=8), 0.0)
+    s.submit(job(2, n=14, traj=16), 0.0)
+    assert s.next_unit(0.5).slices[0].job_id == 2  # backfill while job 1 is young
+    s.submit(job(3, n=14, traj=16), 0.6)
+    assert s.next_unit(1.5) is None               # job 1 waited too long: no backfill
+    s.complete(u0, [np.zeros(16)], 1.6)
+    assert s.next_unit(1.6) is None               # still not enough room for job 1
+    for uid in list(s.in_flight):
+        s.complete(s.in_flight[uid], [np.zeros(16)], 1.7)
+    u = s.next_unit(1.7)
+    assert u.kind == "rank" and u.slices[0].job_id == 1
+
+
+def test_server_runs_a_job_stream_with_overlap():
+    jobs = inputs.draw_job_stream(60, rate_per_s=2000.0, seed=7, n_range=(10, 14), log2_traj_range=(4, 10),
+                                  max_rank=4)
+    ex = FakeExecutor(workers=3)
+    budget = 64 << 20
+    srv = Server(ex, budget_bytes=budget, max_members=256)
+    try:
+        results, stats = run_stream(jobs, srv, time_scale=1.0, timeout=60)
+    finally:
+        srv.close()
+    assert stats["jobs"] == len(jobs)
+    for j in jobs:
+        r = results[j.job_id]
+        expect = np.array([value(j.job_id, t) for t in range(j.trajectories)])
+        np.testing.assert_array_equal(r.fidelities, expect)     # every trajectory exactly once, in place
+        assert r.finish >= r.arrival
+    assert sorted(ex.released) == sorted(j.job_id for j in jobs)
+    assert ex.max_running >= 2                                   # work overlaps
+    assert srv.sched.peak_used <= budget and srv.sched.used == 0
+    # launches mixed jobs of one shape
+    assert any(len(u.slices) > 1 for u in ex.units)
+    assert all(u.members & (u.members - 1) == 0 for u in ex.units if u.kind == "mc")
+    assert stats["latency_p99_s"] >= stats["latency_p50_s"] > 0
+
+
+def test_executor_error_surfaces():
+    class Broken(FakeExecutor):
+        def run(self, w, unit, jobs):
+            raise RuntimeError("device call failed")
+
+    srv = Server(Broken(workers=2), budget_bytes=1 << 30)
+    try:
+        srv.submit(job(0))
+        with pytest.raises(RuntimeError, match="device call failed"):
+            srv.drain(timeout=10)
+    finally:
+        srv.close()
