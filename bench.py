@@ -112,7 +112,7 @@ def measured_peaks():
 
 def plan_source_hash():
     h = hashlib.sha256()
-    for f in ("plan.cu", "internal.cuh", "philox.cuh"):
+    for f in ("plan.cu", "pass.cuh", "internal.cuh", "philox.cuh"):
         with open(os.path.join(ROOT, "paper_1412_2293_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -420,7 +420,36 @@ def extra_rows(h, n, T, esize, stream, peaks):
         "circuit_channels": total_noisy,
         "circuits_per_s_extrapolated": round(1e3 / (per_ch * total_noisy), 4),
         "note": "time of a bounded run of channels (expand, FP64 Gram, FP64 Jacobi, projection) x channels"}
+
+    out["a11_serving"] = serving_row()
     return out
+
+
+def serving_row(num_jobs=100, rate_per_s=200.0, workers=4):
+    """Continuous batching of a mixed stream of fidelity-estimation jobs.
+
+    Poisson arrivals of Grover and QFT jobs, half Monte Carlo (2^6..2^10
+    complex64 trajectories) and half fixed rank (r <= 8, complex128), n from 12
+    to 20, e log-uniform in [1e-4, 1e-2].  Wall-clock throughput and latency
+    from arrival to the job's last fidelity on the host."""
+    from paper_1412_2293_gb300 import inputs
+    from paper_1412_2293_gb300.server import GpuExecutor, Server, run_stream
+    jobs = inputs.draw_job_stream(num_jobs, rate_per_s, seed=inputs.DEFAULT_SEED, n_range=(12, 20),
+                                  log2_traj_range=(6, 10), max_rank=8)
+    srv = Server(GpuExecutor(workers=workers), max_members=1024)
+    try:
+        _, stats = run_stream(jobs, srv, time_scale=1.0, timeout=600)
+        units, max_run = srv.sched._uid, srv.sched.max_in_flight
+    finally:
+        srv.close()
+    mc = [j for j in jobs if j.mode == "statevec"]
+    return {"jobs": stats["jobs"], "mc_jobs": len(mc), "fixed_rank_jobs": len(jobs) - len(mc),
+            "circuits": stats["circuits"], "arrival_rate_per_s": rate_per_s, "workers": workers,
+            "launch_units": units, "max_units_in_flight": max_run,
+            "span_s": round(stats["span_s"], 3), "circuits_per_s": round(stats["circuits_per_s"], 1),
+            "jobs_per_s": round(stats["jobs_per_s"], 2), "latency_p50_s": round(stats["latency_p50_s"], 4),
+            "latency_p99_s": round(stats["latency_p99_s"], 4),
+            "stream": "n 12..20, MC 2^6..2^10 trajectories c64, fixed rank r 1..8 c128, Grover iterations capped at 16"}
 
 
 # ------------------------------------------------------------------ density / fixed rank
