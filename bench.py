@@ -147,7 +147,7 @@ def run_ours(args, rank, world, local_rank):
 
     from paper_1412_2293_gb300 import build as qbuild
     from paper_1412_2293_gb300 import circuits as pcirc
-    from paper_1412_2293_gb300 import qs
+    from paper_1412_2293_gb300 import qs, shard
 
     dist = None
     if world > 1:
@@ -160,7 +160,7 @@ def run_ours(args, rank, world, local_rank):
     dtype = qs.QS_C64 if W.dtype == "c64" else qs.QS_C128
     esize = 8 if dtype == qs.QS_C64 else 16
     stream = torch.cuda.Stream()
-    traj0 = rank * T                                    # weak scaling: each rank its own trajectories
+    traj0, _ = shard.trajectory_range(rank, T)          # weak scaling: each rank its own trajectories
     h = qs.qs_create(n, T, 0, qs.QS_STATEVEC, dtype, stream)
     ref = pcirc.ideal_reference(n, ops, x0, dtype, stream)
     qs.qs_set_reference_from(h, ref, 0)
@@ -206,13 +206,9 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     if sampler:
         sampler.mark(1)
-    elapsed_ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = shard.max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
     ms_per_step = elapsed_ms / args.steps
-    value = updates_per_step * world / (ms_per_step / 1e3)
+    value = shard.job_throughput(updates_per_step, world, ms_per_step / 1e3)
     clocks = sampler.stop() if sampler else None
 
     # end to end through the C ABI with host buffers: every step uploads the
@@ -237,12 +233,8 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.steps):
         fid_e2e = step_e2e()
     torch.cuda.synchronize()
-    t_e2e = (time.perf_counter() - t0) / args.steps
-    if dist is not None:
-        t = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e_value = updates_per_step * world / t_e2e
+    t_e2e = shard.max_over_ranks((time.perf_counter() - t0) / args.steps, dist, "cuda")
+    e2e_value = shard.job_throughput(updates_per_step, world, t_e2e)
     assert np.allclose(fid_e2e, fid, atol=1e-6), "end-to-end run disagrees with the device-resident run"
 
     # roofline of the dominant kernel (the fused pass with the most time).
