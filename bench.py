@@ -168,6 +168,9 @@ def run_ours(args, rank, world, local_rank):
     qs.qs_set_trajectory_offset(h, traj0)
     p = qs.qs_plan_create(h, pcirc.to_gates(ops))
     passes, launches = qs.qs_plan_info(p, h)
+    # kernel configuration of the passes: the fastest on this plan (eager runs, untimed)
+    tune_ms = qs.qs_plan_autotune(p, 2, e, seed, h)
+    kernel_cfg = qs.qs_plan_get_config(p, h)
     qs.qs_plan_set_timing(p, True, h)
     updates_per_step = T * (1 << n) * len(ops)
 
@@ -263,6 +266,8 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": args.workload, "circuit": W.circuit, "n": n, "trajectories_per_gpu": T,
                    "gates": len(ops), "e": e, "noise": "rotation (H), phase (CP), Philox on device",
                    "passes_per_step": passes, "parallelism": f"trajectories sharded over {world} GPU(s)",
+                   "kernel_config": {"low": kernel_cfg[0], "high": kernel_cfg[1],
+                                     "autotune_ms": [round(x, 4) for x in tune_ms]},
                    "circuits_per_s": T * world / (ms_per_step / 1e3),
                    "state_bytes": T * (1 << n) * esize,
                    "l2": "inputs larger than L2 (state of every step is %d MiB)" % (T * (1 << n) * esize >> 20),

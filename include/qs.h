@@ -254,6 +254,25 @@ qs_status qs_plan_profile(qs_plan p, int reps, double e, uint64_t seed, uint64_t
 qs_status qs_plan_set_timing(qs_plan p, int on);
 qs_status qs_plan_last_times(qs_plan p, double* ms, int* kinds, int cap, int* count);
 
+/* Kernel configuration of the fused passes (no counterpart in the paper: the
+ * tiling of the update, Sec. 2, is the implementation's).  For each window
+ * geometry (low: qubits 0..9, high: the 10 highest) a configuration index in
+ * [0, count): complex64 has two of each -- low 0: 12 warps, two tile buffers
+ * per warp; low 1: 16 warps, one buffer; high 0: one block per SM, two
+ * buffers; high 1: two blocks per SM, one buffer -- complex128 one of each.
+ * Results do not depend on the configuration.  qs_plan_configs returns the
+ * counts; qs_plan_set_config rejects an index out of range with
+ * QS_ERR_INVALID_ARG; qs_plan_get_config returns the current choice. */
+qs_status qs_plan_configs(qs_plan p, int* low_count, int* high_count);
+qs_status qs_plan_set_config(qs_plan p, int low_cfg, int high_cfg);
+qs_status qs_plan_get_config(qs_plan p, int* low_cfg, int* high_cfg);
+/* Autotune: time every configuration on this plan (qs_plan_profile with
+ * `reps` runs each, noise e and key seed), keep the fastest per geometry and
+ * write its mean pass time in ms to best_ms[0] (low) and best_ms[1] (high)
+ * (-1 where the plan has no pass of that geometry; best_ms may be NULL).
+ * The runs overwrite the state: set the start state afterwards.  Synchronises. */
+qs_status qs_plan_autotune(qs_plan p, int reps, double e, uint64_t seed, double* best_ms);
+
 /* ------------------------------------------------------------ utilities */
 
 /* The Philox4x32-10 words and normals the device draws for (seed, traj,

@@ -100,6 +100,11 @@ struct PassArgs {
   int fid;
   const void* ref;            // 2^n reference amplitudes
   double* fid_partials;       // [member][tile in member] complex
+  // real one-qubit gates run with their diagonal factored out (see
+  // butterfly_fact); the factors left at the end of the pass are applied
+  // there: per member, diag_off (R units) holds ratio_j = d_j / a_j for each
+  // window bit j and the overall scale prod_j a_j; -1 when the pass has none
+  int diag_off;
 };
 
 // ---------------------------------------------------------------- async copies
@@ -155,37 +160,32 @@ __device__ __forceinline__ cplx<R> ld_c(const R* p) { return __ldg(reinterpret_c
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// Real 2x2 on a complex pair: both components scaled by the same real entry,
-// so complex64 uses the packed two-lane FP32 FMA (one instruction per output
-// amplitude and matrix entry).
+// A real 2x2 gate [[a, b], [c, d]] written as diag(a, d) [[1, r0], [r1, 1]],
+// r0 = b / a, r1 = c / d: one FMA per output component (packed two-lane for
+// complex64).  The diagonal commutes with every diagonal operation of the
+// pass; the precompute folds it into the next gate on the same qubit or
+// leaves it for the end of the pass (PassArgs::diag_off).
 template <typename R>
-__device__ __forceinline__ void butterfly_real(cplx<R>& x0, cplx<R>& x1, R u00, R u01, R u10, R u11) {
+__device__ __forceinline__ void butterfly_fact(cplx<R>& x0, cplx<R>& x1, R r0, R r1) {
   if constexpr (sizeof(R) == 4) {
     const float2 a = x0, b = x1;
-    x0 = fma2(make_float2(u01, u01), b, mul2(make_float2(u00, u00), a));
-    x1 = fma2(make_float2(u11, u11), b, mul2(make_float2(u10, u10), a));
+    x0 = fma2(make_float2(r0, r0), b, a);
+    x1 = fma2(make_float2(r1, r1), a, b);
   } else {
     const cplx<R> a = x0, b = x1;
-    x0 = mk<R>(u00 * a.x + u01 * b.x, u00 * a.y + u01 * b.y);
-    x1 = mk<R>(u10 * a.x + u11 * b.x, u10 * a.y + u11 * b.y);
+    x0 = mk<R>(fma(r0, b.x, a.x), fma(r0, b.y, a.y));
+    x1 = mk<R>(fma(r1, a.x, b.x), fma(r1, a.y, b.y));
   }
 }
 
 template <typename R, int RJ>
 __device__ __forceinline__ void dense_reg(cplx<R> (&a)[kAmps], const R* m, bool real) {
   if (real) {
-    R u00, u01, u10, u11;
-    if constexpr (sizeof(R) == 4) {                     // the 2x2 block is 32-byte aligned
-      const float4 r0 = __ldg(reinterpret_cast<const float4*>(m));
-      const float4 r1 = __ldg(reinterpret_cast<const float4*>(m) + 1);
-      u00 = r0.x; u01 = r0.z; u10 = r1.x; u11 = r1.z;
-    } else {
-      u00 = __ldg(m); u01 = __ldg(m + 2); u10 = __ldg(m + 4); u11 = __ldg(m + 6);
-    }
+    const cplx<R> rr = ld_c(m);                         // (r0, r1)
 #pragma unroll
     for (int r = 0; r < kAmps; ++r) {
       if (r & (1 << RJ)) continue;
-      butterfly_real<R>(a[r], a[r | (1 << RJ)], u00, u01, u10, u11);
+      butterfly_fact<R>(a[r], a[r | (1 << RJ)], rr.x, rr.y);
     }
   } else {
     const cplx<R> u00 = ld_c(m), u01 = ld_c(m + 2), u10 = ld_c(m + 4), u11 = ld_c(m + 6);
@@ -204,15 +204,18 @@ __device__ __forceinline__ void dense_reg(cplx<R> (&a)[kAmps], const R* m, bool 
 template <typename R, int RJ, bool STAGE_A>
 __device__ __forceinline__ void dwin_reg(cplx<R> (&a)[kAmps], const R* T, int tbits) {
   constexpr int Q = 1 << RJ;
-  cplx<R> f[Q];
+  // factor q multiplies the registers with bit RJ set and low bits q; each
+  // factor is consumed right after its load (few live registers)
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int idx = STAGE_A ? (tbits | (q << 5)) : q;
-    f[q] = ld_c(T + 2 * idx);
-  }
+    const cplx<R> f = ld_c(T + 2 * idx);
 #pragma unroll
-  for (int r = 0; r < kAmps; ++r)
-    if (r & (1 << RJ)) a[r] = cmul(f[r & (Q - 1)], a[r]);
+    for (int hi = 0; hi < kAmps / (2 * Q); ++hi) {
+      const int r = q | Q | (hi << (RJ + 1));
+      a[r] = cmul(f, a[r]);
+    }
+  }
 }
 
 template <typename R>
@@ -237,6 +240,35 @@ __device__ __forceinline__ void apply_reg_product(cplx<R> (&a)[kAmps], cplx<R> c
   for (int r = 0; r < 16; ++r) a[r] = cmul(t[r], a[r]);
 #pragma unroll
   for (int r = 0; r < 16; ++r) a[r + 16] = cmul(cmul(t[r], al[4]), a[r + 16]);
+}
+
+// a[rho] *= c * prod_{r in rho} t[r] for real factors (the deferred diagonals
+// of the pass's real gates), by the same doubling over register bits 0..3
+template <typename R>
+__device__ __forceinline__ void apply_real_product(cplx<R> (&a)[kAmps], R c, const R (&t5)[kRegBits]) {
+  R t[16];
+  t[0] = c;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < (1 << r); ++q) t[q | (1 << r)] = t[q] * t5[r];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const R lo = t[r], hi = t[r] * t5[4];
+    if constexpr (sizeof(R) == 4) {
+      a[r] = mul2(make_float2(lo, lo), a[r]);
+      a[r + 16] = mul2(make_float2(hi, hi), a[r + 16]);
+    } else {
+      a[r] = mk<R>(lo * a[r].x, lo * a[r].y);
+      a[r + 16] = mk<R>(hi * a[r + 16].x, hi * a[r + 16].y);
+    }
+  }
+}
+
+// deferred diagonal of window bit a (0..9), or the overall scale (a = 10)
+template <typename R>
+__device__ __forceinline__ R diag_factor_of(const PassArgs& A, const R* P, int a) {
+  return A.diag_off >= 0 ? __ldg(P + A.diag_off + a) : R(1);
 }
 
 // product of the out terms of attach a whose out-of-window bits are set in `fixed`
@@ -281,37 +313,53 @@ __device__ __forceinline__ void run_seg(cplx<R> (&a)[kAmps], const Seg& sg, cons
 }
 
 // ---------------------------------------------------------------- LOW pass
-// Window = qubits 0..9.  Each warp streams a contiguous range of tiles of 1024
-// consecutive amplitudes (consecutive tiles mostly share a member, so its
-// parameters stay in L1) through two shared-memory buffers filled by bulk
-// copies.  Register exchanges happen in place in the current buffer with an
-// XOR swizzle, x -> x ^ ((x >> 5) & 15), under which both register layouts
+// Window = qubits 0..9.  Each warp streams tiles of 1024 consecutive
+// amplitudes (every WARPS-th tile of its block's range, so the block's warps
+// work on neighbouring tiles of one member and share its parameters in L1)
+// through one or two shared-memory buffers filled by bulk copies.  Register
+// exchanges happen in place in the current buffer with an XOR swizzle,
+// x -> x ^ ((x >> 5) & 15), under which both register layouts
 // (stage A: x = lane + 32 r, stage B: x = r + 32 lane) are free of bank
 // conflicts; stores are coalesced from the stage-A layout.
-template <int WARPS> struct LowShape {
-  static constexpr int PER_WARP = 2 * 1024 + 12;       // two tile buffers + out factors
+template <int WARPS, int NBUF> struct LowShape {
+  static constexpr int PER_WARP = NBUF * 1024 + 12;    // tile buffers + out factors
   static constexpr int THREADS = WARPS * 32;
 };
 
+// Shared-memory reads of a tile after its first one: one per register
+// exchange of the program (and, for the low window, the exchange back to the
+// store layout when the program ends in stage B).  With a single tile buffer
+// the next tile's copy may start once the last of them is done.
+__device__ __forceinline__ int exchange_count(const PassArgs& A, int stage, bool back_to_a) {
+  int n = 0;
+  for (int si = 0; si < A.nseg; ++si)
+    if (A.segs[si].stage != stage) { ++n; stage ^= 1; }
+  if (back_to_a && stage == 1) ++n;
+  return n;
+}
+
 __device__ __forceinline__ int low_swz(int x) { return x ^ ((x >> 5) & 15); }
 
-template <typename R, int WARPS>
+template <typename R, int WARPS, int NBUF>
 __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict__ psi, const __grid_constant__ PassArgs A) {
+  static_assert(NBUF == 1 || NBUF == 2, "one or two tile buffers");
   using C = cplx<R>;
-  using S = LowShape<WARPS>;
+  using S = LowShape<WARPS, NBUF>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[WARPS][2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   C* wbase = reinterpret_cast<C*>(smem_raw) + (size_t)warp * S::PER_WARP;
-  C* alpha_sm = wbase + 2048;
+  C* alpha_sm = wbase + NBUF * 1024;
   const uint64_t nmask = (1ull << A.n) - 1;
   const R* params = static_cast<const R*>(A.params);
   const uint32_t tile_bytes = 1024u * (uint32_t)sizeof(C);
-  const uint64_t nwarps = (uint64_t)gridDim.x * WARPS;
-  const uint64_t gw = (uint64_t)blockIdx.x * WARPS + warp;
-  const uint64_t per = (A.tiles + nwarps - 1) / nwarps;
-  const uint64_t first = gw * per;
-  const uint64_t last = first + per < A.tiles ? first + per : A.tiles;
+  // a block owns a contiguous range of tiles; its warps take them in turn, so
+  // at any time they work on neighbouring tiles of one member and share that
+  // member's parameters in L1
+  const uint64_t per = (A.tiles + gridDim.x - 1) / gridDim.x;
+  const uint64_t bfirst = (uint64_t)blockIdx.x * per;
+  const uint64_t last = bfirst + per < A.tiles ? bfirst + per : A.tiles;
+  const uint64_t first = bfirst + warp;
 
   if (lane == 0) {
     mbar_init(&bars[warp][0], 1);
@@ -324,16 +372,34 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
     bulk_g2s(wbase, psi + (first << kWin), tile_bytes, &bars[warp][0]);
   }
   int in_flight = (!A.synth && first < last) ? 1 : 0;
+  const int nx = NBUF == 1 ? exchange_count(A, 0, true) : 0;
   uint32_t it = 0;
-  for (uint64_t t = first; t < last; ++t, ++it) {
-    const int cur = it & 1;
+  for (uint64_t t = first; t < last; t += WARPS, ++it) {
+    const int cur = NBUF == 2 ? (int)(it & 1) : 0;
+    const uint32_t parity = NBUF == 2 ? ((it >> 1) & 1) : (it & 1);
     C* cbuf = wbase + cur * 1024;
-    if (!A.synth && lane == 0 && t + 1 < last) {
+    const uint64_t tn = t + WARPS;                      // this warp's next tile
+    if (NBUF == 2 && !A.synth && lane == 0 && tn < last) {
       fence_proxy_async();
       mbar_expect_tx(&bars[warp][cur ^ 1], tile_bytes);
-      bulk_g2s(wbase + (cur ^ 1) * 1024, psi + ((t + 1) << kWin), tile_bytes, &bars[warp][cur ^ 1]);
+      bulk_g2s(wbase + (cur ^ 1) * 1024, psi + (tn << kWin), tile_bytes, &bars[warp][cur ^ 1]);
       ++in_flight;
     }
+    // single buffer: start the next tile's copy once this tile's last shared read is done
+    int reads_left = nx;
+    auto release = [&]() {
+      if constexpr (NBUF == 1) {
+        if (--reads_left == 0 && !A.synth) {
+          fence_proxy_async();
+          __syncwarp();
+          if (lane == 0 && tn < last) {
+            mbar_expect_tx(&bars[warp][0], tile_bytes);
+            bulk_g2s(wbase, psi + (tn << kWin), tile_bytes, &bars[warp][0]);
+            ++in_flight;
+          }
+        }
+      }
+    };
     const uint64_t base = t << kWin;
     const uint64_t member = base >> A.n;
     const uint64_t mloc = base & nmask;
@@ -345,14 +411,15 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
       for (int r = 0; r < kAmps; ++r)
         a[r] = mk<R>((mloc | (uint64_t)(lane + 32 * r)) == x ? R(1) : R(0), R(0));
     } else {
-      if (!mbar_wait(&bars[warp][cur], (it >> 1) & 1)) {
+      if (!mbar_wait(&bars[warp][cur], parity)) {
         report_timeout(A.status);
-        if (lane == 0 && in_flight > 1) mbar_wait(&bars[warp][cur ^ 1], ((it + 1) >> 1) & 1);
+        if (NBUF == 2 && lane == 0 && in_flight > 1) mbar_wait(&bars[warp][cur ^ 1], ((it + 1) >> 1) & 1);
         return;
       }
       if (lane == 0) --in_flight;
 #pragma unroll
       for (int r = 0; r < kAmps; ++r) a[r] = cbuf[lane + 32 * r];
+      if constexpr (NBUF == 1) { ++reads_left; release(); }   // counts the first read
     }
     int stage = 0;
     for (int si = 0; si < A.nseg; ++si) {
@@ -373,6 +440,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
           for (int r = 0; r < kAmps; ++r) a[r] = cbuf[low_swz(lane + 32 * r)];
         }
         stage ^= 1;
+        release();
       }
       if (stage == 0) run_seg<R, true>(a, sg, P, lane);
       else run_seg<R, false>(a, sg, P, 0);
@@ -385,7 +453,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
       }
     }
     if (A.out_start[11] > 0) {
-      if (lane < 11) alpha_sm[lane] = out_alpha<R>(A, P, lane, mloc);
+      if (lane < 11) {
+        const C f = out_alpha<R>(A, P, lane, mloc);
+        const R d = diag_factor_of<R>(A, P, lane);
+        alpha_sm[lane] = mk<R>(f.x * d, f.y * d);
+      }
       __syncwarp();
       C al[kRegBits];
       C c = alpha_sm[10];
@@ -395,6 +467,16 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
         if ((lane >> r) & 1) c = cmul(c, alpha_sm[stage == 0 ? r : r + 5]);
       }
       apply_reg_product<R>(a, c, al);
+    } else if (A.diag_off >= 0) {
+      const R* dg = P + A.diag_off;
+      R t5[kRegBits];
+      R c = __ldg(dg + 10);
+#pragma unroll
+      for (int r = 0; r < kRegBits; ++r) {
+        t5[r] = __ldg(dg + (stage == 0 ? r + 5 : r));
+        if ((lane >> r) & 1) c *= __ldg(dg + (stage == 0 ? r : r + 5));
+      }
+      apply_real_product<R>(a, c, t5);
     }
     if (stage == 1) {
       __syncwarp();
@@ -403,6 +485,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
       __syncwarp();
 #pragma unroll
       for (int r = 0; r < kAmps; ++r) a[r] = cbuf[low_swz(lane + 32 * r)];
+      release();
     }
     if (A.fid) {
       const C* ref = static_cast<const C*>(A.ref) + mloc;
@@ -450,16 +533,17 @@ __device__ __forceinline__ int high_idx(int x, int col) {
   else return e;
 }
 
-template <typename R, int COLB>
-__global__ void __launch_bounds__(HighShape<COLB>::THREADS, 1)
+template <typename R, int COLB, int NBUF>
+__global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 2 : 1)
     k_pass_high(cplx<R>* __restrict__ psi, const __grid_constant__ CUtensorMap tmap, const __grid_constant__ PassArgs A) {
+  static_assert(NBUF == 1 || NBUF == 2, "one or two tile buffers");
   using C = cplx<R>;
   using S = HighShape<COLB>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ double fid_red[2][S::WARPS];
   C* smbase = reinterpret_cast<C*>(smem_raw);
-  C* alpha_sm = smbase + 2 * S::TILE;                   // [COLS][12]
+  C* alpha_sm = smbase + NBUF * S::TILE;                // [COLS][12]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int col = lane & (S::COLS - 1);
   const int lh = lane >> COLB;
@@ -494,14 +578,30 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, 1)
   };
   if (!A.synth && threadIdx.x == 0 && first < last) issue(first, 0);
   int in_flight = (!A.synth && first < last) ? 1 : 0;
+  const int nx = NBUF == 1 ? exchange_count(A, A.start_stage, false) : 0;
   uint32_t it = 0;
   for (uint64_t t = first; t < last; ++t, ++it) {
-    const int cur = it & 1;
-    if (!A.synth && threadIdx.x == 0 && t + 1 < last) {
+    const int cur = NBUF == 2 ? (int)(it & 1) : 0;
+    const uint32_t parity = NBUF == 2 ? ((it >> 1) & 1) : (it & 1);
+    if (NBUF == 2 && !A.synth && threadIdx.x == 0 && t + 1 < last) {
       fence_proxy_async();
       issue(t + 1, cur ^ 1);
       ++in_flight;
     }
+    // single buffer: start the next tile's copy once this tile's last shared read is done
+    int reads_left = nx;
+    auto release = [&]() {
+      if constexpr (NBUF == 1) {
+        if (--reads_left == 0 && !A.synth) {
+          fence_proxy_async();
+          __syncthreads();
+          if (threadIdx.x == 0 && t + 1 < last) {
+            issue(t + 1, 0);
+            ++in_flight;
+          }
+        }
+      }
+    };
     const uint64_t member = t >> A.tile_shift;
     const uint64_t tl = t & ((1ull << A.tile_shift) - 1);
     const uint32_t tbits = (uint32_t)(tl << COLB);      // the other bits are COLB .. n-11
@@ -517,9 +617,9 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, 1)
       for (int r = 0; r < kAmps; ++r)
         a[r] = mk<R>((uint64_t)(fixed | ((uint32_t)r << sh)) == x ? R(1) : R(0), R(0));
     } else {
-      if (!mbar_wait(&bars[cur], (it >> 1) & 1)) {
+      if (!mbar_wait(&bars[cur], parity)) {
         report_timeout(A.status);
-        if (threadIdx.x == 0 && in_flight > 1) mbar_wait(&bars[cur ^ 1], ((it + 1) >> 1) & 1);
+        if (NBUF == 2 && threadIdx.x == 0 && in_flight > 1) mbar_wait(&bars[cur ^ 1], ((it + 1) >> 1) & 1);
         return;
       }
       if (threadIdx.x == 0) --in_flight;
@@ -531,6 +631,7 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, 1)
 #pragma unroll
         for (int r = 0; r < kAmps; ++r) a[r] = sm[(r | xb) * S::COLS + col];
       }
+      if constexpr (NBUF == 1) { ++reads_left; release(); }   // counts the first read
     }
     for (int si = 0; si < A.nseg; ++si) {
       const Seg& sg = A.segs[si];
@@ -550,6 +651,7 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, 1)
           for (int r = 0; r < kAmps; ++r) a[r] = sm[high_idx<COLB>(xa | (r << 5), col)];
         }
         stage ^= 1;
+        release();
       }
       if (stage == 0) run_seg<R, true>(a, sg, P, xa);
       else run_seg<R, false>(a, sg, P, 0);
@@ -566,7 +668,9 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, 1)
       __syncthreads();
       for (int i = threadIdx.x; i < S::COLS * 11; i += S::THREADS) {
         const int c = i / 11, aa = i % 11;
-        alpha_sm[c * 12 + aa] = out_alpha<R>(A, P, aa, (uint64_t)(tbits | (uint32_t)c));
+        const C f = out_alpha<R>(A, P, aa, (uint64_t)(tbits | (uint32_t)c));
+        const R d = diag_factor_of<R>(A, P, aa);
+        alpha_sm[c * 12 + aa] = mk<R>(f.x * d, f.y * d);
       }
       __syncthreads();
       const C* al_c = alpha_sm + col * 12;
@@ -580,6 +684,18 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, 1)
         if ((xt >> lt) & 1) c = cmul(c, al_c[lt]);
       }
       apply_reg_product<R>(a, c, al);
+    } else if (A.diag_off >= 0) {
+      const R* dg = P + A.diag_off;
+      const int xt = stage == 0 ? xa : xb;
+      R t5[kRegBits];
+      R c = __ldg(dg + 10);
+#pragma unroll
+      for (int r = 0; r < kRegBits; ++r) {
+        t5[r] = __ldg(dg + (stage == 0 ? r + 5 : r));
+        const int lt = stage == 0 ? r : r + 5;
+        if ((xt >> lt) & 1) c *= __ldg(dg + lt);
+      }
+      apply_real_product<R>(a, c, t5);
     }
     const uint32_t fixed = tbits + (uint32_t)col + (stage == 0 ? offa : offb);
     const int sh = stage == 0 ? sha : shb;

@@ -74,7 +74,8 @@ struct DGate {            // a gate as the precompute kernel sees it
 struct Producer {
   int kind;
   int gate;               // DENSE / OUT: gate index
-  int j;                  // DWIN: attach bit; table has 2^j entries
+  int j;                  // DWIN: attach bit, table of 2^j entries; DENSE: window bit
+  int real;               // DENSE: real matrix, stored factored as (r0, r1)
   int contrib_start, contrib_count;
   uint32_t off;
 };
@@ -115,60 +116,108 @@ __device__ __forceinline__ double2 diag_factor(const DGate& g, double e, uint64_
   return make_double2(re, im);
 }
 
+// Member's noisy 2x2 matrix of a one-qubit gate (interleaved complex, row-major).
+__device__ __forceinline__ void noisy_matrix(const DGate& g, double e, uint64_t seed, uint64_t traj, uint64_t gid,
+                                             double (&m)[8]) {
+  for (int q = 0; q < 8; ++q) m[q] = g.U[q];
+  if (!g.noisy) return;
+  const double2 xi = noise_normals(seed, traj, gid);
+  double s, c;
+  sincos(e * xi.x, &s, &c);
+  if (g.noise == QS_NOISE_ROTATION) {
+    // U * [[c, s], [-s, c]]
+    for (int r = 0; r < 2; ++r) {
+      const double u0r = g.U[4 * r], u0i = g.U[4 * r + 1], u1r = g.U[4 * r + 2], u1i = g.U[4 * r + 3];
+      m[4 * r] = u0r * c - u1r * s;
+      m[4 * r + 1] = u0i * c - u1i * s;
+      m[4 * r + 2] = u0r * s + u1r * c;
+      m[4 * r + 3] = u0i * s + u1i * c;
+    }
+  } else {
+    // U * diag(1, e^{-i e xi})
+    for (int r = 0; r < 2; ++r) {
+      const double ur = g.U[4 * r + 2], ui = g.U[4 * r + 3];
+      m[4 * r + 2] = ur * c + ui * s;
+      m[4 * r + 3] = ui * c - ur * s;
+    }
+  }
+}
+
+// Smallest pivot magnitude of a factored real gate: a smaller (or zero) pivot
+// is replaced by this value, an error of at most this much in one matrix
+// entry, far below the precision of R (intermediate values stay in range).
+template <typename R> __device__ __forceinline__ double min_pivot() { return sizeof(R) == 4 ? 0x1p-30 : 0x1p-300; }
+
 template <typename R>
 __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int stride, const DGate* __restrict__ gates,
                                                     const Producer* __restrict__ prods, int num_prods,
                                                     const Contrib* __restrict__ contribs, int num_contribs,
-                                                    int num_dwin, NoiseSrc src, const RunParams* rp) {
+                                                    int num_dwin, int diag_off, NoiseSrc src, const RunParams* rp) {
   extern __shared__ double2 pre_sm[];                   // [num_contribs] factors, then [num_dwin][10]
   const int b = blockIdx.x;
   double e;
   uint64_t seed, traj;
   member_noise(src, rp, b, &e, &seed, &traj);
   R* out = params + (uint64_t)b * stride;
-  // contributions of the phase tables
-  for (int i = threadIdx.x; i < num_contribs; i += blockDim.x) {
-    const DGate& g = gates[contribs[i].gate];
-    pre_sm[i] = diag_factor(g, e, seed, traj, rp->gate_id0 + g.gate_pos);
-  }
-  // dense matrices and out factors
-  for (int i = threadIdx.x; i < num_prods; i += blockDim.x) {
-    const Producer p = prods[i];
-    if (p.kind == PD_DENSE) {
-      const DGate& g = gates[p.gate];
-      double m[8];
-      for (int q = 0; q < 8; ++q) m[q] = g.U[q];
-      if (g.noisy) {
-        const double2 xi = noise_normals(seed, traj, rp->gate_id0 + g.gate_pos);
-        double s, c;
-        sincos(e * xi.x, &s, &c);
-        if (g.noise == QS_NOISE_ROTATION) {
-          // U * [[c, s], [-s, c]]
-          for (int r = 0; r < 2; ++r) {
-            const double u0r = g.U[4 * r], u0i = g.U[4 * r + 1], u1r = g.U[4 * r + 2], u1i = g.U[4 * r + 3];
-            m[4 * r] = u0r * c - u1r * s;
-            m[4 * r + 1] = u0i * c - u1i * s;
-            m[4 * r + 2] = u0r * s + u1r * c;
-            m[4 * r + 3] = u0i * s + u1i * c;
-          }
-        } else {
-          // U * diag(1, e^{-i e xi})
-          for (int r = 0; r < 2; ++r) {
-            const double ur = g.U[4 * r + 2], ui = g.U[4 * r + 3];
-            m[4 * r + 2] = ur * c + ui * s;
-            m[4 * r + 3] = ui * c - ur * s;
-          }
-        }
+  // the last kWin threads build the dense matrices while the others compute
+  // the phase factors
+  constexpr int kPhaseThreads = 128 - kWin;
+  // contributions of the phase tables, and out factors
+  if (threadIdx.x < kPhaseThreads) {
+    for (int i = threadIdx.x; i < num_contribs; i += kPhaseThreads) {
+      const DGate& g = gates[contribs[i].gate];
+      pre_sm[i] = diag_factor(g, e, seed, traj, rp->gate_id0 + g.gate_pos);
+    }
+    for (int i = threadIdx.x; i < num_prods; i += kPhaseThreads) {
+      const Producer p = prods[i];
+      if (p.kind == PD_OUT) {
+        const DGate& g = gates[p.gate];
+        const double2 f = diag_factor(g, e, seed, traj, rp->gate_id0 + g.gate_pos);
+        out[p.off] = (R)f.x;
+        out[p.off + 1] = (R)f.y;
       }
-      for (int q = 0; q < 8; ++q) out[p.off + q] = (R)m[q];
-    } else if (p.kind == PD_OUT) {
-      const DGate& g = gates[p.gate];
-      const double2 f = diag_factor(g, e, seed, traj, rp->gate_id0 + g.gate_pos);
-      out[p.off] = (R)f.x;
-      out[p.off + 1] = (R)f.y;
     }
   }
+  // dense matrices: one thread per window bit walks that bit's gates in
+  // circuit order.  A real gate M' = M diag(pa, pd) (the diagonal left by the
+  // previous real gate on the bit) is stored factored, M' = diag(a, d)
+  // [[1, r0], [r1, 1]], and diag(a, d) is carried on; a complex gate absorbs
+  // the carried diagonal.  What is left at the end goes to the diag block.
+  __shared__ double pivot_a[kWin];
+  if (threadIdx.x >= kPhaseThreads) {
+    const int J = threadIdx.x - kPhaseThreads;
+    double pa = 1.0, pd = 1.0;
+    for (int i = 0; i < num_prods; ++i) {
+      const Producer p = prods[i];
+      if (p.kind != PD_DENSE || p.j != J) continue;
+      const DGate& g = gates[p.gate];
+      double m[8];
+      noisy_matrix(g, e, seed, traj, rp->gate_id0 + g.gate_pos, m);
+      m[0] *= pa; m[1] *= pa; m[4] *= pa; m[5] *= pa;   // column 0
+      m[2] *= pd; m[3] *= pd; m[6] *= pd; m[7] *= pd;   // column 1
+      if (p.real) {
+        const double mp = min_pivot<R>();
+        double a = m[0], d = m[6];
+        if (fabs(a) < mp) a = a < 0.0 ? -mp : mp;
+        if (fabs(d) < mp) d = d < 0.0 ? -mp : mp;
+        out[p.off] = (R)(m[2] / a);
+        out[p.off + 1] = (R)(m[4] / d);
+        pa = a;
+        pd = d;
+      } else {
+        for (int q = 0; q < 8; ++q) out[p.off + q] = (R)m[q];
+        pa = pd = 1.0;
+      }
+    }
+    pivot_a[J] = pa;
+    if (diag_off >= 0) out[diag_off + J] = (R)(pd / pa);
+  }
   __syncthreads();
+  if (diag_off >= 0 && threadIdx.x == 0) {
+    double sc = 1.0;
+    for (int J = 0; J < kWin; ++J) sc *= pivot_a[J];
+    out[diag_off + kWin] = (R)sc;
+  }
   // per-table partner factors f[m], m = 0..9
   double2* fm = pre_sm + num_contribs;
   int w = 0;
@@ -187,22 +236,28 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
     ++w;
   }
   __syncthreads();
-  // tables T[x] = prod_{m in x} f[m]
+  // tables T[x] = prod_{m in x} f[m], by doubling in FP64 shared memory:
+  // T[x + 2^m] = T[x] f[m] for x < 2^m (one complex product per entry)
+  double2* tab = fm + (size_t)num_dwin * kWin;          // 2^9 entries
   w = 0;
   for (int i = 0; i < num_prods; ++i) {
     const Producer p = prods[i];
     if (p.kind != PD_DWIN) continue;
-    const int size = 1 << p.j;
-    for (int x = threadIdx.x; x < size; x += blockDim.x) {
-      double2 acc = make_double2(1.0, 0.0);
-      for (int m = 0; m < p.j; ++m)
-        if ((x >> m) & 1) {
-          const double2 f = fm[w * kWin + m];
-          acc = make_double2(acc.x * f.x - acc.y * f.y, acc.x * f.y + acc.y * f.x);
-        }
-      out[p.off + 2 * x] = (R)acc.x;
-      out[p.off + 2 * x + 1] = (R)acc.y;
+    if (threadIdx.x == 0) tab[0] = make_double2(1.0, 0.0);
+    __syncthreads();
+    for (int m = 0; m < p.j; ++m) {
+      const double2 f = fm[w * kWin + m];
+      for (int x = threadIdx.x; x < (1 << m); x += blockDim.x) {
+        const double2 t = tab[x];
+        tab[x + (1 << m)] = make_double2(t.x * f.x - t.y * f.y, t.x * f.y + t.y * f.x);
+      }
+      __syncthreads();
     }
+    for (int x = threadIdx.x; x < (1 << p.j); x += blockDim.x) {
+      out[p.off + 2 * x] = (R)tab[x].x;
+      out[p.off + 2 * x + 1] = (R)tab[x].y;
+    }
+    __syncthreads();
     ++w;
   }
 }
@@ -237,6 +292,7 @@ struct PassPlan {
   std::vector<Producer> prods;
   std::vector<Contrib> contribs;
   int num_dwin = 0;
+  int diag_off = -1;              // deferred diagonals of the factored real gates
   int stride = 0;                 // R units per member
   std::vector<int> other;
   int tile_shift = 0;             // log2(tiles per member)
@@ -275,6 +331,8 @@ struct qs_plan_s {
   bool graph_timing[6] = {false, false, false, false, false, false};
   double* d_fid = nullptr;        // fused-fidelity partials [member][tile] complex
   int colb = 3;
+  int low_cfg = 0;                // kernel configuration of each window geometry (see launch_pass_kernel)
+  int high_cfg = 0;
   int launches = 0;
   bool timing = false;
   std::vector<cudaEvent_t> events;     // launches + 1 when timing
@@ -398,6 +456,8 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
       Producer pr{};
       pr.kind = PD_DENSE;
       pr.gate = rem[i];
+      pr.j = l;
+      pr.real = x.real;
       x.off = (uint32_t)P->prods.size();                // patched to an offset below
       P->prods.push_back(pr);
       P->ops.push_back(x);
@@ -448,14 +508,21 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
   // parameter layout: dense matrices, tables, out factors
   std::vector<Producer> prods;
   uint32_t off = 0;
+  bool any_real = false;
   for (auto& x : P->ops) {
     if (x.type == OP_DENSE) {
       Producer pr = P->prods[x.off];
       pr.off = off;
       x.off = off;
-      off += 8;
+      off += pr.real ? 2 : 8;                           // (r0, r1) or the complex 2x2
+      any_real |= pr.real != 0;
       prods.push_back(pr);
     }
+  }
+  P->diag_off = -1;
+  if (any_real) {                                       // ratios of the 10 window bits + scale
+    P->diag_off = (int)off;
+    off += 12;
   }
   P->contribs.clear();
   P->num_dwin = 0;
@@ -617,19 +684,25 @@ qs_status upload(qs_plan p, T** dst, const std::vector<T>& v) {
   return QS_OK;
 }
 
-constexpr int kLowWarpsF = 12;  // complex64: 12 warps per block (registers <= 170)
-constexpr int kLowWarpsD = 4;   // complex128: 4 warps (same shared memory)
-
-template <typename R> constexpr int low_warps() { return sizeof(R) == 4 ? kLowWarpsF : kLowWarpsD; }
+// Kernel configurations of the two window geometries.  complex64:
+//   low  0: 12 warps, two tile buffers per warp (registers <= 170)
+//   low  1: 16 warps, one buffer per warp, next copy issued after the tile's
+//           last shared read (registers <= 128)
+//   high 0: one block of 8 warps per SM, two tile buffers
+//   high 1: two blocks per SM, one buffer each (registers <= 128)
+// complex128: low 4 warps / two buffers, high 4 columns / two buffers.
+constexpr int kLowCfgsF = 2, kHighCfgsF = 2, kLowCfgsD = 1, kHighCfgsD = 1;
 template <typename R> constexpr int high_colb() { return sizeof(R) == 4 ? 3 : 2; }
 
-template <typename R>
-size_t low_smem() { return (size_t)low_warps<R>() * LowShape<low_warps<R>()>::PER_WARP * sizeof(cplx<R>); }
-template <typename R>
+template <typename R, int W, int NB>
+size_t low_smem() { return (size_t)W * LowShape<W, NB>::PER_WARP * sizeof(cplx<R>); }
+template <typename R, int NB>
 size_t high_smem() {
   constexpr int colb = high_colb<R>();
-  return (2 * (size_t)HighShape<colb>::TILE + HighShape<colb>::COLS * 12) * sizeof(cplx<R>);
+  return (NB * (size_t)HighShape<colb>::TILE + HighShape<colb>::COLS * 12) * sizeof(cplx<R>);
 }
+int num_low_cfgs(size_t esize) { return esize == 8 ? kLowCfgsF : kLowCfgsD; }
+int num_high_cfgs(size_t esize) { return esize == 8 ? kHighCfgsF : kHighCfgsD; }
 
 // Tensor map of the state as [batch * 1024 rows][2^(n-10) columns] of 8-byte
 // elements (a complex128 amplitude is two of them), boxes of 2^colb amplitudes
@@ -683,6 +756,7 @@ PassArgs pass_args(qs_plan p, const PassPlan& P, int synth, int fid) {
   A.fid = fid;
   A.ref = h->ref;
   A.fid_partials = p->d_fid;
+  A.diag_off = P.diag_off;
   return A;
 }
 
@@ -692,28 +766,42 @@ cudaError_t launch_precompute(qs_plan p, const PassPlan& P, cudaStream_t s) {
   qs_ctx* h = p->h;
   NoiseSrc src{};
   if (h->member_noise) { src.e = h->m_e; src.seed = h->m_seed; src.traj = h->m_traj; }
-  const size_t pre_smem = (P.contribs.size() + (size_t)P.num_dwin * kWin) * sizeof(double2);
+  const size_t pre_smem = (P.contribs.size() + (size_t)P.num_dwin * kWin + (1u << (kWin - 1))) * sizeof(double2);
   k_precompute<R><<<h->batch, 128, pre_smem, s>>>((R*)P.d_params, P.stride, p->d_gates, P.d_prods,
                                                    (int)P.prods.size(), P.d_contribs, (int)P.contribs.size(),
-                                                   P.num_dwin, src, p->d_run);
+                                                   P.num_dwin, P.diag_off, src, p->d_run);
   return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_pass_kernel(qs_plan p, const PassPlan& P, cudaStream_t s, int synth, int fid) {
+  using C = cplx<R>;
   qs_ctx* h = p->h;
   const PassArgs A = pass_args(p, P, synth, fid);
   const int sms = num_sms();
+  auto grid = [&](uint64_t units, int per_sm) {
+    const uint64_t cap = (uint64_t)sms * per_sm;
+    return (int)(units < cap ? units : cap);
+  };
+  C* psi = (C*)h->state;
   if (!P.high) {
-    constexpr int W = low_warps<R>();
-    uint64_t blocks = (A.tiles + W - 1) / W;
-    if (blocks > (uint64_t)sms) blocks = sms;
-    k_pass_low<R, W><<<(int)blocks, W * 32, low_smem<R>(), s>>>((cplx<R>*)h->state, A);
+    if constexpr (sizeof(R) == 4) {
+      if (p->low_cfg == 1)
+        k_pass_low<R, 16, 1><<<grid((A.tiles + 15) / 16, 1), 16 * 32, low_smem<R, 16, 1>(), s>>>(psi, A);
+      else
+        k_pass_low<R, 12, 2><<<grid((A.tiles + 11) / 12, 1), 12 * 32, low_smem<R, 12, 2>(), s>>>(psi, A);
+    } else {
+      k_pass_low<R, 4, 2><<<grid((A.tiles + 3) / 4, 1), 4 * 32, low_smem<R, 4, 2>(), s>>>(psi, A);
+    }
   } else {
     constexpr int CB = high_colb<R>();
-    uint64_t blocks = A.tiles;
-    if (blocks > (uint64_t)sms) blocks = sms;
-    k_pass_high<R, CB><<<(int)blocks, HighShape<CB>::THREADS, high_smem<R>(), s>>>((cplx<R>*)h->state, P.tmap, A);
+    if constexpr (sizeof(R) == 4) {
+      if (p->high_cfg == 1) {
+        k_pass_high<R, CB, 1><<<grid(A.tiles, 2), HighShape<CB>::THREADS, high_smem<R, 1>(), s>>>(psi, P.tmap, A);
+        return cudaGetLastError();
+      }
+    }
+    k_pass_high<R, CB, 2><<<grid(A.tiles, 1), HighShape<CB>::THREADS, high_smem<R, 2>(), s>>>(psi, P.tmap, A);
   }
   return cudaGetLastError();
 }
@@ -734,15 +822,16 @@ cudaError_t set_smem_attrs(size_t esize) {
   static std::atomic<bool> done[2] = {false, false};
   const int which = esize == 8 ? 0 : 1;
   if (done[which]) return cudaSuccess;
+  const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e;
   if (esize == 8) {
-    e = cudaFuncSetAttribute(k_pass_low<float, kLowWarpsF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)low_smem<float>());
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_pass_high<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)high_smem<float>());
+    e = cudaFuncSetAttribute(k_pass_low<float, 12, 2>, attr, (int)low_smem<float, 12, 2>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass_low<float, 16, 1>, attr, (int)low_smem<float, 16, 1>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass_high<float, 3, 2>, attr, (int)high_smem<float, 2>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass_high<float, 3, 1>, attr, (int)high_smem<float, 1>());
   } else {
-    e = cudaFuncSetAttribute(k_pass_low<double, kLowWarpsD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)low_smem<double>());
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_pass_high<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)high_smem<double>());
+    e = cudaFuncSetAttribute(k_pass_low<double, 4, 2>, attr, (int)low_smem<double, 4, 2>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass_high<double, 2, 2>, attr, (int)high_smem<double, 2>());
   }
   if (e == cudaSuccess) done[which] = true;
   return e;
@@ -1048,6 +1137,74 @@ qs_status qs_plan_profile(qs_plan p, int reps, double e, uint64_t seed, uint64_t
   }
   for (auto& x : ev) cudaEventDestroy(x);
   return result;
+}
+
+namespace {
+void drop_graphs(qs_plan p) {
+  for (auto& x : p->exec)
+    if (x) { cudaGraphExecDestroy(x); x = nullptr; }
+}
+}  // namespace
+
+qs_status qs_plan_configs(qs_plan p, int* low_count, int* high_count) {
+  if (!p || !low_count || !high_count) return QS_ERR_INVALID_ARG;
+  *low_count = num_low_cfgs(p->h->esize);
+  *high_count = num_high_cfgs(p->h->esize);
+  return QS_OK;
+}
+
+qs_status qs_plan_set_config(qs_plan p, int low_cfg, int high_cfg) {
+  if (!p) return QS_ERR_INVALID_ARG;
+  if (low_cfg < 0 || low_cfg >= num_low_cfgs(p->h->esize) || high_cfg < 0 || high_cfg >= num_high_cfgs(p->h->esize))
+    return pfail(p, QS_ERR_INVALID_ARG, "kernel configuration out of range");
+  if (low_cfg != p->low_cfg || high_cfg != p->high_cfg) {
+    // graphs hold the old kernels; wait for runs that may still use them
+    if (cudaStreamSynchronize(p->h->stream) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "stream sync");
+    drop_graphs(p);
+    p->low_cfg = low_cfg;
+    p->high_cfg = high_cfg;
+  }
+  return QS_OK;
+}
+
+qs_status qs_plan_get_config(qs_plan p, int* low_cfg, int* high_cfg) {
+  if (!p || !low_cfg || !high_cfg) return QS_ERR_INVALID_ARG;
+  *low_cfg = p->low_cfg;
+  *high_cfg = p->high_cfg;
+  return QS_OK;
+}
+
+qs_status qs_plan_autotune(qs_plan p, int reps, double e, uint64_t seed, double* best_ms) {
+  if (!p || reps < 1) return QS_ERR_INVALID_ARG;
+  const int nl = num_low_cfgs(p->h->esize), nh = num_high_cfgs(p->h->esize);
+  const int ncfg = std::max(nl, nh);
+  std::vector<double> low_ms(ncfg, -1.0), high_ms(ncfg, -1.0);
+  std::vector<double> ms((size_t)std::max(p->launches, 1));
+  std::vector<int> kinds(ms.size());
+  for (int c = 0; c < ncfg; ++c) {
+    qs_status st = qs_plan_set_config(p, std::min(c, nl - 1), std::min(c, nh - 1));
+    if (st != QS_OK) return st;
+    int count = 0;
+    st = qs_plan_profile(p, reps, e, seed, 0, ms.data(), kinds.data(), (int)ms.size(), &count);
+    if (st != QS_OK) return st;
+    double lo = 0.0, hi = 0.0;
+    bool has_lo = false, has_hi = false;
+    for (int i = 0; i < count && i < (int)ms.size(); ++i) {
+      if (kinds[i] == 1) { lo += ms[i]; has_lo = true; }
+      if (kinds[i] == 2) { hi += ms[i]; has_hi = true; }
+    }
+    if (has_lo && c < nl) low_ms[c] = lo;
+    if (has_hi && c < nh) high_ms[c] = hi;
+  }
+  auto best = [](const std::vector<double>& v, int n) {
+    int b = 0;
+    for (int c = 1; c < n; ++c)
+      if (v[c] >= 0.0 && (v[b] < 0.0 || v[c] < v[b])) b = c;
+    return b;
+  };
+  const int bl = best(low_ms, nl), bh = best(high_ms, nh);
+  if (best_ms) { best_ms[0] = low_ms[bl]; best_ms[1] = high_ms[bh]; }
+  return qs_plan_set_config(p, bl, bh);
 }
 
 qs_status qs_plan_set_timing(qs_plan p, int on) {

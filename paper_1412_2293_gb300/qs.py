@@ -78,6 +78,10 @@ _SIGS = {
     "qs_plan_destroy": ([_P], ct.c_int),
     "qs_plan_set_timing": ([_P, ct.c_int], ct.c_int),
     "qs_plan_last_times": ([_P, _D, _I, ct.c_int, _I], ct.c_int),
+    "qs_plan_configs": ([_P, _I, _I], ct.c_int),
+    "qs_plan_set_config": ([_P, ct.c_int, ct.c_int], ct.c_int),
+    "qs_plan_get_config": ([_P, _I, _I], ct.c_int),
+    "qs_plan_autotune": ([_P, ct.c_int, ct.c_double, ct.c_uint64, _D], ct.c_int),
     "qs_fidelity_noalloc": ([_P, _P, ct.c_int, ct.c_int, ct.c_int, _P, _D], ct.c_int),
     "qs_measure_peaks": ([_D, _D], ct.c_int),
     "qs_debug_noise": ([ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_int, ct.POINTER(ct.c_uint32), _D], ct.c_int),
@@ -328,6 +332,29 @@ def qs_plan_profile(p, reps, e, seed, gate_id0=0, cap=4096, h=None):
                                  kinds.ctypes.data_as(_I), cap, ct.byref(count)), h)
     c = min(count.value, cap)
     return ms[:c].copy(), [PROFILE_KINDS[int(k)] for k in kinds[:c]]
+
+
+def qs_plan_configs(p, h=None):
+    a, b = ct.c_int(), ct.c_int()
+    _check(lib().qs_plan_configs(p, ct.byref(a), ct.byref(b)), h)
+    return a.value, b.value
+
+
+def qs_plan_set_config(p, low_cfg, high_cfg, h=None):
+    _check(lib().qs_plan_set_config(p, int(low_cfg), int(high_cfg)), h)
+
+
+def qs_plan_get_config(p, h=None):
+    a, b = ct.c_int(), ct.c_int()
+    _check(lib().qs_plan_get_config(p, ct.byref(a), ct.byref(b)), h)
+    return a.value, b.value
+
+
+def qs_plan_autotune(p, reps=3, e=0.0, seed=0, h=None):
+    """Time every kernel configuration, keep the fastest; returns (low ms, high ms)."""
+    best = np.zeros(2, dtype=np.float64)
+    _check(lib().qs_plan_autotune(p, int(reps), float(e), int(seed), _dptr(best)), h)
+    return float(best[0]), float(best[1])
 
 
 def qs_plan_set_timing(p, on=True, h=None):

@@ -471,3 +471,63 @@ def test_smallest_sizes():
     with Handle(3, 7, 0, qs.QS_STATEVEC, qs.QS_C64) as h:
         qs.qs_apply_gate(h, (2,), ogates.hadamard())
         np.testing.assert_allclose(qs.qs_trace(h), 1.0, atol=1e-6)
+
+
+@pytest.mark.parametrize("circ,n,batch", [("qft", 18, 32), ("grover", 16, 64)])
+def test_every_kernel_configuration_gives_the_same_result(circ, n, batch):
+    """Each pass configuration (tile buffers, warps, blocks per SM) at sizes
+    where every warp or block streams several tiles, with a created start
+    state and the fused fidelity; sampled members against the oracle."""
+    e = 0.02
+    if circ == "qft":
+        ops, xs = inputs.qft_circuit(n), [(97 * b + 11) % (1 << n) for b in range(batch)]
+    else:
+        ops, xs = inputs.grover_circuit(n, 3, 12345 % (1 << n)), [0] * batch
+    ideal0 = ocirc.ideal_state(n, ops, xs[0])
+    results = {}
+    with Handle(n, batch, 0, qs.QS_STATEVEC, qs.QS_C64) as h:
+        qs.qs_set_reference(h, np.asarray(ideal0))
+        p = qs.qs_plan_create(h, pcirc.to_gates(ops))
+        nl, nh = qs.qs_plan_configs(p, h)
+        assert (nl, nh) == (2, 2)
+        for lc in range(nl):
+            for hc in range(nh):
+                qs.qs_plan_set_config(p, lc, hc, h)
+                assert qs.qs_plan_get_config(p, h) == (lc, hc)
+                qs.qs_set_basis_states(h, xs)
+                f = qs.qs_plan_run_fidelity(p, e, SEED, 0, h)
+                results[(lc, hc)] = (f, qs.qs_get_state(h).reshape(batch, -1))
+        with pytest.raises(qs.QSError):
+            qs.qs_plan_set_config(p, 2, 0, h)
+        qs.qs_plan_destroy(p)
+    f0, s0 = results[(0, 0)]
+    for key, (f, st) in results.items():
+        np.testing.assert_allclose(st, s0, atol=1e-6, err_msg=str(key))
+        np.testing.assert_allclose(f, f0, atol=1e-6, err_msg=str(key))
+    for b in (0, batch - 1):
+        want = oracle_traj(n, ops, xs[b], e, b)
+        np.testing.assert_allclose(s0[b], want, atol=TOL[qs.QS_C64])
+        assert abs(f0[b] - osv.fidelity(ideal0, want)) <= 1e-5
+
+
+def test_autotune_picks_a_configuration_and_results_stay_correct():
+    n, batch, e = 16, 32, 0.01
+    ops = inputs.qft_circuit(n)
+    with Handle(n, batch, 0, qs.QS_STATEVEC, qs.QS_C64) as h:
+        p = qs.qs_plan_create(h, pcirc.to_gates(ops))
+        qs.qs_set_basis_state(h, 3)
+        lo, hi = qs.qs_plan_autotune(p, 2, e, SEED, h)
+        assert lo > 0 and hi > 0
+        cfg = qs.qs_plan_get_config(p, h)
+        assert 0 <= cfg[0] < 2 and 0 <= cfg[1] < 2
+        qs.qs_set_basis_state(h, 3)
+        qs.qs_plan_run(p, e, SEED, 0, h)
+        got = qs.qs_get_state(h).reshape(batch, -1)
+        qs.qs_plan_destroy(p)
+    np.testing.assert_allclose(got[1], oracle_traj(n, ops, 3, e, 1), atol=TOL[qs.QS_C64])
+    with Handle(n, 2, 0, qs.QS_STATEVEC, qs.QS_C128) as h:
+        p = qs.qs_plan_create(h, pcirc.to_gates(ops))
+        assert qs.qs_plan_configs(p, h) == (1, 1)
+        qs.qs_plan_autotune(p, 1, e, SEED, h)
+        assert qs.qs_plan_get_config(p, h) == (0, 0)
+        qs.qs_plan_destroy(p)
