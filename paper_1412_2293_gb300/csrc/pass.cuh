@@ -160,32 +160,42 @@ __device__ __forceinline__ cplx<R> ld_c(const R* p) { return __ldg(reinterpret_c
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// A real 2x2 gate [[a, b], [c, d]] written as diag(a, d) [[1, r0], [r1, 1]],
-// r0 = b / a, r1 = c / d: one FMA per output component (packed two-lane for
-// complex64).  The diagonal commutes with every diagonal operation of the
-// pass; the precompute folds it into the next gate on the same qubit or
-// leaves it for the end of the pass (PassArgs::diag_off).
+// A real 2x2 gate [[a, b], [c, d]] written as two shears and a diagonal,
+// diag(a, det / a) [[1, 0], [s1, 1]] [[1, r0], [0, 1]], r0 = b / a,
+// s1 = c a / det: x0 += r0 x1, then x1 += s1 x0, each one FMA per component
+// (packed two-lane for complex64) that updates its register in place.  The
+// diagonal commutes with every diagonal operation of the pass; the
+// precompute folds it into the next gate on the same qubit or leaves it for
+// the end of the pass (PassArgs::diag_off).
 template <typename R>
-__device__ __forceinline__ void butterfly_fact(cplx<R>& x0, cplx<R>& x1, R r0, R r1) {
-  if constexpr (sizeof(R) == 4) {
-    const float2 a = x0, b = x1;
-    x0 = fma2(make_float2(r0, r0), b, a);
-    x1 = fma2(make_float2(r1, r1), a, b);
-  } else {
-    const cplx<R> a = x0, b = x1;
-    x0 = mk<R>(fma(r0, b.x, a.x), fma(r0, b.y, a.y));
-    x1 = mk<R>(fma(r1, a.x, b.x), fma(r1, a.y, b.y));
-  }
+__device__ __forceinline__ void butterfly_fact(cplx<R>& x0, cplx<R>& x1, R r0, R s1) {
+  x0.x = fma(r0, x1.x, x0.x);
+  x0.y = fma(r0, x1.y, x0.y);
+  x1.x = fma(s1, x0.x, x1.x);
+  x1.y = fma(s1, x0.y, x1.y);
 }
 
 template <typename R, int RJ>
 __device__ __forceinline__ void dense_reg(cplx<R> (&a)[kAmps], const R* m, bool real) {
   if (real) {
-    const cplx<R> rr = ld_c(m);                         // (r0, r1)
+    // stored as (r0, r0, s1, s1): the broadcast pairs of the packed FMA come
+    // straight from one 16-byte load (complex64)
+    if constexpr (sizeof(R) == 4) {
+      const float4 q = __ldg(reinterpret_cast<const float4*>(m));
+      const float2 p0 = make_float2(q.x, q.y), p1 = make_float2(q.z, q.w);
 #pragma unroll
-    for (int r = 0; r < kAmps; ++r) {
-      if (r & (1 << RJ)) continue;
-      butterfly_fact<R>(a[r], a[r | (1 << RJ)], rr.x, rr.y);
+      for (int r = 0; r < kAmps; ++r) {
+        if (r & (1 << RJ)) continue;
+        a[r] = fma2(p0, a[r | (1 << RJ)], a[r]);
+        a[r | (1 << RJ)] = fma2(p1, a[r], a[r | (1 << RJ)]);
+      }
+    } else {
+      const R r0 = __ldg(m), s1 = __ldg(m + 2);
+#pragma unroll
+      for (int r = 0; r < kAmps; ++r) {
+        if (r & (1 << RJ)) continue;
+        butterfly_fact<R>(a[r], a[r | (1 << RJ)], r0, s1);
+      }
     }
   } else {
     const cplx<R> u00 = ld_c(m), u01 = ld_c(m + 2), u10 = ld_c(m + 4), u11 = ld_c(m + 6);
@@ -317,12 +327,13 @@ __device__ __forceinline__ void run_seg(cplx<R> (&a)[kAmps], const Seg& sg, cons
 // amplitudes (every WARPS-th tile of its block's range, so the block's warps
 // work on neighbouring tiles of one member and share its parameters in L1)
 // through one or two shared-memory buffers filled by bulk copies.  Register
-// exchanges happen in place in the current buffer with an XOR swizzle,
-// x -> x ^ ((x >> 5) & 15), under which both register layouts
-// (stage A: x = lane + 32 r, stage B: x = r + 32 lane) are free of bank
-// conflicts; stores are coalesced from the stage-A layout.
+// exchanges happen in place in the current buffer, in a layout padded to 33
+// amplitudes per 32 (stage A: amplitude lane + 32 r at word lane + 33 r,
+// stage B: r + 32 lane at r + 33 lane), free of bank conflicts both ways with
+// compile-time offsets; stores are coalesced from the stage-A layout.
 template <int WARPS, int NBUF> struct LowShape {
-  static constexpr int PER_WARP = NBUF * 1024 + 12;    // tile buffers + out factors
+  static constexpr int BUF = 1024 + 32;                // a tile in the padded exchange layout
+  static constexpr int PER_WARP = NBUF * BUF + 12;     // tile buffers + out factors
   static constexpr int THREADS = WARPS * 32;
 };
 
@@ -338,7 +349,6 @@ __device__ __forceinline__ int exchange_count(const PassArgs& A, int stage, bool
   return n;
 }
 
-__device__ __forceinline__ int low_swz(int x) { return x ^ ((x >> 5) & 15); }
 
 template <typename R, int WARPS, int NBUF>
 __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict__ psi, const __grid_constant__ PassArgs A) {
@@ -349,7 +359,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
   __shared__ __align__(8) uint64_t bars[WARPS][2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   C* wbase = reinterpret_cast<C*>(smem_raw) + (size_t)warp * S::PER_WARP;
-  C* alpha_sm = wbase + NBUF * 1024;
+  C* alpha_sm = wbase + NBUF * S::BUF;
   const uint64_t nmask = (1ull << A.n) - 1;
   const R* params = static_cast<const R*>(A.params);
   const uint32_t tile_bytes = 1024u * (uint32_t)sizeof(C);
@@ -377,12 +387,12 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
   for (uint64_t t = first; t < last; t += WARPS, ++it) {
     const int cur = NBUF == 2 ? (int)(it & 1) : 0;
     const uint32_t parity = NBUF == 2 ? ((it >> 1) & 1) : (it & 1);
-    C* cbuf = wbase + cur * 1024;
+    C* cbuf = wbase + cur * S::BUF;
     const uint64_t tn = t + WARPS;                      // this warp's next tile
     if (NBUF == 2 && !A.synth && lane == 0 && tn < last) {
       fence_proxy_async();
       mbar_expect_tx(&bars[warp][cur ^ 1], tile_bytes);
-      bulk_g2s(wbase + (cur ^ 1) * 1024, psi + (tn << kWin), tile_bytes, &bars[warp][cur ^ 1]);
+      bulk_g2s(wbase + (cur ^ 1) * S::BUF, psi + (tn << kWin), tile_bytes, &bars[warp][cur ^ 1]);
       ++in_flight;
     }
     // single buffer: start the next tile's copy once this tile's last shared read is done
@@ -406,10 +416,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
     const R* P = params + member * (uint64_t)A.param_stride;
     C a[kAmps];
     if (A.synth) {
+      // the one amplitude equal to 1: register (x >> 5) & 31 of lane x & 31
       const uint64_t x = A.basis ? A.basis[member] : A.basis0[0];
+      const uint32_t hot = ((x & ~1023ull) == mloc && (int)(x & 31) == lane) ? 1u << ((x >> 5) & 31) : 0u;
 #pragma unroll
-      for (int r = 0; r < kAmps; ++r)
-        a[r] = mk<R>((mloc | (uint64_t)(lane + 32 * r)) == x ? R(1) : R(0), R(0));
+      for (int r = 0; r < kAmps; ++r) a[r] = mk<R>((hot >> r) & 1u ? R(1) : R(0), R(0));
     } else {
       if (!mbar_wait(&bars[warp][cur], parity)) {
         report_timeout(A.status);
@@ -428,16 +439,16 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
         __syncwarp();
         if (stage == 0) {
 #pragma unroll
-          for (int r = 0; r < kAmps; ++r) cbuf[low_swz(lane + 32 * r)] = a[r];
+          for (int r = 0; r < kAmps; ++r) cbuf[lane + 33 * r] = a[r];
           __syncwarp();
 #pragma unroll
-          for (int r = 0; r < kAmps; ++r) a[r] = cbuf[low_swz(r + 32 * lane)];
+          for (int r = 0; r < kAmps; ++r) a[r] = cbuf[r + 33 * lane];
         } else {
 #pragma unroll
-          for (int r = 0; r < kAmps; ++r) cbuf[low_swz(r + 32 * lane)] = a[r];
+          for (int r = 0; r < kAmps; ++r) cbuf[r + 33 * lane] = a[r];
           __syncwarp();
 #pragma unroll
-          for (int r = 0; r < kAmps; ++r) a[r] = cbuf[low_swz(lane + 32 * r)];
+          for (int r = 0; r < kAmps; ++r) a[r] = cbuf[lane + 33 * r];
         }
         stage ^= 1;
         release();
@@ -481,10 +492,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
     if (stage == 1) {
       __syncwarp();
 #pragma unroll
-      for (int r = 0; r < kAmps; ++r) cbuf[low_swz(r + 32 * lane)] = a[r];
+      for (int r = 0; r < kAmps; ++r) cbuf[r + 33 * lane] = a[r];
       __syncwarp();
 #pragma unroll
-      for (int r = 0; r < kAmps; ++r) a[r] = cbuf[low_swz(lane + 32 * r)];
+      for (int r = 0; r < kAmps; ++r) a[r] = cbuf[lane + 33 * r];
       release();
     }
     if (A.fid) {
@@ -516,21 +527,21 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
 // window rows, each loaded as four 256-row boxes of a 2D tensor map
 // [members * 1024 rows][2^(n-10) columns].  The window bits are contiguous,
 // so register r of stage A sits at offset r << win[5] and of stage B at
-// r << win[0].  With 8 columns the in-place exchange swizzles element
-// x * 8 + col by flipping bit 3 with bit 5 of x (conflict-free both ways).
+// r << win[0].  The copy lands in the plain layout [x][col]; the in-place
+// exchange uses one padding row per 32 rows (conflict-free both ways).
 template <int COLB> struct HighShape {
   static constexpr int COLS = 1 << COLB;
   static constexpr int LW = kRegBits - COLB;            // lane bits that are window bits
   static constexpr int WARPS = 1 << COLB;               // warp bits = COLB window bits
   static constexpr int THREADS = WARPS * 32;
-  static constexpr int TILE = COLS * 1024;
+  static constexpr int TILE = COLS * 1024;              // amplitudes of a tile
+  static constexpr int BUF = COLS * (1024 + 32);        // a tile in the padded exchange layout
 };
 
+// exchange layout: row x at (x + x / 32) * COLS (one padding row per 32)
 template <int COLB>
 __device__ __forceinline__ int high_idx(int x, int col) {
-  const int e = x * (1 << COLB) + col;
-  if constexpr (COLB == 3) return e ^ (((x >> 5) & 1) << 3);
-  else return e;
+  return (x + (x >> 5)) * (1 << COLB) + col;
 }
 
 template <typename R, int COLB, int NBUF>
@@ -543,7 +554,7 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 2 : 1)
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ double fid_red[2][S::WARPS];
   C* smbase = reinterpret_cast<C*>(smem_raw);
-  C* alpha_sm = smbase + NBUF * S::TILE;                // [COLS][12]
+  C* alpha_sm = smbase + NBUF * S::BUF;                 // [COLS][12]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int col = lane & (S::COLS - 1);
   const int lh = lane >> COLB;
@@ -571,7 +582,7 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 2 : 1)
     const uint64_t tl = t & ((1ull << A.tile_shift) - 1);
     mbar_expect_tx(&bars[which], tile_bytes);
     const int x = (int)(tl * S::COLS) * elem_cols;
-    C* dst = smbase + which * S::TILE;
+    C* dst = smbase + which * S::BUF;
 #pragma unroll
     for (int b = 0; b < 4; ++b)
       tma_g2s_2d(dst + b * 256 * S::COLS, &tmap, x, (int)(member * 1024 + b * 256), &bars[which]);
@@ -606,16 +617,18 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 2 : 1)
     const uint64_t tl = t & ((1ull << A.tile_shift) - 1);
     const uint32_t tbits = (uint32_t)(tl << COLB);      // the other bits are COLB .. n-11
     const R* P = params + member * (uint64_t)A.param_stride;
-    C* sm = smbase + cur * S::TILE;
+    C* sm = smbase + cur * S::BUF;
     C a[kAmps];
     int stage = A.start_stage;
     if (A.synth) {
+      // the one amplitude equal to 1: register (x >> sh) & 31 of the thread
+      // whose other bits match
       const uint64_t x = A.basis ? A.basis[member] : A.basis0[0];
       const uint32_t fixed = tbits | (uint32_t)col | (stage == 0 ? offa : offb);
       const int sh = stage == 0 ? sha : shb;
+      const uint32_t hot = (x & ~(31ull << sh)) == (uint64_t)fixed ? 1u << ((x >> sh) & 31) : 0u;
 #pragma unroll
-      for (int r = 0; r < kAmps; ++r)
-        a[r] = mk<R>((uint64_t)(fixed | ((uint32_t)r << sh)) == x ? R(1) : R(0), R(0));
+      for (int r = 0; r < kAmps; ++r) a[r] = mk<R>((hot >> r) & 1u ? R(1) : R(0), R(0));
     } else {
       if (!mbar_wait(&bars[cur], parity)) {
         report_timeout(A.status);

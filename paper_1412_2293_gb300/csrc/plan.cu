@@ -75,7 +75,7 @@ struct Producer {
   int kind;
   int gate;               // DENSE / OUT: gate index
   int j;                  // DWIN: attach bit, table of 2^j entries; DENSE: window bit
-  int real;               // DENSE: real matrix, stored factored as (r0, r1)
+  int real;               // DENSE: real matrix, stored as its shears (r0, r0, s1, s1)
   int contrib_start, contrib_count;
   uint32_t off;
 };
@@ -179,10 +179,12 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
     }
   }
   // dense matrices: one thread per window bit walks that bit's gates in
-  // circuit order.  A real gate M' = M diag(pa, pd) (the diagonal left by the
-  // previous real gate on the bit) is stored factored, M' = diag(a, d)
-  // [[1, r0], [r1, 1]], and diag(a, d) is carried on; a complex gate absorbs
-  // the carried diagonal.  What is left at the end goes to the diag block.
+  // circuit order.  A real gate M' = M diag(pa, pd) = [[a, b], [c, d]] (the
+  // diagonal left by the previous real gate on the bit) is stored as the two
+  // shears of M' = diag(a, det / a) [[1, 0], [s1, 1]] [[1, r0], [0, 1]],
+  // r0 = b / a, s1 = c a / det, and diag(a, det / a) is carried on; a complex
+  // gate absorbs the carried diagonal.  What is left at the end goes to the
+  // diag block.
   __shared__ double pivot_a[kWin];
   if (threadIdx.x >= kPhaseThreads) {
     const int J = threadIdx.x - kPhaseThreads;
@@ -197,13 +199,17 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
       m[2] *= pd; m[3] *= pd; m[6] *= pd; m[7] *= pd;   // column 1
       if (p.real) {
         const double mp = min_pivot<R>();
-        double a = m[0], d = m[6];
+        double a = m[0];
         if (fabs(a) < mp) a = a < 0.0 ? -mp : mp;
-        if (fabs(d) < mp) d = d < 0.0 ? -mp : mp;
-        out[p.off] = (R)(m[2] / a);
-        out[p.off + 1] = (R)(m[4] / d);
+        double d2 = m[6] - m[4] * m[2] / a;             // det / a
+        if (fabs(d2) < mp) d2 = d2 < 0.0 ? -mp : mp;
+        const R r0 = (R)(m[2] / a), s1 = (R)(m[4] / d2);
+        out[p.off] = r0;                                // (r0, r0, s1, s1)
+        out[p.off + 1] = r0;
+        out[p.off + 2] = s1;
+        out[p.off + 3] = s1;
         pa = a;
-        pd = d;
+        pd = d2;
       } else {
         for (int q = 0; q < 8; ++q) out[p.off + q] = (R)m[q];
         pa = pd = 1.0;
@@ -514,7 +520,7 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
       Producer pr = P->prods[x.off];
       pr.off = off;
       x.off = off;
-      off += pr.real ? 2 : 8;                           // (r0, r1) or the complex 2x2
+      off += pr.real ? 4 : 8;                           // (r0, r0, s1, s1) or the complex 2x2
       any_real |= pr.real != 0;
       prods.push_back(pr);
     }
@@ -699,7 +705,7 @@ size_t low_smem() { return (size_t)W * LowShape<W, NB>::PER_WARP * sizeof(cplx<R
 template <typename R, int NB>
 size_t high_smem() {
   constexpr int colb = high_colb<R>();
-  return (NB * (size_t)HighShape<colb>::TILE + HighShape<colb>::COLS * 12) * sizeof(cplx<R>);
+  return (NB * (size_t)HighShape<colb>::BUF + HighShape<colb>::COLS * 12) * sizeof(cplx<R>);
 }
 int num_low_cfgs(size_t esize) { return esize == 8 ? kLowCfgsF : kLowCfgsD; }
 int num_high_cfgs(size_t esize) { return esize == 8 ? kHighCfgsF : kHighCfgsD; }
