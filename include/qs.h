@@ -257,9 +257,11 @@ qs_status qs_plan_last_times(qs_plan p, double* ms, int* kinds, int cap, int* co
 /* Kernel configuration of the fused passes (no counterpart in the paper: the
  * tiling of the update, Sec. 2, is the implementation's).  For each window
  * geometry (low: qubits 0..9, high: the 10 highest) a configuration index in
- * [0, count): complex64 has two of each -- low 0: 12 warps, two tile buffers
- * per warp; low 1: 16 warps, one buffer; high 0: one block per SM, two
- * buffers; high 1: two blocks per SM, one buffer -- complex128 one of each.
+ * [0, count): complex64 has two low and three high -- low 0: 12 warps, two
+ * tile buffers per warp; low 1: 16 warps, one buffer; high 0: one block of
+ * 8 warps per SM, two buffers; high 1: two such blocks per SM, one buffer;
+ * high 2: four blocks of 4 warps per SM (4-column tiles), one buffer --
+ * complex128 one of each.
  * Results do not depend on the configuration.  qs_plan_configs returns the
  * counts; qs_plan_set_config rejects an index out of range with
  * QS_ERR_INVALID_ARG; qs_plan_get_config returns the current choice. */

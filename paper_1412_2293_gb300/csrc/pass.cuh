@@ -545,7 +545,7 @@ __device__ __forceinline__ int high_idx(int x, int col) {
 }
 
 template <typename R, int COLB, int NBUF>
-__global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 2 : 1)
+__global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / HighShape<COLB>::WARPS : 1)
     k_pass_high(cplx<R>* __restrict__ psi, const __grid_constant__ CUtensorMap tmap, const __grid_constant__ PassArgs A) {
   static_assert(NBUF == 1 || NBUF == 2, "one or two tile buffers");
   using C = cplx<R>;

@@ -304,7 +304,8 @@ struct PassPlan {
   int tile_shift = 0;             // log2(tiles per member)
   std::vector<Seg> segs;          // the ops in canonical segments (what the kernels run)
   std::vector<Flip> flips;
-  CUtensorMap tmap;               // HIGH: [members * 1024 rows][2^(n-10) columns]
+  CUtensorMap tmap;               // HIGH: [members * 1024 rows][2^(n-10) columns], boxes of 2^colb columns
+  CUtensorMap tmap4;              // HIGH complex64: the same with boxes of 4 columns (configuration 2)
   // device copies
   FOp* d_ops = nullptr;
   OutTerm* d_outs = nullptr;
@@ -696,16 +697,16 @@ qs_status upload(qs_plan p, T** dst, const std::vector<T>& v) {
 //           last shared read (registers <= 128)
 //   high 0: one block of 8 warps per SM, two tile buffers
 //   high 1: two blocks per SM, one buffer each (registers <= 128)
+//   high 2: four blocks of 4 warps per SM (tiles of 4 columns), one buffer each
 // complex128: low 4 warps / two buffers, high 4 columns / two buffers.
-constexpr int kLowCfgsF = 2, kHighCfgsF = 2, kLowCfgsD = 1, kHighCfgsD = 1;
+constexpr int kLowCfgsF = 2, kHighCfgsF = 3, kLowCfgsD = 1, kHighCfgsD = 1;
 template <typename R> constexpr int high_colb() { return sizeof(R) == 4 ? 3 : 2; }
 
 template <typename R, int W, int NB>
 size_t low_smem() { return (size_t)W * LowShape<W, NB>::PER_WARP * sizeof(cplx<R>); }
-template <typename R, int NB>
+template <typename R, int CB, int NB>
 size_t high_smem() {
-  constexpr int colb = high_colb<R>();
-  return (NB * (size_t)HighShape<colb>::BUF + HighShape<colb>::COLS * 12) * sizeof(cplx<R>);
+  return (NB * (size_t)HighShape<CB>::BUF + HighShape<CB>::COLS * 12) * sizeof(cplx<R>);
 }
 int num_low_cfgs(size_t esize) { return esize == 8 ? kLowCfgsF : kLowCfgsD; }
 int num_high_cfgs(size_t esize) { return esize == 8 ? kHighCfgsF : kHighCfgsD; }
@@ -713,7 +714,7 @@ int num_high_cfgs(size_t esize) { return esize == 8 ? kHighCfgsF : kHighCfgsD; }
 // Tensor map of the state as [batch * 1024 rows][2^(n-10) columns] of 8-byte
 // elements (a complex128 amplitude is two of them), boxes of 2^colb amplitudes
 // x 256 rows.
-qs_status make_tmap(qs_plan p, PassPlan* P) {
+qs_status make_tmap(qs_plan p, PassPlan* P, int colb, CUtensorMap* map) {
   static std::atomic<PFN_cuTensorMapEncodeTiled_v12000> encode_fn{nullptr};
   PFN_cuTensorMapEncodeTiled_v12000 encode = encode_fn.load();
   if (!encode) {
@@ -729,14 +730,22 @@ qs_status make_tmap(qs_plan p, PassPlan* P) {
   const uint64_t per = h->esize / 8;                     // 8-byte elements per amplitude
   cuuint64_t dims[2] = {(cuuint64_t)(1ull << (h->n - kWin)) * per, (cuuint64_t)h->batch * 1024};
   cuuint64_t strides[1] = {dims[0] * 8};
-  cuuint32_t box[2] = {(cuuint32_t)((1u << P->colb) * per), 256};
+  cuuint32_t box[2] = {(cuuint32_t)((1u << colb) * per), 256};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = encode(&P->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, h->state, dims, strides, box, estr,
+  (void)P;
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, h->state, dims, strides, box, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return pfail(p, QS_ERR_CUDA, "tensor map encode failed");
   return QS_OK;
 }
+
+// columns per high-window tile of the configuration launched (0 for the low window)
+int launch_colb(qs_plan p, const PassPlan& P) {
+  if (!P.high) return 0;
+  return p->h->esize == 8 && p->high_cfg == 2 ? 2 : P.colb;
+}
+int launch_tile_shift(qs_plan p, const PassPlan& P) { return p->h->n - kWin - launch_colb(p, P); }
 
 PassArgs pass_args(qs_plan p, const PassPlan& P, int synth, int fid) {
   qs_ctx* h = p->h;
@@ -753,8 +762,8 @@ PassArgs pass_args(qs_plan p, const PassPlan& P, int synth, int fid) {
   A.params = P.d_params;
   A.marked = h->m_marked;
   const uint64_t total = (uint64_t)h->batch << h->n;
-  A.tiles = P.high ? total >> (kWin + P.colb) : total >> kWin;
-  A.tile_shift = P.tile_shift;
+  A.tile_shift = launch_tile_shift(p, P);
+  A.tiles = total >> (kWin + launch_colb(p, P));
   A.status = h->dstatus + 2;
   A.synth = synth ? 1 : 0;
   A.basis = synth == 2 ? h->m_basis : nullptr;
@@ -803,11 +812,15 @@ cudaError_t launch_pass_kernel(qs_plan p, const PassPlan& P, cudaStream_t s, int
     constexpr int CB = high_colb<R>();
     if constexpr (sizeof(R) == 4) {
       if (p->high_cfg == 1) {
-        k_pass_high<R, CB, 1><<<grid(A.tiles, 2), HighShape<CB>::THREADS, high_smem<R, 1>(), s>>>(psi, P.tmap, A);
+        k_pass_high<R, CB, 1><<<grid(A.tiles, 2), HighShape<CB>::THREADS, high_smem<R, CB, 1>(), s>>>(psi, P.tmap, A);
+        return cudaGetLastError();
+      }
+      if (p->high_cfg == 2) {
+        k_pass_high<R, 2, 1><<<grid(A.tiles, 4), HighShape<2>::THREADS, high_smem<R, 2, 1>(), s>>>(psi, P.tmap4, A);
         return cudaGetLastError();
       }
     }
-    k_pass_high<R, CB, 2><<<grid(A.tiles, 1), HighShape<CB>::THREADS, high_smem<R, 2>(), s>>>(psi, P.tmap, A);
+    k_pass_high<R, CB, 2><<<grid(A.tiles, 1), HighShape<CB>::THREADS, high_smem<R, CB, 2>(), s>>>(psi, P.tmap, A);
   }
   return cudaGetLastError();
 }
@@ -824,20 +837,33 @@ __global__ void k_fid_finalize(const double* __restrict__ partials, int members,
   out[b] = re * re + im * im;
 }
 
+// Dynamic shared memory of a pass kernel, and a carveout preference just
+// large enough for `blocks` resident blocks per SM, so the rest of the
+// unified L1 caches the members' parameters and phase tables.
+template <typename K>
+cudaError_t set_pass_attrs(K kernel, size_t dyn, int blocks) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  if (e != cudaSuccess) return e;
+  constexpr size_t kSmemPerSM = 228 * 1024, kReservedPerBlock = 1024, kStatic = 1024;
+  const size_t need = (size_t)blocks * (dyn + kStatic + kReservedPerBlock);
+  const int pct = (int)std::min<size_t>(100, (need * 100 + kSmemPerSM - 1) / kSmemPerSM);
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+}
+
 cudaError_t set_smem_attrs(size_t esize) {
   static std::atomic<bool> done[2] = {false, false};
   const int which = esize == 8 ? 0 : 1;
   if (done[which]) return cudaSuccess;
-  const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e;
   if (esize == 8) {
-    e = cudaFuncSetAttribute(k_pass_low<float, 12, 2>, attr, (int)low_smem<float, 12, 2>());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass_low<float, 16, 1>, attr, (int)low_smem<float, 16, 1>());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass_high<float, 3, 2>, attr, (int)high_smem<float, 2>());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass_high<float, 3, 1>, attr, (int)high_smem<float, 1>());
+    e = set_pass_attrs(k_pass_low<float, 12, 2>, low_smem<float, 12, 2>(), 1);
+    if (e == cudaSuccess) e = set_pass_attrs(k_pass_low<float, 16, 1>, low_smem<float, 16, 1>(), 1);
+    if (e == cudaSuccess) e = set_pass_attrs(k_pass_high<float, 3, 2>, high_smem<float, 3, 2>(), 1);
+    if (e == cudaSuccess) e = set_pass_attrs(k_pass_high<float, 3, 1>, high_smem<float, 3, 1>(), 2);
+    if (e == cudaSuccess) e = set_pass_attrs(k_pass_high<float, 2, 1>, high_smem<float, 2, 1>(), 4);
   } else {
-    e = cudaFuncSetAttribute(k_pass_low<double, 4, 2>, attr, (int)low_smem<double, 4, 2>());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass_high<double, 2, 2>, attr, (int)high_smem<double, 2>());
+    e = set_pass_attrs(k_pass_low<double, 4, 2>, low_smem<double, 4, 2>(), 1);
+    if (e == cudaSuccess) e = set_pass_attrs(k_pass_high<double, 2, 2>, high_smem<double, 2, 2>(), 1);
   }
   if (e == cudaSuccess) done[which] = true;
   return e;
@@ -884,7 +910,7 @@ qs_status enqueue_run(qs_plan p, cudaStream_t s, int synth, int fid) {
       if (e == cudaSuccess) e = f32 ? launch_pass_kernel<float>(p, P, s, sy, fd) : launch_pass_kernel<double>(p, P, s, sy, fd);
       mark(P.high ? 2 : 1);
       if (e == cudaSuccess && fd) {
-        const int tiles = 1 << P.tile_shift;
+        const int tiles = 1 << launch_tile_shift(p, P);
         k_fid_finalize<<<(h->batch + 255) / 256, 256, 0, s>>>(p->d_fid, h->batch, tiles, h->small + kSmallOutIndex);
         e = cudaGetLastError();
       }
@@ -1052,8 +1078,9 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
       const size_t bytes = (size_t)P.stride * h->batch * (h->esize / 2);
       if (cudaMalloc(&P.d_params, std::max<size_t>(bytes, 16)) != cudaSuccess) st = pfail(p, QS_ERR_OUT_OF_MEMORY, "plan params");
     }
-    if (st == QS_OK && P.high) st = make_tmap(p, &P);
-    fid_tiles = (size_t)1 << P.tile_shift;
+    if (st == QS_OK && P.high) st = make_tmap(p, &P, P.colb, &P.tmap);
+    if (st == QS_OK && P.high && h->esize == 8) st = make_tmap(p, &P, 2, &P.tmap4);
+    fid_tiles = (size_t)1 << (h->n - kWin);             // the most tiles any configuration has
   }
   if (st == QS_OK && !p->passes.empty() &&
       cudaMalloc((void**)&p->d_fid, 2 * fid_tiles * h->batch * sizeof(double)) != cudaSuccess)

@@ -489,7 +489,7 @@ def test_every_kernel_configuration_gives_the_same_result(circ, n, batch):
         qs.qs_set_reference(h, np.asarray(ideal0))
         p = qs.qs_plan_create(h, pcirc.to_gates(ops))
         nl, nh = qs.qs_plan_configs(p, h)
-        assert (nl, nh) == (2, 2)
+        assert (nl, nh) == (2, 3)
         for lc in range(nl):
             for hc in range(nh):
                 qs.qs_plan_set_config(p, lc, hc, h)
@@ -499,6 +499,8 @@ def test_every_kernel_configuration_gives_the_same_result(circ, n, batch):
                 results[(lc, hc)] = (f, qs.qs_get_state(h).reshape(batch, -1))
         with pytest.raises(qs.QSError):
             qs.qs_plan_set_config(p, 2, 0, h)
+        with pytest.raises(qs.QSError):
+            qs.qs_plan_set_config(p, 0, 3, h)
         qs.qs_plan_destroy(p)
     f0, s0 = results[(0, 0)]
     for key, (f, st) in results.items():
@@ -519,7 +521,7 @@ def test_autotune_picks_a_configuration_and_results_stay_correct():
         lo, hi = qs.qs_plan_autotune(p, 2, e, SEED, h)
         assert lo > 0 and hi > 0
         cfg = qs.qs_plan_get_config(p, h)
-        assert 0 <= cfg[0] < 2 and 0 <= cfg[1] < 2
+        assert 0 <= cfg[0] < 2 and 0 <= cfg[1] < 3
         qs.qs_set_basis_state(h, 3)
         qs.qs_plan_run(p, e, SEED, 0, h)
         got = qs.qs_get_state(h).reshape(batch, -1)
