@@ -86,6 +86,11 @@ struct PassArgs {
   Flip flips[kMaxFlips];
   int out_start[12];          // out terms grouped by attach a (0..9) and 10 = none
   const OutTerm* outs;
+  // out factors per member and out-of-window tile value o (2^(n-10) of them):
+  // 11 complex, entry a = the product of the out terms attached to window bit
+  // a (10: none) whose out-of-window bits are set in o, times the deferred
+  // diagonal of bit a (10: the overall scale); null when the pass has none
+  const void* alpha_tab;
   int param_stride;           // R units per member
   const void* params;
   const uint64_t* marked;     // per-member flip index
@@ -275,23 +280,6 @@ __device__ __forceinline__ void apply_real_product(cplx<R> (&a)[kAmps], R c, con
   }
 }
 
-// deferred diagonal of window bit a (0..9), or the overall scale (a = 10)
-template <typename R>
-__device__ __forceinline__ R diag_factor_of(const PassArgs& A, const R* P, int a) {
-  return A.diag_off >= 0 ? __ldg(P + A.diag_off + a) : R(1);
-}
-
-// product of the out terms of attach a whose out-of-window bits are set in `fixed`
-template <typename R>
-__device__ __forceinline__ cplx<R> out_alpha(const PassArgs& A, const R* P, int a, uint64_t fixed) {
-  cplx<R> acc = mk<R>(R(1), R(0));
-  for (int i = A.out_start[a]; i < A.out_start[a + 1]; ++i) {
-    const OutTerm t = A.outs[i];
-    if ((fixed & t.cmask) == t.cmask) acc = cmul(acc, ld_c(P + t.off));
-  }
-  return acc;
-}
-
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -333,7 +321,7 @@ __device__ __forceinline__ void run_seg(cplx<R> (&a)[kAmps], const Seg& sg, cons
 // compile-time offsets; stores are coalesced from the stage-A layout.
 template <int WARPS, int NBUF> struct LowShape {
   static constexpr int BUF = 1024 + 32;                // a tile in the padded exchange layout
-  static constexpr int PER_WARP = NBUF * BUF + 12;     // tile buffers + out factors
+  static constexpr int PER_WARP = NBUF * BUF;          // tile buffers
   static constexpr int THREADS = WARPS * 32;
 };
 
@@ -359,7 +347,6 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
   __shared__ __align__(8) uint64_t bars[WARPS][2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   C* wbase = reinterpret_cast<C*>(smem_raw) + (size_t)warp * S::PER_WARP;
-  C* alpha_sm = wbase + NBUF * S::BUF;
   const uint64_t nmask = (1ull << A.n) - 1;
   const R* params = static_cast<const R*>(A.params);
   const uint32_t tile_bytes = 1024u * (uint32_t)sizeof(C);
@@ -463,19 +450,14 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
         flip_reg<R>(a, (w & ~regmask) == fixed, stage == 0 ? (int)((w >> 5) & 31) : (int)(w & 31));
       }
     }
-    if (A.out_start[11] > 0) {
-      if (lane < 11) {
-        const C f = out_alpha<R>(A, P, lane, mloc);
-        const R d = diag_factor_of<R>(A, P, lane);
-        alpha_sm[lane] = mk<R>(f.x * d, f.y * d);
-      }
-      __syncwarp();
+    if (A.alpha_tab) {
+      const C* al_g = static_cast<const C*>(A.alpha_tab) + ((member << (A.n - kWin)) | (mloc >> kWin)) * 11;
       C al[kRegBits];
-      C c = alpha_sm[10];
+      C c = ld_c(reinterpret_cast<const R*>(al_g + 10));
 #pragma unroll
       for (int r = 0; r < kRegBits; ++r) {
-        al[r] = alpha_sm[stage == 0 ? r + 5 : r];
-        if ((lane >> r) & 1) c = cmul(c, alpha_sm[stage == 0 ? r : r + 5]);
+        al[r] = ld_c(reinterpret_cast<const R*>(al_g + (stage == 0 ? r + 5 : r)));
+        if ((lane >> r) & 1) c = cmul(c, ld_c(reinterpret_cast<const R*>(al_g + (stage == 0 ? r : r + 5))));
       }
       apply_reg_product<R>(a, c, al);
     } else if (A.diag_off >= 0) {
@@ -554,7 +536,6 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ double fid_red[2][S::WARPS];
   C* smbase = reinterpret_cast<C*>(smem_raw);
-  C* alpha_sm = smbase + NBUF * S::BUF;                 // [COLS][12]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int col = lane & (S::COLS - 1);
   const int lh = lane >> COLB;
@@ -677,24 +658,17 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
         flip_reg<R>(a, (w & ~regmask) == fixed, (int)((w >> sh) & 31));
       }
     }
-    if (A.out_start[11] > 0) {
-      __syncthreads();
-      for (int i = threadIdx.x; i < S::COLS * 11; i += S::THREADS) {
-        const int c = i / 11, aa = i % 11;
-        const C f = out_alpha<R>(A, P, aa, (uint64_t)(tbits | (uint32_t)c));
-        const R d = diag_factor_of<R>(A, P, aa);
-        alpha_sm[c * 12 + aa] = mk<R>(f.x * d, f.y * d);
-      }
-      __syncthreads();
-      const C* al_c = alpha_sm + col * 12;
-      C c = al_c[10];
+    if (A.alpha_tab) {
+      const R* al_c = reinterpret_cast<const R*>(static_cast<const C*>(A.alpha_tab) +
+                                                 ((member << (A.n - kWin)) | tbits | (uint32_t)col) * 11);
+      C c = ld_c(al_c + 2 * 10);
       C al[kRegBits];
       const int xt = stage == 0 ? xa : xb;
 #pragma unroll
       for (int r = 0; r < kRegBits; ++r) {
-        al[r] = al_c[stage == 0 ? r + 5 : r];
+        al[r] = ld_c(al_c + 2 * (stage == 0 ? r + 5 : r));
         const int lt = stage == 0 ? r : r + 5;
-        if ((xt >> lt) & 1) c = cmul(c, al_c[lt]);
+        if ((xt >> lt) & 1) c = cmul(c, ld_c(al_c + 2 * lt));
       }
       apply_reg_product<R>(a, c, al);
     } else if (A.diag_off >= 0) {

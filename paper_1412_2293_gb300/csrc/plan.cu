@@ -80,6 +80,8 @@ struct Producer {
   uint32_t off;
 };
 
+struct OutStarts { int v[12]; };   // out terms of attach a: [v[a], v[a + 1])
+
 struct Contrib {          // DWIN contribution: partner local bit m, gate
   int m;
   int gate;
@@ -268,6 +270,47 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
   }
 }
 
+// Out factors of every tile of a pass: for member b and each value o of the
+// out-of-window bits, entry (o, a) = the product of the out terms attached to
+// window bit a (a = 10: attached to none) whose out-of-window bits are all set
+// in o, times the deferred real diagonal of bit a (the overall scale for
+// a = 10).  The pass kernels read the 11 entries of their tile directly.
+template <typename R>
+__global__ void __launch_bounds__(256) k_out_table(cplx<R>* __restrict__ tab, const R* __restrict__ params, int stride,
+                                                   const OutTerm* __restrict__ outs, OutStarts starts, int diag_off,
+                                                   int obits, int low, uint32_t chunks) {
+  // one member per block: its terms' masks and factors staged in shared memory
+  extern __shared__ unsigned char ot_sm[];
+  const int nterms = starts.v[11];
+  uint64_t* masks = reinterpret_cast<uint64_t*>(ot_sm);
+  cplx<R>* fac = reinterpret_cast<cplx<R>*>(masks + ((nterms + 1) & ~1));   // 16-byte aligned
+  const uint64_t b = blockIdx.x / chunks;
+  const uint64_t per = (11ull << obits);
+  const R* P = params + b * (uint64_t)stride;
+  for (int k = threadIdx.x; k < nterms; k += blockDim.x) {
+    const OutTerm t = outs[k];
+    masks[k] = t.cmask;
+    fac[k] = mk<R>(P[t.off], P[t.off + 1]);
+  }
+  __syncthreads();
+  const uint64_t i = (uint64_t)(blockIdx.x % chunks) * blockDim.x + threadIdx.x;
+  if (i >= per) return;
+  const uint64_t o = i / 11;
+  const int a = (int)(i % 11);
+  const uint64_t fixed = low ? o << kWin : o;           // member-local out-of-window bits
+  R re = R(1), im = R(0);
+  for (int k = starts.v[a]; k < starts.v[a + 1]; ++k) {
+    if ((fixed & masks[k]) == masks[k]) {
+      const cplx<R> f = fac[k];
+      const R nr = re * f.x - im * f.y;
+      im = re * f.y + im * f.x;
+      re = nr;
+    }
+  }
+  const R d = diag_off >= 0 ? P[diag_off + a] : R(1);
+  tab[b * per + i] = mk<R>(re * d, im * d);
+}
+
 }  // namespace fused
 }  // namespace qs
 
@@ -312,6 +355,7 @@ struct PassPlan {
   Producer* d_prods = nullptr;
   Contrib* d_contribs = nullptr;
   void* d_params = nullptr;
+  void* d_alpha = nullptr;        // per member and out-of-window tile value: 11 out factors
 };
 
 struct Step {
@@ -340,7 +384,8 @@ struct qs_plan_s {
   int colb = 3;
   int low_cfg = 0;                // kernel configuration of each window geometry (see launch_pass_kernel)
   int high_cfg = 0;
-  int launches = 0;
+  int launches = 0;               // timing slots of a run (precompute, pass, single step)
+  int kernels = 0;                // kernels one run launches
   bool timing = false;
   std::vector<cudaEvent_t> events;     // launches + 1 when timing
   std::vector<int> event_kinds;
@@ -706,7 +751,7 @@ template <typename R, int W, int NB>
 size_t low_smem() { return (size_t)W * LowShape<W, NB>::PER_WARP * sizeof(cplx<R>); }
 template <typename R, int CB, int NB>
 size_t high_smem() {
-  return (NB * (size_t)HighShape<CB>::BUF + HighShape<CB>::COLS * 12) * sizeof(cplx<R>);
+  return NB * (size_t)HighShape<CB>::BUF * sizeof(cplx<R>);
 }
 int num_low_cfgs(size_t esize) { return esize == 8 ? kLowCfgsF : kLowCfgsD; }
 int num_high_cfgs(size_t esize) { return esize == 8 ? kHighCfgsF : kHighCfgsD; }
@@ -758,6 +803,7 @@ PassArgs pass_args(qs_plan p, const PassPlan& P, int synth, int fid) {
   for (size_t i = 0; i < P.flips.size(); ++i) A.flips[i] = P.flips[i];
   for (int i = 0; i < 12; ++i) A.out_start[i] = P.out_start[i];
   A.outs = P.d_outs;
+  A.alpha_tab = P.d_alpha;
   A.param_stride = P.stride;
   A.params = P.d_params;
   A.marked = h->m_marked;
@@ -785,6 +831,15 @@ cudaError_t launch_precompute(qs_plan p, const PassPlan& P, cudaStream_t s) {
   k_precompute<R><<<h->batch, 128, pre_smem, s>>>((R*)P.d_params, P.stride, p->d_gates, P.d_prods,
                                                    (int)P.prods.size(), P.d_contribs, (int)P.contribs.size(),
                                                    P.num_dwin, P.diag_off, src, p->d_run);
+  if (P.d_alpha) {
+    OutStarts st{};
+    for (int i = 0; i < 12; ++i) st.v[i] = P.out_start[i];
+    const int obits = h->n - kWin;
+    const uint32_t chunks = (uint32_t)(((11ull << obits) + 255) / 256);
+    const size_t sm = (size_t)((P.out_start[11] + 1) & ~1) * sizeof(uint64_t) + (size_t)P.out_start[11] * sizeof(cplx<R>);
+    k_out_table<R><<<(unsigned)(chunks * (uint64_t)h->batch), 256, sm, s>>>(
+        (cplx<R>*)P.d_alpha, (const R*)P.d_params, P.stride, P.d_outs, st, P.diag_off, obits, P.high ? 0 : 1, chunks);
+  }
   return cudaGetLastError();
 }
 
@@ -1077,6 +1132,10 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
     if (st == QS_OK) {
       const size_t bytes = (size_t)P.stride * h->batch * (h->esize / 2);
       if (cudaMalloc(&P.d_params, std::max<size_t>(bytes, 16)) != cudaSuccess) st = pfail(p, QS_ERR_OUT_OF_MEMORY, "plan params");
+      // out factors of every tile: members x 2^(n-10) tile values x 11 complex
+      const size_t alpha_bytes = (((size_t)h->batch * 11) << (h->n - kWin)) * h->esize;
+      if (st == QS_OK && P.out_start[11] > 0 && cudaMalloc(&P.d_alpha, alpha_bytes) != cudaSuccess)
+        st = pfail(p, QS_ERR_OUT_OF_MEMORY, "plan out factors");
     }
     if (st == QS_OK && P.high) st = make_tmap(p, &P, P.colb, &P.tmap);
     if (st == QS_OK && P.high && h->esize == 8) st = make_tmap(p, &P, 2, &P.tmap4);
@@ -1091,6 +1150,10 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
   if (st != QS_OK) { qs_plan_destroy(p); return st; }
   p->launches = 0;
   for (const Step& s : p->steps) p->launches += s.kind == 0 ? 2 : 1;
+  // kernels launched per run (the out-factor table is timed with the precompute)
+  p->kernels = p->launches;
+  for (const Step& s : p->steps)
+    if (s.kind == 0 && p->passes[s.pass].d_alpha) ++p->kernels;
   *out = p;
   return QS_OK;
 }
@@ -1270,7 +1333,7 @@ qs_status qs_plan_last_times(qs_plan p, double* ms, int* kinds, int cap, int* co
 qs_status qs_plan_info(qs_plan p, int* passes, int* launches) {
   if (!p) return QS_ERR_INVALID_ARG;
   if (passes) *passes = (int)p->steps.size();
-  if (launches) *launches = p->launches;
+  if (launches) *launches = p->kernels;
   return QS_OK;
 }
 
@@ -1279,7 +1342,7 @@ qs_status qs_plan_destroy(qs_plan p) {
   if (p->h) cudaStreamSynchronize(p->h->stream);
   for (auto& x : p->exec) if (x) cudaGraphExecDestroy(x);
   for (auto& P : p->passes) {
-    void* ptrs[] = {P.d_ops, P.d_outs, P.d_prods, P.d_contribs, P.d_params};
+    void* ptrs[] = {P.d_ops, P.d_outs, P.d_prods, P.d_contribs, P.d_params, P.d_alpha};
     for (void* x : ptrs) if (x) cudaFree(x);
   }
   if (p->d_gates) cudaFree(p->d_gates);
