@@ -257,8 +257,9 @@ qs_status qs_plan_last_times(qs_plan p, double* ms, int* kinds, int cap, int* co
 /* Kernel configuration of the fused passes (no counterpart in the paper: the
  * tiling of the update, Sec. 2, is the implementation's).  For each window
  * geometry (low: qubits 0..9, high: the 10 highest) a configuration index in
- * [0, count): complex64 has two low and three high -- low 0: 12 warps, two
- * tile buffers per warp; low 1: 16 warps, one buffer; high 0: one block of
+ * [0, count): complex64 has three low and three high -- low 0: 12 warps, two
+ * tile buffers per warp; low 1: 16 warps, one buffer; low 2: 12 warps, one
+ * buffer; high 0: one block of
  * 8 warps per SM, two buffers; high 1: two such blocks per SM, one buffer;
  * high 2: four blocks of 4 warps per SM (4-column tiles), one buffer --
  * complex128 one of each.

@@ -740,11 +740,12 @@ qs_status upload(qs_plan p, T** dst, const std::vector<T>& v) {
 //   low  0: 12 warps, two tile buffers per warp (registers <= 170)
 //   low  1: 16 warps, one buffer per warp, next copy issued after the tile's
 //           last shared read (registers <= 128)
+//   low  2: 12 warps, one buffer per warp (registers <= 170)
 //   high 0: one block of 8 warps per SM, two tile buffers
 //   high 1: two blocks per SM, one buffer each (registers <= 128)
 //   high 2: four blocks of 4 warps per SM (tiles of 4 columns), one buffer each
 // complex128: low 4 warps / two buffers, high 4 columns / two buffers.
-constexpr int kLowCfgsF = 2, kHighCfgsF = 3, kLowCfgsD = 1, kHighCfgsD = 1;
+constexpr int kLowCfgsF = 3, kHighCfgsF = 3, kLowCfgsD = 1, kHighCfgsD = 1;
 template <typename R> constexpr int high_colb() { return sizeof(R) == 4 ? 3 : 2; }
 
 template <typename R, int W, int NB>
@@ -858,6 +859,8 @@ cudaError_t launch_pass_kernel(qs_plan p, const PassPlan& P, cudaStream_t s, int
     if constexpr (sizeof(R) == 4) {
       if (p->low_cfg == 1)
         k_pass_low<R, 16, 1><<<grid((A.tiles + 15) / 16, 1), 16 * 32, low_smem<R, 16, 1>(), s>>>(psi, A);
+      else if (p->low_cfg == 2)
+        k_pass_low<R, 12, 1><<<grid((A.tiles + 11) / 12, 1), 12 * 32, low_smem<R, 12, 1>(), s>>>(psi, A);
       else
         k_pass_low<R, 12, 2><<<grid((A.tiles + 11) / 12, 1), 12 * 32, low_smem<R, 12, 2>(), s>>>(psi, A);
     } else {
@@ -913,6 +916,7 @@ cudaError_t set_smem_attrs(size_t esize) {
   if (esize == 8) {
     e = set_pass_attrs(k_pass_low<float, 12, 2>, low_smem<float, 12, 2>(), 1);
     if (e == cudaSuccess) e = set_pass_attrs(k_pass_low<float, 16, 1>, low_smem<float, 16, 1>(), 1);
+    if (e == cudaSuccess) e = set_pass_attrs(k_pass_low<float, 12, 1>, low_smem<float, 12, 1>(), 1);
     if (e == cudaSuccess) e = set_pass_attrs(k_pass_high<float, 3, 2>, high_smem<float, 3, 2>(), 1);
     if (e == cudaSuccess) e = set_pass_attrs(k_pass_high<float, 3, 1>, high_smem<float, 3, 1>(), 2);
     if (e == cudaSuccess) e = set_pass_attrs(k_pass_high<float, 2, 1>, high_smem<float, 2, 1>(), 4);

@@ -489,7 +489,7 @@ def test_every_kernel_configuration_gives_the_same_result(circ, n, batch):
         qs.qs_set_reference(h, np.asarray(ideal0))
         p = qs.qs_plan_create(h, pcirc.to_gates(ops))
         nl, nh = qs.qs_plan_configs(p, h)
-        assert (nl, nh) == (2, 3)
+        assert (nl, nh) == (3, 3)
         for lc in range(nl):
             for hc in range(nh):
                 qs.qs_plan_set_config(p, lc, hc, h)
@@ -498,7 +498,7 @@ def test_every_kernel_configuration_gives_the_same_result(circ, n, batch):
                 f = qs.qs_plan_run_fidelity(p, e, SEED, 0, h)
                 results[(lc, hc)] = (f, qs.qs_get_state(h).reshape(batch, -1))
         with pytest.raises(qs.QSError):
-            qs.qs_plan_set_config(p, 2, 0, h)
+            qs.qs_plan_set_config(p, 3, 0, h)
         with pytest.raises(qs.QSError):
             qs.qs_plan_set_config(p, 0, 3, h)
         qs.qs_plan_destroy(p)
@@ -521,7 +521,7 @@ def test_autotune_picks_a_configuration_and_results_stay_correct():
         lo, hi = qs.qs_plan_autotune(p, 2, e, SEED, h)
         assert lo > 0 and hi > 0
         cfg = qs.qs_plan_get_config(p, h)
-        assert 0 <= cfg[0] < 2 and 0 <= cfg[1] < 3
+        assert 0 <= cfg[0] < 3 and 0 <= cfg[1] < 3
         qs.qs_set_basis_state(h, 3)
         qs.qs_plan_run(p, e, SEED, 0, h)
         got = qs.qs_get_state(h).reshape(batch, -1)
