@@ -499,6 +499,7 @@ class Server:
             err = None
         except BaseException as exc:
             res, err = None, exc
+        done = []
         with self.lock:
             if err is not None:
                 self.errors.append(err)
@@ -508,7 +509,9 @@ class Server:
                 for jid in done:
                     st = self.sched.jobs[jid]
                     self.results[jid] = JobResult(jid, st.fidelities, st.arrival, st.finish)
-                    self.ex.release_job(jid)
+        for jid in done:                          # frees device memory: outside the lock
+            self.ex.release_job(jid)
+        with self.lock:
             self.free_workers.append(w)
             self.lock.notify_all()
 
