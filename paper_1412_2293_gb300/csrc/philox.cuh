@@ -59,4 +59,18 @@ __device__ __forceinline__ double2 noise_normals(uint64_t seed, uint64_t traj, u
   return make_double2(r * c, r * s);
 }
 
+// The same draw with the logarithm, square root and cosine/sine evaluated in
+// FP32 (for complex64 simulation, where the noise angle only enters FP32
+// arithmetic): the words and uniforms are as above; the normals agree with
+// the FP64 ones to a few FP32 ulp.
+__device__ __forceinline__ float2 noise_normals_f32(uint64_t seed, uint64_t traj, uint64_t gate_id) {
+  const Words4 w = noise_words(seed, traj, gate_id);
+  const float u1 = (float)open_uniform53(w.w[0], w.w[1]);
+  const float u2 = (float)open_uniform53(w.w[2], w.w[3]);
+  const float r = sqrtf(-2.0f * logf(u1));
+  float s, c;
+  sincospif(2.0f * u2, &s, &c);                         // sin, cos of 2 pi u2
+  return make_float2(r * c, r * s);
+}
+
 }  // namespace qs

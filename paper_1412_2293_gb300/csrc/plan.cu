@@ -102,15 +102,32 @@ __device__ __forceinline__ void member_noise(const NoiseSrc& src, const RunParam
   *traj = src.traj ? src.traj[b] : rp->traj0 + (uint64_t)b;
 }
 
+// sin and cos of the noise angle e xi_a of one gate and member: FP64 for
+// complex128; FP32 for complex64, whose amplitudes the angle only enters in
+// FP32 (the normals then come from noise_normals_f32)
+template <typename R>
+__device__ __forceinline__ void noise_sincos(double e, uint64_t seed, uint64_t traj, uint64_t gid, double* s, double* c) {
+  if constexpr (sizeof(R) == 4) {
+    const float2 xi = noise_normals_f32(seed, traj, gid);
+    float sf, cf;
+    sincosf((float)e * xi.x, &sf, &cf);
+    *s = sf;
+    *c = cf;
+  } else {
+    const double2 xi = noise_normals(seed, traj, gid);
+    sincos(e * xi.x, s, c);
+  }
+}
+
 // factor of the |1..1> entry of a diag(1,..,1,x) gate for one member
+template <typename R>
 __device__ __forceinline__ double2 diag_factor(const DGate& g, double e, uint64_t seed, uint64_t traj,
                                                uint64_t gid) {
   const int d = 1 << g.k;
   double re = g.U[2 * ((d - 1) * d + (d - 1))], im = g.U[2 * ((d - 1) * d + (d - 1)) + 1];
   if (g.noisy && g.noise == QS_NOISE_PHASE) {
-    const double2 xi = noise_normals(seed, traj, gid);
     double s, c;
-    sincos(e * xi.x, &s, &c);
+    noise_sincos<R>(e, seed, traj, gid, &s, &c);
     const double t = re * c + im * s;                   // x * e^{-i e xi}
     im = im * c - re * s;
     re = t;
@@ -119,13 +136,13 @@ __device__ __forceinline__ double2 diag_factor(const DGate& g, double e, uint64_
 }
 
 // Member's noisy 2x2 matrix of a one-qubit gate (interleaved complex, row-major).
+template <typename R>
 __device__ __forceinline__ void noisy_matrix(const DGate& g, double e, uint64_t seed, uint64_t traj, uint64_t gid,
                                              double (&m)[8]) {
   for (int q = 0; q < 8; ++q) m[q] = g.U[q];
   if (!g.noisy) return;
-  const double2 xi = noise_normals(seed, traj, gid);
   double s, c;
-  sincos(e * xi.x, &s, &c);
+  noise_sincos<R>(e, seed, traj, gid, &s, &c);
   if (g.noise == QS_NOISE_ROTATION) {
     // U * [[c, s], [-s, c]]
     for (int r = 0; r < 2; ++r) {
@@ -168,13 +185,13 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
   if (threadIdx.x < kPhaseThreads) {
     for (int i = threadIdx.x; i < num_contribs; i += kPhaseThreads) {
       const DGate& g = gates[contribs[i].gate];
-      pre_sm[i] = diag_factor(g, e, seed, traj, rp->gate_id0 + g.gate_pos);
+      pre_sm[i] = diag_factor<R>(g, e, seed, traj, rp->gate_id0 + g.gate_pos);
     }
     for (int i = threadIdx.x; i < num_prods; i += kPhaseThreads) {
       const Producer p = prods[i];
       if (p.kind == PD_OUT) {
         const DGate& g = gates[p.gate];
-        const double2 f = diag_factor(g, e, seed, traj, rp->gate_id0 + g.gate_pos);
+        const double2 f = diag_factor<R>(g, e, seed, traj, rp->gate_id0 + g.gate_pos);
         out[p.off] = (R)f.x;
         out[p.off + 1] = (R)f.y;
       }
@@ -196,7 +213,7 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
       if (p.kind != PD_DENSE || p.j != J) continue;
       const DGate& g = gates[p.gate];
       double m[8];
-      noisy_matrix(g, e, seed, traj, rp->gate_id0 + g.gate_pos, m);
+      noisy_matrix<R>(g, e, seed, traj, rp->gate_id0 + g.gate_pos, m);
       m[0] *= pa; m[1] *= pa; m[4] *= pa; m[5] *= pa;   // column 0
       m[2] *= pd; m[3] *= pd; m[6] *= pd; m[7] *= pd;   // column 1
       if (p.real) {
