@@ -154,36 +154,42 @@ __device__ __forceinline__ double tscale(double a, double v) { return a * v; }
 __device__ __forceinline__ double2 tscale(double2 a, double v) { return make_double2(a.x * v, a.y * v); }
 __device__ __forceinline__ double tphase(double a, double inv) { return a * inv; }                     // sign
 __device__ __forceinline__ double2 tphase(double2 a, double inv) { return make_double2(a.x * inv, -a.y * inv); }  // e^{-i arg}
+__device__ __forceinline__ double trsqrt(double a) { return rsqrt(a); }
+
 
 constexpr int kJP = kMaxGramDim + 1;                    // pitch of the Jacobi arrays
 
 // Parallel cyclic Jacobi on the Hermitian (or real symmetric) A (M x M,
-// pitch kJP), accumulating V.  Each step applies Mp/2 disjoint rotations
-// from the round-robin schedule: pair 0 = (Mp-1, s), pair i = ((s+i) mod
-// (Mp-1), (s-i) mod (Mp-1)).  A rotation zeroes a_pq: a phase makes a_pq
-// real, then the classical angle; the tangent is found in FP32 (any tangent
-// gives an exactly unitary rotation in FP64, the next sweep removes what is
-// left), cos and sin from one FP64 rsqrt.  The update A <- R^dagger A R is
-// done per 2x2 block of the upper triangle and mirrored.  Sweeps stop when
-// no |a_pq| exceeds kRotTol * max|a_ii|.
+// pitch kJP), accumulating V (V <- V R, from any unitary start).  Each step
+// applies Mp/2 disjoint rotations from the round-robin schedule: pair 0 =
+// (Mp-1, s), pair i = ((s+i) mod (Mp-1), (s-i) mod (Mp-1)).  A rotation
+// zeroes a_pq: a phase makes a_pq real, then the classical angle; the tangent
+// is found in FP32 (any tangent gives an exactly unitary rotation, the next
+// sweep removes what is left), cos and sin from one rsqrt.  The update
+// A <- R^dagger A R is done per 2x2 block of the upper triangle and mirrored;
+// a step in which no pair rotates skips it.  Sweeps stop when no |a_pq|
+// exceeds tol * max|a_ii|.  T is double / double2 (FP64) or float / float2
+// (the FP32 pre-pass).  Returns false if the sweep bound was reached.
 template <typename T>
-__device__ void jacobi(T* A, T* V, int M, int* status) {
+__device__ bool jacobi(T* A, T* V, int M, double tol) {
+  using RT = decltype(tre(T{}));
   __shared__ T rot[kMaxGramDim / 2][4];
   __shared__ int pp[kMaxGramDim / 2], qq[kMaxGramDim / 2];
-  __shared__ double thr2;
+  __shared__ RT thr2;
   const int tid = threadIdx.x;
   const int Mp = M + (M & 1);
   const int nb = Mp / 2;
   const int nblk = nb * (nb + 1) / 2;
   for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
     if (tid == 0) {
-      double dmax = 0.0;
+      RT dmax = 0;
       for (int p = 0; p < M; ++p) dmax = fmax(dmax, fabs(tre(A[p * kJP + p])));
-      thr2 = (kRotTol * dmax) * (kRotTol * dmax);
+      thr2 = ((RT)tol * dmax) * ((RT)tol * dmax);
     }
     __syncthreads();
     int did = 0;
     for (int st = 0; st < Mp - 1; ++st) {
+      int sd = 0;
       if (tid < nb) {
         int p, q;
         if (tid == 0) { p = st; q = Mp - 1; }
@@ -194,16 +200,16 @@ __device__ void jacobi(T* A, T* V, int M, int* status) {
         T R00 = tscal<T>(1.0), R01 = tscal<T>(0.0), R10 = tscal<T>(0.0), R11 = tscal<T>(1.0);
         if (q < M) {
           const T apq = A[p * kJP + q];
-          const double a2 = tabs2(apq);
-          if (a2 > thr2 && a2 > 0.0) {
-            did = 1;
-            const double inv = rsqrt(a2);
+          const RT a2 = tabs2(apq);
+          if (a2 > thr2 && a2 > (RT)0) {
+            sd = 1;
+            const RT inv = trsqrt(a2);
             const T ph = tphase(apq, inv);
-            const double theta = (tre(A[q * kJP + q]) - tre(A[p * kJP + p])) * 0.5 * inv;
+            const RT theta = (tre(A[q * kJP + q]) - tre(A[p * kJP + p])) * (RT)0.5 * inv;
             const float th = (float)theta;
             const float tf = copysignf(1.0f, th) / (fabsf(th) + sqrtf(1.0f + th * th));
-            const double t = (double)tf;
-            const double c = rsqrt(1.0 + t * t), sn = t * c;
+            const RT t = (RT)tf;
+            const RT c = trsqrt((RT)1 + t * t), sn = t * c;
             R00 = tscal<T>(c);
             R01 = tscal<T>(sn);
             R10 = tscale(ph, -sn);
@@ -212,7 +218,8 @@ __device__ void jacobi(T* A, T* V, int M, int* status) {
         }
         rot[tid][0] = R00; rot[tid][1] = R01; rot[tid][2] = R10; rot[tid][3] = R11;
       }
-      __syncthreads();
+      if (!__syncthreads_or(sd)) continue;               // nothing rotates in this step
+      did = 1;
       for (int w = tid; w < nblk + M * nb; w += blockDim.x) {
         if (w < nblk) {
           // block (i, j), i <= j: Y = R_i^dagger X R_j
@@ -256,9 +263,9 @@ __device__ void jacobi(T* A, T* V, int M, int* status) {
       }
       __syncthreads();
     }
-    if (!__syncthreads_or(did)) return;                  // no rotation in the whole sweep
+    if (!__syncthreads_or(did)) return true;             // no rotation in the whole sweep
   }
-  if (tid == 0) status[0] = 1;                           // not converged within the sweep bound
+  return false;
 }
 
 // One block: eigendecomposition of the Hermitian G (M x M) by parallel cyclic
@@ -272,13 +279,10 @@ __global__ void __launch_bounds__(512) k_eig_truncate(const double* __restrict__
                                                       double* scale_out, int* status) {
   __shared__ double2 A[kMaxGramDim][kJP];
   __shared__ double2 V[kMaxGramDim][kJP];
-  __shared__ double2 rot[kMaxGramDim / 2][4];          // Gram-Schmidt scratch
   __shared__ int order[kMaxGramDim + 1];
   __shared__ double lam[kMaxGramDim];
   // canonical vectors (columns) reuse A's storage once the eigenvalues are read
   auto& basis = A;
-  __shared__ double2 vtmp[kMaxGramDim];
-  __shared__ double vnorm;
   __shared__ int nbasis;
 
   const int tid = threadIdx.x;
@@ -292,7 +296,7 @@ __global__ void __launch_bounds__(512) k_eig_truncate(const double* __restrict__
       V[p][q] = make_double2(p == q ? 1.0 : 0.0, 0.0);
     }
     __syncthreads();
-    jacobi<double2>(&A[0][0], &V[0][0], M, status);
+    if (!jacobi<double2>(&A[0][0], &V[0][0], M, kRotTol) && tid == 0) status[0] = 1;
     for (int i = tid; i < M; i += blockDim.x) lam[i] = A[i][i].x;
     __syncthreads();
   } else {
@@ -304,7 +308,7 @@ __global__ void __launch_bounds__(512) k_eig_truncate(const double* __restrict__
       Vr[p * kJP + q] = p == q ? 1.0 : 0.0;
     }
     __syncthreads();
-    jacobi<double>(Ar, Vr, M, status);
+    if (!jacobi<double>(Ar, Vr, M, kRotTol) && tid == 0) status[0] = 1;
     for (int i = tid; i < M; i += blockDim.x) lam[i] = Ar[i * kJP + i];
     // widen V to complex in place: read everything first
     double hold[2] = {0.0, 0.0};
@@ -329,63 +333,54 @@ __global__ void __launch_bounds__(512) k_eig_truncate(const double* __restrict__
   const int keep = r < M ? r : M;
   const double lam1 = lam[order[0]] > 0.0 ? lam[order[0]] : 0.0;
 
-  // clusters (anchor = first member) and their canonical bases, until keep
-  int i0 = 0;
-  while (i0 < keep) {
-    int i1 = i0 + 1;
-    while (i1 < M && lam[order[i0]] - lam[order[i1]] <= kTieTol * lam1) ++i1;
-    const int s = i1 - i0;
-    const int first = nbasis;
-    // P = S S^dagger; GS of P e_j, j = 0..M-1, thresholds kGsAccept then kGsFallback
-    for (int pass = 0; pass < 2 && nbasis - first < s; ++pass) {
-      const double thr = pass == 0 ? kGsAccept : kGsFallback;
-      for (int j = 0; j < M && nbasis - first < s; ++j) {
-        // v = P e_j = sum_c S[:, c] conj(S[j, c])
-        for (int k = tid; k < M; k += blockDim.x) {
-          double2 acc = make_double2(0.0, 0.0);
-          for (int c = 0; c < s; ++c) {
-            const int col = order[i0 + c];
-            acc = zadd(acc, zmul(V[k][col], zconj(V[j][col])));
-          }
-          vtmp[k] = acc;
-        }
-        __syncthreads();
-        for (int rep = 0; rep < 2; ++rep) {
-          for (int u = first; u < nbasis; ++u) {
-            // v -= basis_u * <basis_u, v>   (dot product by warp 0)
-            if (tid < 32) {
-              double2 d = tid < M ? zmul(zconj(basis[tid][u]), vtmp[tid]) : make_double2(0.0, 0.0);
-              for (int o = 16; o; o >>= 1) {
-                d.x += __shfl_xor_sync(0xffffffffu, d.x, o);
-                d.y += __shfl_xor_sync(0xffffffffu, d.y, o);
-              }
-              if (tid == 0) rot[0][0] = d;
+  // clusters (anchor = first member) and their canonical bases, until keep;
+  // one warp, lane = row, dot products by shuffles (no block barriers)
+  if (tid < 32) {
+    const int lane = tid;
+    auto wsum = [](double v) {
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      return v;
+    };
+    int found = 0;
+    int i0 = 0;
+    while (i0 < keep) {
+      int i1 = i0 + 1;
+      while (i1 < M && lam[order[i0]] - lam[order[i1]] <= kTieTol * lam1) ++i1;
+      const int s = i1 - i0;
+      const int first = found;
+      // P = S S^dagger; GS of P e_j, j = 0..M-1, thresholds kGsAccept then kGsFallback
+      for (int pass = 0; pass < 2 && found - first < s; ++pass) {
+        const double thr = pass == 0 ? kGsAccept : kGsFallback;
+        for (int j = 0; j < M && found - first < s; ++j) {
+          // v = P e_j = sum_c S[:, c] conj(S[j, c])
+          double2 v = make_double2(0.0, 0.0);
+          if (lane < M)
+            for (int c = 0; c < s; ++c) {
+              const int col = order[i0 + c];
+              v = zadd(v, zmul(V[lane][col], zconj(V[j][col])));
             }
-            __syncthreads();
-            const double2 d = rot[0][0];
-            for (int k = tid; k < M; k += blockDim.x) vtmp[k] = zsub(vtmp[k], zmul(basis[k][u], d));
-            __syncthreads();
+          for (int rep = 0; rep < 2; ++rep)
+            for (int u = first; u < found; ++u) {
+              // v -= basis_u <basis_u, v>
+              const double2 b = lane < M ? basis[lane][u] : make_double2(0.0, 0.0);
+              const double2 t = zmul(zconj(b), v);
+              const double2 d = make_double2(wsum(t.x), wsum(t.y));
+              v = zsub(v, zmul(b, d));
+            }
+          const double vn = sqrt(wsum(v.x * v.x + v.y * v.y));
+          if (vn > thr) {
+            if (lane < M) basis[lane][found] = zscale(v, 1.0 / vn);
+            ++found;
+            __syncwarp();
           }
         }
-        if (tid < 32) {
-          double nv = tid < M ? vtmp[tid].x * vtmp[tid].x + vtmp[tid].y * vtmp[tid].y : 0.0;
-          for (int o = 16; o; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
-          if (tid == 0) vnorm = sqrt(nv);
-        }
-        __syncthreads();
-        if (vnorm > thr) {
-          const double inv = 1.0 / vnorm;
-          for (int k = tid; k < M; k += blockDim.x) basis[k][nbasis] = zscale(vtmp[k], inv);
-          __syncthreads();
-          if (tid == 0) nbasis = nbasis + 1;
-        }
-        __syncthreads();
       }
+      if (found - first < s && lane == 0) status[0] = 2;           // incomplete cluster
+      i0 = i1;
     }
-    if (nbasis - first < s && tid == 0) status[0] = 2;           // incomplete cluster
-    __syncthreads();
-    i0 = i1;
+    if (lane == 0) nbasis = found;
   }
+  __syncthreads();
 
   // outputs
   for (int i = tid; i < M * keep; i += blockDim.x) {
