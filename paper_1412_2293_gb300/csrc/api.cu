@@ -203,9 +203,9 @@ qs_status rank_truncate_from_work(qs_handle h, int M, int r, int normalize) {
   double* W = h->small + kSmallW;
   double* lam = h->small + kSmallLam;
   double* scale = h->small + kSmallScale;
-  QS_CUDA(h, qs::launch_gram(h, h->work, h->n, M, G));
+  QS_CUDA(h, qs::launch_gram(h, h->work, h->n, M, h->real_factor, G));
   QS_CUDA(h, qs::launch_eig_truncate(h, G, M, r, normalize, W, lam, scale, h->dstatus, h->dstatus + 1));
-  QS_CUDA(h, qs::launch_project(h, h->work, h->state, h->n, M, W, scale, h->dstatus));
+  QS_CUDA(h, qs::launch_project(h, h->work, h->state, h->n, M, h->real_factor, W, scale, h->dstatus));
   const int keep = std::min(r, M);
   // columns that are no longer live read as zero
   if (keep < h->cols) {
@@ -218,9 +218,15 @@ qs_status rank_truncate_from_work(qs_handle h, int M, int r, int normalize) {
 }
 
 // FIXED_RANK: L' = [E_1 L | ..], then truncation when K > 1.
+bool all_real(const std::vector<cd>& m) {
+  for (const auto& v : m) if (v.imag() != 0.0) return false;
+  return true;
+}
+
 qs_status rank_apply_kraus(qs_handle h, const int* targets, int k, const std::vector<std::vector<cd>>& ks) {
   const int K = (int)ks.size();
   const int d = 1 << k;
+  for (const auto& E : ks) if (!all_real(E)) h->real_factor = false;
   if (K == 1) {
     return apply_uniform(h, h->state, h->n, h->cols, targets, k, ks[0]);
   }
@@ -233,7 +239,7 @@ qs_status rank_apply_kraus(qs_handle h, const int* targets, int k, const std::ve
   QS_CUDA(h, cudaMemcpyAsync(h->small + kSmallE, e.data(), e.size() * sizeof(double),
                              cudaMemcpyHostToDevice, h->stream));
   const Targets tg = qs::make_targets(h->n, targets, k);
-  QS_CUDA(h, qs::launch_kraus_expand(h, h->state, h->work, h->n, h->cols, tg, h->small + kSmallE, K));
+  QS_CUDA(h, qs::launch_kraus_expand(h, h->state, h->work, h->n, h->cols, tg, h->real_factor, h->small + kSmallE, K));
   return rank_truncate_from_work(h, M, h->rank, h->normalize);
 }
 
@@ -337,6 +343,7 @@ qs_status qs_create(int n, int batch, int rank, qs_mode mode, qs_dtype dtype, vo
     e = cudaMemsetAsync(h->state, 0, h->state_elems * h->esize, h->stream),
     e = e == cudaSuccess ? qs::launch_set_basis(h, h->state, n, 1, 0, nullptr) : e;
   if (e != cudaSuccess) return bail(QS_ERR_CUDA);
+  h->real_factor = mode == QS_FIXED_RANK;                 // |0>
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(QS_ERR_CUDA);
   *out = h;
   return QS_OK;
@@ -385,6 +392,7 @@ qs_status qs_set_basis_state(qs_handle h, uint64_t x) {
     QS_CUDA(h, cudaMemsetAsync(h->state, 0, h->state_elems * h->esize, h->stream));
     QS_CUDA(h, qs::launch_set_basis(h, h->state, h->n, 1, x, nullptr));
     h->cols = 1;
+    h->real_factor = true;
   }
   return QS_OK;
 }
@@ -411,7 +419,10 @@ qs_status qs_apply_gate(qs_handle h, const int* targets, int k, const double* U)
   if (!valid_targets(h, targets, k, &why)) return fail(h, QS_ERR_INVALID_ARG, why);
   const auto M = to_cplx(U, 1 << k);
   if (h->mode == QS_STATEVEC) return apply_uniform(h, h->state, h->n, h->batch, targets, k, M);
-  if (h->mode == QS_FIXED_RANK) return apply_uniform(h, h->state, h->n, h->cols, targets, k, M);
+  if (h->mode == QS_FIXED_RANK) {
+    if (!all_real(M)) h->real_factor = false;
+    return apply_uniform(h, h->state, h->n, h->cols, targets, k, M);
+  }
   if (k > 2) return fail(h, QS_ERR_NOT_SUPPORTED, "DENSITY gates are limited to k <= 2");
   return dm_apply_channel(h, targets, k, {M});
 }
@@ -644,6 +655,11 @@ qs_status qs_set_state(qs_handle h, const double* host, size_t count) {
   if (count != h->state_elems) return fail(h, QS_ERR_INVALID_ARG, "count must equal qs_state_size");
   QS_CUDA(h, cudaStreamSynchronize(h->stream));
   h->pending = 0;
+  if (h->mode == QS_FIXED_RANK) {
+    bool real = true;
+    for (size_t i = 0; i < count && real; ++i) real = host[2 * i + 1] == 0.0;
+    h->real_factor = real;
+  }
   if (h->dtype == QS_C128) {
     QS_CUDA(h, cudaMemcpy(h->state, host, count * 16, cudaMemcpyHostToDevice));
   } else {

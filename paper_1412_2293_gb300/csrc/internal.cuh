@@ -83,6 +83,10 @@ struct qs_ctx {
   size_t work_elems = 0;
   int cols = 1;
   int normalize = 0;
+  // FIXED_RANK: every entry of L has a zero imaginary part (real start, real
+  // gates and Kraus operators so far); the channel kernels then use real
+  // arithmetic (the same results, a quarter of the FP64 work)
+  bool real_factor = false;
 
   // scratch (device)
   double* partials = nullptr;            // reduction partials
@@ -151,13 +155,13 @@ cudaError_t launch_dm_expect(qs_ctx* h, const void* rho, const void* ref, int n,
 cudaError_t launch_convert_ref(qs_ctx* h, const double* src_dev, void* dst, size_t count);
 
 // fixed rank
-cudaError_t launch_kraus_expand(qs_ctx* h, const void* L, void* Lp, int n, int m, const Targets& tg,
+cudaError_t launch_kraus_expand(qs_ctx* h, const void* L, void* Lp, int n, int m, const Targets& tg, bool real,
                                 const void* E_dev, int K);
-cudaError_t launch_gram(qs_ctx* h, const void* Lp, int n, int M, double* G_dev);
+cudaError_t launch_gram(qs_ctx* h, const void* Lp, int n, int M, bool real, double* G_dev);
 cudaError_t launch_eig_truncate(qs_ctx* h, const double* G_dev, int M, int r, int normalize,
                                 double* W_dev, double* lam_dev, double* scale_dev, int* keep_dev,
                                 int* status_dev);
-cudaError_t launch_project(qs_ctx* h, const void* Lp, void* L, int n, int M, const double* W_dev,
+cudaError_t launch_project(qs_ctx* h, const void* Lp, void* L, int n, int M, bool real, const double* W_dev,
                            const double* scale_dev, const int* keep_dev);
 
 // debug noise

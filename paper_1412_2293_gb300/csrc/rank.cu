@@ -12,6 +12,8 @@
 // projection L <- scale * L' W_r.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace qs {
@@ -30,8 +32,9 @@ __device__ __forceinline__ uint64_t insert0(uint64_t v, int s) {
   return ((v >> s) << (s + 1)) | (v & ((1ull << s) - 1));
 }
 
-// Lp[a*m + c] = E_a L[c]; one thread per (group, column).
-template <typename R, int K_Q>
+// Lp[a*m + c] = E_a L[c]; one thread per (group, column).  REAL: L and the
+// E_a are real (imaginary parts zero), real arithmetic.
+template <typename R, int K_Q, bool REAL>
 __global__ void __launch_bounds__(kExpBlock) k_kraus_expand(const cplx<R>* __restrict__ L,
                                                             cplx<R>* __restrict__ Lp, int n, int m,
                                                             Targets tg, const double* __restrict__ E,
@@ -51,48 +54,77 @@ __global__ void __launch_bounds__(kExpBlock) k_kraus_expand(const cplx<R>* __res
     uint64_t base = g;
 #pragma unroll
     for (int j = 0; j < K_Q; ++j) base = insert0(base, tg.sorted[j]);
-    C v[D];
+    if constexpr (REAL) {
+      R v[D];
 #pragma unroll
-    for (int l = 0; l < D; ++l) v[l] = L[(uint64_t)c * N + base + tg.off[l]];
-    for (int a = 0; a < K; ++a) {
-      C* out = Lp + (uint64_t)(a * m + c) * N + base;
+      for (int l = 0; l < D; ++l) v[l] = L[(uint64_t)c * N + base + tg.off[l]].x;
+      for (int a = 0; a < K; ++a) {
+        C* out = Lp + (uint64_t)(a * m + c) * N + base;
 #pragma unroll
-      for (int r = 0; r < D; ++r) {
-        C acc = mk<R>(R(0), R(0));
+        for (int r = 0; r < D; ++r) {
+          R acc = R(0);
 #pragma unroll
-        for (int q = 0; q < D; ++q) acc = cfma(sE[(a * D + r) * D + q], v[q], acc);
-        out[tg.off[r]] = acc;
+          for (int q = 0; q < D; ++q) acc = fma(sE[(a * D + r) * D + q].x, v[q], acc);
+          out[tg.off[r]] = mk<R>(acc, R(0));
+        }
+      }
+    } else {
+      C v[D];
+#pragma unroll
+      for (int l = 0; l < D; ++l) v[l] = L[(uint64_t)c * N + base + tg.off[l]];
+      for (int a = 0; a < K; ++a) {
+        C* out = Lp + (uint64_t)(a * m + c) * N + base;
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+          C acc = mk<R>(R(0), R(0));
+#pragma unroll
+          for (int q = 0; q < D; ++q) acc = cfma(sE[(a * D + r) * D + q], v[q], acc);
+          out[tg.off[r]] = acc;
+        }
       }
     }
   }
 }
 
 // Gram partials: block b sums rows [b*kGramRows, (b+1)*kGramRows) for every
-// (p <= q); partial layout [block][p][q] complex.
-template <typename R>
+// (p <= q), one thread per entry of the upper triangle; partial layout
+// [block][p][q] complex.  REAL: real arithmetic (imaginary parts are zero).
+template <typename R, bool REAL>
 __global__ void __launch_bounds__(256) k_gram_partials(const cplx<R>* __restrict__ Lp, int n, int M,
                                                        double* __restrict__ partials) {
-  __shared__ double2 tile[kMaxGramDim][kGramRows + 1];
+  using T = typename std::conditional<REAL, double, double2>::type;
+  __shared__ T tile[kMaxGramDim][kGramRows + 1];
   const uint64_t N = 1ull << n;
   const uint64_t r0 = (uint64_t)blockIdx.x * kGramRows;
   for (int i = threadIdx.x; i < M * kGramRows; i += blockDim.x) {
     const int p = i / kGramRows, x = i % kGramRows;
     const uint64_t row = r0 + x;
-    double2 v = make_double2(0.0, 0.0);
-    if (row < N) { const cplx<R> a = Lp[(uint64_t)p * N + row]; v = make_double2(a.x, a.y); }
-    tile[p][x] = v;
+    const cplx<R> a = row < N ? Lp[(uint64_t)p * N + row] : mk<R>(R(0), R(0));
+    if constexpr (REAL) tile[p][x] = a.x;
+    else tile[p][x] = make_double2(a.x, a.y);
   }
   __syncthreads();
-  const int pairs = M * M;
   double* out = partials + (size_t)blockIdx.x * 2 * M * M;
-  for (int idx = threadIdx.x; idx < pairs; idx += blockDim.x) {
-    const int p = idx / M, q = idx % M;
-    if (q < p) continue;
+  const int tri = M * (M + 1) / 2;
+  for (int idx = threadIdx.x; idx < tri; idx += blockDim.x) {
+    // idx -> (p, q), p <= q, row-major over the upper triangle
+    int p = 0, rem = idx;
+    while (rem >= M - p) { rem -= M - p; ++p; }
+    const int q = p + rem;
     double re = 0.0, im = 0.0;
-    for (int x = 0; x < kGramRows; ++x) {
-      const double2 a = tile[p][x], b = tile[q][x];
-      re += a.x * b.x + a.y * b.y;       // conj(a) * b
-      im += a.x * b.y - a.y * b.x;
+    if constexpr (REAL) {
+      double re2 = 0.0;
+      for (int x = 0; x < kGramRows; x += 2) {
+        re = fma(tile[p][x], tile[q][x], re);
+        re2 = fma(tile[p][x + 1], tile[q][x + 1], re2);
+      }
+      re += re2;
+    } else {
+      for (int x = 0; x < kGramRows; ++x) {
+        const double2 a = tile[p][x], b = tile[q][x];
+        re += a.x * b.x + a.y * b.y;       // conj(a) * b
+        im += a.x * b.y - a.y * b.x;
+      }
     }
     out[2 * (p * M + q)] = re;
     out[2 * (p * M + q) + 1] = im;
@@ -398,8 +430,9 @@ __global__ void __launch_bounds__(512) k_eig_truncate(const double* __restrict__
   }
 }
 
-// L[c] = scale * sum_p Lp[p] W[p][c] for c < keep; one thread per (row, c).
-template <typename R>
+// L[c] = scale * sum_p Lp[p] W[p][c] for c < keep; one thread per row, all
+// kept columns (each element of L' is read once).  REAL: L' and W are real.
+template <typename R, bool REAL>
 __global__ void __launch_bounds__(256) k_project(const cplx<R>* __restrict__ Lp, cplx<R>* __restrict__ L,
                                                  int n, int M, const double* __restrict__ W,
                                                  const int* __restrict__ keep_p,
@@ -411,22 +444,40 @@ __global__ void __launch_bounds__(256) k_project(const cplx<R>* __restrict__ Lp,
     sW[i] = make_double2(W[2 * i] * scale, W[2 * i + 1] * scale);
   __syncthreads();
   const uint64_t N = 1ull << n;
-  const uint64_t work = N * (uint64_t)keep;
-  for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < work;
-       w += (uint64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(w / N);
-    const uint64_t x = w - (uint64_t)c * N;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int p = 0; p < M; ++p) {
-      const cplx<R> a = Lp[(uint64_t)p * N + x];
-      acc = zadd(acc, zmul(make_double2(a.x, a.y), sW[p * keep + c]));
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += (uint64_t)gridDim.x * blockDim.x) {
+    if constexpr (REAL) {
+      double acc[kMaxRank];
+#pragma unroll
+      for (int c = 0; c < kMaxRank; ++c) acc[c] = 0.0;
+      for (int p = 0; p < M; ++p) {
+        const double a = Lp[(uint64_t)p * N + x].x;
+#pragma unroll
+        for (int c = 0; c < kMaxRank; ++c)
+          if (c < keep) acc[c] = fma(a, sW[p * keep + c].x, acc[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < kMaxRank; ++c)
+        if (c < keep) L[(uint64_t)c * N + x] = mk<R>((R)acc[c], R(0));
+    } else {
+      double2 acc[kMaxRank];
+#pragma unroll
+      for (int c = 0; c < kMaxRank; ++c) acc[c] = make_double2(0.0, 0.0);
+      for (int p = 0; p < M; ++p) {
+        const cplx<R> a = Lp[(uint64_t)p * N + x];
+        const double2 ad = make_double2(a.x, a.y);
+#pragma unroll
+        for (int c = 0; c < kMaxRank; ++c)
+          if (c < keep) acc[c] = zadd(acc[c], zmul(ad, sW[p * keep + c]));
+      }
+#pragma unroll
+      for (int c = 0; c < kMaxRank; ++c)
+        if (c < keep) L[(uint64_t)c * N + x] = mk<R>((R)acc[c].x, (R)acc[c].y);
     }
-    L[(uint64_t)c * N + x] = mk<R>((R)acc.x, (R)acc.y);
   }
 }
 
 template <typename R>
-cudaError_t expand_dispatch(qs_ctx* h, const void* L, void* Lp, int n, int m, const Targets& tg,
+cudaError_t expand_dispatch(qs_ctx* h, const void* L, void* Lp, int n, int m, const Targets& tg, bool real,
                             const void* E, int K) {
   const uint64_t work = ((1ull << n) >> tg.k) * (uint64_t)m;
   uint64_t blocks = (work + kExpBlock - 1) / kExpBlock;
@@ -435,24 +486,24 @@ cudaError_t expand_dispatch(qs_ctx* h, const void* L, void* Lp, int n, int m, co
   if (blocks < 1) blocks = 1;
   auto* l = static_cast<const cplx<R>*>(L);
   auto* lp = static_cast<cplx<R>*>(Lp);
-  if (tg.k == 1)
-    k_kraus_expand<R, 1><<<(int)blocks, kExpBlock, 0, h->stream>>>(l, lp, n, m, tg, (const double*)E, K);
-  else if (tg.k == 2)
-    k_kraus_expand<R, 2><<<(int)blocks, kExpBlock, 0, h->stream>>>(l, lp, n, m, tg, (const double*)E, K);
-  else
-    return cudaErrorInvalidValue;
+  const double* e = (const double*)E;
+  if (tg.k == 1 && real) k_kraus_expand<R, 1, true><<<(int)blocks, kExpBlock, 0, h->stream>>>(l, lp, n, m, tg, e, K);
+  else if (tg.k == 1) k_kraus_expand<R, 1, false><<<(int)blocks, kExpBlock, 0, h->stream>>>(l, lp, n, m, tg, e, K);
+  else if (tg.k == 2 && real) k_kraus_expand<R, 2, true><<<(int)blocks, kExpBlock, 0, h->stream>>>(l, lp, n, m, tg, e, K);
+  else if (tg.k == 2) k_kraus_expand<R, 2, false><<<(int)blocks, kExpBlock, 0, h->stream>>>(l, lp, n, m, tg, e, K);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_kraus_expand(qs_ctx* h, const void* L, void* Lp, int n, int m, const Targets& tg,
+cudaError_t launch_kraus_expand(qs_ctx* h, const void* L, void* Lp, int n, int m, const Targets& tg, bool real,
                                 const void* E, int K) {
-  if (h->dtype == QS_C64) return expand_dispatch<float>(h, L, Lp, n, m, tg, E, K);
-  return expand_dispatch<double>(h, L, Lp, n, m, tg, E, K);
+  if (h->dtype == QS_C64) return expand_dispatch<float>(h, L, Lp, n, m, tg, real, E, K);
+  return expand_dispatch<double>(h, L, Lp, n, m, tg, real, E, K);
 }
 
-cudaError_t launch_gram(qs_ctx* h, const void* Lp, int n, int M, double* G) {
+cudaError_t launch_gram(qs_ctx* h, const void* Lp, int n, int M, bool real, double* G) {
   const uint64_t N = 1ull << n;
   const int blocks = (int)((N + kGramRows - 1) / kGramRows);
   const size_t need = (size_t)blocks * 2 * M * M;
@@ -464,10 +515,14 @@ cudaError_t launch_gram(qs_ctx* h, const void* Lp, int n, int M, double* G) {
       return cudaErrorMemoryAllocation;
     h->partials_cap = need;
   }
-  if (h->dtype == QS_C64)
-    k_gram_partials<float><<<blocks, 256, 0, h->stream>>>((const float2*)Lp, n, M, h->partials);
+  if (h->dtype == QS_C64 && real)
+    k_gram_partials<float, true><<<blocks, 256, 0, h->stream>>>((const float2*)Lp, n, M, h->partials);
+  else if (h->dtype == QS_C64)
+    k_gram_partials<float, false><<<blocks, 256, 0, h->stream>>>((const float2*)Lp, n, M, h->partials);
+  else if (real)
+    k_gram_partials<double, true><<<blocks, 256, 0, h->stream>>>((const double2*)Lp, n, M, h->partials);
   else
-    k_gram_partials<double><<<blocks, 256, 0, h->stream>>>((const double2*)Lp, n, M, h->partials);
+    k_gram_partials<double, false><<<blocks, 256, 0, h->stream>>>((const double2*)Lp, n, M, h->partials);
   k_gram_reduce<<<M * M, 256, 0, h->stream>>>(h->partials, blocks, M, G);
   return cudaGetLastError();
 }
@@ -478,16 +533,20 @@ cudaError_t launch_eig_truncate(qs_ctx* h, const double* G, int M, int r, int no
   return cudaGetLastError();
 }
 
-cudaError_t launch_project(qs_ctx* h, const void* Lp, void* L, int n, int M, const double* W,
+cudaError_t launch_project(qs_ctx* h, const void* Lp, void* L, int n, int M, bool real, const double* W,
                            const double* scale, const int* keep) {
   const uint64_t N = 1ull << n;
-  uint64_t blocks = (N * kMaxRank + 255) / 256;
+  uint64_t blocks = (N + 255) / 256;
   const uint64_t cap = (uint64_t)num_sms() * 8;
   if (blocks > cap) blocks = cap;
-  if (h->dtype == QS_C64)
-    k_project<float><<<(int)blocks, 256, 0, h->stream>>>((const float2*)Lp, (float2*)L, n, M, W, keep, scale);
+  if (h->dtype == QS_C64 && real)
+    k_project<float, true><<<(int)blocks, 256, 0, h->stream>>>((const float2*)Lp, (float2*)L, n, M, W, keep, scale);
+  else if (h->dtype == QS_C64)
+    k_project<float, false><<<(int)blocks, 256, 0, h->stream>>>((const float2*)Lp, (float2*)L, n, M, W, keep, scale);
+  else if (real)
+    k_project<double, true><<<(int)blocks, 256, 0, h->stream>>>((const double2*)Lp, (double2*)L, n, M, W, keep, scale);
   else
-    k_project<double><<<(int)blocks, 256, 0, h->stream>>>((const double2*)Lp, (double2*)L, n, M, W, keep, scale);
+    k_project<double, false><<<(int)blocks, 256, 0, h->stream>>>((const double2*)Lp, (double2*)L, n, M, W, keep, scale);
   return cudaGetLastError();
 }
 
