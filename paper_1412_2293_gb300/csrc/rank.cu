@@ -300,23 +300,109 @@ __device__ bool jacobi(T* A, T* V, int M, double tol) {
   return false;
 }
 
+// After the eigensolver: eigenvalues (diagonal of A) sorted descending
+// (ties keep index order), clusters of ties given a canonical basis, and the
+// outputs W = first keep canonical eigenvectors (M x keep, complex layout),
+// lam_out (sorted), keep and the scale.  T is double (real G: real
+// eigenvectors, real arithmetic) or double2.  Candidate j of a cluster with
+// eigenvectors S is P e_j, P = S S^dagger, minus its components along the
+// cluster's accepted vectors q_t; as the q_t lie in range(P),
+// <q_t, P e_j> = conj(q_t[j]) and |P e_j - ...|^2 = P_jj - sum_t |q_t[j]|^2,
+// so the projections need no dot products.  An accepted vector is
+// normalised by its computed norm.  The cluster stage runs in one warp
+// (lane = row).
+template <typename T>
+__device__ void eig_finish(T* A, T* V, int M, int r, int normalize, double* __restrict__ W,
+                           double* __restrict__ lam_out, int* keep_out, double* scale_out, int* status) {
+  __shared__ int order[kMaxGramDim + 1];
+  __shared__ double lam[kMaxGramDim];
+  __shared__ int nbasis;
+  T* basis = A;                                         // canonical vectors (columns), pitch kJP
+  const int tid = threadIdx.x;
+  for (int i = tid; i < M; i += blockDim.x) lam[i] = tre(A[i * kJP + i]);
+  __syncthreads();
+  if (tid == 0) {
+    for (int i = 0; i < M; ++i) order[i] = i;
+    for (int i = 0; i < M; ++i) {
+      int best = i;
+      for (int j = i + 1; j < M; ++j)
+        if (lam[order[j]] > lam[order[best]]) best = j;
+      const int t = order[i]; order[i] = order[best]; order[best] = t;
+    }
+  }
+  __syncthreads();   // A is free from here on (basis aliases it)
+  const int keep = r < M ? r : M;
+  const double lam1 = lam[order[0]] > 0.0 ? lam[order[0]] : 0.0;
+  if (tid < 32) {
+    const int lane = tid;
+    int found = 0;
+    int i0 = 0;
+    while (i0 < keep) {
+      int i1 = i0 + 1;
+      while (i1 < M && lam[order[i0]] - lam[order[i1]] <= kTieTol * lam1) ++i1;
+      const int s = i1 - i0;
+      const int first = found;
+      // P = S S^dagger; GS of P e_j, j = 0..M-1, thresholds kGsAccept then kGsFallback
+      for (int pass = 0; pass < 2 && found - first < s; ++pass) {
+        const double thr = pass == 0 ? kGsAccept : kGsFallback;
+        for (int j = 0; j < M && found - first < s; ++j) {
+          T v = tscal<T>(0.0);
+          double n2 = 0.0;                               // P_jj, then the residual's norm^2
+          for (int c = 0; c < s; ++c) {
+            const int col = order[i0 + c];
+            const T sj = V[j * kJP + col];
+            if (lane < M) v = tadd(v, tmul(V[lane * kJP + col], tconj(sj)));
+            n2 += tabs2(sj);
+          }
+          for (int t = first; t < found; ++t) {
+            const T qj = basis[j * kJP + t];
+            if (lane < M) v = tadd(v, tscale(tmul(basis[lane * kJP + t], tconj(qj)), -1.0));
+            n2 -= tabs2(qj);
+          }
+          if (n2 > thr * thr) {
+            double nv = lane < M ? tabs2(v) : 0.0;
+            for (int o = 16; o; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
+            if (lane < M) basis[lane * kJP + found] = tscale(v, rsqrt(nv));
+            ++found;
+            __syncwarp();
+          }
+        }
+      }
+      if (found - first < s && lane == 0) status[0] = 2;           // incomplete cluster
+      i0 = i1;
+    }
+    if (lane == 0) nbasis = found;
+  }
+  __syncthreads();
+  // outputs
+  for (int i = tid; i < M * keep; i += blockDim.x) {
+    const int p = i / keep, c = i % keep;
+    const T v = c < nbasis ? basis[p * kJP + c] : tscal<T>(0.0);
+    if constexpr (sizeof(T) == 16) {
+      W[2 * (p * keep + c)] = v.x;
+      W[2 * (p * keep + c) + 1] = v.y;
+    } else {
+      W[2 * (p * keep + c)] = v;
+      W[2 * (p * keep + c) + 1] = 0.0;
+    }
+  }
+  if (tid == 0) {
+    double kept = 0.0;
+    for (int i = 0; i < M; ++i) lam_out[i] = lam[order[i]];
+    for (int i = 0; i < keep; ++i) kept += lam[order[i]];
+    keep_out[0] = keep;
+    scale_out[0] = normalize ? 1.0 / sqrt(kept) : 1.0;
+  }
+}
+
 // One block: eigendecomposition of the Hermitian G (M x M) by parallel cyclic
-// Jacobi (real arithmetic when G is real), eigenvalues sorted descending,
-// clusters of ties given a canonical basis, then W = first r canonical
-// eigenvectors (M x keep), keep = min(r, M), and lam[0..M) sorted
-// descending; out_scale = 1/sqrt(sum lam[:keep]) or 1.
+// Jacobi (real arithmetic when G is real), then eig_finish.
 __global__ void __launch_bounds__(512) k_eig_truncate(const double* __restrict__ Gin, int M, int r,
                                                       int normalize, double* __restrict__ W,
                                                       double* __restrict__ lam_out, int* keep_out,
                                                       double* scale_out, int* status) {
   __shared__ double2 A[kMaxGramDim][kJP];
   __shared__ double2 V[kMaxGramDim][kJP];
-  __shared__ int order[kMaxGramDim + 1];
-  __shared__ double lam[kMaxGramDim];
-  // canonical vectors (columns) reuse A's storage once the eigenvalues are read
-  auto& basis = A;
-  __shared__ int nbasis;
-
   const int tid = threadIdx.x;
   int cplx = 0;
   for (int i = tid; i < M * M; i += blockDim.x) cplx |= Gin[2 * i + 1] != 0.0;
@@ -329,8 +415,8 @@ __global__ void __launch_bounds__(512) k_eig_truncate(const double* __restrict__
     }
     __syncthreads();
     if (!jacobi<double2>(&A[0][0], &V[0][0], M, kRotTol) && tid == 0) status[0] = 1;
-    for (int i = tid; i < M; i += blockDim.x) lam[i] = A[i][i].x;
     __syncthreads();
+    eig_finish<double2>(&A[0][0], &V[0][0], M, r, normalize, W, lam_out, keep_out, scale_out, status);
   } else {
     double* Ar = reinterpret_cast<double*>(&A[0][0]);
     double* Vr = reinterpret_cast<double*>(&V[0][0]);
@@ -341,92 +427,8 @@ __global__ void __launch_bounds__(512) k_eig_truncate(const double* __restrict__
     }
     __syncthreads();
     if (!jacobi<double>(Ar, Vr, M, kRotTol) && tid == 0) status[0] = 1;
-    for (int i = tid; i < M; i += blockDim.x) lam[i] = Ar[i * kJP + i];
-    // widen V to complex in place: read everything first
-    double hold[2] = {0.0, 0.0};
-    for (int i = tid, c = 0; i < M * M && c < 2; i += blockDim.x, ++c) hold[c] = Vr[(i / M) * kJP + i % M];
     __syncthreads();
-    for (int i = tid, c = 0; i < M * M && c < 2; i += blockDim.x, ++c) V[i / M][i % M] = make_double2(hold[c], 0.0);
-    __syncthreads();
-  }
-
-  // sort eigenvalues descending (selection sort, ties keep index order)
-  if (tid == 0) {
-    for (int i = 0; i < M; ++i) order[i] = i;
-    for (int i = 0; i < M; ++i) {
-      int best = i;
-      for (int j = i + 1; j < M; ++j)
-        if (lam[order[j]] > lam[order[best]]) best = j;
-      const int t = order[i]; order[i] = order[best]; order[best] = t;
-    }
-    nbasis = 0;
-  }
-  __syncthreads();   // A is free from here on (basis aliases it)
-  const int keep = r < M ? r : M;
-  const double lam1 = lam[order[0]] > 0.0 ? lam[order[0]] : 0.0;
-
-  // clusters (anchor = first member) and their canonical bases, until keep;
-  // one warp, lane = row, dot products by shuffles (no block barriers)
-  if (tid < 32) {
-    const int lane = tid;
-    auto wsum = [](double v) {
-      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      return v;
-    };
-    int found = 0;
-    int i0 = 0;
-    while (i0 < keep) {
-      int i1 = i0 + 1;
-      while (i1 < M && lam[order[i0]] - lam[order[i1]] <= kTieTol * lam1) ++i1;
-      const int s = i1 - i0;
-      const int first = found;
-      // P = S S^dagger; GS of P e_j, j = 0..M-1, thresholds kGsAccept then kGsFallback
-      for (int pass = 0; pass < 2 && found - first < s; ++pass) {
-        const double thr = pass == 0 ? kGsAccept : kGsFallback;
-        for (int j = 0; j < M && found - first < s; ++j) {
-          // v = P e_j = sum_c S[:, c] conj(S[j, c])
-          double2 v = make_double2(0.0, 0.0);
-          if (lane < M)
-            for (int c = 0; c < s; ++c) {
-              const int col = order[i0 + c];
-              v = zadd(v, zmul(V[lane][col], zconj(V[j][col])));
-            }
-          for (int rep = 0; rep < 2; ++rep)
-            for (int u = first; u < found; ++u) {
-              // v -= basis_u <basis_u, v>
-              const double2 b = lane < M ? basis[lane][u] : make_double2(0.0, 0.0);
-              const double2 t = zmul(zconj(b), v);
-              const double2 d = make_double2(wsum(t.x), wsum(t.y));
-              v = zsub(v, zmul(b, d));
-            }
-          const double vn = sqrt(wsum(v.x * v.x + v.y * v.y));
-          if (vn > thr) {
-            if (lane < M) basis[lane][found] = zscale(v, 1.0 / vn);
-            ++found;
-            __syncwarp();
-          }
-        }
-      }
-      if (found - first < s && lane == 0) status[0] = 2;           // incomplete cluster
-      i0 = i1;
-    }
-    if (lane == 0) nbasis = found;
-  }
-  __syncthreads();
-
-  // outputs
-  for (int i = tid; i < M * keep; i += blockDim.x) {
-    const int p = i / keep, c = i % keep;
-    const double2 v = c < nbasis ? basis[p][c] : make_double2(0.0, 0.0);
-    W[2 * (p * keep + c)] = v.x;
-    W[2 * (p * keep + c) + 1] = v.y;
-  }
-  if (tid == 0) {
-    double kept = 0.0;
-    for (int i = 0; i < M; ++i) lam_out[i] = lam[order[i]];
-    for (int i = 0; i < keep; ++i) kept += lam[order[i]];
-    keep_out[0] = keep;
-    scale_out[0] = normalize ? 1.0 / sqrt(kept) : 1.0;
+    eig_finish<double>(Ar, Vr, M, r, normalize, W, lam_out, keep_out, scale_out, status);
   }
 }
 
