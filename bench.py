@@ -168,8 +168,13 @@ def run_ours(args, rank, world, local_rank):
     qs.qs_set_trajectory_offset(h, traj0)
     p = qs.qs_plan_create(h, pcirc.to_gates(ops))
     passes, launches = qs.qs_plan_info(p, h)
-    # kernel configuration of the passes: the fastest on this plan (eager runs, untimed)
-    tune_ms = qs.qs_plan_autotune(p, 2, e, seed, h)
+    # kernel configuration of the passes: given, or the fastest on this plan (eager runs, untimed)
+    if args.kernel_config:
+        lo, hi = (int(x) for x in args.kernel_config.split(","))
+        qs.qs_plan_set_config(p, lo, hi, h)
+        tune_ms = (-1.0, -1.0)
+    else:
+        tune_ms = qs.qs_plan_autotune(p, 2, e, seed, h)
     kernel_cfg = qs.qs_plan_get_config(p, h)
     qs.qs_plan_set_timing(p, True, h)
     updates_per_step = T * (1 << n) * len(ops)
@@ -595,6 +600,8 @@ def main():
     ap.add_argument("--workload", default="mc_qft_n20_c64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the bounded measurements of the other rows")
+    ap.add_argument("--kernel-config", default=None,
+                    help="low,high pass configuration indices (qs_plan_set_config) instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -153,6 +153,11 @@ __device__ __forceinline__ void tma_g2s_2d(void* dst, const CUtensorMap* map, in
       : "memory");
 }
 
+// bring a 128-byte line into L1 ahead of its use
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ void report_timeout(int* status) {
   if (status) atomicExch(status, kStatusTimeout);
 }
@@ -401,6 +406,9 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
     const uint64_t member = base >> A.n;
     const uint64_t mloc = base & nmask;
     const R* P = params + member * (uint64_t)A.param_stride;
+    // this tile's out factors (read at the end of the tile): into L1 now
+    if (A.alpha_tab && lane < 2)
+      prefetch_l1(static_cast<const C*>(A.alpha_tab) + ((member << (A.n - kWin)) | (mloc >> kWin)) * 11 + lane * 8);
     C a[kAmps];
     if (A.synth) {
       // the one amplitude equal to 1: register (x >> 5) & 31 of lane x & 31
@@ -599,6 +607,13 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
     const uint32_t tbits = (uint32_t)(tl << COLB);      // the other bits are COLB .. n-11
     const R* P = params + member * (uint64_t)A.param_stride;
     C* sm = smbase + cur * S::BUF;
+    // this tile's out factors (read at the end of the tile): into L1 now
+    if (A.alpha_tab) {
+      const char* at = reinterpret_cast<const char*>(static_cast<const C*>(A.alpha_tab) +
+                                                     ((member << (A.n - kWin)) | tbits) * 11);
+      constexpr int kLines = (int)((S::COLS * 11 * sizeof(C)) / 128) + 2;
+      if ((int)threadIdx.x < kLines) prefetch_l1(at + threadIdx.x * 128);
+    }
     C a[kAmps];
     int stage = A.start_stage;
     if (A.synth) {
