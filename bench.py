@@ -16,6 +16,7 @@ complex128 CPU simulator) on a bounded sample of the same workload.
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -294,20 +295,40 @@ def run_ours(args, rank, world, local_rank):
     return result
 
 
-def cpu_baseline(W, ops, x0, gpu_fid0):
-    """The oracle as it stands, on the host: one whole trajectory of the workload.
+def _oracle_trajectory(args):
+    """One oracle trajectory (a worker of the all-core baseline)."""
+    n, ops, x0, e, seed, traj = args
+    from oracle import circuits as ocirc
+    return ocirc.run_trajectory(n, ops, x0, e, seed, traj)
 
-    The same trajectory (counter 0) was run on the GPU in complex64; the
-    difference of the two fidelities is the error of the GPU result against
-    the FP64 oracle."""
+
+def cpu_baseline(W, ops, x0, gpu_fid0):
+    """The oracle as it stands, on the host: whole trajectories of the workload,
+    one per host core in parallel (trajectories are independent), and one on a
+    single thread.
+
+    Trajectory 0 was also run on the GPU in complex64; the difference of the
+    two fidelities is the error of the GPU result against the FP64 oracle."""
+    import multiprocessing as mp
+
     from oracle import circuits as ocirc
     from oracle import statevec as osv
     t0 = time.perf_counter()
     psi = ocirc.run_trajectory(W.n, ops, x0, W.e, W.seed, 0)
-    dt = time.perf_counter() - t0
+    dt1 = time.perf_counter() - t0
     f0 = osv.fidelity(ocirc.ideal_state(W.n, ops, x0), psi)
-    return {"value": (1 << W.n) * len(ops) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"1 of {W.trajectories} trajectories of {W.name} (complex128 NumPy, single thread), {dt:.1f} s",
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_trajectory, [(W.n, [], x0, W.e, W.seed, 0)] * cores)   # workers up
+        t0 = time.perf_counter()
+        pool.map(_oracle_trajectory, [(W.n, ops, x0, W.e, W.seed, b) for b in range(cores)])
+        dtn = time.perf_counter() - t0
+    upd = (1 << W.n) * len(ops)
+    return {"value": upd * cores / dtn, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} of {W.trajectories} trajectories of {W.name}, one per core (complex128 NumPy, "
+                      f"spawned processes), {dtn:.1f} s",
+            "single_thread_value": upd / dt1, "single_thread_s": round(dt1, 2),
             "fidelity_oracle": f0, "fidelity_gpu": float(gpu_fid0), "fidelity_abs_error": abs(f0 - float(gpu_fid0))}
 
 
@@ -423,11 +444,95 @@ def extra_rows(h, n, T, esize, stream, peaks):
         "circuits_per_s_extrapolated": round(1e3 / (per_ch * total_noisy), 4),
         "note": "time of a bounded run of channels (expand, FP64 Gram, FP64 Jacobi, projection) x channels"}
 
+    # a7: rank sweep r = 1, 2, 4, 8 on the same Grover circuit (bounded channels), and the whole
+    # circuit at r = 1 against Eq. 10: F = lambda1^(n + 2nk) p_ideal, lambda1 = (1 + e^-2e^2) / 2
+    sweep = {}
+    for r in (1, 2, 4, 8):
+        hr = qs.qs_create(W3.n, 1, r, qs.QS_FIXED_RANK, qs.QS_C128, stream)
+        qs.qs_set_basis_state(hr, 0)
+        pcirc.apply_ops(hr, ops3[:40], W3.e, W3.seed)
+        qs.qs_synchronize(hr)
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        pcirc.apply_ops(hr, sub, W3.e, W3.seed, gate_id0=40)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sweep[f"r{r}_ms_per_channel"] = round(e0.elapsed_time(e1) / max(noisy, 1), 4)
+        qs.qs_destroy(hr)
+    marked3 = inputs.draw_marked(W3.n, W3.seed)
+    k3 = inputs.grover_iterations(W3.n)
+    hr = qs.qs_create(W3.n, 1, 1, qs.QS_FIXED_RANK, qs.QS_C128, stream)
+    t0 = time.perf_counter()
+    pcirc.apply_ops(hr, ops3, W3.e, W3.seed)
+    p_r1 = float(qs.qs_fidelity(hr, None, marked3)[0])
+    t_r1 = time.perf_counter() - t0
+    qs.qs_destroy(hr)
+    lam1 = (1.0 + math.exp(-2.0 * W3.e ** 2)) / 2.0
+    p_eq10 = lam1 ** (W3.n + 2 * W3.n * k3) * math.sin((2 * k3 + 1) * math.asin(2.0 ** (-W3.n / 2))) ** 2
+    sweep.update({"r1_whole_circuit_s": round(t_r1, 3), "r1_success_probability": p_r1, "eq10": p_eq10,
+                  "r1_rel_diff_from_eq10": abs(p_r1 - p_eq10) / p_eq10})
+    out["a7_rank_sweep_grover_n16"] = sweep
+
+    # a6 vs a7: exact density matrix and fixed rank r = 1..8 on the QFT n = 14, |F_r - F_exact|
+    href = pcirc.ideal_reference(W4.n, ops4, x4, qs.QS_C128, stream)
+    phi = qs.qs_get_state(href)
+    qs.qs_destroy(href)
+    hd = qs.qs_create(W4.n, 1, 0, qs.QS_DENSITY, qs.QS_C128, stream)
+    qs.qs_set_basis_state(hd, x4)
+    pcirc.apply_ops(hd, ops4, W4.e, W4.seed)
+    f_exact = float(qs.qs_fidelity(hd, phi)[0])
+    qs.qs_destroy(hd)
+    cmp = {"f_exact": f_exact}
+    for r in (1, 2, 4, 8):
+        hr = qs.qs_create(W4.n, 1, r, qs.QS_FIXED_RANK, qs.QS_C128, stream)
+        qs.qs_set_basis_state(hr, x4)
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        pcirc.apply_ops(hr, ops4, W4.e, W4.seed)
+        e1.record(stream)
+        f_r = float(qs.qs_fidelity(hr, phi)[0])
+        cmp[f"r{r}"] = {"f": f_r, "abs_diff": abs(f_r - f_exact), "ms_per_circuit": round(e0.elapsed_time(e1), 2)}
+        qs.qs_destroy(hr)
+    out["dm_vs_fixed_rank_qft_n14"] = cmp
+
+    # a3 at the other precision and noise level of the bench circuit: complex128 (128
+    # trajectories, 2 GiB) and complex64 at e = 0.001 (1024 trajectories)
+    Wq = inputs.WORKLOADS["mc_qft_n20_c64"]
+    opsq, xq = Wq.ops(), Wq.initial_basis()
+    for label, dtype_, Tq, eq in (("mc_qft_n20_c128_t128", qs.QS_C128, 128, Wq.e), ("mc_qft_n20_c64_e1e-3", qs.QS_C64, T, 0.001)):
+        hq = qs.qs_create(Wq.n, Tq, 0, qs.QS_STATEVEC, dtype_, stream) if label != "mc_qft_n20_c64_e1e-3" else h
+        refq = pcirc.ideal_reference(Wq.n, opsq, xq, dtype_, stream)
+        qs.qs_set_reference_from(hq, refq, 0)
+        qs.qs_destroy(refq)
+        pq = qs.qs_plan_create(hq, pcirc.to_gates(opsq))
+        qs.qs_plan_autotune(pq, 1, eq, Wq.seed, hq)
+        for _ in range(2):
+            qs.qs_set_basis_state(hq, xq)
+            fq = qs.qs_plan_run_fidelity(pq, eq, Wq.seed, 0, hq)
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        reps = 5
+        for _ in range(reps):
+            qs.qs_set_basis_state(hq, xq)
+            fq = qs.qs_plan_run_fidelity(pq, eq, Wq.seed, 0, hq)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msq = e0.elapsed_time(e1) / reps
+        qs.qs_plan_destroy(pq)
+        if hq is not h:
+            qs.qs_destroy(hq)
+        out[label] = {"ms_per_step": round(msq, 3), "trajectories": Tq, "e": eq,
+                      "updates_per_s": Tq * (1 << Wq.n) * len(opsq) / (msq / 1e3),
+                      "fidelity_mean": float(np.mean(fq))}
+
     out["a11_serving"] = serving_row()
+    cap = out["a11_serving"]["jobs_per_s"]
+    out["a11_serving_rate_sweep"] = {f"{m}x_capacity": serving_row(num_jobs=60, rate_per_s=m * cap, seed_offset=1)
+                                     for m in (0.5, 1.0, 2.0)}
     return out
 
 
-def serving_row(num_jobs=100, rate_per_s=200.0, workers=4):
+def serving_row(num_jobs=100, rate_per_s=200.0, workers=4, seed_offset=0):
     """Continuous batching of a mixed stream of fidelity-estimation jobs.
 
     Poisson arrivals of Grover and QFT jobs, half Monte Carlo (2^6..2^10
@@ -436,7 +541,7 @@ def serving_row(num_jobs=100, rate_per_s=200.0, workers=4):
     from arrival to the job's last fidelity on the host."""
     from paper_1412_2293_gb300 import inputs
     from paper_1412_2293_gb300.server import GpuExecutor, Server, run_stream
-    jobs = inputs.draw_job_stream(num_jobs, rate_per_s, seed=inputs.DEFAULT_SEED, n_range=(12, 20),
+    jobs = inputs.draw_job_stream(num_jobs, rate_per_s, seed=inputs.DEFAULT_SEED + seed_offset, n_range=(12, 20),
                                   log2_traj_range=(6, 10), max_rank=8)
     srv = Server(GpuExecutor(workers=workers), max_members=1024)
     try:

@@ -263,6 +263,7 @@ qs_status qs_plan_last_times(qs_plan p, double* ms, int* kinds, int cap, int* co
  * 8 warps per SM, two buffers; high 1: two such blocks per SM, one buffer;
  * high 2: four blocks of 4 warps per SM (4-column tiles), one buffer --
  * complex128 one of each.
+ * A new plan starts with low 2 / high 1 (complex64), 0 / 0 (complex128).
  * Results do not depend on the configuration.  qs_plan_configs returns the
  * counts; qs_plan_set_config rejects an index out of range with
  * QS_ERR_INVALID_ARG; qs_plan_get_config returns the current choice. */

@@ -1100,6 +1100,9 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
     p->gates.push_back(classify(g, h->n));
   }
   p->colb = h->dtype == QS_C64 ? 3 : 2;
+  // default configurations: the fastest measured on the noisy QFT, n = 20
+  // (12 warps with one buffer; two high-window blocks per SM)
+  if (h->dtype == QS_C64) { p->low_cfg = 2; p->high_cfg = 1; }
   // fused passes use 32-bit member-local offsets
   const bool fuse = h->mode == QS_STATEVEC && h->n >= kWin && h->n <= 32;
   std::vector<int> rem;
