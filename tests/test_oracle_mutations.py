@@ -108,3 +108,34 @@ def test_rank1_formula_pin_detects_an_extra_noisy_gate():
     L = circuits.run_fixed_rank(n, ops, 0, e, 1)
     p = fixed_rank.fidelity(statevec.basis_state(n, 3), L)
     assert abs(p - gates.grover_rank1_success(n, k, e)) > 1e-4
+
+
+def test_mutation_relative_state_on_the_reference_half_is_caught(monkeypatch):
+    """Gates applied to the reference qubits instead of the system: the single-channel pin
+    still holds by symmetry, but the noiseless-circuit pin does not."""
+    import numpy as np
+
+    from oracle import choi, statevec
+    orig = statevec.apply_gate
+
+    def shifted(psi, n2, targets, U):
+        return orig(psi, n2, tuple(t + n2 // 2 for t in targets), U)
+
+    n = 3
+    ops = [inputs.Op(o.kind, o.qubits, o.theta, o.index, False) for o in inputs.qft_circuit(n)]
+    psi = choi.ideal_relative(n, ops)
+    monkeypatch.setattr(choi.statevec, "apply_gate", shifted)
+    rho = choi.relative_state(n, ops, 0.0)
+    monkeypatch.undo()
+    # the ideal vector applies U to the system, the mutated state to the reference: not equal
+    assert abs(np.real(np.vdot(psi, rho @ psi)) - 1.0) > 1e-3
+
+
+def test_mutation_unnormalised_entangled_state_is_caught(monkeypatch):
+    import numpy as np
+
+    from oracle import choi
+    orig = choi.maximally_entangled
+    monkeypatch.setattr(choi, "maximally_entangled", lambda n: orig(n) * 2.0 ** (n / 2))
+    rho = choi.relative_state(2, inputs.qft_circuit(2), 0.1)
+    assert abs(np.trace(rho) - 1.0) > 1e-3

@@ -385,3 +385,71 @@ def test_philox_differs_across_seed_traj_gate():
     assert a != philox.noise_words(1, 2, 4)
     assert a != philox.noise_words(1, 2 + (1 << 32), 3)
     assert a != philox.noise_words(1, 2, 3 + (1 << 32))
+
+
+# ---------------------------------------------------------------- relative states (Sec. 4)
+from oracle import choi as ochoi  # noqa: E402
+
+
+def test_maximally_entangled_state():
+    om = ochoi.maximally_entangled(2)
+    assert abs(np.vdot(om, om) - 1.0) < 1e-15
+    nz = np.flatnonzero(np.abs(om) > 0)
+    np.testing.assert_array_equal(nz, [0, 5, 10, 15])           # |i>|i>, index i + 4 i
+    np.testing.assert_allclose(om[nz], 0.5)
+
+
+@pytest.mark.parametrize("e", [0.05, 0.2])
+def test_relative_state_is_trace_one_with_maximally_mixed_reference(e):
+    n = 3
+    ops = inputs.qft_circuit(n)
+    rho = ochoi.relative_state(n, ops, e)
+    assert abs(np.trace(rho) - 1.0) < 1e-13
+    np.testing.assert_allclose(rho, rho.conj().T, atol=1e-14)
+    assert np.linalg.eigvalsh(rho).min() > -1e-13
+    np.testing.assert_allclose(ochoi.reference_marginal(rho, n), np.eye(1 << n) / (1 << n), atol=1e-14)
+
+
+@pytest.mark.parametrize("e", [0.01, 0.1, 0.3])
+def test_relative_state_fidelity_of_single_channels(e):
+    # one noisy Hadamard: sum_i |tr(H^dag E_i)|^2 / 4 = lambda_1 (tr J = 0), Eq. 6
+    H = gates.hadamard()
+    lam1, _ = gates.hadamard_noise_weights(e)
+    assert abs(ochoi.channel_fidelity(gates.rotation_kraus(H, e), H) - lam1) < 1e-15
+    op = inputs.Op("H", (0,), 0.0, 0, True)
+    rho = ochoi.relative_state(1, [op], e)
+    psi = ochoi.ideal_relative(1, [op])
+    assert abs(np.real(np.vdot(psi, rho @ psi)) - lam1) < 1e-14
+    # one noisy controlled phase: |3 + sqrt P|^2 / 16 + (1 - P) / 16, Eq. 9
+    P = math.exp(-e * e)
+    theta = 0.7
+    U = gates.controlled_phase(theta)
+    want = ((3.0 + math.sqrt(P)) ** 2 + (1.0 - P)) / 16.0
+    assert abs(ochoi.channel_fidelity(gates.phase_kraus(U, e), U) - want) < 1e-15
+    op = inputs.Op("CP", (1, 0), theta, 0, True)
+    rho = ochoi.relative_state(2, [op], e)
+    psi = ochoi.ideal_relative(2, [op])
+    assert abs(np.real(np.vdot(psi, rho @ psi)) - want) < 1e-14
+
+
+def test_noiseless_relative_state_has_fidelity_one():
+    n = 3
+    ops = [inputs.Op(o.kind, o.qubits, o.theta, o.index, False) for o in inputs.qft_circuit(n)]
+    rho = ochoi.relative_state(n, ops, 0.1)
+    psi = ochoi.ideal_relative(n, ops)
+    assert abs(np.real(np.vdot(psi, rho @ psi)) - 1.0) < 1e-13
+
+
+def test_relative_state_is_the_monte_carlo_mean():
+    n, e, T = 2, 0.3, 400
+    ops = inputs.qft_circuit(n)
+    psi = ochoi.ideal_relative(n, ops)
+    rho = ochoi.relative_state(n, ops, e)
+    exact = np.real(np.vdot(psi, rho @ psi))
+    f = np.array([abs(np.vdot(psi, ochoi.relative_trajectory(n, ops, e, 99, b))) ** 2 for b in range(T)])
+    assert abs(f.mean() - exact) < 4 * f.std() / math.sqrt(T) + 1e-12
+
+
+def test_relative_states_reject_phase_flips():
+    with pytest.raises(ValueError):
+        ochoi.relative_state(2, inputs.grover_circuit(2, 1, 3), 0.1)
