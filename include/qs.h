@@ -96,6 +96,16 @@ qs_status qs_set_basis_state(qs_handle h, uint64_t x);
 /* Per-member basis states: xs[b] for b < batch (STATEVEC only). */
 qs_status qs_set_basis_states(qs_handle h, const uint64_t* xs);
 
+/* Choi-Jamiolkowski relative states (Sec. 4): the maximally entangled state
+ * of Eq. 16 on the handle's n = 2m qubits, 2^{-m/2} sum_i |i>_sys |i>_ref,
+ * system = qubits 0..m-1 (amplitude index i + (i << m)).  STATEVEC: every
+ * member; DENSITY: |Omega><Omega|; FIXED_RANK: one column.  A circuit on
+ * qubits 0..m-1 then yields the relative state of Eq. 17; its fidelity with
+ * the ideal relative state (a STATEVEC handle given the same start and the
+ * noiseless circuit) measures the circuit as a whole.  n odd ->
+ * QS_ERR_INVALID_ARG. */
+qs_status qs_set_maximally_entangled(qs_handle h);
+
 /* ------------------------------------------------------------------- gates */
 
 /* Ideal k-qubit gate U (k = 1..4) on `targets` (distinct, < n) -- Sec. 2.

@@ -397,6 +397,23 @@ qs_status qs_set_basis_state(qs_handle h, uint64_t x) {
   return QS_OK;
 }
 
+qs_status qs_set_maximally_entangled(qs_handle h) {
+  if (!h) return QS_ERR_INVALID_ARG;
+  if (h->n % 2) return fail(h, QS_ERR_INVALID_ARG, "the maximally entangled state needs an even qubit count");
+  h->pending = 0;
+  if (h->mode == QS_STATEVEC) {
+    QS_CUDA(h, qs::launch_set_entangled(h, h->state, h->batch, 0));
+  } else if (h->mode == QS_DENSITY) {
+    QS_CUDA(h, qs::launch_set_entangled(h, h->state, 1, 1));
+  } else {
+    QS_CUDA(h, cudaMemsetAsync(h->state, 0, h->state_elems * h->esize, h->stream));
+    QS_CUDA(h, qs::launch_set_entangled(h, h->state, 1, 0));
+    h->cols = 1;
+    h->real_factor = true;
+  }
+  return QS_OK;
+}
+
 qs_status qs_set_basis_states(qs_handle h, const uint64_t* xs) {
   if (!h || !xs) return QS_ERR_INVALID_ARG;
   if (h->mode != QS_STATEVEC) return fail(h, QS_ERR_NOT_SUPPORTED, "per-member basis states need STATEVEC");

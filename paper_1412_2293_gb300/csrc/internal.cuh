@@ -129,6 +129,7 @@ namespace qs {
 
 size_t elem_size(qs_dtype d);
 
+cudaError_t launch_set_entangled(qs_ctx* h, void* psi, int members, int dm);
 cudaError_t launch_set_basis(qs_ctx* h, void* psi, int n, int members, uint64_t x,
                              const uint64_t* xs_dev);
 cudaError_t launch_noise_mats(qs_ctx* h, void* mats, int members, int k, const double* U,

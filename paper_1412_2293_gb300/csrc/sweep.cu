@@ -35,6 +35,26 @@ __device__ __forceinline__ uint64_t insert0(uint64_t v, int s) {
   return ((v >> s) << (s + 1)) | low;
 }
 
+// Maximally entangled state of Eq. 16 on 2m qubits (system = low m bits):
+// amplitude 2^{-m/2} at i + (i << m), i < 2^m, for every member; or, dm,
+// the density matrix |Omega><Omega| on vec indices x * 2^(2m) + y.
+template <typename R>
+__global__ void k_set_entangled(cplx<R>* psi, int m, int members, int dm) {
+  const uint64_t D = 1ull << m;
+  const int n = 2 * m;
+  const uint64_t total = dm ? D * D : D * (uint64_t)members;
+  const R amp = dm ? (R)ldexp(1.0, -m) : (R)sqrt(ldexp(1.0, -m));
+  for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t a = w / D, i = w % D;
+    if (dm) {
+      const uint64_t x = a + (a << m), y = i + (i << m);
+      psi[(x << n) + y] = mk<R>(amp, R(0));
+    } else {
+      psi[(a << n) + i + (i << m)] = mk<R>(amp, R(0));
+    }
+  }
+}
+
 template <typename R>
 __global__ void k_set_basis(cplx<R>* psi, int n, int members, uint64_t x, const uint64_t* xs) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -393,6 +413,19 @@ cudaError_t launch_set_basis(qs_ctx* h, void* psi, int n, int members, uint64_t 
   const int g = (members + kBlock - 1) / kBlock;
   if (h->dtype == QS_C64) k_set_basis<float><<<g, kBlock, 0, h->stream>>>((float2*)psi, n, members, x, xs);
   else k_set_basis<double><<<g, kBlock, 0, h->stream>>>((double2*)psi, n, members, x, xs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_entangled(qs_ctx* h, void* psi, int members, int dm) {
+  const int m = h->n / 2;
+  const size_t elems = dm ? (size_t)1 << (2 * h->n) : ((size_t)members << h->n);
+  cudaError_t e = cudaMemsetAsync(psi, 0, elems * h->esize, h->stream);
+  if (e != cudaSuccess) return e;
+  const uint64_t total = dm ? (1ull << (2 * m)) : ((uint64_t)members << m);
+  uint64_t g = (total + kBlock - 1) / kBlock;
+  if (g > (uint64_t)num_sms() * 16) g = (uint64_t)num_sms() * 16;
+  if (h->dtype == QS_C64) k_set_entangled<float><<<(int)g, kBlock, 0, h->stream>>>((float2*)psi, m, members, dm);
+  else k_set_entangled<double><<<(int)g, kBlock, 0, h->stream>>>((double2*)psi, m, members, dm);
   return cudaGetLastError();
 }
 

@@ -51,6 +51,7 @@ _SIGS = {
     "qs_info": ([_P, _I, _I, _I, _I, _I, _I], ct.c_int),
     "qs_set_basis_state": ([_P, ct.c_uint64], ct.c_int),
     "qs_set_basis_states": ([_P, _U64], ct.c_int),
+    "qs_set_maximally_entangled": ([_P], ct.c_int),
     "qs_apply_gate": ([_P, _I, ct.c_int, _D], ct.c_int),
     "qs_apply_phase_flip": ([_P, ct.c_uint64], ct.c_int),
     "qs_apply_noisy_gate": ([_P, _I, ct.c_int, _D, ct.c_int, ct.c_double, ct.c_uint64, ct.c_uint64], ct.c_int),
@@ -160,6 +161,10 @@ def qs_set_basis_state(h, x):
 def qs_set_basis_states(h, xs):
     a = np.ascontiguousarray(np.asarray(xs, dtype=np.uint64))
     _check(lib().qs_set_basis_states(h, a.ctypes.data_as(_U64)), h)
+
+
+def qs_set_maximally_entangled(h):
+    _check(lib().qs_set_maximally_entangled(h), h)
 
 
 def qs_apply_gate(h, targets, U):
