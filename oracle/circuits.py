@@ -94,3 +94,19 @@ def run_fixed_rank(n, ops, x0, e, r, normalize=False, trace_log=None) -> np.ndar
         else:
             L = fixed_rank.apply_unitary(L, n, op_targets(op), U)
     return L
+
+
+def run_branch(n, ops, x0, e, rotated=False) -> np.ndarray:
+    """Rank-1 by branch selection: every noisy gate replaced by its first Kraus
+    operator (direct, Eq. 9, or rotated, Eq. 14); the state is not renormalised,
+    so |<ideal|psi>|^2 is the rank-1 estimate of the fidelity (Sec. 3.2, Fig. 4)."""
+    psi = statevec.basis_state(n, x0)
+    for op in ops:
+        if op.kind == "FLIP":
+            psi = statevec.phase_flip(psi, op.index)
+            continue
+        U = op_unitary(op)
+        if op.noisy:
+            U = gates.branch_operator(U, op_noise(op), e, rotated)
+        psi = statevec.apply_gate(psi, n, op_targets(op), U)
+    return psi

@@ -106,6 +106,27 @@ def phase_kraus(U: np.ndarray, e: float):
     return [U @ np.diag(d1), U @ np.diag(d2)]
 
 
+def rotated_phase_kraus(U: np.ndarray, e: float):
+    """The rotated Kraus pair of the controlled phase (Eqs. 12-14):
+    B_1 = (E_1 + f E_2) / sqrt(1 + f^2), B_2 = (-f E_1 + E_2) / sqrt(1 + f^2)
+    with {E_1, E_2} of Eq. 9 and f of Eq. 13 -- the same channel, its first
+    operator along the leading singular vector of the matrix psi of Eq. 12."""
+    E1, E2 = phase_kraus(U, e)
+    f = rotated_cp_f(e)
+    s = 1.0 / math.sqrt(1.0 + f * f)
+    return [s * (E1 + f * E2), s * (-f * E1 + E2)]
+
+
+def branch_operator(U: np.ndarray, noise: str, e: float, rotated: bool = False) -> np.ndarray:
+    """The first (dominant) Kraus operator of a noisy gate: sqrt(lambda_1) U for
+    rotation noise (Eq. 6), U diag(1,..,1,sqrt P) for phase noise (Eq. 9), or
+    the rotated B_1 of Eq. 14 -- the single branch kept by the rank-1 estimates
+    behind Eqs. 11 and 15."""
+    if noise == "phase":
+        return (rotated_phase_kraus(U, e) if rotated else phase_kraus(U, e))[0]
+    return kraus_set(U, noise, e)[0]
+
+
 def kraus_set(U: np.ndarray, noise: str, e: float):
     if noise == "rotation":
         return rotation_kraus(U, e)

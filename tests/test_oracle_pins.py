@@ -453,3 +453,46 @@ def test_relative_state_is_the_monte_carlo_mean():
 def test_relative_states_reject_phase_flips():
     with pytest.raises(ValueError):
         ochoi.relative_state(2, inputs.grover_circuit(2, 1, 3), 0.1)
+
+
+# ---------------------------------------------------------------- rotated Kraus pair (Eqs. 12-15)
+@pytest.mark.parametrize("e", [0.01, 0.1, 0.5])
+def test_rotated_pair_follows_the_svd_of_eq12(e):
+    P = math.exp(-e * e)
+    a, b = math.sqrt(P), math.sqrt(1.0 - P)
+    psi = np.array([[1, 1, 1, a], [0, 0, 0, b]], dtype=float)
+    Uv, sv, _ = np.linalg.svd(psi)
+    # squared singular values 2 +- sqrt(1 + 3P) (the printed S repeats sqrt(lambda_1))
+    np.testing.assert_allclose(np.sort(sv ** 2), [2 - math.sqrt(1 + 3 * P), 2 + math.sqrt(1 + 3 * P)], atol=1e-13)
+    f = gates.rotated_cp_f(e)
+    u0 = Uv[:, 0] * np.sign(Uv[0, 0])
+    np.testing.assert_allclose(u0, np.array([1.0, f]) / math.sqrt(1 + f * f), atol=1e-13)   # Eq. 13, first column
+    U = gates.controlled_phase(0.9)
+    B = gates.rotated_phase_kraus(U, e)
+    s = 1 / math.sqrt(1 + f * f)
+    np.testing.assert_allclose(np.diag(U.conj().T @ B[0]), s * np.array([1, 1, 1, a + f * b]), atol=1e-15)     # Eq. 14a
+    np.testing.assert_allclose(np.diag(U.conj().T @ B[1]), s * np.array([-f, -f, -f, -f * a + b]), atol=1e-15)  # Eq. 14b
+    # the same channel as Eq. 9
+    np.testing.assert_allclose(sum(E.conj().T @ E for E in B), np.eye(4), atol=1e-14)
+    np.testing.assert_allclose(density.superoperator(B), density.superoperator(gates.phase_kraus(U, e)), atol=1e-14)
+
+
+def test_branch_rank1_closed_forms():
+    e, n = 0.05, 6
+    # Grover: only Hadamards are noisy, each branch sqrt(lambda_1) H: Eq. 10
+    k = 2
+    w = 13
+    ops = inputs.grover_circuit(n, k, w)
+    psi = circuits.run_branch(n, ops, 0, e)
+    lam1, _ = gates.hadamard_noise_weights(e)
+    assert abs(abs(psi[w]) ** 2 - lam1 ** (n + 2 * n * k) * gates.grover_ideal_success(n, k)) < 1e-13
+    # one controlled phase on |+>|+>: |sum_x d_x / 4|^2 with the branch's diagonal d
+    P = math.exp(-e * e)
+    f = gates.rotated_cp_f(e)
+    plus2 = np.full(4, 0.5, dtype=np.complex128)
+    U = gates.controlled_phase(0.3)
+    for rotated, d in ((False, [1, 1, 1, math.sqrt(P)]),
+                       (True, np.array([1, 1, 1, math.sqrt(P) + f * math.sqrt(1 - P)]) / math.sqrt(1 + f * f))):
+        out = statevec.apply_gate(plus2, 2, (0, 1), gates.branch_operator(U, "phase", e, rotated))
+        ideal = statevec.apply_gate(plus2, 2, (0, 1), U)
+        assert abs(abs(np.vdot(ideal, out)) ** 2 - abs(sum(d) / 4) ** 2) < 1e-15
