@@ -113,7 +113,7 @@ def measured_peaks():
 
 def plan_source_hash():
     h = hashlib.sha256()
-    for f in ("plan.cu", "pass.cuh", "internal.cuh", "philox.cuh"):
+    for f in ("plan.cu", "pass.cuh", "philox.cuh"):
         with open(os.path.join(ROOT, "paper_1412_2293_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -524,6 +524,76 @@ def extra_rows(h, n, T, esize, stream, peaks):
         out[label] = {"ms_per_step": round(msq, 3), "trajectories": Tq, "e": eq,
                       "updates_per_s": Tq * (1 << Wq.n) * len(opsq) / (msq / 1e3),
                       "fidelity_mean": float(np.mean(fq))}
+
+    # f3: Choi-Jamiolkowski relative state of the noisy QFT on 7 system qubits (Sec. 4): the
+    # exact relative state (density matrix of 14 qubits, 4 GiB) and 1024 Monte Carlo
+    # trajectories of the 14-qubit entangled start through the fused passes
+    m7, e7 = 7, 0.01
+    ops7 = inputs.qft_circuit(m7)
+    hi7 = qs.qs_create(2 * m7, 1, 0, qs.QS_STATEVEC, qs.QS_C128, stream)
+    qs.qs_set_maximally_entangled(hi7)
+    p7 = qs.qs_plan_create(hi7, pcirc.to_gates([inputs.Op(o.kind, o.qubits, o.theta, o.index, False) for o in ops7]))
+    qs.qs_plan_run(p7, 0.0, 0, 0, hi7)
+    qs.qs_plan_destroy(p7)
+    psi7 = qs.qs_get_state(hi7)
+    hd7 = qs.qs_create(2 * m7, 1, 0, qs.QS_DENSITY, qs.QS_C128, stream)
+    qs.qs_set_maximally_entangled(hd7)
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    pcirc.apply_ops(hd7, ops7, e7, inputs.DEFAULT_SEED)
+    e1.record(stream)
+    f_dm7 = float(qs.qs_fidelity(hd7, psi7)[0])
+    ms_dm7 = e0.elapsed_time(e1)
+    qs.qs_destroy(hd7)
+    T7 = 1024
+    hm7 = qs.qs_create(2 * m7, T7, 0, qs.QS_STATEVEC, qs.QS_C64, stream)
+    pm7 = qs.qs_plan_create(hm7, pcirc.to_gates(ops7))
+    qs.qs_set_maximally_entangled(hm7)
+    qs.qs_plan_run(pm7, e7, inputs.DEFAULT_SEED, 0, hm7)
+    qs.qs_set_maximally_entangled(hm7)
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    qs.qs_plan_run(pm7, e7, inputs.DEFAULT_SEED, 0, hm7)
+    e1.record(stream)
+    f_mc7 = qs.qs_fidelity(hm7, psi7)
+    ms_mc7 = e0.elapsed_time(e1)
+    qs.qs_plan_destroy(pm7)
+    qs.qs_destroy(hm7)
+    qs.qs_destroy(hi7)
+    out["f3_relative_state_qft_m7"] = {
+        "system_qubits": m7, "e": e7, "fidelity_exact": f_dm7, "density_ms": round(ms_dm7, 2),
+        "fidelity_mc_mean": float(np.mean(f_mc7)), "fidelity_mc_stderr": float(np.std(f_mc7) / math.sqrt(T7)),
+        "mc_trajectories": T7, "mc_ms": round(ms_mc7, 3),
+        "mc_minus_exact_in_stderr": float((np.mean(f_mc7) - f_dm7) / max(np.std(f_mc7) / math.sqrt(T7), 1e-300))}
+
+    # f2: the rank-1 estimates of Fig. 4 for the noisy QFT, n = 12, e = 0.01: exact fidelity
+    # (density matrix), rank 1 by the direct and the rotated (Eqs. 12-14) branch, and the closed
+    # forms Eq. 11 (P_H^n P^(n(n-1)/8)) and Eq. 15 (P_H^n P~_R^(n(n-1)/8))
+    n12, e12, x12 = 12, 0.01, 5
+    ops12 = inputs.qft_circuit(n12)
+    hi12 = pcirc.ideal_reference(n12, ops12, x12, qs.QS_C128, stream)
+    phi12 = qs.qs_get_state(hi12)
+    qs.qs_destroy(hi12)
+    hd12 = qs.qs_create(n12, 1, 0, qs.QS_DENSITY, qs.QS_C128, stream)
+    qs.qs_set_basis_state(hd12, x12)
+    pcirc.apply_ops(hd12, ops12, e12, inputs.DEFAULT_SEED)
+    f_exact12 = float(qs.qs_fidelity(hd12, phi12)[0])
+    qs.qs_destroy(hd12)
+    branch = {}
+    for rotated in (False, True):
+        hb = qs.qs_create(n12, 1, 0, qs.QS_STATEVEC, qs.QS_C128, stream)
+        qs.qs_set_basis_state(hb, x12)
+        pcirc.apply_branch_ops(hb, ops12, e12, rotated)
+        branch["improved" if rotated else "direct"] = float(qs.qs_fidelity(hb, phi12)[0])
+        qs.qs_destroy(hb)
+    P12 = math.exp(-e12 * e12)
+    PH = (1.0 + math.exp(-2.0 * e12 * e12)) / 2.0
+    f12 = (math.sqrt(1.0 + 3.0 * P12) - P12 - 1.0) / math.sqrt(P12 * (1.0 - P12))
+    PR = (math.sqrt(P12) + f12 * math.sqrt(1.0 - P12)) ** 2 / (1.0 + f12 * f12) ** 4
+    ncp = n12 * (n12 - 1) / 8.0
+    out["f2_rank1_estimates_qft_n12"] = {
+        "e": e12, "fidelity_exact": f_exact12, "rank1_direct": branch["direct"], "rank1_improved": branch["improved"],
+        "eq11": PH ** n12 * P12 ** ncp, "eq15": PH ** n12 * PR ** ncp}
 
     out["a11_serving"] = serving_row()
     cap = out["a11_serving"]["jobs_per_s"]

@@ -63,6 +63,24 @@ def apply_ops(h, ops: List[Op], e: float, seed: int, gate_id0: int = 0):
             qs.qs_apply_gate(h, targets, U)
 
 
+def apply_branch_ops(h, ops: List[Op], e: float, rotated: bool = False):
+    """Issue a circuit with every noisy gate replaced by its first Kraus branch
+    (direct, Eq. 9, or rotated, Eqs. 12-14): the rank-1 estimates of Sec. 3.2."""
+    for op in ops:
+        if op.kind == "FLIP":
+            qs.qs_apply_phase_flip(h, op.index)
+            continue
+        if op.kind == "H":
+            targets, U, noise = (op.qubits[0],), _H, qs.QS_NOISE_ROTATION
+        else:
+            j, k = op.qubits
+            targets, U, noise = (k, j), controlled_phase(op.theta), qs.QS_NOISE_PHASE
+        if op.noisy:
+            qs.qs_apply_branch_gate(h, targets, U, noise, e, rotated)
+        else:
+            qs.qs_apply_gate(h, targets, U)
+
+
 def ideal_reference(n: int, ops: List[Op], x0: int, dtype: int, stream=None):
     """A batch-1 handle holding the noiseless circuit output (the fidelity reference)."""
     h = qs.qs_create(n, 1, 0, qs.QS_STATEVEC, dtype, stream)

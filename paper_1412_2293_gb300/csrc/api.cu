@@ -454,6 +454,34 @@ qs_status qs_apply_phase_flip(qs_handle h, uint64_t index) {
   return QS_OK;
 }
 
+qs_status qs_apply_branch_gate(qs_handle h, const int* targets, int k, const double* U, qs_noise noise,
+                               double e, int rotated) {
+  if (!h) return QS_ERR_INVALID_ARG;
+  { const qs_status st = qs::materialize_basis(h); if (st != QS_OK) return st; }
+  if (k < 1 || k > 2) return fail(h, QS_ERR_INVALID_ARG, "noisy gates are defined for k = 1, 2");
+  if (!U) return fail(h, QS_ERR_INVALID_ARG, "U is NULL");
+  if (!(e >= 0.0) || !std::isfinite(e)) return fail(h, QS_ERR_INVALID_ARG, "e must be finite and >= 0");
+  if (noise != QS_NOISE_ROTATION && noise != QS_NOISE_PHASE) return fail(h, QS_ERR_INVALID_ARG, "bad noise kind");
+  std::string why;
+  if (!valid_targets(h, targets, k, &why)) return fail(h, QS_ERR_INVALID_ARG, why);
+  const int d = 1 << k;
+  const auto ks = averaged_kraus(to_cplx(U, d), k, noise, e);
+  std::vector<cd> B = ks[0];
+  const double P = std::exp(-e * e);
+  if (rotated && noise == QS_NOISE_PHASE && P < 1.0) {
+    // Eqs. 12-14: B_1 = (E_1 + f E_2) / sqrt(1 + f^2), f = (sqrt(1 + 3P) - P - 1) / sqrt(P (1 - P))
+    const double f = (std::sqrt(1.0 + 3.0 * P) - P - 1.0) / std::sqrt(P * (1.0 - P));
+    const double sc = 1.0 / std::sqrt(1.0 + f * f);
+    for (size_t i = 0; i < B.size(); ++i) B[i] = sc * (ks[0][i] + f * ks[1][i]);
+  }
+  if (h->mode == QS_DENSITY) return dm_apply_channel(h, targets, k, {B});
+  if (h->mode == QS_FIXED_RANK) {
+    if (!all_real(B)) h->real_factor = false;
+    return apply_uniform(h, h->state, h->n, h->cols, targets, k, B);
+  }
+  return apply_uniform(h, h->state, h->n, h->batch, targets, k, B);
+}
+
 qs_status qs_apply_noisy_gate(qs_handle h, const int* targets, int k, const double* U, qs_noise noise,
                               double e, uint64_t seed, uint64_t gate_id) {
   if (!h) return QS_ERR_INVALID_ARG;

@@ -171,14 +171,42 @@ template <typename R>
 __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int stride, const DGate* __restrict__ gates,
                                                     const Producer* __restrict__ prods, int num_prods,
                                                     const Contrib* __restrict__ contribs, int num_contribs,
-                                                    int num_dwin, int diag_off, NoiseSrc src, const RunParams* rp) {
+                                                    int num_dwin, int num_dense, int diag_off, NoiseSrc src,
+                                                    const RunParams* rp) {
   extern __shared__ double2 pre_sm[];                   // [num_contribs] factors, then [num_dwin][10]
   const int b = blockIdx.x;
   double e;
   uint64_t seed, traj;
   member_noise(src, rp, b, &e, &seed, &traj);
   R* out = params + (uint64_t)b * stride;
-  // the last kWin threads build the dense matrices while the others compute
+  // noisy 2x2 matrices of the dense gates, all threads in parallel, into
+  // shared memory (FP64, [slot][4] complex after the tables' scratch).  A
+  // real gate M is stored as the quantities its factored form needs (see the
+  // chain below): u = M01 / M00, v = M10 M00 / det, w = det / M00^2, 1 / w
+  // and M00 (a pivot below min_pivot is replaced by that value).
+  double2* dmat = pre_sm + num_contribs + (size_t)num_dwin * kWin + (1u << (kWin - 1));
+  for (int i = threadIdx.x; i < num_prods; i += blockDim.x) {
+    const Producer p = prods[i];
+    if (p.kind != PD_DENSE) continue;
+    const DGate& g = gates[p.gate];
+    double m[8];
+    noisy_matrix<R>(g, e, seed, traj, rp->gate_id0 + g.gate_pos, m);
+    double2* slot = dmat + p.contrib_start * 4;
+    if (p.real) {
+      const double mp = min_pivot<R>();
+      double a = m[0];
+      if (fabs(a) < mp) a = a < 0.0 ? -mp : mp;
+      double d2 = m[6] - m[4] * m[2] / a;               // det / M00
+      if (fabs(d2) < mp) d2 = d2 < 0.0 ? -mp : mp;
+      slot[0] = make_double2(m[2] / a, m[4] / d2);      // u, v
+      slot[1] = make_double2(d2 / a, a / d2);           // w, 1 / w
+      slot[2] = make_double2(a, 0.0);                   // M00
+    } else {
+      for (int q = 0; q < 4; ++q) slot[q] = make_double2(m[2 * q], m[2 * q + 1]);
+    }
+  }
+  __syncthreads();
+  // the last kWin threads factor the dense gates while the others compute
   // the phase factors
   constexpr int kPhaseThreads = 128 - kWin;
   // contributions of the phase tables, and out factors
@@ -197,45 +225,46 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
       }
     }
   }
-  // dense matrices: one thread per window bit walks that bit's gates in
-  // circuit order.  A real gate M' = M diag(pa, pd) = [[a, b], [c, d]] (the
-  // diagonal left by the previous real gate on the bit) is stored as the two
-  // shears of M' = diag(a, det / a) [[1, 0], [s1, 1]] [[1, r0], [0, 1]],
-  // r0 = b / a, s1 = c a / det, and diag(a, det / a) is carried on; a complex
-  // gate absorbs the carried diagonal.  What is left at the end goes to the
-  // diag block.
+  // dense gates: one thread per window bit walks that bit's gates in circuit
+  // order.  A real gate M' = M diag(pa, pd) = [[a, b], [c, d]] (the diagonal
+  // left by the previous real gate on the bit) is stored as the two shears of
+  // M' = diag(a, det'/a) [[1, 0], [s1, 1]] [[1, r0], [0, 1]], r0 = b / a,
+  // s1 = c a / det', and diag(a, det'/a) is carried on.  With rho = pd / pa
+  // this is r0 = u rho, s1 = v / rho, new pa = pa M00, new rho = rho w (u, v,
+  // w, M00 of M from above): products only.  A complex gate absorbs the
+  // carried diagonal.  What is left at the end goes to the diag block.
   __shared__ double pivot_a[kWin];
   if (threadIdx.x >= kPhaseThreads) {
     const int J = threadIdx.x - kPhaseThreads;
-    double pa = 1.0, pd = 1.0;
+    double pa = 1.0, rho = 1.0, rho_inv = 1.0;
     for (int i = 0; i < num_prods; ++i) {
       const Producer p = prods[i];
       if (p.kind != PD_DENSE || p.j != J) continue;
-      const DGate& g = gates[p.gate];
-      double m[8];
-      noisy_matrix<R>(g, e, seed, traj, rp->gate_id0 + g.gate_pos, m);
-      m[0] *= pa; m[1] *= pa; m[4] *= pa; m[5] *= pa;   // column 0
-      m[2] *= pd; m[3] *= pd; m[6] *= pd; m[7] *= pd;   // column 1
+      const double2* slot = dmat + p.contrib_start * 4;
       if (p.real) {
-        const double mp = min_pivot<R>();
-        double a = m[0];
-        if (fabs(a) < mp) a = a < 0.0 ? -mp : mp;
-        double d2 = m[6] - m[4] * m[2] / a;             // det / a
-        if (fabs(d2) < mp) d2 = d2 < 0.0 ? -mp : mp;
-        const R r0 = (R)(m[2] / a), s1 = (R)(m[4] / d2);
+        const double2 uv = slot[0], ww = slot[1];
+        const R r0 = (R)(uv.x * rho), s1 = (R)(uv.y * rho_inv);
         out[p.off] = r0;                                // (r0, r0, s1, s1)
         out[p.off + 1] = r0;
         out[p.off + 2] = s1;
         out[p.off + 3] = s1;
-        pa = a;
-        pd = d2;
+        pa *= slot[2].x;
+        rho *= ww.x;
+        rho_inv *= ww.y;
       } else {
-        for (int q = 0; q < 8; ++q) out[p.off + q] = (R)m[q];
-        pa = pd = 1.0;
+        const double pd = rho * pa;
+        for (int q = 0; q < 4; ++q) {
+          const double2 v = slot[q];
+          const double sc = (q & 1) ? pd : pa;          // column 0 by pa, column 1 by pd
+          out[p.off + 2 * q] = (R)(v.x * sc);
+          out[p.off + 2 * q + 1] = (R)(v.y * sc);
+        }
+        pa = 1.0;
+        rho = rho_inv = 1.0;
       }
     }
     pivot_a[J] = pa;
-    if (diag_off >= 0) out[diag_off + J] = (R)(pd / pa);
+    if (diag_off >= 0) out[diag_off + J] = (R)rho;
   }
   __syncthreads();
   if (diag_off >= 0 && threadIdx.x == 0) {
@@ -358,6 +387,7 @@ struct PassPlan {
   std::vector<Producer> prods;
   std::vector<Contrib> contribs;
   int num_dwin = 0;
+  int num_dense = 0;
   int diag_off = -1;              // deferred diagonals of the factored real gates
   int stride = 0;                 // R units per member
   std::vector<int> other;
@@ -527,6 +557,7 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
       pr.gate = rem[i];
       pr.j = l;
       pr.real = x.real;
+      pr.contrib_start = dense_count;                   // DENSE: slot of its matrix in the precompute
       x.off = (uint32_t)P->prods.size();                // patched to an offset below
       P->prods.push_back(pr);
       P->ops.push_back(x);
@@ -588,6 +619,7 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
       prods.push_back(pr);
     }
   }
+  P->num_dense = dense_count;
   P->diag_off = -1;
   if (any_real) {                                       // ratios of the 10 window bits + scale
     P->diag_off = (int)off;
@@ -845,10 +877,11 @@ cudaError_t launch_precompute(qs_plan p, const PassPlan& P, cudaStream_t s) {
   qs_ctx* h = p->h;
   NoiseSrc src{};
   if (h->member_noise) { src.e = h->m_e; src.seed = h->m_seed; src.traj = h->m_traj; }
-  const size_t pre_smem = (P.contribs.size() + (size_t)P.num_dwin * kWin + (1u << (kWin - 1))) * sizeof(double2);
+  const size_t pre_smem =
+      (P.contribs.size() + (size_t)P.num_dwin * kWin + (1u << (kWin - 1)) + 4 * (size_t)P.num_dense) * sizeof(double2);
   k_precompute<R><<<h->batch, 128, pre_smem, s>>>((R*)P.d_params, P.stride, p->d_gates, P.d_prods,
                                                    (int)P.prods.size(), P.d_contribs, (int)P.contribs.size(),
-                                                   P.num_dwin, P.diag_off, src, p->d_run);
+                                                   P.num_dwin, P.num_dense, P.diag_off, src, p->d_run);
   if (P.d_alpha) {
     OutStarts st{};
     for (int i = 0; i < 12; ++i) st.v[i] = P.out_start[i];
@@ -929,7 +962,11 @@ cudaError_t set_smem_attrs(size_t esize) {
   static std::atomic<bool> done[2] = {false, false};
   const int which = esize == 8 ? 0 : 1;
   if (done[which]) return cudaSuccess;
-  cudaError_t e;
+  constexpr size_t kPreSmem = (kMaxContribs + kMaxDwin * kWin + (1u << (kWin - 1)) + 4 * kMaxOps) * sizeof(double2);
+  cudaError_t e = esize == 8
+      ? cudaFuncSetAttribute(k_precompute<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPreSmem)
+      : cudaFuncSetAttribute(k_precompute<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPreSmem);
+  if (e != cudaSuccess) return e;
   if (esize == 8) {
     e = set_pass_attrs(k_pass_low<float, 12, 2>, low_smem<float, 12, 2>(), 1);
     if (e == cudaSuccess) e = set_pass_attrs(k_pass_low<float, 16, 1>, low_smem<float, 16, 1>(), 1);

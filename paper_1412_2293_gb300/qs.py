@@ -55,6 +55,7 @@ _SIGS = {
     "qs_apply_gate": ([_P, _I, ct.c_int, _D], ct.c_int),
     "qs_apply_phase_flip": ([_P, ct.c_uint64], ct.c_int),
     "qs_apply_noisy_gate": ([_P, _I, ct.c_int, _D, ct.c_int, ct.c_double, ct.c_uint64, ct.c_uint64], ct.c_int),
+    "qs_apply_branch_gate": ([_P, _I, ct.c_int, _D, ct.c_int, ct.c_double, ct.c_int], ct.c_int),
     "qs_apply_kraus": ([_P, _I, ct.c_int, _D, ct.c_int], ct.c_int),
     "qs_truncate_rank": ([_P, ct.c_int, ct.c_int], ct.c_int),
     "qs_set_normalize": ([_P, ct.c_int], ct.c_int),
@@ -180,6 +181,12 @@ def qs_apply_noisy_gate(h, targets, U, noise, e, seed, gate_id):
     u = _cplx_interleaved(U)
     _check(lib().qs_apply_noisy_gate(h, _targets(targets), len(targets), _dptr(u), int(noise), float(e),
                                      int(seed), int(gate_id)), h)
+
+
+def qs_apply_branch_gate(h, targets, U, noise, e, rotated=False):
+    u = _cplx_interleaved(U)
+    _check(lib().qs_apply_branch_gate(h, _targets(targets), len(targets), _dptr(u), int(noise), float(e),
+                                      1 if rotated else 0), h)
 
 
 def qs_apply_kraus(h, targets, kraus):

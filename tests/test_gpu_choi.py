@@ -107,3 +107,48 @@ def test_fixed_rank_relative_state_at_full_rank_is_exact():
     L = qs.qs_get_state(h).reshape(16, -1)[:r].T
     qs.qs_destroy(h)
     np.testing.assert_allclose(L @ L.conj().T, ochoi.relative_state(m, ops, e), atol=1e-12)
+
+
+# ---------------------------------------------------------------- rank-1 by branch selection (Eqs. 12-15)
+from oracle import circuits as ocirc  # noqa: E402
+from oracle import gates as ogates  # noqa: E402
+
+
+@pytest.mark.parametrize("n", [6, 9])
+@pytest.mark.parametrize("rotated", [False, True])
+def test_branch_rank1_matches_oracle(n, rotated):
+    e, x0 = 0.05, 11
+    ops = inputs.qft_circuit(n)
+    ideal = ocirc.ideal_state(n, ops, x0)
+    for mode, rank in ((qs.QS_STATEVEC, 0), (qs.QS_FIXED_RANK, 1)):
+        h = qs.qs_create(n, 1, rank, mode, qs.QS_C128)
+        qs.qs_set_basis_state(h, x0)
+        pcirc.apply_branch_ops(h, ops, e, rotated)
+        f = qs.qs_fidelity(h, ideal)[0]
+        got = qs.qs_get_state(h)[: 1 << n]
+        qs.qs_destroy(h)
+        want = ocirc.run_branch(n, ops, x0, e, rotated)
+        np.testing.assert_allclose(got, want, atol=1e-12)
+        fw = abs(np.vdot(ideal, want)) ** 2
+        assert abs(f - fw) <= 1e-12 * fw
+
+
+def test_branch_rank1_grover_is_eq10_and_rotation_improves_qft():
+    e, n = 0.01, 10
+    k, w = inputs.grover_iterations(n), inputs.draw_marked(n, SEED)
+    h = qs.qs_create(n, 1, 0, qs.QS_STATEVEC, qs.QS_C128)
+    pcirc.apply_branch_ops(h, inputs.grover_circuit(n, k, w), e)
+    p = qs.qs_fidelity(h, None, w)[0]
+    qs.qs_destroy(h)
+    want = ogates.grover_rank1_success(n, k, e)
+    assert abs(p - want) <= 1e-12 * want
+    ops = inputs.qft_circuit(n)
+    ideal = ocirc.ideal_state(n, ops, 3)
+    fs = []
+    for rotated in (False, True):
+        h = qs.qs_create(n, 1, 0, qs.QS_STATEVEC, qs.QS_C128)
+        qs.qs_set_basis_state(h, 3)
+        pcirc.apply_branch_ops(h, ops, 0.05, rotated)
+        fs.append(qs.qs_fidelity(h, ideal)[0])
+        qs.qs_destroy(h)
+    assert fs[1] > fs[0]                                   # the rotated branch keeps more of the state
