@@ -357,6 +357,33 @@ __global__ void __launch_bounds__(256) k_out_table(cplx<R>* __restrict__ tab, co
   tab[b * per + i] = mk<R>(re * d, im * d);
 }
 
+// A run of diagonal channels on the exact density matrix (Sec. 3): noiseless
+// diagonal gates and phase flips (rho -> D rho D^dagger) and noisy diagonal
+// gates with the phase-noise Kraus pair of Eq. 9.  Each multiplies rho[x][y]
+// by d(x) conj(d(y)), and a noisy one also by sqrt(P) when exactly one of x, y
+// has all its targets set (the pair gives 1 when both or neither have), so the
+// run multiplies rho[x][y] by u(x) conj(u(y)) qpow[popcount(mask(x) ^ mask(y))]
+// with u = the product of the diagonals and bit c of mask(x) = "x has all
+// targets of noisy gate c set".  vec index x 2^n + y.
+struct QPow { double v[33]; };
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_dm_diag_block(cplx<R>* __restrict__ rho, int n, const double2* __restrict__ u,
+                                                       const uint32_t* __restrict__ mask, QPow qp) {
+  const uint64_t N = 1ull << n;
+  const uint64_t total = N * N;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < total; v += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t x = v >> n, y = v & (N - 1);
+    const double2 ux = u[x], uy = u[y];
+    const uint32_t mx = mask[x], my = mask[y];
+    if ((mx | my) == 0 && ux.x == 1.0 && ux.y == 0.0 && uy.x == 1.0 && uy.y == 0.0) continue;
+    const double d = qp.v[__popc(mx ^ my)];
+    const double fr = (ux.x * uy.x + ux.y * uy.y) * d, fi = (ux.y * uy.x - ux.x * uy.y) * d;
+    const cplx<R> r = rho[v];
+    rho[v] = mk<R>((R)(r.x * fr - r.y * fi), (R)(r.x * fi + r.y * fr));
+  }
+}
+
 }  // namespace fused
 }  // namespace qs
 
@@ -406,9 +433,15 @@ struct PassPlan {
 };
 
 struct Step {
-  int kind;               // 0 = fused pass, 1 = single gate
+  int kind;               // 0 = fused pass, 1 = single gate, 2 = density-matrix diagonal block
   int pass = -1;
-  int gate = -1;
+  int gate = -1;          // single gate, or the diagonal block's index
+};
+
+struct DmBlock {          // density matrix: a run of diagonal channels (k_dm_diag_block)
+  double2* d_u = nullptr;
+  uint32_t* d_mask = nullptr;
+  int noisy = 0;
 };
 
 }  // namespace
@@ -428,6 +461,7 @@ struct qs_plan_s {
   bool graph_member_marked[6] = {false, false, false, false, false, false};
   bool graph_timing[6] = {false, false, false, false, false, false};
   double* d_fid = nullptr;        // fused-fidelity partials [member][tile] complex
+  std::vector<DmBlock> dm_blocks;
   int colb = 3;
   int low_cfg = 0;                // kernel configuration of each window geometry (see launch_pass_kernel)
   int high_cfg = 0;
@@ -982,6 +1016,32 @@ cudaError_t set_smem_attrs(size_t esize) {
   return e;
 }
 
+qs_status run_single(qs_plan p, const PGate& g, const RunParams& rp, int pos);
+
+// a density-matrix diagonal block with noise level rp.e: qpow[k] = sqrt(P)^k, P = exp(-e^2)
+qs_status run_dm_block(qs_plan p, const DmBlock& b, const RunParams& rp) {
+  qs_ctx* h = p->h;
+  QPow qp{};
+  const double q = std::sqrt(std::exp(-rp.e * rp.e));
+  qp.v[0] = 1.0;
+  for (int i = 1; i <= 32; ++i) qp.v[i] = qp.v[i - 1] * q;
+  const uint64_t total = 1ull << (2 * h->n);
+  uint64_t blocks = (total + 255) / 256;
+  const uint64_t cap = (uint64_t)num_sms() * 16;
+  if (blocks > cap) blocks = cap;
+  if (h->dtype == QS_C64)
+    k_dm_diag_block<float><<<(int)blocks, 256, 0, h->stream>>>((float2*)h->state, h->n, b.d_u, b.d_mask, qp);
+  else
+    k_dm_diag_block<double><<<(int)blocks, 256, 0, h->stream>>>((double2*)h->state, h->n, b.d_u, b.d_mask, qp);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? QS_OK : pfail(p, QS_ERR_CUDA, cudaGetErrorString(e));
+}
+
+qs_status run_step(qs_plan p, const Step& st, const RunParams& rp) {
+  if (st.kind == 2) return run_dm_block(p, p->dm_blocks[st.gate], rp);
+  return run_single(p, p->gates[st.gate], rp, st.gate);
+}
+
 qs_status run_single(qs_plan p, const PGate& g, const RunParams& rp, int pos) {
   qs_ctx* h = p->h;
   if (g.g.kind == QS_GATE_FLIP) return qs_apply_phase_flip(h, g.g.index);
@@ -1029,7 +1089,7 @@ qs_status enqueue_run(qs_plan p, cudaStream_t s, int synth, int fid) {
       }
       if (e != cudaSuccess) { h->stream = saved; return pfail(p, QS_ERR_CUDA, std::string("fused pass: ") + cudaGetErrorString(e)); }
     } else {
-      qs_status r = run_single(p, p->gates[st.gate], *p->h_run, st.gate);
+      qs_status r = run_step(p, st, *p->h_run);
       mark(3);
       if (r != QS_OK) { h->stream = saved; return r; }
     }
@@ -1069,7 +1129,7 @@ qs_status run_plan(qs_plan p, double e, uint64_t seed, uint64_t gate_id0, int wa
   // the run owns the start state from here on: later steps (single gates)
   // must not write the basis state again
   if (synth) h->pending = 0;
-  const bool has_single = std::any_of(p->steps.begin(), p->steps.end(), [](const Step& s) { return s.kind == 1; });
+  const bool has_single = std::any_of(p->steps.begin(), p->steps.end(), [](const Step& s) { return s.kind != 0; });
   qs_status st = QS_OK;
   if (has_single) {
     if (cudaMemcpyAsync(p->d_run, p->h_run, sizeof(RunParams), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
@@ -1144,6 +1204,37 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
   const bool fuse = h->mode == QS_STATEVEC && h->n >= kWin && h->n <= 32;
   std::vector<int> rem;
   for (int i = 0; i < num_gates; ++i) rem.push_back(i);
+  std::vector<std::vector<int>> dm_groups;
+  if (h->mode == QS_DENSITY) {
+    // runs of diagonal channels become one sweep each (k_dm_diag_block)
+    auto dm_diag = [&](const PGate& g) {
+      if (g.g.kind == QS_GATE_FLIP) return true;
+      if (g.g.kind != QS_GATE_DENSE || !g.diag) return false;
+      return !g.g.noisy || g.g.noise == QS_NOISE_PHASE;
+    };
+    std::vector<int> cur;
+    int noisy = 0;
+    auto close = [&]() {
+      if (cur.empty()) return;
+      dm_groups.push_back(cur);
+      p->steps.push_back(Step{2, -1, (int)dm_groups.size() - 1});
+      cur.clear();
+      noisy = 0;
+    };
+    for (int i : rem) {
+      const PGate& g = p->gates[i];
+      if (dm_diag(g)) {
+        if (g.g.kind == QS_GATE_DENSE && g.g.noisy && noisy == 32) close();
+        cur.push_back(i);
+        if (g.g.kind == QS_GATE_DENSE && g.g.noisy) ++noisy;
+      } else {
+        close();
+        p->steps.push_back(Step{1, -1, i});
+      }
+    }
+    close();
+    rem.clear();
+  }
   while (!rem.empty()) {
     if (fuse) {
       PassPlan P;
@@ -1183,6 +1274,35 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
     dg[i] = x;
   }
   qs_status st = upload(p, &p->d_gates, dg);
+  for (const auto& grp : dm_groups) {
+    if (st != QS_OK) break;
+    const uint64_t N = 1ull << h->n;
+    std::vector<double2> u(N, make_double2(1.0, 0.0));
+    std::vector<uint32_t> mask(N, 0u);
+    int c = 0;
+    for (int gi : grp) {
+      const PGate& g = p->gates[gi];
+      if (g.g.kind == QS_GATE_FLIP) {
+        if (g.g.index < N) u[g.g.index] = make_double2(-u[g.g.index].x, -u[g.g.index].y);
+        continue;
+      }
+      const int k = g.g.k, d = 1 << k;
+      for (uint64_t x = 0; x < N; ++x) {
+        int l = 0;
+        for (int j = 0; j < k; ++j) l |= (int)((x >> g.g.targets[j]) & 1) << j;
+        const cd f = g.U[(size_t)l * d + l];
+        const double2 a = u[x];
+        u[x] = make_double2(a.x * f.real() - a.y * f.imag(), a.x * f.imag() + a.y * f.real());
+        if (g.g.noisy && l == d - 1) mask[x] |= 1u << c;
+      }
+      if (g.g.noisy) ++c;
+    }
+    DmBlock b;
+    b.noisy = c;
+    st = upload(p, &b.d_u, u);
+    if (st == QS_OK) st = upload(p, &b.d_mask, mask);
+    p->dm_blocks.push_back(b);
+  }
   size_t fid_tiles = 0;
   for (auto& P : p->passes) {
     if (st != QS_OK) break;
@@ -1270,7 +1390,7 @@ qs_status qs_plan_profile(qs_plan p, int reps, double e, uint64_t seed, uint64_t
         kind[li++] = P.high ? 2 : 1;
         if (x != cudaSuccess) { result = pfail(p, QS_ERR_CUDA, cudaGetErrorString(x)); break; }
       } else {
-        result = run_single(p, p->gates[st.gate], *p->h_run, st.gate);
+        result = run_step(p, st, *p->h_run);
         cudaEventRecord(ev[k++], h->stream);
         kind[li++] = 3;
         if (result != QS_OK) break;
@@ -1408,6 +1528,10 @@ qs_status qs_plan_destroy(qs_plan p) {
   }
   if (p->d_gates) cudaFree(p->d_gates);
   if (p->d_fid) cudaFree(p->d_fid);
+  for (auto& b : p->dm_blocks) {
+    if (b.d_u) cudaFree(b.d_u);
+    if (b.d_mask) cudaFree(b.d_mask);
+  }
   if (p->d_run) cudaFree(p->d_run);
   if (p->h_run) cudaFreeHost(p->h_run);
   for (auto& e : p->events) cudaEventDestroy(e);

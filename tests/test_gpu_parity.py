@@ -533,3 +533,34 @@ def test_autotune_picks_a_configuration_and_results_stay_correct():
         qs.qs_plan_autotune(p, 1, e, SEED, h)
         assert qs.qs_plan_get_config(p, h) == (0, 0)
         qs.qs_plan_destroy(p)
+
+
+@pytest.mark.parametrize("circ,n", [("qft", 6), ("qft", 7), ("grover", 5)])
+@pytest.mark.parametrize("dtype", [qs.QS_C128])
+def test_density_plan_with_diagonal_blocks_matches_oracle(circ, n, dtype):
+    """Plans on density matrices run each run of diagonal channels (noisy
+    controlled phases, flips) as one sweep; the result equals the oracle and
+    the gate-by-gate channels."""
+    e = 0.05
+    if circ == "qft":
+        ops, x0 = inputs.qft_circuit(n), 5
+    else:
+        ops, x0 = inputs.grover_circuit(n, 2, 6), 0
+    with Handle(n, 1, 0, qs.QS_DENSITY, dtype) as h:
+        qs.qs_set_basis_state(h, x0)
+        p = qs.qs_plan_create(h, pcirc.to_gates(ops))
+        qs.qs_plan_run(p, e, SEED, 0, h)
+        planned = qs.qs_get_state(h)
+        # the same plan again from the start: the blocks are reusable
+        qs.qs_set_basis_state(h, x0)
+        qs.qs_plan_run(p, e, SEED, 0, h)
+        again = qs.qs_get_state(h)
+        qs.qs_plan_destroy(p)
+    with Handle(n, 1, 0, qs.QS_DENSITY, dtype) as h:
+        qs.qs_set_basis_state(h, x0)
+        pcirc.apply_ops(h, ops, e, SEED)
+        single = qs.qs_get_state(h)
+    rho = ocirc.run_density(n, ops, x0, e)
+    np.testing.assert_allclose(planned, rho.ravel(), atol=1e-12)
+    np.testing.assert_allclose(planned, single, atol=1e-13)
+    np.testing.assert_array_equal(again, planned)
