@@ -131,6 +131,18 @@ qs_status qs_apply_phase_flip(qs_handle h, uint64_t index);
 qs_status qs_apply_noisy_gate(qs_handle h, const int* targets, int k, const double* U,
                               qs_noise noise, double e, uint64_t seed, uint64_t gate_id);
 
+/* Rank-1 estimate by branch selection (Sec. 3.2, the estimates behind Eqs. 11
+ * and 15, Fig. 4): the noisy gate replaced by the first operator of its
+ * xi-averaged Kraus set -- sqrt(lambda_1) U (rotation noise, Eq. 6),
+ * U diag(1,..,1,sqrt P) (phase noise, Eq. 9), or with rotated = 1 for phase
+ * noise the rotated B_1 = (E_1 + f E_2) / sqrt(1 + f^2) of Eqs. 12-14.  The
+ * state is not renormalised: after a circuit, |<ideal|psi>|^2 is the rank-1
+ * estimate of the fidelity.  Applied to every member (STATEVEC), column
+ * (FIXED_RANK) or as B rho B^dagger (DENSITY).  Arguments and errors as
+ * qs_apply_noisy_gate. */
+qs_status qs_apply_branch_gate(qs_handle h, const int* targets, int k, const double* U, qs_noise noise,
+                               double e, int rotated);
+
 /* Quantum operation sum_i E_i rho E_i^dagger (Eq. 3) with num_ops Kraus
  * operators E (num_ops consecutive 2^k x 2^k matrices), k = 1..2.
  * The set must satisfy sum_i E_i^dagger E_i = I within 1e-12 (else
