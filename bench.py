@@ -600,6 +600,52 @@ def extra_rows(h, n, T, esize, stream, peaks):
         "e": e12, "fidelity_exact": f_exact12, "rank1_direct": branch["direct"], "rank1_improved": branch["improved"],
         "eq11": PH ** n12 * P12 ** ncp, "eq15": PH ** n12 * PR ** ncp}
 
+    # f4: T1/T2 relaxation of every qubit of a 14-qubit complex64 density matrix (2^28 entries,
+    # 2.1 GB, larger than L2; two qubits per sweep, one read and one write of rho each), then the
+    # relative-state fidelities of Sec. 4.1-4.3 through the same calls
+    from paper_1412_2293_gb300 import codes
+    n14, relax = 14, (0.01, 3.0, 2.0)
+    hr = qs.qs_create(n14, 1, 0, qs.QS_DENSITY, qs.QS_C64, stream)
+    qs.qs_set_maximally_entangled(hr)
+    allq = list(range(n14))
+    qs.qs_apply_relaxation(hr, allq, *relax)
+    reps = 3
+    e0, e1 = ev(), ev()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        qs.qs_apply_relaxation(hr, allq, *relax)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_relax = e0.elapsed_time(e1) / reps
+    tr_relax = float(qs.qs_trace(hr)[0])
+    qs.qs_destroy(hr)
+    sweeps = (n14 + 1) // 2
+    sweep_bytes = 2 * (1 << (2 * n14)) * 8
+    gbs = sweep_bytes * sweeps / (ms_relax / 1e3) / 1e9
+    t0 = time.perf_counter()
+    p_grid = [0.01, 0.05, 0.1, 0.2, 0.3]
+    phase3 = [codes.code_relative_fidelity("phase3", ("phase", p)) for p in p_grid]
+    shor9 = [codes.code_relative_fidelity("shor9", ("phase", p)) for p in p_grid[:3]]
+    fig8 = {"uncoded": codes.uncoded_relative_fidelity(("relax", 1.0, 3.0, 2.0), gate=np.diag([1.0, -1.0])),
+            "phase3": codes.code_relative_fidelity("phase3", ("relax", 1.0, 3.0, 2.0), logical_z=True),
+            "shor9": codes.code_relative_fidelity("shor9", ("relax", 1.0, 3.0, 2.0), logical_z=True)}
+    ms_codes = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    g5 = codes.qft_gates(5)
+    fig9 = {f"T1={T1:g},T2={T2:g}": codes.circuit_relaxation_fidelity(5, g5, 0.1, T1, T2)
+            for T1 in (1.0, 5.0, 20.0) for T2 in (1.0, 2.0, 10.0) if T2 <= 2 * T1}
+    ms_fig9 = (time.perf_counter() - t0) * 1e3
+    out["f4_relaxation_and_codes"] = {
+        "kernel": "k_dm_relax", "qubits": n14, "dtype": "c64", "t_T1_T2": relax, "sweeps_per_call": sweeps,
+        "bytes_per_sweep": sweep_bytes, "ms_all_qubits": round(ms_relax, 3),
+        "achieved_GBps": round(gbs, 1), "frac_of_measured_hbm": round(gbs / peaks["hbm_gbs"], 4),
+        "trace_after": tr_relax,
+        "phase3_p": p_grid, "phase3_fidelity": phase3,
+        "eq18_fmin_squared": [1.0 - 3.0 * p * p + 2.0 * p ** 3 for p in p_grid],
+        "shor9_fidelity": shor9, "codes_ms": round(ms_codes, 1),
+        "fig8_logical_z_T1_3_T2_2": fig8, "fig9_qft5_t0.1": fig9, "fig9_ms": round(ms_fig9, 1)}
+
     out["a11_serving"] = serving_row()
     cap = out["a11_serving"]["jobs_per_s"]
     out["a11_serving_rate_sweep"] = {f"{m}x_capacity": serving_row(num_jobs=60, rate_per_s=m * cap, seed_offset=1)

@@ -109,7 +109,9 @@ qs_status qs_set_maximally_entangled(qs_handle h);
 /* ------------------------------------------------------------------- gates */
 
 /* Ideal k-qubit gate U (k = 1..4) on `targets` (distinct, < n) -- Sec. 2.
- * DENSITY: rho <- U rho U^dagger via (U (x) U*) on bits (t, t + n), Sec. 3.
+ * DENSITY: rho <- U rho U^dagger via (U (x) U*) on bits (t, t + n), Sec. 3;
+ *   one 2k-qubit sweep for k <= 2, two k-qubit sweeps (U on the row bits
+ *   t + n, U* on the column bits t) for k = 3, 4.
  * FIXED_RANK: L <- U L (no truncation).
  * Errors: INVALID_ARG for bad targets / k / NULL pointers. */
 qs_status qs_apply_gate(qs_handle h, const int* targets, int k, const double* U);
@@ -150,6 +152,23 @@ qs_status qs_apply_branch_gate(qs_handle h, const int* targets, int k, const dou
  * FIXED_RANK: L' = [E_1 L | ... | E_K L], then truncation to the handle's
  * rank when num_ops > 1.  STATEVEC: NOT_SUPPORTED. */
 qs_status qs_apply_kraus(qs_handle h, const int* targets, int k, const double* E, int num_ops);
+
+/* Amplitude (T1) and phase (T2) relaxation over time t of each of the
+ * `count` distinct qubits in `qubits` (Sec. 4 names both processes; the
+ * channel is the textbook one: amplitude damping with gamma = 1 - exp(-t/T1),
+ * then dephasing to a total coherence factor c = exp(-t/T2)):
+ *   rho_00 += gamma rho_11,  rho_11 *= exp(-t/T1),  rho_01, rho_10 *= c.
+ * T1 or T2 = +infinity turns that process off; a phase error of probability p
+ * is T1 = inf with exp(-t/T2) = 1 - 2p (Eq. 19).
+ * DENSITY: in place, two qubits per sweep of rho (each entry read and written
+ *   once per sweep); coefficients in the handle's precision.
+ * FIXED_RANK: per qubit the Kraus set diag(1, c), sqrt(gamma)|0><1|,
+ *   diag(0, sqrt(exp(-t/T1) - c^2)) (zero operators omitted) as
+ *   qs_apply_kraus, i.e. expansion and truncation to the handle's rank.
+ * STATEVEC: NOT_SUPPORTED.
+ * Errors: INVALID_ARG for count < 0, a qubit out of range or repeated,
+ * t < 0 or not finite, T1 <= 0, T2 <= 0, or T2 > 2 T1 (not a channel). */
+qs_status qs_apply_relaxation(qs_handle h, const int* qubits, int count, double t, double T1, double T2);
 
 /* FIXED_RANK: truncate the current factor to rank r (<= handle rank) by the
  * Gram-matrix eigendecomposition (Sec. 3.2).  normalize = 0 keeps the trace

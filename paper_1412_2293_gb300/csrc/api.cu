@@ -440,8 +440,17 @@ qs_status qs_apply_gate(qs_handle h, const int* targets, int k, const double* U)
     if (!all_real(M)) h->real_factor = false;
     return apply_uniform(h, h->state, h->n, h->cols, targets, k, M);
   }
-  if (k > 2) return fail(h, QS_ERR_NOT_SUPPORTED, "DENSITY gates are limited to k <= 2");
-  return dm_apply_channel(h, targets, k, {M});
+  if (k <= 2) return dm_apply_channel(h, targets, k, {M});
+  // k = 3, 4: U on the row bits t + n and conj(U) on the column bits t, two
+  // sweeps of k-qubit gates on the 2n-qubit vector (a 2k-qubit superoperator
+  // would exceed the dense-gate limit)
+  int rows[qs::kMaxK];
+  for (int j = 0; j < k; ++j) rows[j] = targets[j] + h->n;
+  std::vector<cd> Mc(M.size());
+  for (size_t i = 0; i < M.size(); ++i) Mc[i] = std::conj(M[i]);
+  const qs_status st = apply_uniform(h, h->state, 2 * h->n, 1, rows, k, M);
+  if (st != QS_OK) return st;
+  return apply_uniform(h, h->state, 2 * h->n, 1, targets, k, Mc);
 }
 
 qs_status qs_apply_phase_flip(qs_handle h, uint64_t index) {
@@ -528,6 +537,39 @@ qs_status qs_apply_kraus(qs_handle h, const int* targets, int k, const double* E
   if (!kraus_complete(ks, d, 1e-12)) return fail(h, QS_ERR_INVALID_ARG, "sum E^dagger E != I (tolerance 1e-12)");
   if (h->mode == QS_DENSITY) return dm_apply_channel(h, targets, k, ks);
   return rank_apply_kraus(h, targets, k, ks);
+}
+
+qs_status qs_apply_relaxation(qs_handle h, const int* qubits, int count, double t, double T1, double T2) {
+  if (!h) return QS_ERR_INVALID_ARG;
+  if (h->mode == QS_STATEVEC) return fail(h, QS_ERR_NOT_SUPPORTED, "relaxation needs DENSITY or FIXED_RANK");
+  if (count < 0 || (count > 0 && !qubits)) return fail(h, QS_ERR_INVALID_ARG, "bad qubit list");
+  for (int j = 0; j < count; ++j) {
+    if (qubits[j] < 0 || qubits[j] >= h->n) return fail(h, QS_ERR_INVALID_ARG, "qubit out of range");
+    for (int i = 0; i < j; ++i)
+      if (qubits[i] == qubits[j]) return fail(h, QS_ERR_INVALID_ARG, "duplicate qubit");
+  }
+  if (!(t >= 0.0) || !std::isfinite(t)) return fail(h, QS_ERR_INVALID_ARG, "t must be finite and >= 0");
+  if (!(T1 > 0.0) || !(T2 > 0.0)) return fail(h, QS_ERR_INVALID_ARG, "T1 and T2 must be > 0 (inf allowed)");
+  if (T2 > 2.0 * T1) return fail(h, QS_ERR_INVALID_ARG, "T2 > 2 T1 is not a channel");
+  { const qs_status st = qs::materialize_basis(h); if (st != QS_OK) return st; }
+  const double keep = std::exp(-t / T1), c = std::exp(-t / T2), gamma = 1.0 - keep;
+  if (count == 0 || (gamma == 0.0 && c == 1.0)) return QS_OK;
+  if (h->mode == QS_DENSITY) {
+    QS_CUDA(h, qs::launch_dm_relax(h, h->state, h->n, qubits, count, gamma, keep, c));
+    return QS_OK;
+  }
+  // FIXED_RANK: the Kraus set diag(1, c), sqrt(gamma) |0><1|, diag(0, sqrt(keep - c^2)),
+  // zero operators left out, one expansion and truncation per qubit
+  std::vector<std::vector<cd>> ks;
+  ks.push_back({cd(1, 0), cd(0, 0), cd(0, 0), cd(c, 0)});
+  if (gamma > 0.0) ks.push_back({cd(0, 0), cd(std::sqrt(gamma), 0), cd(0, 0), cd(0, 0)});
+  const double d2 = keep - c * c;
+  if (d2 > 0.0) ks.push_back({cd(0, 0), cd(0, 0), cd(0, 0), cd(std::sqrt(d2), 0)});
+  for (int j = 0; j < count; ++j) {
+    const qs_status st = rank_apply_kraus(h, qubits + j, 1, ks);
+    if (st != QS_OK) return st;
+  }
+  return QS_OK;
 }
 
 qs_status qs_truncate_rank(qs_handle h, int r, int normalize) {

@@ -143,6 +143,10 @@ cudaError_t launch_apply_diag(qs_ctx* h, void* psi, int n, int members, const Ta
 cudaError_t launch_phase_flip(qs_ctx* h, void* psi, int n, int members, uint64_t index,
                               const uint64_t* per_member);
 cudaError_t launch_dm_flip(qs_ctx* h, void* rho, int n, uint64_t index);
+// T1/T2 relaxation of `count` qubits of a density matrix, two per sweep
+// (gamma = 1 - exp(-t/T1), keep = exp(-t/T1), c = exp(-t/T2)).
+cudaError_t launch_dm_relax(qs_ctx* h, void* rho, int n, const int* qubits, int count, double gamma,
+                            double keep, double c);
 
 // reductions (results land in h->small, as doubles)
 cudaError_t launch_dot(qs_ctx* h, const void* psi, const void* ref, int n, int members,

@@ -278,6 +278,57 @@ __global__ void k_dm_flip(cplx<R>* rho, int n, uint64_t w) {
   }
 }
 
+// T1/T2 relaxation (amplitude damping with gamma = 1 - keep, then dephasing
+// to a total coherence factor c) of M qubits at once on a density matrix,
+// vec index x * 2^n + y.  For one qubit q and every (x, y) with bit q clear in
+// both, the four entries of the (x_q, y_q) block become
+//   (0,0) += gamma * (1,1),   (1,1) *= keep,   (0,1), (1,0) *= c.
+// A thread owns the 4^M entries that share the other bits (local index bit
+// 2m = y-bit of qubit m, bit 2m + 1 = its x-bit) and applies the M channels
+// in registers, so M qubits cost one read and one write of rho.
+struct RelaxSet {
+  int pos[4];      // the 2M vec-bit positions, ascending (insertion order)
+  int bit[4];      // local bit j -> vec bit position (y-bit q, x-bit q + n)
+};
+
+template <typename R, int M>
+__global__ void __launch_bounds__(256) k_dm_relax(cplx<R>* rho, int n, RelaxSet rs, R gamma, R keep, R c) {
+  constexpr int L = 1 << (2 * M);
+  const uint64_t bases = 1ull << (2 * n - 2 * M);
+  uint64_t off[L];
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    uint64_t o = 0;
+#pragma unroll
+    for (int b = 0; b < 2 * M; ++b) o |= (uint64_t)((j >> b) & 1) << rs.bit[b];
+    off[j] = o;
+  }
+  for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < bases; w += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t base = w;
+#pragma unroll
+    for (int b = 0; b < 2 * M; ++b) base = insert0(base, rs.pos[b]);
+    cplx<R> a[L];
+#pragma unroll
+    for (int j = 0; j < L; ++j) a[j] = rho[base + off[j]];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const int yb = 1 << (2 * m), xb = 2 << (2 * m);
+#pragma unroll
+      for (int j = 0; j < L; ++j) {
+        if (j & (yb | xb)) continue;
+        const cplx<R> d = a[j | yb | xb];
+        a[j].x = fma(gamma, d.x, a[j].x);
+        a[j].y = fma(gamma, d.y, a[j].y);
+        a[j | yb | xb] = mk<R>(keep * d.x, keep * d.y);
+        a[j | yb] = mk<R>(c * a[j | yb].x, c * a[j | yb].y);
+        a[j | xb] = mk<R>(c * a[j | xb].x, c * a[j | xb].y);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < L; ++j) rho[base + off[j]] = a[j];
+  }
+}
+
 __global__ void k_debug_noise(uint64_t seed, uint64_t traj, uint64_t gate_id, int count,
                               uint32_t* words, double* normals) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -490,6 +541,30 @@ cudaError_t launch_phase_flip(qs_ctx* h, void* psi, int n, int members, uint64_t
   if (h->dtype == QS_C64) k_phase_flip<float><<<g, kBlock, 0, h->stream>>>((float2*)psi, n, members, index, per);
   else k_phase_flip<double><<<g, kBlock, 0, h->stream>>>((double2*)psi, n, members, index, per);
   return cudaGetLastError();
+}
+
+cudaError_t launch_dm_relax(qs_ctx* h, void* rho, int n, const int* qubits, int count, double gamma,
+                            double keep, double c) {
+  for (int i = 0; i < count; i += 2) {
+    const int M = std::min(2, count - i);
+    RelaxSet rs{};
+    for (int m = 0; m < M; ++m) { rs.bit[2 * m] = qubits[i + m]; rs.bit[2 * m + 1] = qubits[i + m] + n; }
+    for (int b = 0; b < 2 * M; ++b) rs.pos[b] = rs.bit[b];
+    std::sort(rs.pos, rs.pos + 2 * M);
+    const int g = grid_for(1ull << (2 * n - 2 * M));
+    if (h->dtype == QS_C64) {
+      auto* p = (float2*)rho;
+      if (M == 2) k_dm_relax<float, 2><<<g, kBlock, 0, h->stream>>>(p, n, rs, (float)gamma, (float)keep, (float)c);
+      else k_dm_relax<float, 1><<<g, kBlock, 0, h->stream>>>(p, n, rs, (float)gamma, (float)keep, (float)c);
+    } else {
+      auto* p = (double2*)rho;
+      if (M == 2) k_dm_relax<double, 2><<<g, kBlock, 0, h->stream>>>(p, n, rs, gamma, keep, c);
+      else k_dm_relax<double, 1><<<g, kBlock, 0, h->stream>>>(p, n, rs, gamma, keep, c);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_dm_flip(qs_ctx* h, void* rho, int n, uint64_t w) {

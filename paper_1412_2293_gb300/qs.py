@@ -57,6 +57,7 @@ _SIGS = {
     "qs_apply_noisy_gate": ([_P, _I, ct.c_int, _D, ct.c_int, ct.c_double, ct.c_uint64, ct.c_uint64], ct.c_int),
     "qs_apply_branch_gate": ([_P, _I, ct.c_int, _D, ct.c_int, ct.c_double, ct.c_int], ct.c_int),
     "qs_apply_kraus": ([_P, _I, ct.c_int, _D, ct.c_int], ct.c_int),
+    "qs_apply_relaxation": ([_P, _I, ct.c_int, ct.c_double, ct.c_double, ct.c_double], ct.c_int),
     "qs_truncate_rank": ([_P, ct.c_int, ct.c_int], ct.c_int),
     "qs_set_normalize": ([_P, ct.c_int], ct.c_int),
     "qs_get_rank": ([_P, _I], ct.c_int),
@@ -192,6 +193,11 @@ def qs_apply_branch_gate(h, targets, U, noise, e, rotated=False):
 def qs_apply_kraus(h, targets, kraus):
     e = np.concatenate([_cplx_interleaved(E) for E in kraus])
     _check(lib().qs_apply_kraus(h, _targets(targets), len(targets), _dptr(e), len(kraus)), h)
+
+
+def qs_apply_relaxation(h, qubits, t, T1, T2):
+    """T1/T2 relaxation over t of every qubit in `qubits` (T1, T2 may be math.inf)."""
+    _check(lib().qs_apply_relaxation(h, _targets(qubits), len(qubits), float(t), float(T1), float(T2)), h)
 
 
 def qs_truncate_rank(h, r, normalize=0):
