@@ -108,11 +108,16 @@ qs_status qs_set_maximally_entangled(qs_handle h);
 
 /* ------------------------------------------------------------------- gates */
 
-/* Ideal k-qubit gate U (k = 1..4) on `targets` (distinct, < n) -- Sec. 2.
+/* Ideal k-qubit gate U (k = 1..5) on `targets` (distinct, < n) -- Sec. 2.
  * DENSITY: rho <- U rho U^dagger via (U (x) U*) on bits (t, t + n), Sec. 3;
  *   one 2k-qubit sweep for k <= 2, two k-qubit sweeps (U on the row bits
- *   t + n, U* on the column bits t) for k = 3, 4.
+ *   t + n, U* on the column bits t) for k = 3..5.
  * FIXED_RANK: L <- U L (no truncation).
+ * A dense (non-diagonal) U with k >= 3 on a complex64 state of at least k + 7
+ * qubits (per member; for DENSITY the 2n-qubit vector) runs on the tcgen05
+ * tensor cores as one GEMM over all groups and members: operands split into
+ * tf32 hi + lo parts, hi*hi + lo*hi + hi*lo accumulated in FP32 (relative
+ * error about 1e-6 of sum |U_ij||psi_j|); see qs_set_tensor_cores.
  * Errors: INVALID_ARG for bad targets / k / NULL pointers. */
 qs_status qs_apply_gate(qs_handle h, const int* targets, int k, const double* U);
 
@@ -169,6 +174,11 @@ qs_status qs_apply_kraus(qs_handle h, const int* targets, int k, const double* E
  * Errors: INVALID_ARG for count < 0, a qubit out of range or repeated,
  * t < 0 or not finite, T1 <= 0, T2 <= 0, or T2 > 2 T1 (not a channel). */
 qs_status qs_apply_relaxation(qs_handle h, const int* qubits, int count, double t, double T1, double T2);
+
+/* on = 0 sends complex64 dense blocks with k >= 3 to the CUDA-core sweep
+ * (FP32 complex multiply-adds) instead of the tensor cores; on = 1 (the
+ * default) restores the tensor-core path.  Errors: INVALID_ARG for NULL. */
+qs_status qs_set_tensor_cores(qs_handle h, int on);
 
 /* FIXED_RANK: truncate the current factor to rank r (<= handle rank) by the
  * Gram-matrix eigendecomposition (Sec. 3.2).  normalize = 0 keeps the trace

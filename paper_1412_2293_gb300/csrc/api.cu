@@ -185,6 +185,10 @@ qs_status apply_uniform(qs_handle h, void* psi, int n, int members, const int* t
   }
   qs_status st = upload_mat(h, U);
   if (st != QS_OK) return st;
+  if (k >= 3 && h->dtype == QS_C64 && h->tensor_cores && qs::dense_tc_applicable(n, k)) {
+    QS_CUDA(h, qs::launch_dense_tc(h, psi, n, members, targets, k, static_cast<const float*>(h->mats)));
+    return QS_OK;
+  }
   bool real = true;
   for (const auto& v : U) if (v.imag() != 0.0) real = false;
   QS_CUDA(h, qs::launch_apply_kq(h, psi, n, members, tg, h->mats, false, real));
@@ -254,6 +258,7 @@ qs_status read_results(qs_ctx* h, double* out, int count) {
   int status[4] = {0, 0, 0, 0};
   QS_CUDA(h, cudaMemcpy(status, h->dstatus, sizeof(status), cudaMemcpyDeviceToHost));
   if (status[2] != 0) return fail(h, QS_ERR_TIMEOUT, "a fused pass timed out waiting for a tile copy");
+  if (status[3] != 0) return fail(h, QS_ERR_TIMEOUT, "a tensor-core block timed out waiting for its MMAs");
   if (h->mode == QS_FIXED_RANK && status[1] != 0)
     return fail(h, QS_ERR_CUDA, status[1] == 1 ? "eigensolver did not converge" : "tie-cluster basis incomplete");
   return QS_OK;
@@ -329,7 +334,7 @@ qs_status qs_create(int n, int batch, int rank, qs_mode mode, qs_dtype dtype, vo
   if (mode == QS_FIXED_RANK) partials = std::max<size_t>(partials, ((N + 63) / 64) * 2 * qs::kMaxGramDim * qs::kMaxGramDim);
   h->partials_cap = partials;
   if (cudaMalloc((void**)&h->partials, partials * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return bail(QS_ERR_OUT_OF_MEMORY); }
-  h->mats_cap = std::max<size_t>((size_t)batch * 2 * 16, 2 * 256) * (h->esize / 2);
+  h->mats_cap = std::max<size_t>((size_t)batch * 2 * 16, 2 * 1024) * (h->esize / 2);
   if (cudaMalloc(&h->mats, h->mats_cap) != cudaSuccess) { cudaGetLastError(); return bail(QS_ERR_OUT_OF_MEMORY); }
   h->small_cap = kSmallOut + std::max<size_t>((size_t)batch, 64);
   if (cudaMalloc((void**)&h->small, h->small_cap * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return bail(QS_ERR_OUT_OF_MEMORY); }
@@ -430,7 +435,7 @@ qs_status qs_set_basis_states(qs_handle h, const uint64_t* xs) {
 qs_status qs_apply_gate(qs_handle h, const int* targets, int k, const double* U) {
   if (!h) return QS_ERR_INVALID_ARG;
   { const qs_status st = qs::materialize_basis(h); if (st != QS_OK) return st; }
-  if (k < 1 || k > qs::kMaxK) return fail(h, QS_ERR_INVALID_ARG, "k must be 1..4");
+  if (k < 1 || k > qs::kMaxK) return fail(h, QS_ERR_INVALID_ARG, "k must be 1..5");
   if (!U) return fail(h, QS_ERR_INVALID_ARG, "U is NULL");
   std::string why;
   if (!valid_targets(h, targets, k, &why)) return fail(h, QS_ERR_INVALID_ARG, why);
@@ -581,6 +586,12 @@ qs_status qs_truncate_rank(qs_handle h, int r, int normalize) {
   QS_CUDA(h, cudaMemcpyAsync(h->work, h->state, (size_t)M * (1ull << h->n) * h->esize,
                              cudaMemcpyDeviceToDevice, h->stream));
   return rank_truncate_from_work(h, M, r, normalize);
+}
+
+qs_status qs_set_tensor_cores(qs_handle h, int on) {
+  if (!h) return QS_ERR_INVALID_ARG;
+  h->tensor_cores = on != 0;
+  return QS_OK;
 }
 
 qs_status qs_set_normalize(qs_handle h, int normalize) {

@@ -33,7 +33,7 @@ template <typename C> __host__ __device__ __forceinline__ C cfma(C m, C b, C a) 
 template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
 
 // ----------------------------------------------------------- small structs
-constexpr int kMaxK = 4;                 // dense gates up to 4 qubits (16 x 16)
+constexpr int kMaxK = 5;                 // dense gates up to 5 qubits (32 x 32)
 constexpr int kMaxGramDim = 32;          // K * m of a fixed-rank channel
 constexpr int kMaxRank = 16;             // largest truncation rank
 
@@ -111,6 +111,7 @@ struct qs_ctx {
   // stored fidelity reference (2^n complex in the handle's dtype)
   void* ref = nullptr;
   bool has_ref = false;
+  bool tensor_cores = true;              // complex64 dense blocks with k >= 3 on tcgen05
 
   // STATEVEC start state not yet written: 1 = every member |pending_x>,
   // 2 = member b |m_basis[b]>.  Written by the first consumer (a fused first
@@ -143,6 +144,12 @@ cudaError_t launch_apply_diag(qs_ctx* h, void* psi, int n, int members, const Ta
 cudaError_t launch_phase_flip(qs_ctx* h, void* psi, int n, int members, uint64_t index,
                               const uint64_t* per_member);
 cudaError_t launch_dm_flip(qs_ctx* h, void* rho, int n, uint64_t index);
+// Dense k-qubit block (k = 3..5) on complex64 members with tcgen05 tensor
+// cores (3xTF32 split, FP32 accumulation); U_dev = D x D interleaved floats.
+// cudaErrorNotSupported unless dense_tc_applicable(n, k) and the handle is complex64.
+bool dense_tc_applicable(int n, int k);
+cudaError_t launch_dense_tc(qs_ctx* h, void* psi, int n, int members, const int* targets, int k,
+                            const float* U_dev);
 // T1/T2 relaxation of `count` qubits of a density matrix, two per sweep
 // (gamma = 1 - exp(-t/T1), keep = exp(-t/T1), c = exp(-t/T2)).
 cudaError_t launch_dm_relax(qs_ctx* h, void* rho, int n, const int* qubits, int count, double gamma,

@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kBlock) k_apply_1q(cplx<R>* __restrict__ psi, 
   }
 }
 
-// Dense k-qubit gate (k <= 4) on groups of 2^k amplitudes.  REAL: the
+// Dense k-qubit gate (k <= 5) on groups of 2^k amplitudes.  REAL: the
 // (uniform) matrix has no imaginary part, so each entry costs two multiply-adds.
 template <typename R, int K, bool REAL>
 __global__ void __launch_bounds__(kBlock) k_apply_kq(cplx<R>* __restrict__ psi, int n,
@@ -353,6 +353,7 @@ cudaError_t apply_kq_dispatch(qs_ctx* h, void* psi, int n, int members, const Ta
     case 2: k_apply_kq<R, 2, REAL><<<g, kBlock, 0, h->stream>>>(p, n, ng, tg, m, per_member); break;
     case 3: k_apply_kq<R, 3, REAL><<<g, kBlock, 0, h->stream>>>(p, n, ng, tg, m, per_member); break;
     case 4: k_apply_kq<R, 4, REAL><<<g, kBlock, 0, h->stream>>>(p, n, ng, tg, m, per_member); break;
+    case 5: k_apply_kq<R, 5, REAL><<<g, kBlock, 0, h->stream>>>(p, n, ng, tg, m, per_member); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

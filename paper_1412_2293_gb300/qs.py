@@ -60,6 +60,7 @@ _SIGS = {
     "qs_apply_relaxation": ([_P, _I, ct.c_int, ct.c_double, ct.c_double, ct.c_double], ct.c_int),
     "qs_truncate_rank": ([_P, ct.c_int, ct.c_int], ct.c_int),
     "qs_set_normalize": ([_P, ct.c_int], ct.c_int),
+    "qs_set_tensor_cores": ([_P, ct.c_int], ct.c_int),
     "qs_get_rank": ([_P, _I], ct.c_int),
     "qs_fidelity": ([_P, _D, ct.c_uint64, _D], ct.c_int),
     "qs_set_reference": ([_P, _D], ct.c_int),
@@ -202,6 +203,10 @@ def qs_apply_relaxation(h, qubits, t, T1, T2):
 
 def qs_truncate_rank(h, r, normalize=0):
     _check(lib().qs_truncate_rank(h, int(r), int(normalize)), h)
+
+
+def qs_set_tensor_cores(h, on=True):
+    _check(lib().qs_set_tensor_cores(h, 1 if on else 0), h)
 
 
 def qs_set_normalize(h, normalize):
