@@ -361,6 +361,41 @@ def extra_rows(h, n, T, esize, stream, peaks):
                             "achieved_GBps": round(gbs, 1), "frac_of_measured_hbm": round(gbs / peaks["hbm_gbs"], 4),
                             "targets": targets}
 
+    # f1: dense k-qubit blocks (k = 3..5) over the whole batch, complex64: the tcgen05 path
+    # (split-tf32 GEMM) against the CUDA-core sweep; the state (8 GiB) is larger than L2
+    rng = np.random.default_rng(inputs.DEFAULT_SEED)
+    f1 = {}
+    tf32_peak = peaks["bf16_tflops"] * 1.1 / 2.25          # nominal tf32 / bf16 dense ratio
+    for k, targets in ((3, (2, 9, 15)), (4, (1, 6, 12, 18)), (5, (3, 9, 14, 17, 19))):
+        d = 1 << k
+        U, _ = np.linalg.qr(rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d)))
+        row = {}
+        for tc in (True, False):
+            qs.qs_set_tensor_cores(h, tc)
+            qs.qs_apply_gate(h, targets, U)
+            e0, e1 = ev(), ev()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(3):
+                qs.qs_apply_gate(h, targets, U)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 3
+            gbs = 2 * T * (1 << n) * esize / (ms / 1e3) / 1e9
+            row["tensor_cores" if tc else "cuda_cores"] = {
+                "ms": round(ms, 3), "achieved_GBps": round(gbs, 1),
+                "frac_of_measured_hbm": round(gbs / peaks["hbm_gbs"], 4)}
+        flops = 3 * 8 * d * T * (1 << n)      # three tf32 products of (groups x 2d) by (2d x 2d)
+        tcr = row["tensor_cores"]
+        tcr["tf32_TFLOPs"] = round(flops / (tcr["ms"] / 1e3) / 1e12, 1)
+        tcr["frac_of_tf32_peak"] = round(tcr["tf32_TFLOPs"] / tf32_peak, 4)
+        row["targets"] = targets
+        f1[f"k{k}"] = row
+    qs.qs_set_tensor_cores(h, True)
+    out["f1_dense_blocks"] = {"kernel": "k_dense_tc", "state_bytes": T * (1 << n) * esize, "members": T, "qubits": n,
+                              "tf32_peak_TFLOPs": round(tf32_peak, 1),
+                              "tf32_peak_basis": "measured bf16 dense x 1.1/2.25 (nominal tf32/bf16)", **f1}
+
     # plain FP64 one trajectory per launch sequence vs batched complex64 (Grover n = 10)
     W1 = inputs.WORKLOADS["mc_grover_n10_c128"]
     ops1, x1 = W1.ops(), W1.initial_basis()
@@ -765,6 +800,54 @@ def run_channels(args, rank, world, local_rank):
     return out
 
 
+# ------------------------------------------------------------------ single-kernel runs
+MICRO = {
+    # name: (what, qubits, members or None, k, targets)
+    "dense_k5": ("dense", 20, 128, 5, (3, 9, 14, 17, 19)),
+    "dense_k3": ("dense", 20, 128, 3, (2, 9, 15)),
+    "relax_dm_n13": ("relax", 13, None, 0, ()),
+}
+
+
+def run_micro(args):
+    """One kernel on its own, for a profiler: --warmup + --steps launches of a
+    complex64 dense block (1 GiB batch) or of the density-matrix relaxation
+    (13 qubits, 512 MiB); prints the mean time of the timed launches."""
+    import numpy as np
+    import torch
+
+    from paper_1412_2293_gb300 import build, inputs, qs
+    build.build()
+    what, n, members, k, targets = MICRO[args.micro]
+    stream = torch.cuda.current_stream()
+    if what == "dense":
+        h = qs.qs_create(n, members, 0, qs.QS_STATEVEC, qs.QS_C64, stream)
+        qs.qs_set_basis_state(h, 0)
+        qs.qs_apply_gate(h, (0,), np.array([[1, 1], [1, -1]]) / np.sqrt(2.0))
+        rng = np.random.default_rng(inputs.DEFAULT_SEED)
+        U, _ = np.linalg.qr(rng.normal(size=(1 << k, 1 << k)) + 1j * rng.normal(size=(1 << k, 1 << k)))
+        launch = lambda: qs.qs_apply_gate(h, targets, U)
+        nbytes = 2 * members * (1 << n) * 8
+    else:
+        h = qs.qs_create(n, 1, 0, qs.QS_DENSITY, qs.QS_C64, stream)
+        qs.qs_set_basis_state(h, 0)
+        launch = lambda: qs.qs_apply_relaxation(h, [0, 7], 0.05, 3.0, 2.0)
+        nbytes = 2 * (1 << (2 * n)) * 8
+    for _ in range(args.warmup):
+        launch()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        launch()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    qs.qs_destroy(h)
+    return {"micro": args.micro, "ms_per_launch": round(ms, 4), "GBps": round(nbytes / (ms / 1e3) / 1e9, 1),
+            "launches": args.warmup + args.steps}
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, rank, world):
     """The oracle on the host cores, each step a slice of one trajectory's gates."""
@@ -828,7 +911,12 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the bounded measurements of the other rows")
     ap.add_argument("--kernel-config", default=None,
                     help="low,high pass configuration indices (qs_plan_set_config) instead of autotuning")
+    ap.add_argument("--micro", choices=sorted(MICRO), default=None,
+                    help="time one kernel on its own (for a profiler) instead of the bench step")
     args = ap.parse_args()
+    if args.micro:
+        print(json.dumps(run_micro(args)), flush=True)
+        return
     if args.warmup < 3:
         args.warmup = 3
     rank, world, local_rank = env_rank()

@@ -22,7 +22,9 @@
 // tile's row m from HBM (lanes read consecutive groups), splits it into the
 // hi/lo operand tiles in shared memory, thread 0 issues the MMAs, and after
 // their commit every warp reads its 32 TMEM lanes (rows) back and stores the
-// row to HBM.  Persistent CTAs stride over the tiles.  Every wait on the MMA
+// row to HBM.  Persistent CTAs stride over the tiles; the loads of a CTA's
+// next tile are issued right after the MMAs, so they overlap the MMAs and the
+// epilogue.  Every wait on the MMA
 // commit is bounded: on expiry the kernel records the fact in status and
 // leaves after freeing its tensor memory.
 #include <cuda_runtime.h>
@@ -186,17 +188,22 @@ __global__ void __launch_bounds__(kTcThreads) k_dense_tc(TcArgs args) {
 #pragma unroll
   for (int b = 0; b < kTcFree; ++b) off_m |= (uint64_t)((tid >> b) & 1) << args.free_pos[b];
 
+  auto tile_base = [&](uint64_t t) {
+#pragma unroll
+    for (int b = 0; b < K + kTcFree; ++b) t = insert0(t, args.pos[b]);
+    return t | off_m;
+  };
   uint32_t phase = 0;
   bool ok = true;
-  for (uint64_t t = blockIdx.x; t < args.tiles; t += gridDim.x) {
-    uint64_t base = t;
-#pragma unroll
-    for (int b = 0; b < K + kTcFree; ++b) base = insert0(base, args.pos[b]);
-    base |= off_m;
-    float2 x[D];
+  uint64_t t = blockIdx.x;
+  uint64_t base = tile_base(t);
+  float2 x[D];
+  if (t < args.tiles) {
 #pragma unroll
     for (int j = 0; j < D; ++j) x[j] = args.psi[base + args.off_j[j]];
-    // row m = tid of A: columns 2j, 2j + 1, 2j + 2, 2j + 3 for j even are one 16-byte chunk
+  }
+  while (t < args.tiles) {
+    // row m = tid of A: columns 2j .. 2j + 3 for j even are one 16-byte chunk
 #pragma unroll
     for (int j = 0; j < D; j += 2) {
       const float4 v = make_float4(x[j].x, x[j].y, x[j + 1].x, x[j + 1].y);
@@ -225,6 +232,13 @@ __global__ void __launch_bounds__(kTcThreads) k_dense_tc(TcArgs args) {
       }
       mma_commit(mbar_a);
     }
+    // the next tile's loads are in flight during the MMAs and this tile's epilogue
+    const uint64_t tn = t + gridDim.x;
+    const uint64_t base_n = tile_base(tn);
+    if (tn < args.tiles) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) x[j] = args.psi[base_n + args.off_j[j]];
+    }
     const bool got = mbar_wait(mbar_a, phase);
     if (__syncthreads_or(!got)) { ok = false; break; }   // every thread leaves together
     phase ^= 1;
@@ -236,6 +250,8 @@ __global__ void __launch_bounds__(kTcThreads) k_dense_tc(TcArgs args) {
     for (int i = 0; i < D; ++i) args.psi[base + args.off_j[i]] = make_float2(d[2 * i], d[2 * i + 1]);
     fence_before();
     __syncthreads();
+    t = tn;
+    base = base_n;
   }
   if (!ok) {
     if (tid == 0) atomicExch(args.status, 1);
@@ -262,11 +278,27 @@ cudaError_t launch_k(const TcArgs& a, cudaStream_t s) {
   if (grid == 0) {
     cudaError_t e = cudaFuncSetAttribute(k_dense_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_tc<K>, kTcThreads, smem);
+    e = cudaFuncSetAttribute(k_dense_tc<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
+    // resident CTAs per SM from the kernel's own needs (shared memory with the
+    // per-block reserve, registers at warp granularity of 256, threads, and
+    // tensor-memory columns so that no CTA waits in tcgen05.alloc)
+    cudaFuncAttributes fa{};
+    e = cudaFuncGetAttributes(&fa, k_dense_tc<K>);
+    if (e != cudaSuccess) return e;
+    int dev = 0, smem_sm = 0, reserve = 0, regs_sm = 0, threads_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserve, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + reserve);
+    const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;
+    const int by_regs = regs_sm / (warp_regs * (kTcThreads / 32));
+    const int by_threads = threads_sm / kTcThreads;
     constexpr int cols = (2 << K) < 32 ? 32 : (2 << K);
-    per_sm = std::max(1, std::min(per_sm, 512 / cols));   // every resident CTA gets its tensor memory
+    const int per_sm = std::max(1, std::min({by_smem, by_regs, by_threads, 512 / cols}));
     grid = per_sm * num_sms();
     grid_cache.store(grid);
   }
