@@ -22,8 +22,9 @@
 // tile's row m from HBM (lanes read consecutive groups), splits it into the
 // hi/lo operand tiles in shared memory, thread 0 issues the MMAs, and after
 // their commit every warp reads its 32 TMEM lanes (rows) back and stores the
-// row to HBM.  Persistent CTAs stride over the tiles; the loads of a CTA's
-// next tile are issued right after the MMAs, so they overlap the MMAs and the
+// row to HBM.  Persistent CTAs stride over the tiles; a CTA issues its next
+// tile's loads into a second register set before writing the current tile
+// (k <= 4) or right after the MMAs (k = 5), so they overlap the MMAs and the
 // epilogue.  Every wait on the MMA
 // commit is bounded: on expiry the kernel records the fact in status and
 // leaves after freeing its tensor memory.
@@ -46,7 +47,7 @@ constexpr uint32_t kSpinLimit = 1u << 24;
 struct TcArgs {
   float2* psi;
   uint64_t tiles;                       // members * 2^(n - k - 7)
-  uint64_t off_j[32];                   // index offset of local index j (targets in caller order)
+  uint32_t off_j[32];                   // index offset of local index j (targets in caller order)
   int pos[12];                          // ascending positions of the tile's k + 7 bits
   int free_pos[kTcFree];                // the 7 free bits, ascending (group index m)
   const float* U;                       // D x D interleaved complex, row-major
@@ -197,12 +198,28 @@ __global__ void __launch_bounds__(kTcThreads) k_dense_tc(TcArgs args) {
   bool ok = true;
   uint64_t t = blockIdx.x;
   uint64_t base = tile_base(t);
-  float2 x[D];
+  // two register sets in turn (k <= 4): while one tile is written, multiplied
+  // and stored, the next tile's loads land in the other
+  float2 xa[D], xb[D];
   if (t < args.tiles) {
+    const float2* p = args.psi + base;
 #pragma unroll
-    for (int j = 0; j < D; ++j) x[j] = args.psi[base + args.off_j[j]];
+    for (int j = 0; j < D; ++j) xa[j] = p[args.off_j[j]];
   }
-  while (t < args.tiles) {
+  auto process = [&](float2 (&x)[D], float2 (&xn)[D]) -> bool {
+    if (t >= args.tiles) return false;
+    const uint64_t tn = t + gridDim.x;
+    const uint64_t base_n = tile_base(tn);
+    auto prefetch = [&]() {
+      if (tn < args.tiles) {
+        const float2* p = args.psi + base_n;
+#pragma unroll
+        for (int j = 0; j < D; ++j) xn[j] = p[args.off_j[j]];
+      }
+    };
+    // k <= 4: the next loads go out before this tile's operand writes; k = 5
+    // (twice the registers per set) issues them after the MMAs
+    if constexpr (K <= 4) prefetch();
     // row m = tid of A: columns 2j .. 2j + 3 for j even are one 16-byte chunk
 #pragma unroll
     for (int j = 0; j < D; j += 2) {
@@ -232,26 +249,32 @@ __global__ void __launch_bounds__(kTcThreads) k_dense_tc(TcArgs args) {
       }
       mma_commit(mbar_a);
     }
-    // the next tile's loads are in flight during the MMAs and this tile's epilogue
-    const uint64_t tn = t + gridDim.x;
-    const uint64_t base_n = tile_base(tn);
-    if (tn < args.tiles) {
-#pragma unroll
-      for (int j = 0; j < D; ++j) x[j] = args.psi[base_n + args.off_j[j]];
-    }
+    if constexpr (K > 4) prefetch();
     const bool got = mbar_wait(mbar_a, phase);
-    if (__syncthreads_or(!got)) { ok = false; break; }   // every thread leaves together
+    if (__syncthreads_or(!got)) { ok = false; return false; }   // every thread leaves together
     phase ^= 1;
     fence_after();
-    float d[KD];
-    tmem_load<KD>(tmem + ((uint32_t)(warp * 32) << 16), d);
-    tmem_wait_ld();
+    // read back and store in chunks of at most 32 columns (16 amplitudes)
+    constexpr int kChunk = KD < 32 ? KD : 32;
+    float2* q = args.psi + base;
 #pragma unroll
-    for (int i = 0; i < D; ++i) args.psi[base + args.off_j[i]] = make_float2(d[2 * i], d[2 * i + 1]);
+    for (int c0 = 0; c0 < KD; c0 += kChunk) {
+      float d[kChunk];
+      tmem_load<kChunk>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, d);
+      tmem_wait_ld();
+#pragma unroll
+      for (int i = 0; i < kChunk / 2; ++i) q[args.off_j[c0 / 2 + i]] = make_float2(d[2 * i], d[2 * i + 1]);
+    }
     fence_before();
     __syncthreads();
     t = tn;
     base = base_n;
+    return true;
+  };
+  // k = 5 keeps one set: its late prefetch reuses the registers of the tile
+  // just written to shared memory
+  float2 (&xs)[D] = K <= 4 ? xb : xa;
+  while (process(xa, xs) && process(xs, xa)) {
   }
   if (!ok) {
     if (tid == 0) atomicExch(args.status, 1);
@@ -309,7 +332,7 @@ cudaError_t launch_k(const TcArgs& a, cudaStream_t s) {
 
 }  // namespace
 
-bool dense_tc_applicable(int n, int k) { return k >= 3 && k <= 5 && n - k >= kTcFree; }
+bool dense_tc_applicable(int n, int k) { return k >= 3 && k <= 5 && n - k >= kTcFree && n <= 32; }
 
 cudaError_t launch_dense_tc(qs_ctx* h, void* psi, int n, int members, const int* targets, int k,
                             const float* U_dev) {
@@ -322,8 +345,8 @@ cudaError_t launch_dense_tc(qs_ctx* h, void* psi, int n, int members, const int*
   uint32_t tmask = 0;
   for (int i = 0; i < k; ++i) tmask |= 1u << targets[i];
   for (int j = 0; j < (1 << k); ++j) {
-    uint64_t o = 0;
-    for (int i = 0; i < k; ++i) o |= (uint64_t)((j >> i) & 1) << targets[i];
+    uint32_t o = 0;
+    for (int i = 0; i < k; ++i) o |= (uint32_t)((j >> i) & 1) << targets[i];
     a.off_j[j] = o;
   }
   int nf = 0;
