@@ -681,6 +681,7 @@ def extra_rows(h, n, T, esize, stream, peaks):
         "shor9_fidelity": shor9, "codes_ms": round(ms_codes, 1),
         "fig8_logical_z_T1_3_T2_2": fig8, "fig9_qft5_t0.1": fig9, "fig9_ms": round(ms_fig9, 1)}
 
+    out["a11_serving_large_n"] = serving_large_n_row()
     out["a11_serving"] = serving_row()
     cap = out["a11_serving"]["jobs_per_s"]
     out["a11_serving_rate_sweep"] = {f"{m}x_capacity": serving_row(num_jobs=60, rate_per_s=m * cap, seed_offset=1)
@@ -713,6 +714,34 @@ def serving_row(num_jobs=100, rate_per_s=200.0, workers=4, seed_offset=0):
             "jobs_per_s": round(stats["jobs_per_s"], 2), "latency_p50_s": round(stats["latency_p50_s"], 4),
             "latency_p99_s": round(stats["latency_p99_s"], 4),
             "stream": "n 12..20, MC 2^6..2^10 trajectories c64, fixed rank r 1..8 c128, Grover iterations capped at 16"}
+
+
+def serving_large_n_row():
+    """The upper end of the serving workload's size range: Monte Carlo QFT
+    jobs at n = 24, 26, 28 (2 GiB complex64 per trajectory at n = 28, so the
+    128 trajectories of the largest job run in waves under the HBM budget),
+    a Grover job at n = 24 (16 iterations) and a fixed-rank QFT at n = 24,
+    arriving together."""
+    from paper_1412_2293_gb300 import inputs
+    from paper_1412_2293_gb300.server import GpuExecutor, Server, run_stream
+    specs = [("qft", 24, "statevec", 256, 0), ("qft", 26, "statevec", 128, 0), ("qft", 28, "statevec", 128, 0),
+             ("grover", 24, "statevec", 64, 0), ("qft", 24, "fixed_rank", 1, 4)]
+    jobs = []
+    for i, (circ, n, mode, traj, rank) in enumerate(specs):
+        iters = min(inputs.grover_iterations(n), 16) if circ == "grover" else 0
+        jobs.append(inputs.Job(i, 0.001 * i, circ, n, mode, traj, rank, 1e-3, inputs.DEFAULT_SEED + i, iters))
+    srv = Server(GpuExecutor(workers=2), max_members=1024)
+    try:
+        res, stats = run_stream(jobs, srv, time_scale=1.0, timeout=600)
+        budget = srv.sched.budget
+    finally:
+        srv.close()
+    per_job = {f"{j.circuit}_n{j.n}_{'mc' if j.mode == 'statevec' else 'rank'}": {
+        "trajectories": j.trajectories, "rank": j.rank, "latency_s": round(res[j.job_id].latency, 3),
+        "mean_fidelity": float(sum(res[j.job_id].fidelities) / len(res[j.job_id].fidelities))} for j in jobs}
+    return {"jobs": per_job, "span_s": round(stats["span_s"], 3), "circuits": stats["circuits"],
+            "hbm_budget_GiB": round(budget / 2 ** 30, 1), "peak_budget_used_GiB": round(stats["peak_budget_used"] / 2 ** 30, 1),
+            "largest_state_GiB_per_trajectory": 2 ** 28 * 8 / 2 ** 30}
 
 
 # ------------------------------------------------------------------ density / fixed rank

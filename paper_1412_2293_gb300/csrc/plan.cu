@@ -461,6 +461,8 @@ struct qs_plan_s {
   bool graph_member_marked[6] = {false, false, false, false, false, false};
   bool graph_timing[6] = {false, false, false, false, false, false};
   double* d_fid = nullptr;        // fused-fidelity partials [member][tile] complex
+  void* d_params = nullptr;       // per-member gate parameters of the running pass (shared by the passes)
+  void* d_alpha = nullptr;        // out factors of the running pass (shared by the passes)
   std::vector<DmBlock> dm_blocks;
   int colb = 3;
   int low_cfg = 0;                // kernel configuration of each window geometry (see launch_pass_kernel)
@@ -1304,6 +1306,9 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
     p->dm_blocks.push_back(b);
   }
   size_t fid_tiles = 0;
+  // one parameter buffer and one out-factor table serve every pass: a pass's
+  // precompute runs on the same stream right before the pass itself
+  size_t params_bytes = 16, alpha_bytes = 0;
   for (auto& P : p->passes) {
     if (st != QS_OK) break;
     st = upload(p, &P.d_ops, P.ops);
@@ -1311,16 +1316,22 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
     if (st == QS_OK) st = upload(p, &P.d_prods, P.prods);
     if (st == QS_OK) st = upload(p, &P.d_contribs, P.contribs);
     if (st == QS_OK) {
-      const size_t bytes = (size_t)P.stride * h->batch * (h->esize / 2);
-      if (cudaMalloc(&P.d_params, std::max<size_t>(bytes, 16)) != cudaSuccess) st = pfail(p, QS_ERR_OUT_OF_MEMORY, "plan params");
+      params_bytes = std::max(params_bytes, (size_t)P.stride * h->batch * (h->esize / 2));
       // out factors of every tile: members x 2^(n-10) tile values x 11 complex
-      const size_t alpha_bytes = (((size_t)h->batch * 11) << (h->n - kWin)) * h->esize;
-      if (st == QS_OK && P.out_start[11] > 0 && cudaMalloc(&P.d_alpha, alpha_bytes) != cudaSuccess)
-        st = pfail(p, QS_ERR_OUT_OF_MEMORY, "plan out factors");
+      if (P.out_start[11] > 0) alpha_bytes = (((size_t)h->batch * 11) << (h->n - kWin)) * h->esize;
     }
     if (st == QS_OK && P.high) st = make_tmap(p, &P, P.colb, &P.tmap);
     if (st == QS_OK && P.high && h->esize == 8) st = make_tmap(p, &P, 2, &P.tmap4);
     fid_tiles = (size_t)1 << (h->n - kWin);             // the most tiles any configuration has
+  }
+  if (st == QS_OK && !p->passes.empty()) {
+    if (cudaMalloc(&p->d_params, params_bytes) != cudaSuccess) st = pfail(p, QS_ERR_OUT_OF_MEMORY, "plan params");
+    if (st == QS_OK && alpha_bytes && cudaMalloc(&p->d_alpha, alpha_bytes) != cudaSuccess)
+      st = pfail(p, QS_ERR_OUT_OF_MEMORY, "plan out factors");
+    for (auto& P : p->passes) {
+      P.d_params = p->d_params;
+      P.d_alpha = P.out_start[11] > 0 ? p->d_alpha : nullptr;
+    }
   }
   if (st == QS_OK && !p->passes.empty() &&
       cudaMalloc((void**)&p->d_fid, 2 * fid_tiles * h->batch * sizeof(double)) != cudaSuccess)
@@ -1523,9 +1534,11 @@ qs_status qs_plan_destroy(qs_plan p) {
   if (p->h) cudaStreamSynchronize(p->h->stream);
   for (auto& x : p->exec) if (x) cudaGraphExecDestroy(x);
   for (auto& P : p->passes) {
-    void* ptrs[] = {P.d_ops, P.d_outs, P.d_prods, P.d_contribs, P.d_params, P.d_alpha};
+    void* ptrs[] = {P.d_ops, P.d_outs, P.d_prods, P.d_contribs};
     for (void* x : ptrs) if (x) cudaFree(x);
   }
+  if (p->d_params) cudaFree(p->d_params);
+  if (p->d_alpha) cudaFree(p->d_alpha);
   if (p->d_gates) cudaFree(p->d_gates);
   if (p->d_fid) cudaFree(p->d_fid);
   for (auto& b : p->dm_blocks) {

@@ -81,9 +81,10 @@ def mc_key(job: inputs.Job) -> Tuple:
 
 def member_bytes(n: int) -> int:
     """Device bytes of one complex64 trajectory (upper bound): its amplitudes,
-    reduction partials (1/64 of the state) and at most 512 KiB of per-member
-    gate parameters and phase tables of the fused passes."""
-    return (1 << n) * C64_BYTES + (1 << n) // 64 + (1 << 19)
+    reduction partials (1/64 of the state), the out-of-window factors of the
+    fused passes (11 complex per 1024 amplitudes) and at most 512 KiB of
+    per-member gate parameters and phase tables."""
+    return (1 << n) * C64_BYTES + (1 << n) // 64 + (11 * C64_BYTES << max(n - 10, 0)) + (1 << 19)
 
 
 def rank_bytes(n: int, r: int) -> int:

@@ -177,3 +177,11 @@ def test_executor_error_surfaces():
             srv.drain(timeout=10)
     finally:
         srv.close()
+
+
+def test_member_bytes_cover_state_partials_and_out_factors():
+    from paper_1412_2293_gb300.server import member_bytes
+    for n in (12, 20, 28):
+        state = 8 << n
+        # amplitudes, fused-fidelity partials (1/64) and 11 complex64 out factors per 1024 amplitudes
+        assert member_bytes(n) >= state + (1 << n) // 64 + 88 * (1 << (n - 10))
