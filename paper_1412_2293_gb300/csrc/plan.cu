@@ -533,6 +533,7 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
   P->high = false;
   if (q >= 10) {
     if (n < kWin + colb) return false;               // a high tile needs 2^colb columns
+    if (n > 32) return false;                        // its member-local offsets are 32-bit
     P->high = true;
   }
   for (int l = 0; l < kWin; ++l) P->win[l] = P->high ? n - kWin + l : l;
