@@ -559,6 +559,10 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
   const uint64_t per = (A.tiles + gridDim.x - 1) / gridDim.x;
   const uint64_t first = (uint64_t)blockIdx.x * per;
   const uint64_t last = first + per < A.tiles ? first + per : A.tiles;
+  // a tile index within a member splits into the column block among the
+  // bits below the window (cshift bits) and the value of the bits above it
+  const int cshift = A.win[0] - COLB;
+  const uint64_t cmask = (1ull << cshift) - 1;
 
   if (threadIdx.x == 0) {
     mbar_init(&bars[0], 1);
@@ -570,11 +574,12 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
     const uint64_t member = t >> A.tile_shift;
     const uint64_t tl = t & ((1ull << A.tile_shift) - 1);
     mbar_expect_tx(&bars[which], tile_bytes);
-    const int x = (int)(tl * S::COLS) * elem_cols;
+    const int x = (int)((tl & cmask) * S::COLS) * elem_cols;
+    const uint64_t row0 = ((member << (A.tile_shift - cshift)) | (tl >> cshift)) * 1024;
     C* dst = smbase + which * S::BUF;
 #pragma unroll
     for (int b = 0; b < 4; ++b)
-      tma_g2s_2d(dst + b * 256 * S::COLS, &tmap, x, (int)(member * 1024 + b * 256), &bars[which]);
+      tma_g2s_2d(dst + b * 256 * S::COLS, &tmap, x, (int)(row0 + b * 256), &bars[which]);
   };
   if (!A.synth && threadIdx.x == 0 && first < last) issue(first, 0);
   int in_flight = (!A.synth && first < last) ? 1 : 0;
@@ -604,13 +609,17 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
     };
     const uint64_t member = t >> A.tile_shift;
     const uint64_t tl = t & ((1ull << A.tile_shift) - 1);
-    const uint32_t tbits = (uint32_t)(tl << COLB);      // the other bits are COLB .. n-11
+    // member-local offset of the tile (bits outside the window and the
+    // columns), and the same bits packed below each other (the out-factor
+    // table's index: bits below the window, then the bits above it)
+    const uint32_t tbits = (uint32_t)(((tl >> cshift) << (A.win[0] + kWin)) | ((tl & cmask) << COLB));
+    const uint32_t obits = (uint32_t)(((tl >> cshift) << A.win[0]) | ((tl & cmask) << COLB));
     const R* P = params + member * (uint64_t)A.param_stride;
     C* sm = smbase + cur * S::BUF;
     // this tile's out factors (read at the end of the tile): into L1 now
     if (A.alpha_tab) {
       const char* at = reinterpret_cast<const char*>(static_cast<const C*>(A.alpha_tab) +
-                                                     ((member << (A.n - kWin)) | tbits) * 11);
+                                                     ((member << (A.n - kWin)) | obits) * 11);
       constexpr int kLines = (int)((S::COLS * 11 * sizeof(C)) / 128) + 2;
       if ((int)threadIdx.x < kLines) prefetch_l1(at + threadIdx.x * 128);
     }
@@ -675,7 +684,7 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
     }
     if (A.alpha_tab) {
       const R* al_c = reinterpret_cast<const R*>(static_cast<const C*>(A.alpha_tab) +
-                                                 ((member << (A.n - kWin)) | tbits | (uint32_t)col) * 11);
+                                                 ((member << (A.n - kWin)) | obits | (uint32_t)col) * 11);
       C c = ld_c(al_c + 2 * 10);
       C al[kRegBits];
       const int xt = stage == 0 ? xa : xb;

@@ -21,7 +21,8 @@
 // Grover's oracle and diffusion are single-amplitude flips.
 //
 // Geometry LOW: window = qubits 0..9, one warp per 1024 consecutive
-// amplitudes.  Geometry HIGH: 10 qubits >= COLB; a block handles 2^COLB
+// amplitudes.  Geometry HIGH: the 10 qubits c..c+9, c >= COLB (the top ten,
+// or a window lower down for states above 20 qubits); a block handles 2^COLB
 // consecutive "columns" (qubits 0..COLB-1) of 1024 window combinations, so
 // every global access moves 2^COLB consecutive elements.
 //
@@ -317,14 +318,14 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
 }
 
 // Out factors of every tile of a pass: for member b and each value o of the
-// out-of-window bits, entry (o, a) = the product of the out terms attached to
+// out-of-window bits (those below the window, then those above it), entry (o, a) = the product of the out terms attached to
 // window bit a (a = 10: attached to none) whose out-of-window bits are all set
 // in o, times the deferred real diagonal of bit a (the overall scale for
 // a = 10).  The pass kernels read the 11 entries of their tile directly.
 template <typename R>
 __global__ void __launch_bounds__(256) k_out_table(cplx<R>* __restrict__ tab, const R* __restrict__ params, int stride,
                                                    const OutTerm* __restrict__ outs, OutStarts starts, int diag_off,
-                                                   int obits, int low, uint32_t chunks) {
+                                                   int obits, int wstart, uint32_t chunks) {
   // one member per block: its terms' masks and factors staged in shared memory
   extern __shared__ unsigned char ot_sm[];
   const int nterms = starts.v[11];
@@ -343,7 +344,9 @@ __global__ void __launch_bounds__(256) k_out_table(cplx<R>* __restrict__ tab, co
   if (i >= per) return;
   const uint64_t o = i / 11;
   const int a = (int)(i % 11);
-  const uint64_t fixed = low ? o << kWin : o;           // member-local out-of-window bits
+  // member-local out-of-window bits: o holds the bits below the window
+  // (wstart of them) and above it the bits above the window
+  const uint64_t fixed = ((o >> wstart) << (wstart + kWin)) | (o & ((1ull << wstart) - 1));
   R re = R(1), im = R(0);
   for (int k = starts.v[a]; k < starts.v[a + 1]; ++k) {
     if ((fixed & masks[k]) == masks[k]) {
@@ -421,7 +424,7 @@ struct PassPlan {
   int tile_shift = 0;             // log2(tiles per member)
   std::vector<Seg> segs;          // the ops in canonical segments (what the kernels run)
   std::vector<Flip> flips;
-  CUtensorMap tmap;               // HIGH: [members * 1024 rows][2^(n-10) columns], boxes of 2^colb columns
+  CUtensorMap tmap;               // HIGH: [members * 2^(n-c) rows][2^c columns] (c = win[0]), boxes of 2^colb columns
   CUtensorMap tmap4;              // HIGH complex64: the same with boxes of 4 columns (configuration 2)
   // device copies
   FOp* d_ops = nullptr;
@@ -520,8 +523,31 @@ bool commute(const PGate& a, const PGate& b) {
 int stage_of(int j) { return j >= 5 ? 0 : 1; }
 
 // Greedy pass builder starting at remaining[0]; returns absorbed flags.
-bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n, int colb, size_t op_budget,
-                PassPlan* P, std::vector<char>* absorbed) {
+// Start c of a high window [c, c + 10) for a run whose first dense gate is on
+// qubit q >= 10: of the candidates n - 10 (the top), q - 9 (the run goes
+// down) and q (it goes up), the one holding most of the run's next one-qubit
+// gates; -1 when none is allowed (c >= colb, and the tensor map's row
+// coordinate, members x 2^(n-c), within 31 bits).
+int choose_window(const std::vector<PGate>& G, const std::vector<int>& rem, int n, int colb, uint64_t batch, int q) {
+  int best = -1, best_count = -1;
+  const int cand[3] = {n - kWin, q - (kWin - 1), q};
+  for (int c : cand) {
+    c = std::min(std::max(c, colb), n - kWin);
+    if (c < colb || q < c || q >= c + kWin) continue;
+    if (n - c >= 31 || (batch << (n - c)) >= (1ull << 31)) continue;
+    int count = 0;
+    for (size_t i = 0; i < rem.size() && i < 256; ++i) {
+      const PGate& g = G[rem[i]];
+      if (!g.dense1 && !g.cp && !g.flip) break;
+      if (g.dense1 && g.g.targets[0] >= c && g.g.targets[0] < c + kWin) ++count;
+    }
+    if (count > best_count) { best = c; best_count = count; }
+  }
+  return best;
+}
+
+bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n, int colb, uint64_t batch,
+                size_t op_budget, PassPlan* P, std::vector<char>* absorbed) {
   P->colb = colb;
   // window from the first fusable dense gate (lookahead)
   int q = -1;
@@ -531,12 +557,15 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
     if (g.dense1) { q = g.g.targets[0]; break; }
   }
   P->high = false;
+  int c0 = 0;
   if (q >= 10) {
     if (n < kWin + colb) return false;               // a high tile needs 2^colb columns
     if (n > 32) return false;                        // its member-local offsets are 32-bit
+    c0 = choose_window(G, rem, n, colb, batch, q);
+    if (c0 < 0) return false;
     P->high = true;
   }
-  for (int l = 0; l < kWin; ++l) P->win[l] = P->high ? n - kWin + l : l;
+  for (int l = 0; l < kWin; ++l) P->win[l] = c0 + l;
   int loc[64];
   for (int i = 0; i < 64; ++i) loc[i] = -1;
   for (int l = 0; l < kWin; ++l) loc[P->win[l]] = l;
@@ -860,11 +889,12 @@ qs_status make_tmap(qs_plan p, PassPlan* P, int colb, CUtensorMap* map) {
   }
   qs_ctx* h = p->h;
   const uint64_t per = h->esize / 8;                     // 8-byte elements per amplitude
-  cuuint64_t dims[2] = {(cuuint64_t)(1ull << (h->n - kWin)) * per, (cuuint64_t)h->batch * 1024};
+  // rows: (member, bits above the window, window bits); columns: the bits below the window
+  const int c = P->win[0];
+  cuuint64_t dims[2] = {(cuuint64_t)(1ull << c) * per, (cuuint64_t)h->batch << (h->n - c)};
   cuuint64_t strides[1] = {dims[0] * 8};
   cuuint32_t box[2] = {(cuuint32_t)((1u << colb) * per), 256};
   cuuint32_t estr[2] = {1, 1};
-  (void)P;
   CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, h->state, dims, strides, box, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -926,7 +956,7 @@ cudaError_t launch_precompute(qs_plan p, const PassPlan& P, cudaStream_t s) {
     const uint32_t chunks = (uint32_t)(((11ull << obits) + 255) / 256);
     const size_t sm = (size_t)((P.out_start[11] + 1) & ~1) * sizeof(uint64_t) + (size_t)P.out_start[11] * sizeof(cplx<R>);
     k_out_table<R><<<(unsigned)(chunks * (uint64_t)h->batch), 256, sm, s>>>(
-        (cplx<R>*)P.d_alpha, (const R*)P.d_params, P.stride, P.d_outs, st, P.diag_off, obits, P.high ? 0 : 1, chunks);
+        (cplx<R>*)P.d_alpha, (const R*)P.d_params, P.stride, P.d_outs, st, P.diag_off, obits, P.win[0], chunks);
   }
   return cudaGetLastError();
 }
@@ -1246,7 +1276,7 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
       for (size_t budget = kMaxOps; budget >= 4 && !built; budget /= 2) {
         P = PassPlan();
         std::fill(absorbed.begin(), absorbed.end(), 0);
-        if (!build_pass(p->gates, rem, h->n, p->colb, budget, &P, &absorbed)) break;
+        if (!build_pass(p->gates, rem, h->n, p->colb, (uint64_t)h->batch, budget, &P, &absorbed)) break;
         built = segment_pass(&P);
       }
       if (built) {
