@@ -270,10 +270,10 @@ typedef struct {
 } qs_gate;
 
 /* Build a plan for `h` (the plan keeps a reference to h; destroy it first).
- * STATEVEC handles with n >= 10 get fused passes over two windows: qubits
- * 0..9 and, for n <= 32, the top ten qubits (n >= 13 complex64, n >= 12
- * complex128); gates outside both windows, and other shapes, run gate by
- * gate with the same kernels as the single-gate calls.
+ * STATEVEC handles with n >= 10 get fused passes over windows of ten qubits:
+ * qubits 0..9, and c..c+9 (c >= 3 complex64, c >= 2 complex128) chosen per run
+ * of gates, the top ten first; gates no window can hold, and other shapes,
+ * run gate by gate with the same kernels as the single-gate calls.
  * Errors: INVALID_ARG for a malformed gate (nothing is built). */
 qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_plan* out);
 /* Run the plan once on the handle's stream with noise level e and key seed

@@ -19,6 +19,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include <cstdint>
 
 #include "internal.cuh"
@@ -534,12 +536,14 @@ __device__ __forceinline__ int high_idx(int x, int col) {
   return (x + (x >> 5)) * (1 << COLB) + col;
 }
 
-template <typename R, int COLB, int NBUF>
+template <typename R, int COLB, int NBUF, bool WIDE = false>
 __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / HighShape<COLB>::WARPS : 1)
     k_pass_high(cplx<R>* __restrict__ psi, const __grid_constant__ CUtensorMap tmap, const __grid_constant__ PassArgs A) {
   static_assert(NBUF == 1 || NBUF == 2, "one or two tile buffers");
   using C = cplx<R>;
   using S = HighShape<COLB>;
+  // member-local amplitude offsets: 32-bit up to 32 qubits, 64-bit (WIDE) above
+  using Off = typename std::conditional<WIDE, uint64_t, uint32_t>::type;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ double fid_red[2][S::WARPS];
@@ -553,8 +557,8 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
 
   const int xa = lh | (warp << S::LW);                  // stage A: local bits 0..4
   const int xb = (lh << 5) | (warp << (5 + S::LW));     // stage B: local bits 5..9
-  const uint32_t offa = (uint32_t)xa << A.win[0];       // member-local offsets of the thread bits
-  const uint32_t offb = (uint32_t)(xb >> 5) << A.win[5];
+  const Off offa = (Off)xa << A.win[0];                 // member-local offsets of the thread bits
+  const Off offb = (Off)(xb >> 5) << A.win[5];
   const int sha = A.win[5], shb = A.win[0];             // register r: r << sha (A), r << shb (B)
   const uint64_t per = (A.tiles + gridDim.x - 1) / gridDim.x;
   const uint64_t first = (uint64_t)blockIdx.x * per;
@@ -612,8 +616,8 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
     // member-local offset of the tile (bits outside the window and the
     // columns), and the same bits packed below each other (the out-factor
     // table's index: bits below the window, then the bits above it)
-    const uint32_t tbits = (uint32_t)(((tl >> cshift) << (A.win[0] + kWin)) | ((tl & cmask) << COLB));
-    const uint32_t obits = (uint32_t)(((tl >> cshift) << A.win[0]) | ((tl & cmask) << COLB));
+    const Off tbits = (Off)(((tl >> cshift) << (A.win[0] + kWin)) | ((tl & cmask) << COLB));
+    const Off obits = (Off)(((tl >> cshift) << A.win[0]) | ((tl & cmask) << COLB));
     const R* P = params + member * (uint64_t)A.param_stride;
     C* sm = smbase + cur * S::BUF;
     // this tile's out factors (read at the end of the tile): into L1 now
@@ -629,7 +633,7 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
       // the one amplitude equal to 1: register (x >> sh) & 31 of the thread
       // whose other bits match
       const uint64_t x = A.basis ? A.basis[member] : A.basis0[0];
-      const uint32_t fixed = tbits | (uint32_t)col | (stage == 0 ? offa : offb);
+      const Off fixed = tbits | (Off)col | (stage == 0 ? offa : offb);
       const int sh = stage == 0 ? sha : shb;
       const uint32_t hot = (x & ~(31ull << sh)) == (uint64_t)fixed ? 1u << ((x >> sh) & 31) : 0u;
 #pragma unroll
@@ -678,13 +682,13 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
         const uint64_t w = fl.per_member ? A.marked[member] : fl.index;
         const int sh = stage == 0 ? sha : shb;
         const uint64_t regmask = 31ull << sh;
-        const uint64_t fixed = tbits | (uint32_t)col | (stage == 0 ? offa : offb);
+        const uint64_t fixed = tbits | (Off)col | (stage == 0 ? offa : offb);
         flip_reg<R>(a, (w & ~regmask) == fixed, (int)((w >> sh) & 31));
       }
     }
     if (A.alpha_tab) {
       const R* al_c = reinterpret_cast<const R*>(static_cast<const C*>(A.alpha_tab) +
-                                                 ((member << (A.n - kWin)) | obits | (uint32_t)col) * 11);
+                                                 ((member << (A.n - kWin)) | obits | (Off)col) * 11);
       C c = ld_c(al_c + 2 * 10);
       C al[kRegBits];
       const int xt = stage == 0 ? xa : xb;
@@ -708,14 +712,14 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
       }
       apply_real_product<R>(a, c, t5);
     }
-    const uint32_t fixed = tbits + (uint32_t)col + (stage == 0 ? offa : offb);
+    const Off fixed = tbits + (Off)col + (stage == 0 ? offa : offb);
     const int sh = stage == 0 ? sha : shb;
     if (A.fid) {
       const C* ref = static_cast<const C*>(A.ref) + fixed;
       R re = 0, im = 0;
 #pragma unroll
       for (int r = 0; r < kAmps; ++r) {
-        const C f = __ldcg(ref + ((uint32_t)r << sh));
+        const C f = __ldcg(ref + ((Off)r << sh));
         re += f.x * a[r].x + f.y * a[r].y;
         im += f.x * a[r].y - f.y * a[r].x;
       }
@@ -732,7 +736,7 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
     }
     C* out = psi + (member << A.n) + fixed;
 #pragma unroll
-    for (int r = 0; r < kAmps; ++r) out[(uint32_t)r << sh] = a[r];
+    for (int r = 0; r < kAmps; ++r) out[(Off)r << sh] = a[r];
     __syncthreads();
   }
 }

@@ -560,7 +560,6 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
   int c0 = 0;
   if (q >= 10) {
     if (n < kWin + colb) return false;               // a high tile needs 2^colb columns
-    if (n > 32) return false;                        // its member-local offsets are 32-bit
     c0 = choose_window(G, rem, n, colb, batch, q);
     if (c0 < 0) return false;
     P->high = true;
@@ -985,6 +984,10 @@ cudaError_t launch_pass_kernel(qs_plan p, const PassPlan& P, cudaStream_t s, int
     }
   } else {
     constexpr int CB = high_colb<R>();
+    if (A.n > 32) {                // 64-bit member-local offsets; one configuration
+      k_pass_high<R, CB, 2, true><<<grid(A.tiles, 1), HighShape<CB>::THREADS, high_smem<R, CB, 2>(), s>>>(psi, P.tmap, A);
+      return cudaGetLastError();
+    }
     if constexpr (sizeof(R) == 4) {
       if (p->high_cfg == 1) {
         k_pass_high<R, CB, 1><<<grid(A.tiles, 2), HighShape<CB>::THREADS, high_smem<R, CB, 1>(), s>>>(psi, P.tmap, A);
@@ -1041,9 +1044,11 @@ cudaError_t set_smem_attrs(size_t esize) {
     if (e == cudaSuccess) e = set_pass_attrs(k_pass_high<float, 3, 2>, high_smem<float, 3, 2>(), 1);
     if (e == cudaSuccess) e = set_pass_attrs(k_pass_high<float, 3, 1>, high_smem<float, 3, 1>(), 2);
     if (e == cudaSuccess) e = set_pass_attrs(k_pass_high<float, 2, 1>, high_smem<float, 2, 1>(), 4);
+    if (e == cudaSuccess) e = set_pass_attrs(k_pass_high<float, 3, 2, true>, high_smem<float, 3, 2>(), 1);
   } else {
     e = set_pass_attrs(k_pass_low<double, 4, 2>, low_smem<double, 4, 2>(), 1);
     if (e == cudaSuccess) e = set_pass_attrs(k_pass_high<double, 2, 2>, high_smem<double, 2, 2>(), 1);
+    if (e == cudaSuccess) e = set_pass_attrs(k_pass_high<double, 2, 2, true>, high_smem<double, 2, 2>(), 1);
   }
   if (e == cudaSuccess) done[which] = true;
   return e;
@@ -1234,7 +1239,7 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
   // (12 warps with one buffer; two high-window blocks per SM)
   if (h->dtype == QS_C64) { p->low_cfg = 2; p->high_cfg = 1; }
   // fused passes use 32-bit member-local offsets
-  const bool fuse = h->mode == QS_STATEVEC && h->n >= kWin && h->n <= 32;
+  const bool fuse = h->mode == QS_STATEVEC && h->n >= kWin;
   std::vector<int> rem;
   for (int i = 0; i < num_gates; ++i) rem.push_back(i);
   std::vector<std::vector<int>> dm_groups;

@@ -40,16 +40,16 @@ def test_allocation_beyond_hbm_fails_cleanly():
 
 
 def test_qft_on_2_pow_33_amplitudes():
-    # 64 GiB complex64: tile and amplitude indices beyond 32 bits in every
-    # fused pass.  The noiseless QFT of a basis state has |amplitude|^2 =
-    # 2^-33 everywhere; the norm stays 1.
+    # 64 GiB complex64: member-local offsets beyond 32 bits in every fused
+    # pass (the high windows' 64-bit kernel).  The noiseless QFT of a basis
+    # state has |amplitude|^2 = 2^-33 everywhere; the norm stays 1.
     n, x = 33, 0x1F0F0F0F1
     h = qs.qs_create(n, 1, 0, qs.QS_STATEVEC, qs.QS_C64)
     try:
         ops = inputs.qft_circuit(n, noisy=False)
         p = qs.qs_plan_create(h, pcirc.to_gates(ops))
         passes, _ = qs.qs_plan_info(p, h)
-        assert passes >= 4
+        assert passes == 4                    # windows [23, 33), [13, 23), [3, 13), [0, 10)
         qs.qs_set_basis_state(h, x)
         qs.qs_plan_run(p, 0.0, 1, 0, h)
         qs.qs_plan_destroy(p)
@@ -57,6 +57,13 @@ def test_qft_on_2_pow_33_amplitudes():
             f = qs.qs_fidelity(h, None, y)[0]
             assert abs(f * 2 ** n - 1.0) < 1e-4
         assert abs(qs.qs_trace(h)[0] - 1.0) < 1e-4
+        # the inverse circuit (reversed order, conjugate phases) must bring
+        # every phase back: the state returns to |x>
+        inv = [inputs.Op(o.kind, o.qubits, -o.theta, o.index, False) for o in reversed(ops)]
+        p = qs.qs_plan_create(h, pcirc.to_gates(inv))
+        qs.qs_plan_run(p, 0.0, 1, 0, h)
+        qs.qs_plan_destroy(p)
+        assert abs(qs.qs_fidelity(h, None, x)[0] - 1.0) < 1e-4
     finally:
         qs.qs_destroy(h)
 
