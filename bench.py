@@ -681,6 +681,36 @@ def extra_rows(h, n, T, esize, stream, peaks):
         "shor9_fidelity": shor9, "codes_ms": round(ms_codes, 1),
         "fig8_logical_z_T1_3_T2_2": fig8, "fig9_qft5_t0.1": fig9, "fig9_ms": round(ms_fig9, 1)}
 
+    # the largest single-GPU state vector: one noisy QFT trajectory on 34 qubits (128 GiB
+    # complex64, four fused passes); its fidelity |<QFT x|psi>|^2 is read as the overlap with |x>
+    # after the ideal inverse circuit
+    n34, x34, e34 = 34, 0x2B7E15162, 0.01
+    ops34 = inputs.qft_circuit(n34)
+    h34 = qs.qs_create(n34, 1, 0, qs.QS_STATEVEC, qs.QS_C64, stream)
+    try:
+        p34 = qs.qs_plan_create(h34, pcirc.to_gates(ops34))
+        inv34 = qs.qs_plan_create(h34, pcirc.to_gates(
+            [inputs.Op(o.kind, o.qubits, -o.theta, o.index, False) for o in reversed(ops34)]))
+        passes34, _ = qs.qs_plan_info(p34, h34)
+        qs.qs_set_basis_state(h34, x34)
+        e0, e1 = ev(), ev()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        qs.qs_plan_run(p34, e34, inputs.DEFAULT_SEED, 0, h34)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms34 = e0.elapsed_time(e1)
+        qs.qs_plan_run(inv34, 0.0, 0, 0, h34)
+        f34 = float(qs.qs_fidelity(h34, None, x34)[0])
+        qs.qs_plan_destroy(inv34)
+        qs.qs_plan_destroy(p34)
+    finally:
+        qs.qs_destroy(h34)
+    out["mc_qft_n34_one_trajectory"] = {
+        "qubits": n34, "state_GiB": 2 ** 34 * 8 / 2 ** 30, "gates": len(ops34), "passes": passes34, "e": e34,
+        "ms_per_circuit": round(ms34, 1), "updates_per_s": (1 << n34) * len(ops34) / (ms34 / 1e3),
+        "pass_GBps": round(passes34 * 2 * (1 << n34) * 8 / (ms34 / 1e3) / 1e9, 1), "fidelity": f34}
+
     out["a11_serving_large_n"] = serving_large_n_row()
     out["a11_serving"] = serving_row()
     cap = out["a11_serving"]["jobs_per_s"]
