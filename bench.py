@@ -432,31 +432,40 @@ def extra_rows(h, n, T, esize, stream, peaks):
         "speedup": round((1024 / dt_batch) * dt_plain, 1), "fused_passes": passes,
         "success_prob_max_abs_diff_c64_vs_c128": err, "gates": len(ops1)}
 
-    # a6: exact density matrix of the noisy QFT, n = 14 (2^28 complex128 entries)
+    # a6: exact density matrix of the noisy QFT, n = 14 (2^28 entries): complex128 (FP64 pipe
+    # bound on this GPU) and complex64 (HBM bound), the fidelity of each with the ideal output
     W4 = inputs.WORKLOADS["dm_qft_n14"]
     ops4, x4 = W4.ops(), W4.initial_basis()
-    hd = qs.qs_create(W4.n, 1, 0, qs.QS_DENSITY, qs.QS_C128, stream)
-    qs.qs_set_basis_state(hd, x4)
-    pcirc.apply_ops(hd, ops4[:3], W4.e, W4.seed)
-    qs.qs_synchronize(hd)
-    qs.qs_set_basis_state(hd, x4)
-    # the circuit as a plan: runs of diagonal channels (the controlled phases after each
-    # Hadamard) become one sweep each
-    pd4 = qs.qs_plan_create(hd, pcirc.to_gates(ops4))
-    e0, e1 = ev(), ev()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    qs.qs_plan_run(pd4, W4.e, W4.seed, 0, hd)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_dm = e0.elapsed_time(e1)
-    _, dm_launches = qs.qs_plan_info(pd4, hd)
-    qs.qs_plan_destroy(pd4)
-    tr = float(qs.qs_trace(hd)[0])
-    qs.qs_destroy(hd)
-    out["a6_density_qft_n14"] = {"ms_per_circuit": round(ms_dm, 2), "channels": len(ops4), "launches": dm_launches,
-                                 "entries": 1 << (2 * W4.n), "trace": tr,
-                                 "updates_per_s": (1 << (2 * W4.n)) * len(ops4) / (ms_dm / 1e3)}
+    a6 = {}
+    for dt, name in ((qs.QS_C128, "c128"), (qs.QS_C64, "c64")):
+        hd = qs.qs_create(W4.n, 1, 0, qs.QS_DENSITY, dt, stream)
+        hi4 = pcirc.ideal_reference(W4.n, ops4, x4, dt, stream)
+        qs.qs_set_basis_state(hd, x4)
+        pcirc.apply_ops(hd, ops4[:3], W4.e, W4.seed)
+        qs.qs_synchronize(hd)
+        qs.qs_set_basis_state(hd, x4)
+        # the circuit as a plan: runs of diagonal channels (the controlled phases after each
+        # Hadamard) become one sweep each
+        pd4 = qs.qs_plan_create(hd, pcirc.to_gates(ops4))
+        e0, e1 = ev(), ev()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        qs.qs_plan_run(pd4, W4.e, W4.seed, 0, hd)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_dm = e0.elapsed_time(e1)
+        _, dm_launches = qs.qs_plan_info(pd4, hd)
+        qs.qs_plan_destroy(pd4)
+        qs.qs_set_reference_from(hd, hi4, 0)
+        a6[name] = {"ms_per_circuit": round(ms_dm, 2), "launches": dm_launches,
+                    "trace": float(qs.qs_trace(hd)[0]), "fidelity": float(qs.qs_fidelity_stored(hd)[0]),
+                    "updates_per_s": (1 << (2 * W4.n)) * len(ops4) / (ms_dm / 1e3),
+                    "sweep_GBps": round(dm_launches * 2 * (1 << (2 * W4.n)) * (16 if dt == qs.QS_C128 else 8)
+                                        / (ms_dm / 1e3) / 1e9, 1)}
+        qs.qs_destroy(hi4)
+        qs.qs_destroy(hd)
+    out["a6_density_qft_n14"] = {"channels": len(ops4), "entries": 1 << (2 * W4.n), **a6,
+                                 "fidelity_c64_minus_c128": a6["c64"]["fidelity"] - a6["c128"]["fidelity"]}
 
     # a7: fixed-rank Grover n = 16, r = 8: a bounded run of channels, extrapolated
     W3 = inputs.WORKLOADS["rank_grover_n16"]

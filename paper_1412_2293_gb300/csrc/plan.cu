@@ -368,22 +368,23 @@ __global__ void __launch_bounds__(256) k_out_table(cplx<R>* __restrict__ tab, co
 // run multiplies rho[x][y] by u(x) conj(u(y)) qpow[popcount(mask(x) ^ mask(y))]
 // with u = the product of the diagonals and bit c of mask(x) = "x has all
 // targets of noisy gate c set".  vec index x 2^n + y.
-struct QPow { double v[33]; };
+// Tables and arithmetic in the state's precision (complex64: FP32 throughout).
+template <typename R> struct QPow { R v[33]; };
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_dm_diag_block(cplx<R>* __restrict__ rho, int n, const double2* __restrict__ u,
-                                                       const uint32_t* __restrict__ mask, QPow qp) {
+__global__ void __launch_bounds__(256) k_dm_diag_block(cplx<R>* __restrict__ rho, int n, const cplx<R>* __restrict__ u,
+                                                       const uint32_t* __restrict__ mask, QPow<R> qp) {
   const uint64_t N = 1ull << n;
   const uint64_t total = N * N;
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < total; v += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t x = v >> n, y = v & (N - 1);
-    const double2 ux = u[x], uy = u[y];
+    const cplx<R> ux = u[x], uy = u[y];
     const uint32_t mx = mask[x], my = mask[y];
-    if ((mx | my) == 0 && ux.x == 1.0 && ux.y == 0.0 && uy.x == 1.0 && uy.y == 0.0) continue;
-    const double d = qp.v[__popc(mx ^ my)];
-    const double fr = (ux.x * uy.x + ux.y * uy.y) * d, fi = (ux.y * uy.x - ux.x * uy.y) * d;
+    if ((mx | my) == 0 && ux.x == R(1) && ux.y == R(0) && uy.x == R(1) && uy.y == R(0)) continue;
+    const R d = qp.v[__popc(mx ^ my)];
+    const R fr = (ux.x * uy.x + ux.y * uy.y) * d, fi = (ux.y * uy.x - ux.x * uy.y) * d;
     const cplx<R> r = rho[v];
-    rho[v] = mk<R>((R)(r.x * fr - r.y * fi), (R)(r.x * fi + r.y * fr));
+    rho[v] = mk<R>(r.x * fr - r.y * fi, r.x * fi + r.y * fr);
   }
 }
 
@@ -442,7 +443,8 @@ struct Step {
 };
 
 struct DmBlock {          // density matrix: a run of diagonal channels (k_dm_diag_block)
-  double2* d_u = nullptr;
+  double2* d_u = nullptr;         // complex128 handles
+  float2* d_uf = nullptr;         // complex64 handles
   uint32_t* d_mask = nullptr;
   int noisy = 0;
 };
@@ -1059,7 +1061,7 @@ qs_status run_single(qs_plan p, const PGate& g, const RunParams& rp, int pos);
 // a density-matrix diagonal block with noise level rp.e: qpow[k] = sqrt(P)^k, P = exp(-e^2)
 qs_status run_dm_block(qs_plan p, const DmBlock& b, const RunParams& rp) {
   qs_ctx* h = p->h;
-  QPow qp{};
+  QPow<double> qp{};
   const double q = std::sqrt(std::exp(-rp.e * rp.e));
   qp.v[0] = 1.0;
   for (int i = 1; i <= 32; ++i) qp.v[i] = qp.v[i - 1] * q;
@@ -1067,10 +1069,13 @@ qs_status run_dm_block(qs_plan p, const DmBlock& b, const RunParams& rp) {
   uint64_t blocks = (total + 255) / 256;
   const uint64_t cap = (uint64_t)num_sms() * 16;
   if (blocks > cap) blocks = cap;
-  if (h->dtype == QS_C64)
-    k_dm_diag_block<float><<<(int)blocks, 256, 0, h->stream>>>((float2*)h->state, h->n, b.d_u, b.d_mask, qp);
-  else
+  if (h->dtype == QS_C64) {
+    QPow<float> qf{};
+    for (int i = 0; i <= 32; ++i) qf.v[i] = (float)qp.v[i];
+    k_dm_diag_block<float><<<(int)blocks, 256, 0, h->stream>>>((float2*)h->state, h->n, b.d_uf, b.d_mask, qf);
+  } else {
     k_dm_diag_block<double><<<(int)blocks, 256, 0, h->stream>>>((double2*)h->state, h->n, b.d_u, b.d_mask, qp);
+  }
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? QS_OK : pfail(p, QS_ERR_CUDA, cudaGetErrorString(e));
 }
@@ -1337,7 +1342,13 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
     }
     DmBlock b;
     b.noisy = c;
-    st = upload(p, &b.d_u, u);
+    if (h->dtype == QS_C64) {
+      std::vector<float2> uf(u.size());
+      for (size_t i = 0; i < u.size(); ++i) uf[i] = make_float2((float)u[i].x, (float)u[i].y);
+      st = upload(p, &b.d_uf, uf);
+    } else {
+      st = upload(p, &b.d_u, u);
+    }
     if (st == QS_OK) st = upload(p, &b.d_mask, mask);
     p->dm_blocks.push_back(b);
   }
@@ -1579,6 +1590,7 @@ qs_status qs_plan_destroy(qs_plan p) {
   if (p->d_fid) cudaFree(p->d_fid);
   for (auto& b : p->dm_blocks) {
     if (b.d_u) cudaFree(b.d_u);
+    if (b.d_uf) cudaFree(b.d_uf);
     if (b.d_mask) cudaFree(b.d_mask);
   }
   if (p->d_run) cudaFree(p->d_run);
