@@ -426,11 +426,20 @@ def extra_rows(h, n, T, esize, stream, peaks):
     qs.qs_plan_destroy(pb)
     qs.qs_destroy(hb)
     err = max(abs(fb[b] - plain_f[b]) for b in range(reps))
+    # Fig. 1's quantity: the distribution of 1 - p over the trajectories, and Eq. 10's
+    # rank-1 value lambda_1^(n + 2nk) sin^2((2k+1) asin 2^(-n/2)) beside its mean
+    k1 = W1.extra.get("iterations", inputs.grover_iterations(W1.n))
+    lam1 = (1.0 + math.exp(-2.0 * W1.e * W1.e)) / 2.0
+    eq10 = lam1 ** (W1.n + 2 * W1.n * k1) * math.sin((2 * k1 + 1) * math.asin(2.0 ** (-W1.n / 2.0))) ** 2
+    fbn = np.asarray(fb)
     out["plain_vs_batched_grover_n10"] = {
         "plain_c128_gate_by_gate_circuits_per_s": round(1.0 / dt_plain, 2),
         "batched_c64_fused_circuits_per_s": round(1024 / dt_batch, 1),
         "speedup": round((1024 / dt_batch) * dt_plain, 1), "fused_passes": passes,
-        "success_prob_max_abs_diff_c64_vs_c128": err, "gates": len(ops1)}
+        "success_prob_max_abs_diff_c64_vs_c128": err, "gates": len(ops1), "iterations": k1,
+        "success_prob_mean": float(fbn.mean()), "success_prob_stderr": float(fbn.std() / math.sqrt(len(fbn))),
+        "one_minus_p_p5_p50_p95": [float(x) for x in np.percentile(1.0 - fbn, [5, 50, 95])],
+        "eq10": eq10}
 
     # a6: exact density matrix of the noisy QFT, n = 14 (2^28 entries): complex128 (FP64 pipe
     # bound on this GPU) and complex64 (HBM bound), the fidelity of each with the ideal output
