@@ -91,6 +91,20 @@ def test_tensor_and_cuda_core_paths_agree():
     assert np.abs(a - b).max() > 0
 
 
+@pytest.mark.parametrize("k,targets", [(3, (4, 17, 9)), (4, (0, 12, 19, 6)), (5, (2, 7, 11, 15, 18))])
+def test_many_tiles_per_block(k, targets):
+    # 8 members of 2^20 amplitudes: thousands of tiles, so every persistent
+    # block streams many of them (the next tile's loads overlap the current
+    # one); element by element against the oracle
+    n, members = 20, 8
+    rng = np.random.default_rng(90 + k)
+    U = rand_unitary(rng, 1 << k)
+    psi = rand_states(rng, members, n)
+    got = run(n, members, targets, U, psi, qs.QS_C64)
+    want = np.stack([statevec.apply_gate(p, n, targets, U) for p in psi])
+    assert np.abs(got - want).max() < 4e-6 * bound(U, psi)
+
+
 def test_real_and_permutation_blocks():
     # a Toffoli and a real orthogonal block: exact up to the split's rounding
     n, members = 12, 2
