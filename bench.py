@@ -874,7 +874,65 @@ def run_channels(args, rank, world, local_rank):
                         "peak_source": "FP64 FMA rate measured live (qs_measure_peaks)",
                         "launch_ms_by_kind": {k: round(v, 4) for k, v in kinds.items()}}}
     qs.qs_destroy(h)
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_channels(W, ops, x0, updates_per_step)
     return out
+
+
+def cpu_baseline_channels(W, ops, x0, updates_per_step, budget_s=15.0):
+    """The oracle on one host thread for the density / fixed-rank workloads.
+
+    Fixed rank: the circuit's gates in order at full size until the time
+    budget is spent, extrapolated over the whole gate list.  Density: the
+    complex128 matrix of the full size (4^n entries) is too slow for the
+    oracle, so the same circuit family's gates run at 12 qubits in order, and
+    the time per entry and gate is scaled to 4^n entries."""
+    import numpy as np
+
+    from oracle import circuits as ocirc
+    from oracle import density as oden
+    from oracle import fixed_rank as ofr
+    from oracle import gates as ogates
+    from oracle import statevec as osv
+    from paper_1412_2293_gb300 import inputs
+
+    def step_op(state, op, n, density):
+        if op.kind == "FLIP":
+            return oden.phase_flip(state, op.index) if density else ofr.phase_flip(state, op.index)
+        U = ocirc.op_unitary(op)
+        t = ocirc.op_targets(op)
+        if op.noisy:
+            kr = ogates.kraus_set(U, ocirc.op_noise(op), W.e)
+            if density:
+                return oden.apply_channel(state, n, t, kr)
+            return ofr.truncate(ofr.apply_kraus(state, n, t, kr), W.rank)[0]
+        return oden.apply_unitary(state, n, t, U) if density else ofr.apply_unitary(state, n, t, U)
+
+    density = W.mode == "density"
+    n_s = min(W.n, 12) if density else W.n
+    ops_s = ops if n_s == W.n else (inputs.qft_circuit(n_s) if W.circuit == "qft" else
+                                   inputs.grover_circuit(n_s, inputs.grover_iterations(n_s), 0))
+    state = oden.pure(osv.basis_state(n_s, x0 % (1 << n_s))) if density else ofr.initial_factor(n_s, x0)
+    t0 = time.perf_counter()
+    count = 0
+    for op in ops_s:
+        state = step_op(state, op, n_s, density)
+        count += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    entries_s = (1 << (2 * n_s)) if density else (1 << n_s) * W.rank
+    per_update = dt / (count * entries_s)
+    value = 1.0 / per_update
+    if density and n_s != W.n:
+        sample = (f"first {count} of {len(ops_s)} gates of the {W.circuit} circuit on {n_s} qubits "
+                  f"(4^{n_s} entries, complex128 NumPy, one thread, {dt:.1f} s); time per entry and gate "
+                  f"scaled to the 4^{W.n}-entry workload (extrapolated)")
+    else:
+        sample = (f"first {count} of {len(ops_s)} gates at full size (n = {W.n}, r = {W.rank}; complex128 "
+                  f"NumPy, one thread, {dt:.1f} s), extrapolated over the circuit")
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+            "circuit_s_extrapolated": updates_per_step / value}
 
 
 # ------------------------------------------------------------------ single-kernel runs
