@@ -820,9 +820,22 @@ def run_channels(args, rank, world, local_rank):
     updates_per_step = entries * len(ops)
     ev = lambda: torch.cuda.Event(enable_timing=True)
     per_kind = {}
+    plan = None
+    if mode == qs.QS_DENSITY:
+        # the circuit as a plan (noisy H channels as single sweeps, each run of diagonal
+        # channels as one sweep), timed per launch with events inside the captured graph
+        plan = qs.qs_plan_create(h, pcirc.to_gates(ops))
+        qs.qs_plan_set_timing(plan, True, h)
+        _, plan_kernels = qs.qs_plan_info(plan, h)
 
     def step(timed):
         qs.qs_set_basis_state(h, x0)
+        if plan is not None:
+            qs.qs_plan_run(plan, W.e, W.seed, 0, h)
+            if timed:
+                for m, k in zip(*qs.qs_plan_last_times(plan, h=h)):
+                    per_kind.setdefault("H_channel" if k == "single_gate" else k, []).append(m)
+            return qs.qs_fidelity_stored(h)
         for g, op in enumerate(ops):
             if timed:
                 a, b = ev(), ev()
@@ -844,12 +857,18 @@ def run_channels(args, rank, world, local_rank):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    kinds = {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in per_kind.items()}
+    kinds = {k: statistics.mean(x if isinstance(x, float) else x[0].elapsed_time(x[1]) for x in v)
+             for k, v in per_kind.items()}
+    if plan is not None:
+        qs.qs_plan_destroy(plan)
     if mode == qs.QS_DENSITY:
-        # superoperator of a noisy H: a real 4x4 matrix (l1 H (x) H + l2 HJ (x) HJ) on 2^(2n)
-        # entries; algorithmic FP64 work 4 real-by-complex multiply-adds (16 flop) per entry
-        dom = "H_channel"
-        flop = (1 << (2 * n)) * 16
+        # the kind of launch with the most time: the superoperator of a noisy H (a real 4x4
+        # matrix l1 H (x) H + l2 HJ (x) HJ: 4 real-by-complex multiply-adds, 16 flop per entry)
+        # or a run of diagonal channels (the factor u(x) conj(u(y)) sqrt(P)^k and its product
+        # with the entry: two complex multiplications and a real scale, 14 flop per entry)
+        totals = {k: len(per_kind[k]) * kinds[k] for k in kinds}
+        dom = max(totals, key=totals.get)
+        flop = (1 << (2 * n)) * (14 if dom == "dm_diag_block" else 16)
         bytes_ = 2 * (1 << (2 * n)) * 16
     else:
         dom = "H_channel"
@@ -866,10 +885,13 @@ def run_channels(args, rank, world, local_rank):
            "config": {"workload": args.workload, "mode": W.mode, "circuit": W.circuit, "n": n, "rank": W.rank,
                       "channels": channels, "gates": len(ops), "e": W.e, "circuits_per_s": 1e3 / ms,
                       "fidelity": float(f[0]), "trace": float(qs.qs_trace(h)[0])},
-           "gpu_launches": None,
+           # density: per step the plan's kernels, the start state, the fidelity's two reductions
+           "gpu_launches": args.steps * (plan_kernels + 3) if plan is not None else None,
            "roofline": {"bound": "alu", "achieved": round(achieved, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
                         "frac": round(achieved / fp64_peak, 4), "traffic": None,
-                        "kernel": "noisy-H channel (all its launches)", "avg_launch_ms": round(avg, 4),
+                        "kernel": {"H_channel": "noisy-H channel (all its launches)",
+                                   "dm_diag_block": "k_dm_diag_block (runs of diagonal channels)"}.get(dom, dom),
+                        "avg_launch_ms": round(avg, 4),
                         "algorithmic_flop_per_launch": flop, "algorithmic_bytes_per_launch": bytes_,
                         "peak_source": "FP64 FMA rate measured live (qs_measure_peaks)",
                         "launch_ms_by_kind": {k: round(v, 4) for k, v in kinds.items()}}}

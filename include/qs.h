@@ -295,7 +295,8 @@ qs_status qs_plan_destroy(qs_plan p);
  * (eager launches, `reps` runs averaged; the state is modified as by
  * qs_plan_run).  ms[i] = mean duration of launch i of a run, kinds[i] =
  * 0 noise/parameter precompute, 1 low-window pass, 2 high-window pass,
- * 3 single-gate step (all kernels of the step together); at most `cap`
+ * 3 single-gate step (all kernels of the step together), 4 density-matrix
+ * run of diagonal channels (one sweep); at most `cap`
  * entries, *count = launches per run.  Synchronises. */
 qs_status qs_plan_profile(qs_plan p, int reps, double e, uint64_t seed, uint64_t gate_id0,
                           double* ms, int* kinds, int cap, int* count);

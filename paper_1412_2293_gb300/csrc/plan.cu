@@ -369,7 +369,10 @@ __global__ void __launch_bounds__(256) k_out_table(cplx<R>* __restrict__ tab, co
 // with u = the product of the diagonals and bit c of mask(x) = "x has all
 // targets of noisy gate c set".  vec index x 2^n + y.
 // Tables and arithmetic in the state's precision (complex64: FP32 throughout).
+// Bit 31 of mask(x) marks an index whose factor is exactly 1 with no noisy
+// gate active: pairs of such indices are skipped by an integer test.
 template <typename R> struct QPow { R v[33]; };
+constexpr uint32_t kDmTrivial = 1u << 31;
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_dm_diag_block(cplx<R>* __restrict__ rho, int n, const cplx<R>* __restrict__ u,
@@ -378,10 +381,10 @@ __global__ void __launch_bounds__(256) k_dm_diag_block(cplx<R>* __restrict__ rho
   const uint64_t total = N * N;
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < total; v += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t x = v >> n, y = v & (N - 1);
-    const cplx<R> ux = u[x], uy = u[y];
     const uint32_t mx = mask[x], my = mask[y];
-    if ((mx | my) == 0 && ux.x == R(1) && ux.y == R(0) && uy.x == R(1) && uy.y == R(0)) continue;
-    const R d = qp.v[__popc(mx ^ my)];
+    if (mx & my & kDmTrivial) continue;
+    const cplx<R> ux = u[x], uy = u[y];
+    const R d = qp.v[__popc((mx ^ my) & ~kDmTrivial)];
     const R fr = (ux.x * uy.x + ux.y * uy.y) * d, fi = (ux.y * uy.x - ux.x * uy.y) * d;
     const cplx<R> r = rho[v];
     rho[v] = mk<R>(r.x * fr - r.y * fi, r.x * fi + r.y * fr);
@@ -1106,10 +1109,16 @@ qs_status enqueue_run(qs_plan p, cudaStream_t s, int synth, int fid) {
   cudaStream_t saved = h->stream;
   h->stream = s;
   size_t ev = 0;
+  cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+  if (p->timing) cudaStreamIsCapturing(s, &capturing);
   auto mark = [&](int kind) {
     if (!p->timing) return;
-    // external: under stream capture this becomes an event-record node
-    cudaEventRecordWithFlags(p->events[ev], s, cudaEventRecordExternal);
+    // under stream capture an external record becomes an event-record node;
+    // eager runs (plans with single-gate steps) record plainly
+    if (capturing == cudaStreamCaptureStatusActive)
+      cudaEventRecordWithFlags(p->events[ev], s, cudaEventRecordExternal);
+    else
+      cudaEventRecord(p->events[ev], s);
     if (ev > 0) p->event_kinds[ev - 1] = kind;
     ++ev;
   };
@@ -1133,7 +1142,7 @@ qs_status enqueue_run(qs_plan p, cudaStream_t s, int synth, int fid) {
       if (e != cudaSuccess) { h->stream = saved; return pfail(p, QS_ERR_CUDA, std::string("fused pass: ") + cudaGetErrorString(e)); }
     } else {
       qs_status r = run_step(p, st, *p->h_run);
-      mark(3);
+      mark(st.kind == 2 ? 4 : 3);
       if (r != QS_OK) { h->stream = saved; return r; }
     }
   }
@@ -1267,7 +1276,7 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
     for (int i : rem) {
       const PGate& g = p->gates[i];
       if (dm_diag(g)) {
-        if (g.g.kind == QS_GATE_DENSE && g.g.noisy && noisy == 32) close();
+        if (g.g.kind == QS_GATE_DENSE && g.g.noisy && noisy == 31) close();   // bit 31 of the masks: see kDmTrivial
         cur.push_back(i);
         if (g.g.kind == QS_GATE_DENSE && g.g.noisy) ++noisy;
       } else {
@@ -1340,6 +1349,8 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
       }
       if (g.g.noisy) ++c;
     }
+    for (uint64_t x = 0; x < N; ++x)
+      if (mask[x] == 0 && u[x].x == 1.0 && u[x].y == 0.0) mask[x] = kDmTrivial;
     DmBlock b;
     b.noisy = c;
     if (h->dtype == QS_C64) {
@@ -1450,7 +1461,7 @@ qs_status qs_plan_profile(qs_plan p, int reps, double e, uint64_t seed, uint64_t
       } else {
         result = run_step(p, st, *p->h_run);
         cudaEventRecord(ev[k++], h->stream);
-        kind[li++] = 3;
+        kind[li++] = st.kind == 2 ? 4 : 3;
         if (result != QS_OK) break;
       }
     }

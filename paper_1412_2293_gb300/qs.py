@@ -343,7 +343,7 @@ def qs_plan_info(p, h=None):
     return a.value, b.value
 
 
-PROFILE_KINDS = {0: "precompute", 1: "pass_low", 2: "pass_high", 3: "single_gate"}
+PROFILE_KINDS = {0: "precompute", 1: "pass_low", 2: "pass_high", 3: "single_gate", 4: "dm_diag_block"}
 
 
 def qs_plan_profile(p, reps, e, seed, gate_id0=0, cap=4096, h=None):

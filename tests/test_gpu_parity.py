@@ -535,6 +535,28 @@ def test_autotune_picks_a_configuration_and_results_stay_correct():
         qs.qs_plan_destroy(p)
 
 
+def test_plan_timing_with_single_steps():
+    # a density plan (channels as single steps, diagonal blocks) timed per
+    # launch: kinds and counts match the plan, the state is unchanged by timing
+    n, e = 7, 0.05
+    ops = inputs.qft_circuit(n)
+    states = []
+    for timing in (False, True):
+        with Handle(n, 1, 0, qs.QS_DENSITY, qs.QS_C128) as h:
+            qs.qs_set_basis_state(h, 3)
+            p = qs.qs_plan_create(h, pcirc.to_gates(ops))
+            qs.qs_plan_set_timing(p, timing, h)
+            qs.qs_plan_run(p, e, SEED, 0, h)
+            if timing:
+                ms, kinds = qs.qs_plan_last_times(p, h=h)
+                _, launches = qs.qs_plan_info(p, h)
+                assert len(ms) == launches and all(m >= 0 for m in ms)
+                assert kinds.count("single_gate") == n and kinds.count("dm_diag_block") == n - 1
+            qs.qs_plan_destroy(p)
+            states.append(qs.qs_get_state(h))
+    np.testing.assert_array_equal(states[0], states[1])
+
+
 @pytest.mark.parametrize("circ,n", [("qft", 6), ("qft", 7), ("grover", 5)])
 @pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
 def test_density_plan_with_diagonal_blocks_matches_oracle(circ, n, dtype):
