@@ -468,9 +468,7 @@ def extra_rows(h, n, T, esize, stream, peaks):
         qs.qs_set_reference_from(hd, hi4, 0)
         a6[name] = {"ms_per_circuit": round(ms_dm, 2), "launches": dm_launches,
                     "trace": float(qs.qs_trace(hd)[0]), "fidelity": float(qs.qs_fidelity_stored(hd)[0]),
-                    "updates_per_s": (1 << (2 * W4.n)) * len(ops4) / (ms_dm / 1e3),
-                    "sweep_GBps": round(dm_launches * 2 * (1 << (2 * W4.n)) * (16 if dt == qs.QS_C128 else 8)
-                                        / (ms_dm / 1e3) / 1e9, 1)}
+                    "updates_per_s": (1 << (2 * W4.n)) * len(ops4) / (ms_dm / 1e3)}
         qs.qs_destroy(hi4)
         qs.qs_destroy(hd)
     out["a6_density_qft_n14"] = {"channels": len(ops4), "entries": 1 << (2 * W4.n), **a6,
@@ -865,11 +863,13 @@ def run_channels(args, rank, world, local_rank):
         # the kind of launch with the most time: the superoperator of a noisy H (a real 4x4
         # matrix l1 H (x) H + l2 HJ (x) HJ: 4 real-by-complex multiply-adds, 16 flop per entry)
         # or a run of diagonal channels (the factor u(x) conj(u(y)) sqrt(P)^k and its product
-        # with the entry: two complex multiplications and a real scale, 14 flop per entry)
+        # with the entry: two complex multiplications and a real scale, 14 flop per entry).
+        # rho is Hermitian, so the algorithmic work is that of the entries on or above the
+        # diagonal: half of it (the sweeps on qubits below 5 still do all of it)
         totals = {k: len(per_kind[k]) * kinds[k] for k in kinds}
         dom = max(totals, key=totals.get)
-        flop = (1 << (2 * n)) * (14 if dom == "dm_diag_block" else 16)
-        bytes_ = 2 * (1 << (2 * n)) * 16
+        flop = (1 << (2 * n)) * (14 if dom == "dm_diag_block" else 16) // 2
+        bytes_ = 3 * (1 << (2 * n)) * 16 // 2
     else:
         dom = "H_channel"
         M = 2 * W.rank

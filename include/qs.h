@@ -154,6 +154,12 @@ qs_status qs_apply_branch_gate(qs_handle h, const int* targets, int k, const dou
  * operators E (num_ops consecutive 2^k x 2^k matrices), k = 1..2.
  * The set must satisfy sum_i E_i^dagger E_i = I within 1e-12 (else
  * INVALID_ARG).  DENSITY: superoperator sum_i E_i (x) E_i* on bits (t, t+n).
+ * A DENSITY handle tracks whether its matrix is exactly Hermitian (after
+ * qs_create, qs_set_basis_state, qs_set_maximally_entangled, and qs_set_state
+ * of an exactly Hermitian matrix); while it is, one-qubit channels with a real
+ * superoperator on qubits t >= 5 (every noisy Hadamard, qs_apply_noisy_gate)
+ * and the diagonal blocks of plans compute only the entries on or above the
+ * diagonal and write the ones below as their conjugates.
  * FIXED_RANK: L' = [E_1 L | ... | E_K L], then truncation to the handle's
  * rank when num_ops > 1.  STATEVEC: NOT_SUPPORTED. */
 qs_status qs_apply_kraus(qs_handle h, const int* targets, int k, const double* E, int num_ops);

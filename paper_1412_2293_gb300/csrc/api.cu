@@ -196,7 +196,20 @@ qs_status apply_uniform(qs_handle h, void* psi, int n, int members, const int* t
 }
 
 // DENSITY: superoperator of a Kraus set on bits (t, t + n).
+bool all_real(const std::vector<cd>& m);
+
 qs_status dm_apply_channel(qs_handle h, const int* targets, int k, const std::vector<std::vector<cd>>& ks) {
+  if (k == 1 && h->hermitian && targets[0] >= 5 && h->n >= 6) {
+    // a real, non-diagonal superoperator (every noisy Hadamard) on a Hermitian
+    // rho: the groups on and above the diagonal only, mirrored below
+    const auto S = superop(ks, 2);
+    if (all_real(S) && !is_diagonal(S, 4)) {
+      const qs_status st = upload_mat(h, S);
+      if (st != QS_OK) return st;
+      QS_CUDA(h, qs::launch_dm_superop1_herm(h, h->state, h->n, targets[0], h->mats));
+      return QS_OK;
+    }
+  }
   int t2[2 * qs::kMaxK];
   for (int j = 0; j < k; ++j) { t2[j] = targets[j]; t2[k + j] = targets[j] + h->n; }
   return apply_uniform(h, h->state, 2 * h->n, 1, t2, 2 * k, superop(ks, 1 << k));
@@ -393,6 +406,7 @@ qs_status qs_set_basis_state(qs_handle h, uint64_t x) {
   } else if (h->mode == QS_DENSITY) {
     const uint64_t N = 1ull << h->n;
     QS_CUDA(h, qs::launch_set_basis(h, h->state, 2 * h->n, 1, x * N + x, nullptr));
+    h->hermitian = true;
   } else {
     QS_CUDA(h, cudaMemsetAsync(h->state, 0, h->state_elems * h->esize, h->stream));
     QS_CUDA(h, qs::launch_set_basis(h, h->state, h->n, 1, x, nullptr));
@@ -410,6 +424,7 @@ qs_status qs_set_maximally_entangled(qs_handle h) {
     QS_CUDA(h, qs::launch_set_entangled(h, h->state, h->batch, 0));
   } else if (h->mode == QS_DENSITY) {
     QS_CUDA(h, qs::launch_set_entangled(h, h->state, 1, 1));
+    h->hermitian = true;
   } else {
     QS_CUDA(h, cudaMemsetAsync(h->state, 0, h->state_elems * h->esize, h->stream));
     QS_CUDA(h, qs::launch_set_entangled(h, h->state, 1, 0));
@@ -757,6 +772,18 @@ qs_status qs_set_state(qs_handle h, const double* host, size_t count) {
     bool real = true;
     for (size_t i = 0; i < count && real; ++i) real = host[2 * i + 1] == 0.0;
     h->real_factor = real;
+  }
+  if (h->mode == QS_DENSITY) {
+    // the Hermitian sweeps read only the upper triangle: only for an exactly Hermitian matrix
+    const uint64_t N = 1ull << h->n;
+    bool herm = true;
+    for (uint64_t i = 0; i < N && herm; ++i)
+      for (uint64_t j = i; j < N && herm; ++j) {
+        const double* a = host + 2 * (i * N + j);
+        const double* b = host + 2 * (j * N + i);
+        herm = a[0] == b[0] && a[1] == -b[1];
+      }
+    h->hermitian = herm;
   }
   if (h->dtype == QS_C128) {
     QS_CUDA(h, cudaMemcpy(h->state, host, count * 16, cudaMemcpyHostToDevice));

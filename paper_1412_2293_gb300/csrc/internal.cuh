@@ -112,6 +112,7 @@ struct qs_ctx {
   void* ref = nullptr;
   bool has_ref = false;
   bool tensor_cores = true;              // complex64 dense blocks with k >= 3 on tcgen05
+  bool hermitian = true;                 // DENSITY: the stored matrix is exactly Hermitian
 
   // STATEVEC start state not yet written: 1 = every member |pending_x>,
   // 2 = member b |m_basis[b]>.  Written by the first consumer (a fused first
@@ -154,6 +155,12 @@ cudaError_t launch_dense_tc(qs_ctx* h, void* psi, int n, int members, const int*
 // (gamma = 1 - exp(-t/T1), keep = exp(-t/T1), c = exp(-t/T2)).
 cudaError_t launch_dm_relax(qs_ctx* h, void* rho, int n, const int* qubits, int count, double gamma,
                             double keep, double c);
+// A one-qubit channel with a real superoperator S (local index bit 0 = column
+// bit t, bit 1 = row bit t + n) on a Hermitian density matrix, t >= 5: only
+// the 2 x 2 groups on or above the diagonal are read and multiplied; tiles
+// above the diagonal also write their conjugate transposes through shared
+// memory.  S_dev: 16 values of the handle's precision with stride 2.
+cudaError_t launch_dm_superop1_herm(qs_ctx* h, void* rho, int n, int t, const void* S_dev);
 
 // reductions (results land in h->small, as doubles)
 cudaError_t launch_dot(qs_ctx* h, const void* psi, const void* ref, int n, int members,

@@ -1059,6 +1059,50 @@ cudaError_t set_smem_attrs(size_t esize) {
   return e;
 }
 
+// The same on a Hermitian rho (n >= 5): tiles of 32 x 32 entries; a tile on
+// the diagonal is computed in full, a tile above it is computed and also
+// written, conjugated and transposed, over the tile below it (the factor of
+// (y, x) is the conjugate of that of (x, y)), through shared memory so every
+// access is coalesced: half the reads and half the arithmetic.
+template <typename R>
+__global__ void __launch_bounds__(256) k_dm_diag_block_herm(cplx<R>* __restrict__ rho, int n,
+                                                            const cplx<R>* __restrict__ u,
+                                                            const uint32_t* __restrict__ mask, QPow<R> qp) {
+  __shared__ cplx<R> tile[32][33];
+  const uint64_t N = 1ull << n;
+  const uint64_t TT = N / 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (uint64_t b = blockIdx.x; b < TT * TT; b += gridDim.x) {
+    const uint64_t bx = b / TT, by = b % TT;
+    if (bx > by) continue;
+    const uint64_t y = by * 32 + tx;
+    const uint32_t my = mask[y];
+    const cplx<R> uy = u[y];
+    cplx<R> o[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint64_t x = bx * 32 + ty + 8 * k;
+      const uint32_t mx = mask[x];
+      const cplx<R> r = rho[x * N + y];
+      o[k] = r;
+      if (!(mx & my & kDmTrivial)) {
+        const cplx<R> ux = u[x];
+        const R d = qp.v[__popc((mx ^ my) & ~kDmTrivial)];
+        const R fr = (ux.x * uy.x + ux.y * uy.y) * d, fi = (ux.y * uy.x - ux.x * uy.y) * d;
+        o[k] = mk<R>(r.x * fr - r.y * fi, r.x * fi + r.y * fr);
+        rho[x * N + y] = o[k];
+      }
+    }
+    if (bx == by) continue;                              // uniform across the block
+#pragma unroll
+    for (int k = 0; k < 4; ++k) tile[tx][ty + 8 * k] = cconj(o[k]);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) rho[(by * 32 + ty + 8 * k) * N + bx * 32 + tx] = tile[ty + 8 * k][tx];
+    __syncthreads();
+  }
+}
+
 qs_status run_single(qs_plan p, const PGate& g, const RunParams& rp, int pos);
 
 // a density-matrix diagonal block with noise level rp.e: qpow[k] = sqrt(P)^k, P = exp(-e^2)
@@ -1072,12 +1116,21 @@ qs_status run_dm_block(qs_plan p, const DmBlock& b, const RunParams& rp) {
   uint64_t blocks = (total + 255) / 256;
   const uint64_t cap = (uint64_t)num_sms() * 16;
   if (blocks > cap) blocks = cap;
+  const bool herm = h->hermitian && h->n >= 5;
+  const uint64_t tiles = herm ? (1ull << (2 * h->n - 10)) : 0;
+  const unsigned hblocks = (unsigned)std::min<uint64_t>(tiles, (uint64_t)num_sms() * 8);
   if (h->dtype == QS_C64) {
     QPow<float> qf{};
     for (int i = 0; i <= 32; ++i) qf.v[i] = (float)qp.v[i];
-    k_dm_diag_block<float><<<(int)blocks, 256, 0, h->stream>>>((float2*)h->state, h->n, b.d_uf, b.d_mask, qf);
+    if (herm)
+      k_dm_diag_block_herm<float><<<hblocks, 256, 0, h->stream>>>((float2*)h->state, h->n, b.d_uf, b.d_mask, qf);
+    else
+      k_dm_diag_block<float><<<(int)blocks, 256, 0, h->stream>>>((float2*)h->state, h->n, b.d_uf, b.d_mask, qf);
   } else {
-    k_dm_diag_block<double><<<(int)blocks, 256, 0, h->stream>>>((double2*)h->state, h->n, b.d_u, b.d_mask, qp);
+    if (herm)
+      k_dm_diag_block_herm<double><<<hblocks, 256, 0, h->stream>>>((double2*)h->state, h->n, b.d_u, b.d_mask, qp);
+    else
+      k_dm_diag_block<double><<<(int)blocks, 256, 0, h->stream>>>((double2*)h->state, h->n, b.d_u, b.d_mask, qp);
   }
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? QS_OK : pfail(p, QS_ERR_CUDA, cudaGetErrorString(e));

@@ -329,6 +329,68 @@ __global__ void __launch_bounds__(256) k_dm_relax(cplx<R>* rho, int n, RelaxSet 
   }
 }
 
+// One-qubit channel with a real superoperator on a Hermitian rho, qubit t >=
+// 5.  Groups (the 2 x 2 blocks of rows x0, x0 | T and columns y0, y0 | T, T =
+// 2^t) are indexed with bit t removed from x0 and y0 and tiled 32 x 32; since
+// t >= 5 a tile's 32 group columns are 32 consecutive matrix columns.  A tile
+// on the diagonal is computed in full; a tile above it is computed and also
+// written, conjugated and transposed, over the tile below it (which is never
+// read): half the reads and half the arithmetic, every access coalesced.
+template <typename R>
+__global__ void __launch_bounds__(256) k_dm_superop1_herm(cplx<R>* __restrict__ rho, int n, int t,
+                                                          const R* __restrict__ S2) {
+  __shared__ cplx<R> tile[32][33];
+  R S[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) S[i] = S2[2 * i];
+  const uint64_t N = 1ull << n, T = 1ull << t;
+  const uint64_t TT = (N >> 1) / 32;                     // tiles per dimension
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (uint64_t b = blockIdx.x; b < TT * TT; b += gridDim.x) {
+    const uint64_t bx = b / TT, by = b % TT;
+    if (bx > by) continue;
+    cplx<R> o[4][4];                                     // [row k][quad entry q]
+    uint64_t x0s[4];
+    const uint64_t y0 = insert0(by * 32 + tx, t);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint64_t x0 = insert0(bx * 32 + ty + 8 * k, t);
+      x0s[k] = x0;
+      const uint64_t p[4] = {x0 * N + y0, x0 * N + (y0 | T), (x0 | T) * N + y0, (x0 | T) * N + (y0 | T)};
+      cplx<R> a[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) a[j] = rho[p[j]];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        R re = 0, im = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { re = fma(S[4 * q + j], a[j].x, re); im = fma(S[4 * q + j], a[j].y, im); }
+        o[k][q] = mk<R>(re, im);
+        rho[p[q]] = o[k][q];
+      }
+    }
+    if (bx == by) continue;                              // uniform across the block
+    // the mirrored groups: entry q of group (x0, y0) goes to the transposed position
+    const uint64_t mx0 = insert0(bx * 32 + tx, t);       // column of the mirrored write
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < 4; ++k) tile[tx][ty + 8 * k] = cconj(o[k][q]);
+      __syncthreads();
+      // q = 0: (x0, y0) -> (y0, x0); 1: (x0, y0|T) -> (y0|T, x0); 2: (x0|T, y0) -> (y0, x0|T);
+      // 3: (x0|T, y0|T) -> (y0|T, x0|T)
+      const uint64_t ro = (q & 1) ? T : 0, co = (q & 2) ? T : 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint64_t my0 = insert0(by * 32 + ty + 8 * k, t);
+        rho[(my0 | ro) * N + (mx0 | co)] = tile[ty + 8 * k][tx];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void k_debug_noise(uint64_t seed, uint64_t traj, uint64_t gate_id, int count,
                               uint32_t* words, double* normals) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -541,6 +603,18 @@ cudaError_t launch_phase_flip(qs_ctx* h, void* psi, int n, int members, uint64_t
   const int g = (members + kBlock - 1) / kBlock;
   if (h->dtype == QS_C64) k_phase_flip<float><<<g, kBlock, 0, h->stream>>>((float2*)psi, n, members, index, per);
   else k_phase_flip<double><<<g, kBlock, 0, h->stream>>>((double2*)psi, n, members, index, per);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dm_superop1_herm(qs_ctx* h, void* rho, int n, int t, const void* S_dev) {
+  const uint64_t tt = (1ull << (n - 1)) / 32;
+  uint64_t blocks = tt * tt;
+  const uint64_t cap = (uint64_t)num_sms() * 8;
+  if (blocks > cap) blocks = cap;
+  if (h->dtype == QS_C64)
+    k_dm_superop1_herm<float><<<(unsigned)blocks, 256, 0, h->stream>>>((float2*)rho, n, t, (const float*)S_dev);
+  else
+    k_dm_superop1_herm<double><<<(unsigned)blocks, 256, 0, h->stream>>>((double2*)rho, n, t, (const double*)S_dev);
   return cudaGetLastError();
 }
 

@@ -535,6 +535,44 @@ def test_autotune_picks_a_configuration_and_results_stay_correct():
         qs.qs_plan_destroy(p)
 
 
+@pytest.mark.parametrize("dtype", [qs.QS_C128, qs.QS_C64])
+def test_density_hermitian_sweeps_match_oracle(dtype):
+    # a Hermitian start (basis state): channels on qubits >= 5 and the
+    # diagonal blocks run on the upper tiles and mirror them (several tiles
+    # per dimension at n = 9); against the oracle and a non-Hermitian start
+    # that takes the full sweeps (the same state plus an antihermitian part
+    # that every operation here maps linearly)
+    n, e, x0 = 9, 0.05, 300
+    ops = inputs.qft_circuit(n)
+    tol = 1e-12 if dtype == qs.QS_C128 else 2e-6
+    with Handle(n, 1, 0, qs.QS_DENSITY, dtype) as h:
+        qs.qs_set_basis_state(h, x0)
+        p = qs.qs_plan_create(h, pcirc.to_gates(ops))
+        qs.qs_plan_run(p, e, SEED, 0, h)
+        qs.qs_plan_destroy(p)
+        got = qs.qs_get_state(h).reshape(1 << n, 1 << n)
+    rho = ocirc.run_density(n, ops, x0, e)
+    assert np.abs(got - rho).max() < tol
+    assert np.abs(got - got.conj().T).max() < tol * 1e-2     # Hermitian (to rounding of the full sweeps)
+    # the full sweeps on a matrix that is not Hermitian: linear in the input
+    rng = np.random.default_rng(8)
+    A = (rng.normal(size=(1 << n, 1 << n)) + 1j * rng.normal(size=(1 << n, 1 << n))) / (1 << n)
+    start = osv.basis_state(n, x0)
+    start = np.outer(start, start.conj()) + A
+    with Handle(n, 1, 0, qs.QS_DENSITY, dtype) as h:
+        qs.qs_set_state(h, start.ravel())
+        p = qs.qs_plan_create(h, pcirc.to_gates(ops))
+        qs.qs_plan_run(p, e, SEED, 0, h)
+        qs.qs_plan_destroy(p)
+        got2 = qs.qs_get_state(h).reshape(1 << n, 1 << n)
+    want2 = start
+    for op in ops:
+        U = ocirc.op_unitary(op)
+        kr = ogates.kraus_set(U, ocirc.op_noise(op), e) if op.noisy else [U]
+        want2 = odm.apply_channel(want2, n, ocirc.op_targets(op), kr)
+    assert np.abs(got2 - want2).max() < tol * 10
+
+
 def test_plan_timing_with_single_steps():
     # a density plan (channels as single steps, diagonal blocks) timed per
     # launch: kinds and counts match the plan, the state is unchanged by timing
