@@ -199,7 +199,7 @@ qs_status apply_uniform(qs_handle h, void* psi, int n, int members, const int* t
 bool all_real(const std::vector<cd>& m);
 
 qs_status dm_apply_channel(qs_handle h, const int* targets, int k, const std::vector<std::vector<cd>>& ks) {
-  if (k == 1 && h->hermitian && targets[0] >= 5 && h->n >= 6) {
+  if (k == 1 && h->hermitian && h->n >= 6) {
     // a real, non-diagonal superoperator (every noisy Hadamard) on a Hermitian
     // rho: the groups on and above the diagonal only, mirrored below
     const auto S = superop(ks, 2);

@@ -156,7 +156,7 @@ cudaError_t launch_dense_tc(qs_ctx* h, void* psi, int n, int members, const int*
 cudaError_t launch_dm_relax(qs_ctx* h, void* rho, int n, const int* qubits, int count, double gamma,
                             double keep, double c);
 // A one-qubit channel with a real superoperator S (local index bit 0 = column
-// bit t, bit 1 = row bit t + n) on a Hermitian density matrix, t >= 5: only
+// bit t, bit 1 = row bit t + n) on a Hermitian density matrix (n >= 6): only
 // the 2 x 2 groups on or above the diagonal are read and multiplied; tiles
 // above the diagonal also write their conjugate transposes through shared
 // memory.  S_dev: 16 values of the handle's precision with stride 2.

@@ -391,6 +391,57 @@ __global__ void __launch_bounds__(256) k_dm_superop1_herm(cplx<R>* __restrict__ 
   }
 }
 
+// The same for qubits t < 5: a raw 32 x 32 tile of rho holds whole groups
+// (both partners of every row and column are inside it), so it is loaded into
+// shared memory, each of its 256 groups is transformed by one thread, and the
+// tile is written back and, above the diagonal, also conjugated and
+// transposed over the tile below it.
+template <typename R>
+__global__ void __launch_bounds__(256) k_dm_superop1_herm_low(cplx<R>* __restrict__ rho, int n, int t,
+                                                              const R* __restrict__ S2) {
+  __shared__ cplx<R> tile[32][33];
+  R S[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) S[i] = S2[2 * i];
+  const uint64_t N = 1ull << n;
+  const uint64_t TT = N / 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int T = 1 << t;
+  // this thread's group in the tile: rows r0, r0 | T, columns c0, c0 | T
+  const int gid = threadIdx.x;                           // 256 groups = 16 x 16
+  const int r0 = (int)insert0((uint64_t)(gid >> 4), t), c0 = (int)insert0((uint64_t)(gid & 15), t);
+  for (uint64_t b = blockIdx.x; b < TT * TT; b += gridDim.x) {
+    const uint64_t bx = b / TT, by = b % TT;
+    if (bx > by) continue;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) tile[ty + 8 * k][tx] = rho[(bx * 32 + ty + 8 * k) * N + by * 32 + tx];
+    __syncthreads();
+    {
+      cplx<R> a[4] = {tile[r0][c0], tile[r0][c0 | T], tile[r0 | T][c0], tile[r0 | T][c0 | T]};
+      cplx<R> o[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        R re = 0, im = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { re = fma(S[4 * q + j], a[j].x, re); im = fma(S[4 * q + j], a[j].y, im); }
+        o[q] = mk<R>(re, im);
+      }
+      tile[r0][c0] = o[0];
+      tile[r0][c0 | T] = o[1];
+      tile[r0 | T][c0] = o[2];
+      tile[r0 | T][c0 | T] = o[3];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) rho[(bx * 32 + ty + 8 * k) * N + by * 32 + tx] = tile[ty + 8 * k][tx];
+    if (bx != by) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) rho[(by * 32 + ty + 8 * k) * N + bx * 32 + tx] = cconj(tile[tx][ty + 8 * k]);
+    }
+  }
+}
+
 __global__ void k_debug_noise(uint64_t seed, uint64_t traj, uint64_t gate_id, int count,
                               uint32_t* words, double* normals) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -607,10 +658,19 @@ cudaError_t launch_phase_flip(qs_ctx* h, void* psi, int n, int members, uint64_t
 }
 
 cudaError_t launch_dm_superop1_herm(qs_ctx* h, void* rho, int n, int t, const void* S_dev) {
-  const uint64_t tt = (1ull << (n - 1)) / 32;
+  const uint64_t tt = t < 5 ? 1 : (1ull << (n - 1)) / 32;
   uint64_t blocks = tt * tt;
   const uint64_t cap = (uint64_t)num_sms() * 8;
   if (blocks > cap) blocks = cap;
+  if (t < 5) {
+    uint64_t lb = (1ull << (2 * n - 10));
+    if (lb > cap) lb = cap;
+    if (h->dtype == QS_C64)
+      k_dm_superop1_herm_low<float><<<(unsigned)lb, 256, 0, h->stream>>>((float2*)rho, n, t, (const float*)S_dev);
+    else
+      k_dm_superop1_herm_low<double><<<(unsigned)lb, 256, 0, h->stream>>>((double2*)rho, n, t, (const double*)S_dev);
+    return cudaGetLastError();
+  }
   if (h->dtype == QS_C64)
     k_dm_superop1_herm<float><<<(unsigned)blocks, 256, 0, h->stream>>>((float2*)rho, n, t, (const float*)S_dev);
   else
