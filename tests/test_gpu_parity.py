@@ -544,7 +544,7 @@ def test_density_hermitian_sweeps_match_oracle(dtype):
     # that every operation here maps linearly)
     n, e, x0 = 9, 0.05, 300
     ops = inputs.qft_circuit(n)
-    tol = 1e-12 if dtype == qs.QS_C128 else 2e-6
+    tol = 1e-12 if dtype == qs.QS_C128 else 1e-5 * 2.0 ** (-n)    # entries are of order 2^-n
     with Handle(n, 1, 0, qs.QS_DENSITY, dtype) as h:
         qs.qs_set_basis_state(h, x0)
         p = qs.qs_plan_create(h, pcirc.to_gates(ops))
