@@ -232,7 +232,9 @@ qs_status qs_trace(qs_handle h, double* out);
  * (column-major: column c at offset c * 2^n; columns >= qs_get_rank are 0). */
 qs_status qs_state_size(qs_handle h, size_t* out);
 /* Copy the state to / from host memory as interleaved complex doubles
- * (count = qs_state_size).  Synchronises. */
+ * (count = qs_state_size).  Synchronises.  qs_set_state on a DENSITY handle
+ * checks whether the matrix is exactly Hermitian (rho[j][i] == conj rho[i][j]
+ * bit for bit); only then do the Hermitian sweeps (see qs_apply_kraus) run. */
 qs_status qs_get_state(qs_handle h, double* host, size_t count);
 qs_status qs_set_state(qs_handle h, const double* host, size_t count);
 /* FIXED_RANK: set the number of live columns after qs_set_state. */
