@@ -963,13 +963,16 @@ MICRO = {
     "dense_k5": ("dense", 20, 128, 5, (3, 9, 14, 17, 19)),
     "dense_k3": ("dense", 20, 128, 3, (2, 9, 15)),
     "relax_dm_n13": ("relax", 13, None, 0, ()),
+    "dm_qft_n12": ("dmplan", 12, None, 0, ()),
 }
 
 
 def run_micro(args):
     """One kernel on its own, for a profiler: --warmup + --steps launches of a
     complex64 dense block (1 GiB batch) or of the density-matrix relaxation
-    (13 qubits, 512 MiB); prints the mean time of the timed launches."""
+    (13 qubits, 512 MiB), or runs of the noisy QFT plan on a 12-qubit
+    complex128 density matrix (256 MiB: Hermitian channel sweeps and diagonal
+    blocks); prints the mean time of the timed launches (runs)."""
     import numpy as np
     import torch
 
@@ -985,11 +988,21 @@ def run_micro(args):
         U, _ = np.linalg.qr(rng.normal(size=(1 << k, 1 << k)) + 1j * rng.normal(size=(1 << k, 1 << k)))
         launch = lambda: qs.qs_apply_gate(h, targets, U)
         nbytes = 2 * members * (1 << n) * 8
-    else:
+    elif what == "relax":
         h = qs.qs_create(n, 1, 0, qs.QS_DENSITY, qs.QS_C64, stream)
         qs.qs_set_basis_state(h, 0)
         launch = lambda: qs.qs_apply_relaxation(h, [0, 7], 0.05, 3.0, 2.0)
         nbytes = 2 * (1 << (2 * n)) * 8
+    else:
+        from paper_1412_2293_gb300 import circuits as pcirc
+        h = qs.qs_create(n, 1, 0, qs.QS_DENSITY, qs.QS_C128, stream)
+        plan = qs.qs_plan_create(h, pcirc.to_gates(inputs.qft_circuit(n)))
+        _, nl = qs.qs_plan_info(plan, h)
+
+        def launch():
+            qs.qs_set_basis_state(h, 5)
+            qs.qs_plan_run(plan, 0.01, inputs.DEFAULT_SEED, 0, h)
+        nbytes = nl * 2 * (1 << (2 * n)) * 16
     for _ in range(args.warmup):
         launch()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
