@@ -175,3 +175,35 @@ def test_mutation_swapped_relaxation_rates_is_caught(monkeypatch):
     rho = rand_density(np.random.default_rng(3), 1, rank=2)
     out = density.apply_channel(rho, 1, (0,), rx.relaxation_kraus(0.7, 3.0, 2.0))
     assert abs(out[1, 1] - math.exp(-0.7 / 3.0) * rho[1, 1]) > 1e-3
+
+
+# ------------------------------------------- the product's circuit definitions
+
+def test_product_code_circuits_follow_eq18_and_the_shor_law():
+    # paper_1412_2293_gb300/codes.py defines its own gate matrices, encoders and
+    # decoders for the GPU runs; run through the oracle's density functions
+    # here, they must give the same closed forms (CPU only)
+    from paper_1412_2293_gb300 import codes
+
+    def run(code, p):
+        nq = codes.CODE_QUBITS[code]
+        n = nq + 1
+        rho = density.pure(statevec.basis_state(n, 0))
+        prep = [((0,), codes.H), ((0, nq), codes.CNOT)]
+        for t, U in prep + codes._encoder(code):
+            rho = density.apply_unitary(rho, n, t, U)
+        for q in range(nq):
+            rho = density.apply_channel(rho, n, (q,), codes.phase_error(p))
+        for t, U in codes._decoder(code):
+            rho = density.apply_unitary(rho, n, t, U)
+        for q in range(1, nq):
+            rho = density.apply_channel(rho, n, (q,), codes.RESET)
+        psi = statevec.basis_state(n, 0)
+        for t, U in prep:
+            psi = statevec.apply_gate(psi, n, t, U)
+        return density.fidelity(psi, rho)
+
+    p = 0.13
+    assert abs(run("phase3", p) - eq18_fmin(p) ** 2) < 1e-13
+    pb = block_error(p)
+    assert abs(run("shor9", p) - (1.0 - 3.0 * pb * pb + 2.0 * pb ** 3)) < 1e-12
