@@ -129,11 +129,6 @@ __device__ __forceinline__ void tmem_load<32>(uint32_t taddr, float* v) {
       "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
       : QS_R4(0), QS_R4(4), QS_R4(8), QS_R4(12), QS_R4(16), QS_R4(20), QS_R4(24), QS_R4(28) : "r"(taddr));
 }
-template <>
-__device__ __forceinline__ void tmem_load<64>(uint32_t taddr, float* v) {
-  tmem_load<32>(taddr, v);
-  tmem_load<32>(taddr + 32, v + 32);
-}
 #undef QS_R4
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
