@@ -13,7 +13,11 @@
  *     vectorised form (U (x) U*) vec(rho) of Sec. 3;
  *   - the fixed-rank approximation of Sec. 3.2 (factor L, rho = L L^dagger,
  *     Gram-matrix eigendecomposition, truncation to rank r);
- *   - fidelity and trace reductions (Figs. 1-4, Eq. 10).
+ *   - fidelity and trace reductions (Figs. 1-4, Eq. 10);
+ *   - rank-1 estimates by branch selection (Eqs. 11-15), Choi-Jamiolkowski
+ *     relative states (Sec. 4, Eqs. 16-17) and amplitude / phase relaxation
+ *     (T1, T2; Sec. 4.1-4.3, Eqs. 18-19);
+ *   - dense k-qubit blocks, k <= 5 (complex64 on the tcgen05 tensor cores).
  *
  * Conventions (all entry points):
  *   - Qubit t is bit t of the amplitude index (qubit 0 least significant).
