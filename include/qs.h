@@ -241,6 +241,12 @@ qs_status qs_state_size(qs_handle h, size_t* out);
  * bit for bit); only then do the Hermitian sweeps (see qs_apply_kraus) run. */
 qs_status qs_get_state(qs_handle h, double* host, size_t count);
 qs_status qs_set_state(qs_handle h, const double* host, size_t count);
+/* Copy elements [first, first + count) of the state to host memory as
+ * interleaved complex doubles (for STATEVEC, member b is the range
+ * [b 2^n, (b + 1) 2^n)), without copying the rest.  Synchronises.
+ * Errors: INVALID_ARG if the range exceeds qs_state_size or host is NULL. */
+qs_status qs_get_state_range(qs_handle h, size_t first, size_t count, double* host);
+
 /* FIXED_RANK: set the number of live columns after qs_set_state. */
 qs_status qs_set_rank_columns(qs_handle h, int m);
 

@@ -763,6 +763,23 @@ qs_status qs_get_state(qs_handle h, double* host, size_t count) {
   return QS_OK;
 }
 
+qs_status qs_get_state_range(qs_handle h, size_t first, size_t count, double* host) {
+  if (!h || (!host && count)) return QS_ERR_INVALID_ARG;
+  { const qs_status st = qs::materialize_basis(h); if (st != QS_OK) return st; }
+  if (first > h->state_elems || count > h->state_elems - first)
+    return fail(h, QS_ERR_INVALID_ARG, "range beyond qs_state_size");
+  if (!count) return QS_OK;
+  QS_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (h->dtype == QS_C128) {
+    QS_CUDA(h, cudaMemcpy(host, static_cast<const double2*>(h->state) + first, count * 16, cudaMemcpyDeviceToHost));
+  } else {
+    std::vector<float> f(2 * count);
+    QS_CUDA(h, cudaMemcpy(f.data(), static_cast<const float2*>(h->state) + first, count * 8, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < 2 * count; ++i) host[i] = f[i];
+  }
+  return QS_OK;
+}
+
 qs_status qs_set_state(qs_handle h, const double* host, size_t count) {
   if (!h || !host) return QS_ERR_INVALID_ARG;
   if (count != h->state_elems) return fail(h, QS_ERR_INVALID_ARG, "count must equal qs_state_size");

@@ -172,6 +172,45 @@ __device__ __forceinline__ cplx<R> ld_c(const R* p) { return __ldg(reinterpret_c
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
+// Complex products of the passes.  complex64 runs them on the packed
+// two-lane FP32 pipe: f a = f.x (a.x, a.y) + f.y (-a.y, a.x) is one packed
+// multiply and one packed FMA whose operands are the amplitude with its
+// halves swapped and the factor's halves broadcast or negated -- operand
+// forms the packed instructions take directly, so a complex product is two
+// instructions and its result stays a register pair for the packed shears
+// (four scalar instructions, and moves into pairs, otherwise).
+template <typename R>
+__device__ __forceinline__ cplx<R> pmul(cplx<R> f, cplx<R> a) {
+  if constexpr (sizeof(R) == 4) {
+    const float2 t = mul2(a, make_float2(f.x, f.x));
+    return fma2(make_float2(a.y, a.x), make_float2(-f.y, f.y), t);
+  } else {
+    return cmul(f, a);
+  }
+}
+// c + m b
+template <typename R>
+__device__ __forceinline__ cplx<R> pfma(cplx<R> m, cplx<R> b, cplx<R> c) {
+  if constexpr (sizeof(R) == 4) {
+    const float2 t = fma2(b, make_float2(m.x, m.x), c);
+    return fma2(make_float2(b.y, b.x), make_float2(-m.y, m.y), t);
+  } else {
+    return cfma(m, b, c);
+  }
+}
+// acc += conj(f) a
+template <typename R>
+__device__ __forceinline__ cplx<R> pdot(cplx<R> acc, cplx<R> f, cplx<R> a) {
+  if constexpr (sizeof(R) == 4) {
+    acc = fma2(a, make_float2(f.x, f.x), acc);
+    return fma2(make_float2(a.y, a.x), make_float2(f.y, -f.y), acc);
+  } else {
+    acc.x += f.x * a.x + f.y * a.y;
+    acc.y += f.x * a.y - f.y * a.x;
+    return acc;
+  }
+}
+
 // A real 2x2 gate [[a, b], [c, d]] written as two shears and a diagonal,
 // diag(a, det / a) [[1, 0], [s1, 1]] [[1, r0], [0, 1]], r0 = b / a,
 // s1 = c a / det: x0 += r0 x1, then x1 += s1 x0, each one FMA per component
@@ -215,8 +254,8 @@ __device__ __forceinline__ void dense_reg(cplx<R> (&a)[kAmps], const R* m, bool 
     for (int r = 0; r < kAmps; ++r) {
       if (r & (1 << RJ)) continue;
       const cplx<R> x0 = a[r], x1 = a[r | (1 << RJ)];
-      a[r] = cfma(u01, x1, cmul(u00, x0));
-      a[r | (1 << RJ)] = cfma(u11, x1, cmul(u10, x0));
+      a[r] = pfma<R>(u01, x1, pmul<R>(u00, x0));
+      a[r | (1 << RJ)] = pfma<R>(u11, x1, pmul<R>(u10, x0));
     }
   }
 }
@@ -235,7 +274,7 @@ __device__ __forceinline__ void dwin_reg(cplx<R> (&a)[kAmps], const R* T, int tb
 #pragma unroll
     for (int hi = 0; hi < kAmps / (2 * Q); ++hi) {
       const int r = q | Q | (hi << (RJ + 1));
-      a[r] = cmul(f, a[r]);
+      a[r] = pmul<R>(f, a[r]);
     }
   }
 }
@@ -257,11 +296,11 @@ __device__ __forceinline__ void apply_reg_product(cplx<R> (&a)[kAmps], cplx<R> c
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int q = 0; q < (1 << r); ++q) t[q | (1 << r)] = cmul(t[q], al[r]);
+    for (int q = 0; q < (1 << r); ++q) t[q | (1 << r)] = pmul<R>(al[r], t[q]);
 #pragma unroll
-  for (int r = 0; r < 16; ++r) a[r] = cmul(t[r], a[r]);
+  for (int r = 0; r < 16; ++r) a[r] = pmul<R>(t[r], a[r]);
 #pragma unroll
-  for (int r = 0; r < 16; ++r) a[r + 16] = cmul(cmul(t[r], al[4]), a[r + 16]);
+  for (int r = 0; r < 16; ++r) a[r + 16] = pmul<R>(pmul<R>(al[4], t[r]), a[r + 16]);
 }
 
 // a[rho] *= c * prod_{r in rho} t[r] for real factors (the deferred diagonals
@@ -467,7 +506,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
 #pragma unroll
       for (int r = 0; r < kRegBits; ++r) {
         al[r] = ld_c(reinterpret_cast<const R*>(al_g + (stage == 0 ? r + 5 : r)));
-        if ((lane >> r) & 1) c = cmul(c, ld_c(reinterpret_cast<const R*>(al_g + (stage == 0 ? r : r + 5))));
+        if ((lane >> r) & 1) c = pmul<R>(ld_c(reinterpret_cast<const R*>(al_g + (stage == 0 ? r : r + 5))), c);
       }
       apply_reg_product<R>(a, c, al);
     } else if (A.diag_off >= 0) {
@@ -492,14 +531,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
     }
     if (A.fid) {
       const C* ref = static_cast<const C*>(A.ref) + mloc;
-      R re = 0, im = 0;
+      C acc = mk<R>(R(0), R(0));
 #pragma unroll
-      for (int r = 0; r < kAmps; ++r) {
-        const C f = __ldcg(ref + lane + 32 * r);
-        re += f.x * a[r].x + f.y * a[r].y;
-        im += f.x * a[r].y - f.y * a[r].x;
-      }
-      const double sre = warp_sum_d((double)re), sim = warp_sum_d((double)im);
+      for (int r = 0; r < kAmps; ++r) acc = pdot<R>(acc, __ldcg(ref + lane + 32 * r), a[r]);
+      const double sre = warp_sum_d((double)acc.x), sim = warp_sum_d((double)acc.y);
       if (lane == 0) {
         const uint64_t slot = member * (1ull << A.tile_shift) + (mloc >> kWin);
         A.fid_partials[2 * slot] = sre;
@@ -696,7 +731,7 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
       for (int r = 0; r < kRegBits; ++r) {
         al[r] = ld_c(al_c + 2 * (stage == 0 ? r + 5 : r));
         const int lt = stage == 0 ? r : r + 5;
-        if ((xt >> lt) & 1) c = cmul(c, ld_c(al_c + 2 * lt));
+        if ((xt >> lt) & 1) c = pmul<R>(ld_c(al_c + 2 * lt), c);
       }
       apply_reg_product<R>(a, c, al);
     } else if (A.diag_off >= 0) {
@@ -716,14 +751,10 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
     const int sh = stage == 0 ? sha : shb;
     if (A.fid) {
       const C* ref = static_cast<const C*>(A.ref) + fixed;
-      R re = 0, im = 0;
+      C acc = mk<R>(R(0), R(0));
 #pragma unroll
-      for (int r = 0; r < kAmps; ++r) {
-        const C f = __ldcg(ref + ((Off)r << sh));
-        re += f.x * a[r].x + f.y * a[r].y;
-        im += f.x * a[r].y - f.y * a[r].x;
-      }
-      const double sre = warp_sum_d((double)re), sim = warp_sum_d((double)im);
+      for (int r = 0; r < kAmps; ++r) acc = pdot<R>(acc, __ldcg(ref + ((Off)r << sh)), a[r]);
+      const double sre = warp_sum_d((double)acc.x), sim = warp_sum_d((double)acc.y);
       if (lane == 0) { fid_red[0][warp] = sre; fid_red[1][warp] = sim; }
       __syncthreads();
       if (threadIdx.x == 0) {

@@ -71,6 +71,7 @@ _SIGS = {
     "qs_state_size": ([_P, ct.POINTER(ct.c_size_t)], ct.c_int),
     "qs_get_state": ([_P, _D, ct.c_size_t], ct.c_int),
     "qs_set_state": ([_P, _D, ct.c_size_t], ct.c_int),
+    "qs_get_state_range": ([_P, ct.c_size_t, ct.c_size_t, _D], ct.c_int),
     "qs_set_rank_columns": ([_P, ct.c_int], ct.c_int),
     "qs_set_trajectory_offset": ([_P, ct.c_uint64], ct.c_int),
     "qs_set_member_noise": ([_P, _D, _U64, _U64, _U64], ct.c_int),
@@ -277,6 +278,13 @@ def qs_get_state(h):
     n = qs_state_size(h)
     out = np.zeros(2 * n, dtype=np.float64)
     _check(lib().qs_get_state(h, _dptr(out), n), h)
+    return out.view(np.complex128)
+
+
+def qs_get_state_range(h, first, count):
+    """Elements [first, first + count) of the state as complex128."""
+    out = np.zeros(2 * int(count), dtype=np.float64)
+    _check(lib().qs_get_state_range(h, int(first), int(count), _dptr(out)), h)
     return out.view(np.complex128)
 
 

@@ -17,6 +17,7 @@ from oracle import philox as ophilox
 from oracle import statevec as osv
 from paper_1412_2293_gb300 import circuits as pcirc
 from paper_1412_2293_gb300 import inputs, qs
+from tests.tolerances import assert_amplitudes_close
 
 pytestmark = pytest.mark.gpu
 
@@ -84,7 +85,7 @@ def test_ideal_gate_matches_oracle(dtype, targets):
         qs.qs_apply_gate(h, targets, U)
         got = qs.qs_get_state(h).reshape(batch, -1)
     for b in range(batch):
-        np.testing.assert_allclose(got[b], osv.apply_gate(psi[b], n, targets, U), atol=TOL[dtype])
+        assert_amplitudes_close(got[b], osv.apply_gate(psi[b], n, targets, U), dtype)
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -101,7 +102,7 @@ def test_diagonal_gate_path_matches_oracle(dtype):
         got = qs.qs_get_state(h).reshape(batch, -1)
     for b in range(batch):
         want = osv.phase_flip(osv.apply_gate(psi[b], n, (5, 2), U), 77)
-        np.testing.assert_allclose(got[b], want, atol=TOL[dtype])
+        assert_amplitudes_close(got[b], want, dtype)
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -131,7 +132,7 @@ def test_noisy_gate_matches_oracle(dtype, case):
     for b in range(batch):
         xa, xb = ophilox.normal_pair(SEED, off + b, gid)
         Ub = ogates.noisy_unitary(U, noise, e, xa, xb)
-        np.testing.assert_allclose(got[b], osv.apply_gate(psi[b], n, targets, Ub), atol=TOL[dtype])
+        assert_amplitudes_close(got[b], osv.apply_gate(psi[b], n, targets, Ub), dtype)
 
 
 # ----------------------------------------------------------------- circuits
@@ -159,7 +160,7 @@ def test_plan_trajectories_match_oracle(dtype, circ, n):
     if circ == "qft" and n >= 13:
         assert passes == 2            # one high-window and one low-window pass
     for b in range(batch):
-        np.testing.assert_allclose(got[b], oracle_traj(n, ops, x0, e, b), atol=TOL[dtype])
+        assert_amplitudes_close(got[b], oracle_traj(n, ops, x0, e, b), dtype)
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -174,7 +175,7 @@ def test_gate_by_gate_equals_plan(dtype):
         qs.qs_plan_run(p, e, SEED, 0, h2)
         a = qs.qs_get_state(h1)
         b = qs.qs_get_state(h2)
-        np.testing.assert_allclose(a, b, atol=TOL[dtype])
+        assert_amplitudes_close(a, b, dtype)
         # a second run (graph replay) from the same start gives the same state
         qs.qs_set_basis_state(h2, x0)
         qs.qs_plan_run(p, e, SEED, 0, h2)
@@ -206,7 +207,7 @@ def test_fused_fidelity_and_per_member_starts_match_oracle(dtype, n):
     np.testing.assert_allclose(f_again, f_fused, rtol=0, atol=0)
     for b in range(batch):
         want = oracle_traj(n, ops, xs[b], e, b)
-        np.testing.assert_allclose(got[b], want, atol=TOL[dtype])
+        assert_amplitudes_close(got[b], want, dtype)
         assert abs(f_fused[b] - osv.fidelity(ideal0, want)) <= TOL[dtype] * 10
 
 
@@ -257,7 +258,7 @@ def test_random_circuits_through_the_planner_match_oracle(dtype, n, seed):
                 xa, xb = ophilox.normal_pair(SEED, b, 11 + g)
                 U = ogates.noisy_unitary(U, ocirc.op_noise(op), e, xa, xb)
             psi = osv.apply_gate(psi, n, ocirc.op_targets(op), U)
-        np.testing.assert_allclose(got[b], psi, atol=TOL[dtype] * (10 if dtype == qs.QS_C64 else 1))
+        assert_amplitudes_close(got[b], psi, dtype, k=4.0)
 
 
 def test_plan_with_unfusable_gates_matches_oracle():
@@ -301,11 +302,16 @@ def test_qft_full_size_sampled_trajectories():
         qs.qs_plan_run(p, e, SEED, 0, h)
         f = qs.qs_fidelity_stored(h)
         norms = qs.qs_trace(h)
+        sampled = (0, 513, T - 1)
+        states = {b: qs.qs_get_state_range(h, b << n, 1 << n) for b in sampled}
         qs.qs_plan_destroy(p)
     np.testing.assert_allclose(norms, 1.0, atol=1e-5)
     ideal = ocirc.ideal_state(n, ops, x0)
-    for b in (0, 513, T - 1):
-        want = osv.fidelity(ideal, oracle_traj(n, ops, x0, e, b))
+    for b in sampled:
+        psi = oracle_traj(n, ops, x0, e, b)
+        # every amplitude of the trajectory, element by element
+        assert_amplitudes_close(states[b], psi, qs.QS_C64, err_msg=f"trajectory {b}")
+        want = osv.fidelity(ideal, psi)
         assert abs(f[b] - want) < 1e-5, (b, f[b], want)
     # distribution sanity against Eq. 11 (lower estimate) and 1
     assert np.all(f <= 1 + 1e-5)
@@ -508,7 +514,7 @@ def test_every_kernel_configuration_gives_the_same_result(circ, n, batch):
         np.testing.assert_allclose(f, f0, atol=1e-6, err_msg=str(key))
     for b in (0, batch - 1):
         want = oracle_traj(n, ops, xs[b], e, b)
-        np.testing.assert_allclose(s0[b], want, atol=TOL[qs.QS_C64])
+        assert_amplitudes_close(s0[b], want, qs.QS_C64)
         assert abs(f0[b] - osv.fidelity(ideal0, want)) <= 1e-5
 
 
@@ -526,7 +532,7 @@ def test_autotune_picks_a_configuration_and_results_stay_correct():
         qs.qs_plan_run(p, e, SEED, 0, h)
         got = qs.qs_get_state(h).reshape(batch, -1)
         qs.qs_plan_destroy(p)
-    np.testing.assert_allclose(got[1], oracle_traj(n, ops, 3, e, 1), atol=TOL[qs.QS_C64])
+    assert_amplitudes_close(got[1], oracle_traj(n, ops, 3, e, 1), qs.QS_C64)
     with Handle(n, 2, 0, qs.QS_STATEVEC, qs.QS_C128) as h:
         p = qs.qs_plan_create(h, pcirc.to_gates(ops))
         assert qs.qs_plan_configs(p, h) == (1, 1)

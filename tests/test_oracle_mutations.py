@@ -139,3 +139,45 @@ def test_mutation_unnormalised_entangled_state_is_caught(monkeypatch):
     monkeypatch.setattr(choi, "maximally_entangled", lambda n: orig(n) * 2.0 ** (n / 2))
     rho = choi.relative_state(2, inputs.qft_circuit(2), 0.1)
     assert abs(np.trace(rho) - 1.0) > 1e-3
+
+
+def _kat_fails(monkeypatch, **patch):
+    from oracle import philox
+    from tests.test_oracle_pins import philox_kat_vectors
+    for k, v in patch.items():
+        monkeypatch.setattr(philox, k, v)
+    return any(philox.philox4x32_10(c, k_) != w for c, k_, w in philox_kat_vectors())
+
+
+def test_swapped_philox_multipliers_are_caught_by_known_answers(monkeypatch):
+    from oracle import philox
+    assert _kat_fails(monkeypatch, PHILOX_M0=philox.PHILOX_M1, PHILOX_M1=philox.PHILOX_M0)
+
+
+def test_swapped_weyl_increments_are_caught_by_known_answers(monkeypatch):
+    from oracle import philox
+    assert _kat_fails(monkeypatch, PHILOX_W0=philox.PHILOX_W1, PHILOX_W1=philox.PHILOX_W0)
+
+
+def test_wrong_round_count_is_caught_by_known_answers(monkeypatch):
+    assert _kat_fails(monkeypatch, PHILOX_ROUNDS=7)
+
+
+def test_swapped_product_halves_are_caught_by_known_answers(monkeypatch):
+    # a round that takes lo(M c) where hi(M c) belongs (and vice versa)
+    from oracle import philox
+    M = philox.MASK32
+
+    def bad(counter, key):
+        c0, c1, c2, c3 = (int(x) & M for x in counter)
+        k0, k1 = (int(x) & M for x in key)
+        for rnd in range(10):
+            if rnd:
+                k0 = (k0 + philox.PHILOX_W0) & M
+                k1 = (k1 + philox.PHILOX_W1) & M
+            p0, p1 = philox.PHILOX_M0 * c0, philox.PHILOX_M1 * c2
+            c0, c1, c2, c3 = ((p1 & M) ^ c1 ^ k0, p1 >> 32, (p0 & M) ^ c3 ^ k1, p0 >> 32)
+        return c0, c1, c2, c3
+
+    from tests.test_oracle_pins import philox_kat_vectors
+    assert any(bad(c, k) != w for c, k, w in philox_kat_vectors())

@@ -346,6 +346,50 @@ def test_eq15_reduces_to_eq11_without_rotation():
 
 # ---------------------------------------------------------------- Philox
 
+GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden")
+
+
+def philox_kat_vectors():
+    """Known-answer vectors of Philox4x32-10 (tests/golden/philox4x32_10_kat.txt):
+    (counter[4], key[2], output[4]) as Python ints, from the generator's
+    publication (Salmon et al., SC'11, and its Random123 distribution)."""
+    out = []
+    with open(__import__("os").path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            w = [int(x, 16) for x in line.split()]
+            out.append((tuple(w[0:4]), tuple(w[4:6]), tuple(w[6:10])))
+    return out
+
+
+def test_philox_matches_published_known_answers():
+    kats = philox_kat_vectors()
+    assert len(kats) == 3
+    for ctr, key, want in kats:
+        assert philox.philox4x32_10(ctr, key) == want
+
+
+def test_philox_array_matches_published_known_answers():
+    kats = philox_kat_vectors()
+    cols = [np.array([k[0][i] for k in kats], dtype=np.uint64) for i in range(4)]
+    k0 = np.array([k[1][0] for k in kats], dtype=np.uint64)
+    k1 = np.array([k[1][1] for k in kats], dtype=np.uint64)
+    got = philox.philox4x32_10_array(*cols, k0, k1)
+    for i, (_, _, want) in enumerate(kats):
+        assert tuple(int(g[i]) for g in got) == want
+
+
+def test_noise_words_map_seed_traj_gate_onto_key_and_counter():
+    # counter = (traj lo, traj hi, gate lo, gate hi), key = (seed lo, seed hi):
+    # the third published vector, addressed through the noise draw
+    ctr, key, want = philox_kat_vectors()[2]
+    traj = ctr[0] | (ctr[1] << 32)
+    gate = ctr[2] | (ctr[3] << 32)
+    seed = key[0] | (key[1] << 32)
+    assert philox.noise_words(seed, traj, gate) == want
+
+
 def test_philox_vector_and_scalar_agree():
     trajs = np.array([0, 1, 2**32 - 1, 2**32 + 5, 12345678901])
     gids = np.array([0, 7, 2**32 + 1, 3, 99])
