@@ -250,6 +250,15 @@ qs_status qs_get_state_range(qs_handle h, size_t first, size_t count, double* ho
 /* FIXED_RANK: set the number of live columns after qs_set_state. */
 qs_status qs_set_rank_columns(qs_handle h, int m);
 
+/* Failure detection: every tile-copy wait of the fused passes polls its
+ * mbarrier at most `polls` times (default 2^22, restored by polls < 0;
+ * 0 gives up at once).  A pass whose wait gives up lets the copies it has in
+ * flight land (bounded by the default), records the failure in a device
+ * status word and returns; the next call that reads results (qs_fidelity,
+ * qs_plan_run_fidelity, ...) returns QS_ERR_TIMEOUT once, clears the word, and
+ * the handle stays usable.  Errors: INVALID_ARG for polls >= 2^32. */
+qs_status qs_set_wait_limit(qs_handle h, int64_t polls);
+
 /* --------------------------------------------------- Monte Carlo counters */
 
 /* STATEVEC: member b uses trajectory counter offset + b (default 0), so a
@@ -366,15 +375,19 @@ qs_status qs_debug_noise(uint64_t seed, uint64_t traj, uint64_t gate_id, int cou
  *   states  device pointer, `members` consecutive state vectors of 2^n
  *           complex elements of `dtype` (the STATEVEC layout), caller-owned.
  *   ref     device pointer, 2^n complex elements of `dtype`, caller-owned.
- *   out     host pointer, `members` doubles: |<ref|states_b>|^2, FP64
- *           accumulation across blocks as in qs_fidelity.
+ *   out     host pointer, `members` doubles: |<ref|states_b>|^2; every FP32
+ *           (complex64) partial sums at most 16 products before it joins an
+ *           FP64 sum, and blocks are added in FP64, as in qs_fidelity.
  *   cuda_stream  the stream the work is issued on (NULL = legacy stream);
  *           the call synchronises it before returning.
  * The call allocates nothing: its scratch is a fixed array of
  * 2 * QS_NOALLOC_MAX_PARTIALS + QS_NOALLOC_MAX_MEMBERS doubles (1.5 MiB) that
  * every GPU loading this library holds until the process exits.  The first
  * call on a device looks up that array's device address (cudaGetSymbolAddress
- * with the device current); make that first call before any stream capture.
+ * with the device current) and keeps it; make that first call before any
+ * stream capture.  The kept address belongs to the device's primary context:
+ * do not call this entry point after a cudaDeviceReset or from a context of
+ * the caller's own.
  * All calls on a device share the array: calls whose work overlaps on the GPU
  * (other streams, other host threads) race and must be serialised by the
  * caller.  Errors: INVALID_ARG for NULL pointers, n outside 1..40, members < 1

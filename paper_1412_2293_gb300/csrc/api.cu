@@ -270,8 +270,12 @@ qs_status read_results(qs_ctx* h, double* out, int count) {
   QS_CUDA(h, cudaStreamSynchronize(h->stream));
   int status[4] = {0, 0, 0, 0};
   QS_CUDA(h, cudaMemcpy(status, h->dstatus, sizeof(status), cudaMemcpyDeviceToHost));
-  if (status[2] != 0) return fail(h, QS_ERR_TIMEOUT, "a fused pass timed out waiting for a tile copy");
-  if (status[3] != 0) return fail(h, QS_ERR_TIMEOUT, "a tensor-core block timed out waiting for its MMAs");
+  if (status[2] != 0 || status[3] != 0) {
+    // reported once: the words are cleared so the handle's next run starts clean
+    QS_CUDA(h, cudaMemset(h->dstatus + 2, 0, 2 * sizeof(int)));
+    return fail(h, QS_ERR_TIMEOUT, status[2] != 0 ? "a fused pass timed out waiting for a tile copy"
+                                                  : "a tensor-core block timed out waiting for its MMAs");
+  }
   if (h->mode == QS_FIXED_RANK && status[1] != 0)
     return fail(h, QS_ERR_CUDA, status[1] == 1 ? "eigensolver did not converge" : "tie-cluster basis incomplete");
   return QS_OK;
@@ -820,6 +824,13 @@ qs_status qs_set_rank_columns(qs_handle h, int m) {
   return QS_OK;
 }
 
+qs_status qs_set_wait_limit(qs_handle h, int64_t polls) {
+  if (!h) return QS_ERR_INVALID_ARG;
+  if (polls > 0xffffffffll) return fail(h, QS_ERR_INVALID_ARG, "wait limit above 2^32 - 1 polls");
+  h->wait_polls = polls < 0 ? -1 : polls;
+  return QS_OK;
+}
+
 qs_status qs_set_trajectory_offset(qs_handle h, uint64_t offset) {
   if (!h) return QS_ERR_INVALID_ARG;
   h->traj_offset = offset;
@@ -832,8 +843,11 @@ qs_status qs_set_member_noise(qs_handle h, const double* e, const uint64_t* seed
   if (h->mode != QS_STATEVEC) return fail(h, QS_ERR_NOT_SUPPORTED, "per-member noise needs STATEVEC");
   if (!e && !seed && !traj && !marked) { h->member_noise = false; h->member_marked = false; return QS_OK; }
   if (!e || !seed || !traj) return fail(h, QS_ERR_INVALID_ARG, "e, seed and traj must all be given");
-  for (int b = 0; b < h->batch; ++b)
+  double e_max = 0.0;
+  for (int b = 0; b < h->batch; ++b) {
     if (!(e[b] >= 0.0) || !std::isfinite(e[b])) return fail(h, QS_ERR_INVALID_ARG, "e must be finite and >= 0");
+    e_max = std::max(e_max, e[b]);
+  }
   const size_t B = h->batch;
   if (!h->m_e) QS_CUDA(h, cudaMalloc((void**)&h->m_e, B * sizeof(double)));
   if (!h->m_seed) QS_CUDA(h, cudaMalloc((void**)&h->m_seed, B * sizeof(uint64_t)));
@@ -842,6 +856,7 @@ qs_status qs_set_member_noise(qs_handle h, const double* e, const uint64_t* seed
   QS_CUDA(h, cudaMemcpyAsync(h->m_seed, seed, B * sizeof(uint64_t), cudaMemcpyHostToDevice, h->stream));
   QS_CUDA(h, cudaMemcpyAsync(h->m_traj, traj, B * sizeof(uint64_t), cudaMemcpyHostToDevice, h->stream));
   h->member_noise = true;
+  h->m_e_max = e_max;
   if (marked) {
     for (int b = 0; b < h->batch; ++b)
       if (marked[b] >= (1ull << h->n)) return fail(h, QS_ERR_INVALID_ARG, "marked index out of range");

@@ -107,6 +107,8 @@ struct qs_ctx {
   uint64_t* m_marked = nullptr;
   bool member_noise = false;
   bool member_marked = false;
+  double m_e_max = 0.0;                  // largest per-member e (host copy)
+  int64_t wait_polls = -1;               // fused passes' tile-copy wait limit (-1: the default)
 
   // stored fidelity reference (2^n complex in the handle's dtype)
   void* ref = nullptr;

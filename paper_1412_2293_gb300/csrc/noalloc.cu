@@ -12,10 +12,18 @@
 // a stand-in, so host code never passes it to a kernel: the first call on a
 // device looks up the array's device address with cudaGetSymbolAddress (with
 // that device current) and caches it; later calls on that device reuse it.
-// All calls on a device share the array and it keeps the last call's
-// contents; each call overwrites every partial it reads, so nothing needs
-// clearing, but two calls whose work overlaps on the GPU (different streams,
-// or different host threads) race on the array.
+// The cached address belongs to the device's primary context as it was at
+// that first call: a caller that resets the device (cudaDeviceReset) or runs
+// in a context of its own must not use this entry point afterwards.  All
+// calls on a device share the array and it keeps the last call's contents;
+// each call overwrites every partial it reads, so nothing needs clearing, but
+// two calls whose work overlaps on the GPU (different streams, or different
+// host threads) race on the array.
+//
+// Precision: each thread sums at most kNaTerms products in the state's
+// precision, then adds that partial to an FP64 sum; blocks and chunks are
+// added in FP64 in a fixed order, so the rounding of a complex64 fidelity
+// does not grow with the number of amplitudes a block covers.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -25,13 +33,12 @@
 namespace {
 
 constexpr int kNaBlock = 256;
+constexpr int kNaTerms = 16;             // products per FP32 partial before it joins the FP64 sum
 constexpr int kNaMaxDevices = 64;
 
 // partials: 2 doubles per (member, chunk); results: 1 double per member
 static __device__ __align__(256) double g_noalloc_scratch[2 * QS_NOALLOC_MAX_PARTIALS + QS_NOALLOC_MAX_MEMBERS];
 
-std::mutex g_na_mutex;
-double* g_na_ptr[kNaMaxDevices] = {nullptr};
 
 __device__ __forceinline__ double na_warp_sum(double v) {
 #pragma unroll
@@ -50,13 +57,19 @@ __global__ void __launch_bounds__(kNaBlock) k_na_dot(const qs::cplx<R>* __restri
   const uint64_t beg = (uint64_t)c * chunk;
   const uint64_t end = beg + chunk < N ? beg + chunk : N;
   const qs::cplx<R>* p = psi + (uint64_t)b * N;
-  R re = 0, im = 0;
-  for (uint64_t x = beg + threadIdx.x; x < end; x += blockDim.x) {
-    const qs::cplx<R> a = p[x], r = ref[x];
-    re += r.x * a.x + r.y * a.y;
-    im += r.x * a.y - r.y * a.x;
+  double dre = 0.0, dim = 0.0;
+  for (uint64_t x = beg + threadIdx.x; x < end;) {
+    R re = 0, im = 0;
+    for (int k = 0; k < kNaTerms && x < end; ++k, x += blockDim.x) {
+      const qs::cplx<R> a = p[x], r = ref[x];
+      re += r.x * a.x + r.y * a.y;
+      im += r.x * a.y - r.y * a.x;
+    }
+    dre += (double)re;
+    dim += (double)im;
   }
-  double dre = na_warp_sum((double)re), dim = na_warp_sum((double)im);
+  dre = na_warp_sum(dre);
+  dim = na_warp_sum(dim);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (l == 0) { sre[w] = dre; sim[w] = dim; }
   __syncthreads();
@@ -84,6 +97,9 @@ __global__ void k_na_finalize(const double* __restrict__ partials, int members, 
   }
   results[b] = re * re + im * im;
 }
+
+std::mutex g_na_mutex;
+double* g_na_ptr[kNaMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device (set up once).
 cudaError_t na_scratch(double** out) {

@@ -112,6 +112,13 @@ struct PassArgs {
   // there: per member, diag_off (R units) holds ratio_j = d_j / a_j for each
   // window bit j and the overall scale prod_j a_j; -1 when the pass has none
   int diag_off;
+  // 1: the real gates carry a third shear (see dense_real_reg); only the
+  // interpreted kernels (PROG = 0) run with it
+  int stable;
+  // polls of a tile-copy wait before the pass gives up (kSpinLimit unless the
+  // handle sets another); the clean-up waits of a pass that gave up always
+  // take kSpinLimit
+  uint32_t spin_limit;
 };
 
 // ---------------------------------------------------------------- async copies
@@ -127,10 +134,11 @@ __device__ __forceinline__ void mbar_fence_init() {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-// Bounded wait for the phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for the phase with the given parity: at most `limit` polls;
+// false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = kSpinLimit) {
   const uint32_t a = smem_u32(bar);
-  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+  for (uint32_t i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -227,8 +235,30 @@ __device__ __forceinline__ void butterfly_fact(cplx<R>& x0, cplx<R>& x1, R r0, R
 }
 
 template <typename R, int RJ>
-__device__ __forceinline__ void dense_reg(cplx<R> (&a)[kAmps], const R* m, bool real) {
+__device__ __forceinline__ void dense_real_reg(cplx<R> (&a)[kAmps], const R* m);
+template <typename R, int RJ>
+__device__ __forceinline__ void third_shear_reg(cplx<R> (&a)[kAmps], const R* m);
+
+template <typename R, int RJ>
+__device__ __forceinline__ void dense_reg(cplx<R> (&a)[kAmps], const R* m, bool real, bool stable) {
   if (real) {
+    dense_real_reg<R, RJ>(a, m);
+    if (stable) third_shear_reg<R, RJ>(a, m);
+  } else {
+    const cplx<R> u00 = ld_c(m), u01 = ld_c(m + 2), u10 = ld_c(m + 4), u11 = ld_c(m + 6);
+#pragma unroll
+    for (int r = 0; r < kAmps; ++r) {
+      if (r & (1 << RJ)) continue;
+      const cplx<R> x0 = a[r], x1 = a[r | (1 << RJ)];
+      a[r] = pfma<R>(u01, x1, pmul<R>(u00, x0));
+      a[r | (1 << RJ)] = pfma<R>(u11, x1, pmul<R>(u10, x0));
+    }
+  }
+}
+
+template <typename R, int RJ>
+__device__ __forceinline__ void dense_real_reg(cplx<R> (&a)[kAmps], const R* m) {
+  {
     // stored as (r0, r0, s1, s1): the broadcast pairs of the packed FMA come
     // straight from one 16-byte load (complex64)
     if constexpr (sizeof(R) == 4) {
@@ -248,14 +278,31 @@ __device__ __forceinline__ void dense_reg(cplx<R> (&a)[kAmps], const R* m, bool 
         butterfly_fact<R>(a[r], a[r | (1 << RJ)], r0, s1);
       }
     }
-  } else {
-    const cplx<R> u00 = ld_c(m), u01 = ld_c(m + 2), u10 = ld_c(m + 4), u11 = ld_c(m + 6);
+  }
+}
+
+// The third shear x0 += w x1 of the pivoted form of a real gate (stored as
+// (w, w) after the first two; w = 0 for members whose gate takes the
+// two-shear form).  A gate whose M00 is small against its first column (a
+// bit flip, a rotation near pi) is factored as diag(d0, d1) [[1, w], [0, 1]]
+// [[1, 0], [1, 1]] [[1, p], [0, 1]] with the pivot on M10, so no factor is
+// large.
+template <typename R, int RJ>
+__device__ __forceinline__ void third_shear_reg(cplx<R> (&a)[kAmps], const R* m) {
+  if constexpr (sizeof(R) == 4) {
+    const float2 w = __ldg(reinterpret_cast<const float2*>(m + 4));
 #pragma unroll
     for (int r = 0; r < kAmps; ++r) {
       if (r & (1 << RJ)) continue;
-      const cplx<R> x0 = a[r], x1 = a[r | (1 << RJ)];
-      a[r] = pfma<R>(u01, x1, pmul<R>(u00, x0));
-      a[r | (1 << RJ)] = pfma<R>(u11, x1, pmul<R>(u10, x0));
+      a[r] = fma2(w, a[r | (1 << RJ)], a[r]);
+    }
+  } else {
+    const R w = __ldg(m + 4);
+#pragma unroll
+    for (int r = 0; r < kAmps; ++r) {
+      if (r & (1 << RJ)) continue;
+      a[r].x = fma(w, a[r | (1 << RJ)].x, a[r].x);
+      a[r].y = fma(w, a[r | (1 << RJ)].y, a[r].y);
     }
   }
 }
@@ -269,7 +316,7 @@ __device__ __forceinline__ void dwin_reg(cplx<R> (&a)[kAmps], const R* T, int tb
   // factor is consumed right after its load (few live registers)
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    const int idx = STAGE_A ? (tbits | (q << 5)) : q;
+    const int idx = STAGE_A ? (tbits + (q << 5)) : q;   // tbits < 32
     const cplx<R> f = ld_c(T + 2 * idx);
 #pragma unroll
     for (int hi = 0; hi < kAmps / (2 * Q); ++hi) {
@@ -334,26 +381,53 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 // ---------------------------------------------------------------- segments
 template <typename R, int J, bool SA>
-__device__ __forceinline__ void seg_step(cplx<R> (&a)[kAmps], const Seg& sg, const R* P, int tbits) {
-  if ((sg.dense >> J) & 1) dense_reg<R, J>(a, P + sg.doff[J], (sg.real >> J) & 1);
+__device__ __forceinline__ void seg_step(cplx<R> (&a)[kAmps], const Seg& sg, const R* P, int tbits, bool stable) {
+  if ((sg.dense >> J) & 1) dense_reg<R, J>(a, P + sg.doff[J], (sg.real >> J) & 1, stable);
   if ((sg.dwin >> J) & 1) dwin_reg<R, J, SA>(a, P + sg.woff[J], tbits);
 }
 
 template <typename R, bool SA>
-__device__ __forceinline__ void run_seg(cplx<R> (&a)[kAmps], const Seg& sg, const R* P, int tbits) {
+__device__ __forceinline__ void run_seg(cplx<R> (&a)[kAmps], const Seg& sg, const R* P, int tbits, bool stable) {
   if (sg.desc) {
-    seg_step<R, 4, SA>(a, sg, P, tbits);
-    seg_step<R, 3, SA>(a, sg, P, tbits);
-    seg_step<R, 2, SA>(a, sg, P, tbits);
-    seg_step<R, 1, SA>(a, sg, P, tbits);
-    seg_step<R, 0, SA>(a, sg, P, tbits);
+    seg_step<R, 4, SA>(a, sg, P, tbits, stable);
+    seg_step<R, 3, SA>(a, sg, P, tbits, stable);
+    seg_step<R, 2, SA>(a, sg, P, tbits, stable);
+    seg_step<R, 1, SA>(a, sg, P, tbits, stable);
+    seg_step<R, 0, SA>(a, sg, P, tbits, stable);
   } else {
-    seg_step<R, 0, SA>(a, sg, P, tbits);
-    seg_step<R, 1, SA>(a, sg, P, tbits);
-    seg_step<R, 2, SA>(a, sg, P, tbits);
-    seg_step<R, 3, SA>(a, sg, P, tbits);
-    seg_step<R, 4, SA>(a, sg, P, tbits);
+    seg_step<R, 0, SA>(a, sg, P, tbits, stable);
+    seg_step<R, 1, SA>(a, sg, P, tbits, stable);
+    seg_step<R, 2, SA>(a, sg, P, tbits, stable);
+    seg_step<R, 3, SA>(a, sg, P, tbits, stable);
+    seg_step<R, 4, SA>(a, sg, P, tbits, stable);
   }
+}
+
+// Compile-time programs.  The common pass -- a layer of real one-qubit gates
+// on every register bit of stage A, descending, each followed by its phase
+// table where the program has one, then the same on stage B -- runs as
+// straight-line code: no per-step branches or segment-table lookups, so the
+// compiler schedules the table loads of a step ahead of the work before it.
+// PROG = 0: the segment list is interpreted (any program).  Otherwise bit 10
+// is set, bits 0..4 hold the phase-table mask of stage A and bits 5..9 that
+// of stage B; the planner picks it only for a program of exactly that shape
+// (two descending segments A then B, all five gates real, no flips).
+constexpr int kProgLayers = 1 << 10;
+constexpr int prog_layers(int dwin_a, int dwin_b) { return kProgLayers | dwin_a | (dwin_b << 5); }
+
+template <typename R, bool SA, int W, int J>
+__device__ __forceinline__ void layer_step(cplx<R> (&a)[kAmps], const Seg& sg, const R* P, int tbits) {
+  dense_real_reg<R, J>(a, P + sg.doff[J]);
+  if constexpr (((W >> J) & 1) != 0) dwin_reg<R, J, SA>(a, P + sg.woff[J], tbits);
+}
+
+template <typename R, bool SA, int W>
+__device__ __forceinline__ void run_layer(cplx<R> (&a)[kAmps], const Seg& sg, const R* P, int tbits) {
+  layer_step<R, SA, W, 4>(a, sg, P, tbits);
+  layer_step<R, SA, W, 3>(a, sg, P, tbits);
+  layer_step<R, SA, W, 2>(a, sg, P, tbits);
+  layer_step<R, SA, W, 1>(a, sg, P, tbits);
+  layer_step<R, SA, W, 0>(a, sg, P, tbits);
 }
 
 // ---------------------------------------------------------------- LOW pass
@@ -384,7 +458,7 @@ __device__ __forceinline__ int exchange_count(const PassArgs& A, int stage, bool
 }
 
 
-template <typename R, int WARPS, int NBUF>
+template <typename R, int WARPS, int NBUF, int PROG = 0>
 __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict__ psi, const __grid_constant__ PassArgs A) {
   static_assert(NBUF == 1 || NBUF == 2, "one or two tile buffers");
   using C = cplx<R>;
@@ -454,13 +528,25 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
     if (A.synth) {
       // the one amplitude equal to 1: register (x >> 5) & 31 of lane x & 31
       const uint64_t x = A.basis ? A.basis[member] : A.basis0[0];
-      const uint32_t hot = ((x & ~1023ull) == mloc && (int)(x & 31) == lane) ? 1u << ((x >> 5) & 31) : 0u;
 #pragma unroll
-      for (int r = 0; r < kAmps; ++r) a[r] = mk<R>((hot >> r) & 1u ? R(1) : R(0), R(0));
+      for (int r = 0; r < kAmps; ++r) a[r] = mk<R>(R(0), R(0));
+      if ((x & ~1023ull) == mloc && (int)(x & 31) == lane) {
+        const int hr = (int)((x >> 5) & 31);
+#pragma unroll
+        for (int r = 0; r < kAmps; ++r)
+          if (r == hr) a[r].x = R(1);
+      }
     } else {
-      if (!mbar_wait(&bars[warp][cur], parity)) {
+      // the warp gives up together (a lane that saw the copy land follows
+      // one that did not), after its copies in flight have landed: the
+      // block's shared memory must outlive them
+      if (__any_sync(0xffffffffu, !mbar_wait(&bars[warp][cur], parity, A.spin_limit))) {
         report_timeout(A.status);
-        if (NBUF == 2 && lane == 0 && in_flight > 1) mbar_wait(&bars[warp][cur ^ 1], ((it + 1) >> 1) & 1);
+        if (lane == 0) {
+          mbar_wait(&bars[warp][cur], parity);
+          if (NBUF == 2 && in_flight > 1) mbar_wait(&bars[warp][cur ^ 1], ((it + 1) >> 1) & 1);
+        }
+        __syncwarp();
         return;
       }
       if (lane == 0) --in_flight;
@@ -469,28 +555,39 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
       if constexpr (NBUF == 1) { ++reads_left; release(); }   // counts the first read
     }
     int stage = 0;
-    for (int si = 0; si < A.nseg; ++si) {
+    // register exchange A -> B (to_b) or B -> A in place in the tile buffer
+    auto exchange = [&](bool to_b) {
+      __syncwarp();
+      if (to_b) {
+#pragma unroll
+        for (int r = 0; r < kAmps; ++r) cbuf[lane + 33 * r] = a[r];
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < kAmps; ++r) a[r] = cbuf[r + 33 * lane];
+      } else {
+#pragma unroll
+        for (int r = 0; r < kAmps; ++r) cbuf[r + 33 * lane] = a[r];
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < kAmps; ++r) a[r] = cbuf[lane + 33 * r];
+      }
+    };
+    if constexpr (PROG != 0) {
+      run_layer<R, true, PROG & 31>(a, A.segs[0], P, lane);
+      exchange(true);
+      stage = 1;
+      release();
+      run_layer<R, false, (PROG >> 5) & 31>(a, A.segs[1], P, 0);
+    }
+    for (int si = 0; si < (PROG != 0 ? 0 : A.nseg); ++si) {
       const Seg& sg = A.segs[si];
       if (sg.stage != stage) {
-        __syncwarp();
-        if (stage == 0) {
-#pragma unroll
-          for (int r = 0; r < kAmps; ++r) cbuf[lane + 33 * r] = a[r];
-          __syncwarp();
-#pragma unroll
-          for (int r = 0; r < kAmps; ++r) a[r] = cbuf[r + 33 * lane];
-        } else {
-#pragma unroll
-          for (int r = 0; r < kAmps; ++r) cbuf[r + 33 * lane] = a[r];
-          __syncwarp();
-#pragma unroll
-          for (int r = 0; r < kAmps; ++r) a[r] = cbuf[lane + 33 * r];
-        }
+        exchange(stage == 0);
         stage ^= 1;
         release();
       }
-      if (stage == 0) run_seg<R, true>(a, sg, P, lane);
-      else run_seg<R, false>(a, sg, P, 0);
+      if (stage == 0) run_seg<R, true>(a, sg, P, lane, A.stable != 0);
+      else run_seg<R, false>(a, sg, P, 0, A.stable != 0);
       for (int f = 0; f < sg.nflip; ++f) {
         const Flip fl = A.flips[sg.flip0 + f];
         const uint64_t w = fl.per_member ? A.marked[member] : fl.index;
@@ -521,12 +618,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
       apply_real_product<R>(a, c, t5);
     }
     if (stage == 1) {
-      __syncwarp();
-#pragma unroll
-      for (int r = 0; r < kAmps; ++r) cbuf[r + 33 * lane] = a[r];
-      __syncwarp();
-#pragma unroll
-      for (int r = 0; r < kAmps; ++r) a[r] = cbuf[lane + 33 * r];
+      exchange(false);
       release();
     }
     if (A.fid) {
@@ -571,7 +663,7 @@ __device__ __forceinline__ int high_idx(int x, int col) {
   return (x + (x >> 5)) * (1 << COLB) + col;
 }
 
-template <typename R, int COLB, int NBUF, bool WIDE = false>
+template <typename R, int COLB, int NBUF, bool WIDE = false, int PROG = 0>
 __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / HighShape<COLB>::WARPS : 1)
     k_pass_high(cplx<R>* __restrict__ psi, const __grid_constant__ CUtensorMap tmap, const __grid_constant__ PassArgs A) {
   static_assert(NBUF == 1 || NBUF == 2, "one or two tile buffers");
@@ -666,17 +758,26 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
     int stage = A.start_stage;
     if (A.synth) {
       // the one amplitude equal to 1: register (x >> sh) & 31 of the thread
-      // whose other bits match
+      // whose other bits match (one thread of the member's whole state)
       const uint64_t x = A.basis ? A.basis[member] : A.basis0[0];
       const Off fixed = tbits | (Off)col | (stage == 0 ? offa : offb);
       const int sh = stage == 0 ? sha : shb;
-      const uint32_t hot = (x & ~(31ull << sh)) == (uint64_t)fixed ? 1u << ((x >> sh) & 31) : 0u;
 #pragma unroll
-      for (int r = 0; r < kAmps; ++r) a[r] = mk<R>((hot >> r) & 1u ? R(1) : R(0), R(0));
+      for (int r = 0; r < kAmps; ++r) a[r] = mk<R>(R(0), R(0));
+      if ((x & ~(31ull << sh)) == (uint64_t)fixed) {
+        const int hr = (int)((x >> sh) & 31);
+#pragma unroll
+        for (int r = 0; r < kAmps; ++r)
+          if (r == hr) a[r].x = R(1);
+      }
     } else {
-      if (!mbar_wait(&bars[cur], parity)) {
+      // the block gives up together, after its copies in flight have landed
+      if (__syncthreads_or(!mbar_wait(&bars[cur], parity, A.spin_limit))) {
         report_timeout(A.status);
-        if (NBUF == 2 && threadIdx.x == 0 && in_flight > 1) mbar_wait(&bars[cur ^ 1], ((it + 1) >> 1) & 1);
+        if (threadIdx.x == 0) {
+          mbar_wait(&bars[cur], parity);
+          if (NBUF == 2 && in_flight > 1) mbar_wait(&bars[cur ^ 1], ((it + 1) >> 1) & 1);
+        }
         return;
       }
       if (threadIdx.x == 0) --in_flight;
@@ -690,28 +791,39 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
       }
       if constexpr (NBUF == 1) { ++reads_left; release(); }   // counts the first read
     }
-    for (int si = 0; si < A.nseg; ++si) {
+    // register exchange A -> B (to_b) or B -> A in place in the tile buffer
+    auto exchange = [&](bool to_b) {
+      __syncthreads();
+      if (to_b) {
+#pragma unroll
+        for (int r = 0; r < kAmps; ++r) sm[high_idx<COLB>(xa | (r << 5), col)] = a[r];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kAmps; ++r) a[r] = sm[high_idx<COLB>(r | xb, col)];
+      } else {
+#pragma unroll
+        for (int r = 0; r < kAmps; ++r) sm[high_idx<COLB>(r | xb, col)] = a[r];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kAmps; ++r) a[r] = sm[high_idx<COLB>(xa | (r << 5), col)];
+      }
+    };
+    if constexpr (PROG != 0) {              // the planner guarantees start stage A
+      run_layer<R, true, PROG & 31>(a, A.segs[0], P, xa);
+      exchange(true);
+      stage = 1;
+      release();
+      run_layer<R, false, (PROG >> 5) & 31>(a, A.segs[1], P, 0);
+    }
+    for (int si = 0; si < (PROG != 0 ? 0 : A.nseg); ++si) {
       const Seg& sg = A.segs[si];
       if (sg.stage != stage) {
-        __syncthreads();
-        if (stage == 0) {
-#pragma unroll
-          for (int r = 0; r < kAmps; ++r) sm[high_idx<COLB>(xa | (r << 5), col)] = a[r];
-          __syncthreads();
-#pragma unroll
-          for (int r = 0; r < kAmps; ++r) a[r] = sm[high_idx<COLB>(r | xb, col)];
-        } else {
-#pragma unroll
-          for (int r = 0; r < kAmps; ++r) sm[high_idx<COLB>(r | xb, col)] = a[r];
-          __syncthreads();
-#pragma unroll
-          for (int r = 0; r < kAmps; ++r) a[r] = sm[high_idx<COLB>(xa | (r << 5), col)];
-        }
+        exchange(stage == 0);
         stage ^= 1;
         release();
       }
-      if (stage == 0) run_seg<R, true>(a, sg, P, xa);
-      else run_seg<R, false>(a, sg, P, 0);
+      if (stage == 0) run_seg<R, true>(a, sg, P, xa, A.stable != 0);
+      else run_seg<R, false>(a, sg, P, 0, A.stable != 0);
       for (int f = 0; f < sg.nflip; ++f) {
         const Flip fl = A.flips[sg.flip0 + f];
         const uint64_t w = fl.per_member ? A.marked[member] : fl.index;
@@ -765,9 +877,13 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
         A.fid_partials[2 * slot + 1] = ti;
       }
     }
-    C* out = psi + (member << A.n) + fixed;
+    // register r goes to fixed + r 2^sh: a running 32-bit offset (64-bit for
+    // WIDE) from the member's base instead of a shift and a 64-bit add each
+    C* out = psi + (member << A.n);
+    Off o = fixed;
+    const Off step = (Off)1 << sh;
 #pragma unroll
-    for (int r = 0; r < kAmps; ++r) out[(Off)r << sh] = a[r];
+    for (int r = 0; r < kAmps; ++r, o += step) out[o] = a[r];
     __syncthreads();
   }
 }

@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
                                                     const Producer* __restrict__ prods, int num_prods,
                                                     const Contrib* __restrict__ contribs, int num_contribs,
                                                     int num_dwin, int num_dense, int diag_off, NoiseSrc src,
-                                                    const RunParams* rp) {
+                                                    const RunParams* rp, int stable) {
   extern __shared__ double2 pre_sm[];                   // [num_contribs] factors, then [num_dwin][10]
   const int b = blockIdx.x;
   double e;
@@ -181,10 +181,8 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
   member_noise(src, rp, b, &e, &seed, &traj);
   R* out = params + (uint64_t)b * stride;
   // noisy 2x2 matrices of the dense gates, all threads in parallel, into
-  // shared memory (FP64, [slot][4] complex after the tables' scratch).  A
-  // real gate M is stored as the quantities its factored form needs (see the
-  // chain below): u = M01 / M00, v = M10 M00 / det, w = det / M00^2, 1 / w
-  // and M00 (a pivot below min_pivot is replaced by that value).
+  // shared memory (FP64, [slot][4] complex after the tables' scratch; a real
+  // gate as (M00, M01), (M10, M11)), factored by the chain below.
   double2* dmat = pre_sm + num_contribs + (size_t)num_dwin * kWin + (1u << (kWin - 1));
   for (int i = threadIdx.x; i < num_prods; i += blockDim.x) {
     const Producer p = prods[i];
@@ -194,14 +192,8 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
     noisy_matrix<R>(g, e, seed, traj, rp->gate_id0 + g.gate_pos, m);
     double2* slot = dmat + p.contrib_start * 4;
     if (p.real) {
-      const double mp = min_pivot<R>();
-      double a = m[0];
-      if (fabs(a) < mp) a = a < 0.0 ? -mp : mp;
-      double d2 = m[6] - m[4] * m[2] / a;               // det / M00
-      if (fabs(d2) < mp) d2 = d2 < 0.0 ? -mp : mp;
-      slot[0] = make_double2(m[2] / a, m[4] / d2);      // u, v
-      slot[1] = make_double2(d2 / a, a / d2);           // w, 1 / w
-      slot[2] = make_double2(a, 0.0);                   // M00
+      slot[0] = make_double2(m[0], m[2]);
+      slot[1] = make_double2(m[4], m[6]);
     } else {
       for (int q = 0; q < 4; ++q) slot[q] = make_double2(m[2 * q], m[2 * q + 1]);
     }
@@ -227,31 +219,54 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
     }
   }
   // dense gates: one thread per window bit walks that bit's gates in circuit
-  // order.  A real gate M' = M diag(pa, pd) = [[a, b], [c, d]] (the diagonal
-  // left by the previous real gate on the bit) is stored as the two shears of
-  // M' = diag(a, det'/a) [[1, 0], [s1, 1]] [[1, r0], [0, 1]], r0 = b / a,
-  // s1 = c a / det', and diag(a, det'/a) is carried on.  With rho = pd / pa
-  // this is r0 = u rho, s1 = v / rho, new pa = pa M00, new rho = rho w (u, v,
-  // w, M00 of M from above): products only.  A complex gate absorbs the
-  // carried diagonal.  What is left at the end goes to the diag block.
+  // order.  The diagonal diag(pa, pd) = pa diag(1, rho) left by the previous
+  // real gate on the bit is carried into the next one: pa joins the overall
+  // scale and a real gate M becomes M' = M diag(1, rho) = [[a, b], [c, d]],
+  // factored as diag(d0, d1) [[1, w], [0, 1]] [[1, 0], [q, 1]] [[1, p], [0, 1]]
+  // (the kernel: x0 += p x1, x1 += q x0, x0 += w x1), and diag(d0, d1) is
+  // carried on.  Pivot on a = M'00 (w = 0: d0 = a, p = b / a, d1 = det'/a,
+  // q = c / d1) while |a| >= |column 0| / 4; otherwise (stable runs only) on
+  // c (q = 1: d1 = c, p = d / c - 1, d0 = det'/c, w = a c / det' - 1), where
+  // no factor exceeds about 4 for an orthogonal M.  Runs that are not stable
+  // always take the first form (the host checks that the pivot stays large).
+  // A complex gate absorbs the carried diagonal.  What is left at the end
+  // goes to the diag block.
   __shared__ double pivot_a[kWin];
   if (threadIdx.x >= kPhaseThreads) {
     const int J = threadIdx.x - kPhaseThreads;
-    double pa = 1.0, rho = 1.0, rho_inv = 1.0;
+    double pa = 1.0, rho = 1.0;
     for (int i = 0; i < num_prods; ++i) {
       const Producer p = prods[i];
       if (p.kind != PD_DENSE || p.j != J) continue;
       const double2* slot = dmat + p.contrib_start * 4;
       if (p.real) {
-        const double2 uv = slot[0], ww = slot[1];
-        const R r0 = (R)(uv.x * rho), s1 = (R)(uv.y * rho_inv);
-        out[p.off] = r0;                                // (r0, r0, s1, s1)
-        out[p.off + 1] = r0;
-        out[p.off + 2] = s1;
-        out[p.off + 3] = s1;
-        pa *= slot[2].x;
-        rho *= ww.x;
-        rho_inv *= ww.y;
+        const double mp = min_pivot<R>();
+        auto clamp = [mp](double x) { return fabs(x) < mp ? (x < 0.0 ? -mp : mp) : x; };
+        const double a = slot[0].x, b = slot[0].y * rho, c = slot[1].x, d = slot[1].y * rho;
+        const double det = a * d - b * c;
+        double fp, fq, fw, d0, d1;
+        if (!stable || fabs(a) >= 0.25 * sqrt(a * a + c * c)) {
+          d0 = clamp(a);
+          d1 = clamp(det / d0);
+          fp = b / d0;
+          fq = c / d1;
+          fw = 0.0;
+        } else {
+          d1 = clamp(c);
+          const double dt = clamp(det);
+          fp = d / d1 - 1.0;
+          d0 = dt / d1;
+          fq = 1.0;
+          fw = a * d1 / dt - 1.0;
+        }
+        out[p.off] = (R)fp;                             // (p, p, q, q, w, w)
+        out[p.off + 1] = (R)fp;
+        out[p.off + 2] = (R)fq;
+        out[p.off + 3] = (R)fq;
+        out[p.off + 4] = (R)fw;
+        out[p.off + 5] = (R)fw;
+        pa *= d0;
+        rho = d1 / d0;
       } else {
         const double pd = rho * pa;
         for (int q = 0; q < 4; ++q) {
@@ -261,7 +276,7 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
           out[p.off + 2 * q + 1] = (R)(v.y * sc);
         }
         pa = 1.0;
-        rho = rho_inv = 1.0;
+        rho = 1.0;
       }
     }
     pivot_a[J] = pa;
@@ -427,6 +442,7 @@ struct PassPlan {
   std::vector<int> other;
   int tile_shift = 0;             // log2(tiles per member)
   std::vector<Seg> segs;          // the ops in canonical segments (what the kernels run)
+  int prog = 0;                   // compile-time program of the pass kernel (0: interpreted)
   std::vector<Flip> flips;
   CUtensorMap tmap;               // HIGH: [members * 2^(n-c) rows][2^c columns] (c = win[0]), boxes of 2^colb columns
   CUtensorMap tmap4;              // HIGH complex64: the same with boxes of 4 columns (configuration 2)
@@ -464,10 +480,14 @@ struct qs_plan_s {
   RunParams* h_run = nullptr;     // pinned
   // captured graphs, one per run variant: start (0 loaded, 1 one basis state,
   // 2 per-member basis states) x fused fidelity (0, 1)
-  cudaGraphExec_t exec[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  bool graph_member_noise[6] = {false, false, false, false, false, false};
-  bool graph_member_marked[6] = {false, false, false, false, false, false};
-  bool graph_timing[6] = {false, false, false, false, false, false};
+  // (x 2: real gates in the two-shear form, or pivoted with a third shear)
+  static constexpr int kVariants = 12;
+  cudaGraphExec_t exec[kVariants] = {};
+  bool graph_member_noise[kVariants] = {};
+  bool graph_member_marked[kVariants] = {};
+  bool graph_timing[kVariants] = {};
+  int64_t graph_wait_polls[kVariants] = {};
+  int stable = 0;                 // the running variant: 1 = pivoted real gates
   double* d_fid = nullptr;        // fused-fidelity partials [member][tile] complex
   void* d_params = nullptr;       // per-member gate parameters of the running pass (shared by the passes)
   void* d_alpha = nullptr;        // out factors of the running pass (shared by the passes)
@@ -484,6 +504,16 @@ struct qs_plan_s {
 };
 
 namespace {
+
+// Largest |xi| the noise draw can produce: Box-Muller of a uniform no
+// smaller than 2^-54 gives sqrt(-2 ln 2^-54) = 8.65.
+constexpr double kXiMax = 8.7;
+
+// True when every member is certain to keep the two-shear form of every real
+// one-qubit gate of the plan: |M00| >= |column 0| / 4 for M = U V_noise(theta),
+// |theta| <= e_max kXiMax (rotation noise acting first), bounded from U alone:
+// |M00| >= |U00| cos(theta) - |U01| sin(theta) and |column 0| <= |U|_F.
+bool two_shear_safe(const std::vector<struct PGate>& gates, double e_max);
 
 qs_status pfail(qs_plan p, qs_status st, const std::string& m) {
   if (p && p->h) p->h->err = m;
@@ -526,6 +556,21 @@ bool commute(const PGate& a, const PGate& b) {
 }
 
 int stage_of(int j) { return j >= 5 ? 0 : 1; }
+
+bool two_shear_safe(const std::vector<PGate>& gates, double e_max) {
+  for (const PGate& g : gates) {
+    if (!g.dense1) continue;
+    bool real = true;
+    for (const auto& v : g.U) if (v.imag() != 0.0) real = false;
+    if (!real || (g.g.noisy && g.g.noise == QS_NOISE_PHASE)) continue;   // complex path: no pivot
+    const double th = g.g.noisy ? e_max * kXiMax : 0.0;
+    if (th >= 1.5) return false;
+    const double u00 = std::abs(g.U[0]), u01 = std::abs(g.U[1]);
+    const double fro = std::sqrt(std::norm(g.U[0]) + std::norm(g.U[1]) + std::norm(g.U[2]) + std::norm(g.U[3]));
+    if (u00 * std::cos(th) - u01 * std::sin(th) < 0.25 * fro) return false;
+  }
+  return true;
+}
 
 // Greedy pass builder starting at remaining[0]; returns absorbed flags.
 // Start c of a high window [c, c + 10) for a run whose first dense gate is on
@@ -684,7 +729,7 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
       Producer pr = P->prods[x.off];
       pr.off = off;
       x.off = off;
-      off += pr.real ? 4 : 8;                           // (r0, r0, s1, s1) or the complex 2x2
+      off += 8;                                         // (p, p, q, q, w, w, -, -) or the complex 2x2
       any_real |= pr.real != 0;
       prods.push_back(pr);
     }
@@ -846,6 +891,24 @@ bool segment_pass(PassPlan* P) {
   return P->segs.size() <= (size_t)kMaxSegs && P->flips.size() <= (size_t)kMaxFlips;
 }
 
+// The compiled program a pass can run (see prog_layers), or 0.  Only the
+// shapes compiled into the pass kernels qualify: real one-qubit gates on all
+// ten window bits, stage A then stage B, descending, with the phase tables of
+// the noisy QFT (every bit of stage A, bits 1..4 of stage B).
+constexpr int kLayerPrograms[] = {prog_layers(0x1f, 0x1e)};
+
+int choose_prog(const PassPlan& P) {
+  if (P.segs.size() != 2 || !P.flips.empty() || (P.high && P.start_stage != 0)) return 0;
+  const Seg& a = P.segs[0];
+  const Seg& b = P.segs[1];
+  if (a.stage != 0 || b.stage != 1 || !a.desc || !b.desc || a.nflip || b.nflip) return 0;
+  if (a.dense != 0x1f || b.dense != 0x1f || a.real != 0x1f || b.real != 0x1f) return 0;
+  const int prog = prog_layers(a.dwin, b.dwin);
+  for (int q : kLayerPrograms)
+    if (q == prog) return prog;
+  return 0;
+}
+
 template <typename T>
 qs_status upload(qs_plan p, T** dst, const std::vector<T>& v) {
   if (v.empty()) { *dst = nullptr; return QS_OK; }
@@ -939,6 +1002,8 @@ PassArgs pass_args(qs_plan p, const PassPlan& P, int synth, int fid) {
   A.ref = h->ref;
   A.fid_partials = p->d_fid;
   A.diag_off = P.diag_off;
+  A.stable = p->stable;
+  A.spin_limit = h->wait_polls < 0 ? kSpinLimit : (uint32_t)h->wait_polls;
   return A;
 }
 
@@ -952,7 +1017,7 @@ cudaError_t launch_precompute(qs_plan p, const PassPlan& P, cudaStream_t s) {
       (P.contribs.size() + (size_t)P.num_dwin * kWin + (1u << (kWin - 1)) + 4 * (size_t)P.num_dense) * sizeof(double2);
   k_precompute<R><<<h->batch, 128, pre_smem, s>>>((R*)P.d_params, P.stride, p->d_gates, P.d_prods,
                                                    (int)P.prods.size(), P.d_contribs, (int)P.contribs.size(),
-                                                   P.num_dwin, P.num_dense, P.diag_off, src, p->d_run);
+                                                   P.num_dwin, P.num_dense, P.diag_off, src, p->d_run, p->stable);
   if (P.d_alpha) {
     OutStarts st{};
     for (int i = 0; i < 12; ++i) st.v[i] = P.out_start[i];
@@ -970,15 +1035,21 @@ cudaError_t launch_pass_kernel(qs_plan p, const PassPlan& P, cudaStream_t s, int
   using C = cplx<R>;
   qs_ctx* h = p->h;
   const PassArgs A = pass_args(p, P, synth, fid);
+  const int prog = p->stable ? 0 : P.prog;               // the compiled programs take two shears
   const int sms = num_sms();
   auto grid = [&](uint64_t units, int per_sm) {
     const uint64_t cap = (uint64_t)sms * per_sm;
     return (int)(units < cap ? units : cap);
   };
   C* psi = (C*)h->state;
+  constexpr int kQft = prog_layers(0x1f, 0x1e);
   if (!P.high) {
     if constexpr (sizeof(R) == 4) {
-      if (p->low_cfg == 1)
+      if (prog == kQft && p->low_cfg == 1)
+        k_pass_low<R, 16, 1, kQft><<<grid((A.tiles + 15) / 16, 1), 16 * 32, low_smem<R, 16, 1>(), s>>>(psi, A);
+      else if (prog == kQft && p->low_cfg == 2)
+        k_pass_low<R, 12, 1, kQft><<<grid((A.tiles + 11) / 12, 1), 12 * 32, low_smem<R, 12, 1>(), s>>>(psi, A);
+      else if (p->low_cfg == 1)
         k_pass_low<R, 16, 1><<<grid((A.tiles + 15) / 16, 1), 16 * 32, low_smem<R, 16, 1>(), s>>>(psi, A);
       else if (p->low_cfg == 2)
         k_pass_low<R, 12, 1><<<grid((A.tiles + 11) / 12, 1), 12 * 32, low_smem<R, 12, 1>(), s>>>(psi, A);
@@ -995,11 +1066,17 @@ cudaError_t launch_pass_kernel(qs_plan p, const PassPlan& P, cudaStream_t s, int
     }
     if constexpr (sizeof(R) == 4) {
       if (p->high_cfg == 1) {
-        k_pass_high<R, CB, 1><<<grid(A.tiles, 2), HighShape<CB>::THREADS, high_smem<R, CB, 1>(), s>>>(psi, P.tmap, A);
+        if (prog == kQft)
+          k_pass_high<R, CB, 1, false, kQft><<<grid(A.tiles, 2), HighShape<CB>::THREADS, high_smem<R, CB, 1>(), s>>>(psi, P.tmap, A);
+        else
+          k_pass_high<R, CB, 1><<<grid(A.tiles, 2), HighShape<CB>::THREADS, high_smem<R, CB, 1>(), s>>>(psi, P.tmap, A);
         return cudaGetLastError();
       }
       if (p->high_cfg == 2) {
-        k_pass_high<R, 2, 1><<<grid(A.tiles, 4), HighShape<2>::THREADS, high_smem<R, 2, 1>(), s>>>(psi, P.tmap4, A);
+        if (prog == kQft)
+          k_pass_high<R, 2, 1, false, kQft><<<grid(A.tiles, 4), HighShape<2>::THREADS, high_smem<R, 2, 1>(), s>>>(psi, P.tmap4, A);
+        else
+          k_pass_high<R, 2, 1><<<grid(A.tiles, 4), HighShape<2>::THREADS, high_smem<R, 2, 1>(), s>>>(psi, P.tmap4, A);
         return cudaGetLastError();
       }
     }
@@ -1050,6 +1127,11 @@ cudaError_t set_smem_attrs(size_t esize) {
     if (e == cudaSuccess) e = set_pass_attrs(k_pass_high<float, 3, 1>, high_smem<float, 3, 1>(), 2);
     if (e == cudaSuccess) e = set_pass_attrs(k_pass_high<float, 2, 1>, high_smem<float, 2, 1>(), 4);
     if (e == cudaSuccess) e = set_pass_attrs(k_pass_high<float, 3, 2, true>, high_smem<float, 3, 2>(), 1);
+    constexpr int kQft = prog_layers(0x1f, 0x1e);
+    if (e == cudaSuccess) e = set_pass_attrs(k_pass_low<float, 16, 1, kQft>, low_smem<float, 16, 1>(), 1);
+    if (e == cudaSuccess) e = set_pass_attrs(k_pass_low<float, 12, 1, kQft>, low_smem<float, 12, 1>(), 1);
+    if (e == cudaSuccess) e = set_pass_attrs(k_pass_high<float, 3, 1, false, kQft>, high_smem<float, 3, 1>(), 2);
+    if (e == cudaSuccess) e = set_pass_attrs(k_pass_high<float, 2, 1, false, kQft>, high_smem<float, 2, 1>(), 4);
   } else {
     e = set_pass_attrs(k_pass_low<double, 4, 2>, low_smem<double, 4, 2>(), 1);
     if (e == cudaSuccess) e = set_pass_attrs(k_pass_high<double, 2, 2>, high_smem<double, 2, 2>(), 1);
@@ -1226,6 +1308,7 @@ qs_status run_plan(qs_plan p, double e, uint64_t seed, uint64_t gate_id0, int wa
   const int fid = want_fid && fusable_end(p) ? 1 : 0;
   // the pinned run block may still be read by an earlier launch of the graph
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "stream sync");
+  p->stable = two_shear_safe(p->gates, h->member_noise ? h->m_e_max : e) ? 0 : 1;
   p->h_run->e = e;
   p->h_run->seed = seed;
   p->h_run->gate_id0 = gate_id0;
@@ -1241,9 +1324,9 @@ qs_status run_plan(qs_plan p, double e, uint64_t seed, uint64_t gate_id0, int wa
       return pfail(p, QS_ERR_CUDA, "run params copy");
     st = enqueue_run(p, h->stream, synth, fid);
   } else {
-    const int v = synth * 2 + fid;
+    const int v = p->stable * 6 + synth * 2 + fid;
     if (p->exec[v] && (p->graph_member_noise[v] != h->member_noise || p->graph_member_marked[v] != h->member_marked ||
-                       p->graph_timing[v] != p->timing)) {
+                       p->graph_timing[v] != p->timing || p->graph_wait_polls[v] != h->wait_polls)) {
       cudaGraphExecDestroy(p->exec[v]);
       p->exec[v] = nullptr;
     }
@@ -1264,6 +1347,7 @@ qs_status run_plan(qs_plan p, double e, uint64_t seed, uint64_t gate_id0, int wa
       p->graph_member_noise[v] = h->member_noise;
       p->graph_member_marked[v] = h->member_marked;
       p->graph_timing[v] = p->timing;
+      p->graph_wait_polls[v] = h->wait_polls;
     }
     if (cudaGraphLaunch(p->exec[v], h->stream) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "graph launch");
   }
@@ -1350,6 +1434,7 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
         std::fill(absorbed.begin(), absorbed.end(), 0);
         if (!build_pass(p->gates, rem, h->n, p->colb, (uint64_t)h->batch, budget, &P, &absorbed)) break;
         built = segment_pass(&P);
+        if (built) P.prog = choose_prog(P);
       }
       if (built) {
         bool any = false;
@@ -1483,6 +1568,7 @@ qs_status qs_plan_profile(qs_plan p, int reps, double e, uint64_t seed, uint64_t
   qs_ctx* h = p->h;
   if (h->pending) { qs_status st = materialize_basis(h); if (st != QS_OK) return st; }
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "stream sync");
+  p->stable = two_shear_safe(p->gates, h->member_noise ? h->m_e_max : e) ? 0 : 1;
   p->h_run->e = e;
   p->h_run->seed = seed;
   p->h_run->gate_id0 = gate_id0;

@@ -74,6 +74,7 @@ _SIGS = {
     "qs_get_state_range": ([_P, ct.c_size_t, ct.c_size_t, _D], ct.c_int),
     "qs_set_rank_columns": ([_P, ct.c_int], ct.c_int),
     "qs_set_trajectory_offset": ([_P, ct.c_uint64], ct.c_int),
+    "qs_set_wait_limit": ([_P, ct.c_int64], ct.c_int),
     "qs_set_member_noise": ([_P, _D, _U64, _U64, _U64], ct.c_int),
     "qs_plan_create": ([_P, ct.POINTER(qs_gate), ct.c_int, ct.POINTER(_P)], ct.c_int),
     "qs_plan_run": ([_P, ct.c_double, ct.c_uint64, ct.c_uint64], ct.c_int),
@@ -295,6 +296,10 @@ def qs_set_state(h, state):
 
 def qs_set_rank_columns(h, m):
     _check(lib().qs_set_rank_columns(h, int(m)), h)
+
+
+def qs_set_wait_limit(h, polls):
+    _check(lib().qs_set_wait_limit(h, int(polls)), h)
 
 
 def qs_set_trajectory_offset(h, offset):

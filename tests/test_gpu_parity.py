@@ -261,6 +261,61 @@ def test_random_circuits_through_the_planner_match_oracle(dtype, n, seed):
         assert_amplitudes_close(got[b], psi, dtype, k=4.0)
 
 
+def _ry(theta):
+    c, s_ = math.cos(theta / 2), math.sin(theta / 2)
+    return np.array([[c, -s_], [s_, c]], dtype=np.complex128)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("case", ["bit_flips", "noisy_flips", "near_pi", "strong_noise_h"])
+def test_real_gates_with_small_pivots_match_oracle(dtype, case):
+    """Real one-qubit gates whose M00 is small or zero (a bit flip, a rotation
+    by nearly pi, rotation noise large enough to turn a Hadamard into one)
+    through the fused passes, against the gate-by-gate oracle: the factored
+    form must pivot instead of dividing by the small entry."""
+    rng = np.random.default_rng({"bit_flips": 21, "noisy_flips": 22, "near_pi": 23, "strong_noise_h": 24}[case])
+    n, batch = 13, 3
+    X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+    e = {"bit_flips": 0.03, "noisy_flips": 0.05, "near_pi": 0.03, "strong_noise_h": 0.25}[case]
+    gates = []
+    for _ in range(80):
+        r = rng.random()
+        q = int(rng.integers(n))
+        if r < 0.35:
+            gates.append(qs.make_gate((q,), ogates.hadamard(), noisy=True))
+        elif r < 0.55:
+            j, k = rng.choice(n, size=2, replace=False)
+            gates.append(qs.make_gate((int(j), int(k)), ogates.controlled_phase(float(rng.uniform(0, 6))),
+                                      noisy=True, noise=qs.QS_NOISE_PHASE))
+        elif case == "bit_flips":
+            gates.append(qs.make_gate((q,), X))
+        elif case == "noisy_flips":
+            gates.append(qs.make_gate((q,), X, noisy=True))
+        elif case == "near_pi":
+            gates.append(qs.make_gate((q,), _ry(math.pi - 1e-3 * (1 + rng.random()))))
+        else:
+            gates.append(qs.make_gate((q,), ogates.hadamard(), noisy=True))
+    x0 = int(rng.integers(1 << n))
+    with Handle(n, batch, 0, qs.QS_STATEVEC, dtype) as h:
+        qs.qs_set_basis_state(h, x0)
+        p = qs.qs_plan_create(h, gates)
+        passes, _ = qs.qs_plan_info(p, h)
+        qs.qs_plan_run(p, e, SEED, 7, h)
+        qs.qs_plan_destroy(p)
+        got = qs.qs_get_state(h).reshape(batch, -1)
+    assert passes < len(gates)                                  # the gates ran fused
+    for b in range(batch):
+        psi = osv.basis_state(n, x0)
+        for g, gate in enumerate(gates):
+            d = 1 << gate.k
+            U = np.array(gate.U[:2 * d * d]).view(np.complex128).reshape(d, d)
+            if gate.noisy:
+                xa, xb = ophilox.normal_pair(SEED, b, 7 + g)
+                U = ogates.noisy_unitary(U, "phase" if gate.noise == qs.QS_NOISE_PHASE else "rotation", e, xa, xb)
+            psi = osv.apply_gate(psi, n, tuple(gate.targets[:gate.k]), U)
+        assert_amplitudes_close(got[b], psi, dtype, k=4.0, err_msg=f"{case} member {b}")
+
+
 def test_plan_with_unfusable_gates_matches_oracle():
     rng = np.random.default_rng(9)
     n, batch, e = 11, 2, 0.03
@@ -402,6 +457,37 @@ def test_fixed_rank_matches_oracle(circ, n, r, normalize):
         np.testing.assert_allclose(L @ L.conj().T, rho, atol=1e-12)
 
 
+@pytest.mark.parametrize("r", [2, 4, 8])
+def test_fixed_rank_grover_n16_prefix_matches_oracle(r):
+    """The configuration of the fixed-rank workload (Grover, n = 16, e = 0.01,
+    Sec. 3.2) over its first 304 channels (the start and nine iterations):
+    at 2^16 rows the Gram reduction sums more partial blocks per thread than
+    any smaller test reaches.  Fidelity, trace and L L^dagger on sampled rows
+    against the oracle on the same prefix."""
+    n, e = 16, 0.01
+    w = inputs.draw_marked(n, SEED)
+    ops = inputs.grover_circuit(n, inputs.grover_iterations(n), w)
+    prefix = ops[:16 + 9 * (2 * n + 2)]
+    assert sum(1 for o in prefix if o.noisy) == 304
+    ideal = ocirc.ideal_state(n, prefix, 0)
+    with Handle(n, 1, r, qs.QS_FIXED_RANK, qs.QS_C128) as h:
+        qs.qs_set_basis_state(h, 0)
+        pcirc.apply_ops(h, prefix, e, SEED)
+        f = qs.qs_fidelity(h, ideal)[0]
+        tr = qs.qs_trace(h)[0]
+        m = qs.qs_get_rank(h)
+        L = qs.qs_get_state(h).reshape(r, 1 << n)[:m].T
+    Lo = ocirc.run_fixed_rank(n, prefix, 0, e, r)
+    assert m == Lo.shape[1]
+    fo, to = ofr.fidelity(ideal, Lo), ofr.trace(Lo)
+    assert abs(f - fo) <= 1e-12 * fo, (f, fo)
+    assert abs(tr - to) <= 1e-12 * to, (tr, to)
+    rows = np.sort(np.random.default_rng(r).choice(1 << n, size=96, replace=False))
+    rows = np.union1d(rows, [0, w, (1 << n) - 1])
+    got, want = L[rows] @ L[rows].conj().T, Lo[rows] @ Lo[rows].conj().T
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * np.abs(want).max())
+
+
 def test_explicit_truncation_matches_oracle():
     rng = np.random.default_rng(2)
     n, r = 6, 6
@@ -442,6 +528,29 @@ def test_member_noise_equals_separate_runs():
             qs.qs_plan_destroy(p)
             alone = qs.qs_get_state(h1)
         np.testing.assert_allclose(mixed[b], alone, atol=1e-13)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_clearing_member_noise_restores_the_call_arguments(dtype):
+    """Per-member noise overrides a run's e and seed until it is cleared; after
+    qs_set_member_noise(h, NULL, ...) the next run draws with the call's own e."""
+    n, batch = 12, 3
+    ops = inputs.qft_circuit(n)
+    x0 = inputs.draw_basis_input(n, SEED)
+    with Handle(n, batch, 0, qs.QS_STATEVEC, dtype) as h:
+        p = qs.qs_plan_create(h, pcirc.to_gates(ops))
+        qs.qs_set_member_noise(h, [0.2] * batch, [SEED] * batch, list(range(batch)))
+        qs.qs_set_basis_state(h, x0)
+        qs.qs_plan_run(p, 0.001, SEED, 0, h)               # the members' e = 0.2 wins
+        noisy = qs.qs_get_state(h).reshape(batch, -1)
+        qs.qs_set_member_noise(h)                           # cleared
+        qs.qs_set_basis_state(h, x0)
+        qs.qs_plan_run(p, 0.001, SEED, 0, h)               # the call's e again
+        quiet = qs.qs_get_state(h).reshape(batch, -1)
+        qs.qs_plan_destroy(p)
+    for b in range(batch):
+        assert_amplitudes_close(noisy[b], ocirc.run_trajectory(n, ops, x0, 0.2, SEED, b), dtype)
+        assert_amplitudes_close(quiet[b], ocirc.run_trajectory(n, ops, x0, 0.001, SEED, b), dtype)
 
 
 def test_invalid_arguments_are_rejected():

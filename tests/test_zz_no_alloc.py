@@ -12,6 +12,7 @@ torch) -- the entry point under test allocates nothing.
 import numpy as np
 import pytest
 
+from oracle import statevec as osv
 from paper_1412_2293_gb300 import circuits as pcirc
 from paper_1412_2293_gb300 import inputs, qs
 
@@ -70,3 +71,52 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     with pytest.raises(qs.QSError) as ei:
         qs.qs_fidelity_noalloc(0, d.data_ptr(), 2, 1, qs.QS_C64)
     assert ei.value.status == qs.QS_ERR_INVALID_ARG
+
+
+def _two_component_states(n, members, dtype, seed):
+    """Device states psi_b = cos(t_b) ref + sin(t_b) e^{i p_b} orth with orth
+    orthogonal to ref, so |<ref|psi_b>|^2 = cos(t_b)^2 exactly (made with torch
+    by the test; the entry point allocates nothing)."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    N = 1 << n
+    ref = rng.normal(size=N) + 1j * rng.normal(size=N)
+    ref /= np.linalg.norm(ref)
+    orth = rng.normal(size=N) + 1j * rng.normal(size=N)
+    orth -= np.vdot(ref, orth) * ref
+    orth /= np.linalg.norm(orth)
+    t = rng.uniform(0, np.pi / 2, size=members)
+    ph = rng.uniform(0, 2 * np.pi, size=members)
+    tdt = torch.complex64 if dtype == qs.QS_C64 else torch.complex128
+    d_ref = torch.from_numpy(ref).to("cuda").to(tdt)
+    d_orth = torch.from_numpy(orth).to("cuda").to(tdt)
+    c = torch.from_numpy(np.cos(t)).to("cuda").to(tdt)
+    s = torch.from_numpy(np.sin(t) * np.exp(1j * ph)).to("cuda").to(tdt)
+    states = c[:, None] * d_ref[None, :] + s[:, None] * d_orth[None, :]
+    return states.contiguous(), d_ref, np.cos(t) ** 2
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
+@pytest.mark.parametrize("n,members", [(21, 2), (18, 2048)])
+def test_noalloc_many_chunks_and_capped_chunks_against_closed_form_and_oracle(dtype, n, members):
+    """n = 21 with two members: 512 chunks per member, summed in order.
+    n = 18 with 2048 members: 64 chunks per member would need 131072 partials,
+    so the chunk count is capped at 32 and every block covers 8192 amplitudes
+    (more than the 4096 of an uncapped chunk)."""
+    import torch
+
+    states, d_ref, closed = _two_component_states(n, members, dtype, seed=n * 7 + members)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    tol = 1e-12 if dtype == qs.QS_C128 else 1e-5
+    for _ in range(2):
+        got = qs.qs_fidelity_noalloc(states.data_ptr(), d_ref.data_ptr(), n, members, dtype, stream)
+        np.testing.assert_allclose(got, closed, rtol=0, atol=tol)
+    # the oracle's fidelity of the very vectors the GPU summed, on sampled members
+    ref_h = d_ref.cpu().numpy().astype(np.complex128)
+    for b in sorted({0, members // 2, members - 1}):
+        want = osv.fidelity(ref_h, states[b].cpu().numpy().astype(np.complex128))
+        assert abs(got[b] - want) <= tol, (b, got[b], want)
+    del states
+    torch.cuda.empty_cache()
