@@ -73,9 +73,16 @@ typedef enum {
 
 /* Create a simulator on the current CUDA device.
  *   n       qubits, 1 <= n; memory: STATEVEC batch * 2^n, DENSITY 4^n,
- *           FIXED_RANK 5 * rank * 2^n complex elements (plus small scratch).
- *   batch   STATEVEC: number of trajectories (>= 1); other modes: must be 1.
- *   rank    FIXED_RANK: truncation rank r >= 1; other modes: ignored (0).
+ *           FIXED_RANK batch * (rank + min(32, 8 rank)) * 2^n complex
+ *           elements (plus small scratch).
+ *   batch   STATEVEC: number of trajectories (>= 1).  FIXED_RANK: number of
+ *           independent factors (members, >= 1) that every call advances
+ *           together -- each with its own truncation rank
+ *           (qs_set_member_ranks), column count and, for noisy gates, noise
+ *           level (qs_set_member_noise); one launch of each kernel serves
+ *           all of them.  DENSITY: must be 1.
+ *   rank    FIXED_RANK: truncation rank r >= 1 (the largest of the members');
+ *           other modes: ignored (0).
  *   dtype   QS_C64 (complex float, FP32 arithmetic) or QS_C128 (FP64).
  *           Reductions (fidelity, trace, Gram matrix, eigensolver) always
  *           accumulate in FP64.
@@ -90,11 +97,13 @@ const char* qs_last_error(qs_handle h);
 qs_status qs_synchronize(qs_handle h);
 
 /* Shape of a handle (any pointer may be NULL).  *results = number of doubles
- * qs_fidelity / qs_trace write (batch for STATEVEC, 1 otherwise). */
+ * qs_fidelity / qs_trace write (batch for STATEVEC and FIXED_RANK, 1 for
+ * DENSITY). */
 qs_status qs_info(qs_handle h, int* n, int* batch, int* rank, int* mode, int* dtype, int* results);
 
 /* Every batch member (trajectory / density matrix / factor) <- |x><x|.
- * FIXED_RANK: the factor becomes one column.  Errors: INVALID_ARG if x >= 2^n. */
+ * FIXED_RANK: every member's factor becomes one column.  Errors: INVALID_ARG
+ * if x >= 2^n. */
 qs_status qs_set_basis_state(qs_handle h, uint64_t x);
 
 /* Per-member basis states: xs[b] for b < batch (STATEVEC only). */
@@ -137,7 +146,8 @@ qs_status qs_apply_phase_flip(qs_handle h, uint64_t index);
  * DENSITY / FIXED_RANK: the xi-averaged channel (Eqs. 6, 9): rotation ->
  *   {sqrt(l1) U, sqrt(l2) U J} per target (l1,2 = (1 +- exp(-2e^2))/2),
  *   phase -> {U diag(1,..,sqrt P), U diag(0,..,sqrt(1-P))}, P = exp(-e^2);
- *   FIXED_RANK truncates to the handle's rank afterwards (Sec. 3.2).
+ *   FIXED_RANK truncates every member to its rank afterwards (Sec. 3.2);
+ *   with per-member noise set, member b's channel uses its own e[b].
  * Errors: INVALID_ARG (k, targets, e < 0). */
 qs_status qs_apply_noisy_gate(qs_handle h, const int* targets, int k, const double* U,
                               qs_noise noise, double e, uint64_t seed, uint64_t gate_id);
@@ -190,8 +200,8 @@ qs_status qs_apply_relaxation(qs_handle h, const int* qubits, int count, double 
  * default) restores the tensor-core path.  Errors: INVALID_ARG for NULL. */
 qs_status qs_set_tensor_cores(qs_handle h, int on);
 
-/* FIXED_RANK: truncate the current factor to rank r (<= handle rank) by the
- * Gram-matrix eigendecomposition (Sec. 3.2).  normalize = 0 keeps the trace
+/* FIXED_RANK: truncate every member's factor to rank r (<= handle rank) by
+ * the Gram-matrix eigendecomposition (Sec. 3.2).  normalize = 0 keeps the trace
  * sum of the kept eigenvalues; 1 rescales to unit trace.  Eigenvalues within
  * 1e-10 * Lambda_1 form one cluster whose basis is made canonical by
  * Gram-Schmidt of the projected Gram-space axes.  Other modes: NOT_SUPPORTED. */
@@ -200,8 +210,18 @@ qs_status qs_truncate_rank(qs_handle h, int r, int normalize);
 /* FIXED_RANK: normalisation used by the automatic truncations (default 0). */
 qs_status qs_set_normalize(qs_handle h, int normalize);
 
-/* FIXED_RANK: current number of factor columns (<= rank). */
+/* FIXED_RANK: current number of factor columns (<= rank; the largest over
+ * the members). */
 qs_status qs_get_rank(qs_handle h, int* out);
+
+/* FIXED_RANK: truncation rank of each member, ranks[b] in 1..rank for b <
+ * batch (default: the handle's rank), so members of uneven rank share one
+ * handle and one launch per kernel.  Errors: INVALID_ARG for a rank out of
+ * range, NOT_SUPPORTED for other modes. */
+qs_status qs_set_member_ranks(qs_handle h, const int* ranks);
+
+/* FIXED_RANK: live columns of each member's factor, out[batch]. */
+qs_status qs_get_member_columns(qs_handle h, int* out);
 
 /* ------------------------------------------------------------ reductions */
 
@@ -209,7 +229,8 @@ qs_status qs_get_rank(qs_handle h, int* out);
  *   STATEVEC |<phi|psi_b>|^2 (out[batch]); DENSITY <phi|rho|phi> (out[1]);
  *   FIXED_RANK sum_c |<phi|L_c>|^2 (out[1]).
  * phi = `ref` (2^n interleaved complex doubles, host) if ref != NULL, else
- * the basis state |ref_basis>.  Synchronises.  Errors: INVALID_ARG. */
+ * the basis state |ref_basis>.  FIXED_RANK writes one value per member
+ * (out[batch]).  Synchronises.  Errors: INVALID_ARG. */
 qs_status qs_fidelity(qs_handle h, const double* ref, uint64_t ref_basis, double* out);
 
 /* Store a reference phi on the device once (2^n complex doubles, host), for
@@ -226,14 +247,15 @@ qs_status qs_fidelity_stored(qs_handle h, double* out);
 qs_status qs_fidelity_ref(qs_handle h, qs_handle ref, int first, int count, double* out);
 
 /* Trace: STATEVEC squared norm per member (out[batch]); DENSITY tr(rho);
- * FIXED_RANK sum_c ||L_c||^2.  Synchronises. */
+ * FIXED_RANK sum_c ||L_c||^2 per member (out[batch]).  Synchronises. */
 qs_status qs_trace(qs_handle h, double* out);
 
 /* ------------------------------------------------------- state transfer */
 
 /* Number of complex elements of the state: STATEVEC batch * 2^n,
- * DENSITY 4^n (vec index i * 2^n + j for rho[i][j]), FIXED_RANK rank * 2^n
- * (column-major: column c at offset c * 2^n; columns >= qs_get_rank are 0). */
+ * DENSITY 4^n (vec index i * 2^n + j for rho[i][j]), FIXED_RANK
+ * batch * rank * 2^n (column-major: column c of member b at offset
+ * (b rank + c) 2^n; a member's columns past its live count are 0). */
 qs_status qs_state_size(qs_handle h, size_t* out);
 /* Copy the state to / from host memory as interleaved complex doubles
  * (count = qs_state_size).  Synchronises.  qs_set_state on a DENSITY handle
@@ -247,7 +269,7 @@ qs_status qs_set_state(qs_handle h, const double* host, size_t count);
  * Errors: INVALID_ARG if the range exceeds qs_state_size or host is NULL. */
 qs_status qs_get_state_range(qs_handle h, size_t first, size_t count, double* host);
 
-/* FIXED_RANK: set the number of live columns after qs_set_state. */
+/* FIXED_RANK: set every member's number of live columns after qs_set_state. */
 qs_status qs_set_rank_columns(qs_handle h, int m);
 
 /* Failure detection: every tile-copy wait of the fused passes polls its
@@ -268,7 +290,9 @@ qs_status qs_set_trajectory_offset(qs_handle h, uint64_t offset);
 /* STATEVEC: per-member noise (continuous batching of different jobs in one
  * handle).  e[b], seed[b], traj[b] override the call arguments and the
  * offset for member b; marked[b] (may be NULL) replaces the index of plan
- * flips marked QS_FLIP_PER_MEMBER.  Pass all NULL to clear. */
+ * flips marked QS_FLIP_PER_MEMBER.  FIXED_RANK: e[b] sets member b's
+ * averaged channel in qs_apply_noisy_gate (seed and traj are required but
+ * unused).  Pass all NULL to clear. */
 qs_status qs_set_member_noise(qs_handle h, const double* e, const uint64_t* seed,
                               const uint64_t* traj, const uint64_t* marked);
 
@@ -301,6 +325,11 @@ typedef struct {
  * qubits 0..9, and c..c+9 (c >= 3 complex64, c >= 2 complex128) chosen per run
  * of gates, the top ten first; gates no window can hold, and other shapes,
  * run gate by gate with the same kernels as the single-gate calls.
+ * FIXED_RANK handles: every gate on every member (noisy gates as their
+ * averaged channels with expansion and truncation, Sec. 3.2), the launch
+ * shapes fixed when the plan is made and the column counts kept on the
+ * device, so the whole circuit replays as one CUDA graph; needs K * rank <=
+ * 32 for every noisy gate (NOT_SUPPORTED otherwise).
  * Errors: INVALID_ARG for a malformed gate (nothing is built). */
 qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_plan* out);
 /* Run the plan once on the handle's stream with noise level e and key seed

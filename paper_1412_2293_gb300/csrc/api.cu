@@ -215,49 +215,101 @@ qs_status dm_apply_channel(qs_handle h, const int* targets, int k, const std::ve
   return apply_uniform(h, h->state, 2 * h->n, 1, t2, 2 * k, superop(ks, 1 << k));
 }
 
-qs_status rank_truncate_from_work(qs_handle h, int M, int r, int normalize) {
-  double* G = h->small + kSmallG;
-  double* W = h->small + kSmallW;
-  double* lam = h->small + kSmallLam;
-  double* scale = h->small + kSmallScale;
-  QS_CUDA(h, qs::launch_gram(h, h->work, h->n, M, h->real_factor, G));
-  QS_CUDA(h, qs::launch_eig_truncate(h, G, M, r, normalize, W, lam, scale, h->dstatus, h->dstatus + 1));
-  QS_CUDA(h, qs::launch_project(h, h->work, h->state, h->n, M, h->real_factor, W, scale, h->dstatus));
-  const int keep = std::min(r, M);
-  // columns that are no longer live read as zero
-  if (keep < h->cols) {
-    const size_t N = 1ull << h->n;
-    QS_CUDA(h, cudaMemsetAsync((char*)h->state + (size_t)keep * N * h->esize, 0,
-                               (size_t)(h->cols - keep) * N * h->esize, h->stream));
-  }
-  h->cols = keep;
-  return QS_OK;
-}
-
-// FIXED_RANK: L' = [E_1 L | ..], then truncation when K > 1.
 bool all_real(const std::vector<cd>& m) {
   for (const auto& v : m) if (v.imag() != 0.0) return false;
   return true;
 }
 
-qs_status rank_apply_kraus(qs_handle h, const int* targets, int k, const std::vector<std::vector<cd>>& ks) {
-  const int K = (int)ks.size();
-  const int d = 1 << k;
-  for (const auto& E : ks) if (!all_real(E)) h->real_factor = false;
-  if (K == 1) {
-    return apply_uniform(h, h->state, h->n, h->cols, targets, k, ks[0]);
+// FIXED_RANK: columns the unitary kernels sweep -- the live ones of a single
+// member, or every column of every member (dead columns are zero and stay so)
+int rank_swept(qs_handle h) { return h->batch == 1 ? h->cols : h->batch * h->rank; }
+
+// host mirror of the members' column counts -> device (small synchronous copies)
+qs_status rank_upload_counts(qs_handle h) {
+  QS_CUDA(h, cudaMemcpyAsync(h->rc.cols, h->m_cols.data(), h->batch * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  QS_CUDA(h, cudaMemcpyAsync(h->rc.rank, h->m_rank.data(), h->batch * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  h->cols = *std::max_element(h->m_cols.begin(), h->m_cols.end());
+  return QS_OK;
+}
+
+// Gram matrices, eigensolver, truncation and projection of every member's L'
+// (M_b columns on the device); keep_b = min(r_b, M_b) (r_b = trunc_r when > 0)
+// mirrored on the host.  K: Kraus operators of the channel (L' = K m_b columns).
+qs_status rank_truncate_work(qs_handle h, int K, int trunc_r, int normalize) {
+  int max_M = 0, max_keep = 0;
+  for (int b = 0; b < h->batch; ++b) {
+    const int M = K * h->m_cols[b];
+    const int keep = std::min(trunc_r > 0 ? trunc_r : h->m_rank[b], M);
+    max_M = std::max(max_M, M);
+    max_keep = std::max(max_keep, keep);
+    h->m_cols[b] = keep;
   }
-  const int M = K * h->cols;
-  if (M > qs::kMaxGramDim)
-    return fail(h, QS_ERR_NOT_SUPPORTED, "Kraus count times rank exceeds the Gram-matrix limit of 32");
+  QS_CUDA(h, qs::launch_gram(h, h->real_factor, max_M));
+  QS_CUDA(h, qs::launch_eig_truncate(h, trunc_r, normalize));
+  QS_CUDA(h, qs::launch_project(h, h->real_factor, K, max_keep));
+  h->cols = *std::max_element(h->m_cols.begin(), h->m_cols.end());
+  return QS_OK;
+}
+
+// FIXED_RANK: L'_b = [E_1 L_b | ..], then truncation when K > 1.  ks: one
+// Kraus set for every member, or (per_member) `batch` sets of K operators.
+qs_status rank_apply_kraus(qs_handle h, const int* targets, int k, const std::vector<std::vector<cd>>& ks,
+                           int per_member = 0) {
+  const int d = 1 << k;
+  const int K = per_member ? (int)ks.size() / h->batch : (int)ks.size();
+  for (const auto& E : ks) if (!all_real(E)) h->real_factor = false;
+  if (K == 1 && !per_member) return apply_uniform(h, h->state, h->n, rank_swept(h), targets, k, ks[0]);
+  int max_cols = 0;
+  for (int b = 0; b < h->batch; ++b) {
+    if (K * h->m_cols[b] > std::min(qs::kMaxGramDim, h->mcap))
+      return fail(h, QS_ERR_NOT_SUPPORTED, "Kraus count times rank exceeds the Gram-matrix limit of 32");
+    max_cols = std::max(max_cols, h->m_cols[b]);
+  }
   std::vector<double> e;
   for (const auto& E : ks) { auto v = to_interleaved(E); e.insert(e.end(), v.begin(), v.end()); }
-  (void)d;
-  QS_CUDA(h, cudaMemcpyAsync(h->small + kSmallE, e.data(), e.size() * sizeof(double),
-                             cudaMemcpyHostToDevice, h->stream));
+  const size_t set_bytes = (size_t)K * d * d * 2 * sizeof(double);
+  double* Edev = h->rsmall + qs::kSmallE;
+  if (per_member) {
+    QS_CUDA(h, cudaMemcpy2DAsync(Edev, qs::kRankStride * sizeof(double), e.data(), set_bytes, set_bytes, h->batch,
+                                 cudaMemcpyHostToDevice, h->stream));
+  } else {
+    QS_CUDA(h, cudaMemcpyAsync(Edev, e.data(), set_bytes, cudaMemcpyHostToDevice, h->stream));
+  }
   const Targets tg = qs::make_targets(h->n, targets, k);
-  QS_CUDA(h, qs::launch_kraus_expand(h, h->state, h->work, h->n, h->cols, tg, h->real_factor, h->small + kSmallE, K));
-  return rank_truncate_from_work(h, M, h->rank, h->normalize);
+  QS_CUDA(h, qs::launch_kraus_expand(h, tg, h->real_factor, Edev, K, per_member ? qs::kRankStride : 0, max_cols));
+  return rank_truncate_work(h, K, 0, h->normalize);
+}
+
+// FIXED_RANK: the averaged channel of a noisy gate on every member, then
+// truncation
+qs_status rank_channel_gate(qs_handle h, const int* targets, const qs::KrausGate& g) {
+  const int K = qs::kraus_count(g.k, g.noise);
+  bool real = true;
+  for (int i = 1; i < 2 * (1 << g.k) * (1 << g.k); i += 2) real &= g.U[i] == 0.0;
+  if (!real) h->real_factor = false;
+  int max_cols = 0;
+  for (int b = 0; b < h->batch; ++b) {
+    if (K * h->m_cols[b] > std::min(qs::kMaxGramDim, h->mcap))
+      return fail(h, QS_ERR_NOT_SUPPORTED, "Kraus count times rank exceeds the Gram-matrix limit of 32");
+    max_cols = std::max(max_cols, h->m_cols[b]);
+  }
+  const Targets tg = qs::make_targets(h->n, targets, g.k);
+  QS_CUDA(h, qs::launch_kraus_expand_gate(h, tg, h->real_factor, g, max_cols));
+  return rank_truncate_work(h, K, 0, h->normalize);
+}
+
+// FIXED_RANK: column c = 0 of every member <- |x> (or Eq. 16's state), the rest 0
+qs_status rank_set_start(qs_handle h, int entangled, uint64_t x) {
+  const size_t N = 1ull << h->n;
+  QS_CUDA(h, cudaMemsetAsync(h->state, 0, h->state_elems * h->esize, h->stream));
+  for (int b = 0; b < h->batch; ++b) {
+    void* col0 = (char*)h->state + (size_t)b * h->rank * N * h->esize;
+    if (entangled) QS_CUDA(h, qs::launch_set_entangled(h, col0, 1, 0));
+    else QS_CUDA(h, qs::launch_set_basis(h, col0, h->n, 1, x, nullptr));
+  }
+  std::fill(h->m_cols.begin(), h->m_cols.end(), 1);
+  h->real_factor = true;
+  return rank_upload_counts(h);
 }
 
 qs_status read_out(qs_handle h, double* out, int count) { return qs::read_results(h, out, count); }
@@ -311,7 +363,8 @@ qs_status qs_create(int n, int batch, int rank, qs_mode mode, qs_dtype dtype, vo
   if (mode != QS_STATEVEC && mode != QS_DENSITY && mode != QS_FIXED_RANK) return QS_ERR_INVALID_ARG;
   if (dtype != QS_C64 && dtype != QS_C128) return QS_ERR_INVALID_ARG;
   if (mode == QS_STATEVEC && batch < 1) return QS_ERR_INVALID_ARG;
-  if (mode != QS_STATEVEC && batch != 1) return QS_ERR_INVALID_ARG;
+  if (mode == QS_DENSITY && batch != 1) return QS_ERR_INVALID_ARG;
+  if (mode == QS_FIXED_RANK && batch < 1) return QS_ERR_INVALID_ARG;
   if (mode == QS_FIXED_RANK && (rank < 1 || rank > qs::kMaxRank)) return QS_ERR_INVALID_ARG;
   if (mode == QS_DENSITY && 2 * n > 40) return QS_ERR_INVALID_ARG;
   int ndev = 0;
@@ -332,7 +385,7 @@ qs_status qs_create(int n, int batch, int rank, qs_mode mode, qs_dtype dtype, vo
   size_t members = mode == QS_STATEVEC ? (size_t)batch : 1;
   if (mode == QS_STATEVEC) h->state_elems = (size_t)batch * N;
   else if (mode == QS_DENSITY) h->state_elems = N * N;
-  else h->state_elems = (size_t)rank * N;
+  else h->state_elems = (size_t)batch * rank * N;
 
   auto bail = [&](qs_status st) { qs_destroy(h); return st; };
   size_t free_b = 0, total_b = 0;
@@ -340,15 +393,25 @@ qs_status qs_create(int n, int batch, int rank, qs_mode mode, qs_dtype dtype, vo
   if (h->state_elems * h->esize > free_b) return bail(QS_ERR_OUT_OF_MEMORY);
   if (cudaMalloc(&h->state, h->state_elems * h->esize) != cudaSuccess) { cudaGetLastError(); return bail(QS_ERR_OUT_OF_MEMORY); }
   if (mode == QS_FIXED_RANK) {
-    h->work_elems = (size_t)qs::kMaxGramDim * N;
+    // L' of a member: at most kMaxKraus operators times its rank, and the Gram limit
+    h->mcap = std::min(qs::kMaxGramDim, kMaxKraus * rank);
+    h->work_elems = (size_t)batch * h->mcap * N;
+    if (h->work_elems * h->esize > free_b - h->state_elems * h->esize) return bail(QS_ERR_OUT_OF_MEMORY);
     if (cudaMalloc(&h->work, h->work_elems * h->esize) != cudaSuccess) { cudaGetLastError(); return bail(QS_ERR_OUT_OF_MEMORY); }
-    members = qs::kMaxGramDim;
+    members = (size_t)batch * std::max(h->mcap, rank);
+    if (cudaMalloc((void**)&h->rsmall, (size_t)batch * qs::kRankStride * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return bail(QS_ERR_OUT_OF_MEMORY); }
+    int* counts = nullptr;
+    if (cudaMalloc((void**)&counts, 4 * (size_t)batch * sizeof(int)) != cudaSuccess) { cudaGetLastError(); return bail(QS_ERR_OUT_OF_MEMORY); }
+    h->rc = qs::RankCounts{counts, counts + batch, counts + 2 * batch, counts + 3 * batch};
+    h->m_cols.assign(batch, 1);
+    h->m_rank.assign(batch, rank);
+    if (qs::rank_kernel_attributes() != cudaSuccess) return bail(QS_ERR_CUDA);
   }
   // scratch sized for every reduction of this shape, so that runs never allocate
   const uint64_t chunks = (N + 4095) / 4096;
   size_t partials = 2 * chunks * members;
   if (mode == QS_DENSITY) partials = std::max<size_t>(partials, 2 * N);
-  if (mode == QS_FIXED_RANK) partials = std::max<size_t>(partials, ((N + 63) / 64) * 2 * qs::kMaxGramDim * qs::kMaxGramDim);
+  if (mode == QS_FIXED_RANK) partials = std::max<size_t>(partials, qs::gram_partials_doubles(n, batch));
   h->partials_cap = partials;
   if (cudaMalloc((void**)&h->partials, partials * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return bail(QS_ERR_OUT_OF_MEMORY); }
   h->mats_cap = std::max<size_t>((size_t)batch * 2 * 16, 2 * 1024) * (h->esize / 2);
@@ -360,12 +423,9 @@ qs_status qs_create(int n, int batch, int rank, qs_mode mode, qs_dtype dtype, vo
   h->cols = 1;
   cudaError_t e = cudaSuccess;
   if (mode == QS_STATEVEC) { h->pending = 1; h->pending_x = 0; }
-  else e = qs::launch_set_basis(h, h->state, n, 1, 0, nullptr);
-  if (mode == QS_FIXED_RANK && e == cudaSuccess)
-    e = cudaMemsetAsync(h->state, 0, h->state_elems * h->esize, h->stream),
-    e = e == cudaSuccess ? qs::launch_set_basis(h, h->state, n, 1, 0, nullptr) : e;
+  else if (mode == QS_DENSITY) e = qs::launch_set_basis(h, h->state, n, 1, 0, nullptr);
+  else if (rank_set_start(h, 0, 0) != QS_OK) return bail(QS_ERR_CUDA);
   if (e != cudaSuccess) return bail(QS_ERR_CUDA);
-  h->real_factor = mode == QS_FIXED_RANK;                 // |0>
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(QS_ERR_CUDA);
   *out = h;
   return QS_OK;
@@ -375,7 +435,7 @@ qs_status qs_destroy(qs_handle h) {
   if (!h) return QS_ERR_INVALID_ARG;
   cudaStreamSynchronize(h->stream);
   void* ptrs[] = {h->state, h->work, h->partials, h->mats, h->small, h->dstatus, h->m_e,
-                  h->m_seed, h->m_traj, h->m_marked, h->ref, h->m_basis};
+                  h->m_seed, h->m_traj, h->m_marked, h->ref, h->m_basis, h->rsmall, h->rc.cols};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (h->hpinned) cudaFreeHost(h->hpinned);
   delete h;
@@ -391,7 +451,7 @@ qs_status qs_info(qs_handle h, int* n, int* batch, int* rank, int* mode, int* dt
   if (rank) *rank = h->rank;
   if (mode) *mode = (int)h->mode;
   if (dtype) *dtype = (int)h->dtype;
-  if (results) *results = h->mode == QS_STATEVEC ? h->batch : 1;
+  if (results) *results = h->mode == QS_DENSITY ? 1 : h->batch;
   return QS_OK;
 }
 
@@ -412,10 +472,7 @@ qs_status qs_set_basis_state(qs_handle h, uint64_t x) {
     QS_CUDA(h, qs::launch_set_basis(h, h->state, 2 * h->n, 1, x * N + x, nullptr));
     h->hermitian = true;
   } else {
-    QS_CUDA(h, cudaMemsetAsync(h->state, 0, h->state_elems * h->esize, h->stream));
-    QS_CUDA(h, qs::launch_set_basis(h, h->state, h->n, 1, x, nullptr));
-    h->cols = 1;
-    h->real_factor = true;
+    return rank_set_start(h, 0, x);
   }
   return QS_OK;
 }
@@ -430,10 +487,7 @@ qs_status qs_set_maximally_entangled(qs_handle h) {
     QS_CUDA(h, qs::launch_set_entangled(h, h->state, 1, 1));
     h->hermitian = true;
   } else {
-    QS_CUDA(h, cudaMemsetAsync(h->state, 0, h->state_elems * h->esize, h->stream));
-    QS_CUDA(h, qs::launch_set_entangled(h, h->state, 1, 0));
-    h->cols = 1;
-    h->real_factor = true;
+    return rank_set_start(h, 1, 0);
   }
   return QS_OK;
 }
@@ -462,7 +516,7 @@ qs_status qs_apply_gate(qs_handle h, const int* targets, int k, const double* U)
   if (h->mode == QS_STATEVEC) return apply_uniform(h, h->state, h->n, h->batch, targets, k, M);
   if (h->mode == QS_FIXED_RANK) {
     if (!all_real(M)) h->real_factor = false;
-    return apply_uniform(h, h->state, h->n, h->cols, targets, k, M);
+    return apply_uniform(h, h->state, h->n, rank_swept(h), targets, k, M);
   }
   if (k <= 2) return dm_apply_channel(h, targets, k, {M});
   // k = 3, 4: U on the row bits t + n and conj(U) on the column bits t, two
@@ -482,7 +536,7 @@ qs_status qs_apply_phase_flip(qs_handle h, uint64_t index) {
   { const qs_status st = qs::materialize_basis(h); if (st != QS_OK) return st; }
   if (index >= (1ull << h->n)) return fail(h, QS_ERR_INVALID_ARG, "index out of range");
   if (h->mode == QS_STATEVEC) { QS_CUDA(h, qs::launch_phase_flip(h, h->state, h->n, h->batch, index, nullptr)); }
-  else if (h->mode == QS_FIXED_RANK) { QS_CUDA(h, qs::launch_phase_flip(h, h->state, h->n, h->cols, index, nullptr)); }
+  else if (h->mode == QS_FIXED_RANK) { QS_CUDA(h, qs::launch_phase_flip(h, h->state, h->n, rank_swept(h), index, nullptr)); }
   else { QS_CUDA(h, qs::launch_dm_flip(h, h->state, h->n, index)); }
   return QS_OK;
 }
@@ -510,7 +564,7 @@ qs_status qs_apply_branch_gate(qs_handle h, const int* targets, int k, const dou
   if (h->mode == QS_DENSITY) return dm_apply_channel(h, targets, k, {B});
   if (h->mode == QS_FIXED_RANK) {
     if (!all_real(B)) h->real_factor = false;
-    return apply_uniform(h, h->state, h->n, h->cols, targets, k, B);
+    return apply_uniform(h, h->state, h->n, rank_swept(h), targets, k, B);
   }
   return apply_uniform(h, h->state, h->n, h->batch, targets, k, B);
 }
@@ -542,6 +596,17 @@ qs_status qs_apply_noisy_gate(qs_handle h, const int* targets, int k, const doub
       QS_CUDA(h, qs::launch_apply_kq(h, h->state, h->n, h->batch, tg, h->mats, true));
     }
     return QS_OK;
+  }
+  if (h->mode == QS_FIXED_RANK) {
+    // the averaged channel, its Kraus set built on the device from e (or from
+    // each member's own e, qs_set_member_noise)
+    qs::KrausGate g{};
+    for (int i = 0; i < 2 * d * d; ++i) g.U[i] = U[i];
+    g.k = k;
+    g.noise = noise;
+    g.e_value = e;
+    g.e_member = h->member_noise ? h->m_e : nullptr;
+    return rank_channel_gate(h, targets, g);
   }
   const auto ks = averaged_kraus(M, k, noise, e);
   if (h->mode == QS_DENSITY) return dm_apply_channel(h, targets, k, ks);
@@ -600,11 +665,13 @@ qs_status qs_truncate_rank(qs_handle h, int r, int normalize) {
   if (!h) return QS_ERR_INVALID_ARG;
   if (h->mode != QS_FIXED_RANK) return fail(h, QS_ERR_NOT_SUPPORTED, "truncation needs FIXED_RANK");
   if (r < 1 || r > h->rank) return fail(h, QS_ERR_INVALID_ARG, "r must be 1..rank");
-  const int M = h->cols;
-  // copy L into the work buffer, then truncate from there back into L
-  QS_CUDA(h, cudaMemcpyAsync(h->work, h->state, (size_t)M * (1ull << h->n) * h->esize,
-                             cudaMemcpyDeviceToDevice, h->stream));
-  return rank_truncate_from_work(h, M, r, normalize);
+  // copy every member's L into its work columns (M_b = m_b), then truncate
+  // from there back into L
+  const size_t col_bytes = (1ull << h->n) * h->esize;
+  QS_CUDA(h, cudaMemcpy2DAsync(h->work, (size_t)h->mcap * col_bytes, h->state, (size_t)h->rank * col_bytes,
+                               (size_t)h->rank * col_bytes, h->batch, cudaMemcpyDeviceToDevice, h->stream));
+  QS_CUDA(h, cudaMemcpyAsync(h->rc.M, h->m_cols.data(), h->batch * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  return rank_truncate_work(h, 1, r, normalize);
 }
 
 qs_status qs_set_tensor_cores(qs_handle h, int on) {
@@ -638,12 +705,13 @@ static qs_status upload_ref(qs_handle h, const double* ref, void* dst) {
 static qs_status fidelity_dev(qs_handle h, const void* phi_dev, double* out) {
   double* o = h->small + kSmallOut;
   if (h->mode == QS_STATEVEC) {
-    QS_CUDA(h, qs::launch_dot(h, h->state, phi_dev, h->n, h->batch, false, o));
+    QS_CUDA(h, qs::launch_dot(h, h->state, phi_dev, h->n, h->batch, 1, o));
     return read_out(h, out, h->batch);
   }
   if (h->mode == QS_FIXED_RANK) {
-    QS_CUDA(h, qs::launch_dot(h, h->state, phi_dev, h->n, h->cols, true, o));
-    return read_out(h, out, 1);
+    const int cols = rank_swept(h);
+    QS_CUDA(h, qs::launch_dot(h, h->state, phi_dev, h->n, cols, cols / h->batch, o));
+    return read_out(h, out, h->batch);
   }
   QS_CUDA(h, qs::launch_dm_expect(h, h->state, phi_dev, h->n, o));
   return read_out(h, out, 1);
@@ -657,12 +725,13 @@ qs_status qs_fidelity(qs_handle h, const double* ref, uint64_t ref_basis, double
   if (!ref) {
     if (ref_basis >= N) return fail(h, QS_ERR_INVALID_ARG, "basis index out of range");
     if (h->mode == QS_STATEVEC) {
-      QS_CUDA(h, qs::launch_basis_prob(h, h->state, h->n, h->batch, ref_basis, false, o));
+      QS_CUDA(h, qs::launch_basis_prob(h, h->state, h->n, h->batch, ref_basis, 1, o));
       return read_out(h, out, h->batch);
     }
     if (h->mode == QS_FIXED_RANK) {
-      QS_CUDA(h, qs::launch_basis_prob(h, h->state, h->n, h->cols, ref_basis, true, o));
-      return read_out(h, out, 1);
+      const int cols = rank_swept(h);
+      QS_CUDA(h, qs::launch_basis_prob(h, h->state, h->n, cols, ref_basis, cols / h->batch, o));
+      return read_out(h, out, h->batch);
     }
     // rho[x][x]
     double v[2] = {0.0, 0.0};
@@ -726,7 +795,7 @@ qs_status qs_fidelity_ref(qs_handle h, qs_handle ref, int first, int count, doub
   { const qs_status st = qs::materialize_basis(ref); if (st != QS_OK) return fail(h, st, ref->err); }
   QS_CUDA(h, cudaStreamSynchronize(ref->stream));
   const char* psi = (const char*)h->state + ((size_t)first << h->n) * h->esize;
-  QS_CUDA(h, qs::launch_dot(h, psi, ref->state, h->n, count, false, h->small + kSmallOut));
+  QS_CUDA(h, qs::launch_dot(h, psi, ref->state, h->n, count, 1, h->small + kSmallOut));
   return read_out(h, out, count);
 }
 
@@ -735,12 +804,13 @@ qs_status qs_trace(qs_handle h, double* out) {
   { const qs_status st = qs::materialize_basis(h); if (st != QS_OK) return st; }
   double* o = h->small + kSmallOut;
   if (h->mode == QS_STATEVEC) {
-    QS_CUDA(h, qs::launch_norm(h, h->state, h->n, h->batch, false, o));
+    QS_CUDA(h, qs::launch_norm(h, h->state, h->n, h->batch, 1, o));
     return read_out(h, out, h->batch);
   }
   if (h->mode == QS_FIXED_RANK) {
-    QS_CUDA(h, qs::launch_norm(h, h->state, h->n, h->cols, true, o));
-    return read_out(h, out, 1);
+    const int cols = rank_swept(h);
+    QS_CUDA(h, qs::launch_norm(h, h->state, h->n, cols, cols / h->batch, o));
+    return read_out(h, out, h->batch);
   }
   QS_CUDA(h, qs::launch_dm_trace(h, h->state, h->n, o));
   return read_out(h, out, 1);
@@ -820,7 +890,23 @@ qs_status qs_set_rank_columns(qs_handle h, int m) {
   if (!h) return QS_ERR_INVALID_ARG;
   if (h->mode != QS_FIXED_RANK) return fail(h, QS_ERR_NOT_SUPPORTED, "needs FIXED_RANK");
   if (m < 1 || m > h->rank) return fail(h, QS_ERR_INVALID_ARG, "m must be 1..rank");
-  h->cols = m;
+  std::fill(h->m_cols.begin(), h->m_cols.end(), m);
+  return rank_upload_counts(h);
+}
+
+qs_status qs_set_member_ranks(qs_handle h, const int* ranks) {
+  if (!h || !ranks) return QS_ERR_INVALID_ARG;
+  if (h->mode != QS_FIXED_RANK) return fail(h, QS_ERR_NOT_SUPPORTED, "needs FIXED_RANK");
+  for (int b = 0; b < h->batch; ++b)
+    if (ranks[b] < 1 || ranks[b] > h->rank) return fail(h, QS_ERR_INVALID_ARG, "member ranks must be 1..rank");
+  h->m_rank.assign(ranks, ranks + h->batch);
+  return rank_upload_counts(h);
+}
+
+qs_status qs_get_member_columns(qs_handle h, int* out) {
+  if (!h || !out) return QS_ERR_INVALID_ARG;
+  if (h->mode != QS_FIXED_RANK) return fail(h, QS_ERR_NOT_SUPPORTED, "needs FIXED_RANK");
+  std::copy(h->m_cols.begin(), h->m_cols.end(), out);
   return QS_OK;
 }
 
@@ -840,7 +926,7 @@ qs_status qs_set_trajectory_offset(qs_handle h, uint64_t offset) {
 qs_status qs_set_member_noise(qs_handle h, const double* e, const uint64_t* seed, const uint64_t* traj,
                               const uint64_t* marked) {
   if (!h) return QS_ERR_INVALID_ARG;
-  if (h->mode != QS_STATEVEC) return fail(h, QS_ERR_NOT_SUPPORTED, "per-member noise needs STATEVEC");
+  if (h->mode == QS_DENSITY) return fail(h, QS_ERR_NOT_SUPPORTED, "per-member noise needs STATEVEC or FIXED_RANK");
   if (!e && !seed && !traj && !marked) { h->member_noise = false; h->member_marked = false; return QS_OK; }
   if (!e || !seed || !traj) return fail(h, QS_ERR_INVALID_ARG, "e, seed and traj must all be given");
   double e_max = 0.0;

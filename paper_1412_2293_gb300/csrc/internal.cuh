@@ -56,6 +56,28 @@ struct NoiseSrc {
   uint64_t traj0;                        // member b draws traj0 + b
 };
 
+// Column counts of the members of a FIXED_RANK handle (device arrays of
+// `batch` ints): live columns m_b, truncation rank r_b, columns M_b of the
+// channel in progress, columns kept by its truncation.
+struct RankCounts {
+  int* cols;
+  int* rank;
+  int* M;
+  int* keep;
+};
+
+// A noisy gate whose xi-averaged Kraus set (Eqs. 6, 9) the fixed-rank
+// expansion builds on the device for each member from its noise level e_b:
+// e_member[b] if set, else *e_run if set, else e_value.
+struct KrausGate {
+  double U[32];                          // 2^k x 2^k interleaved complex
+  int k;                                 // 1 or 2
+  int noise;                             // qs_noise
+  double e_value;
+  const double* e_member;
+  const double* e_run;
+};
+
 // ------------------------------------------------------------- error state
 struct Status {
   qs_status code = QS_OK;
@@ -78,11 +100,18 @@ struct qs_ctx {
   void* state = nullptr;                 // STATEVEC batch*2^n, DENSITY 4^n, FIXED_RANK rank*2^n
   size_t state_elems = 0;
 
-  // fixed rank: L' (up to kMaxGramDim columns) and the live column count
+  // FIXED_RANK: `batch` members, member b's factor in columns [b rank, (b+1)
+  // rank) of the state and its L' in columns [b mcap, (b+1) mcap) of `work`;
+  // column counts per member on the device (rc) and mirrored on the host
+  // (m_cols, m_rank; `cols` = the largest live count)
   void* work = nullptr;
   size_t work_elems = 0;
+  int mcap = 0;
   int cols = 1;
   int normalize = 0;
+  qs::RankCounts rc{};
+  double* rsmall = nullptr;              // per member: Gram, eigenvectors, eigenvalues, scale, Kraus sets
+  std::vector<int> m_cols, m_rank;
   // FIXED_RANK: every entry of L has a zero imaginary part (real start, real
   // gates and Kraus operators so far); the channel kernels then use real
   // arithmetic (the same results, a quarter of the FP64 work)
@@ -165,36 +194,51 @@ cudaError_t launch_dm_relax(qs_ctx* h, void* rho, int n, const int* qubits, int 
 cudaError_t launch_dm_superop1_herm(qs_ctx* h, void* rho, int n, int t, const void* S_dev);
 
 // reductions (results land in h->small, as doubles)
+// reductions over `members` state vectors of 2^n; with group > 1 the values
+// of each run of `group` consecutive members are added (a fixed-rank
+// member's columns): out[members / group]
 cudaError_t launch_dot(qs_ctx* h, const void* psi, const void* ref, int n, int members,
-                       bool sum_members, double* out_dev);
-cudaError_t launch_norm(qs_ctx* h, const void* psi, int n, int members, bool sum_members,
+                       int group, double* out_dev);
+cudaError_t launch_norm(qs_ctx* h, const void* psi, int n, int members, int group,
                         double* out_dev);
 cudaError_t launch_basis_prob(qs_ctx* h, const void* psi, int n, int members, uint64_t x,
-                              bool sum_members, double* out_dev);
+                              int group, double* out_dev);
 cudaError_t launch_dm_trace(qs_ctx* h, const void* rho, int n, double* out_dev);
 cudaError_t launch_dm_expect(qs_ctx* h, const void* rho, const void* ref, int n, double* out_dev);
 cudaError_t launch_convert_ref(qs_ctx* h, const double* src_dev, void* dst, size_t count);
 
-// fixed rank
-cudaError_t launch_kraus_expand(qs_ctx* h, const void* L, void* Lp, int n, int m, const Targets& tg, bool real,
-                                const void* E_dev, int K);
-cudaError_t launch_gram(qs_ctx* h, const void* Lp, int n, int M, bool real, double* G_dev);
-cudaError_t launch_eig_truncate(qs_ctx* h, const double* G_dev, int M, int r, int normalize,
-                                double* W_dev, double* lam_dev, double* scale_dev, int* keep_dev,
-                                int* status_dev);
-cudaError_t launch_project(qs_ctx* h, const void* Lp, void* L, int n, int M, bool real, const double* W_dev,
-                           const double* scale_dev, const int* keep_dev);
+// fixed rank, every member of the handle (counts in h->rc): expansion of the
+// factors into L' with K Kraus operators (member b's at E + b e_stride,
+// e_stride = 0: shared), FP64 Gram matrices, eigensolver and truncation (to
+// the members' ranks, or to trunc_r > 0), projection back into the factors.
+// max_* are the largest counts over the members (launch sizes).
+cudaError_t launch_kraus_expand(qs_ctx* h, const Targets& tg, bool real, const double* E_dev, int K, int e_stride,
+                                int max_cols);
+// the same with the Kraus set of a noisy gate built on the device per member
+cudaError_t launch_kraus_expand_gate(qs_ctx* h, const Targets& tg, bool real, const KrausGate& g, int max_cols);
+// Kraus operators of a noisy gate's averaged channel (2 for k = 1 or phase
+// noise, 4 for k = 2 rotation noise)
+inline int kraus_count(int k, int noise) { return noise == QS_NOISE_ROTATION && k == 2 ? 4 : 2; }
+cudaError_t launch_gram(qs_ctx* h, bool real, int max_M);
+cudaError_t launch_eig_truncate(qs_ctx* h, int trunc_r, int normalize);
+cudaError_t launch_project(qs_ctx* h, bool real, int K, int max_keep);
+int gram_rows_per_block(int n);
+// one-time kernel attributes of the fixed-rank kernels (outside any capture)
+cudaError_t rank_kernel_attributes();
+size_t gram_partials_doubles(int n, int members);
 
 // debug noise
 cudaError_t launch_debug_noise(uint64_t seed, uint64_t traj, uint64_t gate_id, int count,
                                uint32_t* words_dev, double* normals_dev, cudaStream_t s);
 
-// layout of the small FP64 scratch block of a handle (doubles)
+// layout of a fixed-rank member's FP64 block in h->rsmall (doubles, stride
+// kRankStride), and of the results in h->small
 constexpr size_t kSmallG = 0;          // Gram matrix, 2 * 32 * 32
 constexpr size_t kSmallW = 2048;       // eigenvectors, 2 * 32 * 16
 constexpr size_t kSmallLam = 3072;     // eigenvalues, 32
 constexpr size_t kSmallScale = 3104;   // 1
 constexpr size_t kSmallE = 3200;       // Kraus operators, <= 2 * 8 * 16
+constexpr int kRankStride = 3456;
 constexpr size_t kSmallOutIndex = 4096;  // results, batch doubles
 
 // Write a pending basis start state into memory (no-op when none is pending).

@@ -456,9 +456,20 @@ struct PassPlan {
 };
 
 struct Step {
-  int kind;               // 0 = fused pass, 1 = single gate, 2 = density-matrix diagonal block
+  int kind;               // 0 = fused pass, 1 = single gate, 2 = density-matrix diagonal block,
+                          // 5 = the gates of a fixed-rank plan (RankOp list)
   int pass = -1;
   int gate = -1;          // single gate, or the diagonal block's index
+};
+
+// One gate of a fixed-rank plan, applied to every member with launch shapes
+// fixed when the plan is made (the members' column counts stay on the device).
+struct RankOp {
+  int kind;               // 0 flip, 1 one-qubit unitary, 2 diagonal, 3 two-qubit dense, 4 noisy channel
+  int gate;
+  size_t mat_off = 0;     // kinds 2, 3: offset (elements of the handle's precision) in d_rank_mats
+  uint32_t mask = 0;      // kind 2: local indices whose factor is not 1
+  bool real = true;       // the gate keeps a real factor real
 };
 
 struct DmBlock {          // density matrix: a run of diagonal channels (k_dm_diag_block)
@@ -492,6 +503,9 @@ struct qs_plan_s {
   void* d_params = nullptr;       // per-member gate parameters of the running pass (shared by the passes)
   void* d_alpha = nullptr;        // out factors of the running pass (shared by the passes)
   std::vector<DmBlock> dm_blocks;
+  std::vector<RankOp> rank_ops;   // FIXED_RANK plans
+  void* d_rank_mats = nullptr;
+  int rank_variant = 0;           // the running variant: real start, per-member noise, normalisation
   int colb = 3;
   int low_cfg = 0;                // kernel configuration of each window geometry (see launch_pass_kernel)
   int high_cfg = 0;
@@ -1218,9 +1232,71 @@ qs_status run_dm_block(qs_plan p, const DmBlock& b, const RunParams& rp) {
   return e == cudaSuccess ? QS_OK : pfail(p, QS_ERR_CUDA, cudaGetErrorString(e));
 }
 
+qs_status run_rank_ops(qs_plan p);
+
 qs_status run_step(qs_plan p, const Step& st, const RunParams& rp) {
   if (st.kind == 2) return run_dm_block(p, p->dm_blocks[st.gate], rp);
+  if (st.kind == 5) return run_rank_ops(p);
   return run_single(p, p->gates[st.gate], rp, st.gate);
+}
+
+// The gates of a fixed-rank plan on every member (enqueued on h->stream, so
+// they can be captured): unitaries on all columns (dead ones are zero),
+// noisy gates as the averaged channel built on the device from the run's e
+// (or the members' own), expansion, Gram matrices, eigensolver, projection.
+qs_status run_rank_ops(qs_plan p) {
+  qs_ctx* h = p->h;
+  const int members = h->batch * h->rank;
+  bool real = (p->rank_variant >> 2) & 1;
+  const bool member_e = (p->rank_variant >> 1) & 1;
+  const int normalize = p->rank_variant & 1;
+  const size_t esz = h->esize / 2;
+  cudaError_t e = cudaSuccess;
+  for (const RankOp& op : p->rank_ops) {
+    const qs_gate& g = p->gates[op.gate].g;
+    if (!op.real) real = false;
+    if (op.kind == 0) {
+      e = launch_phase_flip(h, h->state, h->n, members, g.index, nullptr);
+    } else if (op.kind == 1) {
+      e = launch_apply_1q(h, h->state, h->n, members, g.targets[0], g.U, nullptr);
+    } else {
+      const Targets tg = make_targets(h->n, g.targets, g.k);
+      const void* mat = static_cast<const char*>(p->d_rank_mats) + op.mat_off * esz;
+      if (op.kind == 2) {
+        e = launch_apply_diag(h, h->state, h->n, members, tg, mat, false, op.mask);
+      } else if (op.kind == 3) {
+        e = launch_apply_kq(h, h->state, h->n, members, tg, mat, false, op.real);
+      } else {
+        KrausGate kg{};
+        for (int i = 0; i < 32; ++i) kg.U[i] = g.U[i];
+        kg.k = g.k;
+        kg.noise = g.noise;
+        kg.e_member = member_e ? h->m_e : nullptr;
+        kg.e_run = &p->d_run->e;
+        const int K = kraus_count(g.k, g.noise);
+        e = launch_kraus_expand_gate(h, tg, real, kg, h->rank);
+        if (e == cudaSuccess) e = launch_gram(h, real, std::min(kMaxGramDim, K * h->rank));
+        if (e == cudaSuccess) e = launch_eig_truncate(h, 0, normalize);
+        if (e == cudaSuccess) e = launch_project(h, real, K, h->rank);
+      }
+    }
+    if (e != cudaSuccess) return pfail(p, QS_ERR_CUDA, std::string("fixed-rank plan: ") + cudaGetErrorString(e));
+  }
+  return QS_OK;
+}
+
+// Host mirror of a fixed-rank run: column counts (keep = min(r_b, K m_b) per
+// channel) and whether the factor is still real.
+void advance_rank_mirror(qs_plan p) {
+  qs_ctx* h = p->h;
+  for (const RankOp& op : p->rank_ops) {
+    if (!op.real) h->real_factor = false;
+    if (op.kind != 4) continue;
+    const qs_gate& g = p->gates[op.gate].g;
+    const int K = kraus_count(g.k, g.noise);
+    for (int b = 0; b < h->batch; ++b) h->m_cols[b] = std::min(h->m_rank[b], K * h->m_cols[b]);
+  }
+  h->cols = *std::max_element(h->m_cols.begin(), h->m_cols.end());
 }
 
 qs_status run_single(qs_plan p, const PGate& g, const RunParams& rp, int pos) {
@@ -1309,6 +1385,8 @@ qs_status run_plan(qs_plan p, double e, uint64_t seed, uint64_t gate_id0, int wa
   // the pinned run block may still be read by an earlier launch of the graph
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "stream sync");
   p->stable = two_shear_safe(p->gates, h->member_noise ? h->m_e_max : e) ? 0 : 1;
+  if (h->mode == QS_FIXED_RANK)
+    p->rank_variant = (h->real_factor ? 4 : 0) | (h->member_noise ? 2 : 0) | (h->normalize ? 1 : 0);
   p->h_run->e = e;
   p->h_run->seed = seed;
   p->h_run->gate_id0 = gate_id0;
@@ -1317,14 +1395,16 @@ qs_status run_plan(qs_plan p, double e, uint64_t seed, uint64_t gate_id0, int wa
   // the run owns the start state from here on: later steps (single gates)
   // must not write the basis state again
   if (synth) h->pending = 0;
-  const bool has_single = std::any_of(p->steps.begin(), p->steps.end(), [](const Step& s) { return s.kind != 0; });
+  // fused passes and fixed-rank plans replay as graphs; other single steps run eagerly
+  const bool has_single = std::any_of(p->steps.begin(), p->steps.end(),
+                                      [](const Step& s) { return s.kind != 0 && s.kind != 5; });
   qs_status st = QS_OK;
   if (has_single) {
     if (cudaMemcpyAsync(p->d_run, p->h_run, sizeof(RunParams), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
       return pfail(p, QS_ERR_CUDA, "run params copy");
     st = enqueue_run(p, h->stream, synth, fid);
   } else {
-    const int v = p->stable * 6 + synth * 2 + fid;
+    const int v = h->mode == QS_FIXED_RANK ? p->rank_variant : p->stable * 6 + synth * 2 + fid;
     if (p->exec[v] && (p->graph_member_noise[v] != h->member_noise || p->graph_member_marked[v] != h->member_marked ||
                        p->graph_timing[v] != p->timing || p->graph_wait_polls[v] != h->wait_polls)) {
       cudaGraphExecDestroy(p->exec[v]);
@@ -1351,6 +1431,7 @@ qs_status run_plan(qs_plan p, double e, uint64_t seed, uint64_t gate_id0, int wa
     }
     if (cudaGraphLaunch(p->exec[v], h->stream) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "graph launch");
   }
+  if (st == QS_OK && h->mode == QS_FIXED_RANK) advance_rank_mirror(p);
   return st;
 }
 
@@ -1394,6 +1475,49 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
   std::vector<int> rem;
   for (int i = 0; i < num_gates; ++i) rem.push_back(i);
   std::vector<std::vector<int>> dm_groups;
+  std::vector<double> rank_mats;                         // matrices of kinds 2, 3 (doubles, interleaved)
+  if (h->mode == QS_FIXED_RANK) {
+    // every gate on every member with launch shapes fixed here; the whole
+    // circuit replays as one graph
+    for (int i : rem) {
+      const PGate& g = p->gates[i];
+      RankOp op{};
+      op.gate = i;
+      if (g.g.kind == QS_GATE_FLIP) {
+        op.kind = 0;
+      } else {
+        const int d = 1 << g.g.k;
+        for (const auto& v : g.U) if (v.imag() != 0.0) op.real = false;
+        if (g.g.noisy) {
+          op.kind = 4;
+          if (kraus_count(g.g.k, g.g.noise) * h->rank > kMaxGramDim) {
+            delete p;
+            h->err = "Kraus count times rank exceeds the Gram-matrix limit of 32";
+            return QS_ERR_NOT_SUPPORTED;
+          }
+        } else if (g.g.k == 1 && !is_diag(g.U, 2)) {
+          op.kind = 1;
+        } else if (is_diag(g.U, d)) {
+          op.kind = 2;
+          op.mat_off = rank_mats.size() / 2;
+          for (int l = 0; l < d; ++l) {
+            const cd f = g.U[(size_t)l * d + l];
+            rank_mats.push_back(f.real());
+            rank_mats.push_back(f.imag());
+            if (f != cd(1.0, 0.0)) op.mask |= 1u << l;
+          }
+          if (!op.mask) continue;                         // the identity
+        } else {
+          op.kind = 3;
+          op.mat_off = rank_mats.size() / 2;
+          for (const auto& v : g.U) { rank_mats.push_back(v.real()); rank_mats.push_back(v.imag()); }
+        }
+      }
+      p->rank_ops.push_back(op);
+    }
+    p->steps.push_back(Step{5, -1, -1});
+    rem.clear();
+  }
   if (h->mode == QS_DENSITY) {
     // runs of diagonal channels become one sweep each (k_dm_diag_block)
     auto dm_diag = [&](const PGate& g) {
@@ -1501,6 +1625,14 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
     if (st == QS_OK) st = upload(p, &b.d_mask, mask);
     p->dm_blocks.push_back(b);
   }
+  if (st == QS_OK && !rank_mats.empty()) {
+    if (h->dtype == QS_C64) {
+      std::vector<float> f(rank_mats.begin(), rank_mats.end());
+      st = upload(p, reinterpret_cast<float**>(&p->d_rank_mats), f);
+    } else {
+      st = upload(p, reinterpret_cast<double**>(&p->d_rank_mats), rank_mats);
+    }
+  }
   size_t fid_tiles = 0;
   // one parameter buffer and one out-factor table serve every pass: a pass's
   // precompute runs on the same stream right before the pass itself
@@ -1542,6 +1674,11 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
   p->kernels = p->launches;
   for (const Step& s : p->steps)
     if (s.kind == 0 && p->passes[s.pass].d_alpha) ++p->kernels;
+  if (!p->rank_ops.empty()) {
+    p->kernels -= 1;
+    for (const RankOp& op : p->rank_ops) p->kernels += op.kind == 4 ? 5 : 1;   // channel: expand, Gram x 2, eig, project
+    if (rank_kernel_attributes() != cudaSuccess) { qs_plan_destroy(p); return QS_ERR_CUDA; }
+  }
   *out = p;
   return QS_OK;
 }
@@ -1745,6 +1882,7 @@ qs_status qs_plan_destroy(qs_plan p) {
   }
   if (p->d_run) cudaFree(p->d_run);
   if (p->h_run) cudaFreeHost(p->h_run);
+  if (p->d_rank_mats) cudaFree(p->d_rank_mats);
   for (auto& e : p->events) cudaEventDestroy(e);
   delete p;
   return QS_OK;

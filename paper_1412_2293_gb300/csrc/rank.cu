@@ -12,6 +12,8 @@
 // projection L <- scale * L' W_r.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <atomic>
 #include <type_traits>
 
 #include "internal.cuh"
@@ -21,32 +23,87 @@ namespace qs {
 namespace {
 
 constexpr int kExpBlock = 256;
-constexpr int kGramRows = 64;            // rows of L' per Gram block
+constexpr int kGramRows = 64;            // rows of L' per shared-memory tile of the Gram kernel
+constexpr int kGramTarget = 512;         // about this many row blocks per member (fixed by n)
+constexpr int kTriMax = kMaxGramDim * (kMaxGramDim + 1) / 2;
 constexpr int kJacobiSweeps = 40;        // bound on the eigensolver's sweeps
 constexpr double kTieTol = 1e-10;        // cluster: within 1e-10 * Lambda_1
 constexpr double kGsAccept = 1e-3;       // residual norm to accept a projection
 constexpr double kGsFallback = 1e-8;
 constexpr double kRotTol = 4e-16;        // rotate while |a_pq| > kRotTol * max|a_ii|
+constexpr int kJacobiSweeps32 = 12;      // bound on the FP32 pre-pass
+constexpr double kRotTol32 = 1e-6;       // FP32 pre-pass: rotate while |a_pq| > this * max|a_ii|
 
 __device__ __forceinline__ uint64_t insert0(uint64_t v, int s) {
   return ((v >> s) << (s + 1)) | (v & ((1ull << s) - 1));
 }
 
-// Lp[a*m + c] = E_a L[c]; one thread per (group, column).  REAL: L and the
-// E_a are real (imaginary parts zero), real arithmetic.
+// Lp_b[a m_b + c] = E_a L_b[c] for member b = blockIdx.y; one thread per
+// (group, column).  The member's Kraus operators are E + b e_stride (e_stride
+// = 0: one set for every member).  Block (0, b) records M_b = K m_b.  REAL: L
+// and the E_a are real (imaginary parts zero), real arithmetic.
+// Entry (row, col) of operator `op` of the xi-averaged Kraus set of a noisy
+// gate U (Eqs. 5-6 and 8-9) at noise level e: rotation noise -> U N with N
+// the tensor product over the targets (target 0 the low local bit) of
+// sqrt(l1) I or sqrt(l2) J, J = [[0, 1], [-1, 0]], l1,2 = (1 +- e^{-2e^2})/2;
+// phase noise -> U diag(1, .., 1, sqrt P) and U diag(0, .., 0, sqrt(1 - P)),
+// P = e^{-e^2}.
+__device__ double2 kraus_entry(const KrausGate& g, double e, int op, int row, int col) {
+  const int D = 1 << g.k;
+  double nre[4];                                         // column `col` of N (real)
+  if (g.noise == QS_NOISE_ROTATION) {
+    const double q = exp(-2.0 * e * e);
+    const double s1 = sqrt(0.5 * (1.0 + q)), s2 = sqrt(0.5 * (1.0 - q));
+    for (int x = 0; x < D; ++x) {
+      double v = 1.0;
+      for (int j = 0; j < g.k; ++j) {
+        const int w = (op >> j) & 1, rb = (x >> j) & 1, cb = (col >> j) & 1;
+        v *= w == 0 ? (rb == cb ? s1 : 0.0) : (rb == 0 && cb == 1 ? s2 : (rb == 1 && cb == 0 ? -s2 : 0.0));
+      }
+      nre[x] = v;
+    }
+  } else {
+    const double P = exp(-e * e);
+    for (int x = 0; x < D; ++x) nre[x] = 0.0;
+    if (op == 0) nre[col] = col == D - 1 ? sqrt(P) : 1.0;
+    else if (col == D - 1) nre[col] = sqrt(1.0 - P);
+  }
+  double re = 0.0, im = 0.0;                             // (U N)[row][col]
+  for (int x = 0; x < D; ++x) {
+    re += g.U[2 * (row * D + x)] * nre[x];
+    im += g.U[2 * (row * D + x) + 1] * nre[x];
+  }
+  return make_double2(re, im);
+}
+
 template <typename R, int K_Q, bool REAL>
 __global__ void __launch_bounds__(kExpBlock) k_kraus_expand(const cplx<R>* __restrict__ L,
-                                                            cplx<R>* __restrict__ Lp, int n, int m,
-                                                            Targets tg, const double* __restrict__ E,
-                                                            int K) {
+                                                            cplx<R>* __restrict__ Lp, int n, int rcap, int mcap,
+                                                            Targets tg, const double* __restrict__ E, int K,
+                                                            int e_stride, RankCounts rc, const KrausGate g) {
   using C = cplx<R>;
   constexpr int D = 1 << K_Q;
   __shared__ C sE[8 * D * D];
-  for (int i = threadIdx.x; i < K * D * D; i += blockDim.x) sE[i] = mk<R>((R)E[2 * i], (R)E[2 * i + 1]);
+  const int b = blockIdx.y;
+  if (g.k > 0) {
+    // the member's averaged Kraus set, built here from its noise level
+    const double e = g.e_member ? g.e_member[b] : (g.e_run ? *g.e_run : g.e_value);
+    for (int i = threadIdx.x; i < K * D * D; i += blockDim.x) {
+      const double2 v = kraus_entry(g, e, i / (D * D), (i / D) % D, i % D);
+      sE[i] = mk<R>((R)v.x, (R)v.y);
+    }
+  } else {
+    const double* Eb = E + (size_t)b * e_stride;
+    for (int i = threadIdx.x; i < K * D * D; i += blockDim.x) sE[i] = mk<R>((R)Eb[2 * i], (R)Eb[2 * i + 1]);
+  }
+  const int m = rc.cols[b];
+  if (blockIdx.x == 0 && threadIdx.x == 0) rc.M[b] = K * m;
   __syncthreads();
   const uint64_t N = 1ull << n;
   const uint64_t groups = N >> K_Q;
   const uint64_t total = groups * (uint64_t)m;
+  const C* Lb = L + (uint64_t)b * rcap * N;
+  C* Lpb = Lp + (uint64_t)b * mcap * N;
   for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total;
        w += (uint64_t)gridDim.x * blockDim.x) {
     const int c = (int)(w / groups);
@@ -57,9 +114,9 @@ __global__ void __launch_bounds__(kExpBlock) k_kraus_expand(const cplx<R>* __res
     if constexpr (REAL) {
       R v[D];
 #pragma unroll
-      for (int l = 0; l < D; ++l) v[l] = L[(uint64_t)c * N + base + tg.off[l]].x;
+      for (int l = 0; l < D; ++l) v[l] = Lb[(uint64_t)c * N + base + tg.off[l]].x;
       for (int a = 0; a < K; ++a) {
-        C* out = Lp + (uint64_t)(a * m + c) * N + base;
+        C* out = Lpb + (uint64_t)(a * m + c) * N + base;
 #pragma unroll
         for (int r = 0; r < D; ++r) {
           R acc = R(0);
@@ -71,9 +128,9 @@ __global__ void __launch_bounds__(kExpBlock) k_kraus_expand(const cplx<R>* __res
     } else {
       C v[D];
 #pragma unroll
-      for (int l = 0; l < D; ++l) v[l] = L[(uint64_t)c * N + base + tg.off[l]];
+      for (int l = 0; l < D; ++l) v[l] = Lb[(uint64_t)c * N + base + tg.off[l]];
       for (int a = 0; a < K; ++a) {
-        C* out = Lp + (uint64_t)(a * m + c) * N + base;
+        C* out = Lpb + (uint64_t)(a * m + c) * N + base;
 #pragma unroll
         for (int r = 0; r < D; ++r) {
           C acc = mk<R>(R(0), R(0));
@@ -86,61 +143,97 @@ __global__ void __launch_bounds__(kExpBlock) k_kraus_expand(const cplx<R>* __res
   }
 }
 
-// Gram partials: block b sums rows [b*kGramRows, (b+1)*kGramRows) for every
-// (p <= q), one thread per entry of the upper triangle; partial layout
-// [block][p][q] complex.  REAL: real arithmetic (imaginary parts are zero).
+// (p, q), p <= q, of entry idx of the upper triangle of an M x M matrix,
+// row-major
+__device__ __forceinline__ void tri_pq(int idx, int M, int* p, int* q) {
+  int pp = 0, rem = idx;
+  while (rem >= M - pp) { rem -= M - pp; ++pp; }
+  *p = pp;
+  *q = pp + rem;
+}
+
+// Gram partials of member b = blockIdx.y: block x sums rows
+// [x rows_per_block, (x + 1) rows_per_block) of L'_b, in tiles of kGramRows
+// rows through shared memory, for every entry (p <= q) of the upper triangle
+// (a thread owns entries idx, idx + 256, ...; each entry a fixed-order FP64
+// sum).  Partial layout [member][block][kTriMax] complex.  The row split
+// depends only on n, so a member's result does not depend on the batch.
 template <typename R, bool REAL>
-__global__ void __launch_bounds__(256) k_gram_partials(const cplx<R>* __restrict__ Lp, int n, int M,
+__global__ void __launch_bounds__(256) k_gram_partials(const cplx<R>* __restrict__ Lp, int n, int mcap,
+                                                       int rows_per_block, RankCounts rc,
                                                        double* __restrict__ partials) {
   using T = typename std::conditional<REAL, double, double2>::type;
+  constexpr int kOwn = (kTriMax + 255) / 256;
   __shared__ T tile[kMaxGramDim][kGramRows + 1];
-  const uint64_t N = 1ull << n;
-  const uint64_t r0 = (uint64_t)blockIdx.x * kGramRows;
-  for (int i = threadIdx.x; i < M * kGramRows; i += blockDim.x) {
-    const int p = i / kGramRows, x = i % kGramRows;
-    const uint64_t row = r0 + x;
-    const cplx<R> a = row < N ? Lp[(uint64_t)p * N + row] : mk<R>(R(0), R(0));
-    if constexpr (REAL) tile[p][x] = a.x;
-    else tile[p][x] = make_double2(a.x, a.y);
-  }
-  __syncthreads();
-  double* out = partials + (size_t)blockIdx.x * 2 * M * M;
+  const int b = blockIdx.y;
+  const int M = rc.M[b];
   const int tri = M * (M + 1) / 2;
-  for (int idx = threadIdx.x; idx < tri; idx += blockDim.x) {
-    // idx -> (p, q), p <= q, row-major over the upper triangle
-    int p = 0, rem = idx;
-    while (rem >= M - p) { rem -= M - p; ++p; }
-    const int q = p + rem;
-    double re = 0.0, im = 0.0;
-    if constexpr (REAL) {
-      double re2 = 0.0;
-      for (int x = 0; x < kGramRows; x += 2) {
-        re = fma(tile[p][x], tile[q][x], re);
-        re2 = fma(tile[p][x + 1], tile[q][x + 1], re2);
-      }
-      re += re2;
-    } else {
-      for (int x = 0; x < kGramRows; ++x) {
-        const double2 a = tile[p][x], b = tile[q][x];
-        re += a.x * b.x + a.y * b.y;       // conj(a) * b
-        im += a.x * b.y - a.y * b.x;
+  const uint64_t N = 1ull << n;
+  const cplx<R>* Lpb = Lp + (uint64_t)b * mcap * N;
+  int ep[kOwn], eq[kOwn];
+  double re[kOwn], im[kOwn], re2[kOwn];
+#pragma unroll
+  for (int j = 0; j < kOwn; ++j) {
+    const int idx = threadIdx.x + 256 * j;
+    ep[j] = eq[j] = 0;
+    if (idx < tri) tri_pq(idx, M, &ep[j], &eq[j]);
+    re[j] = im[j] = re2[j] = 0.0;
+  }
+  const uint64_t r0 = (uint64_t)blockIdx.x * rows_per_block;
+  for (int s = 0; s < rows_per_block; s += kGramRows) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < M * kGramRows; i += blockDim.x) {
+      const int p = i / kGramRows, x = i % kGramRows;
+      const uint64_t row = r0 + s + x;
+      const cplx<R> a = row < N ? Lpb[(uint64_t)p * N + row] : mk<R>(R(0), R(0));
+      if constexpr (REAL) tile[p][x] = a.x;
+      else tile[p][x] = make_double2(a.x, a.y);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kOwn; ++j) {
+      if (threadIdx.x + 256 * j >= tri) continue;
+      const int p = ep[j], q = eq[j];
+      if constexpr (REAL) {
+        for (int x = 0; x < kGramRows; x += 2) {
+          re[j] = fma(tile[p][x], tile[q][x], re[j]);
+          re2[j] = fma(tile[p][x + 1], tile[q][x + 1], re2[j]);
+        }
+      } else {
+        for (int x = 0; x < kGramRows; ++x) {
+          const double2 a = tile[p][x], c = tile[q][x];
+          re[j] += a.x * c.x + a.y * c.y;        // conj(a) * c
+          im[j] += a.x * c.y - a.y * c.x;
+        }
       }
     }
-    out[2 * (p * M + q)] = re;
-    out[2 * (p * M + q) + 1] = im;
+  }
+  double* out = partials + ((size_t)b * gridDim.x + blockIdx.x) * 2 * kTriMax;
+#pragma unroll
+  for (int j = 0; j < kOwn; ++j) {
+    const int idx = threadIdx.x + 256 * j;
+    if (idx >= tri) continue;
+    out[2 * idx] = re[j] + re2[j];
+    out[2 * idx + 1] = im[j];
   }
 }
 
-// G[p][q] = sum over the partial blocks (fixed-order tree); one block per
-// entry, lower triangle by conjugation.
-__global__ void __launch_bounds__(256) k_gram_reduce(const double* __restrict__ partials, int blocks, int M, double* G) {
-  const int p = blockIdx.x / M, q = blockIdx.x % M;
-  if (q < p) return;
+// G_b[p][q] = the sum over member b's partial blocks (fixed-order tree), one
+// block per entry of the upper triangle (grid.x) and member (grid.y); the
+// lower triangle by conjugation.
+__global__ void __launch_bounds__(256) k_gram_reduce(const double* __restrict__ partials, int blocks,
+                                                     RankCounts rc, double* __restrict__ small, int sstride) {
+  const int b = blockIdx.y, idx = blockIdx.x;
+  const int M = rc.M[b];
+  if (idx >= M * (M + 1) / 2) return;                    // the whole block
+  int p, q;
+  tri_pq(idx, M, &p, &q);
   __shared__ double sre[256], sim[256];
   double re = 0.0, im = 0.0;
-  for (int b = threadIdx.x; b < blocks; b += blockDim.x) {
-    re += partials[(size_t)b * 2 * M * M + 2 * (p * M + q)];
-    im += partials[(size_t)b * 2 * M * M + 2 * (p * M + q) + 1];
+  const double* part = partials + (size_t)b * blocks * 2 * kTriMax;
+  for (int k = threadIdx.x; k < blocks; k += blockDim.x) {
+    re += part[(size_t)k * 2 * kTriMax + 2 * idx];
+    im += part[(size_t)k * 2 * kTriMax + 2 * idx + 1];
   }
   sre[threadIdx.x] = re;
   sim[threadIdx.x] = im;
@@ -153,6 +246,7 @@ __global__ void __launch_bounds__(256) k_gram_reduce(const double* __restrict__ 
     __syncthreads();
   }
   if (threadIdx.x == 0) {
+    double* G = small + (size_t)b * sstride + kSmallG;
     G[2 * (p * M + q)] = sre[0];
     G[2 * (p * M + q) + 1] = p == q ? 0.0 : sim[0];
     G[2 * (q * M + p)] = sre[0];
@@ -185,6 +279,50 @@ __device__ __forceinline__ double2 tscale(double2 a, double v) { return make_dou
 __device__ __forceinline__ double tphase(double a, double inv) { return a * inv; }                     // sign
 __device__ __forceinline__ double2 tphase(double2 a, double inv) { return make_double2(a.x * inv, -a.y * inv); }  // e^{-i arg}
 __device__ __forceinline__ double trsqrt(double a) { return rsqrt(a); }
+// the same for the FP32 pre-pass (float / float2)
+__device__ __forceinline__ float tmul(float a, float b) { return a * b; }
+__device__ __forceinline__ float2 tmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ float tadd(float a, float b) { return a + b; }
+__device__ __forceinline__ float2 tadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float tconj(float a) { return a; }
+__device__ __forceinline__ float2 tconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float tre(float a) { return a; }
+__device__ __forceinline__ float tre(float2 a) { return a.x; }
+__device__ __forceinline__ float tabs2(float a) { return a * a; }
+__device__ __forceinline__ float tabs2(float2 a) { return a.x * a.x + a.y * a.y; }
+template <> __device__ __forceinline__ float tscal<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ float2 tscal<float2>(double v) { return make_float2((float)v, 0.f); }
+__device__ __forceinline__ float tscale(float a, float v) { return a * v; }
+__device__ __forceinline__ float2 tscale(float2 a, float v) { return make_float2(a.x * v, a.y * v); }
+__device__ __forceinline__ float tphase(float a, float inv) { return a * inv; }
+__device__ __forceinline__ float2 tphase(float2 a, float inv) { return make_float2(a.x * inv, -a.y * inv); }
+__device__ __forceinline__ float trsqrt(float a) { return rsqrtf(a); }
+// e^{-i arg a} for a != 0: the sign of a real a, conj(a) / |a| for a complex
+// one (FP64 unit modulus: an FP32 reciprocal square root refined by two
+// Newton steps in FP64)
+__device__ __forceinline__ double unit_phase(double a) { return a < 0.0 ? -1.0 : 1.0; }
+__device__ __forceinline__ double2 unit_phase(double2 a) {
+  const double a2 = a.x * a.x + a.y * a.y;
+  double y = (double)rsqrtf((float)a2);
+  y = y * fma(-0.5 * a2 * y, y, 1.5);
+  y = y * fma(-0.5 * a2 * y, y, 1.5);
+  return make_double2(a.x * y, -a.y * y);
+}
+__device__ __forceinline__ float unit_phase(float a) { return a < 0.f ? -1.f : 1.f; }
+__device__ __forceinline__ float2 unit_phase(float2 a) {
+  const float inv = rsqrtf(a.x * a.x + a.y * a.y);
+  return make_float2(a.x * inv, -a.y * inv);
+}
+
+// conversions between the FP64 and FP32 forms
+__device__ __forceinline__ float to32f(float a) { return a; }
+__device__ __forceinline__ float2 to32f(float2 a) { return a; }
+__device__ __forceinline__ float to32f(double a) { return (float)a; }
+__device__ __forceinline__ float2 to32f(double2 a) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ float to32(double a) { return (float)a; }
+__device__ __forceinline__ float2 to32(double2 a) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ double to64(float a) { return a; }
+__device__ __forceinline__ double2 to64(float2 a) { return make_double2(a.x, a.y); }
 
 
 constexpr int kJP = kMaxGramDim + 1;                    // pitch of the Jacobi arrays
@@ -192,29 +330,31 @@ constexpr int kJP = kMaxGramDim + 1;                    // pitch of the Jacobi a
 // Parallel cyclic Jacobi on the Hermitian (or real symmetric) A (M x M,
 // pitch kJP), accumulating V (V <- V R, from any unitary start).  Each step
 // applies Mp/2 disjoint rotations from the round-robin schedule: pair 0 =
-// (Mp-1, s), pair i = ((s+i) mod (Mp-1), (s-i) mod (Mp-1)).  A rotation
-// zeroes a_pq: a phase makes a_pq real, then the classical angle; the tangent
-// is found in FP32 (any tangent gives an exactly unitary rotation, the next
-// sweep removes what is left), cos and sin from one rsqrt.  The update
-// A <- R^dagger A R is done per 2x2 block of the upper triangle and mirrored;
-// a step in which no pair rotates skips it.  Sweeps stop when no |a_pq|
-// exceeds tol * max|a_ii|.  T is double / double2 (FP64) or float / float2
-// (the FP32 pre-pass).  Returns false if the sweep bound was reached.
+// (Mp-1, s), pair i = ((s+i) mod (Mp-1), (s-i) mod (Mp-1)).  A pair rotates
+// while |a_pq| > tol * max|a_ii| (decided in FP32: the test needs no more);
+// the rotation zeroes a_pq: a phase makes a_pq real, then the classical angle
+// with the tangent found in FP32 (any tangent gives an exactly unitary
+// rotation, the next sweep removes what is left), cos and sin from one rsqrt.
+// The update A <- R^dagger A R and V <- V R touches only the rotating
+// pairs' rows and columns; a step in which no pair rotates skips it.  Sweeps
+// stop when no pair rotates.  T is double / double2 (FP64) or float / float2 (the
+// FP32 pre-pass).  Returns false if the sweep bound was reached.
 template <typename T>
-__device__ bool jacobi(T* A, T* V, int M, double tol) {
+__device__ bool jacobi(T* A, T* V, int M, double tol, int max_sweeps = kJacobiSweeps) {
   using RT = decltype(tre(T{}));
   __shared__ T rot[kMaxGramDim / 2][4];
-  __shared__ int pp[kMaxGramDim / 2], qq[kMaxGramDim / 2];
-  __shared__ RT thr2;
+  __shared__ int pp[kMaxGramDim / 2], qq[kMaxGramDim / 2], rotates[kMaxGramDim / 2];
+  __shared__ float thr;
   const int tid = threadIdx.x;
   const int Mp = M + (M & 1);
   const int nb = Mp / 2;
-  const int nblk = nb * (nb + 1) / 2;
-  for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
-    if (tid == 0) {
-      RT dmax = 0;
-      for (int p = 0; p < M; ++p) dmax = fmax(dmax, fabs(tre(A[p * kJP + p])));
-      thr2 = ((RT)tol * dmax) * ((RT)tol * dmax);
+
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (tid < 32) {
+      float dmax = 0.f;
+      for (int p = tid; p < M; p += 32) dmax = fmaxf(dmax, fabsf((float)tre(A[p * kJP + p])));
+      for (int o = 16; o; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      if (tid == 0) thr = (float)tol * dmax;
     }
     __syncthreads();
     int did = 0;
@@ -230,16 +370,16 @@ __device__ bool jacobi(T* A, T* V, int M, double tol) {
         T R00 = tscal<T>(1.0), R01 = tscal<T>(0.0), R10 = tscal<T>(0.0), R11 = tscal<T>(1.0);
         if (q < M) {
           const T apq = A[p * kJP + q];
-          const RT a2 = tabs2(apq);
-          if (a2 > thr2 && a2 > (RT)0) {
+          const float af = sqrtf(tabs2(to32f(apq)));
+          if (af > thr && af > 0.f) {
             sd = 1;
-            const RT inv = trsqrt(a2);
-            const T ph = tphase(apq, inv);
-            const RT theta = (tre(A[q * kJP + q]) - tre(A[p * kJP + p])) * (RT)0.5 * inv;
-            const float th = (float)theta;
+            // the angle only has to be close (FP32); cos, sin and the phase
+            // must make R exactly unitary (in R's precision)
+            const float th = (float)(tre(A[q * kJP + q]) - tre(A[p * kJP + p])) * 0.5f / af;
             const float tf = copysignf(1.0f, th) / (fabsf(th) + sqrtf(1.0f + th * th));
             const RT t = (RT)tf;
-            const RT c = trsqrt((RT)1 + t * t), sn = t * c;
+            const RT c = trsqrt(fma(t, t, (RT)1)), sn = t * c;
+            const T ph = unit_phase(apq);
             R00 = tscal<T>(c);
             R01 = tscal<T>(sn);
             R10 = tscale(ph, -sn);
@@ -247,49 +387,32 @@ __device__ bool jacobi(T* A, T* V, int M, double tol) {
           }
         }
         rot[tid][0] = R00; rot[tid][1] = R01; rot[tid][2] = R10; rot[tid][3] = R11;
+        rotates[tid] = sd;
       }
       if (!__syncthreads_or(sd)) continue;               // nothing rotates in this step
       did = 1;
-      for (int w = tid; w < nblk + M * nb; w += blockDim.x) {
-        if (w < nblk) {
-          // block (i, j), i <= j: Y = R_i^dagger X R_j
-          int i = 0, rem = w;
-          while (rem >= nb - i) { rem -= nb - i; ++i; }
-          const int j = i + rem;
-          const int r0 = pp[i], r1 = qq[i], c0 = pp[j], c1 = qq[j];
-          const bool vr1 = r1 < M, vc1 = c1 < M;
-          const T z = tscal<T>(0.0);
-          const T x00 = A[r0 * kJP + c0];
-          const T x01 = vc1 ? A[r0 * kJP + c1] : z;
-          const T x10 = vr1 ? A[r1 * kJP + c0] : z;
-          const T x11 = (vr1 && vc1) ? A[r1 * kJP + c1] : z;
-          const T a00 = rot[j][0], a01 = rot[j][1], a10 = rot[j][2], a11 = rot[j][3];
-          const T t00 = tadd(tmul(x00, a00), tmul(x01, a10)), t01 = tadd(tmul(x00, a01), tmul(x01, a11));
-          const T t10 = tadd(tmul(x10, a00), tmul(x11, a10)), t11 = tadd(tmul(x10, a01), tmul(x11, a11));
-          const T b00 = tconj(rot[i][0]), b01 = tconj(rot[i][2]), b10 = tconj(rot[i][1]), b11 = tconj(rot[i][3]);
-          const T y00 = tadd(tmul(b00, t00), tmul(b01, t10)), y01 = tadd(tmul(b00, t01), tmul(b01, t11));
-          const T y10 = tadd(tmul(b10, t00), tmul(b11, t10)), y11 = tadd(tmul(b10, t01), tmul(b11, t11));
-          A[r0 * kJP + c0] = y00;
-          if (vc1) A[r0 * kJP + c1] = y01;
-          if (vr1) A[r1 * kJP + c0] = y10;
-          if (vr1 && vc1) A[r1 * kJP + c1] = y11;
-          if (i != j) {                                  // Hermitian mirror
-            A[c0 * kJP + r0] = tconj(y00);
-            if (vc1) A[c1 * kJP + r0] = tconj(y01);
-            if (vr1) A[c0 * kJP + r1] = tconj(y10);
-            if (vr1 && vc1) A[c1 * kJP + r1] = tconj(y11);
-          }
-        } else {
-          // V <- V R for row k and pair j
-          const int v = w - nblk;
-          const int k = v / nb, j = v % nb;
-          const int p = pp[j], q = qq[j];
-          if (q < M) {
-            const T vp = V[k * kJP + p], vq = V[k * kJP + q];
-            V[k * kJP + p] = tadd(tmul(vp, rot[j][0]), tmul(vq, rot[j][2]));
-            V[k * kJP + q] = tadd(tmul(vp, rot[j][1]), tmul(vq, rot[j][3]));
-          }
-        }
+      // A <- R^dagger (A R) and V <- V R for the step's disjoint rotations, in
+      // full-lane passes: first the columns p, q of A and of V (item = pair j,
+      // row k; a warp covers two pairs), then the rows p, q of A.  Pairs that
+      // do not rotate are skipped.
+      for (int w = tid; w < 2 * nb * M; w += blockDim.x) {
+        const int which = w / (nb * M), jk = w % (nb * M);
+        const int j = jk / M, k = jk % M;
+        if (!rotates[j]) continue;
+        T* X = which ? V : A;
+        const int p = pp[j], q = qq[j];
+        const T a = X[k * kJP + p], c = X[k * kJP + q];
+        X[k * kJP + p] = tadd(tmul(a, rot[j][0]), tmul(c, rot[j][2]));
+        X[k * kJP + q] = tadd(tmul(a, rot[j][1]), tmul(c, rot[j][3]));
+      }
+      __syncthreads();
+      for (int w = tid; w < nb * M; w += blockDim.x) {
+        const int j = w / M, k = w % M;
+        if (!rotates[j]) continue;
+        const int p = pp[j], q = qq[j];
+        const T a = A[p * kJP + k], c = A[q * kJP + k];
+        A[p * kJP + k] = tadd(tmul(tconj(rot[j][0]), a), tmul(tconj(rot[j][2]), c));
+        A[q * kJP + k] = tadd(tmul(tconj(rot[j][1]), a), tmul(tconj(rot[j][3]), c));
       }
       __syncthreads();
     }
@@ -319,14 +442,11 @@ __device__ void eig_finish(T* A, T* V, int M, int r, int normalize, double* __re
   const int tid = threadIdx.x;
   for (int i = tid; i < M; i += blockDim.x) lam[i] = tre(A[i * kJP + i]);
   __syncthreads();
-  if (tid == 0) {
-    for (int i = 0; i < M; ++i) order[i] = i;
-    for (int i = 0; i < M; ++i) {
-      int best = i;
-      for (int j = i + 1; j < M; ++j)
-        if (lam[order[j]] > lam[order[best]]) best = j;
-      const int t = order[i]; order[i] = order[best]; order[best] = t;
-    }
+  // descending, ties in index order: position of i = how many come before it
+  for (int i = tid; i < M; i += blockDim.x) {
+    int pos = 0;
+    for (int j = 0; j < M; ++j) pos += lam[j] > lam[i] || (lam[j] == lam[i] && j < i);
+    order[pos] = i;
   }
   __syncthreads();   // A is free from here on (basis aliases it)
   const int keep = r < M ? r : M;
@@ -340,6 +460,25 @@ __device__ void eig_finish(T* A, T* V, int M, int r, int normalize, double* __re
       while (i1 < M && lam[order[i0]] - lam[order[i1]] <= kTieTol * lam1) ++i1;
       const int s = i1 - i0;
       const int first = found;
+      if (s == 1) {
+        // one eigenvector v: the first candidate is P e_j = v conj(v_j) for the
+        // first j with |v_j| > kGsAccept -- the loop below, without its search
+        const int col = order[i0];
+        const T vl = lane < M ? V[lane * kJP + col] : tscal<T>(0.0);
+        const unsigned ok = __ballot_sync(0xffffffffu, lane < M && tabs2(vl) > kGsAccept * kGsAccept);
+        if (ok) {
+          const int j = __ffs(ok) - 1;
+          const T sj = V[j * kJP + col];
+          const T v = tmul(vl, tconj(sj));
+          double nv = lane < M ? tabs2(v) : 0.0;
+          for (int o = 16; o; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
+          if (lane < M) basis[lane * kJP + found] = tscale(v, rsqrt(nv));
+          ++found;
+          __syncwarp();
+          i0 = i1;
+          continue;
+        }
+      }
       // P = S S^dagger; GS of P e_j, j = 0..M-1, thresholds kGsAccept then kGsFallback
       for (int pass = 0; pass < 2 && found - first < s; ++pass) {
         const double thr = pass == 0 ? kGsAccept : kGsFallback;
@@ -393,160 +532,272 @@ __device__ void eig_finish(T* A, T* V, int M, int r, int normalize, double* __re
   }
 }
 
-// One block: eigendecomposition of the Hermitian G (M x M) by parallel cyclic
-// Jacobi (real arithmetic when G is real), then eig_finish.
-__global__ void __launch_bounds__(512) k_eig_truncate(const double* __restrict__ Gin, int M, int r,
-                                                      int normalize, double* __restrict__ W,
-                                                      double* __restrict__ lam_out, int* keep_out,
-                                                      double* scale_out, int* status) {
-  __shared__ double2 A[kMaxGramDim][kJP];
-  __shared__ double2 V[kMaxGramDim][kJP];
-  const int tid = threadIdx.x;
+template <typename T> __device__ __forceinline__ T gload(const double* G, int M, int r, int c);
+template <> __device__ __forceinline__ double gload<double>(const double* G, int M, int r, int c) {
+  return G[2 * (r * M + c)];
+}
+template <> __device__ __forceinline__ double2 gload<double2>(const double* G, int M, int r, int c) {
+  return make_double2(G[2 * (r * M + c)], G[2 * (r * M + c) + 1]);
+}
+
+extern __shared__ double2 eig_sm[];                       // three M x kJP matrices of double2
+
+// Eigendecomposition of one member's Gram matrix G (Hermitian, M x M), then
+// eig_finish.  A warp-wide FP64 instruction occupies a scheduler's FP64 unit
+// for about 64 clocks on this GPU, so a Jacobi sweep is several times
+// cheaper in FP32.  The sweeps therefore run first in FP32 (to 1e-6 of the
+// largest eigenvalue); their eigenvectors Q are made orthonormal in FP64 by
+// two Newton-Schulz steps Q <- Q (3 I - Q^dagger Q) / 2 (the error squares:
+// 1e-7 -> 1e-14 -> 1e-28), A = Q^dagger G Q is formed in FP64, and the FP64
+// Jacobi finishes from there, accumulating onto Q: its first sweeps rotate
+// pairs whose off-diagonal the FP32 sweeps left at about 1e-7 of the
+// largest eigenvalue, the later ones only the few pairs still above
+// 4e-16 of it.  The result is an FP64 eigendecomposition of G.
+template <typename T, typename T32>
+__device__ void eig_member(const double* __restrict__ Gin, int M, int r, int normalize, double* __restrict__ W,
+                           double* __restrict__ lam, int* keep, double* scale, int* status) {
+  T* A = reinterpret_cast<T*>(eig_sm);
+  T* V = reinterpret_cast<T*>(eig_sm + kMaxGramDim * kJP);
+  T* X = reinterpret_cast<T*>(eig_sm + 2 * kMaxGramDim * kJP);
+  T32* A32 = reinterpret_cast<T32*>(X);                   // the FP32 pass lives in X's space
+  T32* V32 = A32 + kMaxGramDim * kJP;
+  const int tid = threadIdx.x, MM = M * M;
+  for (int i = tid; i < MM; i += blockDim.x) {
+    const int p = i / M, q = i % M;
+    A32[p * kJP + q] = to32(gload<T>(Gin, M, p, q));
+    V32[p * kJP + q] = tscal<T32>(p == q ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  jacobi<T32>(A32, V32, M, kRotTol32, kJacobiSweeps32);  // not converging here only costs FP64 sweeps
+  __syncthreads();
+  for (int i = tid; i < MM; i += blockDim.x) V[(i / M) * kJP + i % M] = to64(V32[(i / M) * kJP + i % M]);
+  __syncthreads();
+  for (int it = 0; it < 2; ++it) {
+    for (int i = tid; i < MM; i += blockDim.x) {          // X = Q^dagger Q
+      const int rr = i / M, c = i % M;
+      T acc = tscal<T>(0.0);
+      for (int k = 0; k < M; ++k) acc = tadd(acc, tmul(tconj(V[k * kJP + rr]), V[k * kJP + c]));
+      X[rr * kJP + c] = acc;
+    }
+    __syncthreads();
+    for (int i = tid; i < MM; i += blockDim.x) {          // A = Q (3 I - X) / 2
+      const int rr = i / M, c = i % M;
+      T acc = tscale(V[rr * kJP + c], 1.5);
+      for (int k = 0; k < M; ++k) acc = tadd(acc, tscale(tmul(V[rr * kJP + k], X[k * kJP + c]), -0.5));
+      A[rr * kJP + c] = acc;
+    }
+    __syncthreads();
+    for (int i = tid; i < MM; i += blockDim.x) V[(i / M) * kJP + i % M] = A[(i / M) * kJP + i % M];
+    __syncthreads();
+  }
+  for (int i = tid; i < MM; i += blockDim.x) {            // X = G Q
+    const int rr = i / M, c = i % M;
+    T acc = tscal<T>(0.0);
+    for (int k = 0; k < M; ++k) acc = tadd(acc, tmul(gload<T>(Gin, M, rr, k), V[k * kJP + c]));
+    X[rr * kJP + c] = acc;
+  }
+  __syncthreads();
+  for (int i = tid; i < MM; i += blockDim.x) {            // A = Q^dagger X, upper triangle, mirrored
+    const int rr = i / M, c = i % M;
+    if (rr > c) continue;
+    T acc = tscal<T>(0.0);
+    for (int k = 0; k < M; ++k) acc = tadd(acc, tmul(tconj(V[k * kJP + rr]), X[k * kJP + c]));
+    if (rr == c) acc = tscal<T>(tre(acc));
+    A[rr * kJP + c] = acc;
+    A[c * kJP + rr] = tconj(acc);
+  }
+  __syncthreads();
+  if (!jacobi<T>(A, V, M, kRotTol) && tid == 0) status[0] = 1;
+  __syncthreads();
+  eig_finish<T>(A, V, M, r, normalize, W, lam, keep, scale, status);
+}
+
+// One block per member: eigendecomposition of G_b (M_b x M_b; real
+// arithmetic when G_b is real), truncation to r_b (or to trunc_r > 0 for an
+// explicit truncation), keep_b recorded.
+__global__ void __launch_bounds__(256) k_eig_truncate(double* __restrict__ small, int sstride, RankCounts rc,
+                                                      int trunc_r, int normalize, int* status) {
+  const int b = blockIdx.x;
+  const int M = rc.M[b];
+  const int r = trunc_r > 0 ? trunc_r : rc.rank[b];
+  double* base = small + (size_t)b * sstride;
+  const double* Gin = base + kSmallG;
   int cplx = 0;
-  for (int i = tid; i < M * M; i += blockDim.x) cplx |= Gin[2 * i + 1] != 0.0;
+  for (int i = threadIdx.x; i < M * M; i += blockDim.x) cplx |= Gin[2 * i + 1] != 0.0;
   cplx = __syncthreads_or(cplx);
-  if (cplx) {
-    for (int i = tid; i < M * M; i += blockDim.x) {
-      const int p = i / M, q = i % M;
-      A[p][q] = make_double2(Gin[2 * i], Gin[2 * i + 1]);
-      V[p][q] = make_double2(p == q ? 1.0 : 0.0, 0.0);
+  if (cplx)
+    eig_member<double2, float2>(Gin, M, r, normalize, base + kSmallW, base + kSmallLam, rc.keep + b,
+                                base + kSmallScale, status);
+  else
+    eig_member<double, float>(Gin, M, r, normalize, base + kSmallW, base + kSmallLam, rc.keep + b,
+                              base + kSmallScale, status);
+}
+
+// L_b[c] = scale_b sum_p L'_b[p] W_b[p][c] for c < keep_b, columns keep_b..
+// m_b - 1 cleared, then m_b = keep_b; one thread per row and member
+// (grid.y), all kept columns (each element of L' is read once).  KMAX is a
+// power of two >= every keep_b.  REAL: L' and W are real.
+template <typename R, bool REAL, int KMAX>
+__global__ void __launch_bounds__(256) k_project(const cplx<R>* __restrict__ Lp, cplx<R>* __restrict__ L, int n,
+                                                 int mcap, int rcap, int K, const double* __restrict__ small,
+                                                 int sstride, RankCounts rc) {
+  __shared__ double2 sW[kMaxGramDim * KMAX];
+  const int b = blockIdx.y;
+  const int M = rc.M[b], keep = rc.keep[b];
+  const int old_cols = M / K;
+  const double* base = small + (size_t)b * sstride;
+  const double scale = base[kSmallScale];
+  const double* W = base + kSmallW;
+  for (int i = threadIdx.x; i < M * KMAX; i += blockDim.x) {
+    const int p = i / KMAX, c = i % KMAX;
+    sW[i] = c < keep ? make_double2(W[2 * (p * keep + c)] * scale, W[2 * (p * keep + c) + 1] * scale)
+                     : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x == 0) rc.cols[b] = keep;
+  const uint64_t N = 1ull << n;
+  const cplx<R>* Lpb = Lp + (uint64_t)b * mcap * N;
+  cplx<R>* Lb = L + (uint64_t)b * rcap * N;
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += (uint64_t)gridDim.x * blockDim.x) {
+    if constexpr (REAL) {
+      double acc[KMAX];
+#pragma unroll
+      for (int c = 0; c < KMAX; ++c) acc[c] = 0.0;
+      for (int p = 0; p < M; ++p) {
+        const double a = Lpb[(uint64_t)p * N + x].x;
+#pragma unroll
+        for (int c = 0; c < KMAX; ++c) acc[c] = fma(a, sW[p * KMAX + c].x, acc[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < KMAX; ++c)
+        if (c < keep) Lb[(uint64_t)c * N + x] = mk<R>((R)acc[c], R(0));
+    } else {
+      double2 acc[KMAX];
+#pragma unroll
+      for (int c = 0; c < KMAX; ++c) acc[c] = make_double2(0.0, 0.0);
+      for (int p = 0; p < M; ++p) {
+        const cplx<R> a = Lpb[(uint64_t)p * N + x];
+        const double2 ad = make_double2(a.x, a.y);
+#pragma unroll
+        for (int c = 0; c < KMAX; ++c) acc[c] = zadd(acc[c], zmul(ad, sW[p * KMAX + c]));
+      }
+#pragma unroll
+      for (int c = 0; c < KMAX; ++c)
+        if (c < keep) Lb[(uint64_t)c * N + x] = mk<R>((R)acc[c].x, (R)acc[c].y);
     }
-    __syncthreads();
-    if (!jacobi<double2>(&A[0][0], &V[0][0], M, kRotTol) && tid == 0) status[0] = 1;
-    __syncthreads();
-    eig_finish<double2>(&A[0][0], &V[0][0], M, r, normalize, W, lam_out, keep_out, scale_out, status);
-  } else {
-    double* Ar = reinterpret_cast<double*>(&A[0][0]);
-    double* Vr = reinterpret_cast<double*>(&V[0][0]);
-    for (int i = tid; i < M * M; i += blockDim.x) {
-      const int p = i / M, q = i % M;
-      Ar[p * kJP + q] = Gin[2 * i];
-      Vr[p * kJP + q] = p == q ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    if (!jacobi<double>(Ar, Vr, M, kRotTol) && tid == 0) status[0] = 1;
-    __syncthreads();
-    eig_finish<double>(Ar, Vr, M, r, normalize, W, lam_out, keep_out, scale_out, status);
+    for (int c = keep; c < old_cols; ++c) Lb[(uint64_t)c * N + x] = mk<R>(R(0), R(0));
   }
 }
 
-// L[c] = scale * sum_p Lp[p] W[p][c] for c < keep; one thread per row, all
-// kept columns (each element of L' is read once).  REAL: L' and W are real.
-template <typename R, bool REAL>
-__global__ void __launch_bounds__(256) k_project(const cplx<R>* __restrict__ Lp, cplx<R>* __restrict__ L,
-                                                 int n, int M, const double* __restrict__ W,
-                                                 const int* __restrict__ keep_p,
-                                                 const double* __restrict__ scale_p) {
-  __shared__ double2 sW[kMaxGramDim * kMaxRank];
-  const int keep = keep_p[0];
-  const double scale = scale_p[0];
-  for (int i = threadIdx.x; i < M * keep; i += blockDim.x)
-    sW[i] = make_double2(W[2 * i] * scale, W[2 * i + 1] * scale);
-  __syncthreads();
-  const uint64_t N = 1ull << n;
-  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += (uint64_t)gridDim.x * blockDim.x) {
-    if constexpr (REAL) {
-      double acc[kMaxRank];
-#pragma unroll
-      for (int c = 0; c < kMaxRank; ++c) acc[c] = 0.0;
-      for (int p = 0; p < M; ++p) {
-        const double a = Lp[(uint64_t)p * N + x].x;
-#pragma unroll
-        for (int c = 0; c < kMaxRank; ++c)
-          if (c < keep) acc[c] = fma(a, sW[p * keep + c].x, acc[c]);
-      }
-#pragma unroll
-      for (int c = 0; c < kMaxRank; ++c)
-        if (c < keep) L[(uint64_t)c * N + x] = mk<R>((R)acc[c], R(0));
-    } else {
-      double2 acc[kMaxRank];
-#pragma unroll
-      for (int c = 0; c < kMaxRank; ++c) acc[c] = make_double2(0.0, 0.0);
-      for (int p = 0; p < M; ++p) {
-        const cplx<R> a = Lp[(uint64_t)p * N + x];
-        const double2 ad = make_double2(a.x, a.y);
-#pragma unroll
-        for (int c = 0; c < kMaxRank; ++c)
-          if (c < keep) acc[c] = zadd(acc[c], zmul(ad, sW[p * keep + c]));
-      }
-#pragma unroll
-      for (int c = 0; c < kMaxRank; ++c)
-        if (c < keep) L[(uint64_t)c * N + x] = mk<R>((R)acc[c].x, (R)acc[c].y);
-    }
-  }
+// Blocks of a grid-stride kernel over `rows` rows per member: about four
+// 256-thread blocks per SM in all, at least one per member.
+unsigned rows_blocks(uint64_t rows, int members) {
+  const uint64_t want = ((uint64_t)num_sms() * 4 + members - 1) / members;
+  const uint64_t most = (rows + 255) / 256;
+  return (unsigned)std::max<uint64_t>(1, std::min(want, most));
 }
 
 template <typename R>
-cudaError_t expand_dispatch(qs_ctx* h, const void* L, void* Lp, int n, int m, const Targets& tg, bool real,
-                            const void* E, int K) {
-  const uint64_t work = ((1ull << n) >> tg.k) * (uint64_t)m;
-  uint64_t blocks = (work + kExpBlock - 1) / kExpBlock;
-  const uint64_t cap = (uint64_t)num_sms() * 16;
-  if (blocks > cap) blocks = cap;
-  if (blocks < 1) blocks = 1;
-  auto* l = static_cast<const cplx<R>*>(L);
-  auto* lp = static_cast<cplx<R>*>(Lp);
-  const double* e = (const double*)E;
-  if (tg.k == 1 && real) k_kraus_expand<R, 1, true><<<(int)blocks, kExpBlock, 0, h->stream>>>(l, lp, n, m, tg, e, K);
-  else if (tg.k == 1) k_kraus_expand<R, 1, false><<<(int)blocks, kExpBlock, 0, h->stream>>>(l, lp, n, m, tg, e, K);
-  else if (tg.k == 2 && real) k_kraus_expand<R, 2, true><<<(int)blocks, kExpBlock, 0, h->stream>>>(l, lp, n, m, tg, e, K);
-  else if (tg.k == 2) k_kraus_expand<R, 2, false><<<(int)blocks, kExpBlock, 0, h->stream>>>(l, lp, n, m, tg, e, K);
+cudaError_t expand_dispatch(qs_ctx* h, const Targets& tg, bool real, const double* E, int K, int e_stride,
+                            int max_cols, const KrausGate& g) {
+  const uint64_t work = ((1ull << h->n) >> tg.k) * (uint64_t)max_cols;
+  const dim3 grid(rows_blocks(work, h->batch), h->batch);
+  auto* l = static_cast<const cplx<R>*>(h->state);
+  auto* lp = static_cast<cplx<R>*>(h->work);
+  const int n = h->n, rcap = h->rank, mcap = h->mcap;
+  if (tg.k == 1 && real) k_kraus_expand<R, 1, true><<<grid, kExpBlock, 0, h->stream>>>(l, lp, n, rcap, mcap, tg, E, K, e_stride, h->rc, g);
+  else if (tg.k == 1) k_kraus_expand<R, 1, false><<<grid, kExpBlock, 0, h->stream>>>(l, lp, n, rcap, mcap, tg, E, K, e_stride, h->rc, g);
+  else if (tg.k == 2 && real) k_kraus_expand<R, 2, true><<<grid, kExpBlock, 0, h->stream>>>(l, lp, n, rcap, mcap, tg, E, K, e_stride, h->rc, g);
+  else if (tg.k == 2) k_kraus_expand<R, 2, false><<<grid, kExpBlock, 0, h->stream>>>(l, lp, n, rcap, mcap, tg, E, K, e_stride, h->rc, g);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
+template <typename R, bool REAL, int KMAX>
+void project_launch(qs_ctx* h, int K) {
+  const dim3 grid(rows_blocks(1ull << h->n, h->batch), h->batch);
+  k_project<R, REAL, KMAX><<<grid, 256, 0, h->stream>>>(static_cast<const cplx<R>*>(h->work),
+                                                        static_cast<cplx<R>*>(h->state), h->n, h->mcap, h->rank, K,
+                                                        h->rsmall, kRankStride, h->rc);
+}
+
+template <typename R, bool REAL>
+void project_kmax(qs_ctx* h, int K, int max_keep) {
+  if (max_keep <= 1) project_launch<R, REAL, 1>(h, K);
+  else if (max_keep <= 2) project_launch<R, REAL, 2>(h, K);
+  else if (max_keep <= 4) project_launch<R, REAL, 4>(h, K);
+  else if (max_keep <= 8) project_launch<R, REAL, 8>(h, K);
+  else project_launch<R, REAL, 16>(h, K);
+}
+
 }  // namespace
 
-cudaError_t launch_kraus_expand(qs_ctx* h, const void* L, void* Lp, int n, int m, const Targets& tg, bool real,
-                                const void* E, int K) {
-  if (h->dtype == QS_C64) return expand_dispatch<float>(h, L, Lp, n, m, tg, real, E, K);
-  return expand_dispatch<double>(h, L, Lp, n, m, tg, real, E, K);
+int gram_rows_per_block(int n) {
+  const uint64_t N = 1ull << n;
+  const uint64_t per = (N + (uint64_t)kGramRows * kGramTarget - 1) / ((uint64_t)kGramRows * kGramTarget);
+  return (int)(per * kGramRows);
 }
 
-cudaError_t launch_gram(qs_ctx* h, const void* Lp, int n, int M, bool real, double* G) {
+size_t gram_partials_doubles(int n, int members) {
   const uint64_t N = 1ull << n;
-  const int blocks = (int)((N + kGramRows - 1) / kGramRows);
-  const size_t need = (size_t)blocks * 2 * M * M;
-  if (h->partials_cap < need) {
-    if (h->partials) cudaFreeAsync(h->partials, h->stream);
-    h->partials = nullptr;
-    h->partials_cap = 0;
-    if (cudaMallocAsync((void**)&h->partials, need * sizeof(double), h->stream) != cudaSuccess)
-      return cudaErrorMemoryAllocation;
-    h->partials_cap = need;
-  }
+  const uint64_t blocks = (N + gram_rows_per_block(n) - 1) / gram_rows_per_block(n);
+  return (size_t)members * blocks * 2 * kTriMax;
+}
+
+cudaError_t launch_kraus_expand(qs_ctx* h, const Targets& tg, bool real, const double* E, int K, int e_stride,
+                                int max_cols) {
+  KrausGate none{};
+  if (h->dtype == QS_C64) return expand_dispatch<float>(h, tg, real, E, K, e_stride, max_cols, none);
+  return expand_dispatch<double>(h, tg, real, E, K, e_stride, max_cols, none);
+}
+
+cudaError_t launch_kraus_expand_gate(qs_ctx* h, const Targets& tg, bool real, const KrausGate& g, int max_cols) {
+  const int K = kraus_count(g.k, g.noise);
+  if (h->dtype == QS_C64) return expand_dispatch<float>(h, tg, real, nullptr, K, 0, max_cols, g);
+  return expand_dispatch<double>(h, tg, real, nullptr, K, 0, max_cols, g);
+}
+
+cudaError_t launch_gram(qs_ctx* h, bool real, int max_M) {
+  const uint64_t N = 1ull << h->n;
+  const int rows = gram_rows_per_block(h->n);
+  const int blocks = (int)((N + rows - 1) / rows);
+  const dim3 grid(blocks, h->batch);
   if (h->dtype == QS_C64 && real)
-    k_gram_partials<float, true><<<blocks, 256, 0, h->stream>>>((const float2*)Lp, n, M, h->partials);
+    k_gram_partials<float, true><<<grid, 256, 0, h->stream>>>((const float2*)h->work, h->n, h->mcap, rows, h->rc, h->partials);
   else if (h->dtype == QS_C64)
-    k_gram_partials<float, false><<<blocks, 256, 0, h->stream>>>((const float2*)Lp, n, M, h->partials);
+    k_gram_partials<float, false><<<grid, 256, 0, h->stream>>>((const float2*)h->work, h->n, h->mcap, rows, h->rc, h->partials);
   else if (real)
-    k_gram_partials<double, true><<<blocks, 256, 0, h->stream>>>((const double2*)Lp, n, M, h->partials);
+    k_gram_partials<double, true><<<grid, 256, 0, h->stream>>>((const double2*)h->work, h->n, h->mcap, rows, h->rc, h->partials);
   else
-    k_gram_partials<double, false><<<blocks, 256, 0, h->stream>>>((const double2*)Lp, n, M, h->partials);
-  k_gram_reduce<<<M * M, 256, 0, h->stream>>>(h->partials, blocks, M, G);
+    k_gram_partials<double, false><<<grid, 256, 0, h->stream>>>((const double2*)h->work, h->n, h->mcap, rows, h->rc, h->partials);
+  k_gram_reduce<<<dim3(max_M * (max_M + 1) / 2, h->batch), 256, 0, h->stream>>>(h->partials, blocks, h->rc, h->rsmall, kRankStride);
   return cudaGetLastError();
 }
 
-cudaError_t launch_eig_truncate(qs_ctx* h, const double* G, int M, int r, int normalize, double* W,
-                                double* lam, double* scale, int* keep, int* status) {
-  k_eig_truncate<<<1, 512, 0, h->stream>>>(G, M, r, normalize, W, lam, keep, scale, status);
+namespace {
+constexpr int kEigSmem = 3 * kMaxGramDim * kJP * (int)sizeof(double2);
+}
+
+cudaError_t rank_kernel_attributes() {
+  static std::atomic<bool> attr{false};
+  if (attr.load()) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(k_eig_truncate, cudaFuncAttributeMaxDynamicSharedMemorySize, kEigSmem);
+  if (e == cudaSuccess) attr.store(true);
+  return e;
+}
+
+cudaError_t launch_eig_truncate(qs_ctx* h, int trunc_r, int normalize) {
+  const cudaError_t e = rank_kernel_attributes();
+  if (e != cudaSuccess) return e;
+  k_eig_truncate<<<h->batch, 256, kEigSmem, h->stream>>>(h->rsmall, kRankStride, h->rc, trunc_r, normalize, h->dstatus + 1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_project(qs_ctx* h, const void* Lp, void* L, int n, int M, bool real, const double* W,
-                           const double* scale, const int* keep) {
-  const uint64_t N = 1ull << n;
-  uint64_t blocks = (N + 255) / 256;
-  const uint64_t cap = (uint64_t)num_sms() * 8;
-  if (blocks > cap) blocks = cap;
-  if (h->dtype == QS_C64 && real)
-    k_project<float, true><<<(int)blocks, 256, 0, h->stream>>>((const float2*)Lp, (float2*)L, n, M, W, keep, scale);
-  else if (h->dtype == QS_C64)
-    k_project<float, false><<<(int)blocks, 256, 0, h->stream>>>((const float2*)Lp, (float2*)L, n, M, W, keep, scale);
-  else if (real)
-    k_project<double, true><<<(int)blocks, 256, 0, h->stream>>>((const double2*)Lp, (double2*)L, n, M, W, keep, scale);
-  else
-    k_project<double, false><<<(int)blocks, 256, 0, h->stream>>>((const double2*)Lp, (double2*)L, n, M, W, keep, scale);
+cudaError_t launch_project(qs_ctx* h, bool real, int K, int max_keep) {
+  if (h->dtype == QS_C64 && real) project_kmax<float, true>(h, K, max_keep);
+  else if (h->dtype == QS_C64) project_kmax<float, false>(h, K, max_keep);
+  else if (real) project_kmax<double, true>(h, K, max_keep);
+  else project_kmax<double, false>(h, K, max_keep);
   return cudaGetLastError();
 }
 

@@ -88,42 +88,35 @@ __global__ void __launch_bounds__(kRBlock) k_norm_partials(const cplx<R>* __rest
   }
 }
 
-// out[b] = |sum_c partial|^2 (mode 0) or sum_c partial.x (mode 1);
-// with sum_members, out[0] = sum over members instead.
-__global__ void k_finalize(const double* partials, int members, int chunks, int mode,
-                           int sum_members, double* out) {
-  __shared__ double vals[1024];
-  for (int b = threadIdx.x; b < members; b += blockDim.x) {
-    double re = 0.0, im = 0.0;
-    for (int c = 0; c < chunks; ++c) {
-      re += partials[2 * ((uint64_t)b * chunks + c)];
-      im += partials[2 * ((uint64_t)b * chunks + c) + 1];
+// v_b = |sum_c partial|^2 (mode 0) or sum_c partial.x (mode 1), chunks in
+// order; out[g] = v_{g group} + ... + v_{g group + group - 1} in order (group
+// = 1: out[b] = v_b).
+__global__ void k_finalize(const double* partials, int members, int chunks, int mode, int group, double* out) {
+  const int outs = members / group;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < outs; g += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = g * group; b < (g + 1) * group; ++b) {
+      double re = 0.0, im = 0.0;
+      for (int c = 0; c < chunks; ++c) {
+        re += partials[2 * ((uint64_t)b * chunks + c)];
+        im += partials[2 * ((uint64_t)b * chunks + c) + 1];
+      }
+      s += mode == 0 ? re * re + im * im : re;
     }
-    const double v = mode == 0 ? re * re + im * im : re;
-    if (sum_members) { if (b < 1024) vals[b] = v; }
-    else out[b] = v;
-  }
-  if (sum_members) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int b = 0; b < members && b < 1024; ++b) s += vals[b];
-      out[0] = s;
-    }
+    out[g] = s;
   }
 }
 
 template <typename R>
-__global__ void k_basis_prob(const cplx<R>* psi, int n, int members, uint64_t x, int sum_members,
-                             double* out) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+__global__ void k_basis_prob(const cplx<R>* psi, int n, int members, uint64_t x, int group, double* out) {
+  const int outs = members / group;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < outs; g += gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int b = 0; b < members; ++b) {
+    for (int b = g * group; b < (g + 1) * group; ++b) {
       const cplx<R> a = psi[((uint64_t)b << n) + x];
-      const double v = (double)a.x * a.x + (double)a.y * a.y;
-      if (sum_members) s += v; else out[b] = v;
+      s += (double)a.x * a.x + (double)a.y * a.y;
     }
-    if (sum_members) out[0] = s;
+    out[g] = s;
   }
 }
 
@@ -188,7 +181,7 @@ int chunk_count(int n) {
 }  // namespace
 
 cudaError_t launch_dot(qs_ctx* h, const void* psi, const void* ref, int n, int members,
-                       bool sum_members, double* out) {
+                       int group, double* out) {
   const int chunks = chunk_count(n);
   if (!ensure_partials(h, (size_t)2 * chunks * members)) return cudaErrorMemoryAllocation;
   dim3 grid(chunks, members);
@@ -196,11 +189,11 @@ cudaError_t launch_dot(qs_ctx* h, const void* psi, const void* ref, int n, int m
     k_dot_partials<float><<<grid, kRBlock, 0, h->stream>>>((const float2*)psi, (const float2*)ref, n, chunks, kChunk, h->partials);
   else
     k_dot_partials<double><<<grid, kRBlock, 0, h->stream>>>((const double2*)psi, (const double2*)ref, n, chunks, kChunk, h->partials);
-  k_finalize<<<1, 1024, 0, h->stream>>>(h->partials, members, chunks, 0, sum_members, out);
+  k_finalize<<<(members / group + 255) / 256, 256, 0, h->stream>>>(h->partials, members, chunks, 0, group, out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_norm(qs_ctx* h, const void* psi, int n, int members, bool sum_members, double* out) {
+cudaError_t launch_norm(qs_ctx* h, const void* psi, int n, int members, int group, double* out) {
   const int chunks = chunk_count(n);
   if (!ensure_partials(h, (size_t)2 * chunks * members)) return cudaErrorMemoryAllocation;
   dim3 grid(chunks, members);
@@ -208,16 +201,17 @@ cudaError_t launch_norm(qs_ctx* h, const void* psi, int n, int members, bool sum
     k_norm_partials<float><<<grid, kRBlock, 0, h->stream>>>((const float2*)psi, n, chunks, kChunk, h->partials);
   else
     k_norm_partials<double><<<grid, kRBlock, 0, h->stream>>>((const double2*)psi, n, chunks, kChunk, h->partials);
-  k_finalize<<<1, 1024, 0, h->stream>>>(h->partials, members, chunks, 1, sum_members, out);
+  k_finalize<<<(members / group + 255) / 256, 256, 0, h->stream>>>(h->partials, members, chunks, 1, group, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_basis_prob(qs_ctx* h, const void* psi, int n, int members, uint64_t x,
-                              bool sum_members, double* out) {
+                              int group, double* out) {
+  const unsigned g = (unsigned)((members / group + 255) / 256);
   if (h->dtype == QS_C64)
-    k_basis_prob<float><<<1, 32, 0, h->stream>>>((const float2*)psi, n, members, x, sum_members, out);
+    k_basis_prob<float><<<g, 256, 0, h->stream>>>((const float2*)psi, n, members, x, group, out);
   else
-    k_basis_prob<double><<<1, 32, 0, h->stream>>>((const double2*)psi, n, members, x, sum_members, out);
+    k_basis_prob<double><<<g, 256, 0, h->stream>>>((const double2*)psi, n, members, x, group, out);
   return cudaGetLastError();
 }
 
@@ -228,7 +222,7 @@ cudaError_t launch_dm_trace(qs_ctx* h, const void* rho, int n, double* out) {
     k_dm_trace_partials<float><<<chunks, kRBlock, 0, h->stream>>>((const float2*)rho, n, chunks, kChunk, h->partials);
   else
     k_dm_trace_partials<double><<<chunks, kRBlock, 0, h->stream>>>((const double2*)rho, n, chunks, kChunk, h->partials);
-  k_finalize<<<1, 1024, 0, h->stream>>>(h->partials, 1, chunks, 1, 0, out);
+  k_finalize<<<1, 256, 0, h->stream>>>(h->partials, 1, chunks, 1, 1, out);
   return cudaGetLastError();
 }
 
@@ -240,7 +234,7 @@ cudaError_t launch_dm_expect(qs_ctx* h, const void* rho, const void* phi, int n,
   else
     k_dm_expect_rows<double><<<(unsigned)N, kRBlock, 0, h->stream>>>((const double2*)rho, (const double2*)phi, n, h->partials);
   // sum of N row partials: treat them as one member with N chunks, real part
-  k_finalize<<<1, 1024, 0, h->stream>>>(h->partials, 1, (int)N, 1, 0, out);
+  k_finalize<<<1, 256, 0, h->stream>>>(h->partials, 1, (int)N, 1, 1, out);
   return cudaGetLastError();
 }
 

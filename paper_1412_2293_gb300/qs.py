@@ -75,6 +75,8 @@ _SIGS = {
     "qs_set_rank_columns": ([_P, ct.c_int], ct.c_int),
     "qs_set_trajectory_offset": ([_P, ct.c_uint64], ct.c_int),
     "qs_set_wait_limit": ([_P, ct.c_int64], ct.c_int),
+    "qs_set_member_ranks": ([_P, _I], ct.c_int),
+    "qs_get_member_columns": ([_P, _I], ct.c_int),
     "qs_set_member_noise": ([_P, _D, _U64, _U64, _U64], ct.c_int),
     "qs_plan_create": ([_P, ct.POINTER(qs_gate), ct.c_int, ct.POINTER(_P)], ct.c_int),
     "qs_plan_run": ([_P, ct.c_double, ct.c_uint64, ct.c_uint64], ct.c_int),
@@ -296,6 +298,17 @@ def qs_set_state(h, state):
 
 def qs_set_rank_columns(h, m):
     _check(lib().qs_set_rank_columns(h, int(m)), h)
+
+
+def qs_set_member_ranks(h, ranks):
+    r = np.ascontiguousarray(np.asarray(ranks, dtype=np.int32))
+    _check(lib().qs_set_member_ranks(h, r.ctypes.data_as(_I)), h)
+
+
+def qs_get_member_columns(h):
+    out = np.zeros(qs_info(h)["batch"], dtype=np.int32)
+    _check(lib().qs_get_member_columns(h, out.ctypes.data_as(_I)), h)
+    return out
 
 
 def qs_set_wait_limit(h, polls):

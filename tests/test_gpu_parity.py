@@ -488,6 +488,93 @@ def test_fixed_rank_grover_n16_prefix_matches_oracle(r):
     np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * np.abs(want).max())
 
 
+@pytest.mark.parametrize("circ", ["grover", "qft"])
+def test_batched_fixed_rank_members_equal_separate_runs_and_oracle(circ):
+    """Members of uneven rank and noise in one FIXED_RANK handle (one launch
+    per kernel for all of them, Sec. 3.2 per member): each member equals the
+    same job run alone, bit for bit, and the oracle."""
+    n = 9
+    ranks = [1, 2, 4, 8, 3]
+    es = [0.01, 0.03, 0.0, 0.05, 0.02]
+    B = len(ranks)
+    if circ == "qft":
+        ops, x0 = inputs.qft_circuit(n), 5
+    else:
+        ops, x0 = inputs.grover_circuit(n, 3, 77), 0
+    gates_ops = ops
+    ideal = ocirc.ideal_state(n, ops, x0)
+    with Handle(n, B, max(ranks), qs.QS_FIXED_RANK, qs.QS_C128) as h:
+        qs.qs_set_member_ranks(h, ranks)
+        qs.qs_set_member_noise(h, es, [SEED] * B, list(range(B)))
+        qs.qs_set_basis_state(h, x0)
+        pcirc.apply_ops(h, gates_ops, 0.5, SEED)            # the call's e is overridden per member
+        f = qs.qs_fidelity(h, ideal)
+        tr = qs.qs_trace(h)
+        cols = qs.qs_get_member_columns(h)
+        st = qs.qs_get_state(h).reshape(B, max(ranks), 1 << n)
+    for b in range(B):
+        with Handle(n, 1, ranks[b], qs.QS_FIXED_RANK, qs.QS_C128) as h1:
+            qs.qs_set_basis_state(h1, x0)
+            pcirc.apply_ops(h1, gates_ops, es[b], SEED)
+            f1 = qs.qs_fidelity(h1, ideal)[0]
+            m1 = qs.qs_get_rank(h1)
+            L1 = qs.qs_get_state(h1).reshape(ranks[b], 1 << n)
+        assert cols[b] == m1
+        assert f[b] == f1, (b, f[b], f1)                      # bit-identical to the job alone
+        np.testing.assert_array_equal(st[b, :m1], L1[:m1])
+        assert not np.any(st[b, m1:])                          # dead columns stay zero
+        Lo = ocirc.run_fixed_rank(n, ops, x0, es[b], ranks[b])
+        fo = ofr.fidelity(ideal, Lo)
+        assert abs(f[b] - fo) <= 1e-12 * fo, (b, f[b], fo)
+        assert abs(tr[b] - ofr.trace(Lo)) <= 1e-12
+        L = st[b, :m1].T
+        np.testing.assert_allclose(L @ L.conj().T, Lo @ Lo.conj().T, atol=1e-12)
+
+
+@pytest.mark.parametrize("circ,batch", [("grover", 1), ("qft", 1), ("grover", 4), ("qft", 3)])
+def test_fixed_rank_plan_equals_gate_by_gate(circ, batch):
+    """A FIXED_RANK plan (every gate on every member, the circuit replayed as
+    one CUDA graph, Kraus sets built on the device from e) equals the same
+    gates issued one by one, bit for bit, twice in a row; the members' column
+    counts on the host follow."""
+    n, e = 9, 0.03
+    ranks = [8, 2, 5, 1][:batch]
+    if circ == "qft":
+        ops, x0 = inputs.qft_circuit(n), 6
+    else:
+        ops, x0 = inputs.grover_circuit(n, 3, 101), 0
+    es = [0.03, 0.01, 0.0, 0.05][:batch]
+    ideal = ocirc.ideal_state(n, ops, x0)
+    results = []
+    for use_plan in (False, True):
+        with Handle(n, batch, max(ranks), qs.QS_FIXED_RANK, qs.QS_C128) as h:
+            qs.qs_set_member_ranks(h, ranks)
+            if batch > 1:
+                qs.qs_set_member_noise(h, es, [SEED] * batch, list(range(batch)))
+            p = qs.qs_plan_create(h, pcirc.to_gates(ops)) if use_plan else None
+            runs = []
+            for _ in range(2):
+                qs.qs_set_basis_state(h, x0)
+                if use_plan:
+                    qs.qs_plan_run(p, e, SEED, 0, h)
+                else:
+                    pcirc.apply_ops(h, ops, e, SEED)
+                runs.append((qs.qs_fidelity(h, ideal), qs.qs_get_state(h), qs.qs_get_member_columns(h)))
+            if p is not None:
+                qs.qs_plan_destroy(p)
+        results.append(runs)
+    for (fa, sa, ca), (fb, sb, cb) in zip(results[0], results[1]):
+        np.testing.assert_array_equal(fa, fb)
+        np.testing.assert_array_equal(sa, sb)
+        np.testing.assert_array_equal(ca, cb)
+    # and the plan against the oracle
+    f = results[1][1][0]
+    for b in range(batch):
+        Lo = ocirc.run_fixed_rank(n, ops, x0, es[b] if batch > 1 else e, ranks[b])
+        fo = ofr.fidelity(ideal, Lo)
+        assert abs(f[b] - fo) <= 1e-12 * fo, (b, f[b], fo)
+
+
 def test_explicit_truncation_matches_oracle():
     rng = np.random.default_rng(2)
     n, r = 6, 6
