@@ -477,60 +477,53 @@ def extra_rows(h, n, T, esize, stream, peaks):
     out["a6_density_qft_n14"] = {"channels": len(ops4), "entries": 1 << (2 * W4.n), **a6,
                                  "fidelity_c64_minus_c128": a6["c64"]["fidelity"] - a6["c128"]["fidelity"]}
 
-    # a7: fixed-rank Grover n = 16, r = 8: a bounded run of channels, extrapolated
+    # a7: fixed-rank Grover n = 16 as a plan (the circuit replayed as one CUDA graph): the
+    # first 208 channels timed per rank r = 1, 2, 4, 8 (one job), the same with 8 jobs of
+    # ranks 1..8 batched in one handle (a9: rank columns of uneven sizes in one launch), and
+    # the whole circuit at r = 1 against Eq. 10: F = lambda1^(n + 2nk) p_ideal
     W3 = inputs.WORKLOADS["rank_grover_n16"]
     ops3 = W3.ops()
-    nch = 160
-    hr = qs.qs_create(W3.n, 1, W3.rank, qs.QS_FIXED_RANK, qs.QS_C128, stream)
-    qs.qs_set_basis_state(hr, 0)
-    pcirc.apply_ops(hr, ops3[:40], W3.e, W3.seed)
-    qs.qs_synchronize(hr)
-    sub = ops3[40:40 + nch]
-    e0, e1 = ev(), ev()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    pcirc.apply_ops(hr, sub, W3.e, W3.seed, gate_id0=40)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_r = e0.elapsed_time(e1)
+    sub = ops3[:16 + 6 * 34]
     noisy = sum(1 for o in sub if o.noisy)
-    per_ch = ms_r / max(noisy, 1)
     total_noisy = sum(1 for o in ops3 if o.noisy)
-    qs.qs_destroy(hr)
-    out["a7_fixed_rank_grover_n16_r8"] = {
-        "ms_per_channel": round(per_ch, 4), "channels_timed": noisy,
-        "circuit_channels": total_noisy,
-        "circuits_per_s_extrapolated": round(1e3 / (per_ch * total_noisy), 4),
-        "note": "time of a bounded run of channels (expand, FP64 Gram, FP64 Jacobi, projection) x channels"}
 
-    # a7: rank sweep r = 1, 2, 4, 8 on the same Grover circuit (bounded channels), and the whole
-    # circuit at r = 1 against Eq. 10: F = lambda1^(n + 2nk) p_ideal, lambda1 = (1 + e^-2e^2) / 2
+    def rank_plan_ms(ops_, B, ranks):
+        hr = qs.qs_create(W3.n, B, max(ranks), qs.QS_FIXED_RANK, qs.QS_C128, stream)
+        qs.qs_set_member_ranks(hr, ranks)
+        pr = qs.qs_plan_create(hr, pcirc.to_gates(ops_))
+        for _ in range(2):                               # the second run replays the captured graph
+            qs.qs_set_basis_state(hr, 0)
+            torch.cuda.synchronize()
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            qs.qs_plan_run(pr, W3.e, W3.seed, 0, hr)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        qs.qs_plan_destroy(pr)
+        return e0.elapsed_time(e1), hr
+
     sweep = {}
     for r in (1, 2, 4, 8):
-        hr = qs.qs_create(W3.n, 1, r, qs.QS_FIXED_RANK, qs.QS_C128, stream)
-        qs.qs_set_basis_state(hr, 0)
-        pcirc.apply_ops(hr, ops3[:40], W3.e, W3.seed)
-        qs.qs_synchronize(hr)
-        e0, e1 = ev(), ev()
-        e0.record(stream)
-        pcirc.apply_ops(hr, sub, W3.e, W3.seed, gate_id0=40)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        sweep[f"r{r}_ms_per_channel"] = round(e0.elapsed_time(e1) / max(noisy, 1), 4)
+        ms_r, hr = rank_plan_ms(sub, 1, [r])
         qs.qs_destroy(hr)
+        sweep[f"r{r}_ms_per_channel"] = round(ms_r / noisy, 4)
+    ranks8 = [1, 2, 3, 4, 5, 6, 7, 8]
+    ms_b, hr = rank_plan_ms(sub, 8, ranks8)
+    qs.qs_destroy(hr)
+    sweep["batched_8_jobs_r1_to_8"] = {"ms_per_channel": round(ms_b / noisy, 4),
+                                      "ms_per_job_channel": round(ms_b / noisy / 8, 4)}
+    ms_full, hr = rank_plan_ms(ops3, 1, [1])
     marked3 = inputs.draw_marked(W3.n, W3.seed)
     k3 = inputs.grover_iterations(W3.n)
-    hr = qs.qs_create(W3.n, 1, 1, qs.QS_FIXED_RANK, qs.QS_C128, stream)
-    t0 = time.perf_counter()
-    pcirc.apply_ops(hr, ops3, W3.e, W3.seed)
     p_r1 = float(qs.qs_fidelity(hr, None, marked3)[0])
-    t_r1 = time.perf_counter() - t0
     qs.qs_destroy(hr)
     lam1 = (1.0 + math.exp(-2.0 * W3.e ** 2)) / 2.0
     p_eq10 = lam1 ** (W3.n + 2 * W3.n * k3) * math.sin((2 * k3 + 1) * math.asin(2.0 ** (-W3.n / 2))) ** 2
-    sweep.update({"r1_whole_circuit_s": round(t_r1, 3), "r1_success_probability": p_r1, "eq10": p_eq10,
-                  "r1_rel_diff_from_eq10": abs(p_r1 - p_eq10) / p_eq10})
-    out["a7_rank_sweep_grover_n16"] = sweep
+    sweep.update({"channels_timed": noisy, "circuit_channels": total_noisy,
+                  "r1_whole_circuit_s": round(ms_full / 1e3, 4), "r1_success_probability": p_r1, "eq10": p_eq10,
+                  "r1_rel_diff_from_eq10": abs(p_r1 - p_eq10) / p_eq10,
+                  "note": "plan runs (expansion, FP64 Gram, eigensolver, projection per channel, one CUDA graph)"})
+    out["a7_fixed_rank_grover_n16"] = sweep
 
     # a6 vs a7: exact density matrix and fixed rank r = 1..8 on the QFT n = 14, |F_r - F_exact|
     href = pcirc.ideal_reference(W4.n, ops4, x4, qs.QS_C128, stream)
@@ -834,18 +827,19 @@ def run_channels(args, rank, world, local_rank):
     ev = lambda: torch.cuda.Event(enable_timing=True)
     per_kind = {}
     plan = None
+    # the circuit as a plan: density -- noisy H channels as single sweeps, each run of
+    # diagonal channels as one sweep, timed per launch with events inside the captured
+    # graph; fixed rank -- every gate on the device, the circuit replayed as one graph
+    plan = qs.qs_plan_create(h, pcirc.to_gates(ops))
     if mode == qs.QS_DENSITY:
-        # the circuit as a plan (noisy H channels as single sweeps, each run of diagonal
-        # channels as one sweep), timed per launch with events inside the captured graph
-        plan = qs.qs_plan_create(h, pcirc.to_gates(ops))
         qs.qs_plan_set_timing(plan, True, h)
-        _, plan_kernels = qs.qs_plan_info(plan, h)
+    _, plan_kernels = qs.qs_plan_info(plan, h)
 
     def step(timed):
         qs.qs_set_basis_state(h, x0)
         if plan is not None:
             qs.qs_plan_run(plan, W.e, W.seed, 0, h)
-            if timed:
+            if timed and mode == qs.QS_DENSITY:
                 for m, k in zip(*qs.qs_plan_last_times(plan, h=h)):
                     per_kind.setdefault("H_channel" if k == "single_gate" else k, []).append(m)
             return qs.qs_fidelity_stored(h)
@@ -886,11 +880,23 @@ def run_channels(args, rank, world, local_rank):
         flop = (1 << (2 * n)) * (14 if dom == "dm_diag_block" else 16) // 2
         bytes_ = 3 * (1 << (2 * n)) * 16 // 2
     else:
-        dom = "H_channel"
-        M = 2 * W.rank
-        # Gram (M(M+1)/2 pairs) + projection (M x r), complex FP64 multiply-adds over 2^n rows
-        flop = (1 << n) * (M * (M + 1) // 2 + M * W.rank) * 8
-        bytes_ = 3 * (1 << n) * W.rank * 16
+        # the whole step: every channel's Gram matrix (M(M+1)/2 pairs of columns) and
+        # projection (M x keep) over 2^n rows, M = 2 m_prev and keep = min(r, M), the
+        # column count doubling from 1 up to r; FP64 multiply-adds, 2 flop each for the
+        # real factor of Grover (real arithmetic), 8 for a complex one
+        dom = "fixed_rank_step"
+        real = W.circuit == "grover"
+        cols, fma = 1, 0
+        for op in ops:
+            if not op.noisy:
+                continue
+            M = 2 * cols
+            keep = min(W.rank, M)
+            fma += (1 << n) * (M * (M + 1) // 2 + M * keep)
+            cols = keep
+        flop = fma * (2 if real else 8)
+        bytes_ = 3 * (1 << n) * W.rank * 16 * channels
+        kinds = {"fixed_rank_step": ms}
     avg = kinds.get(dom, ms)
     achieved = flop / (avg / 1e3) / 1e12
     fp64_peak, _ = qs.qs_measure_peaks()
@@ -905,7 +911,9 @@ def run_channels(args, rank, world, local_rank):
            "roofline": {"bound": "alu", "achieved": round(achieved, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
                         "frac": round(achieved / fp64_peak, 4), "traffic": None,
                         "kernel": {"H_channel": "noisy-H channel (all its launches)",
-                                   "dm_diag_block": "k_dm_diag_block (runs of diagonal channels)"}.get(dom, dom),
+                                   "dm_diag_block": "k_dm_diag_block (runs of diagonal channels)",
+                                   "fixed_rank_step": "the whole circuit (expansion, Gram, eigensolver, "
+                                                      "projection per channel)"}.get(dom, dom),
                         "avg_launch_ms": round(avg, 4),
                         "algorithmic_flop_per_launch": flop, "algorithmic_bytes_per_launch": bytes_,
                         "peak_source": "FP64 FMA rate measured live (qs_measure_peaks)",

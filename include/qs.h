@@ -106,7 +106,8 @@ qs_status qs_info(qs_handle h, int* n, int* batch, int* rank, int* mode, int* dt
  * if x >= 2^n. */
 qs_status qs_set_basis_state(qs_handle h, uint64_t x);
 
-/* Per-member basis states: xs[b] for b < batch (STATEVEC only). */
+/* Per-member basis states: xs[b] for b < batch (STATEVEC; FIXED_RANK: each
+ * member's factor becomes the one column |xs[b]>). */
 qs_status qs_set_basis_states(qs_handle h, const uint64_t* xs);
 
 /* Choi-Jamiolkowski relative states (Sec. 4): the maximally entangled state
@@ -242,7 +243,8 @@ qs_status qs_fidelity_stored(qs_handle h, double* out);
 
 /* STATEVEC: |<ref_0|psi_b>|^2 for members b = first .. first+count-1, with
  * ref_0 = member 0 of the STATEVEC handle `ref` (same n and dtype; read in
- * place on the device, after `ref`'s stream is synchronised).  out[count].
+ * place on the device, after `ref`'s stream is synchronised); FIXED_RANK:
+ * sum_c |<ref_0|L_{b,c}>|^2 over member b's columns.  out[count].
  * Lets members of one batch (different jobs) use different references. */
 qs_status qs_fidelity_ref(qs_handle h, qs_handle ref, int first, int count, double* out);
 
@@ -292,7 +294,8 @@ qs_status qs_set_trajectory_offset(qs_handle h, uint64_t offset);
  * offset for member b; marked[b] (may be NULL) replaces the index of plan
  * flips marked QS_FLIP_PER_MEMBER.  FIXED_RANK: e[b] sets member b's
  * averaged channel in qs_apply_noisy_gate (seed and traj are required but
- * unused).  Pass all NULL to clear. */
+ * unused) and marked[b] the index of member b's QS_FLIP_PER_MEMBER flips.
+ * Pass all NULL to clear. */
 qs_status qs_set_member_noise(qs_handle h, const double* e, const uint64_t* seed,
                               const uint64_t* traj, const uint64_t* marked);
 

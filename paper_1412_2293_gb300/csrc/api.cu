@@ -299,13 +299,13 @@ qs_status rank_channel_gate(qs_handle h, const int* targets, const qs::KrausGate
 }
 
 // FIXED_RANK: column c = 0 of every member <- |x> (or Eq. 16's state), the rest 0
-qs_status rank_set_start(qs_handle h, int entangled, uint64_t x) {
+qs_status rank_set_start(qs_handle h, int entangled, uint64_t x, const uint64_t* xs = nullptr) {
   const size_t N = 1ull << h->n;
   QS_CUDA(h, cudaMemsetAsync(h->state, 0, h->state_elems * h->esize, h->stream));
   for (int b = 0; b < h->batch; ++b) {
     void* col0 = (char*)h->state + (size_t)b * h->rank * N * h->esize;
     if (entangled) QS_CUDA(h, qs::launch_set_entangled(h, col0, 1, 0));
-    else QS_CUDA(h, qs::launch_set_basis(h, col0, h->n, 1, x, nullptr));
+    else QS_CUDA(h, qs::launch_set_basis(h, col0, h->n, 1, xs ? xs[b] : x, nullptr));
   }
   std::fill(h->m_cols.begin(), h->m_cols.end(), 1);
   h->real_factor = true;
@@ -494,9 +494,10 @@ qs_status qs_set_maximally_entangled(qs_handle h) {
 
 qs_status qs_set_basis_states(qs_handle h, const uint64_t* xs) {
   if (!h || !xs) return QS_ERR_INVALID_ARG;
-  if (h->mode != QS_STATEVEC) return fail(h, QS_ERR_NOT_SUPPORTED, "per-member basis states need STATEVEC");
+  if (h->mode == QS_DENSITY) return fail(h, QS_ERR_NOT_SUPPORTED, "per-member basis states need STATEVEC or FIXED_RANK");
   for (int b = 0; b < h->batch; ++b)
     if (xs[b] >= (1ull << h->n)) return fail(h, QS_ERR_INVALID_ARG, "basis index out of range");
+  if (h->mode == QS_FIXED_RANK) return rank_set_start(h, 0, 0, xs);
   if (!h->m_basis) QS_CUDA(h, cudaMalloc((void**)&h->m_basis, h->batch * sizeof(uint64_t)));
   // an earlier run may still read m_basis
   QS_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -788,14 +789,16 @@ qs_status qs_fidelity_stored(qs_handle h, double* out) {
 
 qs_status qs_fidelity_ref(qs_handle h, qs_handle ref, int first, int count, double* out) {
   if (!h || !ref || !out) return QS_ERR_INVALID_ARG;
-  if (h->mode != QS_STATEVEC || ref->mode != QS_STATEVEC || ref->n != h->n || ref->dtype != h->dtype)
+  if (h->mode == QS_DENSITY || ref->mode != QS_STATEVEC || ref->n != h->n || ref->dtype != h->dtype)
     return fail(h, QS_ERR_INVALID_ARG, "reference must be a STATEVEC handle with the same n and dtype");
   if (first < 0 || count < 1 || first + count > h->batch) return fail(h, QS_ERR_INVALID_ARG, "member range out of bounds");
   { const qs_status st = qs::materialize_basis(h); if (st != QS_OK) return st; }
   { const qs_status st = qs::materialize_basis(ref); if (st != QS_OK) return fail(h, st, ref->err); }
   QS_CUDA(h, cudaStreamSynchronize(ref->stream));
-  const char* psi = (const char*)h->state + ((size_t)first << h->n) * h->esize;
-  QS_CUDA(h, qs::launch_dot(h, psi, ref->state, h->n, count, 1, h->small + kSmallOut));
+  // FIXED_RANK: member b's columns, summed (sum_c |<ref|L_{b,c}>|^2)
+  const size_t cols = h->mode == QS_FIXED_RANK ? (size_t)h->rank : 1;
+  const char* psi = (const char*)h->state + (((size_t)first * cols) << h->n) * h->esize;
+  QS_CUDA(h, qs::launch_dot(h, psi, ref->state, h->n, (int)(count * cols), (int)cols, h->small + kSmallOut));
   return read_out(h, out, count);
 }
 
@@ -946,8 +949,12 @@ qs_status qs_set_member_noise(qs_handle h, const double* e, const uint64_t* seed
   if (marked) {
     for (int b = 0; b < h->batch; ++b)
       if (marked[b] >= (1ull << h->n)) return fail(h, QS_ERR_INVALID_ARG, "marked index out of range");
-    if (!h->m_marked) QS_CUDA(h, cudaMalloc((void**)&h->m_marked, B * sizeof(uint64_t)));
-    QS_CUDA(h, cudaMemcpyAsync(h->m_marked, marked, B * sizeof(uint64_t), cudaMemcpyHostToDevice, h->stream));
+    // FIXED_RANK: one index per column (a member's columns share its index)
+    const size_t per = h->mode == QS_FIXED_RANK ? (size_t)h->rank : 1;
+    std::vector<uint64_t> cols(B * per);
+    for (size_t i = 0; i < cols.size(); ++i) cols[i] = marked[i / per];
+    if (!h->m_marked) QS_CUDA(h, cudaMalloc((void**)&h->m_marked, cols.size() * sizeof(uint64_t)));
+    QS_CUDA(h, cudaMemcpyAsync(h->m_marked, cols.data(), cols.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, h->stream));
     h->member_marked = true;
   } else {
     h->member_marked = false;

@@ -1256,7 +1256,8 @@ qs_status run_rank_ops(qs_plan p) {
     const qs_gate& g = p->gates[op.gate].g;
     if (!op.real) real = false;
     if (op.kind == 0) {
-      e = launch_phase_flip(h, h->state, h->n, members, g.index, nullptr);
+      // QS_FLIP_PER_MEMBER: every column's own index (its member's marked item)
+      e = launch_phase_flip(h, h->state, h->n, members, g.index, g.kind == QS_FLIP_PER_MEMBER ? h->m_marked : nullptr);
     } else if (op.kind == 1) {
       e = launch_apply_1q(h, h->state, h->n, members, g.targets[0], g.U, nullptr);
     } else {
@@ -1450,7 +1451,7 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
     if (g.kind == QS_GATE_FLIP) {
       if (g.index >= (1ull << h->n)) { delete p; h->err = "flip index out of range"; return QS_ERR_INVALID_ARG; }
     } else if (g.kind == QS_FLIP_PER_MEMBER) {
-      if (h->mode != QS_STATEVEC) { delete p; h->err = "per-member flips need STATEVEC"; return QS_ERR_NOT_SUPPORTED; }
+      if (h->mode == QS_DENSITY) { delete p; h->err = "per-member flips need STATEVEC or FIXED_RANK"; return QS_ERR_NOT_SUPPORTED; }
     } else if (g.kind == QS_GATE_DENSE) {
       if (g.k < 1 || g.k > 2) { delete p; h->err = "plan gates must have k = 1 or 2"; return QS_ERR_INVALID_ARG; }
       for (int j = 0; j < g.k; ++j) {
@@ -1483,7 +1484,7 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
       const PGate& g = p->gates[i];
       RankOp op{};
       op.gate = i;
-      if (g.g.kind == QS_GATE_FLIP) {
+      if (g.g.kind == QS_GATE_FLIP || g.g.kind == QS_FLIP_PER_MEMBER) {
         op.kind = 0;
       } else {
         const int d = 1 << g.g.k;

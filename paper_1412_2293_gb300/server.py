@@ -79,6 +79,14 @@ def mc_key(job: inputs.Job) -> Tuple:
     return ("mc", job.circuit, job.n, job.iterations)
 
 
+def rank_key(job: inputs.Job) -> Tuple:
+    return ("rank", job.circuit, job.n, job.iterations)
+
+
+RANK_MAX = 8                          # rank bound of a batched fixed-rank handle
+RANK_MEMBERS = 16                     # most fixed-rank jobs in one launch
+
+
 def member_bytes(n: int) -> int:
     """Device bytes of one complex64 trajectory (upper bound): its amplitudes,
     reduction partials (1/64 of the state), the out-of-window factors of the
@@ -87,10 +95,12 @@ def member_bytes(n: int) -> int:
     return (1 << n) * C64_BYTES + (1 << n) // 64 + (11 * C64_BYTES << max(n - 10, 0)) + (1 << 19)
 
 
-def rank_bytes(n: int, r: int) -> int:
-    """Device bytes of a fixed-rank job: factor, 32-column work buffer, scratch and reference."""
+def rank_bytes(n: int, r: int = RANK_MAX) -> int:
+    """Device bytes of one member of a batched fixed-rank launch (rank bound
+    r): factor, work buffer of min(32, 8 r) columns, Gram partials and other
+    scratch, and the job's reference."""
     N = 1 << n
-    return (r + 32) * N * C128_BYTES + N * 256 + N * C128_BYTES
+    return (r + min(32, 8 * r)) * N * C128_BYTES + N * 256 + N * C128_BYTES
 
 
 def bucket_for(members: int, lo: int, hi: int) -> int:
@@ -135,7 +145,7 @@ class Scheduler:
     def min_bytes(self, job: inputs.Job) -> int:
         """Device memory of the smallest unit a job can run in."""
         if job.mode == "fixed_rank":
-            return rank_bytes(job.n, job.rank)
+            return rank_bytes(job.n)
         return member_bytes(job.n) * self.min_bucket + (1 << job.n) * C64_BYTES
 
     def submit(self, job: inputs.Job, now: float) -> None:
@@ -169,10 +179,9 @@ class Scheduler:
             st = self.jobs[jid]
             job = st.job
             if job.mode == "fixed_rank":
-                b = rank_bytes(job.n, job.rank)
-                if b <= free:
-                    self.order.remove(jid)
-                    return self._issue(Unit("rank", ("rank", job.n, job.rank), [Slice(jid, 0, 1)], 1, b), [])
+                made = self._rank_unit(rank_key(job), free)
+                if made is not None:
+                    return self._issue(made, [])
             else:
                 made = self._mc_unit(mc_key(job), free)
                 if made is not None:
@@ -180,6 +189,27 @@ class Scheduler:
             if pos == 0 and now - st.arrival > self.starve_s:
                 return None
         return None
+
+    def _rank_unit(self, key, free):
+        """Pack pending fixed-rank jobs of one shape (ranks up to RANK_MAX, own
+        e, start, marked item) into one launch of a batched handle."""
+        per = rank_bytes(key[2])
+        fit = largest_bucket(free // per, RANK_MEMBERS)
+        if fit < 1:
+            return None
+        slices = []
+        for jid in self.order:
+            st = self.jobs[jid]
+            if st.job.mode == "fixed_rank" and rank_key(st.job) == key:
+                slices.append(Slice(jid, 0, 1))
+                if len(slices) >= fit:
+                    break
+        if not slices:
+            return None
+        for sl in slices:
+            self.order.remove(sl.job_id)
+        members = bucket_for(len(slices), 1, RANK_MEMBERS)
+        return Unit("rank", key, slices, members, members * per)
 
     def _mc_unit(self, key, free):
         """Pack pending trajectories of every job of one shape into one launch."""
@@ -357,22 +387,49 @@ class GpuExecutor:
         return self._run_mc(w, unit, jobs)
 
     def _run_rank(self, w, unit, jobs):
+        """The fixed-rank jobs of a unit as members of one batched handle: each
+        with its own rank, e, start state and marked item, the circuit run as
+        one replayed plan, each fidelity against the job's own reference."""
         qs = self.qs
         from . import circuits as pc
-        job = jobs[unit.slices[0].job_id].job
-        ref = self._reference(w, job, qs.QS_C128)
+        _, circuit, n, iters = unit.key
         ent = self._checkout(unit.cache_key)
         if ent is None:
-            h = qs.qs_create(job.n, 1, job.rank, qs.QS_FIXED_RANK, qs.QS_C128, self.streams[w])
-            ent = (h, None, unit.bytes)
-        h = ent[0]
+            ops = inputs.grover_circuit(n, iters, 1) if circuit == "grover" else inputs.qft_circuit(n)
+            h = qs.qs_create(n, unit.members, RANK_MAX, qs.QS_FIXED_RANK, qs.QS_C128, self.streams[w])
+            try:
+                p = qs.qs_plan_create(h, pc.to_gates(ops, per_member_flip=True))
+            except BaseException:
+                qs.qs_destroy(h)
+                raise
+            ent = (h, p, unit.bytes)
+        h, p, _ = ent
         try:
-            qs.qs_set_reference_from(h, ref, 0)
-            qs.qs_set_basis_state(h, inputs.job_initial_basis(job))
-            pc.apply_ops(h, inputs.job_ops(job), job.e, job.seed)
-            out = [qs.qs_fidelity_stored(h)]
+            B = unit.members
+            ranks = np.ones(B, dtype=np.int32)
+            e = np.zeros(B)
+            basis = np.zeros(B, dtype=np.uint64)
+            marked = np.zeros(B, dtype=np.uint64)
+            for m, sl in enumerate(unit.slices):
+                job = jobs[sl.job_id].job
+                ranks[m], e[m] = job.rank, job.e
+                basis[m] = inputs.job_initial_basis(job)
+                if circuit == "grover":
+                    marked[m] = inputs.draw_marked(job.n, job.seed)
+            # padding members (rank 1) repeat the last job; their results are dropped
+            m = len(unit.slices)
+            if m < B:
+                e[m:], basis[m:], marked[m:] = e[m - 1], basis[m - 1], marked[m - 1]
+            qs.qs_set_member_ranks(h, ranks)
+            qs.qs_set_member_noise(h, e, np.zeros(B, dtype=np.uint64), np.zeros(B, dtype=np.uint64), marked)
+            qs.qs_set_basis_states(h, basis)
+            qs.qs_plan_run(p, 0.0, 0, 0, h)
+            out = []
+            for m, sl in enumerate(unit.slices):
+                ref = self._reference(w, jobs[sl.job_id].job, qs.QS_C128)
+                out.append(qs.qs_fidelity_ref(h, ref, m, 1))
         except BaseException:
-            self._free(h, None)
+            self._free(h, p)
             raise
         self._checkin(unit.cache_key, ent)
         return out
@@ -459,6 +516,7 @@ class Server:
         self.results: Dict[int, JobResult] = {}
         self.errors: List[BaseException] = []
         self.free_workers = list(range(executor.workers))
+        self.max_rank_jobs = 0                    # most fixed-rank jobs in one launch so far
         self.stop = False
         self.threads: List[threading.Thread] = []
         self.dispatcher = threading.Thread(target=self._dispatch, daemon=True)
@@ -489,6 +547,8 @@ class Server:
                 if unit is None:
                     self.lock.wait(0.01)
                     continue
+                if unit.kind == "rank":
+                    self.max_rank_jobs = max(self.max_rank_jobs, len(unit.slices))
                 w = self.free_workers.pop()
                 th = threading.Thread(target=self._work, args=(w, unit), daemon=True)
                 self.threads.append(th)

@@ -63,6 +63,10 @@ def mixed_jobs():
         J(5, 0.003, "grover", 8, "fixed_rank", 1, 3, 2e-2, 106, inputs.grover_iterations(8)),
         J(6, 0.003, "qft", 9, "fixed_rank", 1, 4, 3e-2, 107, 0),
         J(7, 0.004, "qft", 11, "statevec", 16, 0, 1e-2, 108, 0),
+        # more fixed-rank jobs of the same two shapes (own rank, e, start, marked item)
+        J(8, 0.004, "grover", 8, "fixed_rank", 1, 1, 5e-3, 109, inputs.grover_iterations(8)),
+        J(9, 0.004, "grover", 8, "fixed_rank", 1, 8, 1e-2, 110, inputs.grover_iterations(8)),
+        J(10, 0.004, "qft", 9, "fixed_rank", 1, 2, 1e-3, 111, 0),
     ]
 
 
@@ -75,10 +79,12 @@ def test_server_results_same_alone_and_in_the_mix():
         results, stats = run_stream(jobs, srv, time_scale=1.0, timeout=600)
         max_run = srv.sched.max_in_flight
         units = srv.sched._uid
+        batched_rank = srv.max_rank_jobs
     finally:
         srv.close()
     assert stats["jobs"] == len(jobs)
     assert units > 4 and max_run >= 2
+    assert batched_rank >= 2                                      # fixed-rank jobs shared a launch
 
     # each job alone, in a launch of its own
     ex = GpuExecutor(workers=1, cache_bytes=0)
@@ -86,7 +92,7 @@ def test_server_results_same_alone_and_in_the_mix():
         for j in jobs:
             states = {j.job_id: JobState(j, 0.0)}
             if j.mode == "fixed_rank":
-                u = Unit("rank", ("rank", j.n, j.rank), [Slice(j.job_id, 0, 1)], 1, rank_bytes(j.n, j.rank))
+                u = Unit("rank", ("rank", j.circuit, j.n, j.iterations), [Slice(j.job_id, 0, 1)], 1, rank_bytes(j.n))
             else:
                 B = bucket_for(j.trajectories, 16, 1 << 12)
                 u = Unit("mc", ("mc", j.circuit, j.n, j.iterations), [Slice(j.job_id, 0, j.trajectories)], B,

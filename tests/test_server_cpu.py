@@ -185,3 +185,21 @@ def test_member_bytes_cover_state_partials_and_out_factors():
         state = 8 << n
         # amplitudes, fused-fidelity partials (1/64) and 11 complex64 out factors per 1024 amplitudes
         assert member_bytes(n) >= state + (1 << n) // 64 + 88 * (1 << (n - 10))
+
+
+def test_fixed_rank_jobs_of_one_shape_share_a_launch():
+    n = 12
+    s = Scheduler(1 << 34)
+    k = inputs.grover_iterations(n)
+    for i in range(5):
+        s.submit(job(i, n=n, circuit="grover", mode="fixed_rank", rank=1 + i, iters=k), 0.0)
+    s.submit(job(5, n=n, circuit="qft", mode="fixed_rank", rank=3), 0.0)
+    u = s.next_unit(0.0)
+    assert u.kind == "rank" and [sl.job_id for sl in u.slices] == [0, 1, 2, 3, 4]
+    assert u.members == 8 and u.bytes == 8 * rank_bytes(n)
+    u2 = s.next_unit(0.0)
+    assert u2.kind == "rank" and [sl.job_id for sl in u2.slices] == [5] and u2.members == 1
+    assert s.next_unit(0.0) is None
+    s.complete(u, [np.zeros(1)] * 5, 1.0)
+    s.complete(u2, [np.zeros(1)], 1.0)
+    assert sorted(s.finished) == [0, 1, 2, 3, 4, 5] and s.used == 0
