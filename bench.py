@@ -168,15 +168,18 @@ def run_ours(args, rank, world, local_rank):
     qs.qs_destroy(ref)
     qs.qs_set_trajectory_offset(h, traj0)
     p = qs.qs_plan_create(h, pcirc.to_gates(ops))
-    passes, launches = qs.qs_plan_info(p, h)
-    # kernel configuration of the passes: given, or the fastest on this plan (eager runs, untimed)
+    # window width and kernel configuration of the passes: given, or the fastest on this
+    # plan (eager runs, untimed)
     if args.kernel_config:
         lo, hi = (int(x) for x in args.kernel_config.split(","))
+        qs.qs_plan_set_window(p, args.window, h)
         qs.qs_plan_set_config(p, lo, hi, h)
         tune_ms = (-1.0, -1.0)
     else:
         tune_ms = qs.qs_plan_autotune(p, 2, e, seed, h)
     kernel_cfg = qs.qs_plan_get_config(p, h)
+    window = qs.qs_plan_get_window(p, h)
+    passes, launches = qs.qs_plan_info(p, h)
     qs.qs_plan_set_timing(p, True, h)
     updates_per_step = T * (1 << n) * len(ops)
 
@@ -274,7 +277,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": args.workload, "circuit": W.circuit, "n": n, "trajectories_per_gpu": T,
                    "gates": len(ops), "e": e, "noise": "rotation (H), phase (CP), Philox on device",
                    "passes_per_step": passes, "parallelism": f"trajectories sharded over {world} GPU(s)",
-                   "kernel_config": {"low": kernel_cfg[0], "high": kernel_cfg[1],
+                   "kernel_config": {"window": window, "low": kernel_cfg[0], "high": kernel_cfg[1],
                                      "autotune_ms": [round(x, 4) for x in tune_ms]},
                    "circuits_per_s": T * world / (ms_per_step / 1e3),
                    "state_bytes": T * (1 << n) * esize,
@@ -546,6 +549,53 @@ def extra_rows(h, n, T, esize, stream, peaks):
         cmp[f"r{r}"] = {"f": f_r, "abs_diff": abs(f_r - f_exact), "ms_per_circuit": round(e0.elapsed_time(e1), 2)}
         qs.qs_destroy(hr)
     out["dm_vs_fixed_rank_qft_n14"] = cmp
+
+    # a9: window width m of the passes.  The noisy QFT at n = 20 (this run's 1024
+    # trajectories) and n = 24 (64 trajectories, 8 GiB): each width with its default
+    # kernel configuration, passes per step and the HBM floor of those passes, then the
+    # width and configurations the autotuner picks on a fresh plan
+    Wq = inputs.WORKLOADS["mc_qft_n20_c64"]
+    a9 = {}
+    for nq, Tq in ((Wq.n, T), (24, 64)):
+        opsq = inputs.qft_circuit(nq)
+        xq = inputs.draw_basis_input(nq, Wq.seed)
+        hq = qs.qs_create(nq, Tq, 0, qs.QS_STATEVEC, qs.QS_C64, stream)
+        refq = pcirc.ideal_reference(nq, opsq, xq, qs.QS_C64, stream)
+        qs.qs_set_reference_from(hq, refq, 0)
+        qs.qs_destroy(refq)
+        sb = Tq * (1 << nq) * 8
+        row = {"trajectories": Tq, "state_bytes": sb}
+        fm = {}
+        for m in (10, 11, 12):
+            pq = qs.qs_plan_create(hq, pcirc.to_gates(opsq))
+            qs.qs_plan_set_window(pq, m, hq)
+            npass, _ = qs.qs_plan_info(pq, hq)
+            for _ in range(2):
+                qs.qs_set_basis_state(hq, xq)
+                qs.qs_plan_run_fidelity(pq, Wq.e, Wq.seed, 0, hq)
+            e0, e1 = ev(), ev()
+            reps = 5
+            e0.record(stream)
+            for _ in range(reps):
+                qs.qs_set_basis_state(hq, xq)
+                fq = qs.qs_plan_run_fidelity(pq, Wq.e, Wq.seed, 0, hq)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            msq = e0.elapsed_time(e1) / reps
+            qs.qs_plan_destroy(pq)
+            fm[m] = np.asarray(fq)
+            floor = (2 * npass - 1) * sb / (peaks["hbm_gbs"] * 1e9) * 1e3    # the first pass only writes
+            row[f"m{m}"] = {"passes": npass, "ms_per_step": round(msq, 3), "hbm_floor_ms": round(floor, 3),
+                            "frac_of_floor": round(floor / msq, 4), "fidelity_mean": float(fm[m].mean())}
+        row["fidelity_max_abs_diff_vs_m10"] = max(float(np.abs(fm[m] - fm[10]).max()) for m in (11, 12))
+        pq = qs.qs_plan_create(hq, pcirc.to_gates(opsq))
+        tl, th = qs.qs_plan_autotune(pq, 2, Wq.e, Wq.seed, hq)
+        row["autotuned"] = {"window": qs.qs_plan_get_window(pq, hq), "config": list(qs.qs_plan_get_config(pq, hq)),
+                            "pass_ms": [round(tl, 4), round(th, 4)]}
+        qs.qs_plan_destroy(pq)
+        qs.qs_destroy(hq)
+        a9[f"qft_n{nq}"] = row
+    out["a9_window_width"] = a9
 
     # a3 at the other precision and noise level of the bench circuit: complex128 on the
     # same 1024 trajectories (16 GiB), compared member by member with the complex64 run,
@@ -1104,6 +1154,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the bounded measurements of the other rows")
     ap.add_argument("--kernel-config", default=None,
                     help="low,high pass configuration indices (qs_plan_set_config) instead of autotuning")
+    ap.add_argument("--window", type=int, default=10,
+                    help="window width of the passes with --kernel-config (qs_plan_set_window)")
     ap.add_argument("--micro", choices=sorted(MICRO), default=None,
                     help="time one kernel on its own (for a profiler) instead of the bench step")
     args = ap.parse_args()

@@ -367,15 +367,32 @@ qs_status qs_plan_profile(qs_plan p, int reps, double e, uint64_t seed, uint64_t
 qs_status qs_plan_set_timing(qs_plan p, int on);
 qs_status qs_plan_last_times(qs_plan p, double* ms, int* kinds, int cap, int* count);
 
+/* Window width m of the fused passes (no counterpart in the paper, which
+ * updates the state one gate at a time, Sec. 2: a pass applies the run of
+ * gates acting on m qubits to each tile of 2^m amplitudes with one read and
+ * one write of the state).  m = 10 for a new plan; 11 and 12 need a STATEVEC
+ * complex64 handle with n <= 32 (NOT_SUPPORTED otherwise; INVALID_ARG for
+ * another m).  A wider window takes more gates per pass, so fewer passes over
+ * the state (the QFT at n = 24: two passes for m = 12, three for m = 10).
+ * Setting m re-plans the passes (waits for the handle's stream, drops the
+ * captured graphs and resets the kernel configuration to the new width's
+ * default); results agree with every m up to rounding.  On failure (device
+ * memory) the plan runs nothing until a later call succeeds. */
+qs_status qs_plan_set_window(qs_plan p, int m);
+qs_status qs_plan_get_window(qs_plan p, int* m);
+
 /* Kernel configuration of the fused passes (no counterpart in the paper: the
- * tiling of the update, Sec. 2, is the implementation's).  For each window
- * geometry (low: qubits 0..9, high: the 10 highest) a configuration index in
- * [0, count): complex64 has three low and three high -- low 0: 12 warps, two
+ * tiling of the update, Sec. 2, is the implementation's).  For m = 10 and
+ * each window geometry (low: qubits 0..9, high: the 10 highest) a
+ * configuration index in [0, count): complex64 has three low and three high
+ * -- low 0: 12 warps, two
  * tile buffers per warp; low 1: 16 warps, one buffer; low 2: 12 warps, one
  * buffer; high 0: one block of
  * 8 warps per SM, two buffers; high 1: two such blocks per SM, one buffer;
  * high 2: four blocks of 4 warps per SM (4-column tiles), one buffer --
- * complex128 one of each.
+ * complex128 one of each.  m = 11 and 12 have one of each: low 12 warps in
+ * groups of 2^(m-10) warps per tile, one buffer per group; high one block
+ * of 16 warps per SM, one buffer, tiles of 8 (m = 11) or 4 (m = 12) columns.
  * A new plan starts with low 2 / high 1 (complex64), 0 / 0 (complex128).
  * Results do not depend on the configuration.  qs_plan_configs returns the
  * counts; qs_plan_set_config rejects an index out of range with
@@ -383,11 +400,15 @@ qs_status qs_plan_last_times(qs_plan p, double* ms, int* kinds, int cap, int* co
 qs_status qs_plan_configs(qs_plan p, int* low_count, int* high_count);
 qs_status qs_plan_set_config(qs_plan p, int low_cfg, int high_cfg);
 qs_status qs_plan_get_config(qs_plan p, int* low_cfg, int* high_cfg);
-/* Autotune: time every configuration on this plan (qs_plan_profile with
- * `reps` runs each, noise e and key seed), keep the fastest per geometry and
- * write its mean pass time in ms to best_ms[0] (low) and best_ms[1] (high)
- * (-1 where the plan has no pass of that geometry; best_ms may be NULL).
- * The runs overwrite the state: set the start state afterwards.  Synchronises. */
+/* Autotune: for every window width the handle allows (10, 11 and 12 for a
+ * STATEVEC complex64 handle with m <= n <= 32, else the current one), time
+ * every configuration on this plan (qs_plan_profile with `reps` runs each,
+ * noise e and key seed); keep the width whose run is fastest with its
+ * fastest configuration per geometry, and write those configurations' mean
+ * pass times in ms to best_ms[0] (low) and best_ms[1] (high) (-1 where the
+ * plan has no pass of that geometry; best_ms may be NULL).
+ * qs_plan_get_window then reports the width chosen.  The runs overwrite the
+ * state: set the start state afterwards.  Synchronises. */
 qs_status qs_plan_autotune(qs_plan p, int reps, double e, uint64_t seed, double* best_ms);
 
 /* ------------------------------------------------------------ utilities */

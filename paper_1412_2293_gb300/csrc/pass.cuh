@@ -1,24 +1,28 @@
 // Fused window passes (device side).  See plan.cu for the planner.
 //
-// A pass applies a run of gates whose dense targets lie in a window of 10
-// qubits to every tile of the state in one HBM read and one HBM write (the
-// amplitude update of Sec. 2, with the memory dependence the paper describes
-// kept inside a tile).  Each thread holds 32 amplitudes that differ in 5
-// "register" bits of the window: a one-qubit gate on a register bit is a
-// butterfly over registers; an exchange through shared memory swaps the
-// register bits (stage A: window bits 5..9, stage B: bits 0..4).
+// A pass applies a run of gates whose dense targets lie in a window of M
+// qubits (M = 10, 11 or 12) to every tile of the state in one HBM read and
+// one HBM write (the amplitude update of Sec. 2, with the memory dependence
+// the paper describes kept inside a tile).  Each thread holds 32 amplitudes
+// that differ in 5 "register" bits of the window: a one-qubit gate on a
+// register bit is a butterfly over registers; an exchange through shared
+// memory changes which 5 window bits are in registers.  The register bits of
+// a stage are 5 consecutive window bits: stage 0 (A) the top five, stage 1
+// (B) bits 0..4 and, for M > 10, stage 2 (C) bits 5..9; the other M - 5 bits
+// index the thread (32 lanes x 2^(M-10) warps of a tile).
 //
 // Tiles stream through shared memory: while a block computes tile i, the copy
-// engine fills the other buffer with tile i+1 (a 1D bulk copy per warp for the
-// low window, a 2D tensor-map copy per block for the high window), completion
-// tracked by mbarriers.  Every wait is bounded: on timeout the kernel records
-// an error in a device status word, waits (bounded) for copies it still has
-// in flight, and returns.
+// engine fills the other buffer with tile i+1 (a 1D bulk copy per tile for
+// the low window, a 2D tensor-map copy per block for the high window),
+// completion tracked by mbarriers.  Every wait is bounded: on timeout the
+// kernel records an error in a device status word, waits (bounded) for
+// copies it still has in flight, and returns.
 #pragma once
 
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include <cstdint>
@@ -28,7 +32,8 @@
 namespace qs {
 namespace fused {
 
-constexpr int kWin = 10;
+constexpr int kWin = 10;                   // the default window width M
+constexpr int kMaxWin = 12;                // the widest window (complex64)
 constexpr int kRegBits = 5;
 constexpr int kAmps = 32;
 constexpr int kMaxOther = 48;
@@ -56,7 +61,7 @@ struct FOp {
 // `dwin`) -- followed by `nflip` flips.  The planner only forms a segment
 // when that order keeps every pair of non-commuting gates in circuit order.
 struct Seg {
-  uint8_t stage;      // 0 = A (registers = window bits 5..9), 1 = B (0..4)
+  uint8_t stage;      // 0 = A (registers = window bits M-5..M-1), 1 = B (0..4), 2 = C (5..9)
   uint8_t dense;
   uint8_t dwin;
   uint8_t real;
@@ -82,16 +87,15 @@ struct OutTerm {
 struct PassArgs {
   int n;
   int start_stage;            // 0 = A, 1 = B
-  int win[kWin];
+  int m;                      // window width M (the kernel's template argument)
+  int win[kMaxWin];
   int nseg;
   Seg segs[kMaxSegs];         // the program (constant bank: uniform, cached)
   Flip flips[kMaxFlips];
-  int out_start[12];          // out terms grouped by attach a (0..9) and 10 = none
-  const OutTerm* outs;
-  // out factors per member and out-of-window tile value o (2^(n-10) of them):
-  // 11 complex, entry a = the product of the out terms attached to window bit
-  // a (10: none) whose out-of-window bits are set in o, times the deferred
-  // diagonal of bit a (10: the overall scale); null when the pass has none
+  // out factors per member and out-of-window tile value o (2^(n-M) of them):
+  // M + 1 complex, entry a = the product of the out terms attached to window
+  // bit a (M: none) whose out-of-window bits are set in o, times the deferred
+  // diagonal of bit a (M: the overall scale); null when the pass has none
   const void* alpha_tab;
   int param_stride;           // R units per member
   const void* params;
@@ -120,6 +124,73 @@ struct PassArgs {
   // take kSpinLimit
   uint32_t spin_limit;
 };
+
+// First window bit held in registers in stage S of a window of M bits.
+__host__ __device__ constexpr int stage_base(int m, int s) { return s == 0 ? m - kRegBits : (s == 1 ? 0 : 5); }
+
+// Where register r of thread t (the thread's M - 5 window bits, in
+// increasing order of the bits they stand for) sits in a tile of 2^M
+// amplitudes in stage S: tile_base + r tile_step, in the plain layout (as
+// copied from memory) and in the padded exchange layout, which puts one pad
+// slot after every 32 amplitudes, x -> x + x / 32.  Both layouts keep the
+// accesses of a warp free of bank conflicts in every stage: its lanes hold
+// consecutive amplitudes (stages A, C) or amplitudes 32 apart that the
+// padding moves to consecutive banks (stage B).
+template <int M, int S>
+__device__ __forceinline__ int tile_base(int t) {
+  if constexpr (S == 0) return t;
+  else if constexpr (S == 1) return t << 5;
+  else return (t & 31) | ((t >> 5) << 10);
+}
+template <int M, int S> __device__ __forceinline__ constexpr int tile_step() {
+  return S == 0 ? 1 << (M - 5) : (S == 1 ? 1 : 32);
+}
+template <int M, int S>
+__device__ __forceinline__ int pad_base(int t) {
+  if constexpr (S == 0) return t + (t >> 5);
+  else if constexpr (S == 1) return 33 * t;
+  else return (t & 31) + 1056 * (t >> 5);
+}
+template <int M, int S> __device__ __forceinline__ constexpr int pad_step() {
+  return S == 0 ? (1 << (M - 5)) + (1 << (M - 10)) : (S == 1 ? 1 : 33);
+}
+// the window bit that thread bit k stands for in stage S
+template <int M, int S> __device__ __forceinline__ constexpr int thread_bit(int k) {
+  return S == 0 ? k : (S == 1 ? k + 5 : (k < 5 ? k : k + 5));
+}
+
+// Run f with the stage as a compile-time constant (stage 2 exists for M > 10).
+template <int M, typename F>
+__device__ __forceinline__ void with_stage(int stage, F&& f) {
+  if (stage == 0) {
+    f(std::integral_constant<int, 0>{});
+  } else if (M == kWin || stage == 1) {
+    f(std::integral_constant<int, 1>{});
+  } else {
+    if constexpr (M > kWin) f(std::integral_constant<int, 2>{});
+  }
+}
+
+// Barrier over the 32 G threads of one tile (G = 1: the warp).  Named
+// barrier id + 1 (id 0 is __syncthreads).
+template <int G>
+__device__ __forceinline__ void group_sync(int id) {
+  if constexpr (G == 1) __syncwarp();
+  else asm volatile("bar.sync %0, %1;" ::"r"(id + 1), "r"(G * 32) : "memory");
+}
+// True on every thread of the group when it is true on any of them.
+template <int G>
+__device__ __forceinline__ bool group_any(int id, bool v) {
+  if constexpr (G == 1) {
+    return __any_sync(0xffffffffu, v);
+  } else {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, %2, %3, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(r) : "r"((uint32_t)v), "r"(id + 1), "r"(G * 32) : "memory");
+    return r != 0;
+  }
+}
 
 // ---------------------------------------------------------------- async copies
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -307,17 +378,30 @@ __device__ __forceinline__ void third_shear_reg(cplx<R> (&a)[kAmps], const R* m)
   }
 }
 
-// Multiply registers with bit RJ set by T[idx]: stage A idx = tbits | (low
-// register bits << 5), stage B idx = the register bits below RJ.
-template <typename R, int RJ, bool STAGE_A>
+// Multiply registers with bit RJ set by T[idx], the phase table of window
+// bit SH + RJ over the bits below it: idx = tbits (the thread's window bits
+// below SH) | (register bits below RJ) << SH.  SPLIT (windows above 10
+// qubits): the table is stored as its two factors, 2^SH entries over the
+// thread's bits then 2^RJ over the register bits (the product over a set of
+// bits splits that way), so a tile reads a few hundred entries per table
+// instead of up to 2^11, and the register part is the same for every lane.
+template <typename R, int RJ, int SH, bool SPLIT = false>
 __device__ __forceinline__ void dwin_reg(cplx<R> (&a)[kAmps], const R* T, int tbits) {
   constexpr int Q = 1 << RJ;
+  constexpr bool kSplit = SPLIT && SH > 0;
+  cplx<R> flo = mk<R>(R(1), R(0));
+  if constexpr (kSplit) flo = ld_c(T + 2 * tbits);
   // factor q multiplies the registers with bit RJ set and low bits q; each
   // factor is consumed right after its load (few live registers)
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    const int idx = STAGE_A ? (tbits + (q << 5)) : q;   // tbits < 32
-    const cplx<R> f = ld_c(T + 2 * idx);
+    cplx<R> f;
+    if constexpr (kSplit) {
+      f = q == 0 ? flo : pmul<R>(ld_c(T + 2 * ((1 << SH) + q)), flo);
+    } else {
+      const int idx = SH ? (tbits + (q << SH)) : q;
+      f = ld_c(T + 2 * idx);
+    }
 #pragma unroll
     for (int hi = 0; hi < kAmps / (2 * Q); ++hi) {
       const int r = q | Q | (hi << (RJ + 1));
@@ -380,26 +464,26 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 }
 
 // ---------------------------------------------------------------- segments
-template <typename R, int J, bool SA>
+template <typename R, int J, int SH, bool SPLIT>
 __device__ __forceinline__ void seg_step(cplx<R> (&a)[kAmps], const Seg& sg, const R* P, int tbits, bool stable) {
   if ((sg.dense >> J) & 1) dense_reg<R, J>(a, P + sg.doff[J], (sg.real >> J) & 1, stable);
-  if ((sg.dwin >> J) & 1) dwin_reg<R, J, SA>(a, P + sg.woff[J], tbits);
+  if ((sg.dwin >> J) & 1) dwin_reg<R, J, SH, SPLIT>(a, P + sg.woff[J], tbits);
 }
 
-template <typename R, bool SA>
+template <typename R, int SH, bool SPLIT = false>
 __device__ __forceinline__ void run_seg(cplx<R> (&a)[kAmps], const Seg& sg, const R* P, int tbits, bool stable) {
   if (sg.desc) {
-    seg_step<R, 4, SA>(a, sg, P, tbits, stable);
-    seg_step<R, 3, SA>(a, sg, P, tbits, stable);
-    seg_step<R, 2, SA>(a, sg, P, tbits, stable);
-    seg_step<R, 1, SA>(a, sg, P, tbits, stable);
-    seg_step<R, 0, SA>(a, sg, P, tbits, stable);
+    seg_step<R, 4, SH, SPLIT>(a, sg, P, tbits, stable);
+    seg_step<R, 3, SH, SPLIT>(a, sg, P, tbits, stable);
+    seg_step<R, 2, SH, SPLIT>(a, sg, P, tbits, stable);
+    seg_step<R, 1, SH, SPLIT>(a, sg, P, tbits, stable);
+    seg_step<R, 0, SH, SPLIT>(a, sg, P, tbits, stable);
   } else {
-    seg_step<R, 0, SA>(a, sg, P, tbits, stable);
-    seg_step<R, 1, SA>(a, sg, P, tbits, stable);
-    seg_step<R, 2, SA>(a, sg, P, tbits, stable);
-    seg_step<R, 3, SA>(a, sg, P, tbits, stable);
-    seg_step<R, 4, SA>(a, sg, P, tbits, stable);
+    seg_step<R, 0, SH, SPLIT>(a, sg, P, tbits, stable);
+    seg_step<R, 1, SH, SPLIT>(a, sg, P, tbits, stable);
+    seg_step<R, 2, SH, SPLIT>(a, sg, P, tbits, stable);
+    seg_step<R, 3, SH, SPLIT>(a, sg, P, tbits, stable);
+    seg_step<R, 4, SH, SPLIT>(a, sg, P, tbits, stable);
   }
 }
 
@@ -408,40 +492,51 @@ __device__ __forceinline__ void run_seg(cplx<R> (&a)[kAmps], const Seg& sg, cons
 // table where the program has one, then the same on stage B -- runs as
 // straight-line code: no per-step branches or segment-table lookups, so the
 // compiler schedules the table loads of a step ahead of the work before it.
-// PROG = 0: the segment list is interpreted (any program).  Otherwise bit 10
-// is set, bits 0..4 hold the phase-table mask of stage A and bits 5..9 that
-// of stage B; the planner picks it only for a program of exactly that shape
-// (two descending segments A then B, all five gates real, no flips).
+// PROG = 0: the segment list is interpreted (any program).  Otherwise, for
+// M = 10, bit 10 is set, bits 0..4 hold the phase-table mask of stage A and
+// bits 5..9 that of stage B; the planner picks it only for a program of
+// exactly that shape (two descending segments A then B, all five gates real,
+// no flips).  For M > 10 (prog_wide) bit 30 is set and the program is three
+// descending segments A, C, B, each with its mask of real gates and of phase
+// tables (5 bits each).
 constexpr int kProgLayers = 1 << 10;
 constexpr int prog_layers(int dwin_a, int dwin_b) { return kProgLayers | dwin_a | (dwin_b << 5); }
+constexpr int kProgWide = 1 << 30;
+constexpr int prog_wide(int dense_a, int dwin_a, int dense_c, int dwin_c, int dense_b, int dwin_b) {
+  return kProgWide | dense_a | (dwin_a << 5) | (dense_c << 10) | (dwin_c << 15) | (dense_b << 20) | (dwin_b << 25);
+}
+__host__ __device__ constexpr int prog_field(int prog, int k) { return (prog >> (5 * k)) & 31; }
 
-template <typename R, bool SA, int W, int J>
+template <typename R, int SH, int D, int W, int J, bool SPLIT>
 __device__ __forceinline__ void layer_step(cplx<R> (&a)[kAmps], const Seg& sg, const R* P, int tbits) {
-  dense_real_reg<R, J>(a, P + sg.doff[J]);
-  if constexpr (((W >> J) & 1) != 0) dwin_reg<R, J, SA>(a, P + sg.woff[J], tbits);
+  if constexpr (((D >> J) & 1) != 0) dense_real_reg<R, J>(a, P + sg.doff[J]);
+  if constexpr (((W >> J) & 1) != 0) dwin_reg<R, J, SH, SPLIT>(a, P + sg.woff[J], tbits);
 }
 
-template <typename R, bool SA, int W>
+template <typename R, int SH, int W, int D = 31, bool SPLIT = false>
 __device__ __forceinline__ void run_layer(cplx<R> (&a)[kAmps], const Seg& sg, const R* P, int tbits) {
-  layer_step<R, SA, W, 4>(a, sg, P, tbits);
-  layer_step<R, SA, W, 3>(a, sg, P, tbits);
-  layer_step<R, SA, W, 2>(a, sg, P, tbits);
-  layer_step<R, SA, W, 1>(a, sg, P, tbits);
-  layer_step<R, SA, W, 0>(a, sg, P, tbits);
+  layer_step<R, SH, D, W, 4, SPLIT>(a, sg, P, tbits);
+  layer_step<R, SH, D, W, 3, SPLIT>(a, sg, P, tbits);
+  layer_step<R, SH, D, W, 2, SPLIT>(a, sg, P, tbits);
+  layer_step<R, SH, D, W, 1, SPLIT>(a, sg, P, tbits);
+  layer_step<R, SH, D, W, 0, SPLIT>(a, sg, P, tbits);
 }
 
 // ---------------------------------------------------------------- LOW pass
-// Window = qubits 0..9.  Each warp streams tiles of 1024 consecutive
-// amplitudes (every WARPS-th tile of its block's range, so the block's warps
-// work on neighbouring tiles of one member and share its parameters in L1)
-// through one or two shared-memory buffers filled by bulk copies.  Register
-// exchanges happen in place in the current buffer, in a layout padded to 33
-// amplitudes per 32 (stage A: amplitude lane + 32 r at word lane + 33 r,
-// stage B: r + 32 lane at r + 33 lane), free of bank conflicts both ways with
-// compile-time offsets; stores are coalesced from the stage-A layout.
-template <int WARPS, int NBUF> struct LowShape {
-  static constexpr int BUF = 1024 + 32;                // a tile in the padded exchange layout
-  static constexpr int PER_WARP = NBUF * BUF;          // tile buffers
+// Window = qubits 0..M-1.  A tile is 2^M consecutive amplitudes, handled by a
+// group of G = 2^(M-10) warps (one warp for M = 10).  A block owns a
+// contiguous range of tiles and its groups take them in turn, so at any time
+// they work on neighbouring tiles of one member and share its parameters in
+// L1.  Tiles stream through one or two shared-memory buffers per group,
+// filled by one bulk copy each.  Register exchanges happen in place in the
+// current buffer, in the padded layout (pad_base); stores are coalesced from
+// stage A or C, whose lanes hold consecutive amplitudes.
+template <int WARPS, int NBUF, int M = kWin> struct LowShape {
+  static constexpr int G = 1 << (M - kWin);            // warps per tile
+  static constexpr int GROUPS = WARPS / G;
+  static constexpr int TILE = 1 << M;
+  static constexpr int BUF = TILE + TILE / 32;         // a tile in the padded exchange layout
+  static constexpr int PER_GROUP = NBUF * BUF;         // tile buffers
   static constexpr int THREADS = WARPS * 32;
 };
 
@@ -452,54 +547,56 @@ template <int WARPS, int NBUF> struct LowShape {
 __device__ __forceinline__ int exchange_count(const PassArgs& A, int stage, bool back_to_a) {
   int n = 0;
   for (int si = 0; si < A.nseg; ++si)
-    if (A.segs[si].stage != stage) { ++n; stage ^= 1; }
+    if (A.segs[si].stage != stage) { ++n; stage = A.segs[si].stage; }
   if (back_to_a && stage == 1) ++n;
   return n;
 }
 
-
-template <typename R, int WARPS, int NBUF, int PROG = 0>
+template <typename R, int WARPS, int NBUF, int PROG = 0, int M = kWin>
 __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict__ psi, const __grid_constant__ PassArgs A) {
   static_assert(NBUF == 1 || NBUF == 2, "one or two tile buffers");
+  static_assert(PROG == 0 || (M == kWin) == ((PROG & kProgWide) == 0), "program kind matches the width");
   using C = cplx<R>;
-  using S = LowShape<WARPS, NBUF>;
+  using S = LowShape<WARPS, NBUF, M>;
+  constexpr int G = S::G;
+  static_assert(WARPS % G == 0, "whole groups");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[WARPS][2];
+  __shared__ __align__(8) uint64_t bars[S::GROUPS][2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  C* wbase = reinterpret_cast<C*>(smem_raw) + (size_t)warp * S::PER_WARP;
+  const int grp = warp / G, wig = warp % G;             // group, warp within the group
+  const int t = lane + 32 * wig;                        // the thread's window bits 0..M-6 of its tile
+  const bool leader = lane == 0 && wig == 0;
+  C* wbase = reinterpret_cast<C*>(smem_raw) + (size_t)grp * S::PER_GROUP;
   const uint64_t nmask = (1ull << A.n) - 1;
   const R* params = static_cast<const R*>(A.params);
-  const uint32_t tile_bytes = 1024u * (uint32_t)sizeof(C);
-  // a block owns a contiguous range of tiles; its warps take them in turn, so
-  // at any time they work on neighbouring tiles of one member and share that
-  // member's parameters in L1
+  const uint32_t tile_bytes = (uint32_t)S::TILE * (uint32_t)sizeof(C);
   const uint64_t per = (A.tiles + gridDim.x - 1) / gridDim.x;
   const uint64_t bfirst = (uint64_t)blockIdx.x * per;
   const uint64_t last = bfirst + per < A.tiles ? bfirst + per : A.tiles;
-  const uint64_t first = bfirst + warp;
+  const uint64_t first = bfirst + grp;
 
-  if (lane == 0) {
-    mbar_init(&bars[warp][0], 1);
-    mbar_init(&bars[warp][1], 1);
+  if (leader) {
+    mbar_init(&bars[grp][0], 1);
+    mbar_init(&bars[grp][1], 1);
     mbar_fence_init();
   }
-  __syncwarp();
-  if (!A.synth && lane == 0 && first < last) {
-    mbar_expect_tx(&bars[warp][0], tile_bytes);
-    bulk_g2s(wbase, psi + (first << kWin), tile_bytes, &bars[warp][0]);
+  group_sync<G>(grp);
+  if (!A.synth && leader && first < last) {
+    mbar_expect_tx(&bars[grp][0], tile_bytes);
+    bulk_g2s(wbase, psi + (first << M), tile_bytes, &bars[grp][0]);
   }
   int in_flight = (!A.synth && first < last) ? 1 : 0;
   const int nx = NBUF == 1 ? exchange_count(A, 0, true) : 0;
   uint32_t it = 0;
-  for (uint64_t t = first; t < last; t += WARPS, ++it) {
+  for (uint64_t ti = first; ti < last; ti += S::GROUPS, ++it) {
     const int cur = NBUF == 2 ? (int)(it & 1) : 0;
     const uint32_t parity = NBUF == 2 ? ((it >> 1) & 1) : (it & 1);
     C* cbuf = wbase + cur * S::BUF;
-    const uint64_t tn = t + WARPS;                      // this warp's next tile
-    if (NBUF == 2 && !A.synth && lane == 0 && tn < last) {
+    const uint64_t tn = ti + S::GROUPS;                 // this group's next tile
+    if (NBUF == 2 && !A.synth && leader && tn < last) {
       fence_proxy_async();
-      mbar_expect_tx(&bars[warp][cur ^ 1], tile_bytes);
-      bulk_g2s(wbase + (cur ^ 1) * S::BUF, psi + (tn << kWin), tile_bytes, &bars[warp][cur ^ 1]);
+      mbar_expect_tx(&bars[grp][cur ^ 1], tile_bytes);
+      bulk_g2s(wbase + (cur ^ 1) * S::BUF, psi + (tn << M), tile_bytes, &bars[grp][cur ^ 1]);
       ++in_flight;
     }
     // single buffer: start the next tile's copy once this tile's last shared read is done
@@ -508,167 +605,202 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
       if constexpr (NBUF == 1) {
         if (--reads_left == 0 && !A.synth) {
           fence_proxy_async();
-          __syncwarp();
-          if (lane == 0 && tn < last) {
-            mbar_expect_tx(&bars[warp][0], tile_bytes);
-            bulk_g2s(wbase, psi + (tn << kWin), tile_bytes, &bars[warp][0]);
+          group_sync<G>(grp);
+          if (leader && tn < last) {
+            mbar_expect_tx(&bars[grp][0], tile_bytes);
+            bulk_g2s(wbase, psi + (tn << M), tile_bytes, &bars[grp][0]);
             ++in_flight;
           }
         }
       }
     };
-    const uint64_t base = t << kWin;
+    const uint64_t base = ti << M;
     const uint64_t member = base >> A.n;
     const uint64_t mloc = base & nmask;
     const R* P = params + member * (uint64_t)A.param_stride;
-    // this tile's out factors (read at the end of the tile): into L1 now
-    if (A.alpha_tab && lane < 2)
-      prefetch_l1(static_cast<const C*>(A.alpha_tab) + ((member << (A.n - kWin)) | (mloc >> kWin)) * 11 + lane * 8);
+    const uint64_t aidx = ((member << (A.n - M)) | (mloc >> M)) * (M + 1);   // this tile's out factors
+    // read at the end of the tile: into L1 now
+    if (A.alpha_tab && wig == 0 && lane < 2) prefetch_l1(static_cast<const C*>(A.alpha_tab) + aidx + lane * 8);
     C a[kAmps];
     if (A.synth) {
-      // the one amplitude equal to 1: register (x >> 5) & 31 of lane x & 31
+      // the one amplitude equal to 1: register x >> (M-5) & 31 of thread x & (2^(M-5) - 1)
       const uint64_t x = A.basis ? A.basis[member] : A.basis0[0];
 #pragma unroll
       for (int r = 0; r < kAmps; ++r) a[r] = mk<R>(R(0), R(0));
-      if ((x & ~1023ull) == mloc && (int)(x & 31) == lane) {
-        const int hr = (int)((x >> 5) & 31);
+      if ((x & ~(uint64_t)(S::TILE - 1)) == mloc && (int)(x & ((1u << (M - 5)) - 1)) == t) {
+        const int hr = (int)((x >> (M - 5)) & 31);
 #pragma unroll
         for (int r = 0; r < kAmps; ++r)
           if (r == hr) a[r].x = R(1);
       }
     } else {
-      // the warp gives up together (a lane that saw the copy land follows
+      // the group gives up together (a thread that saw the copy land follows
       // one that did not), after its copies in flight have landed: the
       // block's shared memory must outlive them
-      if (__any_sync(0xffffffffu, !mbar_wait(&bars[warp][cur], parity, A.spin_limit))) {
+      if (group_any<G>(grp, !mbar_wait(&bars[grp][cur], parity, A.spin_limit))) {
         report_timeout(A.status);
-        if (lane == 0) {
-          mbar_wait(&bars[warp][cur], parity);
-          if (NBUF == 2 && in_flight > 1) mbar_wait(&bars[warp][cur ^ 1], ((it + 1) >> 1) & 1);
+        if (leader) {
+          mbar_wait(&bars[grp][cur], parity);
+          if (NBUF == 2 && in_flight > 1) mbar_wait(&bars[grp][cur ^ 1], ((it + 1) >> 1) & 1);
         }
-        __syncwarp();
+        group_sync<G>(grp);
         return;
       }
-      if (lane == 0) --in_flight;
+      if (leader) --in_flight;
+      {
+        const int tb = tile_base<M, 0>(t);
+        constexpr int ts = tile_step<M, 0>();
 #pragma unroll
-      for (int r = 0; r < kAmps; ++r) a[r] = cbuf[lane + 32 * r];
+        for (int r = 0; r < kAmps; ++r) a[r] = cbuf[tb + r * ts];
+      }
       if constexpr (NBUF == 1) { ++reads_left; release(); }   // counts the first read
     }
     int stage = 0;
-    // register exchange A -> B (to_b) or B -> A in place in the tile buffer
-    auto exchange = [&](bool to_b) {
-      __syncwarp();
-      if (to_b) {
+    // register exchange between two stages, in place in the tile buffer
+    auto exchange = [&](int from, int to) {
+      group_sync<G>(grp);
+      with_stage<M>(from, [&](auto F) {
+        constexpr int SF = decltype(F)::value;
+        const int pb = pad_base<M, SF>(t);
 #pragma unroll
-        for (int r = 0; r < kAmps; ++r) cbuf[lane + 33 * r] = a[r];
-        __syncwarp();
+        for (int r = 0; r < kAmps; ++r) cbuf[pb + r * pad_step<M, SF>()] = a[r];
+      });
+      group_sync<G>(grp);
+      with_stage<M>(to, [&](auto T) {
+        constexpr int ST = decltype(T)::value;
+        const int pb = pad_base<M, ST>(t);
 #pragma unroll
-        for (int r = 0; r < kAmps; ++r) a[r] = cbuf[r + 33 * lane];
-      } else {
-#pragma unroll
-        for (int r = 0; r < kAmps; ++r) cbuf[r + 33 * lane] = a[r];
-        __syncwarp();
-#pragma unroll
-        for (int r = 0; r < kAmps; ++r) a[r] = cbuf[lane + 33 * r];
-      }
+        for (int r = 0; r < kAmps; ++r) a[r] = cbuf[pb + r * pad_step<M, ST>()];
+      });
     };
-    if constexpr (PROG != 0) {
-      run_layer<R, true, PROG & 31>(a, A.segs[0], P, lane);
-      exchange(true);
+    if constexpr (PROG != 0 && M == kWin) {
+      run_layer<R, M - kRegBits, PROG & 31>(a, A.segs[0], P, t);
+      exchange(0, 1);
       stage = 1;
       release();
-      run_layer<R, false, (PROG >> 5) & 31>(a, A.segs[1], P, 0);
+      run_layer<R, 0, (PROG >> 5) & 31>(a, A.segs[1], P, 0);
+    } else if constexpr (PROG != 0) {
+      // segments A (when the program has gates there), C, B
+      int si = 0;
+      if constexpr (prog_field(PROG, 0) | prog_field(PROG, 1))
+        run_layer<R, M - kRegBits, prog_field(PROG, 1), prog_field(PROG, 0), true>(a, A.segs[si++], P, t);
+      exchange(0, 2);
+      release();
+      run_layer<R, 5, prog_field(PROG, 3), prog_field(PROG, 2), true>(a, A.segs[si++], P, lane);
+      exchange(2, 1);
+      stage = 1;
+      release();
+      run_layer<R, 0, prog_field(PROG, 5), prog_field(PROG, 4), true>(a, A.segs[si], P, 0);
     }
     for (int si = 0; si < (PROG != 0 ? 0 : A.nseg); ++si) {
       const Seg& sg = A.segs[si];
       if (sg.stage != stage) {
-        exchange(stage == 0);
-        stage ^= 1;
+        exchange(stage, sg.stage);
+        stage = sg.stage;
         release();
       }
-      if (stage == 0) run_seg<R, true>(a, sg, P, lane, A.stable != 0);
-      else run_seg<R, false>(a, sg, P, 0, A.stable != 0);
-      for (int f = 0; f < sg.nflip; ++f) {
-        const Flip fl = A.flips[sg.flip0 + f];
-        const uint64_t w = fl.per_member ? A.marked[member] : fl.index;
-        const uint64_t fixed = mloc | (stage == 0 ? (uint64_t)lane : ((uint64_t)lane << 5));
-        const uint64_t regmask = stage == 0 ? (31ull << 5) : 31ull;
-        flip_reg<R>(a, (w & ~regmask) == fixed, stage == 0 ? (int)((w >> 5) & 31) : (int)(w & 31));
-      }
+      with_stage<M>(stage, [&](auto SC) {
+        constexpr int SS = decltype(SC)::value;
+        constexpr int SH = stage_base(M, SS);
+        run_seg<R, SH, (M > kWin)>(a, sg, P, SS == 0 ? t : (SS == 2 ? lane : 0), A.stable != 0);
+        const uint64_t fixed = mloc | (uint64_t)tile_base<M, SS>(t);
+        constexpr uint64_t regmask = 31ull << SH;
+        for (int f = 0; f < sg.nflip; ++f) {
+          const Flip fl = A.flips[sg.flip0 + f];
+          const uint64_t w = fl.per_member ? A.marked[member] : fl.index;
+          flip_reg<R>(a, (w & ~regmask) == fixed, (int)((w >> SH) & 31));
+        }
+      });
     }
+    // out factors or deferred diagonals: entry B + r for register r, and the
+    // product of the entries of the thread's set window bits times entry M
     if (A.alpha_tab) {
-      const C* al_g = static_cast<const C*>(A.alpha_tab) + ((member << (A.n - kWin)) | (mloc >> kWin)) * 11;
-      C al[kRegBits];
-      C c = ld_c(reinterpret_cast<const R*>(al_g + 10));
+      const R* al_g = reinterpret_cast<const R*>(static_cast<const C*>(A.alpha_tab) + aidx);
+      with_stage<M>(stage, [&](auto SC) {
+        constexpr int SS = decltype(SC)::value;
+        constexpr int B = stage_base(M, SS);
+        C al[kRegBits];
+        C c = ld_c(al_g + 2 * M);
 #pragma unroll
-      for (int r = 0; r < kRegBits; ++r) {
-        al[r] = ld_c(reinterpret_cast<const R*>(al_g + (stage == 0 ? r + 5 : r)));
-        if ((lane >> r) & 1) c = pmul<R>(ld_c(reinterpret_cast<const R*>(al_g + (stage == 0 ? r : r + 5))), c);
-      }
-      apply_reg_product<R>(a, c, al);
+        for (int r = 0; r < kRegBits; ++r) al[r] = ld_c(al_g + 2 * (B + r));
+#pragma unroll
+        for (int k = 0; k < M - kRegBits; ++k)
+          if ((t >> k) & 1) c = pmul<R>(ld_c(al_g + 2 * thread_bit<M, SS>(k)), c);
+        apply_reg_product<R>(a, c, al);
+      });
     } else if (A.diag_off >= 0) {
       const R* dg = P + A.diag_off;
-      R t5[kRegBits];
-      R c = __ldg(dg + 10);
+      with_stage<M>(stage, [&](auto SC) {
+        constexpr int SS = decltype(SC)::value;
+        constexpr int B = stage_base(M, SS);
+        R t5[kRegBits];
+        R c = __ldg(dg + M);
 #pragma unroll
-      for (int r = 0; r < kRegBits; ++r) {
-        t5[r] = __ldg(dg + (stage == 0 ? r + 5 : r));
-        if ((lane >> r) & 1) c *= __ldg(dg + (stage == 0 ? r : r + 5));
-      }
-      apply_real_product<R>(a, c, t5);
+        for (int r = 0; r < kRegBits; ++r) t5[r] = __ldg(dg + B + r);
+#pragma unroll
+        for (int k = 0; k < M - kRegBits; ++k)
+          if ((t >> k) & 1) c *= __ldg(dg + thread_bit<M, SS>(k));
+        apply_real_product<R>(a, c, t5);
+      });
     }
     if (stage == 1) {
-      exchange(false);
+      exchange(1, 0);
+      stage = 0;
       release();
     }
-    if (A.fid) {
-      const C* ref = static_cast<const C*>(A.ref) + mloc;
-      C acc = mk<R>(R(0), R(0));
+    // stage A or C: lanes hold consecutive amplitudes
+    with_stage<M>(stage, [&](auto SC) {
+      constexpr int SS = decltype(SC)::value;
+      if constexpr (SS != 1) {
+        const int tb = tile_base<M, SS>(t);
+        constexpr int ts = tile_step<M, SS>();
+        if (A.fid) {
+          const C* ref = static_cast<const C*>(A.ref) + mloc + tb;
+          C acc = mk<R>(R(0), R(0));
 #pragma unroll
-      for (int r = 0; r < kAmps; ++r) acc = pdot<R>(acc, __ldcg(ref + lane + 32 * r), a[r]);
-      const double sre = warp_sum_d((double)acc.x), sim = warp_sum_d((double)acc.y);
-      if (lane == 0) {
-        const uint64_t slot = member * (1ull << A.tile_shift) + (mloc >> kWin);
-        A.fid_partials[2 * slot] = sre;
-        A.fid_partials[2 * slot + 1] = sim;
+          for (int r = 0; r < kAmps; ++r) acc = pdot<R>(acc, __ldcg(ref + r * ts), a[r]);
+          const double sre = warp_sum_d((double)acc.x), sim = warp_sum_d((double)acc.y);
+          if (lane == 0) {
+            const uint64_t slot = (member * (1ull << A.tile_shift) + (mloc >> M)) * G + wig;
+            A.fid_partials[2 * slot] = sre;
+            A.fid_partials[2 * slot + 1] = sim;
+          }
+        }
+        C* out = psi + base + tb;
+#pragma unroll
+        for (int r = 0; r < kAmps; ++r) out[r * ts] = a[r];
       }
-    }
-    C* out = psi + base + lane;
-#pragma unroll
-    for (int r = 0; r < kAmps; ++r) out[32 * r] = a[r];
-    __syncwarp();
+    });
+    group_sync<G>(grp);
   }
 }
 
 // ---------------------------------------------------------------- HIGH pass
-// Window = the 10 highest qubits (all >= COLB).  A block streams a contiguous
-// range of tiles of 2^COLB consecutive "columns" (qubits 0..COLB-1) x 1024
-// window rows, each loaded as four 256-row boxes of a 2D tensor map
-// [members * 1024 rows][2^(n-10) columns].  The window bits are contiguous,
-// so register r of stage A sits at offset r << win[5] and of stage B at
-// r << win[0].  The copy lands in the plain layout [x][col]; the in-place
-// exchange uses one padding row per 32 rows (conflict-free both ways).
-template <int COLB> struct HighShape {
+// Window = the M qubits c..c+M-1, c >= COLB.  A block streams a contiguous
+// range of tiles of 2^COLB consecutive "columns" (qubits 0..COLB-1) x 2^M
+// window rows, each loaded as boxes of 256 rows of a 2D tensor map
+// [members * 2^(n-c) rows][2^c columns].  A thread's lanes hold the columns
+// and 5 - COLB of its M - 5 window bits, its warp the rest.  The window bits
+// are contiguous, so register r of stage S sits at offset
+// r << (c + stage_base(S)).  The copy lands in the plain layout [x][col]; the
+// in-place exchanges use the padded layout of the rows (pad_base).
+template <int COLB, int M = kWin> struct HighShape {
   static constexpr int COLS = 1 << COLB;
   static constexpr int LW = kRegBits - COLB;            // lane bits that are window bits
-  static constexpr int WARPS = 1 << COLB;               // warp bits = COLB window bits
+  static constexpr int WARPS = 1 << (COLB + M - kWin);  // warp bits = the thread's other window bits
   static constexpr int THREADS = WARPS * 32;
-  static constexpr int TILE = COLS * 1024;              // amplitudes of a tile
-  static constexpr int BUF = COLS * (1024 + 32);        // a tile in the padded exchange layout
+  static constexpr int TILE = COLS << M;                // amplitudes of a tile
+  static constexpr int BUF = COLS * ((1 << M) + (1 << (M - 5)));   // a tile in the padded exchange layout
+  static constexpr int BOXES = (1 << M) / 256;          // tensor-map boxes of 256 rows
 };
 
-// exchange layout: row x at (x + x / 32) * COLS (one padding row per 32)
-template <int COLB>
-__device__ __forceinline__ int high_idx(int x, int col) {
-  return (x + (x >> 5)) * (1 << COLB) + col;
-}
-
-template <typename R, int COLB, int NBUF, bool WIDE = false, int PROG = 0>
-__global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / HighShape<COLB>::WARPS : 1)
+template <typename R, int COLB, int NBUF, bool WIDE = false, int PROG = 0, int M = kWin>
+__global__ void __launch_bounds__(HighShape<COLB, M>::THREADS, NBUF == 1 ? 16 / HighShape<COLB, M>::WARPS : 1)
     k_pass_high(cplx<R>* __restrict__ psi, const __grid_constant__ CUtensorMap tmap, const __grid_constant__ PassArgs A) {
   static_assert(NBUF == 1 || NBUF == 2, "one or two tile buffers");
+  static_assert(PROG == 0 || (M == kWin) == ((PROG & kProgWide) == 0), "program kind matches the width");
   using C = cplx<R>;
-  using S = HighShape<COLB>;
+  using S = HighShape<COLB, M>;
   // member-local amplitude offsets: 32-bit up to 32 qubits, 64-bit (WIDE) above
   using Off = typename std::conditional<WIDE, uint64_t, uint32_t>::type;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -677,22 +809,17 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
   C* smbase = reinterpret_cast<C*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int col = lane & (S::COLS - 1);
-  const int lh = lane >> COLB;
+  const int tw = (lane >> COLB) | (warp << S::LW);      // the thread's M - 5 window bits
   const R* params = static_cast<const R*>(A.params);
   const uint32_t tile_bytes = (uint32_t)(S::TILE * sizeof(C));
   const int elem_cols = (int)(sizeof(C) / 8);          // 8-byte tensor elements per amplitude
-
-  const int xa = lh | (warp << S::LW);                  // stage A: local bits 0..4
-  const int xb = (lh << 5) | (warp << (5 + S::LW));     // stage B: local bits 5..9
-  const Off offa = (Off)xa << A.win[0];                 // member-local offsets of the thread bits
-  const Off offb = (Off)(xb >> 5) << A.win[5];
-  const int sha = A.win[5], shb = A.win[0];             // register r: r << sha (A), r << shb (B)
+  const int c0 = A.win[0];
   const uint64_t per = (A.tiles + gridDim.x - 1) / gridDim.x;
   const uint64_t first = (uint64_t)blockIdx.x * per;
   const uint64_t last = first + per < A.tiles ? first + per : A.tiles;
   // a tile index within a member splits into the column block among the
   // bits below the window (cshift bits) and the value of the bits above it
-  const int cshift = A.win[0] - COLB;
+  const int cshift = c0 - COLB;
   const uint64_t cmask = (1ull << cshift) - 1;
 
   if (threadIdx.x == 0) {
@@ -706,10 +833,10 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
     const uint64_t tl = t & ((1ull << A.tile_shift) - 1);
     mbar_expect_tx(&bars[which], tile_bytes);
     const int x = (int)((tl & cmask) * S::COLS) * elem_cols;
-    const uint64_t row0 = ((member << (A.tile_shift - cshift)) | (tl >> cshift)) * 1024;
+    const uint64_t row0 = ((member << (A.tile_shift - cshift)) | (tl >> cshift)) << M;
     C* dst = smbase + which * S::BUF;
 #pragma unroll
-    for (int b = 0; b < 4; ++b)
+    for (int b = 0; b < S::BOXES; ++b)
       tma_g2s_2d(dst + b * 256 * S::COLS, &tmap, x, (int)(row0 + b * 256), &bars[which]);
   };
   if (!A.synth && threadIdx.x == 0 && first < last) issue(first, 0);
@@ -743,15 +870,15 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
     // member-local offset of the tile (bits outside the window and the
     // columns), and the same bits packed below each other (the out-factor
     // table's index: bits below the window, then the bits above it)
-    const Off tbits = (Off)(((tl >> cshift) << (A.win[0] + kWin)) | ((tl & cmask) << COLB));
-    const Off obits = (Off)(((tl >> cshift) << A.win[0]) | ((tl & cmask) << COLB));
+    const Off tbits = (Off)(((tl >> cshift) << (c0 + M)) | ((tl & cmask) << COLB));
+    const Off obits = (Off)(((tl >> cshift) << c0) | ((tl & cmask) << COLB));
     const R* P = params + member * (uint64_t)A.param_stride;
     C* sm = smbase + cur * S::BUF;
     // this tile's out factors (read at the end of the tile): into L1 now
     if (A.alpha_tab) {
       const char* at = reinterpret_cast<const char*>(static_cast<const C*>(A.alpha_tab) +
-                                                     ((member << (A.n - kWin)) | obits) * 11);
-      constexpr int kLines = (int)((S::COLS * 11 * sizeof(C)) / 128) + 2;
+                                                     ((member << (A.n - M)) | obits) * (M + 1));
+      constexpr int kLines = (int)((S::COLS * (M + 1) * sizeof(C)) / 128) + 2;
       if ((int)threadIdx.x < kLines) prefetch_l1(at + threadIdx.x * 128);
     }
     C a[kAmps];
@@ -760,16 +887,19 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
       // the one amplitude equal to 1: register (x >> sh) & 31 of the thread
       // whose other bits match (one thread of the member's whole state)
       const uint64_t x = A.basis ? A.basis[member] : A.basis0[0];
-      const Off fixed = tbits | (Off)col | (stage == 0 ? offa : offb);
-      const int sh = stage == 0 ? sha : shb;
 #pragma unroll
       for (int r = 0; r < kAmps; ++r) a[r] = mk<R>(R(0), R(0));
-      if ((x & ~(31ull << sh)) == (uint64_t)fixed) {
-        const int hr = (int)((x >> sh) & 31);
+      with_stage<M>(stage, [&](auto SC) {
+        constexpr int SS = decltype(SC)::value;
+        const int sh = c0 + stage_base(M, SS);
+        const Off fixed = tbits | (Off)col | ((Off)tile_base<M, SS>(tw) << c0);
+        if ((x & ~(31ull << sh)) == (uint64_t)fixed) {
+          const int hr = (int)((x >> sh) & 31);
 #pragma unroll
-        for (int r = 0; r < kAmps; ++r)
-          if (r == hr) a[r].x = R(1);
-      }
+          for (int r = 0; r < kAmps; ++r)
+            if (r == hr) a[r].x = R(1);
+        }
+      });
     } else {
       // the block gives up together, after its copies in flight have landed
       if (__syncthreads_or(!mbar_wait(&bars[cur], parity, A.spin_limit))) {
@@ -782,111 +912,170 @@ __global__ void __launch_bounds__(HighShape<COLB>::THREADS, NBUF == 1 ? 16 / Hig
       }
       if (threadIdx.x == 0) --in_flight;
       // the copy lands in the plain layout [x][col]
-      if (stage == 0) {
+      with_stage<M>(stage, [&](auto SC) {
+        constexpr int SS = decltype(SC)::value;
+        const int tb = tile_base<M, SS>(tw) * S::COLS + col;
+        constexpr int ts = tile_step<M, SS>() * S::COLS;
 #pragma unroll
-        for (int r = 0; r < kAmps; ++r) a[r] = sm[(xa | (r << 5)) * S::COLS + col];
-      } else {
-#pragma unroll
-        for (int r = 0; r < kAmps; ++r) a[r] = sm[(r | xb) * S::COLS + col];
-      }
+        for (int r = 0; r < kAmps; ++r) a[r] = sm[tb + r * ts];
+      });
       if constexpr (NBUF == 1) { ++reads_left; release(); }   // counts the first read
     }
-    // register exchange A -> B (to_b) or B -> A in place in the tile buffer
-    auto exchange = [&](bool to_b) {
+    // register exchange between two stages, in place in the tile buffer
+    auto exchange = [&](int from, int to) {
       __syncthreads();
-      if (to_b) {
+      with_stage<M>(from, [&](auto F) {
+        constexpr int SF = decltype(F)::value;
+        const int pb = pad_base<M, SF>(tw) * S::COLS + col;
 #pragma unroll
-        for (int r = 0; r < kAmps; ++r) sm[high_idx<COLB>(xa | (r << 5), col)] = a[r];
-        __syncthreads();
+        for (int r = 0; r < kAmps; ++r) sm[pb + r * (pad_step<M, SF>() * S::COLS)] = a[r];
+      });
+      __syncthreads();
+      with_stage<M>(to, [&](auto T) {
+        constexpr int ST = decltype(T)::value;
+        const int pb = pad_base<M, ST>(tw) * S::COLS + col;
 #pragma unroll
-        for (int r = 0; r < kAmps; ++r) a[r] = sm[high_idx<COLB>(r | xb, col)];
-      } else {
-#pragma unroll
-        for (int r = 0; r < kAmps; ++r) sm[high_idx<COLB>(r | xb, col)] = a[r];
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < kAmps; ++r) a[r] = sm[high_idx<COLB>(xa | (r << 5), col)];
-      }
+        for (int r = 0; r < kAmps; ++r) a[r] = sm[pb + r * (pad_step<M, ST>() * S::COLS)];
+      });
     };
-    if constexpr (PROG != 0) {              // the planner guarantees start stage A
-      run_layer<R, true, PROG & 31>(a, A.segs[0], P, xa);
-      exchange(true);
+    if constexpr (PROG != 0 && M == kWin) {   // the planner guarantees start stage A
+      run_layer<R, M - kRegBits, PROG & 31>(a, A.segs[0], P, tw);
+      exchange(0, 1);
       stage = 1;
       release();
-      run_layer<R, false, (PROG >> 5) & 31>(a, A.segs[1], P, 0);
+      run_layer<R, 0, (PROG >> 5) & 31>(a, A.segs[1], P, 0);
+    } else if constexpr (PROG != 0) {         // segments A, C, B; start stage A
+      run_layer<R, M - kRegBits, prog_field(PROG, 1), prog_field(PROG, 0), true>(a, A.segs[0], P, tw);
+      exchange(0, 2);
+      release();
+      run_layer<R, 5, prog_field(PROG, 3), prog_field(PROG, 2), true>(a, A.segs[1], P, tw & 31);
+      exchange(2, 1);
+      stage = 1;
+      release();
+      run_layer<R, 0, prog_field(PROG, 5), prog_field(PROG, 4), true>(a, A.segs[2], P, 0);
     }
     for (int si = 0; si < (PROG != 0 ? 0 : A.nseg); ++si) {
       const Seg& sg = A.segs[si];
       if (sg.stage != stage) {
-        exchange(stage == 0);
-        stage ^= 1;
+        exchange(stage, sg.stage);
+        stage = sg.stage;
         release();
       }
-      if (stage == 0) run_seg<R, true>(a, sg, P, xa, A.stable != 0);
-      else run_seg<R, false>(a, sg, P, 0, A.stable != 0);
-      for (int f = 0; f < sg.nflip; ++f) {
-        const Flip fl = A.flips[sg.flip0 + f];
-        const uint64_t w = fl.per_member ? A.marked[member] : fl.index;
-        const int sh = stage == 0 ? sha : shb;
+      with_stage<M>(stage, [&](auto SC) {
+        constexpr int SS = decltype(SC)::value;
+        constexpr int SH = stage_base(M, SS);
+        run_seg<R, SH, (M > kWin)>(a, sg, P, SS == 0 ? tw : (SS == 2 ? (tw & 31) : 0), A.stable != 0);
+        const int sh = c0 + SH;
         const uint64_t regmask = 31ull << sh;
-        const uint64_t fixed = tbits | (Off)col | (stage == 0 ? offa : offb);
-        flip_reg<R>(a, (w & ~regmask) == fixed, (int)((w >> sh) & 31));
-      }
+        const Off fixed = tbits | (Off)col | ((Off)tile_base<M, SS>(tw) << c0);
+        for (int f = 0; f < sg.nflip; ++f) {
+          const Flip fl = A.flips[sg.flip0 + f];
+          const uint64_t w = fl.per_member ? A.marked[member] : fl.index;
+          flip_reg<R>(a, (w & ~regmask) == fixed, (int)((w >> sh) & 31));
+        }
+      });
     }
+    // out factors or deferred diagonals (as in the low pass)
     if (A.alpha_tab) {
       const R* al_c = reinterpret_cast<const R*>(static_cast<const C*>(A.alpha_tab) +
-                                                 ((member << (A.n - kWin)) | obits | (Off)col) * 11);
-      C c = ld_c(al_c + 2 * 10);
-      C al[kRegBits];
-      const int xt = stage == 0 ? xa : xb;
+                                                 ((member << (A.n - M)) | obits | (Off)col) * (M + 1));
+      with_stage<M>(stage, [&](auto SC) {
+        constexpr int SS = decltype(SC)::value;
+        constexpr int B = stage_base(M, SS);
+        C c = ld_c(al_c + 2 * M);
+        C al[kRegBits];
 #pragma unroll
-      for (int r = 0; r < kRegBits; ++r) {
-        al[r] = ld_c(al_c + 2 * (stage == 0 ? r + 5 : r));
-        const int lt = stage == 0 ? r : r + 5;
-        if ((xt >> lt) & 1) c = pmul<R>(ld_c(al_c + 2 * lt), c);
-      }
-      apply_reg_product<R>(a, c, al);
+        for (int r = 0; r < kRegBits; ++r) al[r] = ld_c(al_c + 2 * (B + r));
+#pragma unroll
+        for (int k = 0; k < M - kRegBits; ++k)
+          if ((tw >> k) & 1) c = pmul<R>(ld_c(al_c + 2 * thread_bit<M, SS>(k)), c);
+        apply_reg_product<R>(a, c, al);
+      });
     } else if (A.diag_off >= 0) {
       const R* dg = P + A.diag_off;
-      const int xt = stage == 0 ? xa : xb;
-      R t5[kRegBits];
-      R c = __ldg(dg + 10);
+      with_stage<M>(stage, [&](auto SC) {
+        constexpr int SS = decltype(SC)::value;
+        constexpr int B = stage_base(M, SS);
+        R t5[kRegBits];
+        R c = __ldg(dg + M);
 #pragma unroll
-      for (int r = 0; r < kRegBits; ++r) {
-        t5[r] = __ldg(dg + (stage == 0 ? r + 5 : r));
-        const int lt = stage == 0 ? r : r + 5;
-        if ((xt >> lt) & 1) c *= __ldg(dg + lt);
-      }
-      apply_real_product<R>(a, c, t5);
+        for (int r = 0; r < kRegBits; ++r) t5[r] = __ldg(dg + B + r);
+#pragma unroll
+        for (int k = 0; k < M - kRegBits; ++k)
+          if ((tw >> k) & 1) c *= __ldg(dg + thread_bit<M, SS>(k));
+        apply_real_product<R>(a, c, t5);
+      });
     }
-    const Off fixed = tbits + (Off)col + (stage == 0 ? offa : offb);
-    const int sh = stage == 0 ? sha : shb;
-    if (A.fid) {
-      const C* ref = static_cast<const C*>(A.ref) + fixed;
-      C acc = mk<R>(R(0), R(0));
+    with_stage<M>(stage, [&](auto SC) {
+      constexpr int SS = decltype(SC)::value;
+      const int sh = c0 + stage_base(M, SS);
+      const Off fixed = tbits + (Off)col + ((Off)tile_base<M, SS>(tw) << c0);
+      if (A.fid) {
+        const C* ref = static_cast<const C*>(A.ref) + fixed;
+        C acc = mk<R>(R(0), R(0));
 #pragma unroll
-      for (int r = 0; r < kAmps; ++r) acc = pdot<R>(acc, __ldcg(ref + ((Off)r << sh)), a[r]);
-      const double sre = warp_sum_d((double)acc.x), sim = warp_sum_d((double)acc.y);
-      if (lane == 0) { fid_red[0][warp] = sre; fid_red[1][warp] = sim; }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double tr = 0.0, ti = 0.0;
-        for (int w = 0; w < S::WARPS; ++w) { tr += fid_red[0][w]; ti += fid_red[1][w]; }
-        const uint64_t slot = member * (1ull << A.tile_shift) + tl;
-        A.fid_partials[2 * slot] = tr;
-        A.fid_partials[2 * slot + 1] = ti;
+        for (int r = 0; r < kAmps; ++r) acc = pdot<R>(acc, __ldcg(ref + ((Off)r << sh)), a[r]);
+        const double sre = warp_sum_d((double)acc.x), sim = warp_sum_d((double)acc.y);
+        if (lane == 0) { fid_red[0][warp] = sre; fid_red[1][warp] = sim; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double tr = 0.0, tim = 0.0;
+          for (int w = 0; w < S::WARPS; ++w) { tr += fid_red[0][w]; tim += fid_red[1][w]; }
+          const uint64_t slot = member * (1ull << A.tile_shift) + tl;
+          A.fid_partials[2 * slot] = tr;
+          A.fid_partials[2 * slot + 1] = tim;
+        }
       }
-    }
-    // register r goes to fixed + r 2^sh: a running 32-bit offset (64-bit for
-    // WIDE) from the member's base instead of a shift and a 64-bit add each
-    C* out = psi + (member << A.n);
-    Off o = fixed;
-    const Off step = (Off)1 << sh;
+      // register r goes to fixed + r 2^sh: a running 32-bit offset (64-bit for
+      // WIDE) from the member's base instead of a shift and a 64-bit add each
+      C* out = psi + (member << A.n);
+      Off o = fixed;
+      const Off step = (Off)1 << sh;
 #pragma unroll
-    for (int r = 0; r < kAmps; ++r, o += step) out[o] = a[r];
+      for (int r = 0; r < kAmps; ++r, o += step) out[o] = a[r];
+    });
     __syncthreads();
   }
 }
+
+// ---------------------------------------------------------------- host side
+template <typename R, int W, int NB, int M = kWin>
+size_t low_smem() {
+  using S = LowShape<W, NB, M>;
+  return (size_t)S::GROUPS * S::PER_GROUP * sizeof(cplx<R>);
+}
+template <typename R, int CB, int NB, int M = kWin>
+size_t high_smem() {
+  return NB * (size_t)HighShape<CB, M>::BUF * sizeof(cplx<R>);
+}
+
+// Dynamic shared memory of a pass kernel, and a carveout preference just
+// large enough for `blocks` resident blocks per SM, so the rest of the
+// unified L1 caches the members' parameters and phase tables.
+template <typename K>
+cudaError_t set_pass_attrs(K kernel, size_t dyn, int blocks) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  if (e != cudaSuccess) return e;
+  constexpr size_t kSmemPerSM = 228 * 1024, kReservedPerBlock = 1024, kStatic = 1024;
+  const size_t need = (size_t)blocks * (dyn + kStatic + kReservedPerBlock);
+  const int pct = (int)std::min<size_t>(100, (need * 100 + kSmemPerSM - 1) / kSmemPerSM);
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+}
+
+// Windows of 11 and 12 qubits (complex64, pass_wide.cu).  Columns of a high
+// tile: 8 for m = 11, 4 for m = 12 (tiles of 128 KB whose rows fill whole
+// 32-byte sectors).
+constexpr int wide_colb(int m) { return 14 - m; }
+// The compiled program of a pass that applies a real gate, then the phase
+// table over the bits below it, on every bit of the window, top down (the
+// noisy QFT on m qubits of a larger state), or 0 for other widths.
+constexpr int wide_full_prog(int m) {
+  return m == 11 ? prog_wide(0x1f, 0x1f, 0x01, 0x01, 0x1f, 0x1e)
+                 : (m == 12 ? prog_wide(0x1f, 0x1f, 0x03, 0x03, 0x1f, 0x1e) : 0);
+}
+cudaError_t launch_pass_wide(cplx<float>* psi, const CUtensorMap& tmap, const PassArgs& A, bool high, int m, int prog,
+                             int sms, cudaStream_t s);
+cudaError_t set_wide_attrs();
 
 }  // namespace fused
 }  // namespace qs

@@ -1,12 +1,15 @@
 // Circuit plans: fused window passes over the state, replayed as CUDA graphs.
 //
 // A pass applies every gate of a run whose dense targets lie in a window of
-// 10 qubits with one read and one write of the state (the amplitude update of
+// m qubits (m = 10 by default; 11 or 12 for complex64 plans, chosen by
+// qs_plan_set_window or the autotuner) with one read and one write of the
+// state (the amplitude update of
 // Sec. 2 done on a tile in registers and shared memory instead of once per
 // gate in HBM).  Each thread holds 32 amplitudes of a tile that differ in 5
 // "register" bits of the window; a one-qubit gate on a register bit is a
 // butterfly over the thread's registers; an exchange through shared memory
-// swaps which 5 window bits are in registers.
+// changes which 5 window bits are in registers (two register stages for
+// m = 10, three above).
 //
 // Diagonal two-qubit gates with the form diag(1, 1, 1, x) -- the controlled
 // phase shift of Eq. 2 and its Monte Carlo version theta -> theta + e xi
@@ -20,10 +23,10 @@
 //     planner forbids those and the pass applies all of them at its end.
 // Grover's oracle and diffusion are single-amplitude flips.
 //
-// Geometry LOW: window = qubits 0..9, one warp per 1024 consecutive
-// amplitudes.  Geometry HIGH: the 10 qubits c..c+9, c >= COLB (the top ten,
-// or a window lower down for states above 20 qubits); a block handles 2^COLB
-// consecutive "columns" (qubits 0..COLB-1) of 1024 window combinations, so
+// Geometry LOW: window = qubits 0..m-1, 2^(m-10) warps per 2^m consecutive
+// amplitudes.  Geometry HIGH: the m qubits c..c+m-1, c >= COLB (the top m,
+// or a window lower down for larger states); a block handles 2^COLB
+// consecutive "columns" (qubits 0..COLB-1) of 2^m window combinations, so
 // every global access moves 2^COLB consecutive elements.
 //
 // Noise of a run: a precompute kernel draws xi for every noisy gate of a pass
@@ -76,12 +79,13 @@ struct Producer {
   int kind;
   int gate;               // DENSE / OUT: gate index
   int j;                  // DWIN: attach bit, table of 2^j entries; DENSE: window bit
+  int sh;                 // DWIN: 0, or the table split into 2^sh + 2^(j-sh) entries (bits below sh, then the rest)
   int real;               // DENSE: real matrix, stored as its shears (r0, r0, s1, s1)
   int contrib_start, contrib_count;
   uint32_t off;
 };
 
-struct OutStarts { int v[12]; };   // out terms of attach a: [v[a], v[a + 1])
+struct OutStarts { int v[kMaxWin + 2]; };   // out terms of attach a: [v[a], v[a + 1]); a = m: none
 
 struct Contrib {          // DWIN contribution: partner local bit m, gate
   int m;
@@ -173,8 +177,10 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
                                                     const Producer* __restrict__ prods, int num_prods,
                                                     const Contrib* __restrict__ contribs, int num_contribs,
                                                     int num_dwin, int num_dense, int diag_off, NoiseSrc src,
-                                                    const RunParams* rp, int stable) {
-  extern __shared__ double2 pre_sm[];                   // [num_contribs] factors, then [num_dwin][10]
+                                                    const RunParams* rp, int stable, int m) {
+  // [num_contribs] factors, then [num_dwin][kMaxWin] partner factors, a
+  // table of 2^(m-1) entries and the dense matrices
+  extern __shared__ double2 pre_sm[];
   const int b = blockIdx.x;
   double e;
   uint64_t seed, traj;
@@ -183,7 +189,7 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
   // noisy 2x2 matrices of the dense gates, all threads in parallel, into
   // shared memory (FP64, [slot][4] complex after the tables' scratch; a real
   // gate as (M00, M01), (M10, M11)), factored by the chain below.
-  double2* dmat = pre_sm + num_contribs + (size_t)num_dwin * kWin + (1u << (kWin - 1));
+  double2* dmat = pre_sm + num_contribs + (size_t)num_dwin * kMaxWin + (1u << (m - 1));
   for (int i = threadIdx.x; i < num_prods; i += blockDim.x) {
     const Producer p = prods[i];
     if (p.kind != PD_DENSE) continue;
@@ -199,9 +205,9 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
     }
   }
   __syncthreads();
-  // the last kWin threads factor the dense gates while the others compute
-  // the phase factors
-  constexpr int kPhaseThreads = 128 - kWin;
+  // the last kMaxWin threads factor the dense gates (one per window bit)
+  // while the others compute the phase factors
+  constexpr int kPhaseThreads = 128 - kMaxWin;
   // contributions of the phase tables, and out factors
   if (threadIdx.x < kPhaseThreads) {
     for (int i = threadIdx.x; i < num_contribs; i += kPhaseThreads) {
@@ -231,8 +237,8 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
   // always take the first form (the host checks that the pivot stays large).
   // A complex gate absorbs the carried diagonal.  What is left at the end
   // goes to the diag block.
-  __shared__ double pivot_a[kWin];
-  if (threadIdx.x >= kPhaseThreads) {
+  __shared__ double pivot_a[kMaxWin];
+  if (threadIdx.x >= kPhaseThreads && (int)threadIdx.x - kPhaseThreads < m) {
     const int J = threadIdx.x - kPhaseThreads;
     double pa = 1.0, rho = 1.0;
     for (int i = 0; i < num_prods; ++i) {
@@ -285,69 +291,78 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
   __syncthreads();
   if (diag_off >= 0 && threadIdx.x == 0) {
     double sc = 1.0;
-    for (int J = 0; J < kWin; ++J) sc *= pivot_a[J];
-    out[diag_off + kWin] = (R)sc;
+    for (int J = 0; J < m; ++J) sc *= pivot_a[J];
+    out[diag_off + m] = (R)sc;
   }
-  // per-table partner factors f[m], m = 0..9
+  // per-table partner factors f[q], q = 0..m-1
   double2* fm = pre_sm + num_contribs;
   int w = 0;
   for (int i = 0; i < num_prods; ++i) {
     const Producer p = prods[i];
     if (p.kind != PD_DWIN) continue;
-    if (threadIdx.x < kWin) {
+    if ((int)threadIdx.x < m) {
       double2 acc = make_double2(1.0, 0.0);
       for (int c = p.contrib_start; c < p.contrib_start + p.contrib_count; ++c)
         if (contribs[c].m == (int)threadIdx.x) {
           const double2 f = pre_sm[c];
           acc = make_double2(acc.x * f.x - acc.y * f.y, acc.x * f.y + acc.y * f.x);
         }
-      fm[w * kWin + threadIdx.x] = acc;
+      fm[w * kMaxWin + threadIdx.x] = acc;
     }
     ++w;
   }
   __syncthreads();
-  // tables T[x] = prod_{m in x} f[m], by doubling in FP64 shared memory:
-  // T[x + 2^m] = T[x] f[m] for x < 2^m (one complex product per entry)
-  double2* tab = fm + (size_t)num_dwin * kWin;          // 2^9 entries
+  // tables T[x] = prod_{q in x} f[q], by doubling in FP64 shared memory:
+  // T[x + 2^q] = T[x] f[q] for x < 2^q (one complex product per entry)
+  double2* tab = fm + (size_t)num_dwin * kMaxWin;       // 2^(m-1) entries
   w = 0;
   for (int i = 0; i < num_prods; ++i) {
     const Producer p = prods[i];
     if (p.kind != PD_DWIN) continue;
-    if (threadIdx.x == 0) tab[0] = make_double2(1.0, 0.0);
-    __syncthreads();
-    for (int m = 0; m < p.j; ++m) {
-      const double2 f = fm[w * kWin + m];
-      for (int x = threadIdx.x; x < (1 << m); x += blockDim.x) {
-        const double2 t = tab[x];
-        tab[x + (1 << m)] = make_double2(t.x * f.x - t.y * f.y, t.x * f.y + t.y * f.x);
+    // one table over bits [0, j), or two: [0, sh) then [sh, j)
+    const int parts = p.sh > 0 ? 2 : 1;
+    uint32_t o = p.off;
+    for (int part = 0; part < parts; ++part) {
+      const int lo = part == 0 ? 0 : p.sh, hi = (parts == 1 || part == 1) ? p.j : p.sh;
+      if (threadIdx.x == 0) tab[0] = make_double2(1.0, 0.0);
+      __syncthreads();
+      for (int q = lo; q < hi; ++q) {
+        const double2 f = fm[w * kMaxWin + q];
+        const int half = 1 << (q - lo);
+        for (int x = threadIdx.x; x < half; x += blockDim.x) {
+          const double2 t = tab[x];
+          tab[x + half] = make_double2(t.x * f.x - t.y * f.y, t.x * f.y + t.y * f.x);
+        }
+        __syncthreads();
       }
+      for (int x = threadIdx.x; x < (1 << (hi - lo)); x += blockDim.x) {
+        out[o + 2 * x] = (R)tab[x].x;
+        out[o + 2 * x + 1] = (R)tab[x].y;
+      }
+      o += 2u << (hi - lo);
       __syncthreads();
     }
-    for (int x = threadIdx.x; x < (1 << p.j); x += blockDim.x) {
-      out[p.off + 2 * x] = (R)tab[x].x;
-      out[p.off + 2 * x + 1] = (R)tab[x].y;
-    }
-    __syncthreads();
     ++w;
   }
 }
 
 // Out factors of every tile of a pass: for member b and each value o of the
-// out-of-window bits (those below the window, then those above it), entry (o, a) = the product of the out terms attached to
-// window bit a (a = 10: attached to none) whose out-of-window bits are all set
-// in o, times the deferred real diagonal of bit a (the overall scale for
-// a = 10).  The pass kernels read the 11 entries of their tile directly.
+// out-of-window bits (those below the window, then those above it), entry
+// (o, a) = the product of the out terms attached to window bit a (a = m:
+// attached to none) whose out-of-window bits are all set in o, times the
+// deferred real diagonal of bit a (the overall scale for a = m).  The pass
+// kernels read the m + 1 entries of their tile directly.
 template <typename R>
 __global__ void __launch_bounds__(256) k_out_table(cplx<R>* __restrict__ tab, const R* __restrict__ params, int stride,
                                                    const OutTerm* __restrict__ outs, OutStarts starts, int diag_off,
-                                                   int obits, int wstart, uint32_t chunks) {
+                                                   int obits, int wstart, uint32_t chunks, int m) {
   // one member per block: its terms' masks and factors staged in shared memory
   extern __shared__ unsigned char ot_sm[];
-  const int nterms = starts.v[11];
+  const int nterms = starts.v[m + 1];
   uint64_t* masks = reinterpret_cast<uint64_t*>(ot_sm);
   cplx<R>* fac = reinterpret_cast<cplx<R>*>(masks + ((nterms + 1) & ~1));   // 16-byte aligned
   const uint64_t b = blockIdx.x / chunks;
-  const uint64_t per = (11ull << obits);
+  const uint64_t per = ((uint64_t)(m + 1) << obits);
   const R* P = params + b * (uint64_t)stride;
   for (int k = threadIdx.x; k < nterms; k += blockDim.x) {
     const OutTerm t = outs[k];
@@ -357,11 +372,11 @@ __global__ void __launch_bounds__(256) k_out_table(cplx<R>* __restrict__ tab, co
   __syncthreads();
   const uint64_t i = (uint64_t)(blockIdx.x % chunks) * blockDim.x + threadIdx.x;
   if (i >= per) return;
-  const uint64_t o = i / 11;
-  const int a = (int)(i % 11);
+  const uint64_t o = i / (uint64_t)(m + 1);
+  const int a = (int)(i % (uint64_t)(m + 1));
   // member-local out-of-window bits: o holds the bits below the window
   // (wstart of them) and above it the bits above the window
-  const uint64_t fixed = ((o >> wstart) << (wstart + kWin)) | (o & ((1ull << wstart) - 1));
+  const uint64_t fixed = ((o >> wstart) << (wstart + m)) | (o & ((1ull << wstart) - 1));
   R re = R(1), im = R(0);
   for (int k = starts.v[a]; k < starts.v[a + 1]; ++k) {
     if ((fixed & masks[k]) == masks[k]) {
@@ -428,11 +443,12 @@ struct PGate {
 struct PassPlan {
   bool high = false;
   int colb = 3;
-  int win[kWin];
+  int m = kWin;                   // window width
+  int win[kMaxWin];
   int start_stage = 0;
   std::vector<FOp> ops;
   std::vector<OutTerm> outs;      // sorted by attach
-  int out_start[12];
+  int out_start[kMaxWin + 2];     // terms of attach a: [out_start[a], out_start[a + 1]); a = m: none
   std::vector<Producer> prods;
   std::vector<Contrib> contribs;
   int num_dwin = 0;
@@ -445,14 +461,14 @@ struct PassPlan {
   int prog = 0;                   // compile-time program of the pass kernel (0: interpreted)
   std::vector<Flip> flips;
   CUtensorMap tmap;               // HIGH: [members * 2^(n-c) rows][2^c columns] (c = win[0]), boxes of 2^colb columns
-  CUtensorMap tmap4;              // HIGH complex64: the same with boxes of 4 columns (configuration 2)
+  CUtensorMap tmap4;              // HIGH complex64, m = 10: the same with boxes of 4 columns (configuration 2)
   // device copies
   FOp* d_ops = nullptr;
   OutTerm* d_outs = nullptr;
   Producer* d_prods = nullptr;
   Contrib* d_contribs = nullptr;
   void* d_params = nullptr;
-  void* d_alpha = nullptr;        // per member and out-of-window tile value: 11 out factors
+  void* d_alpha = nullptr;        // per member and out-of-window tile value: m + 1 out factors
 };
 
 struct Step {
@@ -507,6 +523,7 @@ struct qs_plan_s {
   void* d_rank_mats = nullptr;
   int rank_variant = 0;           // the running variant: real start, per-member noise, normalisation
   int colb = 3;
+  int m = kWin;                   // window width of the fused passes
   int low_cfg = 0;                // kernel configuration of each window geometry (see launch_pass_kernel)
   int high_cfg = 0;
   int launches = 0;               // timing slots of a run (precompute, pass, single step)
@@ -569,7 +586,14 @@ bool commute(const PGate& a, const PGate& b) {
   return (a.qmask & b.qmask) == 0;
 }
 
-int stage_of(int j) { return j >= 5 ? 0 : 1; }
+// Register stage for window bit j of a window of m bits: the current stage
+// when its register bits hold j, else A (the top five), B (bits 0..4) or C
+// (bits 5..9, m > 10) -- the one that holds j.
+int stage_for(int j, int m, int cur) {
+  if (cur >= 0 && j >= stage_base(m, cur) && j < stage_base(m, cur) + kRegBits) return cur;
+  if (j >= m - kRegBits) return 0;
+  return j < kRegBits ? 1 : 2;
+}
 
 bool two_shear_safe(const std::vector<PGate>& gates, double e_max) {
   for (const PGate& g : gates) {
@@ -587,23 +611,24 @@ bool two_shear_safe(const std::vector<PGate>& gates, double e_max) {
 }
 
 // Greedy pass builder starting at remaining[0]; returns absorbed flags.
-// Start c of a high window [c, c + 10) for a run whose first dense gate is on
-// qubit q >= 10: of the candidates n - 10 (the top), q - 9 (the run goes
+// Start c of a high window [c, c + m) for a run whose first dense gate is on
+// qubit q >= m: of the candidates n - m (the top), q - m + 1 (the run goes
 // down) and q (it goes up), the one holding most of the run's next one-qubit
 // gates; -1 when none is allowed (c >= colb, and the tensor map's row
 // coordinate, members x 2^(n-c), within 31 bits).
-int choose_window(const std::vector<PGate>& G, const std::vector<int>& rem, int n, int colb, uint64_t batch, int q) {
+int choose_window(const std::vector<PGate>& G, const std::vector<int>& rem, int n, int colb, uint64_t batch, int q,
+                  int m) {
   int best = -1, best_count = -1;
-  const int cand[3] = {n - kWin, q - (kWin - 1), q};
+  const int cand[3] = {n - m, q - (m - 1), q};
   for (int c : cand) {
-    c = std::min(std::max(c, colb), n - kWin);
-    if (c < colb || q < c || q >= c + kWin) continue;
+    c = std::min(std::max(c, colb), n - m);
+    if (c < colb || q < c || q >= c + m) continue;
     if (n - c >= 31 || (batch << (n - c)) >= (1ull << 31)) continue;
     int count = 0;
     for (size_t i = 0; i < rem.size() && i < 256; ++i) {
       const PGate& g = G[rem[i]];
       if (!g.dense1 && !g.cp && !g.flip) break;
-      if (g.dense1 && g.g.targets[0] >= c && g.g.targets[0] < c + kWin) ++count;
+      if (g.dense1 && g.g.targets[0] >= c && g.g.targets[0] < c + m) ++count;
     }
     if (count > best_count) { best = c; best_count = count; }
   }
@@ -611,8 +636,9 @@ int choose_window(const std::vector<PGate>& G, const std::vector<int>& rem, int 
 }
 
 bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n, int colb, uint64_t batch,
-                size_t op_budget, PassPlan* P, std::vector<char>* absorbed) {
+                size_t op_budget, int m, PassPlan* P, std::vector<char>* absorbed) {
   P->colb = colb;
+  P->m = m;
   // window from the first fusable dense gate (lookahead)
   int q = -1;
   for (size_t i = 0; i < rem.size() && i < 64; ++i) {
@@ -622,29 +648,36 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
   }
   P->high = false;
   int c0 = 0;
-  if (q >= 10) {
-    if (n < kWin + colb) return false;               // a high tile needs 2^colb columns
-    c0 = choose_window(G, rem, n, colb, batch, q);
+  if (q >= m) {
+    if (n < m + colb) return false;                  // a high tile needs 2^colb columns
+    c0 = choose_window(G, rem, n, colb, batch, q, m);
     if (c0 < 0) return false;
     P->high = true;
   }
-  for (int l = 0; l < kWin; ++l) P->win[l] = c0 + l;
+  for (int l = 0; l < m; ++l) P->win[l] = c0 + l;
   int loc[64];
   for (int i = 0; i < 64; ++i) loc[i] = -1;
-  for (int l = 0; l < kWin; ++l) loc[P->win[l]] = l;
+  for (int l = 0; l < m; ++l) loc[P->win[l]] = l;
 
   std::vector<int> skipped;
   uint64_t locked = 0;                                  // window local bits with out terms
   int stage = -1;
   int dense_count = 0;
-  struct Dw { int j; std::vector<Contrib> cs; };
+  struct Dw { int j; std::vector<Contrib> cs; int sh; };
   std::vector<Dw> dwins;                                // indexed by producer order
   std::vector<std::pair<int, int>> out_gates;           // (attach, gate) in order
   std::vector<uint64_t> out_masks;
   P->ops.clear();
-  auto need_stage = [&](int st) {
-    if (stage == -1) { stage = st; P->start_stage = P->high ? st : 0; if (!P->high && st == 1) { FOp x{}; x.type = OP_EXCH; P->ops.push_back(x); } }
-    else if (stage != st) { FOp x{}; x.type = OP_EXCH; P->ops.push_back(x); stage = st; }
+  // an exchange op names the stage it goes to (j); a low pass starts in stage A
+  auto need_stage = [&](int j) {
+    const int st = stage_for(j, m, stage);
+    if (stage == -1) {
+      stage = st;
+      P->start_stage = P->high ? st : 0;
+      if (!P->high && st != 0) { FOp x{}; x.type = OP_EXCH; x.j = (uint8_t)st; P->ops.push_back(x); }
+    } else if (stage != st) {
+      FOp x{}; x.type = OP_EXCH; x.j = (uint8_t)st; P->ops.push_back(x); stage = st;
+    }
   };
   size_t ncontrib = 0, table_entries = 0;
   for (size_t i = 0; i < rem.size(); ++i) {
@@ -673,7 +706,7 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
     (*absorbed)[i] = 1;
     if (g.dense1) {
       const int l = loc[g.g.targets[0]];
-      need_stage(stage_of(l));
+      need_stage(l);
       FOp x{};
       x.type = OP_DENSE;
       x.j = (uint8_t)l;
@@ -700,18 +733,21 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
       const int p0 = g.g.targets[0], p1 = g.g.targets[1];
       const int l0 = loc[p0], l1 = loc[p1];
       if (l0 >= 0 && l1 >= 0) {
-        const int a = std::max(l0, l1), m = std::min(l0, l1);
-        need_stage(stage_of(a));
+        const int a = std::max(l0, l1), partner = std::min(l0, l1);
+        need_stage(a);
         if (!P->ops.empty() && P->ops.back().type == OP_DWIN && P->ops.back().j == a) {
-          dwins[P->ops.back().off].cs.push_back(Contrib{m, rem[i]});
+          dwins[P->ops.back().off].cs.push_back(Contrib{partner, rem[i]});
         } else {
           FOp x{};
           x.type = OP_DWIN;
           x.j = (uint8_t)a;
           x.off = (uint32_t)dwins.size();
-          dwins.push_back(Dw{a, {Contrib{m, rem[i]}}});
+          // windows above 10 qubits keep the table as its factors over the
+          // thread's bits and the register bits of the stage
+          const int sh = m > kWin ? stage_base(m, stage) : 0;
+          dwins.push_back(Dw{a, {Contrib{partner, rem[i]}}, sh});
           P->ops.push_back(x);
-          table_entries += 1u << a;
+          table_entries += sh > 0 ? (1u << sh) + (1u << (a - sh)) : 1u << a;
         }
         ++ncontrib;
       } else {
@@ -750,9 +786,9 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
   }
   P->num_dense = dense_count;
   P->diag_off = -1;
-  if (any_real) {                                       // ratios of the 10 window bits + scale
+  if (any_real) {                                       // ratios of the m window bits + scale
     P->diag_off = (int)off;
-    off += 12;
+    off += (uint32_t)((m + 1 + 3) & ~3);
   }
   P->contribs.clear();
   P->num_dwin = 0;
@@ -762,12 +798,13 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
       Producer pr{};
       pr.kind = PD_DWIN;
       pr.j = d.j;
+      pr.sh = d.sh;
       pr.contrib_start = (int)P->contribs.size();
       pr.contrib_count = (int)d.cs.size();
       for (auto& c : d.cs) P->contribs.push_back(c);
       pr.off = off;
       x.off = off;
-      off += 2u << d.j;
+      off += d.sh > 0 ? (2u << d.sh) + (2u << (d.j - d.sh)) : 2u << d.j;
       prods.push_back(pr);
       ++P->num_dwin;
     }
@@ -776,13 +813,13 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
   std::vector<int> order(out_gates.size());
   for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    const int ax = out_gates[x].first < 0 ? 10 : out_gates[x].first;
-    const int ay = out_gates[y].first < 0 ? 10 : out_gates[y].first;
+    const int ax = out_gates[x].first < 0 ? m : out_gates[x].first;
+    const int ay = out_gates[y].first < 0 ? m : out_gates[y].first;
     return ax < ay;
   });
   P->outs.clear();
-  for (int i = 0; i < 12; ++i) P->out_start[i] = 0;
-  int cnt[11] = {0};
+  for (int i = 0; i < kMaxWin + 2; ++i) P->out_start[i] = 0;
+  int cnt[kMaxWin + 1] = {0};
   for (int idx : order) {
     const int a = out_gates[idx].first;
     OutTerm t{};
@@ -796,19 +833,19 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
     off += 2;
     prods.push_back(pr);
     P->outs.push_back(t);
-    cnt[a < 0 ? 10 : a]++;
+    cnt[a < 0 ? m : a]++;
   }
   int acc = 0;
-  for (int a = 0; a < 11; ++a) { P->out_start[a] = acc; acc += cnt[a]; }
-  P->out_start[11] = acc;
+  for (int a = 0; a <= m; ++a) { P->out_start[a] = acc; acc += cnt[a]; }
+  P->out_start[m + 1] = acc;
   P->prods = prods;
   P->stride = (int)((off + 3) & ~3u);
   P->other.clear();
   if (P->high) {
     for (int b = P->colb; b < n; ++b) if (loc[b] < 0) P->other.push_back(b);
-    P->tile_shift = n - kWin - P->colb;
+    P->tile_shift = n - m - P->colb;
   } else {
-    P->tile_shift = n - kWin;
+    P->tile_shift = n - m;
   }
   return true;
 }
@@ -832,7 +869,7 @@ bool segment_pass(PassPlan* P) {
   P->flips.clear();
   auto order_ok = [&](const std::vector<Item>& items, bool desc) {
     auto pos = [&](const Item& it) {
-      const int rj = cur_stage == 0 ? it.j - 5 : it.j;
+      const int rj = it.j - stage_base(P->m, cur_stage);
       const int idx = desc ? 4 - rj : rj;
       return 2 * idx + (it.type == OP_DWIN ? 1 : 0);
     };
@@ -855,7 +892,7 @@ bool segment_pass(PassPlan* P) {
     sg.stage = (uint8_t)cur_stage;
     sg.desc = order_ok(cur, true) ? 1 : 0;
     for (const Item& it : cur) {
-      const int rj = cur_stage == 0 ? it.j - 5 : it.j;
+      const int rj = it.j - stage_base(P->m, cur_stage);
       if (it.type == OP_DENSE) {
         sg.dense |= 1u << rj;
         sg.doff[rj] = it.op->off;
@@ -881,7 +918,7 @@ bool segment_pass(PassPlan* P) {
   int stage = P->high ? P->start_stage : 0;
   size_t dw = 0;
   for (const FOp& op : P->ops) {
-    if (op.type == OP_EXCH) { close(); stage ^= 1; continue; }
+    if (op.type == OP_EXCH) { close(); stage = op.j; continue; }
     if (op.type == OP_FLIP || op.type == OP_FLIPM) {
       if (!open) { open = true; cur_stage = stage; }
       pending_flips.push_back(op);
@@ -911,7 +948,26 @@ bool segment_pass(PassPlan* P) {
 // the noisy QFT (every bit of stage A, bits 1..4 of stage B).
 constexpr int kLayerPrograms[] = {prog_layers(0x1f, 0x1e)};
 
+// Windows of 11 and 12 qubits: the full-window program (wide_full_prog),
+// segments A, C, B (a low pass may lack A: it starts in A all the same).
+int choose_wide_prog(const PassPlan& P) {
+  const int want = wide_full_prog(P.m);
+  if (!want || !P.flips.empty() || P.segs.empty() || P.segs.size() > 3) return 0;
+  const int first = 3 - (int)P.segs.size();            // stages A, C, B from index first
+  if (first != 0 && (P.high || first != 1)) return 0;
+  static const int order[3] = {0, 2, 1};
+  int prog = kProgWide;
+  for (size_t i = 0; i < P.segs.size(); ++i) {
+    const Seg& g = P.segs[i];
+    const int k = first + (int)i;
+    if (g.stage != order[k] || !g.desc || g.nflip || g.real != g.dense) return 0;
+    prog |= ((int)g.dense << (10 * k)) | ((int)g.dwin << (10 * k + 5));
+  }
+  return prog == want ? prog : 0;
+}
+
 int choose_prog(const PassPlan& P) {
+  if (P.m != kWin) return choose_wide_prog(P);
   if (P.segs.size() != 2 || !P.flips.empty() || (P.high && P.start_stage != 0)) return 0;
   const Seg& a = P.segs[0];
   const Seg& b = P.segs[1];
@@ -941,17 +997,11 @@ qs_status upload(qs_plan p, T** dst, const std::vector<T>& v) {
 //   high 1: two blocks per SM, one buffer each (registers <= 128)
 //   high 2: four blocks of 4 warps per SM (tiles of 4 columns), one buffer each
 // complex128: low 4 warps / two buffers, high 4 columns / two buffers.
+// Wider windows: see launch_pass_wide.
 constexpr int kLowCfgsF = 3, kHighCfgsF = 3, kLowCfgsD = 1, kHighCfgsD = 1;
 template <typename R> constexpr int high_colb() { return sizeof(R) == 4 ? 3 : 2; }
-
-template <typename R, int W, int NB>
-size_t low_smem() { return (size_t)W * LowShape<W, NB>::PER_WARP * sizeof(cplx<R>); }
-template <typename R, int CB, int NB>
-size_t high_smem() {
-  return NB * (size_t)HighShape<CB>::BUF * sizeof(cplx<R>);
-}
-int num_low_cfgs(size_t esize) { return esize == 8 ? kLowCfgsF : kLowCfgsD; }
-int num_high_cfgs(size_t esize) { return esize == 8 ? kHighCfgsF : kHighCfgsD; }
+int num_low_cfgs(size_t esize, int m) { return m != kWin ? 1 : (esize == 8 ? kLowCfgsF : kLowCfgsD); }
+int num_high_cfgs(size_t esize, int m) { return m != kWin ? 1 : (esize == 8 ? kHighCfgsF : kHighCfgsD); }
 
 // Tensor map of the state as [batch * 1024 rows][2^(n-10) columns] of 8-byte
 // elements (a complex128 amplitude is two of them), boxes of 2^colb amplitudes
@@ -986,28 +1036,33 @@ qs_status make_tmap(qs_plan p, PassPlan* P, int colb, CUtensorMap* map) {
 // columns per high-window tile of the configuration launched (0 for the low window)
 int launch_colb(qs_plan p, const PassPlan& P) {
   if (!P.high) return 0;
+  if (P.m != kWin) return wide_colb(P.m);
   return p->h->esize == 8 && p->high_cfg == 2 ? 2 : P.colb;
 }
-int launch_tile_shift(qs_plan p, const PassPlan& P) { return p->h->n - kWin - launch_colb(p, P); }
+int launch_tile_shift(qs_plan p, const PassPlan& P) { return p->h->n - P.m - launch_colb(p, P); }
+// fused-fidelity partials per member: one per tile, and per warp of a tile in
+// the low window (2^(m-10) warps)
+int fid_slots(qs_plan p, const PassPlan& P) {
+  return (1 << launch_tile_shift(p, P)) * (P.high ? 1 : 1 << (P.m - kWin));
+}
 
 PassArgs pass_args(qs_plan p, const PassPlan& P, int synth, int fid) {
   qs_ctx* h = p->h;
   PassArgs A{};
   A.n = h->n;
+  A.m = P.m;
   A.start_stage = P.start_stage;
-  for (int l = 0; l < kWin; ++l) A.win[l] = P.win[l];
+  for (int l = 0; l < P.m; ++l) A.win[l] = P.win[l];
   A.nseg = (int)P.segs.size();
   for (int i = 0; i < A.nseg; ++i) A.segs[i] = P.segs[i];
   for (size_t i = 0; i < P.flips.size(); ++i) A.flips[i] = P.flips[i];
-  for (int i = 0; i < 12; ++i) A.out_start[i] = P.out_start[i];
-  A.outs = P.d_outs;
   A.alpha_tab = P.d_alpha;
   A.param_stride = P.stride;
   A.params = P.d_params;
   A.marked = h->m_marked;
   const uint64_t total = (uint64_t)h->batch << h->n;
   A.tile_shift = launch_tile_shift(p, P);
-  A.tiles = total >> (kWin + launch_colb(p, P));
+  A.tiles = total >> (P.m + launch_colb(p, P));
   A.status = h->dstatus + 2;
   A.synth = synth ? 1 : 0;
   A.basis = synth == 2 ? h->m_basis : nullptr;
@@ -1028,18 +1083,19 @@ cudaError_t launch_precompute(qs_plan p, const PassPlan& P, cudaStream_t s) {
   NoiseSrc src{};
   if (h->member_noise) { src.e = h->m_e; src.seed = h->m_seed; src.traj = h->m_traj; }
   const size_t pre_smem =
-      (P.contribs.size() + (size_t)P.num_dwin * kWin + (1u << (kWin - 1)) + 4 * (size_t)P.num_dense) * sizeof(double2);
+      (P.contribs.size() + (size_t)P.num_dwin * kMaxWin + (1u << (P.m - 1)) + 4 * (size_t)P.num_dense) * sizeof(double2);
   k_precompute<R><<<h->batch, 128, pre_smem, s>>>((R*)P.d_params, P.stride, p->d_gates, P.d_prods,
                                                    (int)P.prods.size(), P.d_contribs, (int)P.contribs.size(),
-                                                   P.num_dwin, P.num_dense, P.diag_off, src, p->d_run, p->stable);
+                                                   P.num_dwin, P.num_dense, P.diag_off, src, p->d_run, p->stable, P.m);
   if (P.d_alpha) {
     OutStarts st{};
-    for (int i = 0; i < 12; ++i) st.v[i] = P.out_start[i];
-    const int obits = h->n - kWin;
-    const uint32_t chunks = (uint32_t)(((11ull << obits) + 255) / 256);
-    const size_t sm = (size_t)((P.out_start[11] + 1) & ~1) * sizeof(uint64_t) + (size_t)P.out_start[11] * sizeof(cplx<R>);
+    for (int i = 0; i < kMaxWin + 2; ++i) st.v[i] = P.out_start[i];
+    const int obits = h->n - P.m;
+    const int nterms = P.out_start[P.m + 1];
+    const uint32_t chunks = (uint32_t)((((uint64_t)(P.m + 1) << obits) + 255) / 256);
+    const size_t sm = (size_t)((nterms + 1) & ~1) * sizeof(uint64_t) + (size_t)nterms * sizeof(cplx<R>);
     k_out_table<R><<<(unsigned)(chunks * (uint64_t)h->batch), 256, sm, s>>>(
-        (cplx<R>*)P.d_alpha, (const R*)P.d_params, P.stride, P.d_outs, st, P.diag_off, obits, P.win[0], chunks);
+        (cplx<R>*)P.d_alpha, (const R*)P.d_params, P.stride, P.d_outs, st, P.diag_off, obits, P.win[0], chunks, P.m);
   }
   return cudaGetLastError();
 }
@@ -1057,6 +1113,10 @@ cudaError_t launch_pass_kernel(qs_plan p, const PassPlan& P, cudaStream_t s, int
   };
   C* psi = (C*)h->state;
   constexpr int kQft = prog_layers(0x1f, 0x1e);
+  if constexpr (sizeof(R) == 4) {
+    // wider windows (n <= 32, checked when the width is set)
+    if (P.m != kWin) return launch_pass_wide(psi, P.tmap, A, P.high, P.m, prog, sms, s);
+  }
   if (!P.high) {
     if constexpr (sizeof(R) == 4) {
       if (prog == kQft && p->low_cfg == 1)
@@ -1099,36 +1159,34 @@ cudaError_t launch_pass_kernel(qs_plan p, const PassPlan& P, cudaStream_t s, int
   return cudaGetLastError();
 }
 
-// fused fidelity: out[b] = |sum over the last pass's tiles of member b|^2
-__global__ void k_fid_finalize(const double* __restrict__ partials, int members, int tiles, double* __restrict__ out) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= members) return;
+// fused fidelity: out[b] = |sum over the last pass's tiles of member b|^2.
+// One warp per member: lane l adds slots l, l + 32, ... in order, then the
+// lanes' sums meet in a fixed shuffle tree (FP64 throughout, the same order
+// on every run).
+__global__ void __launch_bounds__(256) k_fid_finalize(const double* __restrict__ partials, int members, int tiles,
+                                                      double* __restrict__ out) {
+  const int b = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= members) return;                            // uniform per warp
+  const double* pm = partials + 2 * (uint64_t)b * tiles;
   double re = 0.0, im = 0.0;
-  for (int t = 0; t < tiles; ++t) {
-    re += partials[2 * ((uint64_t)b * tiles + t)];
-    im += partials[2 * ((uint64_t)b * tiles + t) + 1];
+  for (int t = lane; t < tiles; t += 32) {
+    re += pm[2 * t];
+    im += pm[2 * t + 1];
   }
-  out[b] = re * re + im * im;
-}
-
-// Dynamic shared memory of a pass kernel, and a carveout preference just
-// large enough for `blocks` resident blocks per SM, so the rest of the
-// unified L1 caches the members' parameters and phase tables.
-template <typename K>
-cudaError_t set_pass_attrs(K kernel, size_t dyn, int blocks) {
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-  if (e != cudaSuccess) return e;
-  constexpr size_t kSmemPerSM = 228 * 1024, kReservedPerBlock = 1024, kStatic = 1024;
-  const size_t need = (size_t)blocks * (dyn + kStatic + kReservedPerBlock);
-  const int pct = (int)std::min<size_t>(100, (need * 100 + kSmemPerSM - 1) / kSmemPerSM);
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if (lane == 0) out[b] = re * re + im * im;
 }
 
 cudaError_t set_smem_attrs(size_t esize) {
   static std::atomic<bool> done[2] = {false, false};
   const int which = esize == 8 ? 0 : 1;
   if (done[which]) return cudaSuccess;
-  constexpr size_t kPreSmem = (kMaxContribs + kMaxDwin * kWin + (1u << (kWin - 1)) + 4 * kMaxOps) * sizeof(double2);
+  constexpr size_t kPreSmem = (kMaxContribs + kMaxDwin * kMaxWin + (1u << (kMaxWin - 1)) + 4 * kMaxOps) * sizeof(double2);
   cudaError_t e = esize == 8
       ? cudaFuncSetAttribute(k_precompute<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPreSmem)
       : cudaFuncSetAttribute(k_precompute<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPreSmem);
@@ -1146,6 +1204,7 @@ cudaError_t set_smem_attrs(size_t esize) {
     if (e == cudaSuccess) e = set_pass_attrs(k_pass_low<float, 12, 1, kQft>, low_smem<float, 12, 1>(), 1);
     if (e == cudaSuccess) e = set_pass_attrs(k_pass_high<float, 3, 1, false, kQft>, high_smem<float, 3, 1>(), 2);
     if (e == cudaSuccess) e = set_pass_attrs(k_pass_high<float, 2, 1, false, kQft>, high_smem<float, 2, 1>(), 4);
+    if (e == cudaSuccess) e = set_wide_attrs();
   } else {
     e = set_pass_attrs(k_pass_low<double, 4, 2>, low_smem<double, 4, 2>(), 1);
     if (e == cudaSuccess) e = set_pass_attrs(k_pass_high<double, 2, 2>, high_smem<double, 2, 2>(), 1);
@@ -1347,8 +1406,7 @@ qs_status enqueue_run(qs_plan p, cudaStream_t s, int synth, int fid) {
       if (e == cudaSuccess) e = f32 ? launch_pass_kernel<float>(p, P, s, sy, fd) : launch_pass_kernel<double>(p, P, s, sy, fd);
       mark(P.high ? 2 : 1);
       if (e == cudaSuccess && fd) {
-        const int tiles = 1 << launch_tile_shift(p, P);
-        k_fid_finalize<<<(h->batch + 255) / 256, 256, 0, s>>>(p->d_fid, h->batch, tiles, h->small + kSmallOutIndex);
+        k_fid_finalize<<<(h->batch + 7) / 8, 256, 0, s>>>(p->d_fid, h->batch, fid_slots(p, P), h->small + kSmallOutIndex);
         e = cudaGetLastError();
       }
       if (e != cudaSuccess) { h->stream = saved; return pfail(p, QS_ERR_CUDA, std::string("fused pass: ") + cudaGetErrorString(e)); }
@@ -1436,6 +1494,106 @@ qs_status run_plan(qs_plan p, double e, uint64_t seed, uint64_t gate_id0, int wa
   return st;
 }
 
+// Fused passes of a state-vector plan (window width p->m) for the gates in
+// rem, in order; a gate no pass can hold becomes a single step.
+void plan_passes(qs_plan p, std::vector<int> rem) {
+  qs_ctx* h = p->h;
+  const bool fuse = h->mode == QS_STATEVEC && h->n >= p->m;
+  while (!rem.empty()) {
+    if (fuse) {
+      PassPlan P;
+      std::vector<char> absorbed(rem.size(), 0);
+      bool built = false;
+      for (size_t budget = kMaxOps; budget >= 4 && !built; budget /= 2) {
+        P = PassPlan();
+        std::fill(absorbed.begin(), absorbed.end(), 0);
+        // a high window starts at or above the columns of a tile
+        const int colb = p->m == kWin ? p->colb : wide_colb(p->m);
+        if (!build_pass(p->gates, rem, h->n, colb, (uint64_t)h->batch, budget, p->m, &P, &absorbed)) break;
+        built = segment_pass(&P);
+        if (built) P.prog = choose_prog(P);
+      }
+      if (built) {
+        bool any = false;
+        for (char c : absorbed) any |= c != 0;
+        if (any) {
+          p->passes.push_back(P);
+          p->steps.push_back(Step{0, (int)p->passes.size() - 1, -1});
+          std::vector<int> next;
+          for (size_t i = 0; i < rem.size(); ++i) if (!absorbed[i]) next.push_back(rem[i]);
+          rem.swap(next);
+          continue;
+        }
+      }
+    }
+    p->steps.push_back(Step{1, -1, rem[0]});
+    rem.erase(rem.begin());
+  }
+}
+
+// Device copies of the passes' op lists, their tensor maps, and the buffers
+// every pass shares: one parameter block and one out-factor table (a pass's
+// precompute runs on the same stream right before the pass itself) and the
+// fused-fidelity partials.
+qs_status alloc_passes(qs_plan p) {
+  qs_ctx* h = p->h;
+  qs_status st = QS_OK;
+  size_t params_bytes = 16, alpha_bytes = 0;
+  for (auto& P : p->passes) {
+    if (st != QS_OK) break;
+    st = upload(p, &P.d_ops, P.ops);
+    if (st == QS_OK) st = upload(p, &P.d_outs, P.outs);
+    if (st == QS_OK) st = upload(p, &P.d_prods, P.prods);
+    if (st == QS_OK) st = upload(p, &P.d_contribs, P.contribs);
+    if (st == QS_OK) {
+      params_bytes = std::max(params_bytes, (size_t)P.stride * h->batch * (h->esize / 2));
+      // out factors of every tile: members x 2^(n-m) tile values x (m + 1) complex
+      if (P.out_start[P.m + 1] > 0)
+        alpha_bytes = std::max(alpha_bytes, (((size_t)h->batch * (P.m + 1)) << (h->n - P.m)) * h->esize);
+    }
+    if (st == QS_OK && P.high) st = make_tmap(p, &P, P.colb, &P.tmap);
+    if (st == QS_OK && P.high && h->esize == 8 && P.m == kWin) st = make_tmap(p, &P, 2, &P.tmap4);
+  }
+  // the most fidelity partials any configuration writes: 2^(n-10) per member
+  const size_t fid_slots_max = (size_t)1 << (h->n - kWin);
+  if (st == QS_OK && !p->passes.empty()) {
+    if (cudaMalloc(&p->d_params, params_bytes) != cudaSuccess) st = pfail(p, QS_ERR_OUT_OF_MEMORY, "plan params");
+    if (st == QS_OK && alpha_bytes && cudaMalloc(&p->d_alpha, alpha_bytes) != cudaSuccess)
+      st = pfail(p, QS_ERR_OUT_OF_MEMORY, "plan out factors");
+    for (auto& P : p->passes) {
+      P.d_params = p->d_params;
+      P.d_alpha = P.out_start[P.m + 1] > 0 ? p->d_alpha : nullptr;
+    }
+  }
+  if (st == QS_OK && !p->passes.empty() &&
+      cudaMalloc((void**)&p->d_fid, 2 * fid_slots_max * h->batch * sizeof(double)) != cudaSuccess)
+    st = pfail(p, QS_ERR_OUT_OF_MEMORY, "fidelity partials");
+  return st;
+}
+
+void free_passes(qs_plan p) {
+  for (auto& P : p->passes) {
+    void* ptrs[] = {P.d_ops, P.d_outs, P.d_prods, P.d_contribs};
+    for (void* x : ptrs) if (x) cudaFree(x);
+  }
+  p->passes.clear();
+  if (p->d_params) cudaFree(p->d_params);
+  if (p->d_alpha) cudaFree(p->d_alpha);
+  if (p->d_fid) cudaFree(p->d_fid);
+  p->d_params = p->d_alpha = nullptr;
+  p->d_fid = nullptr;
+}
+
+// timing slots (precompute + pass, or one single step) and kernels of one run
+// (the out-factor table is timed with the precompute)
+void count_launches(qs_plan p) {
+  p->launches = 0;
+  for (const Step& s : p->steps) p->launches += s.kind == 0 ? 2 : 1;
+  p->kernels = p->launches;
+  for (const Step& s : p->steps)
+    if (s.kind == 0 && p->passes[s.pass].d_alpha) ++p->kernels;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1472,7 +1630,6 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
   // (12 warps with one buffer; two high-window blocks per SM)
   if (h->dtype == QS_C64) { p->low_cfg = 2; p->high_cfg = 1; }
   // fused passes use 32-bit member-local offsets
-  const bool fuse = h->mode == QS_STATEVEC && h->n >= kWin;
   std::vector<int> rem;
   for (int i = 0; i < num_gates; ++i) rem.push_back(i);
   std::vector<std::vector<int>> dm_groups;
@@ -1549,34 +1706,7 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
     close();
     rem.clear();
   }
-  while (!rem.empty()) {
-    if (fuse) {
-      PassPlan P;
-      std::vector<char> absorbed(rem.size(), 0);
-      bool built = false;
-      for (size_t budget = kMaxOps; budget >= 4 && !built; budget /= 2) {
-        P = PassPlan();
-        std::fill(absorbed.begin(), absorbed.end(), 0);
-        if (!build_pass(p->gates, rem, h->n, p->colb, (uint64_t)h->batch, budget, &P, &absorbed)) break;
-        built = segment_pass(&P);
-        if (built) P.prog = choose_prog(P);
-      }
-      if (built) {
-        bool any = false;
-        for (char c : absorbed) any |= c != 0;
-        if (any) {
-          p->passes.push_back(P);
-          p->steps.push_back(Step{0, (int)p->passes.size() - 1, -1});
-          std::vector<int> next;
-          for (size_t i = 0; i < rem.size(); ++i) if (!absorbed[i]) next.push_back(rem[i]);
-          rem.swap(next);
-          continue;
-        }
-      }
-    }
-    p->steps.push_back(Step{1, -1, rem[0]});
-    rem.erase(rem.begin());
-  }
+  plan_passes(p, rem);
   std::vector<DGate> dg(p->gates.size());
   for (size_t i = 0; i < p->gates.size(); ++i) {
     const qs_gate& g = p->gates[i].g;
@@ -1634,47 +1764,12 @@ qs_status qs_plan_create(qs_handle h, const qs_gate* gates, int num_gates, qs_pl
       st = upload(p, reinterpret_cast<double**>(&p->d_rank_mats), rank_mats);
     }
   }
-  size_t fid_tiles = 0;
-  // one parameter buffer and one out-factor table serve every pass: a pass's
-  // precompute runs on the same stream right before the pass itself
-  size_t params_bytes = 16, alpha_bytes = 0;
-  for (auto& P : p->passes) {
-    if (st != QS_OK) break;
-    st = upload(p, &P.d_ops, P.ops);
-    if (st == QS_OK) st = upload(p, &P.d_outs, P.outs);
-    if (st == QS_OK) st = upload(p, &P.d_prods, P.prods);
-    if (st == QS_OK) st = upload(p, &P.d_contribs, P.contribs);
-    if (st == QS_OK) {
-      params_bytes = std::max(params_bytes, (size_t)P.stride * h->batch * (h->esize / 2));
-      // out factors of every tile: members x 2^(n-10) tile values x 11 complex
-      if (P.out_start[11] > 0) alpha_bytes = (((size_t)h->batch * 11) << (h->n - kWin)) * h->esize;
-    }
-    if (st == QS_OK && P.high) st = make_tmap(p, &P, P.colb, &P.tmap);
-    if (st == QS_OK && P.high && h->esize == 8) st = make_tmap(p, &P, 2, &P.tmap4);
-    fid_tiles = (size_t)1 << (h->n - kWin);             // the most tiles any configuration has
-  }
-  if (st == QS_OK && !p->passes.empty()) {
-    if (cudaMalloc(&p->d_params, params_bytes) != cudaSuccess) st = pfail(p, QS_ERR_OUT_OF_MEMORY, "plan params");
-    if (st == QS_OK && alpha_bytes && cudaMalloc(&p->d_alpha, alpha_bytes) != cudaSuccess)
-      st = pfail(p, QS_ERR_OUT_OF_MEMORY, "plan out factors");
-    for (auto& P : p->passes) {
-      P.d_params = p->d_params;
-      P.d_alpha = P.out_start[11] > 0 ? p->d_alpha : nullptr;
-    }
-  }
-  if (st == QS_OK && !p->passes.empty() &&
-      cudaMalloc((void**)&p->d_fid, 2 * fid_tiles * h->batch * sizeof(double)) != cudaSuccess)
-    st = pfail(p, QS_ERR_OUT_OF_MEMORY, "fidelity partials");
+  if (st == QS_OK) st = alloc_passes(p);
   if (st == QS_OK && cudaMalloc((void**)&p->d_run, sizeof(RunParams)) != cudaSuccess) st = pfail(p, QS_ERR_OUT_OF_MEMORY, "run params");
   if (st == QS_OK && cudaMallocHost((void**)&p->h_run, sizeof(RunParams)) != cudaSuccess) st = pfail(p, QS_ERR_OUT_OF_MEMORY, "run params");
   if (st == QS_OK && set_smem_attrs(h->esize) != cudaSuccess) st = pfail(p, QS_ERR_CUDA, "shared memory attribute");
   if (st != QS_OK) { qs_plan_destroy(p); return st; }
-  p->launches = 0;
-  for (const Step& s : p->steps) p->launches += s.kind == 0 ? 2 : 1;
-  // kernels launched per run (the out-factor table is timed with the precompute)
-  p->kernels = p->launches;
-  for (const Step& s : p->steps)
-    if (s.kind == 0 && p->passes[s.pass].d_alpha) ++p->kernels;
+  count_launches(p);
   if (!p->rank_ops.empty()) {
     p->kernels -= 1;
     for (const RankOp& op : p->rank_ops) p->kernels += op.kind == 4 ? 5 : 1;   // channel: expand, Gram x 2, eig, project
@@ -1771,14 +1866,15 @@ void drop_graphs(qs_plan p) {
 
 qs_status qs_plan_configs(qs_plan p, int* low_count, int* high_count) {
   if (!p || !low_count || !high_count) return QS_ERR_INVALID_ARG;
-  *low_count = num_low_cfgs(p->h->esize);
-  *high_count = num_high_cfgs(p->h->esize);
+  *low_count = num_low_cfgs(p->h->esize, p->m);
+  *high_count = num_high_cfgs(p->h->esize, p->m);
   return QS_OK;
 }
 
 qs_status qs_plan_set_config(qs_plan p, int low_cfg, int high_cfg) {
   if (!p) return QS_ERR_INVALID_ARG;
-  if (low_cfg < 0 || low_cfg >= num_low_cfgs(p->h->esize) || high_cfg < 0 || high_cfg >= num_high_cfgs(p->h->esize))
+  if (low_cfg < 0 || low_cfg >= num_low_cfgs(p->h->esize, p->m) || high_cfg < 0 ||
+      high_cfg >= num_high_cfgs(p->h->esize, p->m))
     return pfail(p, QS_ERR_INVALID_ARG, "kernel configuration out of range");
   if (low_cfg != p->low_cfg || high_cfg != p->high_cfg) {
     // graphs hold the old kernels; wait for runs that may still use them
@@ -1797,27 +1893,83 @@ qs_status qs_plan_get_config(qs_plan p, int* low_cfg, int* high_cfg) {
   return QS_OK;
 }
 
-qs_status qs_plan_autotune(qs_plan p, int reps, double e, uint64_t seed, double* best_ms) {
-  if (!p || reps < 1) return QS_ERR_INVALID_ARG;
-  const int nl = num_low_cfgs(p->h->esize), nh = num_high_cfgs(p->h->esize);
+qs_status qs_plan_set_window(qs_plan p, int m) {
+  if (!p) return QS_ERR_INVALID_ARG;
+  qs_ctx* h = p->h;
+  if (m != 10 && m != 11 && m != 12) return pfail(p, QS_ERR_INVALID_ARG, "window width must be 10, 11 or 12");
+  if (m == p->m) return QS_OK;
+  if (h->mode != QS_STATEVEC || h->dtype != QS_C64)
+    return pfail(p, QS_ERR_NOT_SUPPORTED, "windows of 11 or 12 qubits need a STATEVEC complex64 handle");
+  if (m != kWin && h->n > 32) return pfail(p, QS_ERR_NOT_SUPPORTED, "windows of 11 or 12 qubits need n <= 32");
+  // graphs and a run in flight hold the old passes' buffers
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "stream sync");
+  drop_graphs(p);
+  free_passes(p);
+  p->steps.clear();
+  p->m = m;
+  if (m == kWin) { p->low_cfg = 2; p->high_cfg = 1; }   // the defaults of qs_plan_create
+  else { p->low_cfg = 0; p->high_cfg = 0; }
+  std::vector<int> rem(p->gates.size());
+  for (size_t i = 0; i < rem.size(); ++i) rem[i] = (int)i;
+  plan_passes(p, rem);
+  qs_status st = alloc_passes(p);
+  if (st != QS_OK) {
+    // leave a plan that runs nothing rather than one with missing buffers
+    free_passes(p);
+    p->steps.clear();
+    count_launches(p);
+    return st;
+  }
+  count_launches(p);
+  if (!p->events.empty()) {
+    // timing slots follow the new steps
+    for (auto& ev : p->events) cudaEventDestroy(ev);
+    p->events.clear();
+    p->event_kinds.clear();
+    if (p->timing) {
+      p->timing = false;
+      st = qs_plan_set_timing(p, 1);
+    }
+  }
+  return st;
+}
+
+qs_status qs_plan_get_window(qs_plan p, int* m) {
+  if (!p || !m) return QS_ERR_INVALID_ARG;
+  *m = p->m;
+  return QS_OK;
+}
+
+namespace {
+// Best low and high configurations of the plan's current window width: the
+// time of the low and high passes of one run under each, averaged over reps
+// profiled runs; total = the whole run under the chosen pair.
+qs_status tune_configs(qs_plan p, int reps, double e, uint64_t seed, int* bl, int* bh, double* low_best,
+                       double* high_best, double* total) {
+  const int nl = num_low_cfgs(p->h->esize, p->m), nh = num_high_cfgs(p->h->esize, p->m);
   const int ncfg = std::max(nl, nh);
-  std::vector<double> low_ms(ncfg, -1.0), high_ms(ncfg, -1.0);
+  std::vector<double> low_ms(ncfg, -1.0), high_ms(ncfg, -1.0), other_ms(ncfg, 0.0);
   std::vector<double> ms((size_t)std::max(p->launches, 1));
   std::vector<int> kinds(ms.size());
   for (int c = 0; c < ncfg; ++c) {
     qs_status st = qs_plan_set_config(p, std::min(c, nl - 1), std::min(c, nh - 1));
     if (st != QS_OK) return st;
     int count = 0;
+    // one untimed run first: a kernel's first launch also loads its module
+    st = qs_plan_profile(p, 1, e, seed, 0, ms.data(), kinds.data(), (int)ms.size(), &count);
+    if (st != QS_OK) return st;
     st = qs_plan_profile(p, reps, e, seed, 0, ms.data(), kinds.data(), (int)ms.size(), &count);
     if (st != QS_OK) return st;
-    double lo = 0.0, hi = 0.0;
+    double lo = 0.0, hi = 0.0, other = 0.0;
     bool has_lo = false, has_hi = false;
     for (int i = 0; i < count && i < (int)ms.size(); ++i) {
       if (kinds[i] == 1) { lo += ms[i]; has_lo = true; }
-      if (kinds[i] == 2) { hi += ms[i]; has_hi = true; }
+      else if (kinds[i] == 2) { hi += ms[i]; has_hi = true; }
+      else other += ms[i];
     }
     if (has_lo && c < nl) low_ms[c] = lo;
     if (has_hi && c < nh) high_ms[c] = hi;
+    other_ms[c] = other;
   }
   auto best = [](const std::vector<double>& v, int n) {
     int b = 0;
@@ -1825,9 +1977,49 @@ qs_status qs_plan_autotune(qs_plan p, int reps, double e, uint64_t seed, double*
       if (v[c] >= 0.0 && (v[b] < 0.0 || v[c] < v[b])) b = c;
     return b;
   };
-  const int bl = best(low_ms, nl), bh = best(high_ms, nh);
-  if (best_ms) { best_ms[0] = low_ms[bl]; best_ms[1] = high_ms[bh]; }
-  return qs_plan_set_config(p, bl, bh);
+  *bl = best(low_ms, nl);
+  *bh = best(high_ms, nh);
+  *low_best = low_ms[*bl];
+  *high_best = high_ms[*bh];
+  // precompute and single steps do not depend on the configuration: their
+  // time averaged over the configurations profiled
+  double other = 0.0;
+  for (int c = 0; c < ncfg; ++c) other += other_ms[c];
+  *total = std::max(0.0, *low_best) + std::max(0.0, *high_best) + other / ncfg;
+  return QS_OK;
+}
+}  // namespace
+
+qs_status qs_plan_autotune(qs_plan p, int reps, double e, uint64_t seed, double* best_ms) {
+  if (!p || reps < 1) return QS_ERR_INVALID_ARG;
+  qs_ctx* h = p->h;
+  // window widths to try: 10, and 11 and 12 where the handle allows them
+  std::vector<int> widths = {p->m};
+  if (h->mode == QS_STATEVEC && h->dtype == QS_C64 && h->n <= 32)
+    for (int m = kWin; m <= kMaxWin; ++m)
+      if (m != p->m && h->n >= m) widths.push_back(m);
+  int best_m = p->m, best_l = 0, best_h = 0;
+  double best_total = -1.0, best_lo = -1.0, best_hi = -1.0;
+  for (int m : widths) {
+    qs_status st = qs_plan_set_window(p, m);
+    if (st != QS_OK) return st;
+    int bl = 0, bh = 0;
+    double lo = 0.0, hi = 0.0, total = 0.0;
+    st = tune_configs(p, reps, e, seed, &bl, &bh, &lo, &hi, &total);
+    if (st != QS_OK) return st;
+    if (best_total < 0.0 || total < best_total) {
+      best_total = total;
+      best_m = m;
+      best_l = bl;
+      best_h = bh;
+      best_lo = lo;
+      best_hi = hi;
+    }
+  }
+  qs_status st = qs_plan_set_window(p, best_m);
+  if (st != QS_OK) return st;
+  if (best_ms) { best_ms[0] = best_lo; best_ms[1] = best_hi; }
+  return qs_plan_set_config(p, best_l, best_h);
 }
 
 qs_status qs_plan_set_timing(qs_plan p, int on) {
@@ -1868,14 +2060,8 @@ qs_status qs_plan_destroy(qs_plan p) {
   if (!p) return QS_ERR_INVALID_ARG;
   if (p->h) cudaStreamSynchronize(p->h->stream);
   for (auto& x : p->exec) if (x) cudaGraphExecDestroy(x);
-  for (auto& P : p->passes) {
-    void* ptrs[] = {P.d_ops, P.d_outs, P.d_prods, P.d_contribs};
-    for (void* x : ptrs) if (x) cudaFree(x);
-  }
-  if (p->d_params) cudaFree(p->d_params);
-  if (p->d_alpha) cudaFree(p->d_alpha);
+  free_passes(p);
   if (p->d_gates) cudaFree(p->d_gates);
-  if (p->d_fid) cudaFree(p->d_fid);
   for (auto& b : p->dm_blocks) {
     if (b.d_u) cudaFree(b.d_u);
     if (b.d_uf) cudaFree(b.d_uf);

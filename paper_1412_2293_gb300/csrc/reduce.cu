@@ -8,6 +8,8 @@
 // are -- and everything from the warp level up is FP64.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace qs {
@@ -88,24 +90,34 @@ __global__ void __launch_bounds__(kRBlock) k_norm_partials(const cplx<R>* __rest
   }
 }
 
-// v_b = |sum_c partial|^2 (mode 0) or sum_c partial.x (mode 1), chunks in
-// order; out[g] = v_{g group} + ... + v_{g group + group - 1} in order (group
-// = 1: out[b] = v_b).
-__global__ void k_finalize(const double* partials, int members, int chunks, int mode, int group, double* out) {
+// v_b = |sum_c partial|^2 (mode 0) or sum_c partial.x (mode 1); out[g] =
+// v_{g group} + ... + v_{g group + group - 1} in order (group = 1: out[b] =
+// v_b).  One warp per output: lane l adds chunks l, l + 32, ... in order, the
+// lanes meet in a fixed shuffle tree (the same order on every call).
+__global__ void __launch_bounds__(256) k_finalize(const double* partials, int members, int chunks, int mode, int group,
+                                                  double* out) {
   const int outs = members / group;
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < outs; g += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int g = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); g < outs; g += warps) {
     double s = 0.0;
     for (int b = g * group; b < (g + 1) * group; ++b) {
+      const double* pb = partials + 2 * (uint64_t)b * chunks;
       double re = 0.0, im = 0.0;
-      for (int c = 0; c < chunks; ++c) {
-        re += partials[2 * ((uint64_t)b * chunks + c)];
-        im += partials[2 * ((uint64_t)b * chunks + c) + 1];
+      for (int c = lane; c < chunks; c += 32) {
+        re += pb[2 * c];
+        im += pb[2 * c + 1];
       }
+      re = warp_sum(re);
+      im = warp_sum(im);
       s += mode == 0 ? re * re + im * im : re;
     }
-    out[g] = s;
+    if (lane == 0) out[g] = s;
   }
 }
+
+// warps of the finalize launch for `outs` outputs (eight per block)
+inline unsigned finalize_blocks(int outs) { return (unsigned)std::max(1, std::min((outs + 7) / 8, 4096)); }
 
 template <typename R>
 __global__ void k_basis_prob(const cplx<R>* psi, int n, int members, uint64_t x, int group, double* out) {
@@ -189,7 +201,7 @@ cudaError_t launch_dot(qs_ctx* h, const void* psi, const void* ref, int n, int m
     k_dot_partials<float><<<grid, kRBlock, 0, h->stream>>>((const float2*)psi, (const float2*)ref, n, chunks, kChunk, h->partials);
   else
     k_dot_partials<double><<<grid, kRBlock, 0, h->stream>>>((const double2*)psi, (const double2*)ref, n, chunks, kChunk, h->partials);
-  k_finalize<<<(members / group + 255) / 256, 256, 0, h->stream>>>(h->partials, members, chunks, 0, group, out);
+  k_finalize<<<finalize_blocks(members / group), 256, 0, h->stream>>>(h->partials, members, chunks, 0, group, out);
   return cudaGetLastError();
 }
 
@@ -201,7 +213,7 @@ cudaError_t launch_norm(qs_ctx* h, const void* psi, int n, int members, int grou
     k_norm_partials<float><<<grid, kRBlock, 0, h->stream>>>((const float2*)psi, n, chunks, kChunk, h->partials);
   else
     k_norm_partials<double><<<grid, kRBlock, 0, h->stream>>>((const double2*)psi, n, chunks, kChunk, h->partials);
-  k_finalize<<<(members / group + 255) / 256, 256, 0, h->stream>>>(h->partials, members, chunks, 1, group, out);
+  k_finalize<<<finalize_blocks(members / group), 256, 0, h->stream>>>(h->partials, members, chunks, 1, group, out);
   return cudaGetLastError();
 }
 
@@ -222,7 +234,7 @@ cudaError_t launch_dm_trace(qs_ctx* h, const void* rho, int n, double* out) {
     k_dm_trace_partials<float><<<chunks, kRBlock, 0, h->stream>>>((const float2*)rho, n, chunks, kChunk, h->partials);
   else
     k_dm_trace_partials<double><<<chunks, kRBlock, 0, h->stream>>>((const double2*)rho, n, chunks, kChunk, h->partials);
-  k_finalize<<<1, 256, 0, h->stream>>>(h->partials, 1, chunks, 1, 1, out);
+  k_finalize<<<1, 32, 0, h->stream>>>(h->partials, 1, chunks, 1, 1, out);
   return cudaGetLastError();
 }
 
@@ -234,7 +246,7 @@ cudaError_t launch_dm_expect(qs_ctx* h, const void* rho, const void* phi, int n,
   else
     k_dm_expect_rows<double><<<(unsigned)N, kRBlock, 0, h->stream>>>((const double2*)rho, (const double2*)phi, n, h->partials);
   // sum of N row partials: treat them as one member with N chunks, real part
-  k_finalize<<<1, 256, 0, h->stream>>>(h->partials, 1, (int)N, 1, 1, out);
+  k_finalize<<<1, 32, 0, h->stream>>>(h->partials, 1, (int)N, 1, 1, out);
   return cudaGetLastError();
 }
 

@@ -90,6 +90,8 @@ _SIGS = {
     "qs_plan_set_config": ([_P, ct.c_int, ct.c_int], ct.c_int),
     "qs_plan_get_config": ([_P, _I, _I], ct.c_int),
     "qs_plan_autotune": ([_P, ct.c_int, ct.c_double, ct.c_uint64, _D], ct.c_int),
+    "qs_plan_set_window": ([_P, ct.c_int], ct.c_int),
+    "qs_plan_get_window": ([_P, _I], ct.c_int),
     "qs_fidelity_noalloc": ([_P, _P, ct.c_int, ct.c_int, ct.c_int, _P, _D], ct.c_int),
     "qs_measure_peaks": ([_D, _D], ct.c_int),
     "qs_debug_noise": ([ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_int, ct.POINTER(ct.c_uint32), _D], ct.c_int),
@@ -399,8 +401,19 @@ def qs_plan_get_config(p, h=None):
     return a.value, b.value
 
 
+def qs_plan_set_window(p, m, h=None):
+    _check(lib().qs_plan_set_window(p, int(m)), h)
+
+
+def qs_plan_get_window(p, h=None):
+    m = ct.c_int()
+    _check(lib().qs_plan_get_window(p, ct.byref(m)), h)
+    return m.value
+
+
 def qs_plan_autotune(p, reps=3, e=0.0, seed=0, h=None):
-    """Time every kernel configuration, keep the fastest; returns (low ms, high ms)."""
+    """Time every window width and kernel configuration, keep the fastest;
+    returns (low ms, high ms) of the configurations kept."""
     best = np.zeros(2, dtype=np.float64)
     _check(lib().qs_plan_autotune(p, int(reps), float(e), int(seed), _dptr(best)), h)
     return float(best[0]), float(best[1])
