@@ -785,7 +785,7 @@ def extra_rows(h, n, T, esize, stream, peaks):
         "ms_per_circuit": round(ms34, 1), "updates_per_s": (1 << n34) * len(ops34) / (ms34 / 1e3),
         "pass_GBps": round(passes34 * 2 * (1 << n34) * 8 / (ms34 / 1e3) / 1e9, 1), "fidelity": f34}
 
-    out["a11_serving_large_n"] = serving_large_n_row()
+    out["a11_serving_full_range"] = serving_full_range_row()
     out["a11_serving"] = serving_row()
     cap = out["a11_serving"]["jobs_per_s"]
     out["a11_serving_rate_sweep"] = {f"{m}x_capacity": serving_row(num_jobs=60, rate_per_s=m * cap, seed_offset=1)
@@ -820,32 +820,52 @@ def serving_row(num_jobs=100, rate_per_s=200.0, workers=4, seed_offset=0):
             "stream": "n 12..20, MC 2^6..2^10 trajectories c64, fixed rank r 1..8 c128, Grover iterations capped at 16"}
 
 
-def serving_large_n_row():
-    """The upper end of the serving workload's size range: Monte Carlo QFT
-    jobs at n = 24, 26, 28 (2 GiB complex64 per trajectory at n = 28, so the
-    128 trajectories of the largest job run in waves under the HBM budget),
-    a Grover job at n = 24 (16 iterations) and a fixed-rank QFT at n = 24,
-    arriving together."""
+def serving_full_range_row(num_jobs=24, rate_per_s=4.0, workers=4, limit_s=10.0):
+    """The serving workload over its whole size range: n 12..28, Monte Carlo
+    2^6..2^12 complex64 trajectories or fixed rank r 1..8 (complex128), Grover
+    iterations capped at 16, Poisson arrivals; bounded by the job count.
+    States up to 2 GiB per trajectory run in waves under the HBM budget.  A
+    request whose estimated device time exceeds limit_s runs the largest
+    power-of-two trajectory count that fits (Monte Carlo) or is refused (fixed
+    rank); both are listed."""
+    import numpy as np
+
     from paper_1412_2293_gb300 import inputs
-    from paper_1412_2293_gb300.server import GpuExecutor, Server, run_stream
-    specs = [("qft", 24, "statevec", 256, 0), ("qft", 26, "statevec", 128, 0), ("qft", 28, "statevec", 128, 0),
-             ("grover", 24, "statevec", 64, 0), ("qft", 24, "fixed_rank", 1, 4)]
-    jobs = []
-    for i, (circ, n, mode, traj, rank) in enumerate(specs):
-        iters = min(inputs.grover_iterations(n), 16) if circ == "grover" else 0
-        jobs.append(inputs.Job(i, 0.001 * i, circ, n, mode, traj, rank, 1e-3, inputs.DEFAULT_SEED + i, iters))
-    srv = Server(GpuExecutor(workers=2), max_members=1024)
+    from paper_1412_2293_gb300.server import GpuExecutor, Server, estimate_seconds, run_stream
+    jobs = inputs.draw_job_stream(num_jobs, rate_per_s, seed=inputs.DEFAULT_SEED + 2, n_range=(12, 28),
+                                  log2_traj_range=(6, 12), max_rank=8)
+    srv = Server(GpuExecutor(workers=workers), max_members=1024, limit_s=limit_s)
     try:
-        res, stats = run_stream(jobs, srv, time_scale=1.0, timeout=600)
-        budget = srv.sched.budget
+        res, stats = run_stream(jobs, srv, time_scale=1.0, timeout=900)
+        budget, units = srv.sched.budget, srv.sched._uid
     finally:
         srv.close()
-    per_job = {f"{j.circuit}_n{j.n}_{'mc' if j.mode == 'statevec' else 'rank'}": {
-        "trajectories": j.trajectories, "rank": j.rank, "latency_s": round(res[j.job_id].latency, 3),
-        "mean_fidelity": float(sum(res[j.job_id].fidelities) / len(res[j.job_id].fidelities))} for j in jobs}
-    return {"jobs": per_job, "span_s": round(stats["span_s"], 3), "circuits": stats["circuits"],
-            "hbm_budget_GiB": round(budget / 2 ** 30, 1), "peak_budget_used_GiB": round(stats["peak_budget_used"] / 2 ** 30, 1),
-            "largest_state_GiB_per_trajectory": 2 ** 28 * 8 / 2 ** 30}
+    byid = {j.job_id: j for j in jobs}
+    shape = lambda j: (f"{j.circuit} n={j.n} " + (f"T={j.trajectories}" if j.mode == "statevec" else f"rank {j.rank}"))
+    served = [byid[i] for i in res]
+    lat = {m: [res[j.job_id].latency for j in served if j.mode == m] for m in ("statevec", "fixed_rank")}
+    pct = lambda v, q: round(float(np.percentile(v, q)), 3) if v else None
+    return {"stream": "n 12..28, MC 2^6..2^12 trajectories c64, fixed rank r 1..8 c128, Grover iterations "
+                      "capped at 16, e log-uniform [1e-4, 1e-2]",
+            "jobs_submitted": len(jobs), "jobs_served": stats["jobs"], "circuits": stats["circuits"],
+            "span_s": round(stats["span_s"], 3), "circuits_per_s": round(stats["circuits_per_s"], 1),
+            "jobs_per_s": round(stats["jobs_per_s"], 3),
+            "latency_p50_s": round(stats["latency_p50_s"], 3), "latency_p99_s": round(stats["latency_p99_s"], 3),
+            "mc_latency_p50_p99_s": [pct(lat["statevec"], 50), pct(lat["statevec"], 99)],
+            "fixed_rank_latency_p50_p99_s": [pct(lat["fixed_rank"], 50), pct(lat["fixed_rank"], 99)],
+            "served_n_range": [min(j.n for j in served), max(j.n for j in served)] if served else None,
+            "served_trajectories_max": max((len(res[j.job_id].fidelities) for j in served if j.mode == "statevec"),
+                                           default=0),
+            "limit_s": limit_s,
+            "reduced": {shape(byid[i]): {"served_trajectories": t, "estimate_s": round(estimate_seconds(byid[i]), 1)}
+                        for i, (_, t) in stats["reduced"].items()},
+            "refused": {shape(byid[i]): why for i, why in stats["refused"].items()},
+            "launch_units": units, "hbm_budget_GiB": round(budget / 2 ** 30, 1),
+            "peak_budget_used_GiB": round(stats["peak_budget_used"] / 2 ** 30, 1),
+            "per_job": {f"{j.job_id}: {shape(j)}": {
+                "latency_s": round(res[j.job_id].latency, 3), "estimate_s": round(estimate_seconds(j), 2),
+                "served_trajectories": len(res[j.job_id].fidelities) if j.mode == "statevec" else None,
+                "mean_fidelity": float(np.mean(res[j.job_id].fidelities))} for j in served}}
 
 
 # ------------------------------------------------------------------ density / fixed rank

@@ -6,7 +6,11 @@ T trajectories (Sec. 2: complex64, one fidelity per trajectory) or through
 the fixed-rank density matrix (Sec. 3.2: complex128, rank r).
 
 * Admission: jobs wait until their device memory fits an HBM budget
-  (cudaMemGetInfo at start minus a reserve, or a given byte count).
+  (cudaMemGetInfo at start minus a reserve, or a given byte count).  With a
+  per-request limit on estimated device time (`limit_s`), a Monte Carlo job
+  above it runs the largest power-of-two number of trajectories (at least
+  MIN_TRAJECTORIES) that fits, and says so in its result; a fixed-rank job
+  above it is refused with the estimate as the reason.
 * Batching: Monte Carlo trajectories of every pending job with the same
   shape (circuit, n, Grover iteration count) are packed into one launch of
   one plan; a batch member carries its own job's noise level, key, trajectory
@@ -25,6 +29,7 @@ CPU with a fake executor; `GpuExecutor` does the CUDA work through the C ABI.
 from __future__ import annotations
 
 import collections
+import dataclasses
 import math
 import threading
 import time
@@ -65,7 +70,7 @@ class Unit:
 
 @dataclass
 class JobState:
-    job: inputs.Job
+    job: inputs.Job                   # as served (trajectories possibly reduced by the limit)
     arrival: float
     next_traj: int = 0                # MC: first trajectory not yet scheduled
     done_traj: int = 0
@@ -73,6 +78,8 @@ class JobState:
     finish: Optional[float] = None
     ref_bytes: int = 0                # MC: the ideal reference, held from first launch to completion
     ref_charged: bool = False
+    requested: int = 0                # trajectories the request asked for
+    progress: float = 0.0             # when the job last had a unit issued (its arrival before)
 
 
 def mc_key(job: inputs.Job) -> Tuple:
@@ -103,6 +110,41 @@ def rank_bytes(n: int, r: int = RANK_MAX) -> int:
     return (r + min(32, 8 * r)) * N * C128_BYTES + N * 256 + N * C128_BYTES
 
 
+# Device-time model of a request (seconds).  Monte Carlo: the fused passes
+# read and write every trajectory's state once per pass at an effective
+# MC_BYTES_PER_S (complex64); a pass holds the gates of one window, so the
+# QFT takes ceil(n / 10) passes and Grover's search that many per layer of
+# Hadamards (1 + 2 x iterations layers, the flips between them end a pass).
+# Fixed rank: per channel and amplitude, RANK_S_PER_AMP + r RANK_S_PER_AMP_R
+# seconds (expansion, FP64 Gram matrix, eigensolver and projection over
+# K r <= 32 columns, complex128; fitted to the QFT at n = 20..24, r = 1..8).
+# Estimates for admission only; a job's latency is measured.
+MC_BYTES_PER_S = 4.0e12
+RANK_S_PER_AMP = 0.2e-9
+RANK_S_PER_AMP_R = 0.47e-9
+MIN_TRAJECTORIES = 64
+
+
+def job_gate_counts(job: inputs.Job) -> Tuple[int, int]:
+    """(gates, noisy gates) of a job's circuit."""
+    n = job.n
+    if job.circuit == "grover":
+        return n + job.iterations * (2 + 2 * n), n + 2 * n * job.iterations
+    return n + n * (n - 1) // 2, n + n * (n - 1) // 2
+
+
+def estimate_passes(job: inputs.Job) -> int:
+    per_layer = -(-job.n // 10)
+    return per_layer * (1 + 2 * job.iterations) if job.circuit == "grover" else per_layer
+
+
+def estimate_seconds(job: inputs.Job, trajectories: Optional[int] = None) -> float:
+    if job.mode == "fixed_rank":
+        return job_gate_counts(job)[1] * float(1 << job.n) * (RANK_S_PER_AMP + job.rank * RANK_S_PER_AMP_R)
+    t = job.trajectories if trajectories is None else trajectories
+    return t * float(1 << job.n) * C64_BYTES * 2 * estimate_passes(job) / MC_BYTES_PER_S
+
+
 def bucket_for(members: int, lo: int, hi: int) -> int:
     b = lo
     while b < members:
@@ -125,13 +167,18 @@ class Scheduler:
     so that launches of one shape reuse cached handles and plans."""
 
     def __init__(self, budget_bytes: int, max_members: int = 4096, min_bucket: int = 16,
-                 starve_s: float = 2.0):
+                 starve_s: float = 2.0, limit_s: Optional[float] = None, share: float = 0.5):
         if max_members & (max_members - 1) or min_bucket & (min_bucket - 1) or min_bucket > max_members:
             raise ValueError("min_bucket and max_members must be powers of two, min_bucket <= max_members")
         self.budget = int(budget_bytes)
+        self.limit_s = limit_s                # per-request limit on estimated device seconds, or None
+        self.refused: Dict[int, str] = {}     # job id -> reason
+        self.reduced: Dict[int, Tuple[int, int]] = {}   # job id -> (requested, served) trajectories
         self.max_members = max_members
         self.min_bucket = min_bucket
         self.starve_s = starve_s              # after this wait the oldest job stops backfilling
+        self.share = share                    # most of the budget one shape holds while others wait
+        self.key_used: Dict[Tuple, int] = collections.defaultdict(int)
         self.used = 0
         self.jobs: Dict[int, JobState] = {}
         self.order: List[int] = []            # job ids in arrival order with work left
@@ -148,19 +195,44 @@ class Scheduler:
             return rank_bytes(job.n)
         return member_bytes(job.n) * self.min_bucket + (1 << job.n) * C64_BYTES
 
-    def submit(self, job: inputs.Job, now: float) -> None:
+    def admit(self, job: inputs.Job) -> Tuple[Optional[inputs.Job], str]:
+        """The job as it will run under the per-request limit, or (None, reason)."""
+        if self.limit_s is None:
+            return job, ""
+        est = estimate_seconds(job)
+        if est <= self.limit_s:
+            return job, ""
+        if job.mode == "statevec":
+            t = job.trajectories
+            while t > MIN_TRAJECTORIES and estimate_seconds(job, t) > self.limit_s:
+                t //= 2
+            if estimate_seconds(job, t) <= self.limit_s:
+                return dataclasses.replace(job, trajectories=t), ""
+        return None, f"estimated {est:.1f} s of device time, limit {self.limit_s:.1f} s"
+
+    def submit(self, job: inputs.Job, now: float) -> bool:
+        """Queue a job; False when the per-request limit refuses it."""
         if job.mode not in ("statevec", "fixed_rank") or job.trajectories < 1:
             raise ValueError(f"job {job.job_id}: unsupported mode {job.mode!r}")
-        if job.job_id in self.jobs:
+        if job.job_id in self.jobs or job.job_id in self.refused:
             raise ValueError(f"job {job.job_id} submitted twice")
         if self.min_bytes(job) > self.budget:
             raise MemoryError(f"job {job.job_id} needs {self.min_bytes(job)} bytes, more than the budget {self.budget}")
-        st = JobState(job, now)
+        requested = job.trajectories
+        served, reason = self.admit(job)
+        if served is None:
+            self.refused[job.job_id] = reason
+            return False
+        job = served
+        if job.trajectories != requested:
+            self.reduced[job.job_id] = (requested, job.trajectories)
+        st = JobState(job, now, requested=requested, progress=now)
         if job.mode == "statevec":
             st.fidelities = np.full(job.trajectories, np.nan)
             st.ref_bytes = (1 << job.n) * C64_BYTES
         self.jobs[job.job_id] = st
         self.order.append(job.job_id)
+        return True
 
     def pending(self) -> int:
         return len(self.order)
@@ -172,21 +244,31 @@ class Scheduler:
     def next_unit(self, now: float = 0.0) -> Optional[Unit]:
         """The next unit that fits the budget, oldest job first, or None.
 
+        While other jobs wait, a shape that already has a unit in flight, or a
+        job past its first wave, holds at most `share` of the budget, so a job
+        that runs in many waves leaves room for later arrivals.
         Younger jobs backfill memory the oldest cannot use yet, until the
-        oldest has waited `starve_s` seconds: then nothing new starts before it."""
+        oldest has made no progress (no unit issued) for `starve_s` seconds:
+        then nothing new starts before it."""
         free = self.budget - self.used
+        others = len(self.order) > 1
         for pos, jid in enumerate(list(self.order)):
             st = self.jobs[jid]
             job = st.job
+            key = rank_key(job) if job.mode == "fixed_rank" else mc_key(job)
+            # while others wait, a shape with a unit in flight, or the later waves
+            # of a job, take at most `share` of the budget
+            capped = others and (self.key_used[key] > 0 or st.next_traj > 0)
+            avail = min(free, int(self.share * self.budget) - self.key_used[key]) if capped else free
             if job.mode == "fixed_rank":
-                made = self._rank_unit(rank_key(job), free)
+                made = self._rank_unit(key, avail)
                 if made is not None:
-                    return self._issue(made, [])
+                    return self._issue(made, [], now)
             else:
-                made = self._mc_unit(mc_key(job), free)
+                made = self._mc_unit(key, avail)
                 if made is not None:
-                    return self._issue(*made)
-            if pos == 0 and now - st.arrival > self.starve_s:
+                    return self._issue(*made, now)
+            if pos == 0 and now - st.progress > self.starve_s:
                 return None
         return None
 
@@ -244,10 +326,13 @@ class Scheduler:
                 self.order.remove(sl.job_id)
         return Unit("mc", key, slices, members, members * per), charge
 
-    def _issue(self, unit: Unit, charge: List[int]) -> Unit:
+    def _issue(self, unit: Unit, charge: List[int], now: float = 0.0) -> Unit:
         self._uid += 1
         unit.uid = self._uid
         self.used += unit.bytes
+        self.key_used[unit.key] += unit.bytes
+        for sl in unit.slices:
+            self.jobs[sl.job_id].progress = now
         for jid in charge:
             st = self.jobs[jid]
             st.ref_charged = True
@@ -263,6 +348,7 @@ class Scheduler:
         """Record a finished unit; returns the ids of jobs that are now complete."""
         self.in_flight.pop(unit.uid)
         self.used -= unit.bytes
+        self.key_used[unit.key] -= unit.bytes
         done = []
         for sl, res in zip(unit.slices, results):
             st = self.jobs[sl.job_id]
@@ -502,7 +588,8 @@ class Server:
     """Request loop: admission, batching and overlapped execution of jobs."""
 
     def __init__(self, executor=None, workers: int = 4, budget_bytes: Optional[int] = None,
-                 reserve_bytes: int = 8 << 30, max_members: int = 4096, min_bucket: int = 16):
+                 reserve_bytes: int = 8 << 30, max_members: int = 4096, min_bucket: int = 16,
+                 limit_s: Optional[float] = None):
         if executor is None:
             executor = GpuExecutor(workers)
         if budget_bytes is None:
@@ -510,7 +597,7 @@ class Server:
             free, _ = torch.cuda.mem_get_info()
             budget_bytes = max(free - reserve_bytes - getattr(executor, "cache_bytes", 0), 1 << 28)
         self.ex = executor
-        self.sched = Scheduler(budget_bytes, max_members, min_bucket)
+        self.sched = Scheduler(budget_bytes, max_members, min_bucket, limit_s=limit_s)
         self.lock = threading.Condition()
         self.t0 = time.perf_counter()
         self.results: Dict[int, JobResult] = {}
@@ -525,10 +612,12 @@ class Server:
     def now(self) -> float:
         return time.perf_counter() - self.t0
 
-    def submit(self, job: inputs.Job) -> None:
+    def submit(self, job: inputs.Job) -> bool:
+        """Queue a job; False when the per-request limit refuses it."""
         with self.lock:
-            self.sched.submit(job, self.now())
+            ok = self.sched.submit(job, self.now())
             self.lock.notify_all()
+        return ok
 
     def _dispatch(self):
         while True:
@@ -607,12 +696,13 @@ def run_stream(jobs: List[inputs.Job], server: Server, time_scale: float = 1.0, 
             time.sleep(delay)
         server.submit(job)
     results = server.drain(timeout)
-    lat = np.array([r.latency for r in results.values()])
-    span = max(r.finish for r in results.values()) - t_start
+    lat = np.array([r.latency for r in results.values()]) if results else np.zeros(1)
+    span = (max(r.finish for r in results.values()) - t_start) if results else 0.0
     circuits = sum(len(r.fidelities) for r in results.values())
     stats = {"jobs": len(results), "circuits": int(circuits), "span_s": span,
              "circuits_per_s": circuits / span if span > 0 else math.inf,
              "jobs_per_s": len(results) / span if span > 0 else math.inf,
              "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
-             "peak_budget_used": server.sched.peak_used, "budget": server.sched.budget}
+             "peak_budget_used": server.sched.peak_used, "budget": server.sched.budget,
+             "refused": dict(server.sched.refused), "reduced": dict(server.sched.reduced)}
     return results, stats

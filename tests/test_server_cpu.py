@@ -203,3 +203,65 @@ def test_fixed_rank_jobs_of_one_shape_share_a_launch():
     s.complete(u, [np.zeros(1)] * 5, 1.0)
     s.complete(u2, [np.zeros(1)], 1.0)
     assert sorted(s.finished) == [0, 1, 2, 3, 4, 5] and s.used == 0
+
+
+def test_per_request_limit_reduces_monte_carlo_jobs_and_refuses_fixed_rank():
+    """A Monte Carlo job over the limit runs the largest power-of-two number of
+    trajectories that fits it (at least 64); a fixed-rank job over it is
+    refused; jobs under it are untouched."""
+    from paper_1412_2293_gb300.server import MIN_TRAJECTORIES, estimate_seconds
+    limit = 2.0
+    s = Scheduler(1 << 50, max_members=4096, limit_s=limit)
+    small = job(0, n=12, traj=256)
+    big = job(1, n=26, traj=4096)
+    huge = job(2, n=28, traj=4096, circuit="grover", iters=16)
+    rank_big = job(3, n=26, mode="fixed_rank", rank=8)
+    rank_small = job(4, n=14, mode="fixed_rank", rank=2)
+    assert estimate_seconds(small) < limit < estimate_seconds(big)
+    assert s.submit(small, 0.0) and s.submit(big, 0.0) and s.submit(rank_small, 0.0)
+    served = s.jobs[1].job.trajectories
+    assert served < 4096 and served & (served - 1) == 0 and served >= MIN_TRAJECTORIES
+    assert estimate_seconds(big, served) <= limit < estimate_seconds(big, 2 * served)
+    assert s.reduced == {1: (4096, served)} and s.jobs[1].requested == 4096
+    assert len(s.jobs[1].fidelities) == served and s.jobs[0].job.trajectories == 256
+    # even 64 trajectories of the capped Grover search at n = 28 exceed the limit
+    assert estimate_seconds(huge, MIN_TRAJECTORIES) > limit
+    assert not s.submit(huge, 0.0) and 2 in s.refused
+    assert not s.submit(rank_big, 0.0) and "limit" in s.refused[3]
+    assert sorted(s.jobs) == [0, 1, 4] and s.pending() == 3
+    with pytest.raises(ValueError):
+        s.submit(rank_big, 0.0)                                  # a refused id cannot come back
+
+
+def test_server_reports_refused_and_reduced_jobs():
+    jobs = [job(0, n=12, traj=64), job(1, n=26, traj=4096, arrival=0.001),
+            job(2, n=26, mode="fixed_rank", rank=8, arrival=0.002)]
+    ex = FakeExecutor(workers=2, sec_per_member=1e-7)
+    srv = Server(ex, budget_bytes=1 << 50, max_members=4096, limit_s=2.0)
+    try:
+        results, stats = run_stream(jobs, srv, time_scale=1.0, timeout=60)
+    finally:
+        srv.close()
+    assert sorted(results) == [0, 1] and list(stats["refused"]) == [2]
+    req, served = stats["reduced"][1]
+    assert req == 4096 and len(results[1].fidelities) == served < 4096
+    np.testing.assert_array_equal(results[1].fidelities, [value(1, t) for t in range(served)])
+
+
+def test_a_job_in_many_waves_leaves_room_for_later_arrivals():
+    """A job whose trajectories fill the budget several times over runs in
+    waves; once other jobs wait, its later waves take at most half the
+    budget, so a small job arriving after it starts before it is done."""
+    per = member_bytes(16)
+    s = Scheduler(64 * per + (1 << 16) * 8 * 4, max_members=64, min_bucket=16, starve_s=100.0)
+    s.submit(job(0, n=16, traj=1024), 0.0)
+    u0 = s.next_unit(0.0)
+    assert u0.members == 64                          # the first wave takes what is free
+    s.submit(job(1, n=12, traj=64), 0.1)
+    assert s.next_unit(0.1) is None                  # no room yet
+    s.complete(u0, [np.zeros(64)], 0.2)
+    u2 = s.next_unit(0.2)
+    assert [sl.job_id for sl in u2.slices] == [0] and u2.members == 32
+    u3 = s.next_unit(0.2)
+    assert [sl.job_id for sl in u3.slices] == [1]    # the small job runs beside the big one
+    assert s.jobs[0].next_traj < 1024 and s.used <= s.budget
