@@ -1219,11 +1219,21 @@ cudaError_t set_smem_attrs(size_t esize) {
 // written, conjugated and transposed, over the tile below it (the factor of
 // (y, x) is the conjugate of that of (x, y)), through shared memory so every
 // access is coalesced: half the reads and half the arithmetic.
+// A thread keeps one column y and takes rows x = 8 k + warp, so a row is the
+// same across a warp.  The factor u(x) conj(u(y)) q^popcount(m(x) ^ m(y)) is
+// formed only as far as the row and column need: a trivial row (u = 1, no
+// noisy gate) takes the column's own factor conj(u(y)) q^popcount(m(y)),
+// computed once per tile; a non-trivial row over columns that are all
+// trivial takes u(x) q^popcount(m(x)); only pairs where both are non-trivial
+// pay the full product.  Pairs of trivial rows and columns are skipped.
 template <typename R>
 __global__ void __launch_bounds__(256) k_dm_diag_block_herm(cplx<R>* __restrict__ rho, int n,
                                                             const cplx<R>* __restrict__ u,
                                                             const uint32_t* __restrict__ mask, QPow<R> qp) {
   __shared__ cplx<R> tile[32][33];
+  __shared__ R qv[33];
+  if (threadIdx.x < 33) qv[threadIdx.x] = qp.v[threadIdx.x];
+  __syncthreads();
   const uint64_t N = 1ull << n;
   const uint64_t TT = N / 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -1233,20 +1243,34 @@ __global__ void __launch_bounds__(256) k_dm_diag_block_herm(cplx<R>* __restrict_
     const uint64_t y = by * 32 + tx;
     const uint32_t my = mask[y];
     const cplx<R> uy = u[y];
+    const uint32_t myb = my & ~kDmTrivial;
+    const bool ytriv = (my & kDmTrivial) != 0;
+    const bool cols_trivial = __all_sync(0xffffffffu, ytriv);
+    const R dy = qv[__popc(myb)];
+    const cplx<R> colf = mk<R>(uy.x * dy, -uy.y * dy);  // factor of a trivial row
     cplx<R> o[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const uint64_t x = bx * 32 + ty + 8 * k;
-      const uint32_t mx = mask[x];
+      const uint32_t mx = mask[x];                      // the same across the warp
       const cplx<R> r = rho[x * N + y];
       o[k] = r;
-      if (!(mx & my & kDmTrivial)) {
+      cplx<R> f;
+      if (mx & kDmTrivial) {
+        if (ytriv) continue;
+        f = colf;
+      } else {
         const cplx<R> ux = u[x];
-        const R d = qp.v[__popc((mx ^ my) & ~kDmTrivial)];
-        const R fr = (ux.x * uy.x + ux.y * uy.y) * d, fi = (ux.y * uy.x - ux.x * uy.y) * d;
-        o[k] = mk<R>(r.x * fr - r.y * fi, r.x * fi + r.y * fr);
-        rho[x * N + y] = o[k];
+        if (cols_trivial) {
+          const R dx = qv[__popc(mx)];
+          f = mk<R>(ux.x * dx, ux.y * dx);
+        } else {
+          const R d = qv[__popc(mx ^ myb)];
+          f = mk<R>((ux.x * uy.x + ux.y * uy.y) * d, (ux.y * uy.x - ux.x * uy.y) * d);
+        }
       }
+      o[k] = mk<R>(r.x * f.x - r.y * f.y, r.x * f.y + r.y * f.x);
+      rho[x * N + y] = o[k];
     }
     if (bx == by) continue;                              // uniform across the block
 #pragma unroll
