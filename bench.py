@@ -176,6 +176,7 @@ def run_ours(args, rank, world, local_rank):
         qs.qs_plan_set_config(p, lo, hi, h)
         tune_ms = (-1.0, -1.0)
     else:
+        qs.qs_set_basis_state(h, x0)                     # timed as the steps run: start created by the first pass
         tune_ms = qs.qs_plan_autotune(p, 2, e, seed, h)
     kernel_cfg = qs.qs_plan_get_config(p, h)
     window = qs.qs_plan_get_window(p, h)
@@ -589,6 +590,7 @@ def extra_rows(h, n, T, esize, stream, peaks):
                             "frac_of_floor": round(floor / msq, 4), "fidelity_mean": float(fm[m].mean())}
         row["fidelity_max_abs_diff_vs_m10"] = max(float(np.abs(fm[m] - fm[10]).max()) for m in (11, 12))
         pq = qs.qs_plan_create(hq, pcirc.to_gates(opsq))
+        qs.qs_set_basis_state(hq, xq)
         tl, th = qs.qs_plan_autotune(pq, 2, Wq.e, Wq.seed, hq)
         row["autotuned"] = {"window": qs.qs_plan_get_window(pq, hq), "config": list(qs.qs_plan_get_config(pq, hq)),
                             "pass_ms": [round(tl, 4), round(th, 4)]}
@@ -611,6 +613,7 @@ def extra_rows(h, n, T, esize, stream, peaks):
         qs.qs_set_reference_from(hq, refq, 0)
         qs.qs_destroy(refq)
         pq = qs.qs_plan_create(hq, pcirc.to_gates(opsq))
+        qs.qs_set_basis_state(hq, xq)
         qs.qs_plan_autotune(pq, 1, eq, Wq.seed, hq)
         for _ in range(2):
             qs.qs_set_basis_state(hq, xq)

@@ -352,7 +352,9 @@ qs_status qs_plan_destroy(qs_plan p);
 
 /* Time each kernel of one plan run with CUDA events on the handle's stream
  * (eager launches, `reps` runs averaged; the state is modified as by
- * qs_plan_run).  ms[i] = mean duration of launch i of a run, kinds[i] =
+ * qs_plan_run; a basis start set by qs_set_basis_state(s) and not yet used is
+ * created by the first pass of every profiled run, as plan runs do, and is
+ * used up afterwards).  ms[i] = mean duration of launch i of a run, kinds[i] =
  * 0 noise/parameter precompute, 1 low-window pass, 2 high-window pass,
  * 3 single-gate step (all kernels of the step together), 4 density-matrix
  * run of diagonal channels (one sweep); at most `cap`
@@ -408,7 +410,10 @@ qs_status qs_plan_get_config(qs_plan p, int* low_cfg, int* high_cfg);
  * pass times in ms to best_ms[0] (low) and best_ms[1] (high) (-1 where the
  * plan has no pass of that geometry; best_ms may be NULL).
  * qs_plan_get_window then reports the width chosen.  The runs overwrite the
- * state: set the start state afterwards.  Synchronises. */
+ * state; a basis start set before the call (qs_set_basis_state(s)) is
+ * created by the first pass of every profiled run, so the passes are timed
+ * as the plan's runs from that start will execute them, and it is still the
+ * pending start afterwards.  Synchronises. */
 qs_status qs_plan_autotune(qs_plan p, int reps, double e, uint64_t seed, double* best_ms);
 
 /* ------------------------------------------------------------ utilities */

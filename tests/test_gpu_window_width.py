@@ -250,3 +250,23 @@ def test_full_window_programs_match_oracle(m):
     np.testing.assert_allclose(fids[m], fids[10], rtol=0, atol=2e-6)
     want = ocirc.run_trajectory(n, ops, xs[batch - 1], e, SEED, batch - 1)
     assert_amplitudes_close(got[batch - 1], want, qs.QS_C64)
+
+
+def test_autotune_times_runs_from_the_pending_start_and_keeps_it():
+    """With a basis start set before autotuning, every profiled run creates it
+    in its first pass; afterwards the start is still pending, so the next run
+    begins from it."""
+    n, batch, e, x0 = 15, 8, 0.02, 12345
+    ops = inputs.qft_circuit(n)
+    ideal = ocirc.ideal_state(n, ops, x0)
+    with Handle(n, batch, 0, qs.QS_STATEVEC, qs.QS_C64) as h:
+        qs.qs_set_reference(h, np.asarray(ideal))
+        p = qs.qs_plan_create(h, pcirc.to_gates(ops))
+        qs.qs_set_basis_state(h, x0)
+        qs.qs_plan_autotune(p, 1, e, SEED, h)
+        f = qs.qs_plan_run_fidelity(p, e, SEED, 0, h)         # no new start: the pending one
+        got = qs.qs_get_state(h).reshape(batch, -1)
+        qs.qs_plan_destroy(p)
+    want = ocirc.run_trajectory(n, ops, x0, e, SEED, batch - 1)
+    assert_amplitudes_close(got[batch - 1], want, qs.QS_C64)
+    assert abs(f[batch - 1] - osv.fidelity(ideal, want)) <= 1e-5
