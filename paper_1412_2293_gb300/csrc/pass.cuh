@@ -385,27 +385,54 @@ __device__ __forceinline__ void third_shear_reg(cplx<R> (&a)[kAmps], const R* m)
 // thread's bits then 2^RJ over the register bits (the product over a set of
 // bits splits that way), so a tile reads a few hundred entries per table
 // instead of up to 2^11, and the register part is the same for every lane.
-template <typename R, int RJ, int SH, bool SPLIT = false>
+// TRANS (high window): the entry (tbits, q) is stored at tbits 2^RJ + q, the
+// register index fastest.  Where a thread's factors for q and q + 1 sit side
+// by side (register-bit index fastest: SH = 0, SPLIT or TRANS) complex64
+// reads them with one 16-byte load, half the loads of the table.
+template <typename R, int RJ, int SH, bool SPLIT = false, bool TRANS = false>
 __device__ __forceinline__ void dwin_reg(cplx<R> (&a)[kAmps], const R* T, int tbits) {
   constexpr int Q = 1 << RJ;
   constexpr bool kSplit = SPLIT && SH > 0;
+  constexpr bool kTrans = TRANS && !kSplit && SH > 0;
+  constexpr bool kPair = sizeof(R) == 4 && Q >= 2 && (SH == 0 || kSplit || kTrans);
   cplx<R> flo = mk<R>(R(1), R(0));
   if constexpr (kSplit) flo = ld_c(T + 2 * tbits);
-  // factor q multiplies the registers with bit RJ set and low bits q; each
-  // factor is consumed right after its load (few live registers)
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    cplx<R> f;
-    if constexpr (kSplit) {
-      f = q == 0 ? flo : pmul<R>(ld_c(T + 2 * ((1 << SH) + q)), flo);
-    } else {
-      const int idx = SH ? (tbits + (q << SH)) : q;
-      f = ld_c(T + 2 * idx);
-    }
+  // the factors over q of this thread: one row of the table
+  const R* row = kSplit ? T + 2 * (1 << SH) : (kTrans ? T + 2 * (tbits << RJ) : T);
+  auto apply = [&](int q, cplx<R> f) {
 #pragma unroll
     for (int hi = 0; hi < kAmps / (2 * Q); ++hi) {
       const int r = q | Q | (hi << (RJ + 1));
       a[r] = pmul<R>(f, a[r]);
+    }
+  };
+  if constexpr (kPair) {
+#pragma unroll
+    for (int q = 0; q < Q; q += 2) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(row + 2 * q));
+      cplx<R> f0 = mk<R>(v.x, v.y), f1 = mk<R>(v.z, v.w);
+      if constexpr (kSplit) {
+        f0 = q == 0 ? flo : pmul<R>(f0, flo);
+        f1 = pmul<R>(f1, flo);
+      }
+      apply(q, f0);
+      apply(q + 1, f1);
+    }
+  } else {
+    // factor q multiplies the registers with bit RJ set and low bits q; each
+    // factor is consumed right after its load (few live registers)
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      cplx<R> f;
+      if constexpr (kSplit) {
+        f = q == 0 ? flo : pmul<R>(ld_c(row + 2 * q), flo);
+      } else if constexpr (kTrans) {
+        f = ld_c(row + 2 * q);
+      } else {
+        const int idx = SH ? (tbits + (q << SH)) : q;
+        f = ld_c(T + 2 * idx);
+      }
+      apply(q, f);
     }
   }
 }
@@ -464,26 +491,26 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 }
 
 // ---------------------------------------------------------------- segments
-template <typename R, int J, int SH, bool SPLIT>
+template <typename R, int J, int SH, bool SPLIT, bool TRANS>
 __device__ __forceinline__ void seg_step(cplx<R> (&a)[kAmps], const Seg& sg, const R* P, int tbits, bool stable) {
   if ((sg.dense >> J) & 1) dense_reg<R, J>(a, P + sg.doff[J], (sg.real >> J) & 1, stable);
-  if ((sg.dwin >> J) & 1) dwin_reg<R, J, SH, SPLIT>(a, P + sg.woff[J], tbits);
+  if ((sg.dwin >> J) & 1) dwin_reg<R, J, SH, SPLIT, TRANS>(a, P + sg.woff[J], tbits);
 }
 
-template <typename R, int SH, bool SPLIT = false>
+template <typename R, int SH, bool SPLIT = false, bool TRANS = false>
 __device__ __forceinline__ void run_seg(cplx<R> (&a)[kAmps], const Seg& sg, const R* P, int tbits, bool stable) {
   if (sg.desc) {
-    seg_step<R, 4, SH, SPLIT>(a, sg, P, tbits, stable);
-    seg_step<R, 3, SH, SPLIT>(a, sg, P, tbits, stable);
-    seg_step<R, 2, SH, SPLIT>(a, sg, P, tbits, stable);
-    seg_step<R, 1, SH, SPLIT>(a, sg, P, tbits, stable);
-    seg_step<R, 0, SH, SPLIT>(a, sg, P, tbits, stable);
+    seg_step<R, 4, SH, SPLIT, TRANS>(a, sg, P, tbits, stable);
+    seg_step<R, 3, SH, SPLIT, TRANS>(a, sg, P, tbits, stable);
+    seg_step<R, 2, SH, SPLIT, TRANS>(a, sg, P, tbits, stable);
+    seg_step<R, 1, SH, SPLIT, TRANS>(a, sg, P, tbits, stable);
+    seg_step<R, 0, SH, SPLIT, TRANS>(a, sg, P, tbits, stable);
   } else {
-    seg_step<R, 0, SH, SPLIT>(a, sg, P, tbits, stable);
-    seg_step<R, 1, SH, SPLIT>(a, sg, P, tbits, stable);
-    seg_step<R, 2, SH, SPLIT>(a, sg, P, tbits, stable);
-    seg_step<R, 3, SH, SPLIT>(a, sg, P, tbits, stable);
-    seg_step<R, 4, SH, SPLIT>(a, sg, P, tbits, stable);
+    seg_step<R, 0, SH, SPLIT, TRANS>(a, sg, P, tbits, stable);
+    seg_step<R, 1, SH, SPLIT, TRANS>(a, sg, P, tbits, stable);
+    seg_step<R, 2, SH, SPLIT, TRANS>(a, sg, P, tbits, stable);
+    seg_step<R, 3, SH, SPLIT, TRANS>(a, sg, P, tbits, stable);
+    seg_step<R, 4, SH, SPLIT, TRANS>(a, sg, P, tbits, stable);
   }
 }
 
@@ -507,19 +534,19 @@ constexpr int prog_wide(int dense_a, int dwin_a, int dense_c, int dwin_c, int de
 }
 __host__ __device__ constexpr int prog_field(int prog, int k) { return (prog >> (5 * k)) & 31; }
 
-template <typename R, int SH, int D, int W, int J, bool SPLIT>
+template <typename R, int SH, int D, int W, int J, bool SPLIT, bool TRANS>
 __device__ __forceinline__ void layer_step(cplx<R> (&a)[kAmps], const Seg& sg, const R* P, int tbits) {
   if constexpr (((D >> J) & 1) != 0) dense_real_reg<R, J>(a, P + sg.doff[J]);
-  if constexpr (((W >> J) & 1) != 0) dwin_reg<R, J, SH, SPLIT>(a, P + sg.woff[J], tbits);
+  if constexpr (((W >> J) & 1) != 0) dwin_reg<R, J, SH, SPLIT, TRANS>(a, P + sg.woff[J], tbits);
 }
 
-template <typename R, int SH, int W, int D = 31, bool SPLIT = false>
+template <typename R, int SH, int W, int D = 31, bool SPLIT = false, bool TRANS = false>
 __device__ __forceinline__ void run_layer(cplx<R> (&a)[kAmps], const Seg& sg, const R* P, int tbits) {
-  layer_step<R, SH, D, W, 4, SPLIT>(a, sg, P, tbits);
-  layer_step<R, SH, D, W, 3, SPLIT>(a, sg, P, tbits);
-  layer_step<R, SH, D, W, 2, SPLIT>(a, sg, P, tbits);
-  layer_step<R, SH, D, W, 1, SPLIT>(a, sg, P, tbits);
-  layer_step<R, SH, D, W, 0, SPLIT>(a, sg, P, tbits);
+  layer_step<R, SH, D, W, 4, SPLIT, TRANS>(a, sg, P, tbits);
+  layer_step<R, SH, D, W, 3, SPLIT, TRANS>(a, sg, P, tbits);
+  layer_step<R, SH, D, W, 2, SPLIT, TRANS>(a, sg, P, tbits);
+  layer_step<R, SH, D, W, 1, SPLIT, TRANS>(a, sg, P, tbits);
+  layer_step<R, SH, D, W, 0, SPLIT, TRANS>(a, sg, P, tbits);
 }
 
 // ---------------------------------------------------------------- LOW pass
@@ -939,7 +966,7 @@ __global__ void __launch_bounds__(HighShape<COLB, M>::THREADS, NBUF == 1 ? 16 / 
       });
     };
     if constexpr (PROG != 0 && M == kWin) {   // the planner guarantees start stage A
-      run_layer<R, M - kRegBits, PROG & 31>(a, A.segs[0], P, tw);
+      run_layer<R, M - kRegBits, PROG & 31, 31, false, true>(a, A.segs[0], P, tw);
       exchange(0, 1);
       stage = 1;
       release();
@@ -964,7 +991,7 @@ __global__ void __launch_bounds__(HighShape<COLB, M>::THREADS, NBUF == 1 ? 16 / 
       with_stage<M>(stage, [&](auto SC) {
         constexpr int SS = decltype(SC)::value;
         constexpr int SH = stage_base(M, SS);
-        run_seg<R, SH, (M > kWin)>(a, sg, P, SS == 0 ? tw : (SS == 2 ? (tw & 31) : 0), A.stable != 0);
+        run_seg<R, SH, (M > kWin), true>(a, sg, P, SS == 0 ? tw : (SS == 2 ? (tw & 31) : 0), A.stable != 0);
         const int sh = c0 + SH;
         const uint64_t regmask = 31ull << sh;
         const Off fixed = tbits | (Off)col | ((Off)tile_base<M, SS>(tw) << c0);

@@ -80,6 +80,7 @@ struct Producer {
   int gate;               // DENSE / OUT: gate index
   int j;                  // DWIN: attach bit, table of 2^j entries; DENSE: window bit
   int sh;                 // DWIN: 0, or the table split into 2^sh + 2^(j-sh) entries (bits below sh, then the rest)
+  int tq;                 // DWIN: 0, or the entry for x stored at (x mod 2^tq) 2^(j-tq) + x / 2^tq (high passes)
   int real;               // DENSE: real matrix, stored as its shears (r0, r0, s1, s1)
   int contrib_start, contrib_count;
   uint32_t off;
@@ -335,11 +336,13 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
         }
         __syncthreads();
       }
-      for (int x = threadIdx.x; x < (1 << (hi - lo)); x += blockDim.x) {
-        out[o + 2 * x] = (R)tab[x].x;
-        out[o + 2 * x + 1] = (R)tab[x].y;
+      const int bits = hi - lo;
+      for (int x = threadIdx.x; x < (1 << bits); x += blockDim.x) {
+        const int at = p.tq > 0 ? ((x & ((1 << p.tq) - 1)) << (bits - p.tq)) | (x >> p.tq) : x;
+        out[o + 2 * at] = (R)tab[x].x;
+        out[o + 2 * at + 1] = (R)tab[x].y;
       }
-      o += 2u << (hi - lo);
+      o += ((2u << bits) + 3u) & ~3u;                  // each part starts 16-byte aligned
       __syncthreads();
     }
     ++w;
@@ -663,7 +666,7 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
   uint64_t locked = 0;                                  // window local bits with out terms
   int stage = -1;
   int dense_count = 0;
-  struct Dw { int j; std::vector<Contrib> cs; int sh; };
+  struct Dw { int j; std::vector<Contrib> cs; int sh; int tq; };
   std::vector<Dw> dwins;                                // indexed by producer order
   std::vector<std::pair<int, int>> out_gates;           // (attach, gate) in order
   std::vector<uint64_t> out_masks;
@@ -745,7 +748,10 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
           // windows above 10 qubits keep the table as its factors over the
           // thread's bits and the register bits of the stage
           const int sh = m > kWin ? stage_base(m, stage) : 0;
-          dwins.push_back(Dw{a, {Contrib{partner, rem[i]}}, sh});
+          // a high pass keeps a whole table register-index fastest: a lane's
+          // factors for neighbouring register values are adjacent
+          const int tq = (P->high && sh == 0) ? stage_base(m, stage) : 0;
+          dwins.push_back(Dw{a, {Contrib{partner, rem[i]}}, sh, tq});
           P->ops.push_back(x);
           table_entries += sh > 0 ? (1u << sh) + (1u << (a - sh)) : 1u << a;
         }
@@ -799,12 +805,15 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
       pr.kind = PD_DWIN;
       pr.j = d.j;
       pr.sh = d.sh;
+      pr.tq = d.tq;
       pr.contrib_start = (int)P->contribs.size();
       pr.contrib_count = (int)d.cs.size();
       for (auto& c : d.cs) P->contribs.push_back(c);
       pr.off = off;
       x.off = off;
-      off += d.sh > 0 ? (2u << d.sh) + (2u << (d.j - d.sh)) : 2u << d.j;
+      // parts rounded to 4 R units: every part starts 16-byte aligned (pair loads)
+      auto part = [](int bits) { return ((2u << bits) + 3u) & ~3u; };
+      off += d.sh > 0 ? part(d.sh) + part(d.j - d.sh) : part(d.j);
       prods.push_back(pr);
       ++P->num_dwin;
     }
