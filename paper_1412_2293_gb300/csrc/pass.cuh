@@ -484,6 +484,18 @@ __device__ __forceinline__ void apply_real_product(cplx<R> (&a)[kAmps], R c, con
   }
 }
 
+// sum_r conj(ref_r) a_r over a thread's 32 registers, in four interleaved
+// FP32 partials (chains of 8 instead of one of 32), added pairwise at the end
+template <typename R, typename F>
+__device__ __forceinline__ cplx<R> reg_dot(const cplx<R> (&a)[kAmps], F&& ref_at) {
+  cplx<R> acc[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) acc[k] = mk<R>(R(0), R(0));
+#pragma unroll
+  for (int r = 0; r < kAmps; ++r) acc[r & 3] = pdot<R>(acc[r & 3], ref_at(r), a[r]);
+  return mk<R>((acc[0].x + acc[1].x) + (acc[2].x + acc[3].x), (acc[0].y + acc[1].y) + (acc[2].y + acc[3].y));
+}
+
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -783,9 +795,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_pass_low(cplx<R>* __restrict_
         constexpr int ts = tile_step<M, SS>();
         if (A.fid) {
           const C* ref = static_cast<const C*>(A.ref) + mloc + tb;
-          C acc = mk<R>(R(0), R(0));
-#pragma unroll
-          for (int r = 0; r < kAmps; ++r) acc = pdot<R>(acc, __ldcg(ref + r * ts), a[r]);
+          const C acc = reg_dot<R>(a, [&](int r) { return __ldcg(ref + r * ts); });
           const double sre = warp_sum_d((double)acc.x), sim = warp_sum_d((double)acc.y);
           if (lane == 0) {
             const uint64_t slot = (member * (1ull << A.tile_shift) + (mloc >> M)) * G + wig;
@@ -1039,9 +1049,7 @@ __global__ void __launch_bounds__(HighShape<COLB, M>::THREADS, NBUF == 1 ? 16 / 
       const Off fixed = tbits + (Off)col + ((Off)tile_base<M, SS>(tw) << c0);
       if (A.fid) {
         const C* ref = static_cast<const C*>(A.ref) + fixed;
-        C acc = mk<R>(R(0), R(0));
-#pragma unroll
-        for (int r = 0; r < kAmps; ++r) acc = pdot<R>(acc, __ldcg(ref + ((Off)r << sh)), a[r]);
+        const C acc = reg_dot<R>(a, [&](int r) { return __ldcg(ref + ((Off)r << sh)); });
         const double sre = warp_sum_d((double)acc.x), sim = warp_sum_d((double)acc.y);
         if (lane == 0) { fid_red[0][warp] = sre; fid_red[1][warp] = sim; }
         __syncthreads();
