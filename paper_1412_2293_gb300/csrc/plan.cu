@@ -355,6 +355,8 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
 // attached to none) whose out-of-window bits are all set in o, times the
 // deferred real diagonal of bit a (the overall scale for a = m).  The pass
 // kernels read the m + 1 entries of their tile directly.
+constexpr int kOutPerThread = 64;    // out-factor entries per thread: a member's terms staged once per block
+
 template <typename R>
 __global__ void __launch_bounds__(256) k_out_table(cplx<R>* __restrict__ tab, const R* __restrict__ params, int stride,
                                                    const OutTerm* __restrict__ outs, OutStarts starts, int diag_off,
@@ -373,24 +375,28 @@ __global__ void __launch_bounds__(256) k_out_table(cplx<R>* __restrict__ tab, co
     fac[k] = mk<R>(P[t.off], P[t.off + 1]);
   }
   __syncthreads();
-  const uint64_t i = (uint64_t)(blockIdx.x % chunks) * blockDim.x + threadIdx.x;
-  if (i >= per) return;
-  const uint64_t o = i / (uint64_t)(m + 1);
-  const int a = (int)(i % (uint64_t)(m + 1));
-  // member-local out-of-window bits: o holds the bits below the window
-  // (wstart of them) and above it the bits above the window
-  const uint64_t fixed = ((o >> wstart) << (wstart + m)) | (o & ((1ull << wstart) - 1));
-  R re = R(1), im = R(0);
-  for (int k = starts.v[a]; k < starts.v[a + 1]; ++k) {
-    if ((fixed & masks[k]) == masks[k]) {
-      const cplx<R> f = fac[k];
-      const R nr = re * f.x - im * f.y;
-      im = re * f.y + im * f.x;
-      re = nr;
+  // the block's chunk of the member's entries: kOutPerThread per thread
+  const uint64_t span = (uint64_t)blockDim.x * kOutPerThread;
+  const uint64_t i0 = (uint64_t)(blockIdx.x % chunks) * span;
+  const uint64_t i1 = i0 + span < per ? i0 + span : per;
+  for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const uint64_t o = i / (uint64_t)(m + 1);
+    const int a = (int)(i % (uint64_t)(m + 1));
+    // member-local out-of-window bits: o holds the bits below the window
+    // (wstart of them) and above it the bits above the window
+    const uint64_t fixed = ((o >> wstart) << (wstart + m)) | (o & ((1ull << wstart) - 1));
+    R re = R(1), im = R(0);
+    for (int k = starts.v[a]; k < starts.v[a + 1]; ++k) {
+      if ((fixed & masks[k]) == masks[k]) {
+        const cplx<R> f = fac[k];
+        const R nr = re * f.x - im * f.y;
+        im = re * f.y + im * f.x;
+        re = nr;
+      }
     }
+    const R d = diag_off >= 0 ? P[diag_off + a] : R(1);
+    tab[b * per + i] = mk<R>(re * d, im * d);
   }
-  const R d = diag_off >= 0 ? P[diag_off + a] : R(1);
-  tab[b * per + i] = mk<R>(re * d, im * d);
 }
 
 // A run of diagonal channels on the exact density matrix (Sec. 3): noiseless
@@ -1101,7 +1107,8 @@ cudaError_t launch_precompute(qs_plan p, const PassPlan& P, cudaStream_t s) {
     for (int i = 0; i < kMaxWin + 2; ++i) st.v[i] = P.out_start[i];
     const int obits = h->n - P.m;
     const int nterms = P.out_start[P.m + 1];
-    const uint32_t chunks = (uint32_t)((((uint64_t)(P.m + 1) << obits) + 255) / 256);
+    const uint64_t span = 256ull * kOutPerThread;
+    const uint32_t chunks = (uint32_t)((((uint64_t)(P.m + 1) << obits) + span - 1) / span);
     const size_t sm = (size_t)((nterms + 1) & ~1) * sizeof(uint64_t) + (size_t)nterms * sizeof(cplx<R>);
     k_out_table<R><<<(unsigned)(chunks * (uint64_t)h->batch), 256, sm, s>>>(
         (cplx<R>*)P.d_alpha, (const R*)P.d_params, P.stride, P.d_outs, st, P.diag_off, obits, P.win[0], chunks, P.m);
