@@ -369,6 +369,28 @@ class Scheduler:
         return done
 
 
+def choose_window(qs, p, h, n: int) -> int:
+    """Window width of a Monte Carlo plan: 11 or 12 qubits when that leaves two
+    passes where 10 needs more (the QFT at n = 21..24), else 10.
+
+    A Monte Carlo plan runs from basis starts, so its first pass only writes
+    the state; with two passes the wider window's only reading pass is the low
+    one, which keeps its speed.  A plan with more passes (Grover's search, or
+    n > 24) would read the state through wide high windows, whose single
+    128 KiB tile per SM leaves the load exposed, so it stays at 10."""
+    passes10 = qs.qs_plan_info(p, h)[0]
+    if passes10 <= 2:
+        return 10
+    for m in (11, 12):
+        if n < m:
+            break
+        qs.qs_plan_set_window(p, m, h)
+        if qs.qs_plan_info(p, h)[0] == 2:
+            return m
+    qs.qs_plan_set_window(p, 10, h)
+    return 10
+
+
 # ------------------------------------------------------------------ GPU executor
 class GpuExecutor:
     """Runs units through the C ABI; one CUDA stream per worker thread.
@@ -531,6 +553,7 @@ class GpuExecutor:
             h = qs.qs_create(n, unit.members, 0, qs.QS_STATEVEC, qs.QS_C64, self.streams[w])
             try:
                 p = qs.qs_plan_create(h, pc.to_gates(ops, per_member_flip=True))
+                choose_window(qs, p, h, n)
             except BaseException:
                 qs.qs_destroy(h)
                 raise

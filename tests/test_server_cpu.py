@@ -265,3 +265,27 @@ def test_a_job_in_many_waves_leaves_room_for_later_arrivals():
     u3 = s.next_unit(0.2)
     assert [sl.job_id for sl in u3.slices] == [1]    # the small job runs beside the big one
     assert s.jobs[0].next_traj < 1024 and s.used <= s.budget
+
+
+def test_window_choice_takes_a_wider_window_only_for_two_passes():
+    """choose_window: 11 or 12 qubits when that leaves two passes (a write-only
+    first pass and the last) where 10 needs more; otherwise back to 10."""
+    from paper_1412_2293_gb300.server import choose_window
+
+    class FakeQs:
+        def __init__(self, passes):
+            self.passes, self.m, self.calls = passes, 10, []
+
+        def qs_plan_info(self, p, h=None):
+            return self.passes[self.m], 0
+
+        def qs_plan_set_window(self, p, m, h=None):
+            self.calls.append(m)
+            self.m = m
+
+    cases = [(22, {10: 3, 11: 2, 12: 2}, 11), (24, {10: 3, 11: 3, 12: 2}, 12), (20, {10: 2, 11: 2, 12: 2}, 10),
+             (21, {10: 99, 11: 66, 12: 66}, 10), (11, {10: 3, 11: 2}, 11), (10, {10: 4}, 10)]
+    for n, passes, want in cases:
+        q = FakeQs(passes)
+        assert choose_window(q, None, None, n) == want, (n, passes)
+        assert q.m == want                                   # the plan is left at the width returned
