@@ -155,28 +155,39 @@ __device__ __forceinline__ void tri_pq(int idx, int M, int* p, int* q) {
 // Gram partials of member b = blockIdx.y: block x sums rows
 // [x rows_per_block, (x + 1) rows_per_block) of L'_b, in tiles of kGramRows
 // rows through shared memory, for every entry (p <= q) of the upper triangle
-// (a thread owns entries idx, idx + 256, ...; each entry a fixed-order FP64
-// sum).  Partial layout [member][block][kTriMax] complex.  The row split
+// (each entry a fixed-order FP64 sum).  A thread owns entries idx, idx +
+// kGramThreads, ...; when the triangle has at most kGramThreads / 2 entries
+// (M <= 21) its rows are split instead among G = min(kGramThreads / tri,
+// kGramRows) groups of threads (group g takes the tile rows x = g mod G), so
+// nearly every thread
+// works and the FP64 units of all four schedulers are busy, and the groups'
+// sums are added in group order at the end.  Partial layout [member][block][kTriMax] complex.  The row split
 // depends only on n, so a member's result does not depend on the batch.
+constexpr int kGramThreads = 512;
+
 template <typename R, bool REAL>
-__global__ void __launch_bounds__(256) k_gram_partials(const cplx<R>* __restrict__ Lp, int n, int mcap,
-                                                       int rows_per_block, RankCounts rc,
-                                                       double* __restrict__ partials) {
+__global__ void __launch_bounds__(kGramThreads) k_gram_partials(const cplx<R>* __restrict__ Lp, int n, int mcap,
+                                                                int rows_per_block, RankCounts rc,
+                                                                double* __restrict__ partials) {
   using T = typename std::conditional<REAL, double, double2>::type;
-  constexpr int kOwn = (kTriMax + 255) / 256;
+  constexpr int kOwn = (kTriMax + kGramThreads - 1) / kGramThreads;
   __shared__ T tile[kMaxGramDim][kGramRows + 1];
+  __shared__ double2 gsum[kGramThreads];
   const int b = blockIdx.y;
   const int M = rc.M[b];
   const int tri = M * (M + 1) / 2;
+  // row groups per entry (at most one per row of a tile)
+  const int G = tri <= kGramThreads / 2 ? min(kGramThreads / tri, kGramRows) : 1;
+  const int g = G > 1 ? (int)threadIdx.x / tri : 0;    // this thread's group (G: idle)
   const uint64_t N = 1ull << n;
   const cplx<R>* Lpb = Lp + (uint64_t)b * mcap * N;
   int ep[kOwn], eq[kOwn];
   double re[kOwn], im[kOwn], re2[kOwn];
 #pragma unroll
   for (int j = 0; j < kOwn; ++j) {
-    const int idx = threadIdx.x + 256 * j;
+    const int idx = G > 1 ? (j == 0 ? (int)threadIdx.x % tri : tri) : (int)threadIdx.x + kGramThreads * j;
     ep[j] = eq[j] = 0;
-    if (idx < tri) tri_pq(idx, M, &ep[j], &eq[j]);
+    if (idx < tri && g < G) tri_pq(idx, M, &ep[j], &eq[j]);
     re[j] = im[j] = re2[j] = 0.0;
   }
   const uint64_t r0 = (uint64_t)blockIdx.x * rows_per_block;
@@ -190,9 +201,27 @@ __global__ void __launch_bounds__(256) k_gram_partials(const cplx<R>* __restrict
       else tile[p][x] = make_double2(a.x, a.y);
     }
     __syncthreads();
+    if (G > 1) {
+      if (g >= G) continue;
+      const int p = ep[0], q = eq[0];
+      if constexpr (REAL) {
+        int k = 0;
+        for (int x = g; x < kGramRows; x += G, ++k) {
+          if (k & 1) re2[0] = fma(tile[p][x], tile[q][x], re2[0]);
+          else re[0] = fma(tile[p][x], tile[q][x], re[0]);
+        }
+      } else {
+        for (int x = g; x < kGramRows; x += G) {
+          const double2 a = tile[p][x], c = tile[q][x];
+          re[0] += a.x * c.x + a.y * c.y;        // conj(a) * c
+          im[0] += a.x * c.y - a.y * c.x;
+        }
+      }
+      continue;
+    }
 #pragma unroll
     for (int j = 0; j < kOwn; ++j) {
-      if (threadIdx.x + 256 * j >= tri) continue;
+      if (threadIdx.x + kGramThreads * j >= tri) continue;
       const int p = ep[j], q = eq[j];
       if constexpr (REAL) {
         for (int x = 0; x < kGramRows; x += 2) {
@@ -209,9 +238,24 @@ __global__ void __launch_bounds__(256) k_gram_partials(const cplx<R>* __restrict
     }
   }
   double* out = partials + ((size_t)b * gridDim.x + blockIdx.x) * 2 * kTriMax;
+  if (G > 1) {
+    // the groups' sums of each entry, added in group order
+    if (g < G) gsum[threadIdx.x] = make_double2(re[0] + re2[0], im[0]);
+    __syncthreads();
+    if ((int)threadIdx.x < tri) {
+      double sr = 0.0, si = 0.0;
+      for (int k = 0; k < G; ++k) {
+        sr += gsum[k * tri + threadIdx.x].x;
+        si += gsum[k * tri + threadIdx.x].y;
+      }
+      out[2 * threadIdx.x] = sr;
+      out[2 * threadIdx.x + 1] = si;
+    }
+    return;
+  }
 #pragma unroll
   for (int j = 0; j < kOwn; ++j) {
-    const int idx = threadIdx.x + 256 * j;
+    const int idx = threadIdx.x + kGramThreads * j;
     if (idx >= tri) continue;
     out[2 * idx] = re[j] + re2[j];
     out[2 * idx + 1] = im[j];
@@ -763,13 +807,13 @@ cudaError_t launch_gram(qs_ctx* h, bool real, int max_M) {
   const int blocks = (int)((N + rows - 1) / rows);
   const dim3 grid(blocks, h->batch);
   if (h->dtype == QS_C64 && real)
-    k_gram_partials<float, true><<<grid, 256, 0, h->stream>>>((const float2*)h->work, h->n, h->mcap, rows, h->rc, h->partials);
+    k_gram_partials<float, true><<<grid, kGramThreads, 0, h->stream>>>((const float2*)h->work, h->n, h->mcap, rows, h->rc, h->partials);
   else if (h->dtype == QS_C64)
-    k_gram_partials<float, false><<<grid, 256, 0, h->stream>>>((const float2*)h->work, h->n, h->mcap, rows, h->rc, h->partials);
+    k_gram_partials<float, false><<<grid, kGramThreads, 0, h->stream>>>((const float2*)h->work, h->n, h->mcap, rows, h->rc, h->partials);
   else if (real)
-    k_gram_partials<double, true><<<grid, 256, 0, h->stream>>>((const double2*)h->work, h->n, h->mcap, rows, h->rc, h->partials);
+    k_gram_partials<double, true><<<grid, kGramThreads, 0, h->stream>>>((const double2*)h->work, h->n, h->mcap, rows, h->rc, h->partials);
   else
-    k_gram_partials<double, false><<<grid, 256, 0, h->stream>>>((const double2*)h->work, h->n, h->mcap, rows, h->rc, h->partials);
+    k_gram_partials<double, false><<<grid, kGramThreads, 0, h->stream>>>((const double2*)h->work, h->n, h->mcap, rows, h->rc, h->partials);
   k_gram_reduce<<<dim3(max_M * (max_M + 1) / 2, h->batch), 256, 0, h->stream>>>(h->partials, blocks, h->rc, h->rsmall, kRankStride);
   return cudaGetLastError();
 }

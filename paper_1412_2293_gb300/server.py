@@ -116,12 +116,13 @@ def rank_bytes(n: int, r: int = RANK_MAX) -> int:
 # QFT takes ceil(n / 10) passes and Grover's search that many per layer of
 # Hadamards (1 + 2 x iterations layers, the flips between them end a pass).
 # Fixed rank: per channel and amplitude, RANK_S_PER_AMP + r RANK_S_PER_AMP_R
-# seconds (expansion, FP64 Gram matrix, eigensolver and projection over
-# K r <= 32 columns, complex128; fitted to the QFT at n = 20..24, r = 1..8).
-# Estimates for admission only; a job's latency is measured.
+# + r^2 RANK_S_PER_AMP_R2 seconds (expansion and projection grow with r, the
+# FP64 Gram matrix with (K r)^2; complex128; fitted to the QFT at n = 20..24,
+# r = 1, 2, 4, 8).  Estimates for admission only; a job's latency is measured.
 MC_BYTES_PER_S = 4.0e12
-RANK_S_PER_AMP = 0.2e-9
-RANK_S_PER_AMP_R = 0.47e-9
+RANK_S_PER_AMP = 0.05e-9
+RANK_S_PER_AMP_R = 0.22e-9
+RANK_S_PER_AMP_R2 = 0.028e-9
 MIN_TRAJECTORIES = 64
 
 
@@ -140,7 +141,9 @@ def estimate_passes(job: inputs.Job) -> int:
 
 def estimate_seconds(job: inputs.Job, trajectories: Optional[int] = None) -> float:
     if job.mode == "fixed_rank":
-        return job_gate_counts(job)[1] * float(1 << job.n) * (RANK_S_PER_AMP + job.rank * RANK_S_PER_AMP_R)
+        r = job.rank
+        return job_gate_counts(job)[1] * float(1 << job.n) * (RANK_S_PER_AMP + r * RANK_S_PER_AMP_R +
+                                                              r * r * RANK_S_PER_AMP_R2)
     t = job.trajectories if trajectories is None else trajectories
     return t * float(1 << job.n) * C64_BYTES * 2 * estimate_passes(job) / MC_BYTES_PER_S
 
