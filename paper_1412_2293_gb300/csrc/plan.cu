@@ -531,6 +531,8 @@ struct qs_plan_s {
   std::vector<RankOp> rank_ops;   // FIXED_RANK plans
   void* d_rank_mats = nullptr;
   int rank_variant = 0;           // the running variant: real start, per-member noise, normalisation
+  int rank_kmax = 0;              // the largest member rank: the projection's column bound
+  int graph_kmax[kVariants] = {};
   int colb = 3;
   int m = kWin;                   // window width of the fused passes
   int low_cfg = 0;                // kernel configuration of each window geometry (see launch_pass_kernel)
@@ -1377,7 +1379,7 @@ qs_status run_rank_ops(qs_plan p) {
         e = launch_kraus_expand_gate(h, tg, real, kg, h->rank);
         if (e == cudaSuccess) e = launch_gram(h, real, std::min(kMaxGramDim, K * h->rank));
         if (e == cudaSuccess) e = launch_eig_truncate(h, 0, normalize);
-        if (e == cudaSuccess) e = launch_project(h, real, K, h->rank);
+        if (e == cudaSuccess) e = launch_project(h, real, K, p->rank_kmax);
       }
     }
     if (e != cudaSuccess) return pfail(p, QS_ERR_CUDA, std::string("fixed-rank plan: ") + cudaGetErrorString(e));
@@ -1484,8 +1486,10 @@ qs_status run_plan(qs_plan p, double e, uint64_t seed, uint64_t gate_id0, int wa
   // the pinned run block may still be read by an earlier launch of the graph
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "stream sync");
   p->stable = two_shear_safe(p->gates, h->member_noise ? h->m_e_max : e) ? 0 : 1;
-  if (h->mode == QS_FIXED_RANK)
+  if (h->mode == QS_FIXED_RANK) {
     p->rank_variant = (h->real_factor ? 4 : 0) | (h->member_noise ? 2 : 0) | (h->normalize ? 1 : 0);
+    p->rank_kmax = *std::max_element(h->m_rank.begin(), h->m_rank.end());
+  }
   p->h_run->e = e;
   p->h_run->seed = seed;
   p->h_run->gate_id0 = gate_id0;
@@ -1505,7 +1509,8 @@ qs_status run_plan(qs_plan p, double e, uint64_t seed, uint64_t gate_id0, int wa
   } else {
     const int v = h->mode == QS_FIXED_RANK ? p->rank_variant : p->stable * 6 + synth * 2 + fid;
     if (p->exec[v] && (p->graph_member_noise[v] != h->member_noise || p->graph_member_marked[v] != h->member_marked ||
-                       p->graph_timing[v] != p->timing || p->graph_wait_polls[v] != h->wait_polls)) {
+                       p->graph_timing[v] != p->timing || p->graph_wait_polls[v] != h->wait_polls ||
+                       p->graph_kmax[v] != p->rank_kmax)) {
       cudaGraphExecDestroy(p->exec[v]);
       p->exec[v] = nullptr;
     }
@@ -1527,6 +1532,7 @@ qs_status run_plan(qs_plan p, double e, uint64_t seed, uint64_t gate_id0, int wa
       p->graph_member_marked[v] = h->member_marked;
       p->graph_timing[v] = p->timing;
       p->graph_wait_polls[v] = h->wait_polls;
+      p->graph_kmax[v] = p->rank_kmax;
     }
     if (cudaGraphLaunch(p->exec[v], h->stream) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "graph launch");
   }
@@ -1852,6 +1858,10 @@ qs_status qs_plan_profile(qs_plan p, int reps, double e, uint64_t seed, uint64_t
   }
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return pfail(p, QS_ERR_CUDA, "stream sync");
   p->stable = two_shear_safe(p->gates, h->member_noise ? h->m_e_max : e) ? 0 : 1;
+  if (h->mode == QS_FIXED_RANK) {
+    p->rank_variant = (h->real_factor ? 4 : 0) | (h->member_noise ? 2 : 0) | (h->normalize ? 1 : 0);
+    p->rank_kmax = *std::max_element(h->m_rank.begin(), h->m_rank.end());
+  }
   p->h_run->e = e;
   p->h_run->seed = seed;
   p->h_run->gate_id0 = gate_id0;

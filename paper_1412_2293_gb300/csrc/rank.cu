@@ -76,7 +76,7 @@ __device__ double2 kraus_entry(const KrausGate& g, double e, int op, int row, in
   return make_double2(re, im);
 }
 
-template <typename R, int K_Q, bool REAL>
+template <typename R, int K_Q, bool REAL, bool DIAG = false>
 __global__ void __launch_bounds__(kExpBlock) k_kraus_expand(const cplx<R>* __restrict__ L,
                                                             cplx<R>* __restrict__ Lp, int n, int rcap, int mcap,
                                                             Targets tg, const double* __restrict__ E, int K,
@@ -120,8 +120,12 @@ __global__ void __launch_bounds__(kExpBlock) k_kraus_expand(const cplx<R>* __res
 #pragma unroll
         for (int r = 0; r < D; ++r) {
           R acc = R(0);
+          if constexpr (DIAG) {
+            acc = sE[(a * D + r) * D + r].x * v[r];
+          } else {
 #pragma unroll
-          for (int q = 0; q < D; ++q) acc = fma(sE[(a * D + r) * D + q].x, v[q], acc);
+            for (int q = 0; q < D; ++q) acc = fma(sE[(a * D + r) * D + q].x, v[q], acc);
+          }
           out[tg.off[r]] = mk<R>(acc, R(0));
         }
       }
@@ -134,8 +138,12 @@ __global__ void __launch_bounds__(kExpBlock) k_kraus_expand(const cplx<R>* __res
 #pragma unroll
         for (int r = 0; r < D; ++r) {
           C acc = mk<R>(R(0), R(0));
+          if constexpr (DIAG) {
+            acc = cmul(sE[(a * D + r) * D + r], v[r]);
+          } else {
 #pragma unroll
-          for (int q = 0; q < D; ++q) acc = cfma(sE[(a * D + r) * D + q], v[q], acc);
+            for (int q = 0; q < D; ++q) acc = cfma(sE[(a * D + r) * D + q], v[q], acc);
+          }
           out[tg.off[r]] = acc;
         }
       }
@@ -213,8 +221,8 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_partials(const cplx<R>* _
       } else {
         for (int x = g; x < kGramRows; x += G) {
           const double2 a = tile[p][x], c = tile[q][x];
-          re[0] += a.x * c.x + a.y * c.y;        // conj(a) * c
-          im[0] += a.x * c.y - a.y * c.x;
+          re[0] = fma(a.x, c.x, fma(a.y, c.y, re[0]));   // conj(a) * c, four FMAs
+          im[0] = fma(a.x, c.y, fma(-a.y, c.x, im[0]));
         }
       }
       continue;
@@ -231,8 +239,8 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_partials(const cplx<R>* _
       } else {
         for (int x = 0; x < kGramRows; ++x) {
           const double2 a = tile[p][x], c = tile[q][x];
-          re[j] += a.x * c.x + a.y * c.y;        // conj(a) * c
-          im[j] += a.x * c.y - a.y * c.x;
+          re[j] = fma(a.x, c.x, fma(a.y, c.y, re[j]));   // conj(a) * c, four FMAs
+          im[j] = fma(a.x, c.y, fma(-a.y, c.x, im[j]));
         }
       }
     }
@@ -320,8 +328,6 @@ template <> __device__ __forceinline__ double tscal<double>(double v) { return v
 template <> __device__ __forceinline__ double2 tscal<double2>(double v) { return make_double2(v, 0.0); }
 __device__ __forceinline__ double tscale(double a, double v) { return a * v; }
 __device__ __forceinline__ double2 tscale(double2 a, double v) { return make_double2(a.x * v, a.y * v); }
-__device__ __forceinline__ double tphase(double a, double inv) { return a * inv; }                     // sign
-__device__ __forceinline__ double2 tphase(double2 a, double inv) { return make_double2(a.x * inv, -a.y * inv); }  // e^{-i arg}
 __device__ __forceinline__ double trsqrt(double a) { return rsqrt(a); }
 // the same for the FP32 pre-pass (float / float2)
 __device__ __forceinline__ float tmul(float a, float b) { return a * b; }
@@ -338,8 +344,6 @@ template <> __device__ __forceinline__ float tscal<float>(double v) { return (fl
 template <> __device__ __forceinline__ float2 tscal<float2>(double v) { return make_float2((float)v, 0.f); }
 __device__ __forceinline__ float tscale(float a, float v) { return a * v; }
 __device__ __forceinline__ float2 tscale(float2 a, float v) { return make_float2(a.x * v, a.y * v); }
-__device__ __forceinline__ float tphase(float a, float inv) { return a * inv; }
-__device__ __forceinline__ float2 tphase(float2 a, float inv) { return make_float2(a.x * inv, -a.y * inv); }
 __device__ __forceinline__ float trsqrt(float a) { return rsqrtf(a); }
 // e^{-i arg a} for a != 0: the sign of a real a, conj(a) / |a| for a complex
 // one (FP64 unit modulus: an FP32 reciprocal square root refined by two
@@ -710,7 +714,8 @@ __global__ void __launch_bounds__(256) k_project(const cplx<R>* __restrict__ Lp,
       for (int p = 0; p < M; ++p) {
         const double a = Lpb[(uint64_t)p * N + x].x;
 #pragma unroll
-        for (int c = 0; c < KMAX; ++c) acc[c] = fma(a, sW[p * KMAX + c].x, acc[c]);
+        for (int c = 0; c < KMAX; ++c)
+          if (c < keep) acc[c] = fma(a, sW[p * KMAX + c].x, acc[c]);   // keep: the same across the block
       }
 #pragma unroll
       for (int c = 0; c < KMAX; ++c)
@@ -721,9 +726,14 @@ __global__ void __launch_bounds__(256) k_project(const cplx<R>* __restrict__ Lp,
       for (int c = 0; c < KMAX; ++c) acc[c] = make_double2(0.0, 0.0);
       for (int p = 0; p < M; ++p) {
         const cplx<R> a = Lpb[(uint64_t)p * N + x];
-        const double2 ad = make_double2(a.x, a.y);
+        const double ax = a.x, ay = a.y;
 #pragma unroll
-        for (int c = 0; c < KMAX; ++c) acc[c] = zadd(acc[c], zmul(ad, sW[p * KMAX + c]));
+        for (int c = 0; c < KMAX; ++c) {
+          if (c >= keep) continue;                         // keep: the same across the block
+          const double2 w = sW[p * KMAX + c];              // a * w, four FMAs
+          acc[c].x = fma(ax, w.x, fma(-ay, w.y, acc[c].x));
+          acc[c].y = fma(ax, w.y, fma(ay, w.x, acc[c].y));
+        }
       }
 #pragma unroll
       for (int c = 0; c < KMAX; ++c)
@@ -749,7 +759,14 @@ cudaError_t expand_dispatch(qs_ctx* h, const Targets& tg, bool real, const doubl
   auto* l = static_cast<const cplx<R>*>(h->state);
   auto* lp = static_cast<cplx<R>*>(h->work);
   const int n = h->n, rcap = h->rank, mcap = h->mcap;
-  if (tg.k == 1 && real) k_kraus_expand<R, 1, true><<<grid, kExpBlock, 0, h->stream>>>(l, lp, n, rcap, mcap, tg, E, K, e_stride, h->rc, g);
+  // a diagonal gate with phase noise has diagonal Kraus operators: one product per output
+  bool diag = g.k == 2 && g.noise == QS_NOISE_PHASE;
+  for (int r = 0; diag && r < 4; ++r)
+    for (int c = 0; c < 4; ++c)
+      if (r != c && (g.U[2 * (r * 4 + c)] != 0.0 || g.U[2 * (r * 4 + c) + 1] != 0.0)) diag = false;
+  if (diag && real) k_kraus_expand<R, 2, true, true><<<grid, kExpBlock, 0, h->stream>>>(l, lp, n, rcap, mcap, tg, E, K, e_stride, h->rc, g);
+  else if (diag) k_kraus_expand<R, 2, false, true><<<grid, kExpBlock, 0, h->stream>>>(l, lp, n, rcap, mcap, tg, E, K, e_stride, h->rc, g);
+  else if (tg.k == 1 && real) k_kraus_expand<R, 1, true><<<grid, kExpBlock, 0, h->stream>>>(l, lp, n, rcap, mcap, tg, E, K, e_stride, h->rc, g);
   else if (tg.k == 1) k_kraus_expand<R, 1, false><<<grid, kExpBlock, 0, h->stream>>>(l, lp, n, rcap, mcap, tg, E, K, e_stride, h->rc, g);
   else if (tg.k == 2 && real) k_kraus_expand<R, 2, true><<<grid, kExpBlock, 0, h->stream>>>(l, lp, n, rcap, mcap, tg, E, K, e_stride, h->rc, g);
   else if (tg.k == 2) k_kraus_expand<R, 2, false><<<grid, kExpBlock, 0, h->stream>>>(l, lp, n, rcap, mcap, tg, E, K, e_stride, h->rc, g);

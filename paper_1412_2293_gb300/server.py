@@ -120,9 +120,9 @@ def rank_bytes(n: int, r: int = RANK_MAX) -> int:
 # FP64 Gram matrix with (K r)^2; complex128; fitted to the QFT at n = 20..24,
 # r = 1, 2, 4, 8).  Estimates for admission only; a job's latency is measured.
 MC_BYTES_PER_S = 4.0e12
-RANK_S_PER_AMP = 0.05e-9
-RANK_S_PER_AMP_R = 0.22e-9
-RANK_S_PER_AMP_R2 = 0.028e-9
+RANK_S_PER_AMP = 0.052e-9
+RANK_S_PER_AMP_R = 0.018e-9
+RANK_S_PER_AMP_R2 = 0.030e-9
 MIN_TRAJECTORIES = 64
 
 
