@@ -163,14 +163,17 @@ __device__ __forceinline__ void tri_pq(int idx, int M, int* p, int* q) {
 // Gram partials of member b = blockIdx.y: block x sums rows
 // [x rows_per_block, (x + 1) rows_per_block) of L'_b, in tiles of kGramRows
 // rows through shared memory, for every entry (p <= q) of the upper triangle
-// (each entry a fixed-order FP64 sum).  A thread owns entries idx, idx +
-// kGramThreads, ...; when the triangle has at most kGramThreads / 2 entries
-// (M <= 21) its rows are split instead among G = min(kGramThreads / tri,
-// kGramRows) groups of threads (group g takes the tile rows x = g mod G), so
-// nearly every thread
+// (each entry a fixed-order FP64 sum).  Blocks of 16 tiles of rows or more
+// (n >= 19) run kGramThreads threads, smaller ones half as many (their
+// channels are latency-bound, and fewer warps meet at each barrier).  A thread
+// owns entries idx, idx + blockDim, ...; when the block is large and the
+// triangle has at most blockDim / 2 entries (M <= 21 at 512 threads) its rows
+// are split instead among G = min(blockDim / tri, kGramRows) groups of
+// threads (group g takes the tile rows x = g mod G), so nearly every thread
 // works and the FP64 units of all four schedulers are busy, and the groups'
-// sums are added in group order at the end.  Partial layout [member][block][kTriMax] complex.  The row split
-// depends only on n, so a member's result does not depend on the batch.
+// sums are added in group order at the end.  Partial layout
+// [member][block][kTriMax] complex.  The row split and the block size depend
+// only on n, so a member's result does not depend on the batch.
 constexpr int kGramThreads = 512;
 
 template <typename R, bool REAL>
@@ -178,14 +181,18 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_partials(const cplx<R>* _
                                                                 int rows_per_block, RankCounts rc,
                                                                 double* __restrict__ partials) {
   using T = typename std::conditional<REAL, double, double2>::type;
-  constexpr int kOwn = (kTriMax + kGramThreads - 1) / kGramThreads;
+  // threads: kGramThreads where rows are split (blocks of 16 tiles or more), else half
+  constexpr int kOwn = (kTriMax + kGramThreads / 2 - 1) / (kGramThreads / 2);
+  const int nt = (int)blockDim.x;
   __shared__ T tile[kMaxGramDim][kGramRows + 1];
   __shared__ double2 gsum[kGramThreads];
   const int b = blockIdx.y;
   const int M = rc.M[b];
   const int tri = M * (M + 1) / 2;
-  // row groups per entry (at most one per row of a tile)
-  const int G = tri <= kGramThreads / 2 ? min(kGramThreads / tri, kGramRows) : 1;
+  // row groups per entry (at most one per row of a tile); only where a block
+  // has rows enough to keep them busy (from n = 19 on), the small factors'
+  // channels being latency-bound
+  const int G = tri <= nt / 2 && rows_per_block >= 16 * kGramRows ? min(nt / tri, kGramRows) : 1;
   const int g = G > 1 ? (int)threadIdx.x / tri : 0;    // this thread's group (G: idle)
   const uint64_t N = 1ull << n;
   const cplx<R>* Lpb = Lp + (uint64_t)b * mcap * N;
@@ -193,7 +200,7 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_partials(const cplx<R>* _
   double re[kOwn], im[kOwn], re2[kOwn];
 #pragma unroll
   for (int j = 0; j < kOwn; ++j) {
-    const int idx = G > 1 ? (j == 0 ? (int)threadIdx.x % tri : tri) : (int)threadIdx.x + kGramThreads * j;
+    const int idx = G > 1 ? (j == 0 ? (int)threadIdx.x % tri : tri) : (int)threadIdx.x + nt * j;
     ep[j] = eq[j] = 0;
     if (idx < tri && g < G) tri_pq(idx, M, &ep[j], &eq[j]);
     re[j] = im[j] = re2[j] = 0.0;
@@ -229,7 +236,7 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_partials(const cplx<R>* _
     }
 #pragma unroll
     for (int j = 0; j < kOwn; ++j) {
-      if (threadIdx.x + kGramThreads * j >= tri) continue;
+      if ((int)threadIdx.x + nt * j >= tri) continue;
       const int p = ep[j], q = eq[j];
       if constexpr (REAL) {
         for (int x = 0; x < kGramRows; x += 2) {
@@ -263,7 +270,7 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_partials(const cplx<R>* _
   }
 #pragma unroll
   for (int j = 0; j < kOwn; ++j) {
-    const int idx = threadIdx.x + kGramThreads * j;
+    const int idx = (int)threadIdx.x + nt * j;
     if (idx >= tri) continue;
     out[2 * idx] = re[j] + re2[j];
     out[2 * idx + 1] = im[j];
@@ -823,14 +830,15 @@ cudaError_t launch_gram(qs_ctx* h, bool real, int max_M) {
   const int rows = gram_rows_per_block(h->n);
   const int blocks = (int)((N + rows - 1) / rows);
   const dim3 grid(blocks, h->batch);
+  const int nt = rows >= 16 * kGramRows ? kGramThreads : kGramThreads / 2;   // see k_gram_partials
   if (h->dtype == QS_C64 && real)
-    k_gram_partials<float, true><<<grid, kGramThreads, 0, h->stream>>>((const float2*)h->work, h->n, h->mcap, rows, h->rc, h->partials);
+    k_gram_partials<float, true><<<grid, nt, 0, h->stream>>>((const float2*)h->work, h->n, h->mcap, rows, h->rc, h->partials);
   else if (h->dtype == QS_C64)
-    k_gram_partials<float, false><<<grid, kGramThreads, 0, h->stream>>>((const float2*)h->work, h->n, h->mcap, rows, h->rc, h->partials);
+    k_gram_partials<float, false><<<grid, nt, 0, h->stream>>>((const float2*)h->work, h->n, h->mcap, rows, h->rc, h->partials);
   else if (real)
-    k_gram_partials<double, true><<<grid, kGramThreads, 0, h->stream>>>((const double2*)h->work, h->n, h->mcap, rows, h->rc, h->partials);
+    k_gram_partials<double, true><<<grid, nt, 0, h->stream>>>((const double2*)h->work, h->n, h->mcap, rows, h->rc, h->partials);
   else
-    k_gram_partials<double, false><<<grid, kGramThreads, 0, h->stream>>>((const double2*)h->work, h->n, h->mcap, rows, h->rc, h->partials);
+    k_gram_partials<double, false><<<grid, nt, 0, h->stream>>>((const double2*)h->work, h->n, h->mcap, rows, h->rc, h->partials);
   k_gram_reduce<<<dim3(max_M * (max_M + 1) / 2, h->batch), 256, 0, h->stream>>>(h->partials, blocks, h->rc, h->rsmall, kRankStride);
   return cudaGetLastError();
 }
