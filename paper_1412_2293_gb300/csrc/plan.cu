@@ -84,6 +84,7 @@ struct Producer {
   int real;               // DENSE: real matrix, stored as its shears (r0, r0, s1, s1)
   int contrib_start, contrib_count;
   uint32_t off;
+  int toff;               // DWIN: offset of its parts in the precompute's FP64 table scratch
 };
 
 struct OutStarts { int v[kMaxWin + 2]; };   // out terms of attach a: [v[a], v[a + 1]); a = m: none
@@ -173,179 +174,250 @@ __device__ __forceinline__ void noisy_matrix(const DGate& g, double e, uint64_t 
 // entry, far below the precision of R (intermediate values stay in range).
 template <typename R> __device__ __forceinline__ double min_pivot() { return sizeof(R) == 4 ? 0x1p-30 : 0x1p-300; }
 
+constexpr int kSmallBits = 5;        // table levels the precompute runs for all parts together
+
+// Members' parameters of one pass, one block of 128 threads per member: the
+// noisy matrices of the dense gates in their factored forms, the phase
+// tables, the out factors.  The producer list holds the dense gates, then the
+// tables, then the out terms (the order build_pass writes).  Every draw and
+// product is independent of the others except two chains: the dense gates of
+// one window bit (the diagonal carried from gate to gate) and the doubling of
+// one table; warp 0 runs the first (one lane per window bit), warps 1-3 the
+// second (whole tables per warp), with no block barrier between them.
 template <typename R>
 __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int stride, const DGate* __restrict__ gates,
                                                     const Producer* __restrict__ prods, int num_prods,
                                                     const Contrib* __restrict__ contribs, int num_contribs,
-                                                    int num_dwin, int num_dense, int diag_off, NoiseSrc src,
-                                                    const RunParams* rp, int stable, int m) {
-  // [num_contribs] factors, then [num_dwin][kMaxWin] partner factors, a
-  // table of 2^(m-1) entries and the dense matrices
+                                                    int num_dwin, int num_dense, int tab_entries, int diag_off,
+                                                    NoiseSrc src, const RunParams* rp, int stable, int m) {
+  // shared: [num_contribs] factors, [num_dwin][kMaxWin] partner factors,
+  // [tab_entries] FP64 table scratch (a table's parts from its toff), the
+  // dense matrices ([num_dense][4] complex), then a copy of the dense and
+  // table producers and the contributions' partner bits
   extern __shared__ double2 pre_sm[];
-  const int b = blockIdx.x;
+  double2* cf = pre_sm;
+  double2* fm = cf + num_contribs;
+  double2* tab = fm + (size_t)num_dwin * kMaxWin;
+  double2* dmat = tab + tab_entries;
+  Producer* sp = reinterpret_cast<Producer*>(dmat + 4 * (size_t)num_dense);
+  const int nsp = num_dense + num_dwin;
+  unsigned char* cbit = reinterpret_cast<unsigned char*>(sp + nsp);
+  const int b = blockIdx.x, tid = threadIdx.x;
   double e;
   uint64_t seed, traj;
   member_noise(src, rp, b, &e, &seed, &traj);
   R* out = params + (uint64_t)b * stride;
-  // noisy 2x2 matrices of the dense gates, all threads in parallel, into
-  // shared memory (FP64, [slot][4] complex after the tables' scratch; a real
-  // gate as (M00, M01), (M10, M11)), factored by the chain below.
-  double2* dmat = pre_sm + num_contribs + (size_t)num_dwin * kMaxWin + (1u << (m - 1));
-  for (int i = threadIdx.x; i < num_prods; i += blockDim.x) {
-    const Producer p = prods[i];
-    if (p.kind != PD_DENSE) continue;
-    const DGate& g = gates[p.gate];
-    double m[8];
-    noisy_matrix<R>(g, e, seed, traj, rp->gate_id0 + g.gate_pos, m);
-    double2* slot = dmat + p.contrib_start * 4;
-    if (p.real) {
-      slot[0] = make_double2(m[0], m[2]);
-      slot[1] = make_double2(m[4], m[6]);
-    } else {
-      for (int q = 0; q < 4; ++q) slot[q] = make_double2(m[2 * q], m[2 * q + 1]);
-    }
-  }
-  __syncthreads();
-  // the last kMaxWin threads factor the dense gates (one per window bit)
-  // while the others compute the phase factors
-  constexpr int kPhaseThreads = 128 - kMaxWin;
-  // contributions of the phase tables, and out factors
-  if (threadIdx.x < kPhaseThreads) {
-    for (int i = threadIdx.x; i < num_contribs; i += kPhaseThreads) {
-      const DGate& g = gates[contribs[i].gate];
-      pre_sm[i] = diag_factor<R>(g, e, seed, traj, rp->gate_id0 + g.gate_pos);
-    }
-    for (int i = threadIdx.x; i < num_prods; i += kPhaseThreads) {
-      const Producer p = prods[i];
-      if (p.kind == PD_OUT) {
-        const DGate& g = gates[p.gate];
-        const double2 f = diag_factor<R>(g, e, seed, traj, rp->gate_id0 + g.gate_pos);
-        out[p.off] = (R)f.x;
-        out[p.off + 1] = (R)f.y;
-      }
-    }
-  }
-  // dense gates: one thread per window bit walks that bit's gates in circuit
-  // order.  The diagonal diag(pa, pd) = pa diag(1, rho) left by the previous
-  // real gate on the bit is carried into the next one: pa joins the overall
-  // scale and a real gate M becomes M' = M diag(1, rho) = [[a, b], [c, d]],
-  // factored as diag(d0, d1) [[1, w], [0, 1]] [[1, 0], [q, 1]] [[1, p], [0, 1]]
-  // (the kernel: x0 += p x1, x1 += q x0, x0 += w x1), and diag(d0, d1) is
-  // carried on.  Pivot on a = M'00 (w = 0: d0 = a, p = b / a, d1 = det'/a,
-  // q = c / d1) while |a| >= |column 0| / 4; otherwise (stable runs only) on
-  // c (q = 1: d1 = c, p = d / c - 1, d0 = det'/c, w = a c / det' - 1), where
-  // no factor exceeds about 4 for an orthogonal M.  Runs that are not stable
-  // always take the first form (the host checks that the pivot stays large).
-  // A complex gate absorbs the carried diagonal.  What is left at the end
-  // goes to the diag block.
-  __shared__ double pivot_a[kMaxWin];
-  if (threadIdx.x >= kPhaseThreads && (int)threadIdx.x - kPhaseThreads < m) {
-    const int J = threadIdx.x - kPhaseThreads;
-    double pa = 1.0, rho = 1.0;
-    for (int i = 0; i < num_prods; ++i) {
-      const Producer p = prods[i];
-      if (p.kind != PD_DENSE || p.j != J) continue;
-      const double2* slot = dmat + p.contrib_start * 4;
+
+  // per-part bookkeeping of the tables (2b): order by size, bits, scratch,
+  // first partner factor, output offset; parts with more than q bits (q <=
+  // kSmallBits) and all parts
+  __shared__ int perm[2 * kMaxDwin], sbits[2 * kMaxDwin], stoff[2 * kMaxDwin], sfb[2 * kMaxDwin];
+  __shared__ uint32_t sout[2 * kMaxDwin];
+  __shared__ int nact[kSmallBits + 2];
+  if (tid < kSmallBits + 2) nact[tid] = 0;
+  auto w_base = [](int w) { return w * kMaxWin; };
+
+  // (1) every draw, one item per thread: the noisy 2x2 matrices of the dense
+  // gates (FP64, [slot][4] complex; a real gate as (M00, M01), (M10, M11)),
+  // the factors of the table contributions, the out factors (straight to
+  // the parameters); and the copy of the producers
+  for (int i = tid; i < nsp; i += blockDim.x) sp[i] = prods[i];
+  const int num_out = num_prods - nsp;
+  for (int k = tid; k < num_dense + num_contribs + num_out; k += blockDim.x) {
+    if (k < num_dense) {
+      const Producer p = prods[k];
+      const DGate& g = gates[p.gate];
+      double mm[8];
+      noisy_matrix<R>(g, e, seed, traj, rp->gate_id0 + g.gate_pos, mm);
+      double2* slot = dmat + p.contrib_start * 4;
       if (p.real) {
-        const double mp = min_pivot<R>();
-        auto clamp = [mp](double x) { return fabs(x) < mp ? (x < 0.0 ? -mp : mp) : x; };
-        const double a = slot[0].x, b = slot[0].y * rho, c = slot[1].x, d = slot[1].y * rho;
-        const double det = a * d - b * c;
-        double fp, fq, fw, d0, d1;
-        if (!stable || fabs(a) >= 0.25 * sqrt(a * a + c * c)) {
-          d0 = clamp(a);
-          d1 = clamp(det / d0);
-          fp = b / d0;
-          fq = c / d1;
-          fw = 0.0;
-        } else {
-          d1 = clamp(c);
-          const double dt = clamp(det);
-          fp = d / d1 - 1.0;
-          d0 = dt / d1;
-          fq = 1.0;
-          fw = a * d1 / dt - 1.0;
-        }
-        out[p.off] = (R)fp;                             // (p, p, q, q, w, w)
-        out[p.off + 1] = (R)fp;
-        out[p.off + 2] = (R)fq;
-        out[p.off + 3] = (R)fq;
-        out[p.off + 4] = (R)fw;
-        out[p.off + 5] = (R)fw;
-        pa *= d0;
-        rho = d1 / d0;
+        slot[0] = make_double2(mm[0], mm[2]);
+        slot[1] = make_double2(mm[4], mm[6]);
       } else {
-        const double pd = rho * pa;
-        for (int q = 0; q < 4; ++q) {
-          const double2 v = slot[q];
-          const double sc = (q & 1) ? pd : pa;          // column 0 by pa, column 1 by pd
-          out[p.off + 2 * q] = (R)(v.x * sc);
-          out[p.off + 2 * q + 1] = (R)(v.y * sc);
-        }
-        pa = 1.0;
-        rho = 1.0;
+        for (int q = 0; q < 4; ++q) slot[q] = make_double2(mm[2 * q], mm[2 * q + 1]);
       }
+    } else if (k < num_dense + num_contribs) {
+      const int i = k - num_dense;
+      const Contrib c = contribs[i];
+      const DGate& g = gates[c.gate];
+      cf[i] = diag_factor<R>(g, e, seed, traj, rp->gate_id0 + g.gate_pos);
+      cbit[i] = (unsigned char)c.m;
+    } else {
+      const Producer p = prods[nsp + k - num_dense - num_contribs];   // an out term
+      const DGate& g = gates[p.gate];
+      const double2 f = diag_factor<R>(g, e, seed, traj, rp->gate_id0 + g.gate_pos);
+      out[p.off] = (R)f.x;
+      out[p.off + 1] = (R)f.y;
     }
-    pivot_a[J] = pa;
-    if (diag_off >= 0) out[diag_off + J] = (R)rho;
   }
   __syncthreads();
-  if (diag_off >= 0 && threadIdx.x == 0) {
-    double sc = 1.0;
-    for (int J = 0; J < m; ++J) sc *= pivot_a[J];
-    out[diag_off + m] = (R)sc;
-  }
-  // per-table partner factors f[q], q = 0..m-1
-  double2* fm = pre_sm + num_contribs;
-  int w = 0;
-  for (int i = 0; i < num_prods; ++i) {
-    const Producer p = prods[i];
-    if (p.kind != PD_DWIN) continue;
-    if ((int)threadIdx.x < m) {
+
+  if (tid < 32) {
+    // (2a) dense gates: lane J walks window bit J's gates in circuit order.
+    // The diagonal diag(pa, pd) = pa diag(1, rho) left by the previous real
+    // gate on the bit is carried into the next one: pa joins the overall
+    // scale and a real gate M becomes M' = M diag(1, rho) = [[a, b], [c, d]],
+    // factored as diag(d0, d1) [[1, w], [0, 1]] [[1, 0], [q, 1]] [[1, p], [0, 1]]
+    // (the kernel: x0 += p x1, x1 += q x0, x0 += w x1), and diag(d0, d1) is
+    // carried on.  Pivot on a = M'00 (w = 0: d0 = a, p = b / a, d1 = det'/a,
+    // q = c / d1) while |a| >= |column 0| / 4; otherwise (stable runs only) on
+    // c (q = 1: d1 = c, p = d / c - 1, d0 = det'/c, w = a c / det' - 1), where
+    // no factor exceeds about 4 for an orthogonal M.  Runs that are not stable
+    // always take the first form (the host checks that the pivot stays large).
+    // A complex gate absorbs the carried diagonal.  What is left at the end
+    // goes to the diag block.  The lanes step through their own gates side by
+    // side (each finds its next gate, then all factor at once).
+    __shared__ double pivot_a[kMaxWin];
+    const int J = tid;
+    if (J < m) {
+      double pa = 1.0, rho = 1.0;
+      int i = 0;
+      for (;;) {
+        while (i < num_dense && sp[i].j != J) ++i;
+        if (i >= num_dense) break;
+        const Producer& p = sp[i++];
+        const double2* slot = dmat + p.contrib_start * 4;
+        if (p.real) {
+          const double mp = min_pivot<R>();
+          auto clamp = [mp](double x) { return fabs(x) < mp ? (x < 0.0 ? -mp : mp) : x; };
+          const double a = slot[0].x, bb = slot[0].y * rho, c = slot[1].x, d = slot[1].y * rho;
+          const double det = a * d - bb * c;
+          double fp, fq, fw, d0, d1;
+          if (!stable || fabs(a) >= 0.25 * sqrt(a * a + c * c)) {
+            d0 = clamp(a);
+            d1 = clamp(det / d0);
+            fp = bb / d0;
+            fq = c / d1;
+            fw = 0.0;
+          } else {
+            d1 = clamp(c);
+            const double dt = clamp(det);
+            fp = d / d1 - 1.0;
+            d0 = dt / d1;
+            fq = 1.0;
+            fw = a * d1 / dt - 1.0;
+          }
+          out[p.off] = (R)fp;                           // (p, p, q, q, w, w)
+          out[p.off + 1] = (R)fp;
+          out[p.off + 2] = (R)fq;
+          out[p.off + 3] = (R)fq;
+          out[p.off + 4] = (R)fw;
+          out[p.off + 5] = (R)fw;
+          pa *= d0;
+          rho = d1 / d0;
+        } else {
+          const double pd = rho * pa;
+          for (int q = 0; q < 4; ++q) {
+            const double2 v = slot[q];
+            const double sc = (q & 1) ? pd : pa;        // column 0 by pa, column 1 by pd
+            out[p.off + 2 * q] = (R)(v.x * sc);
+            out[p.off + 2 * q + 1] = (R)(v.y * sc);
+          }
+          pa = 1.0;
+          rho = 1.0;
+        }
+      }
+      pivot_a[J] = pa;
+      if (diag_off >= 0) out[diag_off + J] = (R)rho;
+    }
+    __syncwarp();
+    if (diag_off >= 0 && tid == 0) {
+      double sc = 1.0;
+      for (int q = 0; q < m; ++q) sc *= pivot_a[q];
+      out[diag_off + m] = (R)sc;
+    }
+  } else {
+    // (2b) partner factors f[q] of each table (the product of its
+    // contributions with partner bit q, in list order), one (table, q) per
+    // thread of warps 1-3; a single contribution is taken as it is (the
+    // product 1 f is f exactly), so the usual case needs no FP64 product
+    for (int k = tid - 32; k < num_dwin * m; k += blockDim.x - 32) {
+      const int w = k / m, q = k % m;
+      const Producer& p = sp[num_dense + w];
       double2 acc = make_double2(1.0, 0.0);
+      bool first = true;
       for (int c = p.contrib_start; c < p.contrib_start + p.contrib_count; ++c)
-        if (contribs[c].m == (int)threadIdx.x) {
-          const double2 f = pre_sm[c];
-          acc = make_double2(acc.x * f.x - acc.y * f.y, acc.x * f.y + acc.y * f.x);
+        if (cbit[c] == q) {
+          const double2 f = cf[c];
+          acc = first ? f : make_double2(acc.x * f.x - acc.y * f.y, acc.x * f.y + acc.y * f.x);
+          first = false;
         }
-      fm[w * kMaxWin + threadIdx.x] = acc;
+      fm[w * kMaxWin + q] = acc;
     }
-    ++w;
-  }
-  __syncthreads();
-  // tables T[x] = prod_{q in x} f[q], by doubling in FP64 shared memory:
-  // T[x + 2^q] = T[x] f[q] for x < 2^q (one complex product per entry)
-  double2* tab = fm + (size_t)num_dwin * kMaxWin;       // 2^(m-1) entries
-  w = 0;
-  for (int i = 0; i < num_prods; ++i) {
-    const Producer p = prods[i];
-    if (p.kind != PD_DWIN) continue;
-    // one table over bits [0, j), or two: [0, sh) then [sh, j)
-    const int parts = p.sh > 0 ? 2 : 1;
-    uint32_t o = p.off;
-    for (int part = 0; part < parts; ++part) {
-      const int lo = part == 0 ? 0 : p.sh, hi = (parts == 1 || part == 1) ? p.j : p.sh;
-      if (threadIdx.x == 0) tab[0] = make_double2(1.0, 0.0);
-      __syncthreads();
-      for (int q = lo; q < hi; ++q) {
-        const double2 f = fm[w * kMaxWin + q];
-        const int half = 1 << (q - lo);
-        for (int x = threadIdx.x; x < half; x += blockDim.x) {
-          const double2 t = tab[x];
-          tab[x + half] = make_double2(t.x * f.x - t.y * f.y, t.x * f.y + t.y * f.x);
+    // tables T[x] = prod_{q in x} f[q] over the bits of a part (a table is
+    // one part over bits [0, j) or two, [0, sh) then [sh, j)), by doubling in
+    // FP64: T[x + 2^q] = T[x] f[q] for x < 2^q, one complex product per
+    // entry.  A warp-wide FP64 instruction costs the same with 1 or 32 lanes
+    // busy, so the first kSmallBits levels of all parts run together (the
+    // parts sorted by size, a level's items spread over warps 1-3); each
+    // larger part then finishes its levels in one warp.  Written in R.
+    const int u = tid - 32, lane = tid & 31, wq = (tid >> 5) - 1;
+    auto slot_bits = [&](int sl) {
+      const Producer& p = sp[num_dense + (sl >> 1)];
+      if (p.sh > 0) return (sl & 1) ? p.j - p.sh : p.sh;
+      return (sl & 1) ? -1 : p.j;
+    };
+    const int nslot = 2 * num_dwin;
+    for (int sl = u; sl < nslot; sl += blockDim.x - 32) {
+      const int bits = slot_bits(sl);
+      if (bits < 0) continue;
+      const Producer& p = sp[num_dense + (sl >> 1)];
+      const int part = sl & 1;
+      int rank = 0;                                     // by bits descending, then slot
+      for (int v = 0; v < nslot; ++v) {
+        const int bv = slot_bits(v);
+        rank += bv > bits || (bv == bits && v < sl);
+      }
+      perm[rank] = sl;
+      sbits[sl] = bits;
+      stoff[sl] = p.toff + (part ? 1 << p.sh : 0);
+      sfb[sl] = w_base(sl >> 1) + (part ? p.sh : 0);
+      sout[sl] = p.off + (part ? ((2u << p.sh) + 3u) & ~3u : 0u);
+      tab[stoff[sl]] = make_double2(1.0, 0.0);
+      for (int q = 0; q <= kSmallBits; ++q)
+        if (bits > q) atomicAdd(&nact[q], 1);
+      atomicAdd(&nact[kSmallBits + 1], 1);
+    }
+    asm volatile("bar.sync 1, 96;" ::: "memory");       // warps 1-3 only
+    for (int q = 0; q < kSmallBits; ++q) {
+      const int items = nact[q] << q;
+      for (int k = u; k < items; k += blockDim.x - 32) {
+        const int sl = perm[k >> q], x = k & ((1 << q) - 1);
+        double2* t = tab + stoff[sl];
+        const double2 f = fm[sfb[sl] + q];
+        const double2 v = t[x];
+        t[x + (1 << q)] = make_double2(v.x * f.x - v.y * f.y, v.x * f.y + v.y * f.x);
+      }
+      asm volatile("bar.sync 1, 96;" ::: "memory");
+    }
+    auto write_part = [&](int sl) {
+      const int bits = sbits[sl];
+      const double2* t = tab + stoff[sl];
+      const int tq = sp[num_dense + (sl >> 1)].tq;
+      const uint32_t o = sout[sl];
+      for (int x = lane; x < (1 << bits); x += 32) {
+        const int at = tq > 0 ? ((x & ((1 << tq) - 1)) << (bits - tq)) | (x >> tq) : x;
+        out[o + 2 * at] = (R)t[x].x;
+        out[o + 2 * at + 1] = (R)t[x].y;
+      }
+    };
+    // larger parts: the remaining levels and the write, round robin over the warps
+    const int nbig = nact[kSmallBits], nall = nact[kSmallBits + 1];
+    for (int i = wq; i < nbig; i += 3) {
+      const int sl = perm[i];
+      double2* t = tab + stoff[sl];
+      for (int q = kSmallBits; q < sbits[sl]; ++q) {
+        const double2 f = fm[sfb[sl] + q];
+        const int half = 1 << q;
+        for (int x = lane; x < half; x += 32) {
+          const double2 v = t[x];
+          t[x + half] = make_double2(v.x * f.x - v.y * f.y, v.x * f.y + v.y * f.x);
         }
-        __syncthreads();
+        __syncwarp();
       }
-      const int bits = hi - lo;
-      for (int x = threadIdx.x; x < (1 << bits); x += blockDim.x) {
-        const int at = p.tq > 0 ? ((x & ((1 << p.tq) - 1)) << (bits - p.tq)) | (x >> p.tq) : x;
-        out[o + 2 * at] = (R)tab[x].x;
-        out[o + 2 * at + 1] = (R)tab[x].y;
-      }
-      o += ((2u << bits) + 3u) & ~3u;                  // each part starts 16-byte aligned
-      __syncthreads();
+      write_part(sl);
     }
-    ++w;
+    for (int i = nbig + wq; i < nall; i += 3) write_part(perm[i]);
   }
 }
 
@@ -355,47 +427,102 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
 // attached to none) whose out-of-window bits are all set in o, times the
 // deferred real diagonal of bit a (the overall scale for a = m).  The pass
 // kernels read the m + 1 entries of their tile directly.
-constexpr int kOutPerThread = 64;    // out-factor entries per thread: a member's terms staged once per block
+//
+// The product factors over o = y 2^L + x (x: the low L = kOutLoBits bits): a
+// term whose bits all lie in x's part (in y's) depends on x (on y) alone, so
+// an entry is Tlo[a][x] Thi[a][y] times the terms whose bits lie in both (none
+// for two-qubit gates with one qubit in the window).  A block builds Tlo over
+// every x (the diagonal of a folded in) and Thi over the y of its chunk, then
+// writes each entry with one product.
+constexpr int kOutPerThread = 64;    // out-factor entries per thread (a block's chunk)
+constexpr int kOutLoBits = 6;        // bits of o in Tlo
+
+// entries of Thi a block of 256 threads needs at most, per attach
+inline int out_table_ny(int obits, int m) {
+  const uint64_t span = 256ull * kOutPerThread, A = (uint64_t)m + 1;
+  const int L = obits < kOutLoBits ? obits : kOutLoBits;
+  const uint64_t ny = ((((span - 1) / A) + 1) >> L) + 2;
+  const uint64_t all = 1ull << (obits - L);
+  return (int)(ny < all ? ny : all);
+}
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_out_table(cplx<R>* __restrict__ tab, const R* __restrict__ params, int stride,
                                                    const OutTerm* __restrict__ outs, OutStarts starts, int diag_off,
-                                                   int obits, int wstart, uint32_t chunks, int m) {
-  // one member per block: its terms' masks and factors staged in shared memory
+                                                   int obits, int wstart, uint32_t chunks, int m, int ny_max) {
+  // shared: the member's terms (masks, factors, classes), Tlo[m + 1][2^L], Thi[m + 1][ny_max]
   extern __shared__ unsigned char ot_sm[];
   const int nterms = starts.v[m + 1];
+  const int A = m + 1;
+  const int L = obits < kOutLoBits ? obits : kOutLoBits;
+  const int nx = 1 << L;
   uint64_t* masks = reinterpret_cast<uint64_t*>(ot_sm);
   cplx<R>* fac = reinterpret_cast<cplx<R>*>(masks + ((nterms + 1) & ~1));   // 16-byte aligned
+  cplx<R>* tlo = fac + nterms;
+  cplx<R>* thi = tlo + A * nx;
+  unsigned char* cls = reinterpret_cast<unsigned char*>(thi + A * ny_max);
   const uint64_t b = blockIdx.x / chunks;
-  const uint64_t per = ((uint64_t)(m + 1) << obits);
+  const uint64_t per = (uint64_t)A << obits;
   const R* P = params + b * (uint64_t)stride;
+  // member-local out-of-window bits of o: the wstart bits below the window,
+  // then the bits above it
+  auto expand = [&](uint64_t o) { return ((o >> wstart) << (wstart + m)) | (o & ((1ull << wstart) - 1)); };
+  const uint64_t lo_bits = expand((1ull << L) - 1);
+  __shared__ int sv[kMaxWin + 2];                      // term ranges by attach
+  if ((int)threadIdx.x < m + 2) sv[threadIdx.x] = starts.v[threadIdx.x];
+  int straddle = 0;
   for (int k = threadIdx.x; k < nterms; k += blockDim.x) {
     const OutTerm t = outs[k];
     masks[k] = t.cmask;
     fac[k] = mk<R>(P[t.off], P[t.off + 1]);
+    const int c = (t.cmask & ~lo_bits) == 0 ? 0 : ((t.cmask & lo_bits) == 0 ? 1 : 2);
+    cls[k] = (unsigned char)c;
+    straddle |= c == 2;
   }
-  __syncthreads();
-  // the block's chunk of the member's entries: kOutPerThread per thread
+  straddle = __syncthreads_or(straddle);
+  // the block's chunk of the member's entries and the y it covers
   const uint64_t span = (uint64_t)blockDim.x * kOutPerThread;
   const uint64_t i0 = (uint64_t)(blockIdx.x % chunks) * span;
   const uint64_t i1 = i0 + span < per ? i0 + span : per;
-  for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    const uint64_t o = i / (uint64_t)(m + 1);
-    const int a = (int)(i % (uint64_t)(m + 1));
-    // member-local out-of-window bits: o holds the bits below the window
-    // (wstart of them) and above it the bits above the window
-    const uint64_t fixed = ((o >> wstart) << (wstart + m)) | (o & ((1ull << wstart) - 1));
-    R re = R(1), im = R(0);
-    for (int k = starts.v[a]; k < starts.v[a + 1]; ++k) {
-      if ((fixed & masks[k]) == masks[k]) {
+  const uint64_t y0 = (i0 / A) >> L;
+  const int ny = (int)((((i1 - 1) / A) >> L) - y0 + 1);   // <= ny_max (out_table_ny)
+  auto term_product = [&](int a, int want, uint64_t fixed, R re, R im) {
+    for (int k = sv[a]; k < sv[a + 1]; ++k) {
+      if (cls[k] == want && (fixed & masks[k]) == masks[k]) {
         const cplx<R> f = fac[k];
         const R nr = re * f.x - im * f.y;
         im = re * f.y + im * f.x;
         re = nr;
       }
     }
-    const R d = diag_off >= 0 ? P[diag_off + a] : R(1);
-    tab[b * per + i] = mk<R>(re * d, im * d);
+    return mk<R>(re, im);
+  };
+  for (int k = threadIdx.x; k < A * (nx + ny); k += blockDim.x) {
+    const int a = k % A, u = k / A;
+    if (u < nx) {
+      const R d = diag_off >= 0 ? P[diag_off + a] : R(1);
+      tlo[a * nx + u] = term_product(a, 0, expand((uint64_t)u), d, R(0));
+    } else {
+      const int yy = u - nx;
+      thi[a * ny_max + yy] = term_product(a, 1, expand((y0 + yy) << L), R(1), R(0));
+    }
+  }
+  __syncthreads();
+  // entry i = o (m + 1) + a of the member: o and a stepped along with i
+  // (no division per entry)
+  const uint32_t step = blockDim.x, dq = step / A, dr = step % A;
+  uint64_t i = i0 + threadIdx.x;
+  uint64_t o = i / (uint64_t)A;
+  uint32_t a = (uint32_t)(i % (uint64_t)A);
+  cplx<R>* dst = tab + b * per;
+  for (; i < i1; i += step) {
+    const cplx<R> x = tlo[a * nx + (uint32_t)(o & (nx - 1))], y = thi[a * ny_max + (uint32_t)((o >> L) - y0)];
+    cplx<R> v = mk<R>(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x);
+    if (straddle) v = term_product((int)a, 2, expand(o), v.x, v.y);
+    dst[i] = v;
+    o += dq;
+    a += dr;
+    if (a >= (uint32_t)A) { a -= A; ++o; }
   }
 }
 
@@ -463,6 +590,7 @@ struct PassPlan {
   int num_dwin = 0;
   int num_dense = 0;
   int diag_off = -1;              // deferred diagonals of the factored real gates
+  int tab_entries = 0;            // FP64 scratch entries of the tables in the precompute
   int stride = 0;                 // R units per member
   std::vector<int> other;
   int tile_shift = 0;             // log2(tiles per member)
@@ -695,7 +823,9 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
     const PGate& g = G[rem[i]];
     if (!g.dense1 && !g.cp && !g.flip) break;           // a gate the pass cannot hold ends the scan
     // bounds of one pass: precompute shared memory and the per-member block
-    if (ncontrib >= kMaxContribs || dwins.size() >= kMaxDwin || table_entries >= kMaxTableEntries ||
+    // (a new table has at most 2^(m-1) entries: the total stays within kMaxTableEntries)
+    if (ncontrib >= kMaxContribs || dwins.size() >= kMaxDwin ||
+        table_entries + (1u << (m - 1)) > kMaxTableEntries ||
         out_gates.size() >= kMaxOut || P->ops.size() + 2 > op_budget)
       break;
     bool ok = true;
@@ -806,6 +936,7 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
   }
   P->contribs.clear();
   P->num_dwin = 0;
+  P->tab_entries = 0;
   for (auto& x : P->ops) {
     if (x.type == OP_DWIN) {
       Dw& d = dwins[x.off];
@@ -814,6 +945,8 @@ bool build_pass(const std::vector<PGate>& G, const std::vector<int>& rem, int n,
       pr.j = d.j;
       pr.sh = d.sh;
       pr.tq = d.tq;
+      pr.toff = P->tab_entries;
+      P->tab_entries += d.sh > 0 ? (1 << d.sh) + (1 << (d.j - d.sh)) : 1 << d.j;
       pr.contrib_start = (int)P->contribs.size();
       pr.contrib_count = (int)d.cs.size();
       for (auto& c : d.cs) P->contribs.push_back(c);
@@ -1093,17 +1226,25 @@ PassArgs pass_args(qs_plan p, const PassPlan& P, int synth, int fid) {
   return A;
 }
 
+// Shared memory of k_precompute: contribution factors, partner factors, table
+// scratch and dense matrices (FP64 complex), the dense and table producers,
+// the contributions' partner bits.
+size_t precompute_smem(size_t contribs, size_t dwin, size_t tab_entries, size_t dense) {
+  return (contribs + dwin * kMaxWin + tab_entries + 4 * dense) * sizeof(double2) + (dense + dwin) * sizeof(Producer) +
+         contribs;
+}
+
 // Members' noise draws, matrices, phase tables and out factors of one pass.
 template <typename R>
 cudaError_t launch_precompute(qs_plan p, const PassPlan& P, cudaStream_t s) {
   qs_ctx* h = p->h;
   NoiseSrc src{};
   if (h->member_noise) { src.e = h->m_e; src.seed = h->m_seed; src.traj = h->m_traj; }
-  const size_t pre_smem =
-      (P.contribs.size() + (size_t)P.num_dwin * kMaxWin + (1u << (P.m - 1)) + 4 * (size_t)P.num_dense) * sizeof(double2);
+  const size_t pre_smem = precompute_smem(P.contribs.size(), P.num_dwin, P.tab_entries, P.num_dense);
   k_precompute<R><<<h->batch, 128, pre_smem, s>>>((R*)P.d_params, P.stride, p->d_gates, P.d_prods,
                                                    (int)P.prods.size(), P.d_contribs, (int)P.contribs.size(),
-                                                   P.num_dwin, P.num_dense, P.diag_off, src, p->d_run, p->stable, P.m);
+                                                   P.num_dwin, P.num_dense, P.tab_entries, P.diag_off, src,
+                                                   p->d_run, p->stable, P.m);
   if (P.d_alpha) {
     OutStarts st{};
     for (int i = 0; i < kMaxWin + 2; ++i) st.v[i] = P.out_start[i];
@@ -1111,9 +1252,13 @@ cudaError_t launch_precompute(qs_plan p, const PassPlan& P, cudaStream_t s) {
     const int nterms = P.out_start[P.m + 1];
     const uint64_t span = 256ull * kOutPerThread;
     const uint32_t chunks = (uint32_t)((((uint64_t)(P.m + 1) << obits) + span - 1) / span);
-    const size_t sm = (size_t)((nterms + 1) & ~1) * sizeof(uint64_t) + (size_t)nterms * sizeof(cplx<R>);
+    const int L = obits < kOutLoBits ? obits : kOutLoBits;
+    const int ny_max = out_table_ny(obits, P.m);
+    const size_t sm = (size_t)((nterms + 1) & ~1) * sizeof(uint64_t) +
+                      ((size_t)nterms + (size_t)(P.m + 1) * ((1u << L) + ny_max)) * sizeof(cplx<R>) + nterms;
     k_out_table<R><<<(unsigned)(chunks * (uint64_t)h->batch), 256, sm, s>>>(
-        (cplx<R>*)P.d_alpha, (const R*)P.d_params, P.stride, P.d_outs, st, P.diag_off, obits, P.win[0], chunks, P.m);
+        (cplx<R>*)P.d_alpha, (const R*)P.d_params, P.stride, P.d_outs, st, P.diag_off, obits, P.win[0], chunks, P.m,
+        ny_max);
   }
   return cudaGetLastError();
 }
@@ -1204,10 +1349,10 @@ cudaError_t set_smem_attrs(size_t esize) {
   static std::atomic<bool> done[2] = {false, false};
   const int which = esize == 8 ? 0 : 1;
   if (done[which]) return cudaSuccess;
-  constexpr size_t kPreSmem = (kMaxContribs + kMaxDwin * kMaxWin + (1u << (kMaxWin - 1)) + 4 * kMaxOps) * sizeof(double2);
+  const size_t pre_max = precompute_smem(kMaxContribs, kMaxDwin, kMaxTableEntries, kMaxOps);
   cudaError_t e = esize == 8
-      ? cudaFuncSetAttribute(k_precompute<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPreSmem)
-      : cudaFuncSetAttribute(k_precompute<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPreSmem);
+      ? cudaFuncSetAttribute(k_precompute<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pre_max)
+      : cudaFuncSetAttribute(k_precompute<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pre_max);
   if (e != cudaSuccess) return e;
   if (esize == 8) {
     e = set_pass_attrs(k_pass_low<float, 12, 2>, low_smem<float, 12, 2>(), 1);
