@@ -431,26 +431,28 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
 // The product factors over o = y 2^L + x (x: the low L = kOutLoBits bits): a
 // term whose bits all lie in x's part (in y's) depends on x (on y) alone, so
 // an entry is Tlo[a][x] Thi[a][y] times the terms whose bits lie in both (none
-// for two-qubit gates with one qubit in the window).  A block builds Tlo over
-// every x (the diagonal of a folded in) and Thi over the y of its chunk, then
-// writes each entry with one product.
-constexpr int kOutPerThread = 64;    // out-factor entries per thread (a block's chunk)
+// for two-qubit gates with one qubit in the window).  A block takes a run of
+// y (entries [y 2^L (m + 1), (y + 1) 2^L (m + 1)) each), builds Tlo over every
+// x (the diagonal of a folded in) and Thi over its y, and each thread keeps
+// one column c = x (m + 1) + a of the run's rows: one product per entry,
+// the warps' stores contiguous.
 constexpr int kOutLoBits = 6;        // bits of o in Tlo
+constexpr int kOutEntries = 16384;   // out-factor entries per block (at least one row of y)
 
-// entries of Thi a block of 256 threads needs at most, per attach
-inline int out_table_ny(int obits, int m) {
-  const uint64_t span = 256ull * kOutPerThread, A = (uint64_t)m + 1;
+// rows of y per block (the Thi entries per attach a block needs)
+inline int out_table_rows(int obits, int m) {
   const int L = obits < kOutLoBits ? obits : kOutLoBits;
-  const uint64_t ny = ((((span - 1) / A) + 1) >> L) + 2;
-  const uint64_t all = 1ull << (obits - L);
-  return (int)(ny < all ? ny : all);
+  const int row = (m + 1) << L;
+  const int rows = kOutEntries / row > 1 ? kOutEntries / row : 1;
+  const int all = 1 << (obits - L);
+  return rows < all ? rows : all;
 }
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_out_table(cplx<R>* __restrict__ tab, const R* __restrict__ params, int stride,
                                                    const OutTerm* __restrict__ outs, OutStarts starts, int diag_off,
-                                                   int obits, int wstart, uint32_t chunks, int m, int ny_max) {
-  // shared: the member's terms (masks, factors, classes), Tlo[m + 1][2^L], Thi[m + 1][ny_max]
+                                                   int obits, int wstart, uint32_t chunks, int m, int rows) {
+  // shared: the member's terms (masks, factors, classes), Tlo[m + 1][2^L], Thi[m + 1][rows]
   extern __shared__ unsigned char ot_sm[];
   const int nterms = starts.v[m + 1];
   const int A = m + 1;
@@ -460,9 +462,8 @@ __global__ void __launch_bounds__(256) k_out_table(cplx<R>* __restrict__ tab, co
   cplx<R>* fac = reinterpret_cast<cplx<R>*>(masks + ((nterms + 1) & ~1));   // 16-byte aligned
   cplx<R>* tlo = fac + nterms;
   cplx<R>* thi = tlo + A * nx;
-  unsigned char* cls = reinterpret_cast<unsigned char*>(thi + A * ny_max);
+  unsigned char* cls = reinterpret_cast<unsigned char*>(thi + A * rows);
   const uint64_t b = blockIdx.x / chunks;
-  const uint64_t per = (uint64_t)A << obits;
   const R* P = params + b * (uint64_t)stride;
   // member-local out-of-window bits of o: the wstart bits below the window,
   // then the bits above it
@@ -480,12 +481,10 @@ __global__ void __launch_bounds__(256) k_out_table(cplx<R>* __restrict__ tab, co
     straddle |= c == 2;
   }
   straddle = __syncthreads_or(straddle);
-  // the block's chunk of the member's entries and the y it covers
-  const uint64_t span = (uint64_t)blockDim.x * kOutPerThread;
-  const uint64_t i0 = (uint64_t)(blockIdx.x % chunks) * span;
-  const uint64_t i1 = i0 + span < per ? i0 + span : per;
-  const uint64_t y0 = (i0 / A) >> L;
-  const int ny = (int)((((i1 - 1) / A) >> L) - y0 + 1);   // <= ny_max (out_table_ny)
+  // the block's rows of y
+  const uint64_t y0 = (uint64_t)(blockIdx.x % chunks) * rows;
+  const uint64_t ycount = 1ull << (obits - L);
+  const int ny = (int)(y0 + rows < ycount ? rows : ycount - y0);
   auto term_product = [&](int a, int want, uint64_t fixed, R re, R im) {
     for (int k = sv[a]; k < sv[a + 1]; ++k) {
       if (cls[k] == want && (fixed & masks[k]) == masks[k]) {
@@ -504,25 +503,21 @@ __global__ void __launch_bounds__(256) k_out_table(cplx<R>* __restrict__ tab, co
       tlo[a * nx + u] = term_product(a, 0, expand((uint64_t)u), d, R(0));
     } else {
       const int yy = u - nx;
-      thi[a * ny_max + yy] = term_product(a, 1, expand((y0 + yy) << L), R(1), R(0));
+      thi[a * rows + yy] = term_product(a, 1, expand((y0 + yy) << L), R(1), R(0));
     }
   }
   __syncthreads();
-  // entry i = o (m + 1) + a of the member: o and a stepped along with i
-  // (no division per entry)
-  const uint32_t step = blockDim.x, dq = step / A, dr = step % A;
-  uint64_t i = i0 + threadIdx.x;
-  uint64_t o = i / (uint64_t)A;
-  uint32_t a = (uint32_t)(i % (uint64_t)A);
-  cplx<R>* dst = tab + b * per;
-  for (; i < i1; i += step) {
-    const cplx<R> x = tlo[a * nx + (uint32_t)(o & (nx - 1))], y = thi[a * ny_max + (uint32_t)((o >> L) - y0)];
-    cplx<R> v = mk<R>(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x);
-    if (straddle) v = term_product((int)a, 2, expand(o), v.x, v.y);
-    dst[i] = v;
-    o += dq;
-    a += dr;
-    if (a >= (uint32_t)A) { a -= A; ++o; }
+  const int row = A * nx;
+  cplx<R>* dst = tab + (b << obits) * A + y0 * row;
+  for (int c = threadIdx.x; c < row; c += blockDim.x) {
+    const int x = c / A, a = c % A;
+    const cplx<R> t = tlo[a * nx + x];
+    for (int yy = 0; yy < ny; ++yy) {
+      const cplx<R> h = thi[a * rows + yy];
+      cplx<R> v = mk<R>(t.x * h.x - t.y * h.y, t.x * h.y + t.y * h.x);
+      if (straddle) v = term_product(a, 2, expand(((y0 + yy) << L) | (uint64_t)x), v.x, v.y);
+      dst[(uint64_t)yy * row + c] = v;
+    }
   }
 }
 
@@ -1250,15 +1245,14 @@ cudaError_t launch_precompute(qs_plan p, const PassPlan& P, cudaStream_t s) {
     for (int i = 0; i < kMaxWin + 2; ++i) st.v[i] = P.out_start[i];
     const int obits = h->n - P.m;
     const int nterms = P.out_start[P.m + 1];
-    const uint64_t span = 256ull * kOutPerThread;
-    const uint32_t chunks = (uint32_t)((((uint64_t)(P.m + 1) << obits) + span - 1) / span);
     const int L = obits < kOutLoBits ? obits : kOutLoBits;
-    const int ny_max = out_table_ny(obits, P.m);
+    const int rows = out_table_rows(obits, P.m);
+    const uint32_t chunks = (uint32_t)(((1ull << (obits - L)) + rows - 1) / rows);
     const size_t sm = (size_t)((nterms + 1) & ~1) * sizeof(uint64_t) +
-                      ((size_t)nterms + (size_t)(P.m + 1) * ((1u << L) + ny_max)) * sizeof(cplx<R>) + nterms;
+                      ((size_t)nterms + (size_t)(P.m + 1) * ((1u << L) + rows)) * sizeof(cplx<R>) + nterms;
     k_out_table<R><<<(unsigned)(chunks * (uint64_t)h->batch), 256, sm, s>>>(
         (cplx<R>*)P.d_alpha, (const R*)P.d_params, P.stride, P.d_outs, st, P.diag_off, obits, P.win[0], chunks, P.m,
-        ny_max);
+        rows);
   }
   return cudaGetLastError();
 }
