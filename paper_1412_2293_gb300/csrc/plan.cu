@@ -347,10 +347,11 @@ __global__ void __launch_bounds__(128) k_precompute(R* __restrict__ params, int 
     // tables T[x] = prod_{q in x} f[q] over the bits of a part (a table is
     // one part over bits [0, j) or two, [0, sh) then [sh, j)), by doubling in
     // FP64: T[x + 2^q] = T[x] f[q] for x < 2^q, one complex product per
-    // entry.  A warp-wide FP64 instruction costs the same with 1 or 32 lanes
-    // busy, so the first kSmallBits levels of all parts run together (the
-    // parts sorted by size, a level's items spread over warps 1-3); each
-    // larger part then finishes its levels in one warp.  Written in R.
+    // entry.  Level q of one part has 2^q items, so the first kSmallBits
+    // levels of a part alone would issue FP64 instructions with few lanes
+    // busy: those levels run for all parts together (the parts sorted by
+    // size, a level's items spread over warps 1-3), and each larger part
+    // then finishes its levels in one warp.  Written in R.
     const int u = tid - 32, lane = tid & 31, wq = (tid >> 5) - 1;
     auto slot_bits = [&](int sl) {
       const Producer& p = sp[num_dense + (sl >> 1)];
