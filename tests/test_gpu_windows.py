@@ -143,3 +143,43 @@ def test_qft_n28_three_passes():
         assert np.abs(f - 1.0).max() < 1e-4
     finally:
         qs.qs_destroy(h)
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
+def test_out_terms_spanning_both_halves_of_the_out_factor_index(dtype):
+    # n = 18: the first dense gate, H(8), puts the first pass on the window
+    # [0, 10); its out-factor index holds qubits 10..17, split into 10..15 and
+    # 16..17.  The controlled phases at the start act before any gate the pass
+    # skips, so it takes those outside the window as out terms: CP(12, 17),
+    # CP(10, 16), CP(15, 16) have one qubit in each half, CP(10, 11) and
+    # CP(16, 17) lie in one half, CP(3, 16) and CP(5, 14) attach to a window
+    # bit.  Later passes take the rest.
+    n, batch, e = 18, 2, 0.05
+    ops = [inputs.Op("CP", (2, 7), theta=0.7, noisy=True), inputs.Op("CP", (12, 17), theta=1.9, noisy=True),
+           inputs.Op("CP", (10, 16), theta=2.6, noisy=False), inputs.Op("CP", (15, 16), theta=0.4, noisy=True),
+           inputs.Op("CP", (10, 11), theta=1.1, noisy=True), inputs.Op("CP", (16, 17), theta=2.2, noisy=True),
+           inputs.Op("CP", (3, 16), theta=0.8, noisy=True), inputs.Op("CP", (5, 14), theta=1.4, noisy=True)]
+    ops += [inputs.Op("H", (q,), noisy=True) for q in range(8, n)]
+    ops += [inputs.Op("CP", (9, 15), theta=0.9, noisy=True), inputs.Op("CP", (6, 13), theta=1.3, noisy=True)]
+    ops += [inputs.Op("H", (q,), noisy=True) for q in range(0, 10)]
+    ops += [inputs.Op("CP", (2, 5), theta=0.5, noisy=True), inputs.Op("CP", (4, 12), theta=1.7, noisy=True)]
+    x0 = 0b101101110010111011
+    h = qs.qs_create(n, batch, 0, qs.QS_STATEVEC, dtype)
+    try:
+        qs.qs_set_basis_state(h, x0)
+        p = qs.qs_plan_create(h, pcirc.to_gates(ops))
+        qs.qs_plan_run(p, e, SEED, 9, h)
+        qs.qs_plan_destroy(p)
+        got = qs.qs_get_state(h).reshape(batch, -1)
+    finally:
+        qs.qs_destroy(h)
+    tol = 1e-12 if dtype == qs.QS_C128 else 2e-5
+    for b in range(batch):
+        psi = osv.basis_state(n, x0)
+        for g, op in enumerate(ops):
+            U = ocirc.op_unitary(op)
+            if op.noisy:
+                xa, xb = ophilox.normal_pair(SEED, b, 9 + g)
+                U = ogates.noisy_unitary(U, ocirc.op_noise(op), e, xa, xb)
+            psi = osv.apply_gate(psi, n, ocirc.op_targets(op), U)
+        assert np.abs(got[b] - psi).max() < tol * np.abs(psi).max() * 10
